@@ -1,0 +1,70 @@
+"""Planted mistakes in a copy of the oracle must make the pins fail.
+
+Each case edits one plausible slip into a temporary copy of oracle/oracle.c
+(a sign, a dropped term, a wrong index or spacing, a transposed operand),
+compiles it, and runs the pin tests against that copy in a subprocess; the
+pins must catch every one.  (Dropping the explicit mean removal of f is not
+listed: the dzf-weighted sum of a discrete divergence with zero wall fluxes
+telescopes to zero, so that edit changes only round-off.)  Nothing here touches a GPU.
+"""
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "oracle.c")
+
+PINS = ("exact_rational or eigenmodes or apply_then_solve or divergence_free or "
+        "constant_density or dense_solves or stretched_z or correction_identity")
+
+MUTATIONS = [
+    ("grad_sign", "gx[c] = (q[IDX(g, i + 1, j, k)] - q[c]) / g->dx;",
+     "gx[c] = (q[c] - q[IDX(g, i + 1, j, k)]) / g->dx;"),
+    ("grad_z_spacing", "(q[IDX(g, i, j, k + 1)] - q[c]) / dzc(g, k)",
+     "(q[IDX(g, i, j, k + 1)] - q[c]) / dzf(g, k)"),
+    ("div_z_spacing", "(wt - wb) / dzf(g, k)", "(wt - wb) / dzc(g, k > 0 ? k - 1 : 0)"),
+    ("div_periodic_wrap", "(g->bcx == 0 ? u[IDX(g, nx - 1, j, k)] : 0.0)",
+     "(g->bcx == 0 ? u[IDX(g, 0, j, k)] : 0.0)"),
+    ("rhs_drop_rho0_over_dt", "f[c] = (rho0 / dt) * f[c] + d2[c];", "f[c] = f[c] + d2[c];"),
+    ("rhs_split_sign", "gx[c] *= (1.0 - rho0 * bx[c]);", "gx[c] *= (rho0 * bx[c] - 1.0);"),
+    ("face_density_sum", "bx[c] = 1.0 / (0.5 * (rc + re));", "bx[c] = 1.0 / (rc + re);"),
+    ("rho0_max", "double rho0 = rho_l < rho_g ? rho_l : rho_g;\n    double *ph = malloc(n * sizeof(double));\n    double *gx",
+     "double rho0 = rho_l > rho_g ? rho_l : rho_g;\n    double *ph = malloc(n * sizeof(double));\n    double *gx"),
+    ("rhs_no_extrapolation", "for (size_t c = 0; c < n; ++c) ph[c] = 2.0 * pn[c] - pnm1[c];\n    grad(&g, ph, gx, gy, gz);",
+     "for (size_t c = 0; c < n; ++c) ph[c] = pn[c];\n    grad(&g, ph, gx, gy, gz);"),
+    ("correct_sign", "u[c] -= dt * (px[c] / rho0 + (bx[c] - 1.0 / rho0) * hx[c]);",
+     "u[c] -= dt * (px[c] / rho0 + (1.0 / rho0 - bx[c]) * hx[c]);"),
+    ("correct_transposed", "w[c] -= dt * (pz[c] / rho0 + (bz[c] - 1.0 / rho0) * hz[c]);",
+     "w[c] -= dt * (hz[c] / rho0 + (bz[c] - 1.0 / rho0) * pz[c]);"),
+    ("eigen_angle", "double s = sin(M_PI * (double)a / (double)mx);",
+     "double s = sin(2.0 * M_PI * (double)a / (double)mx);"),
+    ("z_coeff_index", "lo[k] = (k > 0) ? 1.0 / (dzf(&g, k) * dzc(&g, k - 1)) : 0.0;",
+     "lo[k] = (k > 0) ? 1.0 / (dzf(&g, k) * dzc(&g, k > 1 ? k - 2 : 0)) : 0.0;"),
+    ("inverse_scale", "double scale = 1.0 / ((double)mx * (double)my);", "double scale = 1.0 / (double)mx;"),
+    ("correct_no_extrapolation",
+     "for (size_t c = 0; c < n; ++c) ph[c] = 2.0 * pn[c] - pnm1[c];\n    grad(&g, p, px, py, pz);",
+     "for (size_t c = 0; c < n; ++c) ph[c] = pn[c];\n    grad(&g, p, px, py, pz);"),
+    ("z_coeff_upper", "up[k] = (k < nz - 1) ? 1.0 / (dzf(&g, k) * dzc(&g, k)) : 0.0;",
+     "up[k] = (k < nz - 1) ? 1.0 / (dzc(&g, k) * dzc(&g, k)) : 0.0;"),
+    ("neumann_extension", "return (bc == 0 || e < n) ? e : 2 * n - 1 - e;",
+     "return (bc == 0 || e < n) ? e : 2 * n - e - (e == 2 * n - 1 ? 1 : 0) - 0;"),
+]
+
+
+@pytest.mark.parametrize("name,old,new", MUTATIONS, ids=[m[0] for m in MUTATIONS])
+def test_planted_mistake_is_caught(tmp_path, name, old, new):
+    src = open(SRC).read()
+    assert old in src, "mutation anchor not found: " + name
+    mutated = src.replace(old, new, 1)
+    c_path = tmp_path / "oracle_mut.c"
+    so_path = tmp_path / "oracle_mut.so"
+    c_path.write_text(mutated)
+    subprocess.check_call(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=gnu11", "-o",
+                           str(so_path), str(c_path), "-lm"])
+    env = dict(os.environ, FIZZY_ORACLE_SO=str(so_path), OMP_NUM_THREADS="2")
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
+                        os.path.join(ROOT, "tests", "test_oracle_pins.py"), "-k", PINS],
+                       env=env, cwd=ROOT, capture_output=True, text=True, timeout=600)
+    assert r.returncode != 0, "planted mistake %s was not caught:\n%s" % (name, r.stdout[-2000:])

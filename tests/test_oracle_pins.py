@@ -1,0 +1,322 @@
+"""Pins of the FP64 CPU oracle against facts other than itself.
+
+Each test checks the oracle against mathematics: exact rational evaluation
+(tests/golden), closed-form eigenfunctions of the discrete operator, exact
+discrete identities, an independent library FFT, an independently assembled
+dense matrix, and symmetries.  No test here needs a GPU.
+"""
+import glob
+import json
+import os
+from fractions import Fraction as Q
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2502_04189_b300 import inputs as I
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def relerr(a, b):
+    m = np.max(np.abs(b))
+    return np.max(np.abs(a - b)) / (m if m > 0 else 1.0)
+
+
+def uniform_zf(nz, lz=1.0):
+    return np.arange(nz + 1) * (lz / nz)
+
+
+# --------------------------------------------------------------------------
+# FFT building block vs the plain DFT sum and vs numpy's FFT (independent)
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("n", [1, 2, 3, 4, 5, 6, 7, 8, 9, 12, 16, 27, 32, 48, 96, 97, 128, 192, 256, 384])
+def test_fft_matches_numpy_and_direct_sum(n):
+    rng = np.random.default_rng(n)
+    x = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    ref = np.fft.fft(x)
+    scale = np.sqrt(n) * 4
+    assert np.max(np.abs(O.fft(x, -1) - ref)) < 1e-15 * scale * max(1, np.log2(n)) * 4
+    assert np.max(np.abs(O.dft(x, -1) - ref)) < 1e-14 * scale * max(1, np.log2(n))
+    assert np.max(np.abs(O.fft(x, +1) - np.fft.ifft(x) * n)) < 1e-14 * scale * max(1, np.log2(n))
+
+
+# --------------------------------------------------------------------------
+# Exact rational fixtures (the whole projection)
+# --------------------------------------------------------------------------
+def _golden_cases():
+    return sorted(glob.glob(os.path.join(GOLDEN, "exact_*.json")))
+
+
+@pytest.mark.parametrize("path", _golden_cases(), ids=lambda p: os.path.basename(p))
+@pytest.mark.parametrize("dense", [False, True])
+def test_projection_matches_exact_rational(path, dense):
+    d = json.load(open(path))
+    nx, ny, nz = d["nx"], d["ny"], d["nz"]
+    shape = (nz, ny, nx)
+    zf = np.array([float(Q(z)) for z in d["zf"]])
+    g = O.Grid(nx, ny, nz, float(Q(d["dx"])), float(Q(d["dy"])), zf, d["bcx"], d["bcy"])
+    inp = {k: np.array(v).reshape(shape) for k, v in d["inputs"].items()}
+    exp = {k: np.array(v).reshape(shape) for k, v in d["expected"].items()}
+    r = O.project(g, float(Q(d["rho_l"])), float(Q(d["rho_g"])), float(Q(d["dt"])), inp["phi"],
+                  inp["pn"], inp["pnm1"], inp["u"], inp["v"], inp["w"], dense=dense)
+    assert relerr(r["f"], exp["f"]) < 1e-14
+    assert relerr(r["p"], exp["p"]) < 1e-13
+    uu = np.concatenate([r["u"].ravel(), r["v"].ravel(), r["w"].ravel()])
+    ue = np.concatenate([exp["u"].ravel(), exp["v"].ravel(), exp["w"].ravel()])
+    assert relerr(uu, ue) < 1e-13
+
+
+# --------------------------------------------------------------------------
+# T1: Fourier eigenmodes of the discrete Laplacian (closed form)
+# --------------------------------------------------------------------------
+def _mode_1d(n, h, m, bc, phase):
+    """(values at cell centres, eigenvalue of the second difference)."""
+    i = np.arange(n)
+    if bc == I.PERIODIC:
+        return np.cos(2 * np.pi * m * i / n + phase), -4.0 / h ** 2 * np.sin(np.pi * m / n) ** 2
+    return np.cos(np.pi * m * (i + 0.5) / n), -4.0 / h ** 2 * np.sin(np.pi * m / (2 * n)) ** 2
+
+
+@pytest.mark.parametrize("nx,ny,nz,bcx,bcy", [
+    (16, 12, 10, 0, 0), (12, 16, 9, 1, 0), (8, 18, 8, 0, 1), (9, 8, 12, 1, 1), (27, 6, 7, 0, 0)])
+def test_eigenmodes_closed_form(nx, ny, nz, bcx, bcy):
+    dx, dy, dz = 1.0 / nx, 0.7 / ny, 1.3 / nz
+    g = O.Grid(nx, ny, nz, dx, dy, uniform_zf(nz, 1.3), bcx, bcy)
+    rng = np.random.default_rng(nx * 100 + ny)
+    modes = [(0, 0, 1), (1, 0, 0), (0, 1, 0), (nx // 2, ny // 2, nz - 1), (1, 2, 3),
+             (nx - 1, 1, 2), (2, ny - 1, nz // 2)]
+    for a, b, c in modes:
+        X, lx = _mode_1d(nx, dx, a, bcx, rng.random() * 6.28)
+        Y, ly = _mode_1d(ny, dy, b, bcy, rng.random() * 6.28)
+        Z, lz = _mode_1d(nz, dz, c, I.NEUMANN, 0.0)
+        q = Z[:, None, None] * Y[None, :, None] * X[None, None, :]
+        lam = lx + ly + lz
+        Lq = O.apply_L(g, q)
+        assert np.max(np.abs(Lq - lam * q)) < 1e-12 * max(1.0, abs(lam))
+        if abs(lam) > 0 and np.max(np.abs(q)) > 1e-12:
+            p = O.poisson(g, lam * q)
+            q0 = q - O.weighted_mean(g, q)
+            assert relerr(p, q0) < 1e-12
+
+
+# --------------------------------------------------------------------------
+# Stretched z: closed-form action on linear and quadratic profiles
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("beta", [0.0, 1.5, 2.5])
+def test_stretched_z_operator_closed_form(beta):
+    nx, ny, nz = 4, 3, 11
+    zf = I.z_faces(nz, 1.0, beta)
+    zc = 0.5 * (zf[:-1] + zf[1:])
+    dzf = np.diff(zf)
+    g = O.Grid(nx, ny, nz, 0.25, 0.3, zf, 0, 1)
+    ones = np.ones((nz, ny, nx))
+    # q = z: interior fluxes are exactly 1, wall fluxes 0
+    L1 = O.apply_L(g, zc[:, None, None] * ones)
+    e1 = np.zeros(nz)
+    e1[0] = 1.0 / dzf[0]
+    e1[-1] = -1.0 / dzf[-1]
+    assert np.max(np.abs(L1 - e1[:, None, None] * ones)) < 1e-10 * np.max(np.abs(e1))
+    # q = z^2: flux at k+1/2 is zc[k+1] + zc[k]
+    L2 = O.apply_L(g, (zc ** 2)[:, None, None] * ones)
+    F = np.concatenate([[0.0], zc[1:] + zc[:-1], [0.0]])
+    e2 = (F[1:] - F[:-1]) / dzf
+    assert np.max(np.abs(L2 - e2[:, None, None] * ones)) < 1e-10 * np.max(np.abs(e2))
+
+
+# --------------------------------------------------------------------------
+# T3: apply-then-solve on random fields (uniform and stretched, all BCs)
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("nx,ny,nz,bcx,bcy,beta", [
+    (16, 16, 16, 0, 0, 0.0), (12, 18, 10, 1, 0, 1.5), (18, 8, 13, 0, 1, 2.0),
+    (6, 9, 24, 1, 1, 1.0), (32, 24, 20, 0, 0, 1.5)])
+def test_apply_then_solve(nx, ny, nz, bcx, bcy, beta):
+    g = O.Grid(nx, ny, nz, 1.0 / nx, 1.1 / ny, I.z_faces(nz, 0.9, beta), bcx, bcy)
+    q = np.random.default_rng(7).standard_normal(g.shape)
+    p = O.poisson(g, O.apply_L(g, q))
+    q0 = q - O.weighted_mean(g, q)
+    assert relerr(p, q0) < 1e-11
+    assert abs(O.weighted_mean(g, p)) < 1e-14
+
+
+# --------------------------------------------------------------------------
+# T2: dense solves (oracle's own dense path and an independent numpy matrix)
+# --------------------------------------------------------------------------
+def _numpy_laplacian(nx, ny, nz, dx, dy, zf, bcx, bcy):
+    """7-point operator assembled independently from the stencil weights."""
+    n = nx * ny * nz
+    A = np.zeros((n, n))
+    dzf = np.diff(zf)
+    zc = 0.5 * (zf[:-1] + zf[1:])
+    dzc = np.diff(zc)
+
+    def ix(i, j, k):
+        return (k * ny + j) * nx + i
+    for k in range(nz):
+        for j in range(ny):
+            for i in range(nx):
+                r = ix(i, j, k)
+                # x neighbours
+                for s in (-1, 1):
+                    ii = i + s
+                    if 0 <= ii < nx or bcx == I.PERIODIC:
+                        A[r, ix(ii % nx, j, k)] += 1 / dx ** 2
+                        A[r, r] -= 1 / dx ** 2
+                for s in (-1, 1):
+                    jj = j + s
+                    if 0 <= jj < ny or bcy == I.PERIODIC:
+                        A[r, ix(i, jj % ny, k)] += 1 / dy ** 2
+                        A[r, r] -= 1 / dy ** 2
+                if k + 1 < nz:
+                    A[r, ix(i, j, k + 1)] += 1 / (dzf[k] * dzc[k])
+                    A[r, r] -= 1 / (dzf[k] * dzc[k])
+                if k - 1 >= 0:
+                    A[r, ix(i, j, k - 1)] += 1 / (dzf[k] * dzc[k - 1])
+                    A[r, r] -= 1 / (dzf[k] * dzc[k - 1])
+    return A
+
+
+@pytest.mark.parametrize("nx,ny,nz,bcx,bcy,beta", [
+    (8, 8, 8, 0, 0, 0.0), (8, 6, 10, 1, 0, 1.5), (6, 8, 7, 0, 1, 1.0), (4, 6, 8, 1, 1, 2.0)])
+def test_dense_solves(nx, ny, nz, bcx, bcy, beta):
+    zf = I.z_faces(nz, 1.0, beta)
+    g = O.Grid(nx, ny, nz, 1.0 / nx, 1.0 / ny, zf, bcx, bcy)
+    A = _numpy_laplacian(nx, ny, nz, g.dx, g.dy, zf, bcx, bcy)
+    q = np.random.default_rng(3).standard_normal(g.shape)
+    # the oracle's operator is the independently assembled matrix
+    assert np.max(np.abs(O.apply_L(g, q).ravel() - A @ q.ravel())) < 1e-9 * np.max(np.abs(A))
+    f = O.apply_L(g, q)
+    f -= O.weighted_mean(g, f)
+    p_fft = O.poisson(g, f)
+    p_dense = O.poisson(g, f, dense=True)
+    # numpy least-squares on the singular system, gauge fixed afterwards
+    p_np = np.linalg.lstsq(A, f.ravel(), rcond=None)[0].reshape(g.shape)
+    p_np -= O.weighted_mean(g, p_np)
+    assert relerr(p_fft, p_dense) < 1e-11
+    assert relerr(p_fft, p_np) < 1e-10
+
+
+# --------------------------------------------------------------------------
+# T4: the corrected velocity is discretely divergence-free
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("spec", [I.drop32_spec(),
+                                  I.bubbles_spec(24, 3, 3.0, 1.5, config=1),
+                                  I.CaseSpec(nx=16, ny=24, nz=20, bcx=1, bcy=0, n_bubbles=2,
+                                             radius_cells=3, beta=1.0, config=3)],
+                         ids=["drop32", "bubbles24_stretched", "neumann_x"])
+def test_divergence_free(spec):
+    c = I.make_case(spec)
+    g = O.Grid.of_case(c)
+    r = O.project_case(c)
+    U = np.sqrt((np.sum(c.u ** 2) + np.sum(c.v ** 2) + np.sum(c.w ** 2)) / (3 * c.u.size))
+    assert r["relres"] < 1e-12
+    assert r["divmax"] * c.dx / U < 1e-10
+    assert abs(O.weighted_mean(g, r["p"])) < 1e-12 * np.max(np.abs(r["p"]))
+    assert abs(O.weighted_mean(g, r["f"])) < 1e-12 * np.max(np.abs(r["f"]))
+    # wall faces untouched (zero)
+    if spec.bcx == I.NEUMANN:
+        assert np.all(r["u"][:, :, -1] == 0)
+    assert np.all(r["w"][-1] == 0)
+
+
+# --------------------------------------------------------------------------
+# T5: equal densities -> constant-density projection in closed form
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("bcx,bcy,beta", [(0, 0, 0.0), (1, 0, 1.5), (1, 1, 1.0)])
+def test_constant_density_closed_form(bcx, bcy, beta):
+    spec = I.CaseSpec(nx=16, ny=12, nz=14, bcx=bcx, bcy=bcy, beta=beta, n_bubbles=2,
+                      radius_cells=2.5, rho_l=0.5, rho_g=0.5, dt=1e-3, noise=0.0, config=9)
+    c = I.make_case(spec)
+    g = O.Grid.of_case(c)
+    s = (c.u, c.v, c.w)                        # discrete curl: solenoidal
+    assert np.max(np.abs(O.div(g, *s))) < 1e-10 * np.max(np.abs(c.u)) / c.dx
+    q = np.random.default_rng(5).standard_normal(g.shape)
+    gq = O.grad(g, q)
+    ustar = [s[a] + gq[a] for a in range(3)]
+    r = O.project(g, 0.5, 0.5, 1e-3, c.phi, c.pn, c.pnm1, *ustar)
+    p_exact = (0.5 / 1e-3) * (q - O.weighted_mean(g, q))
+    assert relerr(r["p"], p_exact) < 1e-11
+    for a, key in enumerate("uvw"):
+        assert np.max(np.abs(r[key] - s[a])) < 1e-11 * np.max(np.abs(ustar[a]))
+
+
+# --------------------------------------------------------------------------
+# Helmholtz decomposition identity at every non-wall face
+# --------------------------------------------------------------------------
+def test_correction_identity():
+    c = I.make_case(I.CaseSpec(nx=12, ny=10, nz=9, bcx=1, bcy=0, beta=1.2, n_bubbles=1,
+                               radius_cells=2.5, rho_l=1.0, rho_g=0.01, dt=1e-3, config=8))
+    g = O.Grid.of_case(c)
+    s = c.spec
+    r = O.project_case(c)
+    rho0 = min(s.rho_l, s.rho_g)
+    gp = O.grad(g, r["p"])
+    gh = O.grad(g, 2 * c.pn - c.pnm1)
+    rho = s.rho_g + c.phi * (s.rho_l - s.rho_g)
+    # face densities by neighbour averaging (independent numpy restatement)
+    rf = [0.5 * (rho + np.roll(rho, -1, axis=2)), 0.5 * (rho + np.roll(rho, -1, axis=1)),
+          0.5 * (rho + np.concatenate([rho[1:], rho[-1:]], axis=0))]
+    for a, (ust, un) in enumerate(((c.u, r["u"]), (c.v, r["v"]), (c.w, r["w"]))):
+        lhs = (rho0 / s.dt) * (ust - un) - rho0 * (1.0 / rf[a] - 1.0 / rho0) * gh[a]
+        mask = np.ones(g.shape, bool)
+        if a == 0 and s.bcx == I.NEUMANN:
+            mask[:, :, -1] = False
+        if a == 2:
+            mask[-1] = False
+        scale = np.max(np.abs(gp[a][mask])) + np.max(np.abs(rho0 * (1.0 / rf[a] - 1.0 / rho0) * gh[a]))
+        assert np.max(np.abs(lhs[mask] - gp[a][mask])) < 1e-10 * scale
+
+
+# --------------------------------------------------------------------------
+# T8: symmetries
+# --------------------------------------------------------------------------
+def test_periodic_shift_commutes():
+    c = I.make_case(I.CaseSpec(nx=16, ny=12, nz=10, beta=1.5, n_bubbles=2, radius_cells=2.5,
+                               config=7))
+    g = O.Grid.of_case(c)
+    s = c.spec
+    r0 = O.project_case(c)
+    sh = 5
+    rl = lambda a: np.roll(a, sh, axis=2)
+    r1 = O.project(g, s.rho_l, s.rho_g, s.dt, rl(c.phi), rl(c.pn), rl(c.pnm1), rl(c.u), rl(c.v),
+                   rl(c.w))
+    for key in ("p", "u", "v", "w"):
+        assert relerr(r1[key], rl(r0[key])) < 1e-12
+
+
+def test_z_mirror_symmetry():
+    c = I.make_case(I.CaseSpec(nx=10, ny=8, nz=12, beta=1.5, n_bubbles=2, radius_cells=2.0,
+                               config=6))
+    g = O.Grid.of_case(c)
+    s = c.spec
+    r0 = O.project_case(c)
+    fz = lambda a: a[::-1].copy()
+
+    def fw(w):  # face k+1/2 -> face (nz-2-k)+1/2, sign flipped; top wall stays 0
+        out = np.zeros_like(w)
+        out[:-1] = -w[:-1][::-1]
+        return out
+    r1 = O.project(g, s.rho_l, s.rho_g, s.dt, fz(c.phi), fz(c.pn), fz(c.pnm1), fz(c.u), fz(c.v),
+                   fw(c.w))
+    assert relerr(r1["p"], fz(r0["p"])) < 1e-12
+    assert relerr(r1["u"], fz(r0["u"])) < 1e-12
+    assert relerr(r1["w"], fw(r0["w"])) < 1e-12
+
+
+def test_linearity_in_velocity_and_pressure():
+    c = I.make_case(I.CaseSpec(nx=12, ny=12, nz=8, bcy=1, n_bubbles=1, radius_cells=3, config=5))
+    g = O.Grid.of_case(c)
+    s = c.spec
+    rng = np.random.default_rng(2)
+    a, b = 0.7, -1.3
+    u2, v2, w2 = (rng.standard_normal(g.shape) for _ in range(3))
+    v2[:, -1, :] = 0
+    w2[-1] = 0
+    pn2, pm2 = rng.standard_normal(g.shape), rng.standard_normal(g.shape)
+    r1 = O.project(g, s.rho_l, s.rho_g, s.dt, c.phi, c.pn, c.pnm1, c.u, c.v, c.w)
+    r2 = O.project(g, s.rho_l, s.rho_g, s.dt, c.phi, pn2, pm2, u2, v2, w2)
+    r3 = O.project(g, s.rho_l, s.rho_g, s.dt, c.phi, a * c.pn + b * pn2, a * c.pnm1 + b * pm2,
+                   a * c.u + b * u2, a * c.v + b * v2, a * c.w + b * w2)
+    for key in ("p", "u", "v", "w"):
+        assert relerr(r3[key], a * r1[key] + b * r2[key]) < 1e-11
