@@ -1,0 +1,341 @@
+#!/usr/bin/env python3
+"""Benchmark of the variable-density pressure-correction projection on B300.
+
+Metric: grid points per second of one projection (right-hand side, FFT/DCT +
+z-tridiagonal Poisson solve, variable-density correction) on the 256^3
+bubble-laden workload: periodic x/y, walls in z, uniform grid, 40 drops of
+radius 8 cells, density ratio 1000, k^-5/3 solenoidal u* (rms 1) plus 1 %
+noise, two 8-mode pressure fields, dt = 1e-4; FP64 mode (the mixed
+FP32/FP64-refinement mode is reported beside it).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl fizzy|reference]
+
+One JSON line is printed by rank 0.  Under torchrun every rank runs an
+independent replica on its own GPU (the projection does not shard in this
+build), so scaling is weak and value = points of all ranks / max rank time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2502_04189_b300 import inputs as I  # noqa: E402
+
+METRIC = "grid pts/s per projection, mixed vs FP64 at 1e-10 residual; HBM %; p50/p99 ms"
+HBM_PEAK_FALLBACK = 6400.0        # GB/s, recipe fallback
+FP64_PEAK_NOMINAL = 1.25          # TFLOP/s, nominal B300 FP64 (recipe table)
+
+WORKLOADS = {
+    "bubbles256": I.bubbles256_spec,
+    "drop32": I.drop32_spec,
+    "bubbles512_stretched": I.bubbles512_stretched_spec,
+}
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return HBM_PEAK_FALLBACK, "fallback"
+
+
+def algorithmic_per_point(nx, ny, mixed):
+    """Algorithmic HBM bytes and FP64 flops (FMA = 2) per grid point of each
+    kernel of one projection.  Transform passes use the conventional real-FFT
+    count 2.5 log2(n) flops per point (FP64 passes only)."""
+    lx, ly = 2.5 * math.log2(nx), 2.5 * math.log2(ny)
+    if not mixed:
+        return {
+            "flux": (72, 47), "div_fwdx": (32, 8 + lx), "fwd_y": (16, ly), "thomas": (16, 5),
+            "inv_y": (16, ly), "inv_x": (16, lx), "correct": (56, 12)}
+    return {
+        "flux": (72, 47), "div_fwdx": (36, 8), "fwd_y": (8, 0), "thomas": (8, 0), "inv_y": (8, 0),
+        "inv_x": (12, 0), "resid_fwdx": (20, 17), "fwd_y_refine": (8, 0), "thomas_refine": (8, 0),
+        "inv_y_refine": (8, 0), "inv_x_update": (20, 1), "resid_check": (16, 17), "correct": (56, 12)}
+
+
+class ClockSampler:
+    """nvidia-smi clocks/throttle sampling during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self):
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((int(parts[0]), float(parts[1]), float(parts[2]), float(parts[3]), parts[4:]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        # the busiest GPU is ours
+        by_gpu = {}
+        for r in rows:
+            by_gpu.setdefault(r[0], []).append(r)
+        gid = max(by_gpu, key=lambda g: np.mean([r[3] for r in by_gpu[g]]))
+        rs = by_gpu[gid]
+        loaded = [r for r in rs if r[3] > 200.0] or rs
+        names = ["active", "hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in loaded:
+            for nm, val in zip(names[1:], r[4][1:]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median([r[1] for r in loaded])),
+                "sm_max_mhz": float(max(r[2] for r in rs)),
+                "power_w_max": float(max(r[3] for r in rs)),
+                "samples": len(loaded), "reasons": sorted(reasons)}
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def oracle_time(case, reps=1):
+    """Wall time of the CPU oracle's projection on case (rank 0 host cores)."""
+    import oracle as O
+    best = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        O.project_case(case)
+        best.append(time.perf_counter() - t0)
+    return min(best), O.num_threads()
+
+
+def run_reference(args):
+    """The oracle on the host cores: each step = one projection of a 256 x 256 x 32
+    slab drawn with the same recipe (same x/y transform lengths and spacing)."""
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle as O
+    spec = WORKLOADS[args.workload]()
+    sample_spec = I.CaseSpec(**{**spec.__dict__, "nz": min(spec.nz, 32), "lz": spec.lz * min(spec.nz, 32) / spec.nz,
+                                "n_bubbles": max(1, spec.n_bubbles * min(spec.nz, 32) // spec.nz)})
+    case = I.make_case(sample_spec)
+    for _ in range(args.warmup):
+        O.project_case(case)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        O.project_case(case)
+    dt = time.perf_counter() - t0
+    pts = case.npts * args.steps
+    value = pts / dt
+    sample = "%dx%dx%d slab of the %s recipe per step" % (sample_spec.nx, sample_spec.ny, sample_spec.nz,
+                                                          args.workload)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "pts/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": args.workload, "grid": [spec.nx, spec.ny, spec.nz],
+                                             "precision": "fp64", "l2": "inputs larger than L2"},
+            "cpu_baseline": {"value": value, "unit": "pts/s", "cores": O.num_threads(),
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "pts/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_fizzy(args):
+    import torch
+    import paper_2502_04189_b300 as F
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    spec = WORKLOADS[args.workload]()
+    case = I.make_case(spec)
+    npts = case.npts
+    prec = F.MIXED if args.precision == "mixed" else F.FP64
+
+    def dev(a):
+        return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+    phi, pn, pnm1 = dev(case.phi), dev(case.pn), dev(case.pnm1)
+    u, v, w = dev(case.u), dev(case.v), dev(case.w)
+    p = torch.empty_like(phi)
+    stream = torch.cuda.current_stream()
+
+    def timed_run(precision, steps, warmup, per_kernel):
+        plan = F.Plan.for_case(case, precision=precision)
+        for _ in range(warmup):
+            plan.solve(phi, pn, pnm1, u, v, w, p, stream=stream)
+        torch.cuda.synchronize()
+        if per_kernel:
+            plan.set_timing(True)
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            plan.solve(phi, pn, pnm1, u, v, w, p, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        ms = e0.elapsed_time(e1)
+        kern = plan.timing() if per_kernel else {}
+        st = plan.stats(stream)
+        launches = plan.launches_per_solve() * steps
+        plan.close()
+        return ms, kern, st, launches
+
+    clocks = ClockSampler()
+    clocks.start()
+    ms, kern, st, launches = timed_run(prec, args.steps, args.warmup, True)
+    clk = clocks.stop()
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = npts * args.steps * world / (ms / 1e3)
+
+    # the other precision on the same inputs (context for "mixed vs FP64")
+    other = F.FP64 if prec == F.MIXED else F.MIXED
+    ms_o, _, st_o, _ = timed_run(other, max(3, args.steps // 4), args.warmup, False)
+    value_o = npts * max(3, args.steps // 4) / (ms_o / 1e3)
+
+    # roofline of the dominant kernel
+    hbm_peak, hbm_src = measured_peaks()
+    per_pt = algorithmic_per_point(spec.nx, spec.ny, prec == F.MIXED)
+    dom = max(kern, key=lambda k: kern[k][0]) if kern else None
+    roof = None
+    if dom:
+        tot_ms, cnt = kern[dom]
+        avg_s = tot_ms / cnt / 1e3
+        b_pt, fl_pt = per_pt.get(dom, (0, 0))
+        gbs = b_pt * npts / avg_s / 1e9
+        tfl = fl_pt * npts / avg_s / 1e12
+        t_hbm = b_pt / (hbm_peak * 1e9)
+        t_alu = fl_pt / (FP64_PEAK_NOMINAL * 1e12)
+        if t_alu > t_hbm:
+            roof = {"bound": "alu", "achieved": tfl, "peak": FP64_PEAK_NOMINAL, "unit": "TFLOP/s",
+                    "frac": tfl / FP64_PEAK_NOMINAL, "traffic": None, "kernel": dom,
+                    "peak_source": "nominal FP64 (recipe table)",
+                    "hbm_gbs": gbs, "hbm_frac": gbs / hbm_peak}
+        else:
+            roof = {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
+                    "frac": gbs / hbm_peak, "traffic": None, "kernel": dom,
+                    "peak_source": hbm_src}
+    kernels = {k: {"ms_avg": v[0] / v[1], "launches": v[1],
+                   "share": v[0] / max(1e-9, sum(x[0] for x in kern.values()))} for k, v in kern.items()}
+
+    # end-to-end through the public host-buffer entry point
+    e2e = None
+    if args.e2e_steps > 0:
+        plan = F.Plan.for_case(case, precision=prec)
+        hb = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in
+              (case.phi, case.pn, case.pnm1, case.u, case.v, case.w)]
+        hp = torch.empty(case.shape, dtype=torch.float64).pin_memory()
+        for _ in range(2):
+            plan.solve_host(*hb, hp, stream=stream)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            plan.solve_host(*hb, hp, stream=stream)
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        if dist:
+            t = torch.tensor([el], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            el = float(t.item())
+        plan.close()
+        e2e = {"value": npts * args.e2e_steps * world / el, "unit": "pts/s",
+               "h2d_bytes_per_step": 6 * 8 * npts, "d2h_bytes_per_step": 4 * 8 * npts,
+               "ms_per_step": el / args.e2e_steps * 1e3}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        t_or, cores = oracle_time(case, reps=2)
+        cpu = {"value": npts / t_or, "unit": "pts/s", "cores": cores, "kind": "oracle",
+               "sample": "one full %dx%dx%d projection (best of 2)" % (spec.nx, spec.ny, spec.nz)}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "pts/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f64" if prec == F.FP64 else "f32+f64",
+                "data": "synthetic",
+                "config": {"workload": args.workload, "grid": [spec.nx, spec.ny, spec.nz],
+                           "precision": args.precision, "bc": "periodic x,y; walls z",
+                           "l2": "inputs (6 x %d MiB) larger than L2" % (npts * 8 >> 20),
+                           "parallelism": "replicas" if world > 1 else "single"},
+                "gpu_launches": launches, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+                "clocks": clk, "kernels": kernels,
+                "stats": {k: st[k] for k in ("iterations", "converged", "relres")},
+                ("mixed" if other == F.MIXED else "fp64"): {
+                    "value": value_o, "unit": "pts/s", "ms_per_step": ms_o / max(3, args.steps // 4),
+                    "iterations": st_o["iterations"], "relres": st_o["relres"]}}
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="fizzy", choices=["fizzy", "reference"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--workload", default="bubbles256", choices=list(WORKLOADS))
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_fizzy(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,150 @@
+/*
+ * fizzy_proj.h -- C ABI of the B300 (sm_103a) variable-density
+ * pressure-correction projection.
+ *
+ * The operation (CaNS-Fizzy paper, "Methods and Implementation strategy":
+ * second-order finite differences on a staggered Cartesian grid, pressure
+ * correction whose variable-coefficient Poisson equation is turned into a
+ * constant-coefficient one by the Dong & Shen / Dodd & Ferrante splitting of
+ * Frantzis & Grigoriadis, solved by the fast direct FFT solver of CaNS; and
+ * "Mathematical model": density mapped linearly over the phase field):
+ *
+ *   rho    = rho_g + phi (rho_l - rho_g)              (cell centres)
+ *   beta_f = 1 / (mean of the two adjacent centre rho) (faces)
+ *   rho0   = min(rho_l, rho_g),   phat = 2 p^n - p^(n-1)
+ *   f      = (rho0/dt) D(u*) + D[(1 - rho0 beta_f) G phat]   (mean removed)
+ *   D G p  = f      -- real FFT (periodic) or DCT-II (wall) along x and y,
+ *                      one tridiagonal solve per (kx, ky) along z,
+ *                      inverse transforms; p has zero dzf-weighted mean
+ *   u      = u* - dt [G p / rho0 + (beta_f - 1/rho0) G phat]  (non-wall faces)
+ *
+ * G is the centre-to-face gradient, D the face-to-centre divergence.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Arrays are double, C order [nz][ny][nx] (x fastest), caller-owned.
+ *  - Staggering: u[k][j][i] is the x-face i+1/2, v[k][j][i] the y-face j+1/2,
+ *    w[k][j][i] the z-face k+1/2.  z is always wall-bounded (homogeneous
+ *    Neumann p); x and y are periodic or wall-bounded.  In a wall direction
+ *    the last face (i = nx-1, j = ny-1, k = nz-1) is the far wall and must
+ *    hold 0 on input; the near wall face is implicit.  Wall faces are 0 on
+ *    output.
+ *  - "stream" is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Device work is asynchronous on it unless stated otherwise.
+ *  - Return codes: FIZZY_OK (0) or a negative FIZZY_ERR_* value; no entry
+ *    point aborts, exits or traps.  fizzy_proj_errstr() names a code and
+ *    fizzy_proj_last_error() gives the last message recorded on a plan.
+ */
+#ifndef FIZZY_PROJ_H
+#define FIZZY_PROJ_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    FIZZY_OK = 0,
+    FIZZY_ERR_INVALID = -1,       /* bad argument (null pointer, extent < 2, rho <= 0, dt <= 0, ...) */
+    FIZZY_ERR_UNSUPPORTED = -2,   /* nx or ny with a prime factor other than 2 and 3, or too large  */
+    FIZZY_ERR_NOMEM = -3,         /* device allocation failed                                       */
+    FIZZY_ERR_CUDA = -4,          /* a CUDA call failed; message kept on the plan                   */
+    FIZZY_ERR_NOT_CONVERGED = -5, /* mixed mode: refinement stopped above tol (output still written) */
+    FIZZY_ERR_TIMEOUT = -6        /* a bounded device wait gave up (batched executor)               */
+};
+
+enum { FIZZY_BC_PERIODIC = 0, FIZZY_BC_NEUMANN = 1 };
+
+enum {
+    FIZZY_PREC_FP64 = 0,  /* every pass in FP64                                           */
+    FIZZY_PREC_MIXED = 1  /* FP32 transforms + z-solve, refined by FP64 residuals r = f - L p */
+};
+
+/* flags */
+#define FIZZY_FLAG_CHECK 1u /* also compute u_rms, max|D u| and (FP64 mode) relres into the stats */
+
+/* Maximum x/y extent of one transform line. */
+#define FIZZY_MAX_N 1024
+
+/* Plan descriptor.  All fields are read at plan time only. */
+typedef struct fizzy_proj_desc {
+    int nx, ny, nz;       /* cells; nx, ny in [2, FIZZY_MAX_N] with prime factors 2 and 3 only; nz >= 2 */
+    double dx, dy;        /* uniform x and y spacing (> 0)                                     */
+    double dz;            /* uniform z spacing (> 0), used when zf == NULL                      */
+    const double *zf;     /* host array of nz+1 increasing z face coordinates, or NULL          */
+    int bc_x, bc_y;       /* FIZZY_BC_PERIODIC or FIZZY_BC_NEUMANN                              */
+    double rho_l, rho_g;  /* phase densities (> 0, within [1e-30, 1e30]); phi = 1 is rho_l      */
+    double dt;            /* time step (> 0)                                                    */
+    int precision;        /* FIZZY_PREC_FP64 or FIZZY_PREC_MIXED                                */
+    double tol;           /* mixed: stop when max|f - L p| / max|f| <= tol (0 -> 1e-10)         */
+    int max_refine;       /* mixed: at most this many refinement sweeps (0 -> 4, max 16)        */
+    unsigned flags;       /* FIZZY_FLAG_*                                                       */
+} fizzy_proj_desc;
+
+/* Diagnostics of the last solve (host memory). */
+typedef struct fizzy_proj_stats {
+    int iterations;    /* mixed: refinement sweeps run (0 in FP64 mode)                          */
+    int converged;     /* mixed: 1 if relres <= tol; FP64 mode: 1                                */
+    double relres;     /* max|f - L p| / max|f| (mixed always; FP64 only with FIZZY_FLAG_CHECK)  */
+    double f_max;      /* max|f|                                                                 */
+    double div_max;    /* max|D u| over all cells (FIZZY_FLAG_CHECK)                             */
+    double u_rms;      /* rms of u* over all face values (FIZZY_FLAG_CHECK)                      */
+    double div_metric; /* div_max * dx / u_rms (FIZZY_FLAG_CHECK)                                */
+} fizzy_proj_stats;
+
+typedef struct fizzy_proj_plan_s *fizzy_proj_plan_t;
+
+/* Build a plan: validates the descriptor, builds the eigenvalue, twiddle and
+ * z-factorisation tables on the host and allocates all device tables and the
+ * workspace (fizzy_proj_workspace_bytes()).  Grid, densities, dt and precision
+ * are fixed per plan.  Synchronous.  On failure *out is NULL. */
+int fizzy_proj_plan(fizzy_proj_plan_t *out, const fizzy_proj_desc *d, void *stream);
+
+/* Device bytes a plan for d would allocate (tables + workspace), 0 if d is invalid. */
+size_t fizzy_proj_workspace_bytes(const fizzy_proj_desc *d);
+
+/* One projection on device pointers.
+ *   phi, p_n, p_nm1 : in, cell centred.
+ *   u, v, w         : in u* (wall faces 0), out u (overwritten in place).
+ *   p_np1           : out p^(n+1) with zero dzf-weighted mean; must not alias the inputs.
+ *   st              : NULL -> fully asynchronous on stream (graph-capturable);
+ *                     non-NULL host pointer -> the call synchronises the stream and fills it.
+ * Returns FIZZY_ERR_NOT_CONVERGED (outputs still written) only when st is given. */
+int fizzy_proj_solve(fizzy_proj_plan_t p, const double *phi, const double *p_n, const double *p_nm1,
+                     double *u, double *v, double *w, double *p_np1, fizzy_proj_stats *st,
+                     void *stream);
+
+/* Read the stats of the last solve issued on p (synchronises stream). */
+int fizzy_proj_get_stats(fizzy_proj_plan_t p, fizzy_proj_stats *st, void *stream);
+
+/* End-to-end variant on HOST buffers (pinned memory recommended): copies the
+ * six inputs to plan-owned device buffers, solves, copies u, v, w and p back,
+ * and synchronises the stream.  The device staging buffers are allocated on
+ * first use and kept by the plan. */
+int fizzy_proj_solve_host(fizzy_proj_plan_t p, const double *phi, const double *p_n,
+                          const double *p_nm1, double *u, double *v, double *w, double *p_np1,
+                          fizzy_proj_stats *st, void *stream);
+
+/* Free everything owned by the plan; NULL is a no-op.  Synchronises the device. */
+int fizzy_proj_destroy(fizzy_proj_plan_t p);
+
+const char *fizzy_proj_errstr(int code);
+const char *fizzy_proj_last_error(fizzy_proj_plan_t p);
+
+/* Number of kernels one fizzy_proj_solve launches on the plan (for launch accounting). */
+int fizzy_proj_launches_per_solve(fizzy_proj_plan_t p);
+
+/* Per-kernel timing (diagnostics).  While enabled, every kernel launch of a
+ * solve is bracketed by CUDA events recorded on the solve's stream (up to 8192
+ * launches are kept; later ones are not timed).  fizzy_proj_timing() waits for
+ * the recorded events, folds them into per-kernel totals and reports kernel
+ * slot idx: its name, total milliseconds and launch count since the last
+ * reset (enable = 1 resets).  Returns the number of slots, or a negative code. */
+int fizzy_proj_set_timing(fizzy_proj_plan_t p, int enable);
+int fizzy_proj_timing(fizzy_proj_plan_t p, int idx, const char **name, double *ms, int *launches);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FIZZY_PROJ_H */

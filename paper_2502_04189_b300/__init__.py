@@ -1,0 +1,159 @@
+"""B300-native variable-density pressure-correction projection (CaNS-Fizzy hot path).
+
+Python binding of the C ABI in include/fizzy_proj.h.  Every step of the
+projection runs in the CUDA library libfizzyproj.so; this module only
+marshals arguments (torch tensors provide device pointers and streams).
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _abi
+from ._abi import Stats
+
+PERIODIC = 0
+NEUMANN = 1
+FP64 = 0
+MIXED = 1
+FLAG_CHECK = 1
+
+
+class FizzyError(RuntimeError):
+    def __init__(self, code, msg=""):
+        self.code = code
+        super().__init__("fizzy_proj error %d (%s)%s" % (code, _abi.ERRORS.get(code, "?"),
+                                                          ": " + msg if msg else ""))
+
+
+def _stream_handle(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _ptr(t):
+    if t.dtype.__str__() != "torch.float64" or not t.is_contiguous() or not t.is_cuda:
+        raise ValueError("expected a contiguous float64 CUDA tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def make_desc(nx, ny, nz, dx, dy, zf=None, dz=None, bcx=PERIODIC, bcy=PERIODIC, rho_l=1.0,
+              rho_g=1e-3, dt=1e-4, precision=FP64, tol=0.0, max_refine=0, flags=0):
+    d = _abi.Desc()
+    d.nx, d.ny, d.nz = int(nx), int(ny), int(nz)
+    d.dx, d.dy = float(dx), float(dy)
+    keep = None
+    if zf is not None:
+        keep = np.ascontiguousarray(zf, dtype=np.float64)
+        d.zf = keep.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        d.dz = 0.0
+    else:
+        d.dz = float(dz)
+    d.bc_x, d.bc_y = int(bcx), int(bcy)
+    d.rho_l, d.rho_g, d.dt = float(rho_l), float(rho_g), float(dt)
+    d.precision, d.tol, d.max_refine, d.flags = int(precision), float(tol), int(max_refine), int(flags)
+    return d, keep
+
+
+def workspace_bytes(**kw) -> int:
+    d, _keep = make_desc(**kw)
+    return int(_abi.lib().fizzy_proj_workspace_bytes(ctypes.byref(d)))
+
+
+class Plan:
+    """A projection plan (fizzy_proj_plan / fizzy_proj_destroy)."""
+
+    def __init__(self, nx, ny, nz, dx, dy, zf=None, dz=None, bcx=PERIODIC, bcy=PERIODIC,
+                 rho_l=1.0, rho_g=1e-3, dt=1e-4, precision=FP64, tol=0.0, max_refine=0,
+                 check=False, stream=None):
+        self.shape = (int(nz), int(ny), int(nx))
+        self.precision = precision
+        d, keep = make_desc(nx, ny, nz, dx, dy, zf, dz, bcx, bcy, rho_l, rho_g, dt, precision,
+                            tol, max_refine, FLAG_CHECK if check else 0)
+        h = ctypes.c_void_p()
+        rc = _abi.lib().fizzy_proj_plan(ctypes.byref(h), ctypes.byref(d),
+                                        ctypes.c_void_p(0) if stream is None else _stream_handle(stream))
+        del keep
+        if rc != 0:
+            raise FizzyError(rc)
+        self._h = h
+
+    @classmethod
+    def for_case(cls, case, precision=FP64, check=False, **kw):
+        s = case.spec
+        return cls(s.nx, s.ny, s.nz, case.dx, case.dy, zf=case.zf, bcx=s.bcx, bcy=s.bcy,
+                   rho_l=s.rho_l, rho_g=s.rho_g, dt=s.dt, precision=precision, check=check, **kw)
+
+    def _check(self, rc):
+        if rc not in (0, -5):
+            raise FizzyError(rc, _abi.lib().fizzy_proj_last_error(self._h).decode())
+        return rc
+
+    def solve(self, phi, pn, pnm1, u, v, w, p_out, stats=False, stream=None):
+        """One projection on CUDA float64 tensors; u, v, w are overwritten with u.
+        Returns a stats dict if stats=True (synchronises), else None (async)."""
+        st = Stats() if stats else None
+        rc = _abi.lib().fizzy_proj_solve(self._h, _ptr(phi), _ptr(pn), _ptr(pnm1), _ptr(u), _ptr(v),
+                                         _ptr(w), _ptr(p_out), ctypes.byref(st) if st else None,
+                                         _stream_handle(stream))
+        self._check(rc)
+        return st.as_dict() if st else None
+
+    def solve_host(self, phi, pn, pnm1, u, v, w, p_out, stats=False, stream=None):
+        """End-to-end solve on host arrays (numpy or CPU tensors, pinned preferred)."""
+        def hp(a):
+            if hasattr(a, "data_ptr"):
+                return ctypes.c_void_p(a.data_ptr())
+            return ctypes.c_void_p(a.ctypes.data)
+        st = Stats() if stats else None
+        rc = _abi.lib().fizzy_proj_solve_host(self._h, hp(phi), hp(pn), hp(pnm1), hp(u), hp(v),
+                                              hp(w), hp(p_out), ctypes.byref(st) if st else None,
+                                              _stream_handle(stream))
+        self._check(rc)
+        return st.as_dict() if st else None
+
+    def stats(self, stream=None):
+        st = Stats()
+        self._check(_abi.lib().fizzy_proj_get_stats(self._h, ctypes.byref(st), _stream_handle(stream)))
+        return st.as_dict()
+
+    def set_timing(self, enable: bool):
+        self._check(_abi.lib().fizzy_proj_set_timing(self._h, 1 if enable else 0))
+
+    def timing(self):
+        """{kernel name: (total ms, launches)} accumulated since set_timing(True)."""
+        L = _abi.lib()
+        out = {}
+        n = L.fizzy_proj_timing(self._h, -1, None, None, None)
+        self._check(min(n, 0))
+        for idx in range(n):
+            name, ms, cnt = ctypes.c_char_p(), ctypes.c_double(), ctypes.c_int()
+            L.fizzy_proj_timing(self._h, idx, ctypes.byref(name), ctypes.byref(ms), ctypes.byref(cnt))
+            if cnt.value:
+                out[name.value.decode()] = (ms.value, cnt.value)
+        return out
+
+    def launches_per_solve(self) -> int:
+        return int(_abi.lib().fizzy_proj_launches_per_solve(self._h))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _abi.lib().fizzy_proj_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

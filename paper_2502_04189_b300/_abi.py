@@ -1,0 +1,77 @@
+"""ctypes declarations of the C ABI in include/fizzy_proj.h (no logic here)."""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libfizzyproj.so")
+
+FIZZY_OK = 0
+ERRORS = {-1: "invalid argument", -2: "unsupported size", -3: "out of device memory",
+          -4: "CUDA error", -5: "not converged", -6: "device wait timeout"}
+
+# every symbol include/fizzy_proj.h declares
+EXPORTED = ("fizzy_proj_plan", "fizzy_proj_workspace_bytes", "fizzy_proj_solve",
+            "fizzy_proj_get_stats", "fizzy_proj_solve_host", "fizzy_proj_destroy",
+            "fizzy_proj_errstr", "fizzy_proj_last_error", "fizzy_proj_launches_per_solve",
+            "fizzy_proj_set_timing", "fizzy_proj_timing")
+
+
+class Desc(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("dx", ctypes.c_double), ("dy", ctypes.c_double), ("dz", ctypes.c_double),
+                ("zf", ctypes.POINTER(ctypes.c_double)),
+                ("bc_x", ctypes.c_int), ("bc_y", ctypes.c_int),
+                ("rho_l", ctypes.c_double), ("rho_g", ctypes.c_double), ("dt", ctypes.c_double),
+                ("precision", ctypes.c_int), ("tol", ctypes.c_double),
+                ("max_refine", ctypes.c_int), ("flags", ctypes.c_uint)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("converged", ctypes.c_int),
+                ("relres", ctypes.c_double), ("f_max", ctypes.c_double),
+                ("div_max", ctypes.c_double), ("u_rms", ctypes.c_double),
+                ("div_metric", ctypes.c_double)]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+_lib = None
+
+
+def lib():
+    """Load libfizzyproj.so; raises if the CUDA library has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("CUDA library %s is missing: run paper_2502_04189_b300/build.py "
+                               "(there is no CPU fallback)" % LIB_PATH)
+        L = ctypes.CDLL(LIB_PATH)
+        vp, dp = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)
+        L.fizzy_proj_plan.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(Desc), vp]
+        L.fizzy_proj_plan.restype = ctypes.c_int
+        L.fizzy_proj_workspace_bytes.argtypes = [ctypes.POINTER(Desc)]
+        L.fizzy_proj_workspace_bytes.restype = ctypes.c_size_t
+        L.fizzy_proj_solve.argtypes = [vp] + [vp] * 7 + [ctypes.POINTER(Stats), vp]
+        L.fizzy_proj_solve.restype = ctypes.c_int
+        L.fizzy_proj_solve_host.argtypes = [vp] + [vp] * 7 + [ctypes.POINTER(Stats), vp]
+        L.fizzy_proj_solve_host.restype = ctypes.c_int
+        L.fizzy_proj_get_stats.argtypes = [vp, ctypes.POINTER(Stats), vp]
+        L.fizzy_proj_get_stats.restype = ctypes.c_int
+        L.fizzy_proj_destroy.argtypes = [vp]
+        L.fizzy_proj_destroy.restype = ctypes.c_int
+        L.fizzy_proj_errstr.argtypes = [ctypes.c_int]
+        L.fizzy_proj_errstr.restype = ctypes.c_char_p
+        L.fizzy_proj_last_error.argtypes = [vp]
+        L.fizzy_proj_last_error.restype = ctypes.c_char_p
+        L.fizzy_proj_launches_per_solve.argtypes = [vp]
+        L.fizzy_proj_launches_per_solve.restype = ctypes.c_int
+        L.fizzy_proj_set_timing.argtypes = [vp, ctypes.c_int]
+        L.fizzy_proj_set_timing.restype = ctypes.c_int
+        L.fizzy_proj_timing.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_char_p),
+                                        ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)]
+        L.fizzy_proj_timing.restype = ctypes.c_int
+        _lib = L
+    return _lib

@@ -1,0 +1,662 @@
+// fizzy_proj.cu -- host side of the C ABI declared in include/fizzy_proj.h:
+// plan construction (grid metrics, eigenvalues, twiddles and z-factorisation
+// tables built on the host in FP64), the kernel sequence of one projection,
+// and the stats/error plumbing.
+#include "fizzy_proj.h"
+#include "kern_passes.cuh"
+
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+using namespace fz;
+
+namespace {
+
+struct FFTHost {
+    FFTDesc d64, d32;
+    void *tw64 = nullptr, *tw32 = nullptr, *cs64 = nullptr, *cs32 = nullptr;
+};
+
+}  // namespace
+
+struct fizzy_proj_plan_s {
+    fizzy_proj_desc desc;
+    std::vector<double> zf;
+    int mixed = 0, check = 0;
+    double tol = 1e-10;
+    int max_refine = 4;
+    GridDev g;
+    double sigma = 0.0;
+    // device memory
+    std::vector<void *> allocs;
+    size_t bytes = 0;
+    FFTHost fx, fy;
+    int Ux = 0, Uy = 0;
+    double *mtab64 = nullptr, *ibtab64 = nullptr, *cup64 = nullptr;
+    float *mtab32 = nullptr, *ibtab32 = nullptr, *cup32 = nullptr;
+    double *qx = nullptr, *qy = nullptr, *qz = nullptr;
+    double *fhat64 = nullptr;
+    float *fhat32 = nullptr;
+    double *f = nullptr;
+    DevStats *st = nullptr;
+    double *usq_part = nullptr, *usq_sum = nullptr;
+    int n_usq_part = 0;
+    // end-to-end staging (solve_host)
+    double *stage[7] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    // launch shapes
+    int Lx = 1, TXy = 2;
+    size_t smem_x64 = 0, smem_x32 = 0, smem_y64 = 0, smem_y32 = 0;
+    std::string err;
+    // per-kernel timing
+    int timing = 0;
+    std::vector<cudaEvent_t> ev;        // 2 per recorded launch
+    std::vector<int> ev_slot;           // kernel slot of each recorded launch
+    int ev_used = 0;
+    double t_ms[16] = {0};
+    int t_cnt[16] = {0};
+};
+
+namespace {
+
+enum {
+    KS_FLUX, KS_XFWD, KS_YFWD, KS_THOMAS, KS_YINV, KS_XINV, KS_XRES, KS_YFWD_R, KS_THOMAS_R,
+    KS_YINV_R, KS_XACC, KS_RESMAX, KS_CORRECT, KS_DIVMAX, KS_SUM, KS_N
+};
+const char *kSlotName[KS_N] = {"flux", "div_fwdx", "fwd_y", "thomas", "inv_y", "inv_x",
+                               "resid_fwdx", "fwd_y_refine", "thomas_refine", "inv_y_refine",
+                               "inv_x_update", "resid_check", "correct", "div_check", "sum_partials"};
+const int kMaxTimed = 8192;
+
+const char *kErrStr[] = {"ok", "invalid argument", "unsupported size", "out of device memory",
+                         "CUDA error", "not converged", "device wait timeout"};
+
+bool radix23(int n) {
+    if (n < 2) return false;
+    while (n % 2 == 0) n /= 2;
+    while (n % 3 == 0) n /= 3;
+    return n == 1;
+}
+
+int set_err(fizzy_proj_plan_t p, int code, const std::string &msg) {
+    if (p) p->err = msg;
+    return code;
+}
+
+int cuda_err(fizzy_proj_plan_t p, cudaError_t e, const char *where) {
+    std::string m = std::string(where) + ": " + cudaGetErrorString(e);
+    return set_err(p, FIZZY_ERR_CUDA, m);
+}
+
+template <typename T> T *dev_alloc(fizzy_proj_plan_t p, size_t count, int *status) {
+    if (*status) return nullptr;
+    void *ptr = nullptr;
+    const size_t b = count * sizeof(T);
+    cudaError_t e = cudaMalloc(&ptr, b > 0 ? b : 16);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        *status = FIZZY_ERR_NOMEM;
+        p->err = "cudaMalloc of " + std::to_string(b) + " bytes failed";
+        return nullptr;
+    }
+    p->allocs.push_back(ptr);
+    p->bytes += b;
+    return (T *)ptr;
+}
+
+// Radix sequence of a Stockham plan: 4s first, then one 2, then 3s.
+int make_radices(int n, int *rad) {
+    int s = 0;
+    while (n % 4 == 0) { rad[s++] = 4; n /= 4; }
+    while (n % 2 == 0) { rad[s++] = 2; n /= 2; }
+    while (n % 3 == 0) { rad[s++] = 3; n /= 3; }
+    return s;
+}
+
+// exp(-2 pi i t / n) and (cos, sin)(pi m / (2n)) in long double, rounded once.
+void make_fft_tables(int n, std::vector<double> &tw, std::vector<double> &cs) {
+    const long double pi = 3.141592653589793238462643383279502884L;
+    tw.resize(2 * (size_t)n);
+    for (int t = 0; t < n; ++t) {
+        const long double a = 2.0L * pi * (long double)t / (long double)n;
+        tw[2 * t] = (double)cosl(a);
+        tw[2 * t + 1] = (double)(-sinl(a));
+    }
+    cs.resize(2 * (size_t)(n / 2 + 2), 0.0);
+    for (int m = 0; m <= n / 2; ++m) {
+        const long double a = pi * (long double)m / (2.0L * (long double)n);
+        cs[2 * m] = (double)cosl(a);
+        cs[2 * m + 1] = (double)sinl(a);
+    }
+}
+
+int build_fft(fizzy_proj_plan_t p, int n, int bc, FFTHost &F, int *status) {
+    std::vector<double> tw, cs;
+    make_fft_tables(n, tw, cs);
+    std::vector<float> tw32(tw.begin(), tw.end()), cs32(cs.begin(), cs.end());
+    F.tw64 = dev_alloc<double>(p, tw.size(), status);
+    F.cs64 = dev_alloc<double>(p, cs.size(), status);
+    if (p->mixed) {
+        F.tw32 = dev_alloc<float>(p, tw32.size(), status);
+        F.cs32 = dev_alloc<float>(p, cs32.size(), status);
+    }
+    if (*status) return *status;
+    cudaMemcpy(F.tw64, tw.data(), tw.size() * sizeof(double), cudaMemcpyHostToDevice);
+    cudaMemcpy(F.cs64, cs.data(), cs.size() * sizeof(double), cudaMemcpyHostToDevice);
+    if (p->mixed) {
+        cudaMemcpy(F.tw32, tw32.data(), tw32.size() * sizeof(float), cudaMemcpyHostToDevice);
+        cudaMemcpy(F.cs32, cs32.data(), cs32.size() * sizeof(float), cudaMemcpyHostToDevice);
+    }
+    FFTDesc d;
+    memset(&d, 0, sizeof(d));
+    d.n = n;
+    d.nst = make_radices(n, d.rad);
+    d.kind = (bc == FIZZY_BC_NEUMANN) ? KIND_DCT : KIND_PERIODIC;
+    F.d64 = d;
+    F.d64.tw = F.tw64;
+    F.d64.cs = F.cs64;
+    F.d32 = d;
+    F.d32.tw = F.tw32;
+    F.d32.cs = F.cs32;
+    return 0;
+}
+
+// Eigenvalue of the second difference at transform index u.
+double eig(int u, int n, double h, int bc) {
+    const long double pi = 3.141592653589793238462643383279502884L;
+    const long double a = (bc == FIZZY_BC_PERIODIC) ? pi * u / (long double)n
+                                                    : pi * u / (2.0L * (long double)n);
+    const long double s = sinl(a);
+    return (double)(-4.0L / ((long double)h * h) * s * s);
+}
+
+int validate(const fizzy_proj_desc *d) {
+    if (!d) return FIZZY_ERR_INVALID;
+    if (d->nx < 2 || d->ny < 2 || d->nz < 2) return FIZZY_ERR_INVALID;
+    if (!(d->dx > 0) || !(d->dy > 0)) return FIZZY_ERR_INVALID;
+    if (!d->zf && !(d->dz > 0)) return FIZZY_ERR_INVALID;
+    if (d->bc_x != FIZZY_BC_PERIODIC && d->bc_x != FIZZY_BC_NEUMANN) return FIZZY_ERR_INVALID;
+    if (d->bc_y != FIZZY_BC_PERIODIC && d->bc_y != FIZZY_BC_NEUMANN) return FIZZY_ERR_INVALID;
+    if (!(d->rho_l >= 1e-30 && d->rho_l <= 1e30) || !(d->rho_g >= 1e-30 && d->rho_g <= 1e30))
+        return FIZZY_ERR_INVALID;
+    if (!(d->dt > 0) || !std::isfinite(d->dt)) return FIZZY_ERR_INVALID;
+    if (d->precision != FIZZY_PREC_FP64 && d->precision != FIZZY_PREC_MIXED) return FIZZY_ERR_INVALID;
+    if (d->tol < 0 || d->max_refine < 0 || d->max_refine > 16) return FIZZY_ERR_INVALID;
+    if (d->zf)
+        for (int k = 0; k < d->nz; ++k)
+            if (!(d->zf[k + 1] > d->zf[k])) return FIZZY_ERR_INVALID;
+    if (!radix23(d->nx) || !radix23(d->ny)) return FIZZY_ERR_UNSUPPORTED;
+    if (d->nx > FIZZY_MAX_N || d->ny > FIZZY_MAX_N) return FIZZY_ERR_UNSUPPORTED;
+    if ((double)d->nx * d->ny * d->nz > 4.0e9) return FIZZY_ERR_UNSUPPORTED;
+    return FIZZY_OK;
+}
+
+// shapes of the transform passes
+int x_lines_per_cta(int n) {
+    int L = 1024 / n;
+    if (L < 1) L = 1;
+    if (L > 16) L = 16;
+    return L;
+}
+int y_tile_cols(int n) {
+    int L = 1024 / n;
+    if (L < 2) L = 2;
+    if (L > 8) L = 8;
+    return 2 * L;
+}
+template <typename T> size_t pass_smem(int n, int L) {
+    return sizeof(typename C2<T>::t) * ((size_t)n + (n / 2 + 2) + 2 * (size_t)L * (n + 1));
+}
+
+size_t usq_blocks(const fizzy_proj_desc *d) {
+    return (size_t)((d->nx + 31) / 32) * ((d->ny + 7) / 8) * d->nz;
+}
+
+size_t plan_bytes(const fizzy_proj_desc *d) {
+    const size_t N = (size_t)d->nx * d->ny * d->nz;
+    const int mixed = d->precision == FIZZY_PREC_MIXED;
+    const size_t Ux = d->bc_x == FIZZY_BC_PERIODIC ? d->nx / 2 + 1 : d->nx;
+    const size_t Uy = d->bc_y == FIZZY_BC_PERIODIC ? d->ny / 2 + 1 : d->ny;
+    const size_t tab = Ux * Uy * d->nz;
+    size_t b = 0;
+    b += 3 * N * 8;                   // q
+    b += mixed ? N * 4 + N * 8 : N * 8;  // spectral workspace (+ f in mixed)
+    b += 2 * tab * 8;                 // FP64 factorisation tables
+    if (mixed) b += 2 * tab * 4;      // FP32 factorisation tables
+    b += 16 * (size_t)d->nz * 8;      // per-k tables
+    b += 4 * (size_t)(d->nx + d->ny + 4) * 16;  // twiddles
+    b += usq_blocks(d) * 8 + 4096;    // partials + stats
+    return b;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *fizzy_proj_errstr(int code) {
+    if (code > 0 || code < -6) return "unknown error";
+    return kErrStr[-code];
+}
+
+const char *fizzy_proj_last_error(fizzy_proj_plan_t p) { return p ? p->err.c_str() : ""; }
+
+size_t fizzy_proj_workspace_bytes(const fizzy_proj_desc *d) {
+    if (validate(d) != FIZZY_OK) return 0;
+    return plan_bytes(d);
+}
+
+int fizzy_proj_destroy(fizzy_proj_plan_t p) {
+    if (!p) return FIZZY_OK;
+    cudaDeviceSynchronize();
+    for (auto &e : p->ev) cudaEventDestroy(e);
+    for (void *a : p->allocs) cudaFree(a);
+    for (int t = 0; t < 7; ++t)
+        if (p->stage[t]) cudaFree(p->stage[t]);
+    delete p;
+    return FIZZY_OK;
+}
+
+int fizzy_proj_plan(fizzy_proj_plan_t *out, const fizzy_proj_desc *d, void *stream) {
+    (void)stream;
+    if (!out) return FIZZY_ERR_INVALID;
+    *out = nullptr;
+    int v = validate(d);
+    if (v) return v;
+    fizzy_proj_plan_s *p = new fizzy_proj_plan_s();
+    p->desc = *d;
+    p->mixed = d->precision == FIZZY_PREC_MIXED;
+    p->check = (d->flags & FIZZY_FLAG_CHECK) ? 1 : 0;
+    p->tol = d->tol > 0 ? d->tol : 1e-10;
+    p->max_refine = d->max_refine > 0 ? d->max_refine : 4;
+    const int nx = d->nx, ny = d->ny, nz = d->nz;
+    const size_t N = (size_t)nx * ny * nz;
+    p->zf.resize(nz + 1);
+    for (int k = 0; k <= nz; ++k) p->zf[k] = d->zf ? d->zf[k] : d->dz * k;
+    p->desc.zf = nullptr;
+
+    // ---- grid metrics (host, FP64)
+    const double rho0 = std::min(d->rho_l, d->rho_g);
+    std::vector<double> dzf(nz), zc(nz), dzc(nz, 0.0);
+    for (int k = 0; k < nz; ++k) {
+        dzf[k] = p->zf[k + 1] - p->zf[k];
+        zc[k] = 0.5 * (p->zf[k] + p->zf[k + 1]);
+    }
+    for (int k = 0; k + 1 < nz; ++k) dzc[k] = zc[k + 1] - zc[k];
+    double lz = 0.0;
+    for (int k = 0; k < nz; ++k) lz += dzf[k];
+    p->sigma = 1.0 / (4.0 * (double)nx * (double)ny);
+    const double sig = p->sigma;
+    // per-k tables, packed: 11 arrays of nz
+    enum { T_GZ2, T_GZ0, T_DVZ, T_DVZS, T_CGZ, T_LZA, T_LZC, T_IZF, T_DZF, T_DZC, T_NTAB };
+    std::vector<double> zt((size_t)T_NTAB * nz, 0.0);
+    for (int k = 0; k < nz; ++k) {
+        const bool top = (k == nz - 1);
+        const double idzc = top ? 0.0 : 1.0 / dzc[k];
+        zt[T_GZ2 * nz + k] = 2.0 * idzc;
+        zt[T_GZ0 * nz + k] = idzc / rho0;
+        zt[T_DVZ * nz + k] = rho0 / dzf[k];
+        zt[T_DVZS * nz + k] = sig * rho0 / dzf[k];
+        zt[T_CGZ * nz + k] = d->dt / rho0 * idzc;
+        zt[T_LZA * nz + k] = (k > 0) ? 1.0 / (dzf[k] * dzc[k - 1]) : 0.0;
+        zt[T_LZC * nz + k] = top ? 0.0 : 1.0 / (dzf[k] * dzc[k]);
+        zt[T_IZF * nz + k] = 1.0 / dzf[k];
+        zt[T_DZF * nz + k] = dzf[k];
+        zt[T_DZC * nz + k] = dzc[k];
+    }
+    int status = 0;
+    double *zt_d = dev_alloc<double>(p, zt.size(), &status);
+    if (status) {
+        int st = status;
+        fizzy_proj_destroy(p);
+        return st;
+    }
+    cudaMemcpy(zt_d, zt.data(), zt.size() * sizeof(double), cudaMemcpyHostToDevice);
+
+    GridDev &g = p->g;
+    memset(&g, 0, sizeof(g));
+    g.nx = nx;
+    g.ny = ny;
+    g.nz = nz;
+    g.bcx = d->bc_x;
+    g.bcy = d->bc_y;
+    g.idt = 1.0 / d->dt;
+    g.two_rho_g = 2.0 * d->rho_g;
+    g.drho = d->rho_l - d->rho_g;
+    g.gx2 = 2.0 / d->dx;
+    g.gx0 = 1.0 / (rho0 * d->dx);
+    g.gy2 = 2.0 / d->dy;
+    g.gy0 = 1.0 / (rho0 * d->dy);
+    g.dvx = rho0 / d->dx;
+    g.dvy = rho0 / d->dy;
+    g.dvx_s = sig * rho0 / d->dx;
+    g.dvy_s = sig * rho0 / d->dy;
+    g.dt = d->dt;
+    g.cgx = d->dt / (rho0 * d->dx);
+    g.cgy = d->dt / (rho0 * d->dy);
+    g.idx2 = 1.0 / (d->dx * d->dx);
+    g.idy2 = 1.0 / (d->dy * d->dy);
+    g.idx1 = 1.0 / d->dx;
+    g.idy1 = 1.0 / d->dy;
+    g.gz2 = zt_d + T_GZ2 * nz;
+    g.gz0 = zt_d + T_GZ0 * nz;
+    g.dvz = zt_d + T_DVZ * nz;
+    g.dvz_s = zt_d + T_DVZS * nz;
+    g.cgz = zt_d + T_CGZ * nz;
+    g.lza = zt_d + T_LZA * nz;
+    g.lzc = zt_d + T_LZC * nz;
+    g.izf = zt_d + T_IZF * nz;
+    g.dzf = zt_d + T_DZF * nz;
+    g.dzc = zt_d + T_DZC * nz;
+    g.inv_lz = 1.0 / lz;
+    g.sigma = sig;
+
+    // ---- transforms
+    build_fft(p, nx, d->bc_x, p->fx, &status);
+    build_fft(p, ny, d->bc_y, p->fy, &status);
+
+    // ---- z factorisation tables per distinct eigenvalue pair
+    const int Ux = d->bc_x == FIZZY_BC_PERIODIC ? nx / 2 + 1 : nx;
+    const int Uy = d->bc_y == FIZZY_BC_PERIODIC ? ny / 2 + 1 : ny;
+    p->Ux = Ux;
+    p->Uy = Uy;
+    const size_t ts = (size_t)Ux * Uy;
+    std::vector<double> mt(ts * nz, 0.0), ib(ts * nz, 0.0);
+    std::vector<double> lam_x(Ux), lam_y(Uy);
+    for (int u = 0; u < Ux; ++u) lam_x[u] = eig(u, nx, d->dx, d->bc_x);
+    for (int u = 0; u < Uy; ++u) lam_y[u] = eig(u, ny, d->dy, d->bc_y);
+    const double *A = &zt[T_LZA * nz];
+    const double *C = &zt[T_LZC * nz];
+#pragma omp parallel for schedule(static)
+    for (long long uu = 0; uu < (long long)ts; ++uu) {
+        const int ux = (int)(uu % Ux), uy = (int)(uu / Ux);
+        if (ux == 0 && uy == 0) continue;  // singular line handled in the kernel
+        const double lam = lam_x[ux] + lam_y[uy];
+        double beta = -(A[0] + C[0]) + lam;
+        ib[uu] = 1.0 / beta;
+        for (int k = 1; k < nz; ++k) {
+            const double m = A[k] / beta;
+            beta = (-(A[k] + C[k]) + lam) - m * C[k - 1];
+            mt[(size_t)k * ts + uu] = m;
+            ib[(size_t)k * ts + uu] = 1.0 / beta;
+        }
+    }
+    p->mtab64 = dev_alloc<double>(p, ts * nz, &status);
+    p->ibtab64 = dev_alloc<double>(p, ts * nz, &status);
+    p->cup64 = dev_alloc<double>(p, nz, &status);
+    if (p->mixed) {
+        p->mtab32 = dev_alloc<float>(p, ts * nz, &status);
+        p->ibtab32 = dev_alloc<float>(p, ts * nz, &status);
+        p->cup32 = dev_alloc<float>(p, nz, &status);
+    }
+    // ---- workspace
+    p->qx = dev_alloc<double>(p, N, &status);
+    p->qy = dev_alloc<double>(p, N, &status);
+    p->qz = dev_alloc<double>(p, N, &status);
+    if (p->mixed) {
+        p->fhat32 = dev_alloc<float>(p, N, &status);
+        p->f = dev_alloc<double>(p, N, &status);
+    } else {
+        p->fhat64 = dev_alloc<double>(p, N, &status);
+    }
+    p->st = dev_alloc<DevStats>(p, 1, &status);
+    p->n_usq_part = (int)usq_blocks(d);
+    p->usq_part = dev_alloc<double>(p, p->n_usq_part, &status);
+    p->usq_sum = dev_alloc<double>(p, 1, &status);
+    if (status) {
+        int st = status;
+        fizzy_proj_destroy(p);
+        return st;
+    }
+    cudaMemcpy(p->mtab64, mt.data(), mt.size() * sizeof(double), cudaMemcpyHostToDevice);
+    cudaMemcpy(p->ibtab64, ib.data(), ib.size() * sizeof(double), cudaMemcpyHostToDevice);
+    cudaMemcpy(p->cup64, C, nz * sizeof(double), cudaMemcpyHostToDevice);
+    if (p->mixed) {
+        std::vector<float> t32(mt.size());
+        for (size_t t = 0; t < mt.size(); ++t) t32[t] = (float)mt[t];
+        cudaMemcpy(p->mtab32, t32.data(), t32.size() * sizeof(float), cudaMemcpyHostToDevice);
+        for (size_t t = 0; t < ib.size(); ++t) t32[t] = (float)ib[t];
+        cudaMemcpy(p->ibtab32, t32.data(), t32.size() * sizeof(float), cudaMemcpyHostToDevice);
+        std::vector<float> c32(C, C + nz);
+        cudaMemcpy(p->cup32, c32.data(), nz * sizeof(float), cudaMemcpyHostToDevice);
+    }
+    cudaMemset(p->st, 0, sizeof(DevStats));
+
+    // ---- launch shapes and shared-memory opt-in
+    p->Lx = x_lines_per_cta(nx);
+    p->TXy = y_tile_cols(ny);
+    p->smem_x64 = pass_smem<double>(nx, p->Lx);
+    p->smem_x32 = pass_smem<float>(nx, p->Lx);
+    p->smem_y64 = pass_smem<double>(ny, p->TXy / 2);
+    p->smem_y32 = pass_smem<float>(ny, p->TXy / 2);
+    const int big = 200 * 1024;
+    cudaFuncSetAttribute(k_xfwd<double, XF_F64_DIVQ>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    cudaFuncSetAttribute(k_xfwd<float, XF_MIX_DIVQ>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    cudaFuncSetAttribute(k_xfwd<float, XF_MIX_RESID>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    cudaFuncSetAttribute(k_xinv<double, XI_STORE>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    cudaFuncSetAttribute(k_xinv<float, XI_STORE>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    cudaFuncSetAttribute(k_xinv<float, XI_ACCUM>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    cudaFuncSetAttribute(k_ypass<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    cudaFuncSetAttribute(k_ypass<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    cudaFuncSetAttribute(k_ypass<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    cudaFuncSetAttribute(k_ypass<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        int st = cuda_err(nullptr, e, "plan");
+        fizzy_proj_destroy(p);
+        return st;
+    }
+    *out = p;
+    return FIZZY_OK;
+}
+
+int fizzy_proj_launches_per_solve(fizzy_proj_plan_t p) {
+    if (!p) return 0;
+    int n = p->mixed ? 8 + 5 * p->max_refine : 7;
+    if (p->check) n += p->mixed ? 2 : 3;
+    return n;
+}
+
+static void read_stats(fizzy_proj_plan_t p, const DevStats &h, double usq, fizzy_proj_stats *st) {
+    memset(st, 0, sizeof(*st));
+    const size_t N = (size_t)p->desc.nx * p->desc.ny * p->desc.nz;
+    st->iterations = p->mixed ? h.iterations : 0;
+    st->converged = p->mixed ? h.converged : 1;
+    st->relres = h.relres;
+    memcpy(&st->f_max, &h.fmax_bits, sizeof(double));
+    memcpy(&st->div_max, &h.divmax_bits, sizeof(double));
+    st->u_rms = p->check ? std::sqrt(usq / (3.0 * (double)N)) : 0.0;
+    st->div_metric = (p->check && st->u_rms > 0) ? st->div_max * p->desc.dx / st->u_rms : 0.0;
+}
+
+int fizzy_proj_get_stats(fizzy_proj_plan_t p, fizzy_proj_stats *st, void *stream) {
+    if (!p || !st) return FIZZY_ERR_INVALID;
+    cudaStream_t s = (cudaStream_t)stream;
+    DevStats h;
+    double usq = 0.0;
+    cudaError_t e = cudaMemcpyAsync(&h, p->st, sizeof(h), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && p->check)
+        e = cudaMemcpyAsync(&usq, p->usq_sum, sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_err(p, e, "get_stats");
+    read_stats(p, h, usq, st);
+    if (p->mixed && !st->converged) return FIZZY_ERR_NOT_CONVERGED;
+    return FIZZY_OK;
+}
+
+static inline void tmark(fizzy_proj_plan_t p, int slot, cudaStream_t s, bool begin) {
+    if (!p->timing) return;
+    if (begin) {
+        if (p->ev_used >= kMaxTimed) return;
+        cudaEventRecord(p->ev[2 * p->ev_used], s);
+        p->ev_slot[p->ev_used] = slot;
+    } else {
+        if (p->ev_used >= kMaxTimed || p->ev_slot[p->ev_used] != slot) return;
+        cudaEventRecord(p->ev[2 * p->ev_used + 1], s);
+        ++p->ev_used;
+    }
+}
+#define TIMED(slot, launch)          \
+    do {                             \
+        tmark(p, slot, s, true);     \
+        launch;                      \
+        tmark(p, slot, s, false);    \
+    } while (0)
+
+int fizzy_proj_set_timing(fizzy_proj_plan_t p, int enable) {
+    if (!p) return FIZZY_ERR_INVALID;
+    if (enable && p->ev.empty()) {
+        p->ev.resize(2 * kMaxTimed);
+        p->ev_slot.assign(kMaxTimed, -1);
+        for (auto &e : p->ev) {
+            cudaError_t r = cudaEventCreate(&e);
+            if (r != cudaSuccess) return cuda_err(p, r, "event create");
+        }
+    }
+    p->timing = enable ? 1 : 0;
+    p->ev_used = 0;
+    for (int k = 0; k < KS_N; ++k) {
+        p->t_ms[k] = 0.0;
+        p->t_cnt[k] = 0;
+    }
+    return FIZZY_OK;
+}
+
+int fizzy_proj_timing(fizzy_proj_plan_t p, int idx, const char **name, double *ms, int *launches) {
+    if (!p) return FIZZY_ERR_INVALID;
+    for (int t = 0; t < p->ev_used; ++t) {
+        cudaError_t r = cudaEventSynchronize(p->ev[2 * t + 1]);
+        if (r != cudaSuccess) return cuda_err(p, r, "event sync");
+        float e = 0.f;
+        cudaEventElapsedTime(&e, p->ev[2 * t], p->ev[2 * t + 1]);
+        p->t_ms[p->ev_slot[t]] += e;
+        p->t_cnt[p->ev_slot[t]] += 1;
+    }
+    p->ev_used = 0;
+    if (idx >= 0 && idx < KS_N) {
+        if (name) *name = kSlotName[idx];
+        if (ms) *ms = p->t_ms[idx];
+        if (launches) *launches = p->t_cnt[idx];
+    }
+    return KS_N;
+}
+
+int fizzy_proj_solve(fizzy_proj_plan_t p, const double *phi, const double *p_n, const double *p_nm1,
+                     double *u, double *v, double *w, double *p_np1, fizzy_proj_stats *st,
+                     void *stream) {
+    if (!p) return FIZZY_ERR_INVALID;
+    if (!phi || !p_n || !p_nm1 || !u || !v || !w || !p_np1)
+        return set_err(p, FIZZY_ERR_INVALID, "null array pointer");
+    if (p_np1 == phi || p_np1 == p_n || p_np1 == p_nm1 || p_np1 == u || p_np1 == v || p_np1 == w)
+        return set_err(p, FIZZY_ERR_INVALID, "p_np1 aliases an input");
+    cudaStream_t s = (cudaStream_t)stream;
+    const GridDev &g = p->g;
+    const int nx = g.nx, ny = g.ny, nz = g.nz;
+    const dim3 cblk(32, 8), cgrd((nx + 31) / 32, (ny + 7) / 8, nz);
+    const dim3 rblk(256), rgrd((nx + 255) / 256, ny, nz);
+    const int nlines = ny * nz;
+    const int xgrid = (nlines + 2 * p->Lx - 1) / (2 * p->Lx);
+    const dim3 ygrid((nx + p->TXy - 1) / p->TXy, nz);
+    const dim3 tgrid((nx + 127) / 128, ny);
+    XArgs xa;
+    memset(&xa, 0, sizeof(xa));
+    xa.qx = p->qx;
+    xa.qy = p->qy;
+    xa.qz = p->qz;
+    xa.st = p->st;
+    xa.tol = p->tol;
+    cudaError_t e = cudaSuccess;
+    if (p->mixed || p->check) e = cudaMemsetAsync(p->st, 0, sizeof(DevStats), s);
+    if (e != cudaSuccess) return cuda_err(p, e, "memset");
+
+    TIMED(KS_FLUX, (k_flux<<<cgrd, cblk, 0, s>>>(g, phi, p_n, p_nm1, u, v, w, p->qx, p->qy, p->qz,
+                                                p->check ? p->usq_part : nullptr)));
+    if (!p->mixed) {
+        xa.out = p->fhat64;
+        TIMED(KS_XFWD, (k_xfwd<double, XF_F64_DIVQ><<<xgrid, 256, p->smem_x64, s>>>(g, p->fx.d64, p->Lx, xa)));
+        TIMED(KS_YFWD, (k_ypass<double, false><<<ygrid, 256, p->smem_y64, s>>>(nx, ny, p->fy.d64, p->TXy, p->fhat64, nullptr)));
+        TIMED(KS_THOMAS, (k_thomas<double><<<tgrid, 128, 0, s>>>(g, p->Ux, p->Uy, p->mtab64, p->ibtab64, p->cup64, p->fhat64, nullptr)));
+        TIMED(KS_YINV, (k_ypass<double, true><<<ygrid, 256, p->smem_y64, s>>>(nx, ny, p->fy.d64, p->TXy, p->fhat64, nullptr)));
+        TIMED(KS_XINV, (k_xinv<double, XI_STORE><<<xgrid, 256, p->smem_x64, s>>>(g, p->fx.d64, p->Lx, p->fhat64, p_np1, p->st)));
+        if (p->check) {
+            XArgs ca = xa;
+            ca.p = p_np1;
+            ca.slot = 0;
+            TIMED(KS_RESMAX, (k_residmax<<<rgrd, rblk, 0, s>>>(g, ca, 1)));
+        }
+    } else {
+        xa.out = p->fhat32;
+        xa.f_out = p->f;
+        const int *conv = &p->st->converged;
+        TIMED(KS_XFWD, (k_xfwd<float, XF_MIX_DIVQ><<<xgrid, 256, p->smem_x32, s>>>(g, p->fx.d32, p->Lx, xa)));
+        TIMED(KS_YFWD, (k_ypass<float, false><<<ygrid, 256, p->smem_y32, s>>>(nx, ny, p->fy.d32, p->TXy, p->fhat32, nullptr)));
+        TIMED(KS_THOMAS, (k_thomas<float><<<tgrid, 128, 0, s>>>(g, p->Ux, p->Uy, p->mtab32, p->ibtab32, p->cup32, p->fhat32, nullptr)));
+        TIMED(KS_YINV, (k_ypass<float, true><<<ygrid, 256, p->smem_y32, s>>>(nx, ny, p->fy.d32, p->TXy, p->fhat32, nullptr)));
+        TIMED(KS_XINV, (k_xinv<float, XI_STORE><<<xgrid, 256, p->smem_x32, s>>>(g, p->fx.d32, p->Lx, p->fhat32, p_np1, p->st)));
+        XArgs ra = xa;
+        ra.f = p->f;
+        ra.p = p_np1;
+        ra.f_out = nullptr;
+        for (int sw = 0; sw < p->max_refine; ++sw) {
+            ra.slot = sw;
+            TIMED(KS_XRES, (k_xfwd<float, XF_MIX_RESID><<<xgrid, 256, p->smem_x32, s>>>(g, p->fx.d32, p->Lx, ra)));
+            TIMED(KS_YFWD_R, (k_ypass<float, false><<<ygrid, 256, p->smem_y32, s>>>(nx, ny, p->fy.d32, p->TXy, p->fhat32, conv)));
+            TIMED(KS_THOMAS_R, (k_thomas<float><<<tgrid, 128, 0, s>>>(g, p->Ux, p->Uy, p->mtab32, p->ibtab32, p->cup32, p->fhat32, conv)));
+            TIMED(KS_YINV_R, (k_ypass<float, true><<<ygrid, 256, p->smem_y32, s>>>(nx, ny, p->fy.d32, p->TXy, p->fhat32, conv)));
+            TIMED(KS_XACC, (k_xinv<float, XI_ACCUM><<<xgrid, 256, p->smem_x32, s>>>(g, p->fx.d32, p->Lx, p->fhat32, p_np1, p->st)));
+        }
+        ra.slot = p->max_refine;
+        TIMED(KS_RESMAX, (k_residmax<<<rgrd, rblk, 0, s>>>(g, ra, 0)));
+    }
+    TIMED(KS_CORRECT, (k_correct<<<cgrd, cblk, 0, s>>>(g, p_np1, p->qx, p->qy, p->qz, u, v, w)));
+    if (p->check) {
+        TIMED(KS_DIVMAX, (k_divmax<<<rgrd, rblk, 0, s>>>(g, u, v, w, p->st)));
+        TIMED(KS_SUM, (k_sum_partials<<<1, 1024, 0, s>>>(p->usq_part, p->n_usq_part, p->usq_sum)));
+    }
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_err(p, e, "solve launch");
+    if (st) return fizzy_proj_get_stats(p, st, stream);
+    return FIZZY_OK;
+}
+
+int fizzy_proj_solve_host(fizzy_proj_plan_t p, const double *phi, const double *p_n,
+                          const double *p_nm1, double *u, double *v, double *w, double *p_np1,
+                          fizzy_proj_stats *st, void *stream) {
+    if (!p) return FIZZY_ERR_INVALID;
+    if (!phi || !p_n || !p_nm1 || !u || !v || !w || !p_np1)
+        return set_err(p, FIZZY_ERR_INVALID, "null array pointer");
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t N = (size_t)p->desc.nx * p->desc.ny * p->desc.nz;
+    const size_t B = N * sizeof(double);
+    for (int t = 0; t < 7; ++t) {
+        if (!p->stage[t]) {
+            cudaError_t e = cudaMalloc(&p->stage[t], B);
+            if (e != cudaSuccess) {
+                (void)cudaGetLastError();
+                p->stage[t] = nullptr;
+                return set_err(p, FIZZY_ERR_NOMEM, "staging allocation failed");
+            }
+        }
+    }
+    const double *hin[6] = {phi, p_n, p_nm1, u, v, w};
+    cudaError_t e = cudaSuccess;
+    for (int t = 0; t < 6 && e == cudaSuccess; ++t)
+        e = cudaMemcpyAsync(p->stage[t], hin[t], B, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return cuda_err(p, e, "H2D");
+    int rc = fizzy_proj_solve(p, p->stage[0], p->stage[1], p->stage[2], p->stage[3], p->stage[4],
+                              p->stage[5], p->stage[6], nullptr, stream);
+    if (rc) return rc;
+    double *hout[4] = {u, v, w, p_np1};
+    const int src[4] = {3, 4, 5, 6};
+    for (int t = 0; t < 4 && e == cudaSuccess; ++t)
+        e = cudaMemcpyAsync(hout[t], p->stage[src[t]], B, cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return cuda_err(p, e, "D2H");
+    if (st) return fizzy_proj_get_stats(p, st, stream);
+    e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_err(p, e, "sync");
+    return FIZZY_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,123 @@
+// Shared device helpers for the projection kernels (sm_103a).
+//
+// Design note: on this part FP64 instructions (DFMA/DADD/DMUL and the
+// F2F conversions between float and double) issue at roughly 1/74 of the FP32
+// rate, so every kernel here counts FP64 instructions per grid point.  Bit-level
+// conversions below move values between float and double with integer
+// instructions only (IEEE 754 field arithmetic) where a conversion would
+// otherwise cost an FP64 issue slot.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace fz {
+
+template <typename T> struct C2;
+template <> struct C2<double> { typedef double2 t; };
+template <> struct C2<float> { typedef float2 t; };
+
+__device__ __forceinline__ double fmaT(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ float fmaT(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+
+__device__ __forceinline__ double2 mk2(double x, double y) { return make_double2(x, y); }
+__device__ __forceinline__ float2 mk2(float x, float y) { return make_float2(x, y); }
+
+// double -> float for a positive normal value whose exponent fits a float
+// (|x| in about [1.2e-38, 3.4e38]); truncates the mantissa (relative error
+// below 2^-23).  Three integer instructions instead of an FP64 conversion.
+__device__ __forceinline__ float pos_f64_to_f32_trunc(double x) {
+    const int hi = __double2hiint(x);
+    const int lo = __double2loint(x);
+    // (hi << 3 | lo >> 29) puts the low 9 exponent bits on top of the 23
+    // leading mantissa bits; re-biasing the exponent (1023 -> 127) is a
+    // subtraction of 896 = 512 + 384 modulo 2^9 on that field.
+    const unsigned b = __funnelshift_l((unsigned)lo, (unsigned)hi, 3) - (384u << 23);
+    return __uint_as_float(b);
+}
+
+// float -> double for a positive normal float (exact).  Integer-only.
+__device__ __forceinline__ double pos_f32_to_f64(float f) {
+    const unsigned b = __float_as_uint(f);
+    return __hiloint2double((int)((b >> 3) + (896u << 20)), (int)(b << 29));
+}
+
+// 1/s for s > 0 (positive normal double within float range), relative error
+// about 2^-44: an FP32 seed (approximate reciprocal of the truncated
+// argument, error below 2^-22) refined by one Newton-Raphson step in FP64,
+// r1 = r0 + r0 (1 - s r0), which squares the relative error.  Costs two FP64
+// instructions.
+__device__ __forceinline__ double rcp_pos_nr1(double s) {
+    float sf = pos_f64_to_f32_trunc(s);
+    float rf;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rf) : "f"(sf));
+    const double r0 = pos_f32_to_f64(rf);
+    const double e = __fma_rn(-s, r0, 1.0);
+    return __fma_rn(r0, e, r0);
+}
+
+// |x| as an unsigned 64-bit pattern: for non-negative doubles the integer
+// order of the bit patterns is the numeric order, so max-reductions run on the
+// integer units (and atomicMax on the pattern is exact and order-independent).
+__device__ __forceinline__ unsigned long long absbits(double x) {
+    return (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull;
+}
+__device__ __forceinline__ unsigned absbits(float x) { return __float_as_uint(x) & 0x7fffffffu; }
+
+__device__ __forceinline__ unsigned long long umax64(unsigned long long a, unsigned long long b) {
+    return a > b ? a : b;
+}
+
+__device__ __forceinline__ int block_tid() {
+    return threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+}
+__device__ __forceinline__ int block_nthreads() { return blockDim.x * blockDim.y * blockDim.z; }
+
+// Block-wide max of a 64-bit pattern, then one atomicMax per block.
+// Every thread of the block must call it (it contains barriers).
+__device__ __forceinline__ void block_max_atomic(unsigned long long v, unsigned long long *dst) {
+    __shared__ unsigned long long red[32];
+    for (int o = 16; o > 0; o >>= 1) v = umax64(v, __shfl_xor_sync(0xffffffffu, v, o));
+    const int lane = block_tid() & 31, wid = block_tid() >> 5;
+    const int nw = (block_nthreads() + 31) >> 5;
+    __syncthreads();
+    if (lane == 0) red[wid] = v;
+    __syncthreads();
+    if (wid == 0) {
+        v = lane < nw ? red[lane] : 0ull;
+        for (int o = 16; o > 0; o >>= 1) v = umax64(v, __shfl_xor_sync(0xffffffffu, v, o));
+        if (lane == 0 && v) atomicMax(dst, v);
+    }
+}
+
+// Block-wide sum (deterministic order within the block); thread 0 gets the
+// result.  Every thread of the block must call it (it contains barriers).
+__device__ __forceinline__ double block_sum(double v) {
+    __shared__ double red[32];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int lane = block_tid() & 31, wid = block_tid() >> 5;
+    const int nw = (block_nthreads() + 31) >> 5;
+    __syncthreads();
+    if (lane == 0) red[wid] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (wid == 0) {
+        s = lane < nw ? red[lane] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    }
+    return s;
+}
+
+// Device-side state of one solve (reset at the start of every solve).
+struct DevStats {
+    unsigned long long fmax_bits;      // max|f|
+    unsigned long long rmax_bits[20];  // max|r| per residual evaluation (mixed)
+    unsigned long long divmax_bits;    // max|D u|
+    unsigned int done_blocks[20];      // last-block counters of the residual kernels
+    int converged;                     // mixed: set once relres <= tol
+    int iterations;                    // mixed: sweeps that ran
+    int n_resid;                       // residual evaluations that ran
+    double relres;                     // last relres
+    double usq_partial_dummy;          // (alignment)
+};
+
+}  // namespace fz

@@ -1,0 +1,217 @@
+// Real-to-real transforms along x and y for the fast Poisson solver
+// (CaNS-style direct solver, paper "Methods and Implementation strategy":
+// FFT along the periodic directions; here also the DCT-II basis for walls).
+//
+// Scheme (own design for sm_103a):
+//  * Two real lines a, b are packed into one complex line z = a + i b and
+//    transformed by a single complex FFT; the two real spectra are separated
+//    afterwards with Z[m] and conj(Z[n-m]).
+//  * Periodic direction: real DFT in half-complex order (index m <= n/2 holds
+//    Re A_m, index n-m holds Im A_m).  Wall direction: DCT-II obtained from the
+//    same FFT after the even/odd reordering of Makhoul (1980),
+//    v_t = x_2t, v_(n-1-t) = x_(2t+1), and a post-twiddle exp(-i pi m / (2n)).
+//  * Both forward variants output 2x the plain sums and both inverse variants
+//    return 2n x the input, so a 2-D round trip scales by 4 nx ny; the solver
+//    folds 1/(4 nx ny) into the right-hand side.
+//  * The complex FFT is a Stockham autosort (self-sorting) mixed-radix
+//    (4, 2, 3) FFT in shared memory with ping-pong buffers and one barrier per
+//    stage; twiddles come from a per-plan table staged into shared memory.
+#pragma once
+#include "kern_common.cuh"
+
+namespace fz {
+
+enum { KIND_PERIODIC = 0, KIND_DCT = 1 };
+
+// One transform direction (kernel argument, by value).
+struct FFTDesc {
+    int n;           // transform length
+    int nst;         // number of Stockham stages
+    int rad[16];     // radix of each stage (4, 2 or 3)
+    int kind;        // KIND_PERIODIC or KIND_DCT
+    const void *tw;  // n complex: exp(-2 pi i t / n)          (T2 of the kernel's type)
+    const void *cs;  // n/2+1 complex: (cos, sin)(pi m / (2 n)) (T2)
+};
+
+// position of input sample i inside the (possibly reordered) complex line
+__device__ __forceinline__ int line_pos(int i, int n, int kind) {
+    return (kind == KIND_DCT) ? ((i & 1) ? n - 1 - (i >> 1) : (i >> 1)) : i;
+}
+
+template <typename T, bool INV>
+__device__ __forceinline__ void twiddle(typename C2<T>::t &x, typename C2<T>::t w) {
+    T r, i;
+    if (!INV) {
+        r = fmaT(x.x, w.x, -x.y * w.y);
+        i = fmaT(x.x, w.y, x.y * w.x);
+    } else {
+        r = fmaT(x.x, w.x, x.y * w.y);
+        i = fmaT(x.y, w.x, -x.x * w.y);
+    }
+    x.x = r;
+    x.y = i;
+}
+
+// One Stockham stage over L lines (line stride ls) from src to dst.
+template <typename T, bool INV>
+__device__ __forceinline__ void stockham_stage(const typename C2<T>::t *__restrict__ src,
+                                               typename C2<T>::t *__restrict__ dst, int n, int L,
+                                               int ls, int R, int Ns,
+                                               const typename C2<T>::t *__restrict__ tw) {
+    typedef typename C2<T>::t T2;
+    const int m = n / R;
+    const int total = L * m;
+    const int twq = n / (Ns * R);
+    for (int t = threadIdx.x; t < total; t += blockDim.x) {
+        const int l = t / m;
+        const int b = t - l * m;
+        const int j = b % Ns;
+        const T2 *in = src + l * ls + b;
+        T2 *out = dst + l * ls + (b - j) * R + j;
+        const int ts = j * twq;
+        if (R == 4) {
+            T2 x0 = in[0], x1 = in[m], x2 = in[2 * m], x3 = in[3 * m];
+            if (Ns > 1) {
+                twiddle<T, INV>(x1, tw[ts]);
+                twiddle<T, INV>(x2, tw[2 * ts]);
+                twiddle<T, INV>(x3, tw[3 * ts]);
+            }
+            const T ar = x0.x + x2.x, ai = x0.y + x2.y;
+            const T br = x0.x - x2.x, bi = x0.y - x2.y;
+            const T cr = x1.x + x3.x, ci = x1.y + x3.y;
+            const T dr = x1.x - x3.x, di = x1.y - x3.y;
+            out[0] = mk2(ar + cr, ai + ci);
+            out[2 * Ns] = mk2(ar - cr, ai - ci);
+            if (!INV) {  // y1 = b - i d, y3 = b + i d
+                out[Ns] = mk2(br + di, bi - dr);
+                out[3 * Ns] = mk2(br - di, bi + dr);
+            } else {     // y1 = b + i d, y3 = b - i d
+                out[Ns] = mk2(br - di, bi + dr);
+                out[3 * Ns] = mk2(br + di, bi - dr);
+            }
+        } else if (R == 2) {
+            T2 x0 = in[0], x1 = in[m];
+            if (Ns > 1) twiddle<T, INV>(x1, tw[ts]);
+            out[0] = mk2(x0.x + x1.x, x0.y + x1.y);
+            out[Ns] = mk2(x0.x - x1.x, x0.y - x1.y);
+        } else {  // R == 3
+            T2 x0 = in[0], x1 = in[m], x2 = in[2 * m];
+            if (Ns > 1) {
+                twiddle<T, INV>(x1, tw[ts]);
+                twiddle<T, INV>(x2, tw[2 * ts]);
+            }
+            const T h = (T)0.86602540378443864676;  // sqrt(3)/2
+            const T sr = x1.x + x2.x, si = x1.y + x2.y;
+            const T mr = fmaT((T)-0.5, sr, x0.x), mi = fmaT((T)-0.5, si, x0.y);
+            const T dr = (x1.x - x2.x) * h, di = (x1.y - x2.y) * h;
+            out[0] = mk2(x0.x + sr, x0.y + si);
+            if (!INV) {  // t3 = -i h d
+                out[Ns] = mk2(mr + di, mi - dr);
+                out[2 * Ns] = mk2(mr - di, mi + dr);
+            } else {
+                out[Ns] = mk2(mr - di, mi + dr);
+                out[2 * Ns] = mk2(mr + di, mi - dr);
+            }
+        }
+    }
+}
+
+// Full complex FFT of L lines; data starts in a, b is the other buffer.
+// Returns the buffer that holds the result.  Ends with a barrier.
+template <typename T, bool INV>
+__device__ typename C2<T>::t *fft_lines(typename C2<T>::t *a, typename C2<T>::t *b, int L, int ls,
+                                        const FFTDesc &D, const typename C2<T>::t *tw) {
+    int Ns = 1;
+    for (int s = 0; s < D.nst; ++s) {
+        const int R = D.rad[s];
+        stockham_stage<T, INV>(a, b, D.n, L, ls, R, Ns, tw);
+        __syncthreads();
+        typename C2<T>::t *t = a;
+        a = b;
+        b = t;
+        Ns *= R;
+    }
+    return a;
+}
+
+// Stage the twiddle tables of D into shared memory (tw: n entries, cs: n/2+1).
+template <typename T>
+__device__ __forceinline__ void load_tables(const FFTDesc &D, typename C2<T>::t *tw_s,
+                                            typename C2<T>::t *cs_s) {
+    typedef typename C2<T>::t T2;
+    const T2 *tw = (const T2 *)D.tw;
+    const T2 *cs = (const T2 *)D.cs;
+    for (int t = threadIdx.x; t < D.n; t += blockDim.x) tw_s[t] = tw[t];
+    if (D.kind == KIND_DCT)
+        for (int t = threadIdx.x; t <= D.n / 2; t += blockDim.x) cs_s[t] = cs[t];
+}
+
+// Forward separation for the pair index m of one complex line Z (length n):
+// writes the two real spectra (scaled by 2) through out(a_or_b, index, value).
+template <typename T, typename F>
+__device__ __forceinline__ void fwd_separate(const typename C2<T>::t *Z, int n, int m, int kind,
+                                             const typename C2<T>::t *cs, F &&out) {
+    typedef typename C2<T>::t T2;
+    if (m == 0) {
+        const T2 z = Z[0];
+        out(0, 0, z.x + z.x);
+        out(1, 0, z.y + z.y);
+        return;
+    }
+    const T2 z = Z[m];
+    if (2 * m == n) {  // Nyquist (even n): both spectra are real there
+        const T f = (kind == KIND_DCT) ? (T)1.41421356237309504880 : (T)2;  // 2 cos(pi/4) or 2
+        out(0, m, f * z.x);
+        out(1, m, f * z.y);
+        return;
+    }
+    const T2 y = Z[n - m];
+    const T var = z.x + y.x, vai = z.y - y.y;  // 2 A_m
+    const T vbr = z.y + y.y, vbi = y.x - z.x;  // 2 B_m
+    if (kind == KIND_PERIODIC) {
+        out(0, m, var);
+        out(0, n - m, vai);
+        out(1, m, vbr);
+        out(1, n - m, vbi);
+    } else {  // X[m] = Re(w V), X[n-m] = -Im(w V), w = c - i s
+        const T c = cs[m].x, s = cs[m].y;
+        out(0, m, fmaT(c, var, s * vai));
+        out(0, n - m, fmaT(s, var, -c * vai));
+        out(1, m, fmaT(c, vbr, s * vbi));
+        out(1, n - m, fmaT(s, vbr, -c * vbi));
+    }
+}
+
+// Inverse combination for pair index m: given the real spectra values of lines
+// a and b (get(a_or_b, index)), writes Z[m] and Z[n-m] of the packed line.
+template <typename T, typename G>
+__device__ __forceinline__ void inv_combine(typename C2<T>::t *Z, int n, int m, int kind,
+                                            const typename C2<T>::t *cs, G &&get) {
+    if (m == 0) {
+        Z[0] = mk2(get(0, 0), get(1, 0));
+        return;
+    }
+    if (2 * m == n) {
+        const T f = (kind == KIND_DCT) ? (T)1.41421356237309504880 : (T)1;
+        Z[m] = mk2(f * get(0, m), f * get(1, m));
+        return;
+    }
+    T ar, ai, br, bi;
+    if (kind == KIND_PERIODIC) {
+        ar = get(0, m);
+        ai = get(0, n - m);
+        br = get(1, m);
+        bi = get(1, n - m);
+    } else {  // V[m] = (c + i s)(X[m] - i X[n-m])
+        const T c = cs[m].x, s = cs[m].y;
+        const T xa = get(0, m), ya = get(0, n - m), xb = get(1, m), yb = get(1, n - m);
+        ar = fmaT(c, xa, s * ya);
+        ai = fmaT(s, xa, -c * ya);
+        br = fmaT(c, xb, s * yb);
+        bi = fmaT(s, xb, -c * yb);
+    }
+    Z[m] = mk2(ar - bi, ai + br);
+    Z[n - m] = mk2(ar + bi, br - ai);
+}
+
+}  // namespace fz

@@ -1,0 +1,556 @@
+// Pass kernels of the projection (sm_103a).
+//
+//   k_flux      : q = u*/dt - (beta_f - 1/rho0) G phat on every face        (FP64)
+//   k_xfwd      : f = rho0 D(q)  or  r = f - L_h p, then forward x-transform
+//   k_ypass     : forward / inverse y-transform on strided column tiles
+//   k_thomas    : one tridiagonal solve per (kx, ky) z-line (factorised tables)
+//   k_xinv      : inverse x-transform, p = value or p += value
+//   k_correct   : u = dt q - (dt/rho0) G p^(n+1)                             (FP64)
+//   k_divmax    : max |D u| (diagnostics)
+//   k_residmax  : max |f - L_h p| without a transform (mixed final check)
+//
+// The provisional face flux q carries the split: the right-hand side of the
+// constant-coefficient equation is rho0 D(q) (= (rho0/dt) D(u*) +
+// D[(1 - rho0 beta_f) G phat] since rho0 (beta_f - 1/rho0) = -(1 - rho0 beta_f)),
+// and the correction u = u* - dt[G p/rho0 + (beta_f - 1/rho0) G phat] is
+// dt q - (dt/rho0) G p.  Storing q once makes the correction three FP64
+// instructions per face and guarantees that the right-hand side and the
+// correction use the very same face coefficients, so D(u) equals
+// (dt/rho0)(f - L_h p) to round-off.
+#pragma once
+#include "kern_common.cuh"
+#include "kern_fft.cuh"
+
+namespace fz {
+
+enum { BC_PERIODIC = 0, BC_NEUMANN = 1 };
+
+// Grid and physical constants (kernel argument, by value).
+struct GridDev {
+    int nx, ny, nz;
+    int bcx, bcy;
+    // flux constants
+    double idt;        // 1/dt
+    double two_rho_g;  // 2 rho_g
+    double drho;       // rho_l - rho_g
+    double gx2, gx0;   // 2/dx, 1/(rho0 dx)
+    double gy2, gy0;   // 2/dy, 1/(rho0 dy)
+    // divergence constants, unscaled (rho0/h) and scaled by sigma = 1/(4 nx ny)
+    double dvx, dvy, dvx_s, dvy_s;
+    // correction constants
+    double dt, cgx, cgy;  // dt, dt/(rho0 dx), dt/(rho0 dy)
+    // Laplacian / divergence constants
+    double idx2, idy2;    // 1/dx^2, 1/dy^2
+    double idx1, idy1;    // 1/dx, 1/dy
+    // per-k tables (device, FP64, length nz)
+    const double *gz2;    // 2/dzc_(k+1/2)            (0 at k = nz-1)
+    const double *gz0;    // 1/(rho0 dzc_(k+1/2))     (0 at k = nz-1)
+    const double *dvz;    // rho0/dzf_k
+    const double *dvz_s;  // sigma rho0/dzf_k
+    const double *cgz;    // dt/(rho0 dzc_(k+1/2))    (0 at k = nz-1)
+    const double *lza;    // a_k = 1/(dzf_k dzc_(k-1/2)), 0 at k = 0
+    const double *lzc;    // c_k = 1/(dzf_k dzc_(k+1/2)), 0 at k = nz-1
+    const double *izf;    // 1/dzf_k
+    const double *dzf;    // dzf_k
+    const double *dzc;    // dzc_(k+1/2), 0 at k = nz-1
+    double inv_lz;        // 1 / sum_k dzf_k
+    double sigma;         // 1/(4 nx ny)
+};
+
+__device__ __forceinline__ size_t cidx(const GridDev &g, int i, int j, int k) {
+    return ((size_t)k * g.ny + j) * (size_t)g.nx + i;
+}
+
+// ---------------------------------------------------------------------------
+// Provisional face flux q (3 face families).  9 FP64 instructions per face.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_flux(GridDev g, const double *__restrict__ phi,
+                                              const double *__restrict__ pn,
+                                              const double *__restrict__ pnm1,
+                                              const double *__restrict__ u,
+                                              const double *__restrict__ v,
+                                              const double *__restrict__ w,
+                                              double *__restrict__ qx, double *__restrict__ qy,
+                                              double *__restrict__ qz,
+                                              double *__restrict__ usq_part) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int k = blockIdx.z;
+    double usq = 0.0;
+    if (i < g.nx && j < g.ny) {
+        const size_t c = cidx(g, i, j, k);
+        const double phc = phi[c];
+        const double hc = fmaT(2.0, pn[c], -pnm1[c]);
+        const double uc = u[c], vc = v[c], wc = w[c];
+        if (usq_part) usq = fmaT(uc, uc, fmaT(vc, vc, wc * wc));
+        // x-face i+1/2
+        double q = 0.0;
+        if (!(g.bcx == BC_NEUMANN && i == g.nx - 1)) {
+            const size_t e = (i == g.nx - 1) ? c - i : c + 1;
+            const double he = fmaT(2.0, pn[e], -pnm1[e]);
+            const double r = rcp_pos_nr1(fmaT(g.drho, phc + phi[e], g.two_rho_g));
+            const double gh = fmaT(r, g.gx2, -g.gx0);
+            q = fmaT(uc, g.idt, -gh * (he - hc));
+        }
+        qx[c] = q;
+        // y-face j+1/2
+        q = 0.0;
+        if (!(g.bcy == BC_NEUMANN && j == g.ny - 1)) {
+            const size_t nn = (j == g.ny - 1) ? c - (size_t)j * g.nx : c + g.nx;
+            const double hn = fmaT(2.0, pn[nn], -pnm1[nn]);
+            const double r = rcp_pos_nr1(fmaT(g.drho, phc + phi[nn], g.two_rho_g));
+            const double gh = fmaT(r, g.gy2, -g.gy0);
+            q = fmaT(vc, g.idt, -gh * (hn - hc));
+        }
+        qy[c] = q;
+        // z-face k+1/2 (top wall at k = nz-1)
+        q = 0.0;
+        if (k < g.nz - 1) {
+            const size_t t = c + (size_t)g.nx * g.ny;
+            const double ht = fmaT(2.0, pn[t], -pnm1[t]);
+            const double r = rcp_pos_nr1(fmaT(g.drho, phc + phi[t], g.two_rho_g));
+            const double gh = fmaT(r, g.gz2[k], -g.gz0[k]);
+            q = fmaT(wc, g.idt, -gh * (ht - hc));
+        }
+        qz[c] = q;
+    }
+    if (usq_part) {
+        const double s = block_sum(usq);
+        if (threadIdx.x == 0 && threadIdx.y == 0)
+            usq_part[((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = s;
+    }
+}
+
+// Deterministic final sum of per-block partials (one block).
+__global__ void k_sum_partials(const double *__restrict__ part, int n, double *__restrict__ out) {
+    double s = 0.0;
+    for (int t = threadIdx.x; t < n; t += blockDim.x) s += part[t];
+    s = block_sum(s);
+    if (threadIdx.x == 0) *out = s;
+}
+
+// rho0-weighted divergence of q at one cell; cx, cy, cz are rho0/h (maybe scaled).
+__device__ __forceinline__ double div_q(const GridDev &g, int i, int j, int k, double cx, double cy,
+                                        double cz, const double *__restrict__ qx,
+                                        const double *__restrict__ qy,
+                                        const double *__restrict__ qz) {
+    const size_t c = cidx(g, i, j, k);
+    const double qe = qx[c];
+    const double qw = (i > 0) ? qx[c - 1] : (g.bcx == BC_PERIODIC ? qx[c + g.nx - 1] : 0.0);
+    const double qn = qy[c];
+    const double qs = (j > 0) ? qy[c - g.nx] : (g.bcy == BC_PERIODIC ? qy[c + (size_t)(g.ny - 1) * g.nx] : 0.0);
+    const double qt = qz[c];
+    const double qb = (k > 0) ? qz[c - (size_t)g.nx * g.ny] : 0.0;
+    return fmaT(cx, qe - qw, fmaT(cy, qn - qs, cz * (qt - qb)));
+}
+
+// L_h p at one cell in flux (difference) form: each face difference is
+// formed first, so a smooth p loses no accuracy to cancellation.  Wall faces
+// carry zero flux (ghost value = centre value).
+__device__ __forceinline__ double lap(const GridDev &g, int i, int j, int k,
+                                      const double *__restrict__ p) {
+    const size_t c = cidx(g, i, j, k);
+    const double pc = p[c];
+    double pe, pw, pn_, ps;
+    if (i < g.nx - 1) pe = p[c + 1];
+    else pe = (g.bcx == BC_PERIODIC) ? p[c - i] : pc;
+    if (i > 0) pw = p[c - 1];
+    else pw = (g.bcx == BC_PERIODIC) ? p[c + g.nx - 1] : pc;
+    if (j < g.ny - 1) pn_ = p[c + g.nx];
+    else pn_ = (g.bcy == BC_PERIODIC) ? p[c - (size_t)j * g.nx] : pc;
+    if (j > 0) ps = p[c - g.nx];
+    else ps = (g.bcy == BC_PERIODIC) ? p[c + (size_t)(g.ny - 1) * g.nx] : pc;
+    const size_t pl = (size_t)g.nx * g.ny;
+    const double pt = (k < g.nz - 1) ? p[c + pl] : pc;
+    const double pb = (k > 0) ? p[c - pl] : pc;
+    double acc = ((pe - pc) - (pc - pw)) * g.idx2;
+    acc = fmaT((pn_ - pc) - (pc - ps), g.idy2, acc);
+    acc = fmaT(g.lzc[k], pt - pc, acc);
+    return fmaT(-g.lza[k], pc - pb, acc);
+}
+
+__device__ __forceinline__ double resid(const GridDev &g, int i, int j, int k,
+                                        const double *__restrict__ f,
+                                        const double *__restrict__ p) {
+    return f[cidx(g, i, j, k)] - lap(g, i, j, k, p);
+}
+
+// 2^e as a double (e within the normal range)
+__device__ __forceinline__ double pow2d(int e) {
+    return __hiloint2double((e + 1023) << 20, 0);
+}
+// binary exponent of a positive double given by its bit pattern (0 -> 0)
+__device__ __forceinline__ int exp_of_bits(unsigned long long b) {
+    return b ? (int)((b >> 52) & 0x7ff) - 1023 : 0;
+}
+
+// double -> float with the binary exponent shifted by -es (x * 2^-es),
+// truncating; |result| below 2^-126 flushes to zero.  Integer-only.
+__device__ __forceinline__ float f64_to_f32_shift(double x, int es) {
+    const unsigned hi = (unsigned)__double2hiint(x);
+    const unsigned lo = (unsigned)__double2loint(x);
+    const int e = (int)((hi >> 20) & 0x7ff) - es;  // biased double exponent after the shift
+    if (e <= 896) return __uint_as_float(hi & 0x80000000u);
+    const unsigned b = ((unsigned)(e - 896) << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29);
+    return __uint_as_float(b | (hi & 0x80000000u));
+}
+// float -> double times 2^es (flush float denormals to zero).  Integer-only.
+__device__ __forceinline__ double f32_to_f64_shift(float f, int es) {
+    const unsigned b = __float_as_uint(f);
+    const unsigned a = b & 0x7fffffffu;
+    if (a < 0x00800000u) return __hiloint2double((int)(b & 0x80000000u), 0);
+    const unsigned hi = (((a >> 23) + 896u + (unsigned)es) << 20) | ((a >> 3) & 0xfffffu);
+    return __hiloint2double((int)(hi | (b & 0x80000000u)), (int)(a << 29));
+}
+
+enum {
+    XF_F64_DIVQ = 0,   // FP64 mode: sigma rho0 D(q), FP64 transform
+    XF_MIX_DIVQ = 1,   // mixed: f = rho0 D(q) stored (FP64), FP32 transform of sigma f
+    XF_MIX_RESID = 2   // mixed: r = f - L_h p, FP32 transform of sigma 2^-e r
+};
+
+struct XArgs {
+    const double *qx, *qy, *qz;  // divergence sources
+    const double *f;             // residual source f (MIX_RESID)
+    const double *p;             // residual source p (MIX_RESID)
+    double *f_out;               // MIX_DIVQ: f stored here
+    void *out;                   // transformed output (T), [nz][ny][nx]
+    DevStats *st;
+    int slot;                    // residual slot (MIX_RESID)
+    double tol;
+    int track_fmax;              // F64_DIVQ: record max|sigma f|
+};
+
+// Forward x-pass: per CTA 2L real x-lines (flattened line index (k, j)).
+template <typename T, int MODE>
+__global__ void __launch_bounds__(256) k_xfwd(GridDev g, FFTDesc D, int L, XArgs a) {
+    typedef typename C2<T>::t T2;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int n = D.n, ls = n + 1;
+    T2 *tw_s = (T2 *)smem_raw;
+    T2 *cs_s = tw_s + n;
+    T2 *A = cs_s + (n / 2 + 2);
+    T2 *B = A + L * ls;
+    if (MODE == XF_MIX_RESID && a.st->converged) return;
+    load_tables<T>(D, tw_s, cs_s);
+    const int nlines = g.ny * g.nz;
+    const int line0 = blockIdx.x * 2 * L;
+    unsigned long long mx = 0ull;
+    int ef = 0;
+    float scale32 = (float)g.sigma;
+    if (MODE == XF_MIX_RESID) {
+        ef = exp_of_bits(a.st->fmax_bits);
+    }
+    // 1. source values into the packed complex lines
+    for (int idx = threadIdx.x; idx < 2 * L * n; idx += blockDim.x) {
+        const int r = idx / n, i = idx - r * n;
+        const int line = line0 + r;
+        T val = (T)0;
+        if (line < nlines) {
+            const int j = line % g.ny, k = line / g.ny;
+            if (MODE == XF_F64_DIVQ) {
+                const double f = div_q(g, i, j, k, g.dvx_s, g.dvy_s, g.dvz_s[k], a.qx, a.qy, a.qz);
+                if (a.track_fmax) mx = umax64(mx, absbits(f));
+                val = (T)f;
+            } else if (MODE == XF_MIX_DIVQ) {
+                const double f = div_q(g, i, j, k, g.dvx, g.dvy, g.dvz[k], a.qx, a.qy, a.qz);
+                a.f_out[cidx(g, i, j, k)] = f;
+                mx = umax64(mx, absbits(f));
+                val = (T)(f64_to_f32_shift(f, 0) * scale32);
+            } else {
+                const double rr = resid(g, i, j, k, a.f, a.p);
+                mx = umax64(mx, absbits(rr));
+                val = (T)(f64_to_f32_shift(rr, ef) * scale32);
+            }
+        }
+        ((T *)(A + (r >> 1) * ls))[2 * line_pos(i, n, D.kind) + (r & 1)] = val;
+    }
+    if (MODE == XF_MIX_DIVQ) block_max_atomic(mx, &a.st->fmax_bits);
+    if (MODE == XF_F64_DIVQ && a.track_fmax) block_max_atomic(mx, &a.st->fmax_bits);
+    if (MODE == XF_MIX_RESID) block_max_atomic(mx, &a.st->rmax_bits[a.slot]);
+    __syncthreads();
+    // 2. complex FFT
+    const T2 *Z = fft_lines<T, false>(A, B, L, ls, D, tw_s);
+    // 3. separate and store
+    T *out = (T *)a.out;
+    const int M = n / 2 + 1;
+    for (int t = threadIdx.x; t < L * M; t += blockDim.x) {
+        const int l = t / M, m = t - l * M;
+        const int la = line0 + 2 * l;
+        fwd_separate<T>(Z + l * ls, n, m, D.kind, cs_s, [&](int ab, int ix, T v) {
+            const int line = la + ab;
+            if (line < nlines) out[(size_t)line * n + ix] = v;
+        });
+    }
+    // 4. mixed residual: the last block to finish decides convergence
+    if (MODE == XF_MIX_RESID) {
+        __shared__ int last;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            const unsigned ticket = atomicAdd(&a.st->done_blocks[a.slot], 1u);
+            last = (ticket == gridDim.x - 1);
+        }
+        __syncthreads();
+        if (last && threadIdx.x == 0) {
+            __threadfence();
+            const unsigned long long rb = atomicMax(&a.st->rmax_bits[a.slot], 0ull);
+            const double rmax = __longlong_as_double((long long)rb);
+            const double fmax = __longlong_as_double((long long)a.st->fmax_bits);
+            const double rel = fmax > 0.0 ? rmax / fmax : rmax;
+            a.st->relres = rel;
+            a.st->n_resid = a.slot + 1;
+            a.st->iterations = a.slot;
+            if (rel <= a.tol) a.st->converged = 1;
+        }
+    }
+}
+
+// Residual-only check (no transform): max |f - L_h p| into rmax_bits[slot];
+// the last block sets relres/converged.  f_from_q != 0: f = rho0 D(q) on the fly.
+__global__ void __launch_bounds__(256) k_residmax(GridDev g, XArgs a, int f_from_q) {
+    if (a.st->converged && !f_from_q) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y, k = blockIdx.z;
+    unsigned long long mx = 0ull, fm = 0ull;
+    if (i < g.nx) {
+        if (f_from_q) {  // FP64-mode check: f recomputed from q
+            const double f = div_q(g, i, j, k, g.dvx, g.dvy, g.dvz[k], a.qx, a.qy, a.qz);
+            fm = absbits(f);
+            mx = absbits(f - lap(g, i, j, k, a.p));
+        } else {
+            mx = absbits(resid(g, i, j, k, a.f, a.p));
+        }
+    }
+    block_max_atomic(mx, &a.st->rmax_bits[a.slot]);
+    if (f_from_q) block_max_atomic(fm, &a.st->fmax_bits);
+    __shared__ int last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned nb = gridDim.x * gridDim.y * gridDim.z;
+        const unsigned ticket = atomicAdd(&a.st->done_blocks[a.slot], 1u);
+        last = (ticket == nb - 1);
+    }
+    __syncthreads();
+    if (last && threadIdx.x == 0) {
+        __threadfence();
+        const unsigned long long rb = atomicMax(&a.st->rmax_bits[a.slot], 0ull);
+        const unsigned long long fb = atomicMax(&a.st->fmax_bits, 0ull);
+        const double rmax = __longlong_as_double((long long)rb);
+        const double fmax = __longlong_as_double((long long)fb);
+        const double rel = fmax > 0.0 ? rmax / fmax : rmax;
+        a.st->relres = rel;
+        if (!f_from_q) {
+            a.st->n_resid = a.slot + 1;
+            a.st->iterations = a.slot;
+            if (rel <= a.tol) a.st->converged = 1;
+        }
+    }
+}
+
+// Forward / inverse y-pass on a tile of TX columns of plane k (in place).
+template <typename T, bool INV>
+__global__ void __launch_bounds__(256) k_ypass(int nx, int ny, FFTDesc D, int TX, T *data,
+                                               const int *conv) {
+    typedef typename C2<T>::t T2;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    if (conv && *conv) return;
+    const int n = D.n, ls = n + 1;
+    const int L = TX / 2;
+    T2 *tw_s = (T2 *)smem_raw;
+    T2 *cs_s = tw_s + n;
+    T2 *A = cs_s + (n / 2 + 2);
+    T2 *B = A + L * ls;
+    load_tables<T>(D, tw_s, cs_s);
+    const int i0 = blockIdx.x * TX;
+    const int ncols = min(TX, nx - i0);
+    T *plane = data + (size_t)blockIdx.y * ny * nx + i0;
+    const int M = n / 2 + 1;
+    if (!INV) {
+        for (int idx = threadIdx.x; idx < n * TX; idx += blockDim.x) {
+            const int j = idx / TX, c = idx - j * TX;
+            const T val = (c < ncols) ? plane[(size_t)j * nx + c] : (T)0;
+            ((T *)(A + (c >> 1) * ls))[2 * line_pos(j, n, D.kind) + (c & 1)] = val;
+        }
+        __syncthreads();
+        const T2 *Z = fft_lines<T, false>(A, B, L, ls, D, tw_s);
+        for (int t = threadIdx.x; t < L * M; t += blockDim.x) {
+            const int m = t / L, l = t - m * L;
+            fwd_separate<T>(Z + l * ls, n, m, D.kind, cs_s, [&](int ab, int ix, T v) {
+                const int c = 2 * l + ab;
+                if (c < ncols) plane[(size_t)ix * nx + c] = v;
+            });
+        }
+    } else {
+        __syncthreads();
+        for (int t = threadIdx.x; t < L * M; t += blockDim.x) {
+            const int m = t / L, l = t - m * L;
+            inv_combine<T>(A + l * ls, n, m, D.kind, cs_s, [&](int ab, int ix) -> T {
+                const int c = 2 * l + ab;
+                return (c < ncols) ? plane[(size_t)ix * nx + c] : (T)0;
+            });
+        }
+        __syncthreads();
+        const T2 *Z = fft_lines<T, true>(A, B, L, ls, D, tw_s);
+        for (int idx = threadIdx.x; idx < n * TX; idx += blockDim.x) {
+            const int j = idx / TX, c = idx - j * TX;
+            if (c < ncols)
+                plane[(size_t)j * nx + c] = ((const T *)(Z + (c >> 1) * ls))[2 * line_pos(j, n, D.kind) + (c & 1)];
+        }
+    }
+}
+
+enum { XI_STORE = 0, XI_ACCUM = 1 };
+
+// Inverse x-pass: per CTA 2L real x-lines; writes p (FP64).
+template <typename T, int MODE>
+__global__ void __launch_bounds__(256) k_xinv(GridDev g, FFTDesc D, int L, const T *in, double *p,
+                                              const DevStats *st) {
+    typedef typename C2<T>::t T2;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    if (MODE == XI_ACCUM && st->converged) return;
+    const int n = D.n, ls = n + 1;
+    T2 *tw_s = (T2 *)smem_raw;
+    T2 *cs_s = tw_s + n;
+    T2 *A = cs_s + (n / 2 + 2);
+    T2 *B = A + L * ls;
+    load_tables<T>(D, tw_s, cs_s);
+    const int nlines = g.ny * g.nz;
+    const int line0 = blockIdx.x * 2 * L;
+    const int M = n / 2 + 1;
+    __syncthreads();
+    for (int t = threadIdx.x; t < L * M; t += blockDim.x) {
+        const int l = t / M, m = t - l * M;
+        const int la = line0 + 2 * l;
+        inv_combine<T>(A + l * ls, n, m, D.kind, cs_s, [&](int ab, int ix) -> T {
+            const int line = la + ab;
+            return (line < nlines) ? in[(size_t)line * n + ix] : (T)0;
+        });
+    }
+    __syncthreads();
+    const T2 *Z = fft_lines<T, true>(A, B, L, ls, D, tw_s);
+    int ef = 0;
+    if (MODE == XI_ACCUM) ef = exp_of_bits(st->fmax_bits);
+    for (int idx = threadIdx.x; idx < 2 * L * n; idx += blockDim.x) {
+        const int r = idx / n, i = idx - r * n;
+        const int line = line0 + r;
+        if (line < nlines) {
+            const T v = ((const T *)(Z + (r >> 1) * ls))[2 * line_pos(i, n, D.kind) + (r & 1)];
+            double *dst = p + (size_t)line * n + i;
+            if (MODE == XI_STORE) {
+                if (sizeof(T) == 8) *dst = (double)v;
+                else *dst = f32_to_f64_shift((float)v, 0);
+            } else {
+                *dst = *dst + f32_to_f64_shift((float)v, ef);
+            }
+        }
+    }
+}
+
+// Tridiagonal z-solves.  One thread per (kx, ky) line; the forward sweep keeps
+// its modified right-hand side in place, the backward sweep overwrites it with
+// the solution.  Factorisation tables m_k and 1/beta_k depend only on the
+// eigenvalue pair, stored once per distinct pair: index ((k*Uy + uy)*Ux + ux).
+// The (0,0) line is singular: its right-hand side mean is removed, the fluxes
+// are integrated from the bottom wall and the result is given zero
+// dzf-weighted mean (the pressure gauge).
+template <typename T>
+__global__ void __launch_bounds__(128) k_thomas(GridDev g, int Ux, int Uy, const T *__restrict__ mtab,
+                                                const T *__restrict__ ibtab,
+                                                const T *__restrict__ cup, T *data,
+                                                const int *conv) {
+    if (conv && *conv) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y;
+    if (i >= g.nx) return;
+    const size_t plane = (size_t)g.nx * g.ny;
+    T *d = data + (size_t)j * g.nx + i;
+    const int nz = g.nz;
+    if (i == 0 && j == 0) {
+        double s = 0.0;
+        for (int k = 0; k < nz; ++k) s = fmaT(g.dzf[k], (double)d[k * plane], s);
+        const double fbar = s * g.inv_lz;
+        double F = 0.0, pk = 0.0, ps = 0.0;
+        for (int k = 0; k < nz; ++k) {
+            const double fk = (double)d[k * plane];  // read f_k before p_k overwrites it
+            d[k * plane] = (T)pk;
+            ps = fmaT(g.dzf[k], pk, ps);
+            if (k < nz - 1) {
+                F = fmaT(g.dzf[k], fk - fbar, F);  // flux at face k+1/2
+                pk = fmaT(g.dzc[k], F, pk);        // p_(k+1)
+            }
+        }
+        const double pbar = ps * g.inv_lz;
+        for (int k = 0; k < nz; ++k) d[k * plane] = (T)((double)d[k * plane] - pbar);
+        return;
+    }
+    const int ux = (g.bcx == BC_PERIODIC) ? min(i, g.nx - i) : i;
+    const int uy = (g.bcy == BC_PERIODIC) ? min(j, g.ny - j) : j;
+    const size_t tb = (size_t)uy * Ux + ux;
+    const size_t ts = (size_t)Ux * Uy;
+    T prev = d[0];
+    for (int k = 1; k < nz; ++k) {
+        prev = fmaT(-mtab[k * ts + tb], prev, d[k * plane]);
+        d[k * plane] = prev;
+    }
+    T pk = prev * ibtab[(nz - 1) * ts + tb];
+    d[(nz - 1) * plane] = pk;
+    for (int k = nz - 2; k >= 0; --k) {
+        pk = fmaT(-cup[k], pk, d[k * plane]) * ibtab[k * ts + tb];
+        d[k * plane] = pk;
+    }
+}
+
+// u = dt q - (dt/rho0) G p on non-wall faces; wall faces 0.  3 FP64 per face.
+__global__ void __launch_bounds__(256) k_correct(GridDev g, const double *__restrict__ p,
+                                                 const double *__restrict__ qx,
+                                                 const double *__restrict__ qy,
+                                                 const double *__restrict__ qz,
+                                                 double *__restrict__ u, double *__restrict__ v,
+                                                 double *__restrict__ w) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int k = blockIdx.z;
+    if (i >= g.nx || j >= g.ny) return;
+    const size_t c = cidx(g, i, j, k);
+    const double pc = p[c];
+    double r = 0.0;
+    if (!(g.bcx == BC_NEUMANN && i == g.nx - 1)) {
+        const size_t e = (i == g.nx - 1) ? c - i : c + 1;
+        r = fmaT(-g.cgx, p[e] - pc, g.dt * qx[c]);
+    }
+    u[c] = r;
+    r = 0.0;
+    if (!(g.bcy == BC_NEUMANN && j == g.ny - 1)) {
+        const size_t nn = (j == g.ny - 1) ? c - (size_t)j * g.nx : c + g.nx;
+        r = fmaT(-g.cgy, p[nn] - pc, g.dt * qy[c]);
+    }
+    v[c] = r;
+    r = 0.0;
+    if (k < g.nz - 1) r = fmaT(-g.cgz[k], p[c + (size_t)g.nx * g.ny] - pc, g.dt * qz[c]);
+    w[c] = r;
+}
+
+// max |D u| (diagnostics).
+__global__ void __launch_bounds__(256) k_divmax(GridDev g, const double *__restrict__ u,
+                                                const double *__restrict__ v,
+                                                const double *__restrict__ w, DevStats *st) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y, k = blockIdx.z;
+    unsigned long long mx = 0ull;
+    if (i < g.nx) {
+        const size_t c = cidx(g, i, j, k);
+        const double ue = (g.bcx == BC_NEUMANN && i == g.nx - 1) ? 0.0 : u[c];
+        const double uw = (i > 0) ? u[c - 1] : (g.bcx == BC_PERIODIC ? u[c + g.nx - 1] : 0.0);
+        const double vn = (g.bcy == BC_NEUMANN && j == g.ny - 1) ? 0.0 : v[c];
+        const double vs = (j > 0) ? v[c - g.nx] : (g.bcy == BC_PERIODIC ? v[c + (size_t)(g.ny - 1) * g.nx] : 0.0);
+        const double wt = (k == g.nz - 1) ? 0.0 : w[c];
+        const double wb = (k > 0) ? w[c - (size_t)g.nx * g.ny] : 0.0;
+        const double d = fmaT(ue - uw, g.idx1, fmaT(vn - vs, g.idy1, (wt - wb) * g.izf[k]));
+        mx = absbits(d);
+    }
+    block_max_atomic(mx, &st->divmax_bits);
+}
+
+}  // namespace fz

@@ -1,0 +1,71 @@
+"""C-ABI library checks that need no GPU: it loads, exports every symbol the
+header declares, and rejects bad descriptors on the host before any CUDA call."""
+import ctypes
+import os
+import re
+
+import pytest
+
+import paper_2502_04189_b300 as F
+from paper_2502_04189_b300 import _abi
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def header_symbols():
+    txt = open(os.path.join(ROOT, "include", "fizzy_proj.h")).read()
+    return sorted(set(re.findall(r"\b(fizzy_[a-z_]+)\s*\(", txt)))
+
+
+def test_library_exports_every_declared_symbol():
+    L = _abi.lib()
+    declared = header_symbols()
+    assert declared, "no declarations parsed"
+    for name in declared:
+        assert hasattr(L, name), name
+    assert sorted(_abi.EXPORTED) == declared
+
+
+def test_errstr():
+    L = _abi.lib()
+    assert L.fizzy_proj_errstr(0) == b"ok"
+    assert L.fizzy_proj_errstr(-5) == b"not converged"
+    assert L.fizzy_proj_errstr(-99) == b"unknown error"
+
+
+def base(**kw):
+    d = dict(nx=16, ny=12, nz=8, dx=1 / 16, dy=1 / 12, dz=1 / 8)
+    d.update(kw)
+    return d
+
+
+@pytest.mark.parametrize("kw,code", [
+    (dict(nx=1), -1), (dict(nz=1), -1), (dict(dx=0.0), -1), (dict(dz=-1.0), -1),
+    (dict(rho_l=0.0), -1), (dict(rho_g=-1.0), -1), (dict(dt=0.0), -1), (dict(bcx=7), -1),
+    (dict(precision=3), -1), (dict(max_refine=99), -1), (dict(nx=10), -2), (dict(ny=14), -2),
+    (dict(nx=2048), -2), (dict(zf=[0.0, 0.5, 0.4, 1.0], nz=3), -1)])
+def test_plan_rejects_bad_descriptors(kw, code):
+    d, keep = F.make_desc(**base(**kw))
+    h = ctypes.c_void_p()
+    rc = _abi.lib().fizzy_proj_plan(ctypes.byref(h), ctypes.byref(d), None)
+    assert rc == code
+    assert not h.value
+    assert _abi.lib().fizzy_proj_workspace_bytes(ctypes.byref(d)) == 0
+
+
+def test_null_plan_calls_are_safe():
+    L = _abi.lib()
+    assert L.fizzy_proj_destroy(None) == 0
+    assert L.fizzy_proj_solve(None, *([None] * 7), None, None) == -1
+    assert L.fizzy_proj_plan(None, None, None) == -1
+    assert L.fizzy_proj_launches_per_solve(None) == 0
+
+
+def test_workspace_bytes_scale():
+    b1 = F.workspace_bytes(**base())
+    b2 = F.workspace_bytes(**base(nz=16))
+    bm = F.workspace_bytes(**base(precision=1))
+    assert 0 < b1 < b2
+    assert bm > b1
+    big = F.workspace_bytes(nx=512, ny=512, nz=512, dx=1, dy=1, dz=1, precision=1)
+    assert 4e9 < big < 8e9

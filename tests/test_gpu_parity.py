@@ -1,0 +1,153 @@
+"""GPU projection vs the FP64 CPU oracle, element by element (needs a B300).
+
+Tolerances: max relative error (max|x_gpu - x_oracle| / max|x_oracle|, p after
+removing its dzf-weighted mean, u over all three face families) <= 1e-12 in
+FP64 mode and <= 1e-9 in mixed mode after refinement to relres <= 1e-10;
+max|D u| dx / U <= 1e-10.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+import paper_2502_04189_b300 as F
+from paper_2502_04189_b300 import inputs as I
+
+from gpu_util import compare, gpu_project, relerr, to_dev
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-12
+TOLMIX = 1e-9
+
+
+def small_cases():
+    return {
+        "drop32": I.drop32_spec(),
+        "b48x36x20_nx_stretch": I.CaseSpec(nx=48, ny=36, nz=20, bcx=1, bcy=0, beta=1.5,
+                                           n_bubbles=3, radius_cells=4, config=11),
+        "b96x64x33": I.CaseSpec(nx=96, ny=64, nz=33, n_bubbles=4, radius_cells=5, config=12),
+        "b27x18x12_ny": I.CaseSpec(nx=27, ny=18, nz=12, bcx=0, bcy=1, n_bubbles=1,
+                                   radius_cells=3, config=13),
+        "b384x6x5": I.CaseSpec(nx=384, ny=6, nz=5, bcx=1, bcy=1, n_bubbles=1, radius_cells=2,
+                               config=14),
+        "b6x512x4": I.CaseSpec(nx=6, ny=512, nz=4, bcx=0, bcy=0, n_bubbles=1, radius_cells=1,
+                               config=15),
+        "b1024x4x3": I.CaseSpec(nx=1024, ny=4, nz=3, bcx=0, bcy=1, n_bubbles=1,
+                                radius_cells=1, config=16),
+        "b2x2x2": I.CaseSpec(nx=2, ny=2, nz=2, bcx=0, bcy=1, n_bubbles=1, radius_cells=0.5,
+                             config=17, velocity="iid"),
+        "b81x3x7_nn": I.CaseSpec(nx=81, ny=3, nz=7, bcx=1, bcy=1, beta=2.0, n_bubbles=1,
+                                 radius_cells=2, config=18),
+    }
+
+
+CASES = small_cases()
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_fp64_matches_oracle(cuda_ok, name):
+    c = I.make_case(CASES[name])
+    ref = O.project_case(c)
+    got = gpu_project(c, F.FP64)
+    ep, eu = compare(c, got, ref)
+    assert ep <= TOL64, ep
+    assert eu <= TOL64, eu
+    st = got["stats"]
+    assert st["relres"] < 1e-11
+    assert st["div_metric"] < 1e-10
+    assert abs(O.weighted_mean(O.Grid.of_case(c), got["p"])) <= 1e-12 * np.max(np.abs(got["p"]))
+
+
+@pytest.mark.parametrize("name", ["drop32", "b48x36x20_nx_stretch", "b96x64x33", "b27x18x12_ny",
+                                  "b384x6x5", "b81x3x7_nn"])
+def test_mixed_matches_oracle(cuda_ok, name):
+    c = I.make_case(CASES[name])
+    ref = O.project_case(c)
+    got = gpu_project(c, F.MIXED)
+    st = got["stats"]
+    assert st["converged"] == 1
+    assert st["relres"] <= 1e-10
+    assert 1 <= st["iterations"] <= 4
+    ep, eu = compare(c, got, ref)
+    assert ep <= TOLMIX, ep
+    assert eu <= TOLMIX, eu
+    assert st["div_metric"] < 1e-10
+
+
+def test_equal_density_closed_form(cuda_ok):
+    """rho_l = rho_g and u* = s + G q (s a discrete curl): p = (rho0/dt) q, u = s."""
+    spec = I.CaseSpec(nx=48, ny=32, nz=24, bcx=1, bcy=0, beta=1.5, n_bubbles=2,
+                      radius_cells=3, rho_l=0.5, rho_g=0.5, dt=1e-3, noise=0.0, config=21)
+    c = I.make_case(spec)
+    g = O.Grid.of_case(c)
+    s = (c.u.copy(), c.v.copy(), c.w.copy())
+    q = np.random.default_rng(4).standard_normal(g.shape)
+    gq = O.grad(g, q)
+    c.u, c.v, c.w = (s[a] + gq[a] for a in range(3))
+    for prec, tol in ((F.FP64, 1e-11), (F.MIXED, 1e-9)):
+        got = gpu_project(c, prec)
+        p_exact = (0.5 / 1e-3) * (q - O.weighted_mean(g, q))
+        assert relerr(got["p"] - O.weighted_mean(g, got["p"]), p_exact) < tol
+        for a, key in enumerate("uvw"):
+            assert np.max(np.abs(got[key] - s[a])) < tol * np.max(np.abs(gq[a]) + np.abs(s[a]))
+
+
+def test_repeat_is_bitwise_deterministic(cuda_ok):
+    c = I.make_case(CASES["b96x64x33"])
+    for prec in (F.FP64, F.MIXED):
+        plan = F.Plan.for_case(c, precision=prec, check=True)
+        a = gpu_project(c, plan=plan)
+        b = gpu_project(c, plan=plan)
+        plan.close()
+        for k in ("p", "u", "v", "w"):
+            assert np.array_equal(a[k], b[k]), k
+
+
+def test_not_converged_is_reported(cuda_ok):
+    c = I.make_case(CASES["b48x36x20_nx_stretch"])
+    plan = F.Plan.for_case(c, precision=F.MIXED, check=True, tol=1e-30, max_refine=1)
+    got = gpu_project(c, plan=plan)
+    plan.close()
+    st = got["stats"]
+    assert st["converged"] == 0
+    assert st["iterations"] == 1
+    assert st["relres"] > 0
+    ref = O.project_case(c)
+    ep, eu = compare(c, got, ref)
+    assert ep < 1e-6  # one sweep still lands close
+
+
+def test_solve_host_matches_device(cuda_ok):
+    c = I.make_case(CASES["b96x64x33"])
+    plan = F.Plan.for_case(c, precision=F.FP64)
+    d = gpu_project(c, plan=plan)
+    u, v, w = c.u.copy(), c.v.copy(), c.w.copy()
+    p = np.empty_like(c.phi)
+    plan.solve_host(c.phi, c.pn, c.pnm1, u, v, w, p)
+    plan.close()
+    for key, arr in (("p", p), ("u", u), ("v", v), ("w", w)):
+        assert np.array_equal(arr, d[key]), key
+
+
+def test_native_library_is_loaded(cuda_ok):
+    c = I.make_case(CASES["drop32"])
+    gpu_project(c)
+    maps = open("/proc/self/maps").read()
+    assert "libfizzyproj.so" in maps
+
+
+# ---------------------------------------------------------------------------
+# Full-size workloads, in the launch configuration bench.py times
+# ---------------------------------------------------------------------------
+def test_bubbles256_fp64_full_size(cuda_ok):
+    c = I.make_case(I.bubbles256_spec())
+    ref = O.project_case(c)
+    got = gpu_project(c, F.FP64)
+    ep, eu = compare(c, got, ref)
+    assert ep <= TOL64, ep
+    assert eu <= TOL64, eu
+    assert got["stats"]["div_metric"] <= 1e-10
+    got_m = gpu_project(c, F.MIXED)
+    ep, eu = compare(c, got_m, ref)
+    assert got_m["stats"]["relres"] <= 1e-10
+    assert ep <= TOLMIX and eu <= TOLMIX, (ep, eu)
