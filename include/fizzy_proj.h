@@ -79,17 +79,19 @@ typedef struct fizzy_proj_desc {
     int precision;        /* FIZZY_PREC_FP64 or FIZZY_PREC_MIXED                                */
     double tol;           /* mixed: stop when max|f - L p| / max|f| <= tol (0 -> 1e-10)         */
     int max_refine;       /* mixed: at most this many refinement sweeps (0 -> 4, max 16)        */
+    double div_tol;       /* mixed: also stop only when max|D u| dx / U <= div_tol, with U the   */
+                          /* rms of u* and D u = (dt/rho0)(f - L p) (0 -> 1e-10; < 0 -> off)    */
     unsigned flags;       /* FIZZY_FLAG_*                                                       */
 } fizzy_proj_desc;
 
 /* Diagnostics of the last solve (host memory). */
 typedef struct fizzy_proj_stats {
     int iterations;    /* mixed: refinement sweeps run (0 in FP64 mode)                          */
-    int converged;     /* mixed: 1 if relres <= tol; FP64 mode: 1                                */
+    int converged;     /* mixed: 1 if relres <= tol and the divergence estimate <= div_tol; FP64: 1 */
     double relres;     /* max|f - L p| / max|f| (mixed always; FP64 only with FIZZY_FLAG_CHECK)  */
     double f_max;      /* max|f|                                                                 */
     double div_max;    /* max|D u| over all cells (FIZZY_FLAG_CHECK)                             */
-    double u_rms;      /* rms of u* over all face values (FIZZY_FLAG_CHECK)                      */
+    double u_rms;      /* rms of u* over all face values (mixed always; FP64 with FIZZY_FLAG_CHECK) */
     double div_metric; /* div_max * dx / u_rms (FIZZY_FLAG_CHECK)                                */
 } fizzy_proj_stats;
 

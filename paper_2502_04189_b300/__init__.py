@@ -43,7 +43,7 @@ def _ptr(t):
 
 
 def make_desc(nx, ny, nz, dx, dy, zf=None, dz=None, bcx=PERIODIC, bcy=PERIODIC, rho_l=1.0,
-              rho_g=1e-3, dt=1e-4, precision=FP64, tol=0.0, max_refine=0, flags=0):
+              rho_g=1e-3, dt=1e-4, precision=FP64, tol=0.0, max_refine=0, flags=0, div_tol=0.0):
     d = _abi.Desc()
     d.nx, d.ny, d.nz = int(nx), int(ny), int(nz)
     d.dx, d.dy = float(dx), float(dy)
@@ -57,6 +57,7 @@ def make_desc(nx, ny, nz, dx, dy, zf=None, dz=None, bcx=PERIODIC, bcy=PERIODIC, 
     d.bc_x, d.bc_y = int(bcx), int(bcy)
     d.rho_l, d.rho_g, d.dt = float(rho_l), float(rho_g), float(dt)
     d.precision, d.tol, d.max_refine, d.flags = int(precision), float(tol), int(max_refine), int(flags)
+    d.div_tol = float(div_tol)
     return d, keep
 
 
@@ -70,11 +71,11 @@ class Plan:
 
     def __init__(self, nx, ny, nz, dx, dy, zf=None, dz=None, bcx=PERIODIC, bcy=PERIODIC,
                  rho_l=1.0, rho_g=1e-3, dt=1e-4, precision=FP64, tol=0.0, max_refine=0,
-                 check=False, stream=None):
+                 check=False, stream=None, div_tol=0.0):
         self.shape = (int(nz), int(ny), int(nx))
         self.precision = precision
         d, keep = make_desc(nx, ny, nz, dx, dy, zf, dz, bcx, bcy, rho_l, rho_g, dt, precision,
-                            tol, max_refine, FLAG_CHECK if check else 0)
+                            tol, max_refine, FLAG_CHECK if check else 0, div_tol)
         h = ctypes.c_void_p()
         rc = _abi.lib().fizzy_proj_plan(ctypes.byref(h), ctypes.byref(d),
                                         ctypes.c_void_p(0) if stream is None else _stream_handle(stream))

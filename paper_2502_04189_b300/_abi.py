@@ -25,7 +25,8 @@ class Desc(ctypes.Structure):
                 ("bc_x", ctypes.c_int), ("bc_y", ctypes.c_int),
                 ("rho_l", ctypes.c_double), ("rho_g", ctypes.c_double), ("dt", ctypes.c_double),
                 ("precision", ctypes.c_int), ("tol", ctypes.c_double),
-                ("max_refine", ctypes.c_int), ("flags", ctypes.c_uint)]
+                ("max_refine", ctypes.c_int), ("div_tol", ctypes.c_double),
+                ("flags", ctypes.c_uint)]
 
 
 class Stats(ctypes.Structure):

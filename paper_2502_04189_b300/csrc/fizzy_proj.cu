@@ -28,6 +28,7 @@ struct fizzy_proj_plan_s {
     std::vector<double> zf;
     int mixed = 0, check = 0;
     double tol = 1e-10;
+    double div_tol = 1e-10;
     int max_refine = 4;
     GridDev g;
     double sigma = 0.0;
@@ -271,6 +272,7 @@ int fizzy_proj_plan(fizzy_proj_plan_t *out, const fizzy_proj_desc *d, void *stre
     p->check = (d->flags & FIZZY_FLAG_CHECK) ? 1 : 0;
     p->tol = d->tol > 0 ? d->tol : 1e-10;
     p->max_refine = d->max_refine > 0 ? d->max_refine : 4;
+    p->div_tol = d->div_tol > 0 ? d->div_tol : (d->div_tol < 0 ? -1.0 : 1e-10);
     const int nx = d->nx, ny = d->ny, nz = d->nz;
     const size_t N = (size_t)nx * ny * nz;
     p->zf.resize(nz + 1);
@@ -290,13 +292,13 @@ int fizzy_proj_plan(fizzy_proj_plan_t *out, const fizzy_proj_desc *d, void *stre
     p->sigma = 1.0 / (4.0 * (double)nx * (double)ny);
     const double sig = p->sigma;
     // per-k tables, packed: 11 arrays of nz
-    enum { T_GZ2, T_GZ0, T_DVZ, T_DVZS, T_CGZ, T_LZA, T_LZC, T_IZF, T_DZF, T_DZC, T_NTAB };
+    enum { T_CHZ, T_DVZ, T_DVZS, T_CGZ, T_LZA, T_LZC, T_IZF, T_DZF, T_DZC, T_NTAB };
+    const double adrho = std::fabs(d->rho_l - d->rho_g);
     std::vector<double> zt((size_t)T_NTAB * nz, 0.0);
     for (int k = 0; k < nz; ++k) {
         const bool top = (k == nz - 1);
         const double idzc = top ? 0.0 : 1.0 / dzc[k];
-        zt[T_GZ2 * nz + k] = 2.0 * idzc;
-        zt[T_GZ0 * nz + k] = idzc / rho0;
+        zt[T_CHZ * nz + k] = adrho / rho0 * idzc;
         zt[T_DVZ * nz + k] = rho0 / dzf[k];
         zt[T_DVZS * nz + k] = sig * rho0 / dzf[k];
         zt[T_CGZ * nz + k] = d->dt / rho0 * idzc;
@@ -323,12 +325,10 @@ int fizzy_proj_plan(fizzy_proj_plan_t *out, const fizzy_proj_desc *d, void *stre
     g.bcx = d->bc_x;
     g.bcy = d->bc_y;
     g.idt = 1.0 / d->dt;
-    g.two_rho_g = 2.0 * d->rho_g;
-    g.drho = d->rho_l - d->rho_g;
-    g.gx2 = 2.0 / d->dx;
-    g.gx0 = 1.0 / (rho0 * d->dx);
-    g.gy2 = 2.0 / d->dy;
-    g.gy0 = 1.0 / (rho0 * d->dy);
+    g.two_rho0 = 2.0 * rho0;
+    g.adrho = adrho;
+    g.chx = adrho / (rho0 * d->dx);
+    g.chy = adrho / (rho0 * d->dy);
     g.dvx = rho0 / d->dx;
     g.dvy = rho0 / d->dy;
     g.dvx_s = sig * rho0 / d->dx;
@@ -340,8 +340,7 @@ int fizzy_proj_plan(fizzy_proj_plan_t *out, const fizzy_proj_desc *d, void *stre
     g.idy2 = 1.0 / (d->dy * d->dy);
     g.idx1 = 1.0 / d->dx;
     g.idy1 = 1.0 / d->dy;
-    g.gz2 = zt_d + T_GZ2 * nz;
-    g.gz0 = zt_d + T_GZ0 * nz;
+    g.chz = zt_d + T_CHZ * nz;
     g.dvz = zt_d + T_DVZ * nz;
     g.dvz_s = zt_d + T_DVZS * nz;
     g.cgz = zt_d + T_CGZ * nz;
@@ -352,6 +351,9 @@ int fizzy_proj_plan(fizzy_proj_plan_t *out, const fizzy_proj_desc *d, void *stre
     g.dzc = zt_d + T_DZC * nz;
     g.inv_lz = 1.0 / lz;
     g.sigma = sig;
+    g.div_scale = d->dt / rho0 * d->dx;
+    g.inv_3n = 1.0 / (3.0 * (double)N);
+    g.div_tol = p->div_tol;
 
     // ---- transforms
     build_fft(p, nx, d->bc_x, p->fx, &status);
@@ -405,6 +407,7 @@ int fizzy_proj_plan(fizzy_proj_plan_t *out, const fizzy_proj_desc *d, void *stre
     p->n_usq_part = (int)usq_blocks(d);
     p->usq_part = dev_alloc<double>(p, p->n_usq_part, &status);
     p->usq_sum = dev_alloc<double>(p, 1, &status);
+    p->g.usq = p->usq_sum;
     if (status) {
         int st = status;
         fizzy_proj_destroy(p);
@@ -454,8 +457,8 @@ int fizzy_proj_plan(fizzy_proj_plan_t *out, const fizzy_proj_desc *d, void *stre
 
 int fizzy_proj_launches_per_solve(fizzy_proj_plan_t p) {
     if (!p) return 0;
-    int n = p->mixed ? 8 + 5 * p->max_refine : 7;
-    if (p->check) n += p->mixed ? 2 : 3;
+    int n = p->mixed ? 9 + 5 * p->max_refine : 7;
+    if (p->check) n += p->mixed ? 1 : 3;
     return n;
 }
 
@@ -467,7 +470,7 @@ static void read_stats(fizzy_proj_plan_t p, const DevStats &h, double usq, fizzy
     st->relres = h.relres;
     memcpy(&st->f_max, &h.fmax_bits, sizeof(double));
     memcpy(&st->div_max, &h.divmax_bits, sizeof(double));
-    st->u_rms = p->check ? std::sqrt(usq / (3.0 * (double)N)) : 0.0;
+    st->u_rms = (p->check || p->mixed) ? std::sqrt(usq / (3.0 * (double)N)) : 0.0;
     st->div_metric = (p->check && st->u_rms > 0) ? st->div_max * p->desc.dx / st->u_rms : 0.0;
 }
 
@@ -477,7 +480,7 @@ int fizzy_proj_get_stats(fizzy_proj_plan_t p, fizzy_proj_stats *st, void *stream
     DevStats h;
     double usq = 0.0;
     cudaError_t e = cudaMemcpyAsync(&h, p->st, sizeof(h), cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess && p->check)
+    if (e == cudaSuccess && (p->check || p->mixed))
         e = cudaMemcpyAsync(&usq, p->usq_sum, sizeof(double), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_err(p, e, "get_stats");
@@ -571,8 +574,15 @@ int fizzy_proj_solve(fizzy_proj_plan_t p, const double *phi, const double *p_n, 
     if (p->mixed || p->check) e = cudaMemsetAsync(p->st, 0, sizeof(DevStats), s);
     if (e != cudaSuccess) return cuda_err(p, e, "memset");
 
-    TIMED(KS_FLUX, (k_flux<<<cgrd, cblk, 0, s>>>(g, phi, p_n, p_nm1, u, v, w, p->qx, p->qy, p->qz,
-                                                p->check ? p->usq_part : nullptr)));
+    const bool need_usq = p->check || p->mixed;
+    if (p->desc.rho_g <= p->desc.rho_l)
+        TIMED(KS_FLUX, (k_flux<true><<<cgrd, cblk, 0, s>>>(g, phi, p_n, p_nm1, u, v, w, p->qx, p->qy,
+                                                           p->qz, need_usq ? p->usq_part : nullptr)));
+    else
+        TIMED(KS_FLUX, (k_flux<false><<<cgrd, cblk, 0, s>>>(g, phi, p_n, p_nm1, u, v, w, p->qx, p->qy,
+                                                            p->qz, need_usq ? p->usq_part : nullptr)));
+    if (need_usq)
+        TIMED(KS_SUM, (k_sum_partials<<<1, 1024, 0, s>>>(p->usq_part, p->n_usq_part, p->usq_sum)));
     if (!p->mixed) {
         xa.out = p->fhat64;
         TIMED(KS_XFWD, (k_xfwd<double, XF_F64_DIVQ><<<xgrid, 256, p->smem_x64, s>>>(g, p->fx.d64, p->Lx, xa)));
@@ -611,10 +621,7 @@ int fizzy_proj_solve(fizzy_proj_plan_t p, const double *phi, const double *p_n, 
         TIMED(KS_RESMAX, (k_residmax<<<rgrd, rblk, 0, s>>>(g, ra, 0)));
     }
     TIMED(KS_CORRECT, (k_correct<<<cgrd, cblk, 0, s>>>(g, p_np1, p->qx, p->qy, p->qz, u, v, w)));
-    if (p->check) {
-        TIMED(KS_DIVMAX, (k_divmax<<<rgrd, rblk, 0, s>>>(g, u, v, w, p->st)));
-        TIMED(KS_SUM, (k_sum_partials<<<1, 1024, 0, s>>>(p->usq_part, p->n_usq_part, p->usq_sum)));
-    }
+    if (p->check) TIMED(KS_DIVMAX, (k_divmax<<<rgrd, rblk, 0, s>>>(g, u, v, w, p->st)));
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_err(p, e, "solve launch");
     if (st) return fizzy_proj_get_stats(p, st, stream);

@@ -1,6 +1,7 @@
 // Pass kernels of the projection (sm_103a).
 //
 //   k_flux      : q = u*/dt - (beta_f - 1/rho0) G phat on every face        (FP64)
+//                 (beta_f - 1/rho0 formed without cancellation, see face_flux)
 //   k_xfwd      : f = rho0 D(q)  or  r = f - L_h p, then forward x-transform
 //   k_ypass     : forward / inverse y-transform on strided column tiles
 //   k_thomas    : one tridiagonal solve per (kx, ky) z-line (factorised tables)
@@ -31,10 +32,9 @@ struct GridDev {
     int bcx, bcy;
     // flux constants
     double idt;        // 1/dt
-    double two_rho_g;  // 2 rho_g
-    double drho;       // rho_l - rho_g
-    double gx2, gx0;   // 2/dx, 1/(rho0 dx)
-    double gy2, gy0;   // 2/dy, 1/(rho0 dy)
+    double two_rho0;   // 2 rho0
+    double adrho;      // |rho_l - rho_g|
+    double chx, chy;   // |drho| / (rho0 dx), |drho| / (rho0 dy)
     // divergence constants, unscaled (rho0/h) and scaled by sigma = 1/(4 nx ny)
     double dvx, dvy, dvx_s, dvy_s;
     // correction constants
@@ -43,8 +43,7 @@ struct GridDev {
     double idx2, idy2;    // 1/dx^2, 1/dy^2
     double idx1, idy1;    // 1/dx, 1/dy
     // per-k tables (device, FP64, length nz)
-    const double *gz2;    // 2/dzc_(k+1/2)            (0 at k = nz-1)
-    const double *gz0;    // 1/(rho0 dzc_(k+1/2))     (0 at k = nz-1)
+    const double *chz;    // |drho| / (rho0 dzc_(k+1/2))  (0 at k = nz-1)
     const double *dvz;    // rho0/dzf_k
     const double *dvz_s;  // sigma rho0/dzf_k
     const double *cgz;    // dt/(rho0 dzc_(k+1/2))    (0 at k = nz-1)
@@ -55,15 +54,52 @@ struct GridDev {
     const double *dzc;    // dzc_(k+1/2), 0 at k = nz-1
     double inv_lz;        // 1 / sum_k dzf_k
     double sigma;         // 1/(4 nx ny)
+    // mixed-mode stopping rule
+    double div_scale;     // (dt/rho0) dx: max|D u| dx = div_scale max|f - L p|
+    double inv_3n;        // 1/(3 nx ny nz)
+    double div_tol;       // < 0: divergence criterion off
+    const double *usq;    // sum of u*^2 over all faces (device scalar)
 };
+
+// Mixed-mode stopping rule, evaluated by one thread once max|r| is known:
+// relres <= tol and, unless disabled, the divergence the correction will
+// leave, max|D u| dx / U = (dt/rho0) max|r| dx / U, <= div_tol.
+__device__ __forceinline__ bool refine_done(const GridDev &g, double rmax, double fmax, double tol,
+                                            double *rel_out) {
+    const double rel = fmax > 0.0 ? rmax / fmax : rmax;
+    *rel_out = rel;
+    if (!(rel <= tol)) return false;
+    if (g.div_tol < 0.0) return true;
+    const double U = sqrt(*g.usq * g.inv_3n);
+    return U > 0.0 ? rmax * g.div_scale / U <= g.div_tol : rmax == 0.0;
+}
 
 __device__ __forceinline__ size_t cidx(const GridDev &g, int i, int j, int k) {
     return ((size_t)k * g.ny + j) * (size_t)g.nx + i;
 }
 
 // ---------------------------------------------------------------------------
-// Provisional face flux q (3 face families).  9 FP64 instructions per face.
+// Provisional face flux q (3 face families).  10 FP64 instructions per face.
+//
+// The split coefficient gamma_f = beta_f - 1/rho0 is formed without the
+// cancellation of that difference: with rho_f - rho0 = |drho| psi_f, where
+// psi = phi when rho0 = rho_g and psi = 1 - phi when rho0 = rho_l,
+//     gamma_f = -(|drho| / rho0) psi_f beta_f,
+// so gamma_f keeps the relative accuracy of the reciprocal (and is exactly 0
+// in the pure rho0 phase).  With t = psi_a + psi_b and s = rho_a + rho_b =
+// 2 rho0 + |drho| t (so beta_f = 2/s), the flux is
+//     q = u*/dt - gamma_f (phat_b - phat_a)/h = u*/dt + (|drho|/(rho0 h)) t (1/s) dphat.
 // ---------------------------------------------------------------------------
+template <bool RHO0_IS_G>
+__device__ __forceinline__ double face_flux(const GridDev &g, double phi_a, double phi_b,
+                                            double ph_a, double ph_b, double ustar, double ch) {
+    const double sum = phi_a + phi_b;
+    const double t = RHO0_IS_G ? sum : 2.0 - sum;
+    const double r = rcp_pos_nr1(fmaT(g.adrho, t, g.two_rho0));
+    return fmaT(ch, (t * r) * (ph_b - ph_a), ustar * g.idt);
+}
+
+template <bool RHO0_IS_G>
 __global__ void __launch_bounds__(256) k_flux(GridDev g, const double *__restrict__ phi,
                                               const double *__restrict__ pn,
                                               const double *__restrict__ pnm1,
@@ -87,30 +123,21 @@ __global__ void __launch_bounds__(256) k_flux(GridDev g, const double *__restric
         double q = 0.0;
         if (!(g.bcx == BC_NEUMANN && i == g.nx - 1)) {
             const size_t e = (i == g.nx - 1) ? c - i : c + 1;
-            const double he = fmaT(2.0, pn[e], -pnm1[e]);
-            const double r = rcp_pos_nr1(fmaT(g.drho, phc + phi[e], g.two_rho_g));
-            const double gh = fmaT(r, g.gx2, -g.gx0);
-            q = fmaT(uc, g.idt, -gh * (he - hc));
+            q = face_flux<RHO0_IS_G>(g, phc, phi[e], hc, fmaT(2.0, pn[e], -pnm1[e]), uc, g.chx);
         }
         qx[c] = q;
         // y-face j+1/2
         q = 0.0;
         if (!(g.bcy == BC_NEUMANN && j == g.ny - 1)) {
             const size_t nn = (j == g.ny - 1) ? c - (size_t)j * g.nx : c + g.nx;
-            const double hn = fmaT(2.0, pn[nn], -pnm1[nn]);
-            const double r = rcp_pos_nr1(fmaT(g.drho, phc + phi[nn], g.two_rho_g));
-            const double gh = fmaT(r, g.gy2, -g.gy0);
-            q = fmaT(vc, g.idt, -gh * (hn - hc));
+            q = face_flux<RHO0_IS_G>(g, phc, phi[nn], hc, fmaT(2.0, pn[nn], -pnm1[nn]), vc, g.chy);
         }
         qy[c] = q;
         // z-face k+1/2 (top wall at k = nz-1)
         q = 0.0;
         if (k < g.nz - 1) {
             const size_t t = c + (size_t)g.nx * g.ny;
-            const double ht = fmaT(2.0, pn[t], -pnm1[t]);
-            const double r = rcp_pos_nr1(fmaT(g.drho, phc + phi[t], g.two_rho_g));
-            const double gh = fmaT(r, g.gz2[k], -g.gz0[k]);
-            q = fmaT(wc, g.idt, -gh * (ht - hc));
+            q = face_flux<RHO0_IS_G>(g, phc, phi[t], hc, fmaT(2.0, pn[t], -pnm1[t]), wc, g.chz[k]);
         }
         qz[c] = q;
     }
@@ -297,11 +324,12 @@ __global__ void __launch_bounds__(256) k_xfwd(GridDev g, FFTDesc D, int L, XArgs
             const unsigned long long rb = atomicMax(&a.st->rmax_bits[a.slot], 0ull);
             const double rmax = __longlong_as_double((long long)rb);
             const double fmax = __longlong_as_double((long long)a.st->fmax_bits);
-            const double rel = fmax > 0.0 ? rmax / fmax : rmax;
+            double rel;
+            const bool done = refine_done(g, rmax, fmax, a.tol, &rel);
             a.st->relres = rel;
             a.st->n_resid = a.slot + 1;
             a.st->iterations = a.slot;
-            if (rel <= a.tol) a.st->converged = 1;
+            if (done) a.st->converged = 1;
         }
     }
 }
@@ -339,12 +367,15 @@ __global__ void __launch_bounds__(256) k_residmax(GridDev g, XArgs a, int f_from
         const unsigned long long fb = atomicMax(&a.st->fmax_bits, 0ull);
         const double rmax = __longlong_as_double((long long)rb);
         const double fmax = __longlong_as_double((long long)fb);
-        const double rel = fmax > 0.0 ? rmax / fmax : rmax;
-        a.st->relres = rel;
         if (!f_from_q) {
+            double rel;
+            const bool done = refine_done(g, rmax, fmax, a.tol, &rel);
+            a.st->relres = rel;
             a.st->n_resid = a.slot + 1;
             a.st->iterations = a.slot;
-            if (rel <= a.tol) a.st->converged = 1;
+            if (done) a.st->converged = 1;
+        } else {
+            a.st->relres = fmax > 0.0 ? rmax / fmax : rmax;
         }
     }
 }
