@@ -146,6 +146,41 @@ int fizzy_proj_launches_per_solve(fizzy_proj_plan_t p);
 int fizzy_proj_set_timing(fizzy_proj_plan_t p, int enable);
 int fizzy_proj_timing(fizzy_proj_plan_t p, int idx, const char **name, double *ms, int *launches);
 
+/* ------------------------------------------------------------------------
+ * Allocation-free projection (FP64 mode, small grids).
+ *
+ * The paper has no counterpart to this entry point; it exists for callers
+ * that cannot call cudaMalloc: host applications that own every byte of
+ * device memory through their own allocator or memory pool and forbid
+ * allocations by libraries they load, and code that must not trigger an
+ * allocation's implicit device synchronisation in the middle of its own
+ * stream-ordered work.  It needs no plan: every call rebuilds the eigenvalue,
+ * twiddle and z-factorisation tables on the host (a few milliseconds) and
+ * copies them into scratch.
+ *
+ * Scratch: one file-scope static __device__ array of FIZZY_NOALLOC_SCRATCH_BYTES
+ * bytes inside the library holds the tables and the workspace.  Every GPU
+ * that loads the library holds this array until the process exits.  The
+ * caller passes inputs and outputs exactly as for fizzy_proj_solve().
+ *
+ * Limits: nx * ny * nz <= FIZZY_NOALLOC_MAX_CELLS, nx and ny <= 512 (prime
+ * factors 2 and 3), nz <= 4096; larger grids return FIZZY_ERR_UNSUPPORTED
+ * without touching the device.  precision must be FIZZY_PREC_FP64 and flags 0.
+ *
+ * The first call on a device looks up the device address of the scratch
+ * array (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  All calls share the one array and its host-side
+ * staging buffer, which keep the previous call's contents: calls that overlap
+ * (on different streams, or from several host threads at once) race and must
+ * be serialised by the caller.  Returns FIZZY_OK or a FIZZY_ERR_* code; no
+ * stats are produced.
+ * ------------------------------------------------------------------------ */
+#define FIZZY_NOALLOC_MAX_CELLS 262144
+#define FIZZY_NOALLOC_SCRATCH_BYTES 12935488
+int fizzy_proj_solve_noalloc(const fizzy_proj_desc *d, const double *phi, const double *p_n,
+                             const double *p_nm1, double *u, double *v, double *w,
+                             double *p_np1, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

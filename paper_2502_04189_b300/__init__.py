@@ -158,3 +158,20 @@ class Plan:
 
     def __exit__(self, *a):
         self.close()
+
+
+def solve_noalloc(phi, pn, pnm1, u, v, w, p_out, stream=None, **desc):
+    """Allocation-free FP64 projection for small grids (fizzy_proj_solve_noalloc).
+
+    For callers that may not allocate device memory: it needs no plan and
+    works in a static scratch array inside the library (at most
+    NOALLOC_MAX_CELLS = 262144 cells; nx, ny <= 512).  Calls that overlap on
+    the GPU share that scratch and race; serialise them.  desc takes the
+    keyword arguments of make_desc (precision FP64, no flags)."""
+    d, keep = make_desc(**desc)
+    rc = _abi.lib().fizzy_proj_solve_noalloc(ctypes.byref(d), _ptr(phi), _ptr(pn), _ptr(pnm1),
+                                             _ptr(u), _ptr(v), _ptr(w), _ptr(p_out),
+                                             _stream_handle(stream))
+    del keep
+    if rc != 0:
+        raise FizzyError(rc)

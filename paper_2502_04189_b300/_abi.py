@@ -15,7 +15,8 @@ ERRORS = {-1: "invalid argument", -2: "unsupported size", -3: "out of device mem
 EXPORTED = ("fizzy_proj_plan", "fizzy_proj_workspace_bytes", "fizzy_proj_solve",
             "fizzy_proj_get_stats", "fizzy_proj_solve_host", "fizzy_proj_destroy",
             "fizzy_proj_errstr", "fizzy_proj_last_error", "fizzy_proj_launches_per_solve",
-            "fizzy_proj_set_timing", "fizzy_proj_timing")
+            "fizzy_proj_set_timing", "fizzy_proj_timing", "fizzy_proj_solve_noalloc")
+NOALLOC_MAX_CELLS = 262144
 
 
 class Desc(ctypes.Structure):
@@ -74,5 +75,7 @@ def lib():
         L.fizzy_proj_timing.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_char_p),
                                         ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)]
         L.fizzy_proj_timing.restype = ctypes.c_int
+        L.fizzy_proj_solve_noalloc.argtypes = [ctypes.POINTER(Desc)] + [vp] * 7 + [vp]
+        L.fizzy_proj_solve_noalloc.restype = ctypes.c_int
         _lib = L
     return _lib

@@ -667,3 +667,231 @@ int fizzy_proj_solve_host(fizzy_proj_plan_t p, const double *phi, const double *
 }
 
 }  // extern "C"
+// ===========================================================================
+// Allocation-free projection (fizzy_proj_solve_noalloc): the FP64 kernel
+// sequence of fizzy_proj_solve on tables and workspace kept in one static
+// device array, for callers that cannot allocate device memory.
+// ===========================================================================
+namespace {
+
+constexpr int kNaMaxCells = FIZZY_NOALLOC_MAX_CELLS;
+constexpr int kNaMaxN = 512;
+constexpr int kNaMaxNz = 4096;
+constexpr int kNaZTabs = 9;  // per-k tables, in the order of the plan's T_* enum
+// layout in doubles: q (3N) | fhat (N) | m table (N) | 1/beta table (N) |
+// per-k tables (9 x nz) | upper z coefficient (nz) | x twiddles | x cos/sin |
+// y twiddles | y cos/sin
+constexpr size_t kNaTw = 2 * (size_t)kNaMaxN;
+constexpr size_t kNaCs = 2 * (size_t)(kNaMaxN / 2 + 2);
+constexpr size_t kNaDoubles = 6 * (size_t)kNaMaxCells + (kNaZTabs + 1) * (size_t)kNaMaxNz +
+                              2 * (kNaTw + kNaCs) + 32;
+static_assert(kNaDoubles * sizeof(double) == FIZZY_NOALLOC_SCRATCH_BYTES,
+              "header scratch size out of date");
+
+// The scratch: shared by every call on a device, held until process exit.
+static __device__ __align__(256) double g_noalloc_scratch[kNaDoubles];
+// Host-side staging of the tables (also shared by all calls).
+static double g_noalloc_host[2 * (size_t)kNaMaxCells + (kNaZTabs + 1) * (size_t)kNaMaxNz +
+                            2 * (kNaTw + kNaCs)];
+// Device address of the scratch per device ordinal (0 = not looked up yet).
+static double *g_noalloc_dev[256];
+
+// Twiddle and cos/sin tables written straight into a caller buffer (the same
+// values as make_fft_tables, without host heap temporaries).
+void fill_fft_tables(int n, double *tw, double *cs) {
+    const long double pi = 3.141592653589793238462643383279502884L;
+    for (int t = 0; t < n; ++t) {
+        const long double a = 2.0L * pi * (long double)t / (long double)n;
+        tw[2 * t] = (double)cosl(a);
+        tw[2 * t + 1] = (double)(-sinl(a));
+    }
+    for (int m = 0; m < n / 2 + 2; ++m) cs[2 * m] = cs[2 * m + 1] = 0.0;
+    for (int m = 0; m <= n / 2; ++m) {
+        const long double a = pi * (long double)m / (2.0L * (long double)n);
+        cs[2 * m] = (double)cosl(a);
+        cs[2 * m + 1] = (double)sinl(a);
+    }
+}
+
+}  // namespace
+
+extern "C" int fizzy_proj_solve_noalloc(const fizzy_proj_desc *d, const double *phi,
+                                        const double *p_n, const double *p_nm1, double *u,
+                                        double *v, double *w, double *p_np1, void *stream) {
+    const int vrc = validate(d);
+    if (vrc) return vrc;
+    if (!phi || !p_n || !p_nm1 || !u || !v || !w || !p_np1) return FIZZY_ERR_INVALID;
+    if (d->precision != FIZZY_PREC_FP64 || d->flags != 0) return FIZZY_ERR_INVALID;
+    const int nx = d->nx, ny = d->ny, nz = d->nz;
+    if ((long long)nx * ny * nz > kNaMaxCells || nx > kNaMaxN || ny > kNaMaxN || nz > kNaMaxNz)
+        return FIZZY_ERR_UNSUPPORTED;
+    // set-up, once per device, with that device current
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) return FIZZY_ERR_CUDA;
+    if (!g_noalloc_dev[dev]) {
+        void *ptr = nullptr;
+        if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr) {
+            (void)cudaGetLastError();
+            return FIZZY_ERR_CUDA;
+        }
+        g_noalloc_dev[dev] = (double *)ptr;
+    }
+    double *S = g_noalloc_dev[dev];
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t N = (size_t)nx * ny * nz;
+
+    // ---- device regions
+    double *qx = S, *qy = S + kNaMaxCells, *qz = S + 2 * (size_t)kNaMaxCells;
+    double *fhat = S + 3 * (size_t)kNaMaxCells;
+    double *dtab = S + 4 * (size_t)kNaMaxCells;  // m | ib | z tables | cup | fft tables
+    // ---- host tables, laid out exactly like the device region starting at dtab
+    double *H = g_noalloc_host;
+    const int Ux = d->bc_x == FIZZY_BC_PERIODIC ? nx / 2 + 1 : nx;
+    const int Uy = d->bc_y == FIZZY_BC_PERIODIC ? ny / 2 + 1 : ny;
+    const size_t ts = (size_t)Ux * Uy;
+    double *hm = H, *hib = H + kNaMaxCells;
+    double *hz = H + 2 * (size_t)kNaMaxCells;       // kNaZTabs x kNaMaxNz
+    double *hcup = hz + kNaZTabs * (size_t)kNaMaxNz;
+    double *hfft = hcup + kNaMaxNz;                 // tw_x | cs_x | tw_y | cs_y
+    const double rho0 = std::min(d->rho_l, d->rho_g);
+    const double adrho = std::fabs(d->rho_l - d->rho_g);
+    static double zf[kNaMaxNz + 1], zc[kNaMaxNz];
+    for (int k = 0; k <= nz; ++k) zf[k] = d->zf ? d->zf[k] : d->dz * k;
+    for (int k = 0; k < nz; ++k) zc[k] = 0.5 * (zf[k] + zf[k + 1]);
+    double lz = 0.0;
+    const double sig = 1.0 / (4.0 * (double)nx * (double)ny);
+    // per-k tables (same definitions and arithmetic as the plan's)
+    enum { Z_CHZ, Z_DVZ, Z_DVZS, Z_CGZ, Z_LZA, Z_LZC, Z_IZF, Z_DZF, Z_DZC };
+    for (int k = 0; k < nz; ++k) lz += zf[k + 1] - zf[k];
+    for (int k = 0; k < nz; ++k) {
+        const double dzf_k = zf[k + 1] - zf[k];
+        const bool top = (k == nz - 1);
+        const double dzc_k = top ? 0.0 : zc[k + 1] - zc[k];
+        const double dzc_km = (k > 0) ? zc[k] - zc[k - 1] : 0.0;
+        const double idzc = top ? 0.0 : 1.0 / dzc_k;
+        hz[Z_CHZ * kNaMaxNz + k] = adrho / rho0 * idzc;
+        hz[Z_DVZ * kNaMaxNz + k] = rho0 / dzf_k;
+        hz[Z_DVZS * kNaMaxNz + k] = sig * rho0 / dzf_k;
+        hz[Z_CGZ * kNaMaxNz + k] = d->dt / rho0 * idzc;
+        hz[Z_LZA * kNaMaxNz + k] = (k > 0) ? 1.0 / (dzf_k * dzc_km) : 0.0;
+        hz[Z_LZC * kNaMaxNz + k] = top ? 0.0 : 1.0 / (dzf_k * dzc_k);
+        hz[Z_IZF * kNaMaxNz + k] = 1.0 / dzf_k;
+        hz[Z_DZF * kNaMaxNz + k] = dzf_k;
+        hz[Z_DZC * kNaMaxNz + k] = dzc_k;
+        hcup[k] = hz[Z_LZC * kNaMaxNz + k];
+    }
+    // transform tables
+    fill_fft_tables(nx, hfft, hfft + kNaTw);
+    fill_fft_tables(ny, hfft + kNaTw + kNaCs, hfft + 2 * kNaTw + kNaCs);
+    // z factorisation per distinct eigenvalue pair
+    const double *A = &hz[Z_LZA * kNaMaxNz];
+    const double *C = &hz[Z_LZC * kNaMaxNz];
+    for (size_t uu = 0; uu < ts; ++uu) {
+        const int ux = (int)(uu % Ux), uy = (int)(uu / Ux);
+        if (ux == 0 && uy == 0) {
+            for (int k = 0; k < nz; ++k) hm[(size_t)k * ts] = hib[(size_t)k * ts] = 0.0;
+            continue;
+        }
+        const double lam = eig(ux, nx, d->dx, d->bc_x) + eig(uy, ny, d->dy, d->bc_y);
+        double beta = -(A[0] + C[0]) + lam;
+        hm[uu] = 0.0;
+        hib[uu] = 1.0 / beta;
+        for (int k = 1; k < nz; ++k) {
+            const double m = A[k] / beta;
+            beta = (-(A[k] + C[k]) + lam) - m * C[k - 1];
+            hm[(size_t)k * ts + uu] = m;
+            hib[(size_t)k * ts + uu] = 1.0 / beta;
+        }
+    }
+    // copy the used parts: m and 1/beta tables, then per-k + transform tables
+    cudaError_t e = cudaMemcpyAsync(dtab, hm, ts * nz * sizeof(double), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(dtab + kNaMaxCells, hib, ts * nz * sizeof(double), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(dtab + 2 * (size_t)kNaMaxCells, hz,
+                            ((kNaZTabs + 1) * (size_t)kNaMaxNz + 2 * (kNaTw + kNaCs)) * sizeof(double),
+                            cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        return FIZZY_ERR_CUDA;
+    }
+
+    // ---- kernel arguments pointing into the scratch
+    double *dz_ = dtab + 2 * (size_t)kNaMaxCells;
+    double *dcup = dz_ + kNaZTabs * (size_t)kNaMaxNz;
+    double *dfft = dcup + kNaMaxNz;
+    GridDev g;
+    memset(&g, 0, sizeof(g));
+    g.nx = nx;
+    g.ny = ny;
+    g.nz = nz;
+    g.bcx = d->bc_x;
+    g.bcy = d->bc_y;
+    g.idt = 1.0 / d->dt;
+    g.two_rho0 = 2.0 * rho0;
+    g.adrho = adrho;
+    g.chx = adrho / (rho0 * d->dx);
+    g.chy = adrho / (rho0 * d->dy);
+    g.dvx = rho0 / d->dx;
+    g.dvy = rho0 / d->dy;
+    g.dvx_s = sig * rho0 / d->dx;
+    g.dvy_s = sig * rho0 / d->dy;
+    g.dt = d->dt;
+    g.cgx = d->dt / (rho0 * d->dx);
+    g.cgy = d->dt / (rho0 * d->dy);
+    g.idx2 = 1.0 / (d->dx * d->dx);
+    g.idy2 = 1.0 / (d->dy * d->dy);
+    g.idx1 = 1.0 / d->dx;
+    g.idy1 = 1.0 / d->dy;
+    g.chz = dz_ + Z_CHZ * kNaMaxNz;
+    g.dvz = dz_ + Z_DVZ * kNaMaxNz;
+    g.dvz_s = dz_ + Z_DVZS * kNaMaxNz;
+    g.cgz = dz_ + Z_CGZ * kNaMaxNz;
+    g.lza = dz_ + Z_LZA * kNaMaxNz;
+    g.lzc = dz_ + Z_LZC * kNaMaxNz;
+    g.izf = dz_ + Z_IZF * kNaMaxNz;
+    g.dzf = dz_ + Z_DZF * kNaMaxNz;
+    g.dzc = dz_ + Z_DZC * kNaMaxNz;
+    g.inv_lz = 1.0 / lz;
+    g.sigma = sig;
+    g.div_tol = -1.0;
+    FFTDesc Dx, Dy;
+    memset(&Dx, 0, sizeof(Dx));
+    memset(&Dy, 0, sizeof(Dy));
+    Dx.n = nx;
+    Dx.nst = make_radices(nx, Dx.rad);
+    Dx.kind = d->bc_x == FIZZY_BC_NEUMANN ? KIND_DCT : KIND_PERIODIC;
+    Dx.tw = dfft;
+    Dx.cs = dfft + kNaTw;
+    Dy.n = ny;
+    Dy.nst = make_radices(ny, Dy.rad);
+    Dy.kind = d->bc_y == FIZZY_BC_NEUMANN ? KIND_DCT : KIND_PERIODIC;
+    Dy.tw = dfft + kNaTw + kNaCs;
+    Dy.cs = dfft + 2 * kNaTw + kNaCs;
+    const int Lx = x_lines_per_cta(nx), TXy = y_tile_cols(ny);
+    const size_t smx = pass_smem<double>(nx, Lx), smy = pass_smem<double>(ny, TXy / 2);
+    const dim3 cblk(32, 8), cgrd((nx + 31) / 32, (ny + 7) / 8, nz);
+    const int xgrid = (ny * nz + 2 * Lx - 1) / (2 * Lx);
+    const dim3 ygrid((nx + TXy - 1) / TXy, nz);
+    const dim3 tgrid((nx + 127) / 128, ny);
+    XArgs xa;
+    memset(&xa, 0, sizeof(xa));
+    xa.qx = qx;
+    xa.qy = qy;
+    xa.qz = qz;
+    xa.out = fhat;
+    (void)N;
+
+    if (d->rho_g <= d->rho_l)
+        k_flux<true><<<cgrd, cblk, 0, s>>>(g, phi, p_n, p_nm1, u, v, w, qx, qy, qz, nullptr);
+    else
+        k_flux<false><<<cgrd, cblk, 0, s>>>(g, phi, p_n, p_nm1, u, v, w, qx, qy, qz, nullptr);
+    k_xfwd<double, XF_F64_DIVQ><<<xgrid, 256, smx, s>>>(g, Dx, Lx, xa);
+    k_ypass<double, false><<<ygrid, 256, smy, s>>>(nx, ny, Dy, TXy, fhat, nullptr);
+    k_thomas<double><<<tgrid, 128, 0, s>>>(g, Ux, Uy, dtab, dtab + kNaMaxCells, dcup, fhat, nullptr);
+    k_ypass<double, true><<<ygrid, 256, smy, s>>>(nx, ny, Dy, TXy, fhat, nullptr);
+    k_xinv<double, XI_STORE><<<xgrid, 256, smx, s>>>(g, Dx, Lx, fhat, p_np1, nullptr);
+    k_correct<<<cgrd, cblk, 0, s>>>(g, p_np1, qx, qy, qz, u, v, w);
+    e = cudaGetLastError();
+    return e == cudaSuccess ? FIZZY_OK : FIZZY_ERR_CUDA;
+}
