@@ -117,6 +117,21 @@ int make_radices(int n, int *rad) {
     return s;
 }
 
+// Stage constants of an FFTDesc for length n (see FFTDesc).
+void fill_stages(FFTDesc &d, int n) {
+    d.n = n;
+    d.nst = make_radices(n, d.rad);
+    int ns = 1;
+    for (int s = 0; s < d.nst; ++s) {
+        d.m[s] = n / d.rad[s];
+        d.ns[s] = ns;
+        d.twq[s] = n / (ns * d.rad[s]);
+        d.rm[s] = d.m[s] > 1 ? (unsigned)((1ull << 32) / (unsigned)d.m[s] + 1) : 0u;
+        d.rns[s] = ns > 1 ? (unsigned)((1ull << 32) / (unsigned)ns + 1) : 0u;
+        ns *= d.rad[s];
+    }
+}
+
 // exp(-2 pi i t / n) and (cos, sin)(pi m / (2n)) in long double, rounded once.
 void make_fft_tables(int n, std::vector<double> &tw, std::vector<double> &cs) {
     const long double pi = 3.141592653589793238462643383279502884L;
@@ -153,8 +168,7 @@ int build_fft(fizzy_proj_plan_t p, int n, int bc, FFTHost &F, int *status) {
     }
     FFTDesc d;
     memset(&d, 0, sizeof(d));
-    d.n = n;
-    d.nst = make_radices(n, d.rad);
+    fill_stages(d, n);
     d.kind = (bc == FIZZY_BC_NEUMANN) ? KIND_DCT : KIND_PERIODIC;
     F.d64 = d;
     F.d64.tw = F.tw64;
@@ -212,8 +226,13 @@ template <typename T> size_t pass_smem(int n, int L) {
     return sizeof(typename C2<T>::t) * ((size_t)n + (n / 2 + 2) + 2 * (size_t)L * (n + 1));
 }
 
+constexpr int kFluxKc = 16;  // planes marched by one flux CTA
+dim3 flux_grid(int nx, int ny, int nz) {
+    return dim3((nx + FLUX_BX - 1) / FLUX_BX, (ny + FLUX_BY - 1) / FLUX_BY, (nz + kFluxKc - 1) / kFluxKc);
+}
 size_t usq_blocks(const fizzy_proj_desc *d) {
-    return (size_t)((d->nx + 31) / 32) * ((d->ny + 7) / 8) * d->nz;
+    const dim3 gr = flux_grid(d->nx, d->ny, d->nz);
+    return (size_t)gr.x * gr.y * gr.z;
 }
 
 size_t plan_bytes(const fizzy_proj_desc *d) {
@@ -299,8 +318,8 @@ int fizzy_proj_plan(fizzy_proj_plan_t *out, const fizzy_proj_desc *d, void *stre
         const bool top = (k == nz - 1);
         const double idzc = top ? 0.0 : 1.0 / dzc[k];
         zt[T_CHZ * nz + k] = adrho / rho0 * idzc;
-        zt[T_DVZ * nz + k] = rho0 / dzf[k];
-        zt[T_DVZS * nz + k] = sig * rho0 / dzf[k];
+        zt[T_DVZ * nz + k] = rho0 / (d->dt * dzf[k]);
+        zt[T_DVZS * nz + k] = sig * rho0 / (d->dt * dzf[k]);
         zt[T_CGZ * nz + k] = d->dt / rho0 * idzc;
         zt[T_LZA * nz + k] = (k > 0) ? 1.0 / (dzf[k] * dzc[k - 1]) : 0.0;
         zt[T_LZC * nz + k] = top ? 0.0 : 1.0 / (dzf[k] * dzc[k]);
@@ -329,10 +348,10 @@ int fizzy_proj_plan(fizzy_proj_plan_t *out, const fizzy_proj_desc *d, void *stre
     g.adrho = adrho;
     g.chx = adrho / (rho0 * d->dx);
     g.chy = adrho / (rho0 * d->dy);
-    g.dvx = rho0 / d->dx;
-    g.dvy = rho0 / d->dy;
-    g.dvx_s = sig * rho0 / d->dx;
-    g.dvy_s = sig * rho0 / d->dy;
+    g.dvx = rho0 / (d->dt * d->dx);
+    g.dvy = rho0 / (d->dt * d->dy);
+    g.dvx_s = sig * rho0 / (d->dt * d->dx);
+    g.dvy_s = sig * rho0 / (d->dt * d->dy);
     g.dt = d->dt;
     g.cgx = d->dt / (rho0 * d->dx);
     g.cgy = d->dt / (rho0 * d->dy);
@@ -562,7 +581,8 @@ int fizzy_proj_solve(fizzy_proj_plan_t p, const double *phi, const double *p_n, 
     const int nlines = ny * nz;
     const int xgrid = (nlines + 2 * p->Lx - 1) / (2 * p->Lx);
     const dim3 ygrid((nx + p->TXy - 1) / p->TXy, nz);
-    const dim3 tgrid((nx + 127) / 128, ny);
+    const int tthreads = g.bcx == FIZZY_BC_PERIODIC ? nx / 2 + 1 : nx;
+    const dim3 tgrid((tthreads + THOMAS_BLOCK - 1) / THOMAS_BLOCK, ny);
     XArgs xa;
     memset(&xa, 0, sizeof(xa));
     xa.qx = p->qx;
@@ -575,19 +595,20 @@ int fizzy_proj_solve(fizzy_proj_plan_t p, const double *phi, const double *p_n, 
     if (e != cudaSuccess) return cuda_err(p, e, "memset");
 
     const bool need_usq = p->check || p->mixed;
+    const dim3 fgrd = flux_grid(nx, ny, nz), fblk(FLUX_BX, FLUX_BY);
     if (p->desc.rho_g <= p->desc.rho_l)
-        TIMED(KS_FLUX, (k_flux<true><<<cgrd, cblk, 0, s>>>(g, phi, p_n, p_nm1, u, v, w, p->qx, p->qy,
-                                                           p->qz, need_usq ? p->usq_part : nullptr)));
+        TIMED(KS_FLUX, (k_flux<true><<<fgrd, fblk, 0, s>>>(g, kFluxKc, phi, p_n, p_nm1, u, v, w, p->qx,
+                                                           p->qy, p->qz, need_usq ? p->usq_part : nullptr)));
     else
-        TIMED(KS_FLUX, (k_flux<false><<<cgrd, cblk, 0, s>>>(g, phi, p_n, p_nm1, u, v, w, p->qx, p->qy,
-                                                            p->qz, need_usq ? p->usq_part : nullptr)));
+        TIMED(KS_FLUX, (k_flux<false><<<fgrd, fblk, 0, s>>>(g, kFluxKc, phi, p_n, p_nm1, u, v, w, p->qx,
+                                                            p->qy, p->qz, need_usq ? p->usq_part : nullptr)));
     if (need_usq)
         TIMED(KS_SUM, (k_sum_partials<<<1, 1024, 0, s>>>(p->usq_part, p->n_usq_part, p->usq_sum)));
     if (!p->mixed) {
         xa.out = p->fhat64;
         TIMED(KS_XFWD, (k_xfwd<double, XF_F64_DIVQ><<<xgrid, 256, p->smem_x64, s>>>(g, p->fx.d64, p->Lx, xa)));
         TIMED(KS_YFWD, (k_ypass<double, false><<<ygrid, 256, p->smem_y64, s>>>(nx, ny, p->fy.d64, p->TXy, p->fhat64, nullptr)));
-        TIMED(KS_THOMAS, (k_thomas<double><<<tgrid, 128, 0, s>>>(g, p->Ux, p->Uy, p->mtab64, p->ibtab64, p->cup64, p->fhat64, nullptr)));
+        TIMED(KS_THOMAS, (k_thomas<double><<<tgrid, THOMAS_BLOCK, thomas_smem<double>(), s>>>(g, p->Ux, p->Uy, p->mtab64, p->ibtab64, p->cup64, p->fhat64, nullptr)));
         TIMED(KS_YINV, (k_ypass<double, true><<<ygrid, 256, p->smem_y64, s>>>(nx, ny, p->fy.d64, p->TXy, p->fhat64, nullptr)));
         TIMED(KS_XINV, (k_xinv<double, XI_STORE><<<xgrid, 256, p->smem_x64, s>>>(g, p->fx.d64, p->Lx, p->fhat64, p_np1, p->st)));
         if (p->check) {
@@ -602,7 +623,7 @@ int fizzy_proj_solve(fizzy_proj_plan_t p, const double *phi, const double *p_n, 
         const int *conv = &p->st->converged;
         TIMED(KS_XFWD, (k_xfwd<float, XF_MIX_DIVQ><<<xgrid, 256, p->smem_x32, s>>>(g, p->fx.d32, p->Lx, xa)));
         TIMED(KS_YFWD, (k_ypass<float, false><<<ygrid, 256, p->smem_y32, s>>>(nx, ny, p->fy.d32, p->TXy, p->fhat32, nullptr)));
-        TIMED(KS_THOMAS, (k_thomas<float><<<tgrid, 128, 0, s>>>(g, p->Ux, p->Uy, p->mtab32, p->ibtab32, p->cup32, p->fhat32, nullptr)));
+        TIMED(KS_THOMAS, (k_thomas<float><<<tgrid, THOMAS_BLOCK, thomas_smem<float>(), s>>>(g, p->Ux, p->Uy, p->mtab32, p->ibtab32, p->cup32, p->fhat32, nullptr)));
         TIMED(KS_YINV, (k_ypass<float, true><<<ygrid, 256, p->smem_y32, s>>>(nx, ny, p->fy.d32, p->TXy, p->fhat32, nullptr)));
         TIMED(KS_XINV, (k_xinv<float, XI_STORE><<<xgrid, 256, p->smem_x32, s>>>(g, p->fx.d32, p->Lx, p->fhat32, p_np1, p->st)));
         XArgs ra = xa;
@@ -613,7 +634,7 @@ int fizzy_proj_solve(fizzy_proj_plan_t p, const double *phi, const double *p_n, 
             ra.slot = sw;
             TIMED(KS_XRES, (k_xfwd<float, XF_MIX_RESID><<<xgrid, 256, p->smem_x32, s>>>(g, p->fx.d32, p->Lx, ra)));
             TIMED(KS_YFWD_R, (k_ypass<float, false><<<ygrid, 256, p->smem_y32, s>>>(nx, ny, p->fy.d32, p->TXy, p->fhat32, conv)));
-            TIMED(KS_THOMAS_R, (k_thomas<float><<<tgrid, 128, 0, s>>>(g, p->Ux, p->Uy, p->mtab32, p->ibtab32, p->cup32, p->fhat32, conv)));
+            TIMED(KS_THOMAS_R, (k_thomas<float><<<tgrid, THOMAS_BLOCK, thomas_smem<float>(), s>>>(g, p->Ux, p->Uy, p->mtab32, p->ibtab32, p->cup32, p->fhat32, conv)));
             TIMED(KS_YINV_R, (k_ypass<float, true><<<ygrid, 256, p->smem_y32, s>>>(nx, ny, p->fy.d32, p->TXy, p->fhat32, conv)));
             TIMED(KS_XACC, (k_xinv<float, XI_ACCUM><<<xgrid, 256, p->smem_x32, s>>>(g, p->fx.d32, p->Lx, p->fhat32, p_np1, p->st)));
         }
@@ -667,6 +688,7 @@ int fizzy_proj_solve_host(fizzy_proj_plan_t p, const double *phi, const double *
 }
 
 }  // extern "C"
+
 // ===========================================================================
 // Allocation-free projection (fizzy_proj_solve_noalloc): the FP64 kernel
 // sequence of fizzy_proj_solve on tables and workspace kept in one static
@@ -770,8 +792,8 @@ extern "C" int fizzy_proj_solve_noalloc(const fizzy_proj_desc *d, const double *
         const double dzc_km = (k > 0) ? zc[k] - zc[k - 1] : 0.0;
         const double idzc = top ? 0.0 : 1.0 / dzc_k;
         hz[Z_CHZ * kNaMaxNz + k] = adrho / rho0 * idzc;
-        hz[Z_DVZ * kNaMaxNz + k] = rho0 / dzf_k;
-        hz[Z_DVZS * kNaMaxNz + k] = sig * rho0 / dzf_k;
+        hz[Z_DVZ * kNaMaxNz + k] = rho0 / (d->dt * dzf_k);
+        hz[Z_DVZS * kNaMaxNz + k] = sig * rho0 / (d->dt * dzf_k);
         hz[Z_CGZ * kNaMaxNz + k] = d->dt / rho0 * idzc;
         hz[Z_LZA * kNaMaxNz + k] = (k > 0) ? 1.0 / (dzf_k * dzc_km) : 0.0;
         hz[Z_LZC * kNaMaxNz + k] = top ? 0.0 : 1.0 / (dzf_k * dzc_k);
@@ -832,10 +854,10 @@ extern "C" int fizzy_proj_solve_noalloc(const fizzy_proj_desc *d, const double *
     g.adrho = adrho;
     g.chx = adrho / (rho0 * d->dx);
     g.chy = adrho / (rho0 * d->dy);
-    g.dvx = rho0 / d->dx;
-    g.dvy = rho0 / d->dy;
-    g.dvx_s = sig * rho0 / d->dx;
-    g.dvy_s = sig * rho0 / d->dy;
+    g.dvx = rho0 / (d->dt * d->dx);
+    g.dvy = rho0 / (d->dt * d->dy);
+    g.dvx_s = sig * rho0 / (d->dt * d->dx);
+    g.dvy_s = sig * rho0 / (d->dt * d->dy);
     g.dt = d->dt;
     g.cgx = d->dt / (rho0 * d->dx);
     g.cgy = d->dt / (rho0 * d->dy);
@@ -858,13 +880,11 @@ extern "C" int fizzy_proj_solve_noalloc(const fizzy_proj_desc *d, const double *
     FFTDesc Dx, Dy;
     memset(&Dx, 0, sizeof(Dx));
     memset(&Dy, 0, sizeof(Dy));
-    Dx.n = nx;
-    Dx.nst = make_radices(nx, Dx.rad);
+    fill_stages(Dx, nx);
     Dx.kind = d->bc_x == FIZZY_BC_NEUMANN ? KIND_DCT : KIND_PERIODIC;
     Dx.tw = dfft;
     Dx.cs = dfft + kNaTw;
-    Dy.n = ny;
-    Dy.nst = make_radices(ny, Dy.rad);
+    fill_stages(Dy, ny);
     Dy.kind = d->bc_y == FIZZY_BC_NEUMANN ? KIND_DCT : KIND_PERIODIC;
     Dy.tw = dfft + kNaTw + kNaCs;
     Dy.cs = dfft + 2 * kNaTw + kNaCs;
@@ -873,7 +893,8 @@ extern "C" int fizzy_proj_solve_noalloc(const fizzy_proj_desc *d, const double *
     const dim3 cblk(32, 8), cgrd((nx + 31) / 32, (ny + 7) / 8, nz);
     const int xgrid = (ny * nz + 2 * Lx - 1) / (2 * Lx);
     const dim3 ygrid((nx + TXy - 1) / TXy, nz);
-    const dim3 tgrid((nx + 127) / 128, ny);
+    const int tthreads = d->bc_x == FIZZY_BC_PERIODIC ? nx / 2 + 1 : nx;
+    const dim3 tgrid((tthreads + THOMAS_BLOCK - 1) / THOMAS_BLOCK, ny);
     XArgs xa;
     memset(&xa, 0, sizeof(xa));
     xa.qx = qx;
@@ -882,13 +903,14 @@ extern "C" int fizzy_proj_solve_noalloc(const fizzy_proj_desc *d, const double *
     xa.out = fhat;
     (void)N;
 
+    const dim3 fgrd = flux_grid(nx, ny, nz), fblk(FLUX_BX, FLUX_BY);
     if (d->rho_g <= d->rho_l)
-        k_flux<true><<<cgrd, cblk, 0, s>>>(g, phi, p_n, p_nm1, u, v, w, qx, qy, qz, nullptr);
+        k_flux<true><<<fgrd, fblk, 0, s>>>(g, kFluxKc, phi, p_n, p_nm1, u, v, w, qx, qy, qz, nullptr);
     else
-        k_flux<false><<<cgrd, cblk, 0, s>>>(g, phi, p_n, p_nm1, u, v, w, qx, qy, qz, nullptr);
+        k_flux<false><<<fgrd, fblk, 0, s>>>(g, kFluxKc, phi, p_n, p_nm1, u, v, w, qx, qy, qz, nullptr);
     k_xfwd<double, XF_F64_DIVQ><<<xgrid, 256, smx, s>>>(g, Dx, Lx, xa);
     k_ypass<double, false><<<ygrid, 256, smy, s>>>(nx, ny, Dy, TXy, fhat, nullptr);
-    k_thomas<double><<<tgrid, 128, 0, s>>>(g, Ux, Uy, dtab, dtab + kNaMaxCells, dcup, fhat, nullptr);
+    k_thomas<double><<<tgrid, THOMAS_BLOCK, thomas_smem<double>(), s>>>(g, Ux, Uy, dtab, dtab + kNaMaxCells, dcup, fhat, nullptr);
     k_ypass<double, true><<<ygrid, 256, smy, s>>>(nx, ny, Dy, TXy, fhat, nullptr);
     k_xinv<double, XI_STORE><<<xgrid, 256, smx, s>>>(g, Dx, Lx, fhat, p_np1, nullptr);
     k_correct<<<cgrd, cblk, 0, s>>>(g, p_np1, qx, qy, qz, u, v, w);

@@ -107,6 +107,47 @@ __device__ __forceinline__ double block_sum(double v) {
     return s;
 }
 
+// 2^e as a double (e within the normal range)
+__device__ __forceinline__ double pow2d(int e) {
+    return __hiloint2double((e + 1023) << 20, 0);
+}
+// binary exponent of a positive double given by its bit pattern (0 -> 0)
+__device__ __forceinline__ int exp_of_bits(unsigned long long b) {
+    return b ? (int)((b >> 52) & 0x7ff) - 1023 : 0;
+}
+
+// double -> float with the binary exponent shifted by -es (x * 2^-es),
+// truncating; |result| below 2^-126 flushes to zero.  Integer-only.
+__device__ __forceinline__ float f64_to_f32_shift(double x, int es) {
+    const unsigned hi = (unsigned)__double2hiint(x);
+    const unsigned lo = (unsigned)__double2loint(x);
+    const int e = (int)((hi >> 20) & 0x7ff) - es;  // biased double exponent after the shift
+    if (e <= 896) return __uint_as_float(hi & 0x80000000u);
+    const unsigned b = ((unsigned)(e - 896) << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29);
+    return __uint_as_float(b | (hi & 0x80000000u));
+}
+// float -> double times 2^es (flush float denormals to zero).  Integer-only.
+__device__ __forceinline__ double f32_to_f64_shift(float f, int es) {
+    const unsigned b = __float_as_uint(f);
+    const unsigned a = b & 0x7fffffffu;
+    if (a < 0x00800000u) return __hiloint2double((int)(b & 0x80000000u), 0);
+    const unsigned hi = (((a >> 23) + 896u + (unsigned)es) << 20) | ((a >> 3) & 0xfffffu);
+    return __hiloint2double((int)(hi | (b & 0x80000000u)), (int)(a << 29));
+}
+
+// Asynchronous global -> shared copies (cp.async, LDGSTS): the copy runs in
+// the background and the issuing thread waits for its own groups.
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void *smem, const void *gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(s), "l"(gmem), "n"(BYTES)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
 // Device-side state of one solve (reset at the start of every solve).
 struct DevStats {
     unsigned long long fmax_bits;      // max|f|

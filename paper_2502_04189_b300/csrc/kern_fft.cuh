@@ -23,15 +23,26 @@ namespace fz {
 
 enum { KIND_PERIODIC = 0, KIND_DCT = 1 };
 
-// One transform direction (kernel argument, by value).
+constexpr int FFT_MAX_STAGES = 12;
+
+// One transform direction (kernel argument, by value).  Per stage s: radix
+// rad[s], butterfly stride m[s] = n/rad[s], span ns[s] (product of the
+// earlier radices), twiddle step twq[s] = n/(ns[s] rad[s]) and the
+// multiply-high reciprocals of m[s] and ns[s]: for 0 <= x < 2^31/d,
+// floor(x/d) = umulhi(x, floor(2^32/d) + 1)  (d > 1).
 struct FFTDesc {
     int n;           // transform length
     int nst;         // number of Stockham stages
-    int rad[16];     // radix of each stage (4, 2 or 3)
     int kind;        // KIND_PERIODIC or KIND_DCT
+    int rad[FFT_MAX_STAGES], m[FFT_MAX_STAGES], ns[FFT_MAX_STAGES], twq[FFT_MAX_STAGES];
+    unsigned rm[FFT_MAX_STAGES], rns[FFT_MAX_STAGES];
     const void *tw;  // n complex: exp(-2 pi i t / n)          (T2 of the kernel's type)
     const void *cs;  // n/2+1 complex: (cos, sin)(pi m / (2 n)) (T2)
 };
+
+__device__ __forceinline__ int fdiv(int x, int d, unsigned r) {
+    return d == 1 ? x : (int)__umulhi((unsigned)x, r);
+}
 
 // position of input sample i inside the (possibly reordered) complex line
 __device__ __forceinline__ int line_pos(int i, int n, int kind) {
@@ -55,17 +66,15 @@ __device__ __forceinline__ void twiddle(typename C2<T>::t &x, typename C2<T>::t 
 // One Stockham stage over L lines (line stride ls) from src to dst.
 template <typename T, bool INV>
 __device__ __forceinline__ void stockham_stage(const typename C2<T>::t *__restrict__ src,
-                                               typename C2<T>::t *__restrict__ dst, int n, int L,
-                                               int ls, int R, int Ns,
-                                               const typename C2<T>::t *__restrict__ tw) {
+                                               typename C2<T>::t *__restrict__ dst, int L, int ls,
+                                               int R, int m, unsigned rm, int Ns, unsigned rns,
+                                               int twq, const typename C2<T>::t *__restrict__ tw) {
     typedef typename C2<T>::t T2;
-    const int m = n / R;
     const int total = L * m;
-    const int twq = n / (Ns * R);
     for (int t = threadIdx.x; t < total; t += blockDim.x) {
-        const int l = t / m;
+        const int l = fdiv(t, m, rm);
         const int b = t - l * m;
-        const int j = b % Ns;
+        const int j = b - fdiv(b, Ns, rns) * Ns;
         const T2 *in = src + l * ls + b;
         T2 *out = dst + l * ls + (b - j) * R + j;
         const int ts = j * twq;
@@ -121,15 +130,14 @@ __device__ __forceinline__ void stockham_stage(const typename C2<T>::t *__restri
 template <typename T, bool INV>
 __device__ typename C2<T>::t *fft_lines(typename C2<T>::t *a, typename C2<T>::t *b, int L, int ls,
                                         const FFTDesc &D, const typename C2<T>::t *tw) {
-    int Ns = 1;
-    for (int s = 0; s < D.nst; ++s) {
-        const int R = D.rad[s];
-        stockham_stage<T, INV>(a, b, D.n, L, ls, R, Ns, tw);
+#pragma unroll
+    for (int s = 0; s < FFT_MAX_STAGES; ++s) {
+        if (s >= D.nst) break;
+        stockham_stage<T, INV>(a, b, L, ls, D.rad[s], D.m[s], D.rm[s], D.ns[s], D.rns[s], D.twq[s], tw);
         __syncthreads();
         typename C2<T>::t *t = a;
         a = b;
         b = t;
-        Ns *= R;
     }
     return a;
 }

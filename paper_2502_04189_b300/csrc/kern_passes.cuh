@@ -1,23 +1,24 @@
 // Pass kernels of the projection (sm_103a).
 //
-//   k_flux      : q = u*/dt - (beta_f - 1/rho0) G phat on every face        (FP64)
+//   k_flux      : q' = dt q = u* - dt (beta_f - 1/rho0) G phat on every face (FP64)
 //                 (beta_f - 1/rho0 formed without cancellation, see face_flux)
 //   k_xfwd      : f = rho0 D(q)  or  r = f - L_h p, then forward x-transform
 //   k_ypass     : forward / inverse y-transform on strided column tiles
 //   k_thomas    : one tridiagonal solve per (kx, ky) z-line (factorised tables)
 //   k_xinv      : inverse x-transform, p = value or p += value
-//   k_correct   : u = dt q - (dt/rho0) G p^(n+1)                             (FP64)
+//   k_correct   : u = q' - (dt/rho0) G p^(n+1)                               (FP64)
 //   k_divmax    : max |D u| (diagnostics)
 //   k_residmax  : max |f - L_h p| without a transform (mixed final check)
 //
-// The provisional face flux q carries the split: the right-hand side of the
-// constant-coefficient equation is rho0 D(q) (= (rho0/dt) D(u*) +
-// D[(1 - rho0 beta_f) G phat] since rho0 (beta_f - 1/rho0) = -(1 - rho0 beta_f)),
-// and the correction u = u* - dt[G p/rho0 + (beta_f - 1/rho0) G phat] is
-// dt q - (dt/rho0) G p.  Storing q once makes the correction three FP64
-// instructions per face and guarantees that the right-hand side and the
-// correction use the very same face coefficients, so D(u) equals
-// (dt/rho0)(f - L_h p) to round-off.
+// The provisional face flux q = u*/dt - (beta_f - 1/rho0) G phat carries the
+// split: the right-hand side of the constant-coefficient equation is rho0 D(q)
+// (= (rho0/dt) D(u*) + D[(1 - rho0 beta_f) G phat] since
+// rho0 (beta_f - 1/rho0) = -(1 - rho0 beta_f)), and the correction
+// u = u* - dt[G p/rho0 + (beta_f - 1/rho0) G phat] is dt q - (dt/rho0) G p.
+// It is stored as q' = dt q, so f = (rho0/dt) D(q') and u = q' - (dt/rho0) G p
+// (two FP64 instructions per face); the right-hand side and the correction
+// use the very same face coefficients, so D(u) equals (dt/rho0)(f - L_h p) to
+// round-off.
 #pragma once
 #include "kern_common.cuh"
 #include "kern_fft.cuh"
@@ -79,28 +80,44 @@ __device__ __forceinline__ size_t cidx(const GridDev &g, int i, int j, int k) {
 }
 
 // ---------------------------------------------------------------------------
-// Provisional face flux q (3 face families).  10 FP64 instructions per face.
+// Provisional face flux, stored scaled by dt:  q' = dt q  (3 face families).
 //
 // The split coefficient gamma_f = beta_f - 1/rho0 is formed without the
 // cancellation of that difference: with rho_f - rho0 = |drho| psi_f, where
 // psi = phi when rho0 = rho_g and psi = 1 - phi when rho0 = rho_l,
 //     gamma_f = -(|drho| / rho0) psi_f beta_f,
-// so gamma_f keeps the relative accuracy of the reciprocal (and is exactly 0
+// so gamma_f keeps the relative accuracy of the division (and is exactly 0
 // in the pure rho0 phase).  With t = psi_a + psi_b and s = rho_a + rho_b =
-// 2 rho0 + |drho| t (so beta_f = 2/s), the flux is
-//     q = u*/dt - gamma_f (phat_b - phat_a)/h = u*/dt + (|drho|/(rho0 h)) t (1/s) dphat.
+// 2 rho0 + |drho| t (so beta_f = 2/s) and kappa = t/s,
+//     q' = dt q = u* - dt gamma_f (phat_b - phat_a)/h = u* + (dt |drho|/(rho0 h)) kappa dphat.
+// kappa comes from an FP32 quotient refined by one Newton step on the
+// quotient in FP64, kappa = k0 + r0 (t - s k0) (r0 the FP32 reciprocal of s),
+// which squares the FP32 error (relative error about 2^-43).
+// 7 FP64 instructions per face (8 when rho0 = rho_l).
 // ---------------------------------------------------------------------------
 template <bool RHO0_IS_G>
 __device__ __forceinline__ double face_flux(const GridDev &g, double phi_a, double phi_b,
-                                            double ph_a, double ph_b, double ustar, double ch) {
+                                            double ph_a, double ph_b, double ustar, double dtch) {
     const double sum = phi_a + phi_b;
     const double t = RHO0_IS_G ? sum : 2.0 - sum;
-    const double r = rcp_pos_nr1(fmaT(g.adrho, t, g.two_rho0));
-    return fmaT(ch, (t * r) * (ph_b - ph_a), ustar * g.idt);
+    const double s = fmaT(g.adrho, t, g.two_rho0);
+    const float tf = f64_to_f32_shift(t, 0);
+    float rf;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rf) : "f"(pos_f64_to_f32_trunc(s)));
+    const double k0 = f32_to_f64_shift(tf * rf, 0);
+    const double r0 = pos_f32_to_f64(rf);
+    const double kappa = fmaT(r0, fmaT(-s, k0, t), k0);
+    return fmaT(dtch, kappa * (ph_b - ph_a), ustar);
 }
 
+constexpr int FLUX_BX = 32, FLUX_BY = 8;
+
+// One CTA covers a 32 x 8 (i, j) tile and marches up kc planes; phat and phi
+// of each plane sit in shared memory with a one-cell halo in +x and +y, and
+// the +z neighbour read in one plane is carried as the centre of the next,
+// so phat is evaluated about once per cell.
 template <bool RHO0_IS_G>
-__global__ void __launch_bounds__(256) k_flux(GridDev g, const double *__restrict__ phi,
+__global__ void __launch_bounds__(256) k_flux(GridDev g, int kc, const double *__restrict__ phi,
                                               const double *__restrict__ pn,
                                               const double *__restrict__ pnm1,
                                               const double *__restrict__ u,
@@ -109,42 +126,76 @@ __global__ void __launch_bounds__(256) k_flux(GridDev g, const double *__restric
                                               double *__restrict__ qx, double *__restrict__ qy,
                                               double *__restrict__ qz,
                                               double *__restrict__ usq_part) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const int j = blockIdx.y * blockDim.y + threadIdx.y;
-    const int k = blockIdx.z;
-    double usq = 0.0;
-    if (i < g.nx && j < g.ny) {
-        const size_t c = cidx(g, i, j, k);
-        const double phc = phi[c];
-        const double hc = fmaT(2.0, pn[c], -pnm1[c]);
-        const double uc = u[c], vc = v[c], wc = w[c];
-        if (usq_part) usq = fmaT(uc, uc, fmaT(vc, vc, wc * wc));
-        // x-face i+1/2
-        double q = 0.0;
-        if (!(g.bcx == BC_NEUMANN && i == g.nx - 1)) {
-            const size_t e = (i == g.nx - 1) ? c - i : c + 1;
-            q = face_flux<RHO0_IS_G>(g, phc, phi[e], hc, fmaT(2.0, pn[e], -pnm1[e]), uc, g.chx);
+    __shared__ double s_ph[FLUX_BY + 1][FLUX_BX + 1];
+    __shared__ double s_phi[FLUX_BY + 1][FLUX_BX + 1];
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int tid = ty * FLUX_BX + tx;
+    const int i0 = blockIdx.x * FLUX_BX, j0 = blockIdx.y * FLUX_BY;
+    const int i = i0 + tx, j = j0 + ty;
+    const int k0 = blockIdx.z * kc;
+    const int k1 = min(k0 + kc, g.nz);
+    const bool in = (i < g.nx && j < g.ny);
+    const size_t plane = (size_t)g.nx * g.ny;
+    // source cell of every tile slot: wrap (periodic) or clamp (wall; the
+    // value of a clamped slot is never used)
+    auto src_i = [&](int ii) { return ii < g.nx ? ii : (g.bcx == BC_PERIODIC ? ii % g.nx : g.nx - 1); };
+    auto src_j = [&](int jj) { return jj < g.ny ? jj : (g.bcy == BC_PERIODIC ? jj % g.ny : g.ny - 1); };
+    const size_t own = (size_t)src_j(j) * g.nx + src_i(i);
+    // halo slot handled by this thread: tid < 32 -> row FLUX_BY, 32..39 -> column FLUX_BX
+    int hy = -1, hx = -1;
+    size_t hoff = 0;
+    if (tid < FLUX_BX) {
+        hy = FLUX_BY;
+        hx = tid;
+    } else if (tid < FLUX_BX + FLUX_BY) {
+        hy = tid - FLUX_BX;
+        hx = FLUX_BX;
+    }
+    if (hy >= 0) hoff = (size_t)src_j(j0 + hy) * g.nx + src_i(i0 + hx);
+    const double dtchx = g.dt * g.chx, dtchy = g.dt * g.chy;
+    double ph_c = 0.0, phi_c = 0.0, usq = 0.0;
+    for (int k = k0; k < k1; ++k) {
+        const size_t base = (size_t)k * plane;
+        if (k == k0) {
+            phi_c = phi[base + own];
+            ph_c = fmaT(2.0, pn[base + own], -pnm1[base + own]);
         }
-        qx[c] = q;
-        // y-face j+1/2
-        q = 0.0;
-        if (!(g.bcy == BC_NEUMANN && j == g.ny - 1)) {
-            const size_t nn = (j == g.ny - 1) ? c - (size_t)j * g.nx : c + g.nx;
-            q = face_flux<RHO0_IS_G>(g, phc, phi[nn], hc, fmaT(2.0, pn[nn], -pnm1[nn]), vc, g.chy);
+        s_ph[ty][tx] = ph_c;
+        s_phi[ty][tx] = phi_c;
+        if (hy >= 0) {
+            s_phi[hy][hx] = phi[base + hoff];
+            s_ph[hy][hx] = fmaT(2.0, pn[base + hoff], -pnm1[base + hoff]);
         }
-        qy[c] = q;
-        // z-face k+1/2 (top wall at k = nz-1)
-        q = 0.0;
-        if (k < g.nz - 1) {
-            const size_t t = c + (size_t)g.nx * g.ny;
-            q = face_flux<RHO0_IS_G>(g, phc, phi[t], hc, fmaT(2.0, pn[t], -pnm1[t]), wc, g.chz[k]);
+        __syncthreads();
+        double ph_t = 0.0, phi_t = 0.0;
+        if (k + 1 < g.nz) {
+            phi_t = phi[base + plane + own];
+            ph_t = fmaT(2.0, pn[base + plane + own], -pnm1[base + plane + own]);
         }
-        qz[c] = q;
+        if (in) {
+            const size_t c = base + (size_t)j * g.nx + i;
+            const double uc = u[c], vc = v[c], wc = w[c];
+            if (usq_part) usq = fmaT(uc, uc, fmaT(vc, vc, fmaT(wc, wc, usq)));
+            double q = 0.0;
+            if (!(g.bcx == BC_NEUMANN && i == g.nx - 1))
+                q = face_flux<RHO0_IS_G>(g, phi_c, s_phi[ty][tx + 1], ph_c, s_ph[ty][tx + 1], uc, dtchx);
+            qx[c] = q;
+            q = 0.0;
+            if (!(g.bcy == BC_NEUMANN && j == g.ny - 1))
+                q = face_flux<RHO0_IS_G>(g, phi_c, s_phi[ty + 1][tx], ph_c, s_ph[ty + 1][tx], vc, dtchy);
+            qy[c] = q;
+            q = 0.0;
+            if (k + 1 < g.nz) q = face_flux<RHO0_IS_G>(g, phi_c, phi_t, ph_c, ph_t, wc, g.dt * g.chz[k]);
+            qz[c] = q;
+        }
+        ph_c = ph_t;
+        phi_c = phi_t;
+        __syncthreads();
     }
     if (usq_part) {
-        const double s = block_sum(usq);
-        if (threadIdx.x == 0 && threadIdx.y == 0)
-            usq_part[((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = s;
+        const double sm = block_sum(usq);
+        if (tid == 0)
+            usq_part[((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = sm;
     }
 }
 
@@ -200,34 +251,6 @@ __device__ __forceinline__ double resid(const GridDev &g, int i, int j, int k,
                                         const double *__restrict__ f,
                                         const double *__restrict__ p) {
     return f[cidx(g, i, j, k)] - lap(g, i, j, k, p);
-}
-
-// 2^e as a double (e within the normal range)
-__device__ __forceinline__ double pow2d(int e) {
-    return __hiloint2double((e + 1023) << 20, 0);
-}
-// binary exponent of a positive double given by its bit pattern (0 -> 0)
-__device__ __forceinline__ int exp_of_bits(unsigned long long b) {
-    return b ? (int)((b >> 52) & 0x7ff) - 1023 : 0;
-}
-
-// double -> float with the binary exponent shifted by -es (x * 2^-es),
-// truncating; |result| below 2^-126 flushes to zero.  Integer-only.
-__device__ __forceinline__ float f64_to_f32_shift(double x, int es) {
-    const unsigned hi = (unsigned)__double2hiint(x);
-    const unsigned lo = (unsigned)__double2loint(x);
-    const int e = (int)((hi >> 20) & 0x7ff) - es;  // biased double exponent after the shift
-    if (e <= 896) return __uint_as_float(hi & 0x80000000u);
-    const unsigned b = ((unsigned)(e - 896) << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29);
-    return __uint_as_float(b | (hi & 0x80000000u));
-}
-// float -> double times 2^es (flush float denormals to zero).  Integer-only.
-__device__ __forceinline__ double f32_to_f64_shift(float f, int es) {
-    const unsigned b = __float_as_uint(f);
-    const unsigned a = b & 0x7fffffffu;
-    if (a < 0x00800000u) return __hiloint2double((int)(b & 0x80000000u), 0);
-    const unsigned hi = (((a >> 23) + 896u + (unsigned)es) << 20) | ((a >> 3) & 0xfffffu);
-    return __hiloint2double((int)(hi | (b & 0x80000000u)), (int)(a << 29));
 }
 
 enum {
@@ -479,61 +502,201 @@ __global__ void __launch_bounds__(256) k_xinv(GridDev g, FFTDesc D, int L, const
     }
 }
 
-// Tridiagonal z-solves.  One thread per (kx, ky) line; the forward sweep keeps
-// its modified right-hand side in place, the backward sweep overwrites it with
-// the solution.  Factorisation tables m_k and 1/beta_k depend only on the
-// eigenvalue pair, stored once per distinct pair: index ((k*Uy + uy)*Ux + ux).
+// Tridiagonal z-solves, one per (kx, ky) line, with factorisation tables
+// m_k and 1/beta_k that depend only on the eigenvalue pair and are stored once
+// per distinct pair at index ((k*Uy + uy)*Ux + ux).  In a periodic x
+// direction the half-complex indices i and nx-i share their eigenvalue, so one
+// thread solves both lines against one table read.  The forward sweep keeps
+// its modified right-hand side in place and the backward sweep overwrites it
+// with the solution.  Each thread streams its line values and table entries
+// through a THOMAS_S-stage cp.async ring in shared memory (its own slots:
+// no barrier), so THOMAS_S planes of loads are in flight per thread while the
+// sequential recurrence runs.
 // The (0,0) line is singular: its right-hand side mean is removed, the fluxes
 // are integrated from the bottom wall and the result is given zero
 // dzf-weighted mean (the pressure gauge).
-template <typename T>
-__global__ void __launch_bounds__(128) k_thomas(GridDev g, int Ux, int Uy, const T *__restrict__ mtab,
-                                                const T *__restrict__ ibtab,
-                                                const T *__restrict__ cup, T *data,
-                                                const int *conv) {
-    if (conv && *conv) return;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const int j = blockIdx.y;
-    if (i >= g.nx) return;
-    const size_t plane = (size_t)g.nx * g.ny;
-    T *d = data + (size_t)j * g.nx + i;
-    const int nz = g.nz;
-    if (i == 0 && j == 0) {
-        double s = 0.0;
-        for (int k = 0; k < nz; ++k) s = fmaT(g.dzf[k], (double)d[k * plane], s);
-        const double fbar = s * g.inv_lz;
-        double F = 0.0, pk = 0.0, ps = 0.0;
-        for (int k = 0; k < nz; ++k) {
-            const double fk = (double)d[k * plane];  // read f_k before p_k overwrites it
-            d[k * plane] = (T)pk;
-            ps = fmaT(g.dzf[k], pk, ps);
-            if (k < nz - 1) {
-                F = fmaT(g.dzf[k], fk - fbar, F);  // flux at face k+1/2
-                pk = fmaT(g.dzc[k], F, pk);        // p_(k+1)
-            }
+constexpr int THOMAS_S = 16;
+constexpr int THOMAS_BLOCK = 64;
+
+template <typename T, int NL>
+__device__ __forceinline__ void thomas_lines(int nz, size_t plane, T *d0, T *d1, size_t ts,
+                                             size_t tb, const T *__restrict__ mtab,
+                                             const T *__restrict__ ibtab,
+                                             const T *__restrict__ cup, T *ring) {
+    // ring slot (stage, item) of this thread: ring[(stage*(NL+1) + item)*THOMAS_BLOCK + tid]
+    const int tid = threadIdx.x;
+    T *d[2] = {d0, d1};
+    auto slot = [&](int stage, int item) -> T * {
+        return ring + ((size_t)(stage * (NL + 1) + item) * THOMAS_BLOCK + tid);
+    };
+    // ---- forward sweep over k = 1 .. nz-1; plane k lives in stage (k-1) % S
+#pragma unroll 1
+    for (int q = 0; q < THOMAS_S; ++q) {
+        const int k = 1 + q;
+        if (k < nz) {
+            cp_async<sizeof(T)>(slot(q, NL), mtab + (size_t)k * ts + tb);
+#pragma unroll
+            for (int l = 0; l < NL; ++l) cp_async<sizeof(T)>(slot(q, l), d[l] + (size_t)k * plane);
         }
-        const double pbar = ps * g.inv_lz;
-        for (int k = 0; k < nz; ++k) d[k * plane] = (T)((double)d[k * plane] - pbar);
-        return;
+        cp_async_commit();
     }
-    const int ux = (g.bcx == BC_PERIODIC) ? min(i, g.nx - i) : i;
+    T prev[2];
+#pragma unroll
+    for (int l = 0; l < NL; ++l) prev[l] = d[l][0];
+    int st = 0;
+#pragma unroll 1
+    for (int k = 1; k < nz; ++k) {
+        cp_async_wait<THOMAS_S - 1>();
+        const T m = *slot(st, NL);
+#pragma unroll
+        for (int l = 0; l < NL; ++l) {
+            prev[l] = fmaT(-m, prev[l], *slot(st, l));
+            d[l][(size_t)k * plane] = prev[l];
+        }
+        const int kn = k + THOMAS_S;
+        if (kn < nz) {
+            cp_async<sizeof(T)>(slot(st, NL), mtab + (size_t)kn * ts + tb);
+#pragma unroll
+            for (int l = 0; l < NL; ++l) cp_async<sizeof(T)>(slot(st, l), d[l] + (size_t)kn * plane);
+        }
+        cp_async_commit();
+        st = (st + 1 == THOMAS_S) ? 0 : st + 1;
+    }
+    cp_async_wait<0>();
+    // ---- backward sweep: p_(nz-1) = d_(nz-1)/beta, p_k = (d_k - c_k p_(k+1))/beta_k
+    const T ibt = ibtab[(size_t)(nz - 1) * ts + tb];
+#pragma unroll
+    for (int l = 0; l < NL; ++l) {
+        prev[l] = prev[l] * ibt;
+        d[l][(size_t)(nz - 1) * plane] = prev[l];
+    }
+    // plane k (descending from nz-2) lives in stage (nz-2-k) % S
+#pragma unroll 1
+    for (int q = 0; q < THOMAS_S; ++q) {
+        const int k = nz - 2 - q;
+        if (k >= 0) {
+            cp_async<sizeof(T)>(slot(q, NL), ibtab + (size_t)k * ts + tb);
+#pragma unroll
+            for (int l = 0; l < NL; ++l) cp_async<sizeof(T)>(slot(q, l), d[l] + (size_t)k * plane);
+        }
+        cp_async_commit();
+    }
+    st = 0;
+#pragma unroll 1
+    for (int k = nz - 2; k >= 0; --k) {
+        cp_async_wait<THOMAS_S - 1>();
+        const T ib = *slot(st, NL);
+        const T c = cup[k];
+#pragma unroll
+        for (int l = 0; l < NL; ++l) {
+            prev[l] = fmaT(-c, prev[l], *slot(st, l)) * ib;
+            d[l][(size_t)k * plane] = prev[l];
+        }
+        const int kn = k - THOMAS_S;
+        if (kn >= 0) {
+            cp_async<sizeof(T)>(slot(st, NL), ibtab + (size_t)kn * ts + tb);
+#pragma unroll
+            for (int l = 0; l < NL; ++l) cp_async<sizeof(T)>(slot(st, l), d[l] + (size_t)kn * plane);
+        }
+        cp_async_commit();
+        st = (st + 1 == THOMAS_S) ? 0 : st + 1;
+    }
+    cp_async_wait<0>();
+}
+
+// The singular (0,0) line, solved by one warp.  With a_k = dzf_k (f_k - fbar)
+// (fbar the dzf-weighted mean, removed so the line is compatible), the flux
+// through face k+1/2 is the inclusive prefix sum F_(k+1/2) = sum_(k'<=k) a_k'
+// (zero flux through the bottom wall) and the pressure is the exclusive prefix
+// sum p_k = sum_(k'<k) dzc_(k'+1/2) F_(k'+1/2) (p_0 = 0); both sums run as warp
+// scans over chunks of 32 planes.  Finally the dzf-weighted mean of p is
+// removed (the pressure gauge).
+__device__ __forceinline__ double warp_sum(double v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ double warp_inclusive_scan(double v, int lane) {
+    for (int o = 1; o < 32; o <<= 1) {
+        const double u = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += u;
+    }
+    return v;
+}
+
+template <typename T>
+__device__ void singular_line_warp(const GridDev &g, T *d, size_t plane) {
+    const int lane = threadIdx.x & 31;
+    const int nz = g.nz;
+    double s = 0.0;
+    for (int k = lane; k < nz; k += 32) s = fmaT(g.dzf[k], (double)d[(size_t)k * plane], s);
+    const double fbar = warp_sum(s) * g.inv_lz;
+    double Fc = 0.0, pc = 0.0, ps = 0.0;
+    for (int k0 = 0; k0 < nz; k0 += 32) {
+        const int k = k0 + lane;
+        double a = 0.0, h = 0.0;
+        if (k < nz) {
+            a = g.dzf[k] * ((double)d[(size_t)k * plane] - fbar);
+            h = g.dzc[k];  // 0 at the top wall
+        }
+        const double F = warp_inclusive_scan(a, lane) + Fc;  // F_(k+1/2)
+        const double inc = h * F;                             // p_(k+1) - p_k
+        const double sc = warp_inclusive_scan(inc, lane);
+        const double pk = pc + (sc - inc);                    // exclusive: p_k
+        if (k < nz) {
+            d[(size_t)k * plane] = (T)pk;
+            ps = fmaT(g.dzf[k], pk, ps);
+        }
+        Fc = __shfl_sync(0xffffffffu, F, 31);
+        pc += __shfl_sync(0xffffffffu, sc, 31);
+    }
+    const double pbar = warp_sum(ps) * g.inv_lz;
+    for (int k = lane; k < nz; k += 32)
+        d[(size_t)k * plane] = (T)((double)d[(size_t)k * plane] - pbar);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(THOMAS_BLOCK) k_thomas(GridDev g, int Ux, int Uy,
+                                                         const T *__restrict__ mtab,
+                                                         const T *__restrict__ ibtab,
+                                                         const T *__restrict__ cup, T *data,
+                                                         const int *conv) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    if (conv && *conv) return;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y;
+    if (blockIdx.x == 0 && j == 0 && threadIdx.x < 32) {
+        singular_line_warp<T>(g, data, (size_t)g.nx * g.ny);  // line (0,0)
+        if (t == 0) return;
+    }
+    int i1, i2 = -1;
+    if (g.bcx == BC_PERIODIC) {
+        if (t > g.nx / 2) return;
+        i1 = t;
+        if (t > 0 && 2 * t != g.nx) i2 = g.nx - t;
+    } else {
+        if (t >= g.nx) return;
+        i1 = t;
+    }
+    const size_t plane = (size_t)g.nx * g.ny;
+    T *d = data + (size_t)j * g.nx + i1;
+    const int nz = g.nz;
+    const int ux = i1;  // periodic: i1 <= nx/2 is already the distinct index
     const int uy = (g.bcy == BC_PERIODIC) ? min(j, g.ny - j) : j;
     const size_t tb = (size_t)uy * Ux + ux;
     const size_t ts = (size_t)Ux * Uy;
-    T prev = d[0];
-    for (int k = 1; k < nz; ++k) {
-        prev = fmaT(-mtab[k * ts + tb], prev, d[k * plane]);
-        d[k * plane] = prev;
-    }
-    T pk = prev * ibtab[(nz - 1) * ts + tb];
-    d[(nz - 1) * plane] = pk;
-    for (int k = nz - 2; k >= 0; --k) {
-        pk = fmaT(-cup[k], pk, d[k * plane]) * ibtab[k * ts + tb];
-        d[k * plane] = pk;
-    }
+    T *ring = (T *)smem_raw;
+    if (i2 >= 0)
+        thomas_lines<T, 2>(nz, plane, d, data + (size_t)j * g.nx + i2, ts, tb, mtab, ibtab, cup, ring);
+    else
+        thomas_lines<T, 1>(nz, plane, d, d, ts, tb, mtab, ibtab, cup, ring);
 }
 
-// u = dt q - (dt/rho0) G p on non-wall faces; wall faces 0.  3 FP64 per face.
+template <typename T> constexpr size_t thomas_smem() {
+    return (size_t)THOMAS_S * 3 * THOMAS_BLOCK * sizeof(T);
+}
+
+// u = q' - (dt/rho0) G p on non-wall faces (q' = dt q); wall faces 0.
+// 2 FP64 instructions per face.
 __global__ void __launch_bounds__(256) k_correct(GridDev g, const double *__restrict__ p,
                                                  const double *__restrict__ qx,
                                                  const double *__restrict__ qy,
@@ -549,17 +712,17 @@ __global__ void __launch_bounds__(256) k_correct(GridDev g, const double *__rest
     double r = 0.0;
     if (!(g.bcx == BC_NEUMANN && i == g.nx - 1)) {
         const size_t e = (i == g.nx - 1) ? c - i : c + 1;
-        r = fmaT(-g.cgx, p[e] - pc, g.dt * qx[c]);
+        r = fmaT(-g.cgx, p[e] - pc, qx[c]);
     }
     u[c] = r;
     r = 0.0;
     if (!(g.bcy == BC_NEUMANN && j == g.ny - 1)) {
         const size_t nn = (j == g.ny - 1) ? c - (size_t)j * g.nx : c + g.nx;
-        r = fmaT(-g.cgy, p[nn] - pc, g.dt * qy[c]);
+        r = fmaT(-g.cgy, p[nn] - pc, qy[c]);
     }
     v[c] = r;
     r = 0.0;
-    if (k < g.nz - 1) r = fmaT(-g.cgz[k], p[c + (size_t)g.nx * g.ny] - pc, g.dt * qz[c]);
+    if (k < g.nz - 1) r = fmaT(-g.cgz[k], p[c + (size_t)g.nx * g.ny] - pc, qz[c]);
     w[c] = r;
 }
 
