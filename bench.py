@@ -53,6 +53,19 @@ def measured_peaks():
         return HBM_PEAK_FALLBACK, "fallback"
 
 
+def measured_traffic(kernel):
+    """DRAM bytes per launch of a kernel from the committed ncu summaries
+    (lines 'traffic_per_launch_bytes <kernel> <bytes>' in profiles/*.md)."""
+    import glob
+    name = {"flux": "k_flux", "resid_fwdx": "k_xfwd_resid", "div_fwdx": "k_xfwd"}.get(kernel, kernel)
+    for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
+        for line in open(path):
+            parts = line.split()
+            if len(parts) == 3 and parts[0] == "traffic_per_launch_bytes" and parts[1] == name:
+                return int(parts[2])
+    return None
+
+
 def algorithmic_per_point(nx, ny, mixed):
     """Algorithmic HBM bytes and FP64 flops (FMA = 2) per grid point of each
     kernel of one projection.  Transform passes use the conventional real-FFT
@@ -255,15 +268,17 @@ def run_fizzy(args):
         tfl = fl_pt * npts / avg_s / 1e12
         t_hbm = b_pt / (hbm_peak * 1e9)
         t_alu = fl_pt / (FP64_PEAK_NOMINAL * 1e12)
+        traffic = measured_traffic(dom) if (spec.nx, spec.ny, spec.nz) == (256, 256, 256) else None
         if t_alu > t_hbm:
             roof = {"bound": "alu", "achieved": tfl, "peak": FP64_PEAK_NOMINAL, "unit": "TFLOP/s",
-                    "frac": tfl / FP64_PEAK_NOMINAL, "traffic": None, "kernel": dom,
+                    "frac": tfl / FP64_PEAK_NOMINAL, "traffic": traffic, "kernel": dom,
                     "peak_source": "nominal FP64 (recipe table)",
-                    "hbm_gbs": gbs, "hbm_frac": gbs / hbm_peak}
+                    "algorithmic_bytes": b_pt * npts, "hbm_gbs": gbs,
+                    "hbm_frac": gbs / hbm_peak, "hbm_peak_source": hbm_src}
         else:
             roof = {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
-                    "frac": gbs / hbm_peak, "traffic": None, "kernel": dom,
-                    "peak_source": hbm_src}
+                    "frac": gbs / hbm_peak, "traffic": traffic, "kernel": dom,
+                    "algorithmic_bytes": b_pt * npts, "peak_source": hbm_src}
     kernels = {k: {"ms_avg": v[0] / v[1], "launches": v[1],
                    "share": v[0] / max(1e-9, sum(x[0] for x in kern.values()))} for k, v in kern.items()}
 

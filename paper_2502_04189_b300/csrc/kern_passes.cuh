@@ -65,18 +65,35 @@ struct GridDev {
 // Mixed-mode stopping rule, evaluated by one thread once max|r| is known:
 // relres <= tol and, unless disabled, the divergence the correction will
 // leave, max|D u| dx / U = (dt/rho0) max|r| dx / U, <= div_tol.
+template <bool CG>
 __device__ __forceinline__ bool refine_done(const GridDev &g, double rmax, double fmax, double tol,
                                             double *rel_out) {
     const double rel = fmax > 0.0 ? rmax / fmax : rmax;
     *rel_out = rel;
     if (!(rel <= tol)) return false;
     if (g.div_tol < 0.0) return true;
-    const double U = sqrt(*g.usq * g.inv_3n);
+    const double U = sqrt((CG ? __ldcg(g.usq) : *g.usq) * g.inv_3n);
     return U > 0.0 ? rmax * g.div_scale / U <= g.div_tol : rmax == 0.0;
 }
 
 __device__ __forceinline__ size_t cidx(const GridDev &g, int i, int j, int k) {
     return ((size_t)k * g.ny + j) * (size_t)g.nx + i;
+}
+
+// Every kernel body below works on a "virtual block" VB (the CTA-level
+// coordinates it would get from blockIdx) so that the same code runs as a
+// stand-alone kernel and as a work item of the persistent batch kernel.
+// CG selects how data written earlier in the same launch is read: the
+// persistent kernel reads such data with ld.global.cg (L2 only), because a
+// line another SM has rewritten may still sit in this SM's L1.
+struct VB {
+    int x, y, z;
+};
+__device__ __forceinline__ VB vb_of_grid() { return VB{(int)blockIdx.x, (int)blockIdx.y, (int)blockIdx.z}; }
+
+template <bool CG, typename T> __device__ __forceinline__ T ldp(const T *p) {
+    if (CG) return __ldcg(p);
+    return *p;
 }
 
 // ---------------------------------------------------------------------------
@@ -117,22 +134,17 @@ constexpr int FLUX_BX = 32, FLUX_BY = 8;
 // the +z neighbour read in one plane is carried as the centre of the next,
 // so phat is evaluated about once per cell.
 template <bool RHO0_IS_G>
-__global__ void __launch_bounds__(256) k_flux(GridDev g, int kc, const double *__restrict__ phi,
-                                              const double *__restrict__ pn,
-                                              const double *__restrict__ pnm1,
-                                              const double *__restrict__ u,
-                                              const double *__restrict__ v,
-                                              const double *__restrict__ w,
-                                              double *__restrict__ qx, double *__restrict__ qy,
-                                              double *__restrict__ qz,
-                                              double *__restrict__ usq_part) {
+__device__ __forceinline__ void flux_body(const GridDev &g, int kc, VB vb, const double *phi,
+                                          const double *pn, const double *pnm1, const double *u,
+                                          const double *v, const double *w, double *qx, double *qy,
+                                          double *qz, double *usq_slot) {
     __shared__ double s_ph[FLUX_BY + 1][FLUX_BX + 1];
     __shared__ double s_phi[FLUX_BY + 1][FLUX_BX + 1];
-    const int tx = threadIdx.x, ty = threadIdx.y;
-    const int tid = ty * FLUX_BX + tx;
-    const int i0 = blockIdx.x * FLUX_BX, j0 = blockIdx.y * FLUX_BY;
+    const int tid = block_tid();
+    const int tx = tid & (FLUX_BX - 1), ty = tid / FLUX_BX;
+    const int i0 = vb.x * FLUX_BX, j0 = vb.y * FLUX_BY;
     const int i = i0 + tx, j = j0 + ty;
-    const int k0 = blockIdx.z * kc;
+    const int k0 = vb.z * kc;
     const int k1 = min(k0 + kc, g.nz);
     const bool in = (i < g.nx && j < g.ny);
     const size_t plane = (size_t)g.nx * g.ny;
@@ -175,7 +187,7 @@ __global__ void __launch_bounds__(256) k_flux(GridDev g, int kc, const double *_
         if (in) {
             const size_t c = base + (size_t)j * g.nx + i;
             const double uc = u[c], vc = v[c], wc = w[c];
-            if (usq_part) usq = fmaT(uc, uc, fmaT(vc, vc, fmaT(wc, wc, usq)));
+            if (usq_slot) usq = fmaT(uc, uc, fmaT(vc, vc, fmaT(wc, wc, usq)));
             double q = 0.0;
             if (!(g.bcx == BC_NEUMANN && i == g.nx - 1))
                 q = face_flux<RHO0_IS_G>(g, phi_c, s_phi[ty][tx + 1], ph_c, s_ph[ty][tx + 1], uc, dtchx);
@@ -192,65 +204,84 @@ __global__ void __launch_bounds__(256) k_flux(GridDev g, int kc, const double *_
         phi_c = phi_t;
         __syncthreads();
     }
-    if (usq_part) {
+    if (usq_slot) {
         const double sm = block_sum(usq);
-        if (tid == 0)
-            usq_part[((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = sm;
+        if (tid == 0) *usq_slot = sm;
     }
 }
 
-// Deterministic final sum of per-block partials (one block).
-__global__ void k_sum_partials(const double *__restrict__ part, int n, double *__restrict__ out) {
-    double s = 0.0;
-    for (int t = threadIdx.x; t < n; t += blockDim.x) s += part[t];
-    s = block_sum(s);
-    if (threadIdx.x == 0) *out = s;
+template <bool RHO0_IS_G>
+__global__ void __launch_bounds__(256) k_flux(GridDev g, int kc, const double *__restrict__ phi,
+                                              const double *__restrict__ pn,
+                                              const double *__restrict__ pnm1,
+                                              const double *__restrict__ u,
+                                              const double *__restrict__ v,
+                                              const double *__restrict__ w,
+                                              double *__restrict__ qx, double *__restrict__ qy,
+                                              double *__restrict__ qz,
+                                              double *__restrict__ usq_part) {
+    double *slot = usq_part ? usq_part + ((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x
+                            : nullptr;
+    flux_body<RHO0_IS_G>(g, kc, vb_of_grid(), phi, pn, pnm1, u, v, w, qx, qy, qz, slot);
 }
 
-// rho0-weighted divergence of q at one cell; cx, cy, cz are rho0/h (maybe scaled).
+// Deterministic final sum of per-block partials (one block).
+template <bool CG>
+__device__ __forceinline__ void sum_partials_body(const double *part, int n, double *out) {
+    double s = 0.0;
+    for (int t = block_tid(); t < n; t += block_nthreads()) s += ldp<CG>(part + t);
+    s = block_sum(s);
+    if (block_tid() == 0) *out = s;
+}
+__global__ void k_sum_partials(const double *__restrict__ part, int n, double *__restrict__ out) {
+    sum_partials_body<false>(part, n, out);
+}
+
+// rho0-weighted divergence of q' at one cell; cx, cy, cz are rho0/(dt h) (maybe scaled).
+template <bool CG>
 __device__ __forceinline__ double div_q(const GridDev &g, int i, int j, int k, double cx, double cy,
-                                        double cz, const double *__restrict__ qx,
-                                        const double *__restrict__ qy,
-                                        const double *__restrict__ qz) {
+                                        double cz, const double *qx, const double *qy,
+                                        const double *qz) {
     const size_t c = cidx(g, i, j, k);
-    const double qe = qx[c];
-    const double qw = (i > 0) ? qx[c - 1] : (g.bcx == BC_PERIODIC ? qx[c + g.nx - 1] : 0.0);
-    const double qn = qy[c];
-    const double qs = (j > 0) ? qy[c - g.nx] : (g.bcy == BC_PERIODIC ? qy[c + (size_t)(g.ny - 1) * g.nx] : 0.0);
-    const double qt = qz[c];
-    const double qb = (k > 0) ? qz[c - (size_t)g.nx * g.ny] : 0.0;
+    const double qe = ldp<CG>(qx + c);
+    const double qw = (i > 0) ? ldp<CG>(qx + c - 1) : (g.bcx == BC_PERIODIC ? ldp<CG>(qx + c + g.nx - 1) : 0.0);
+    const double qn = ldp<CG>(qy + c);
+    const double qs = (j > 0) ? ldp<CG>(qy + c - g.nx)
+                              : (g.bcy == BC_PERIODIC ? ldp<CG>(qy + c + (size_t)(g.ny - 1) * g.nx) : 0.0);
+    const double qt = ldp<CG>(qz + c);
+    const double qb = (k > 0) ? ldp<CG>(qz + c - (size_t)g.nx * g.ny) : 0.0;
     return fmaT(cx, qe - qw, fmaT(cy, qn - qs, cz * (qt - qb)));
 }
 
 // L_h p at one cell in flux (difference) form: each face difference is
 // formed first, so a smooth p loses no accuracy to cancellation.  Wall faces
 // carry zero flux (ghost value = centre value).
-__device__ __forceinline__ double lap(const GridDev &g, int i, int j, int k,
-                                      const double *__restrict__ p) {
+template <bool CG>
+__device__ __forceinline__ double lap(const GridDev &g, int i, int j, int k, const double *p) {
     const size_t c = cidx(g, i, j, k);
-    const double pc = p[c];
+    const double pc = ldp<CG>(p + c);
     double pe, pw, pn_, ps;
-    if (i < g.nx - 1) pe = p[c + 1];
-    else pe = (g.bcx == BC_PERIODIC) ? p[c - i] : pc;
-    if (i > 0) pw = p[c - 1];
-    else pw = (g.bcx == BC_PERIODIC) ? p[c + g.nx - 1] : pc;
-    if (j < g.ny - 1) pn_ = p[c + g.nx];
-    else pn_ = (g.bcy == BC_PERIODIC) ? p[c - (size_t)j * g.nx] : pc;
-    if (j > 0) ps = p[c - g.nx];
-    else ps = (g.bcy == BC_PERIODIC) ? p[c + (size_t)(g.ny - 1) * g.nx] : pc;
+    if (i < g.nx - 1) pe = ldp<CG>(p + c + 1);
+    else pe = (g.bcx == BC_PERIODIC) ? ldp<CG>(p + c - i) : pc;
+    if (i > 0) pw = ldp<CG>(p + c - 1);
+    else pw = (g.bcx == BC_PERIODIC) ? ldp<CG>(p + c + g.nx - 1) : pc;
+    if (j < g.ny - 1) pn_ = ldp<CG>(p + c + g.nx);
+    else pn_ = (g.bcy == BC_PERIODIC) ? ldp<CG>(p + c - (size_t)j * g.nx) : pc;
+    if (j > 0) ps = ldp<CG>(p + c - g.nx);
+    else ps = (g.bcy == BC_PERIODIC) ? ldp<CG>(p + c + (size_t)(g.ny - 1) * g.nx) : pc;
     const size_t pl = (size_t)g.nx * g.ny;
-    const double pt = (k < g.nz - 1) ? p[c + pl] : pc;
-    const double pb = (k > 0) ? p[c - pl] : pc;
+    const double pt = (k < g.nz - 1) ? ldp<CG>(p + c + pl) : pc;
+    const double pb = (k > 0) ? ldp<CG>(p + c - pl) : pc;
     double acc = ((pe - pc) - (pc - pw)) * g.idx2;
     acc = fmaT((pn_ - pc) - (pc - ps), g.idy2, acc);
     acc = fmaT(g.lzc[k], pt - pc, acc);
     return fmaT(-g.lza[k], pc - pb, acc);
 }
 
-__device__ __forceinline__ double resid(const GridDev &g, int i, int j, int k,
-                                        const double *__restrict__ f,
-                                        const double *__restrict__ p) {
-    return f[cidx(g, i, j, k)] - lap(g, i, j, k, p);
+template <bool CG>
+__device__ __forceinline__ double resid(const GridDev &g, int i, int j, int k, const double *f,
+                                        const double *p) {
+    return ldp<CG>(f + cidx(g, i, j, k)) - lap<CG>(g, i, j, k, p);
 }
 
 enum {
@@ -272,25 +303,24 @@ struct XArgs {
 };
 
 // Forward x-pass: per CTA 2L real x-lines (flattened line index (k, j)).
-template <typename T, int MODE>
-__global__ void __launch_bounds__(256) k_xfwd(GridDev g, FFTDesc D, int L, XArgs a) {
+// ntiles: number of CTAs of this pass (for the last-block decision).
+template <typename T, int MODE, bool CG>
+__device__ __forceinline__ void xfwd_body(const GridDev &g, const FFTDesc &D, int L, const XArgs &a,
+                                          int bx, int ntiles, unsigned char *smem_raw) {
     typedef typename C2<T>::t T2;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     const int n = D.n, ls = n + 1;
     T2 *tw_s = (T2 *)smem_raw;
     T2 *cs_s = tw_s + n;
     T2 *A = cs_s + (n / 2 + 2);
     T2 *B = A + L * ls;
-    if (MODE == XF_MIX_RESID && a.st->converged) return;
+    if (MODE == XF_MIX_RESID && ldp<CG>(&a.st->converged)) return;
     load_tables<T>(D, tw_s, cs_s);
     const int nlines = g.ny * g.nz;
-    const int line0 = blockIdx.x * 2 * L;
+    const int line0 = bx * 2 * L;
     unsigned long long mx = 0ull;
     int ef = 0;
     float scale32 = (float)g.sigma;
-    if (MODE == XF_MIX_RESID) {
-        ef = exp_of_bits(a.st->fmax_bits);
-    }
+    if (MODE == XF_MIX_RESID) ef = exp_of_bits(ldp<CG>(&a.st->fmax_bits));
     // 1. source values into the packed complex lines
     for (int idx = threadIdx.x; idx < 2 * L * n; idx += blockDim.x) {
         const int r = idx / n, i = idx - r * n;
@@ -299,16 +329,16 @@ __global__ void __launch_bounds__(256) k_xfwd(GridDev g, FFTDesc D, int L, XArgs
         if (line < nlines) {
             const int j = line % g.ny, k = line / g.ny;
             if (MODE == XF_F64_DIVQ) {
-                const double f = div_q(g, i, j, k, g.dvx_s, g.dvy_s, g.dvz_s[k], a.qx, a.qy, a.qz);
+                const double f = div_q<CG>(g, i, j, k, g.dvx_s, g.dvy_s, g.dvz_s[k], a.qx, a.qy, a.qz);
                 if (a.track_fmax) mx = umax64(mx, absbits(f));
                 val = (T)f;
             } else if (MODE == XF_MIX_DIVQ) {
-                const double f = div_q(g, i, j, k, g.dvx, g.dvy, g.dvz[k], a.qx, a.qy, a.qz);
+                const double f = div_q<CG>(g, i, j, k, g.dvx, g.dvy, g.dvz[k], a.qx, a.qy, a.qz);
                 a.f_out[cidx(g, i, j, k)] = f;
                 mx = umax64(mx, absbits(f));
                 val = (T)(f64_to_f32_shift(f, 0) * scale32);
             } else {
-                const double rr = resid(g, i, j, k, a.f, a.p);
+                const double rr = resid<CG>(g, i, j, k, a.f, a.p);
                 mx = umax64(mx, absbits(rr));
                 val = (T)(f64_to_f32_shift(rr, ef) * scale32);
             }
@@ -339,16 +369,17 @@ __global__ void __launch_bounds__(256) k_xfwd(GridDev g, FFTDesc D, int L, XArgs
         if (threadIdx.x == 0) {
             __threadfence();
             const unsigned ticket = atomicAdd(&a.st->done_blocks[a.slot], 1u);
-            last = (ticket == gridDim.x - 1);
+            last = (ticket == (unsigned)ntiles - 1);
         }
         __syncthreads();
         if (last && threadIdx.x == 0) {
             __threadfence();
             const unsigned long long rb = atomicMax(&a.st->rmax_bits[a.slot], 0ull);
+            const unsigned long long fb = atomicMax(&a.st->fmax_bits, 0ull);
             const double rmax = __longlong_as_double((long long)rb);
-            const double fmax = __longlong_as_double((long long)a.st->fmax_bits);
+            const double fmax = __longlong_as_double((long long)fb);
             double rel;
-            const bool done = refine_done(g, rmax, fmax, a.tol, &rel);
+            const bool done = refine_done<CG>(g, rmax, fmax, a.tol, &rel);
             a.st->relres = rel;
             a.st->n_resid = a.slot + 1;
             a.st->iterations = a.slot;
@@ -357,20 +388,29 @@ __global__ void __launch_bounds__(256) k_xfwd(GridDev g, FFTDesc D, int L, XArgs
     }
 }
 
+template <typename T, int MODE>
+__global__ void __launch_bounds__(256) k_xfwd(GridDev g, FFTDesc D, int L, XArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    xfwd_body<T, MODE, false>(g, D, L, a, blockIdx.x, gridDim.x, smem_raw);
+}
+
 // Residual-only check (no transform): max |f - L_h p| into rmax_bits[slot];
 // the last block sets relres/converged.  f_from_q != 0: f = rho0 D(q) on the fly.
-__global__ void __launch_bounds__(256) k_residmax(GridDev g, XArgs a, int f_from_q) {
-    if (a.st->converged && !f_from_q) return;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const int j = blockIdx.y, k = blockIdx.z;
+// Virtual block: x = tile of 256 cells along x, y = j, z = k.
+template <bool CG>
+__device__ __forceinline__ void residmax_body(const GridDev &g, const XArgs &a, int f_from_q, VB vb,
+                                              int ntiles) {
+    if (!f_from_q && ldp<CG>(&a.st->converged)) return;
+    const int i = vb.x * blockDim.x + threadIdx.x;
+    const int j = vb.y, k = vb.z;
     unsigned long long mx = 0ull, fm = 0ull;
     if (i < g.nx) {
         if (f_from_q) {  // FP64-mode check: f recomputed from q
-            const double f = div_q(g, i, j, k, g.dvx, g.dvy, g.dvz[k], a.qx, a.qy, a.qz);
+            const double f = div_q<CG>(g, i, j, k, g.dvx, g.dvy, g.dvz[k], a.qx, a.qy, a.qz);
             fm = absbits(f);
-            mx = absbits(f - lap(g, i, j, k, a.p));
+            mx = absbits(f - lap<CG>(g, i, j, k, a.p));
         } else {
-            mx = absbits(resid(g, i, j, k, a.f, a.p));
+            mx = absbits(resid<CG>(g, i, j, k, a.f, a.p));
         }
     }
     block_max_atomic(mx, &a.st->rmax_bits[a.slot]);
@@ -379,9 +419,8 @@ __global__ void __launch_bounds__(256) k_residmax(GridDev g, XArgs a, int f_from
     __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
-        const unsigned nb = gridDim.x * gridDim.y * gridDim.z;
         const unsigned ticket = atomicAdd(&a.st->done_blocks[a.slot], 1u);
-        last = (ticket == nb - 1);
+        last = (ticket == (unsigned)ntiles - 1);
     }
     __syncthreads();
     if (last && threadIdx.x == 0) {
@@ -392,7 +431,7 @@ __global__ void __launch_bounds__(256) k_residmax(GridDev g, XArgs a, int f_from
         const double fmax = __longlong_as_double((long long)fb);
         if (!f_from_q) {
             double rel;
-            const bool done = refine_done(g, rmax, fmax, a.tol, &rel);
+            const bool done = refine_done<CG>(g, rmax, fmax, a.tol, &rel);
             a.st->relres = rel;
             a.st->n_resid = a.slot + 1;
             a.st->iterations = a.slot;
@@ -403,13 +442,17 @@ __global__ void __launch_bounds__(256) k_residmax(GridDev g, XArgs a, int f_from
     }
 }
 
-// Forward / inverse y-pass on a tile of TX columns of plane k (in place).
-template <typename T, bool INV>
-__global__ void __launch_bounds__(256) k_ypass(int nx, int ny, FFTDesc D, int TX, T *data,
-                                               const int *conv) {
+__global__ void __launch_bounds__(256) k_residmax(GridDev g, XArgs a, int f_from_q) {
+    residmax_body<false>(g, a, f_from_q, vb_of_grid(), gridDim.x * gridDim.y * gridDim.z);
+}
+
+// Forward / inverse y-pass on a tile of TX columns (tile bx) of plane k (in place).
+template <typename T, bool INV, bool CG>
+__device__ __forceinline__ void ypass_body(int nx, int ny, const FFTDesc &D, int TX, T *data,
+                                           const int *conv, int bx, int kplane,
+                                           unsigned char *smem_raw) {
     typedef typename C2<T>::t T2;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    if (conv && *conv) return;
+    if (conv && ldp<CG>(conv)) return;
     const int n = D.n, ls = n + 1;
     const int L = TX / 2;
     T2 *tw_s = (T2 *)smem_raw;
@@ -417,14 +460,14 @@ __global__ void __launch_bounds__(256) k_ypass(int nx, int ny, FFTDesc D, int TX
     T2 *A = cs_s + (n / 2 + 2);
     T2 *B = A + L * ls;
     load_tables<T>(D, tw_s, cs_s);
-    const int i0 = blockIdx.x * TX;
+    const int i0 = bx * TX;
     const int ncols = min(TX, nx - i0);
-    T *plane = data + (size_t)blockIdx.y * ny * nx + i0;
+    T *plane = data + (size_t)kplane * ny * nx + i0;
     const int M = n / 2 + 1;
     if (!INV) {
         for (int idx = threadIdx.x; idx < n * TX; idx += blockDim.x) {
             const int j = idx / TX, c = idx - j * TX;
-            const T val = (c < ncols) ? plane[(size_t)j * nx + c] : (T)0;
+            const T val = (c < ncols) ? ldp<CG>(plane + (size_t)j * nx + c) : (T)0;
             ((T *)(A + (c >> 1) * ls))[2 * line_pos(j, n, D.kind) + (c & 1)] = val;
         }
         __syncthreads();
@@ -442,7 +485,7 @@ __global__ void __launch_bounds__(256) k_ypass(int nx, int ny, FFTDesc D, int TX
             const int m = t / L, l = t - m * L;
             inv_combine<T>(A + l * ls, n, m, D.kind, cs_s, [&](int ab, int ix) -> T {
                 const int c = 2 * l + ab;
-                return (c < ncols) ? plane[(size_t)ix * nx + c] : (T)0;
+                return (c < ncols) ? ldp<CG>(plane + (size_t)ix * nx + c) : (T)0;
             });
         }
         __syncthreads();
@@ -455,15 +498,22 @@ __global__ void __launch_bounds__(256) k_ypass(int nx, int ny, FFTDesc D, int TX
     }
 }
 
+template <typename T, bool INV>
+__global__ void __launch_bounds__(256) k_ypass(int nx, int ny, FFTDesc D, int TX, T *data,
+                                               const int *conv) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    ypass_body<T, INV, false>(nx, ny, D, TX, data, conv, blockIdx.x, blockIdx.y, smem_raw);
+}
+
 enum { XI_STORE = 0, XI_ACCUM = 1 };
 
 // Inverse x-pass: per CTA 2L real x-lines; writes p (FP64).
-template <typename T, int MODE>
-__global__ void __launch_bounds__(256) k_xinv(GridDev g, FFTDesc D, int L, const T *in, double *p,
-                                              const DevStats *st) {
+template <typename T, int MODE, bool CG>
+__device__ __forceinline__ void xinv_body(const GridDev &g, const FFTDesc &D, int L, const T *in,
+                                          double *p, const DevStats *st, int bx,
+                                          unsigned char *smem_raw) {
     typedef typename C2<T>::t T2;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    if (MODE == XI_ACCUM && st->converged) return;
+    if (MODE == XI_ACCUM && ldp<CG>(&st->converged)) return;
     const int n = D.n, ls = n + 1;
     T2 *tw_s = (T2 *)smem_raw;
     T2 *cs_s = tw_s + n;
@@ -471,7 +521,7 @@ __global__ void __launch_bounds__(256) k_xinv(GridDev g, FFTDesc D, int L, const
     T2 *B = A + L * ls;
     load_tables<T>(D, tw_s, cs_s);
     const int nlines = g.ny * g.nz;
-    const int line0 = blockIdx.x * 2 * L;
+    const int line0 = bx * 2 * L;
     const int M = n / 2 + 1;
     __syncthreads();
     for (int t = threadIdx.x; t < L * M; t += blockDim.x) {
@@ -479,13 +529,13 @@ __global__ void __launch_bounds__(256) k_xinv(GridDev g, FFTDesc D, int L, const
         const int la = line0 + 2 * l;
         inv_combine<T>(A + l * ls, n, m, D.kind, cs_s, [&](int ab, int ix) -> T {
             const int line = la + ab;
-            return (line < nlines) ? in[(size_t)line * n + ix] : (T)0;
+            return (line < nlines) ? ldp<CG>(in + (size_t)line * n + ix) : (T)0;
         });
     }
     __syncthreads();
     const T2 *Z = fft_lines<T, true>(A, B, L, ls, D, tw_s);
     int ef = 0;
-    if (MODE == XI_ACCUM) ef = exp_of_bits(st->fmax_bits);
+    if (MODE == XI_ACCUM) ef = exp_of_bits(ldp<CG>(&st->fmax_bits));
     for (int idx = threadIdx.x; idx < 2 * L * n; idx += blockDim.x) {
         const int r = idx / n, i = idx - r * n;
         const int line = line0 + r;
@@ -496,10 +546,17 @@ __global__ void __launch_bounds__(256) k_xinv(GridDev g, FFTDesc D, int L, const
                 if (sizeof(T) == 8) *dst = (double)v;
                 else *dst = f32_to_f64_shift((float)v, 0);
             } else {
-                *dst = *dst + f32_to_f64_shift((float)v, ef);
+                *dst = ldp<CG>(dst) + f32_to_f64_shift((float)v, ef);
             }
         }
     }
+}
+
+template <typename T, int MODE>
+__global__ void __launch_bounds__(256) k_xinv(GridDev g, FFTDesc D, int L, const T *in, double *p,
+                                              const DevStats *st) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    xinv_body<T, MODE, false>(g, D, L, in, p, st, blockIdx.x, smem_raw);
 }
 
 // Tridiagonal z-solves, one per (kx, ky) line, with factorisation tables
@@ -623,19 +680,19 @@ __device__ __forceinline__ double warp_inclusive_scan(double v, int lane) {
     return v;
 }
 
-template <typename T>
+template <typename T, bool CG>
 __device__ void singular_line_warp(const GridDev &g, T *d, size_t plane) {
     const int lane = threadIdx.x & 31;
     const int nz = g.nz;
     double s = 0.0;
-    for (int k = lane; k < nz; k += 32) s = fmaT(g.dzf[k], (double)d[(size_t)k * plane], s);
+    for (int k = lane; k < nz; k += 32) s = fmaT(g.dzf[k], (double)ldp<CG>(d + (size_t)k * plane), s);
     const double fbar = warp_sum(s) * g.inv_lz;
     double Fc = 0.0, pc = 0.0, ps = 0.0;
     for (int k0 = 0; k0 < nz; k0 += 32) {
         const int k = k0 + lane;
         double a = 0.0, h = 0.0;
         if (k < nz) {
-            a = g.dzf[k] * ((double)d[(size_t)k * plane] - fbar);
+            a = g.dzf[k] * ((double)ldp<CG>(d + (size_t)k * plane) - fbar);
             h = g.dzc[k];  // 0 at the top wall
         }
         const double F = warp_inclusive_scan(a, lane) + Fc;  // F_(k+1/2)
@@ -651,7 +708,117 @@ __device__ void singular_line_warp(const GridDev &g, T *d, size_t plane) {
     }
     const double pbar = warp_sum(ps) * g.inv_lz;
     for (int k = lane; k < nz; k += 32)
-        d[(size_t)k * plane] = (T)((double)d[(size_t)k * plane] - pbar);
+        d[(size_t)k * plane] = (T)((double)ldp<CG>(d + (size_t)k * plane) - pbar);
+}
+
+// Register-prefetch variant of thomas_lines for the persistent batch kernel:
+// THOMAS_U planes of loads (L2-only when CG) are issued ahead of each block of
+// the recurrence.
+constexpr int THOMAS_U = 8;
+
+template <typename T, int NL, bool CG>
+__device__ __forceinline__ void thomas_lines_reg(int nz, size_t plane, T *d0, T *d1, size_t ts,
+                                                 size_t tb, const T *__restrict__ mtab,
+                                                 const T *__restrict__ ibtab,
+                                                 const T *__restrict__ cup) {
+    T *d[2] = {d0, d1};
+    T prev[2];
+#pragma unroll
+    for (int l = 0; l < NL; ++l) prev[l] = ldp<CG>(d[l]);
+    int k = 1;
+    for (; k + THOMAS_U <= nz; k += THOMAS_U) {
+        T fv[NL][THOMAS_U], mv[THOMAS_U];
+#pragma unroll
+        for (int q = 0; q < THOMAS_U; ++q) {
+            mv[q] = mtab[(size_t)(k + q) * ts + tb];
+#pragma unroll
+            for (int l = 0; l < NL; ++l) fv[l][q] = ldp<CG>(d[l] + (size_t)(k + q) * plane);
+        }
+#pragma unroll
+        for (int q = 0; q < THOMAS_U; ++q)
+#pragma unroll
+            for (int l = 0; l < NL; ++l) {
+                prev[l] = fmaT(-mv[q], prev[l], fv[l][q]);
+                d[l][(size_t)(k + q) * plane] = prev[l];
+            }
+    }
+    for (; k < nz; ++k) {
+        const T m = mtab[(size_t)k * ts + tb];
+#pragma unroll
+        for (int l = 0; l < NL; ++l) {
+            prev[l] = fmaT(-m, prev[l], ldp<CG>(d[l] + (size_t)k * plane));
+            d[l][(size_t)k * plane] = prev[l];
+        }
+    }
+    const T ibt = ibtab[(size_t)(nz - 1) * ts + tb];
+#pragma unroll
+    for (int l = 0; l < NL; ++l) {
+        prev[l] = prev[l] * ibt;
+        d[l][(size_t)(nz - 1) * plane] = prev[l];
+    }
+    k = nz - 2;
+    for (; k - THOMAS_U + 1 >= 0; k -= THOMAS_U) {
+        T dv[NL][THOMAS_U], iv[THOMAS_U], cv[THOMAS_U];
+#pragma unroll
+        for (int q = 0; q < THOMAS_U; ++q) {
+            iv[q] = ibtab[(size_t)(k - q) * ts + tb];
+            cv[q] = cup[k - q];
+#pragma unroll
+            for (int l = 0; l < NL; ++l) dv[l][q] = ldp<CG>(d[l] + (size_t)(k - q) * plane);
+        }
+#pragma unroll
+        for (int q = 0; q < THOMAS_U; ++q)
+#pragma unroll
+            for (int l = 0; l < NL; ++l) {
+                prev[l] = fmaT(-cv[q], prev[l], dv[l][q]) * iv[q];
+                d[l][(size_t)(k - q) * plane] = prev[l];
+            }
+    }
+    for (; k >= 0; --k) {
+        const T ib = ibtab[(size_t)k * ts + tb], c = cup[k];
+#pragma unroll
+        for (int l = 0; l < NL; ++l) {
+            prev[l] = fmaT(-c, prev[l], ldp<CG>(d[l] + (size_t)k * plane)) * ib;
+            d[l][(size_t)k * plane] = prev[l];
+        }
+    }
+}
+
+// Lines are numbered line = t + TT*j with TT = nx/2+1 x-pairs (periodic x) or
+// nx (wall x); one virtual block covers lines line_base .. line_base +
+// blockDim - 1.  Warp 0 of the block holding line 0 first solves the singular
+// (0,0) line.  ASYNC: cp.async ring in shared memory (ring must hold
+// THOMAS_S*3*blockDim values); otherwise register prefetch.
+template <typename T, bool ASYNC, bool CG>
+__device__ __forceinline__ void thomas_body(const GridDev &g, int Ux, int Uy, const T *mtab,
+                                            const T *ibtab, const T *cup, T *data, const int *conv,
+                                            int line_base, T *ring) {
+    if (conv && ldp<CG>(conv)) return;
+    const size_t plane = (size_t)g.nx * g.ny;
+    if (line_base == 0 && threadIdx.x < 32) {
+        singular_line_warp<T, CG>(g, data, plane);  // line (0,0)
+        if (threadIdx.x == 0) return;
+    }
+    const int TT = (g.bcx == BC_PERIODIC) ? g.nx / 2 + 1 : g.nx;
+    const int line = line_base + threadIdx.x;
+    if (line >= TT * g.ny) return;
+    const int j = line / TT, t = line - j * TT;
+    int i1 = t, i2 = -1;
+    if (g.bcx == BC_PERIODIC && t > 0 && 2 * t != g.nx) i2 = g.nx - t;
+    const int ux = i1;  // periodic: i1 <= nx/2 is already the distinct index
+    const int uy = (g.bcy == BC_PERIODIC) ? min(j, g.ny - j) : j;
+    const size_t tb = (size_t)uy * Ux + ux;
+    const size_t ts = (size_t)Ux * Uy;
+    T *d1 = data + (size_t)j * g.nx + i1;
+    T *d2 = data + (size_t)j * g.nx + (i2 >= 0 ? i2 : i1);
+    const int nz = g.nz;
+    if (ASYNC) {
+        if (i2 >= 0) thomas_lines<T, 2>(nz, plane, d1, d2, ts, tb, mtab, ibtab, cup, ring);
+        else thomas_lines<T, 1>(nz, plane, d1, d1, ts, tb, mtab, ibtab, cup, ring);
+    } else {
+        if (i2 >= 0) thomas_lines_reg<T, 2, CG>(nz, plane, d1, d2, ts, tb, mtab, ibtab, cup);
+        else thomas_lines_reg<T, 1, CG>(nz, plane, d1, d1, ts, tb, mtab, ibtab, cup);
+    }
 }
 
 template <typename T>
@@ -661,34 +828,8 @@ __global__ void __launch_bounds__(THOMAS_BLOCK) k_thomas(GridDev g, int Ux, int 
                                                          const T *__restrict__ cup, T *data,
                                                          const int *conv) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    if (conv && *conv) return;
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    const int j = blockIdx.y;
-    if (blockIdx.x == 0 && j == 0 && threadIdx.x < 32) {
-        singular_line_warp<T>(g, data, (size_t)g.nx * g.ny);  // line (0,0)
-        if (t == 0) return;
-    }
-    int i1, i2 = -1;
-    if (g.bcx == BC_PERIODIC) {
-        if (t > g.nx / 2) return;
-        i1 = t;
-        if (t > 0 && 2 * t != g.nx) i2 = g.nx - t;
-    } else {
-        if (t >= g.nx) return;
-        i1 = t;
-    }
-    const size_t plane = (size_t)g.nx * g.ny;
-    T *d = data + (size_t)j * g.nx + i1;
-    const int nz = g.nz;
-    const int ux = i1;  // periodic: i1 <= nx/2 is already the distinct index
-    const int uy = (g.bcy == BC_PERIODIC) ? min(j, g.ny - j) : j;
-    const size_t tb = (size_t)uy * Ux + ux;
-    const size_t ts = (size_t)Ux * Uy;
-    T *ring = (T *)smem_raw;
-    if (i2 >= 0)
-        thomas_lines<T, 2>(nz, plane, d, data + (size_t)j * g.nx + i2, ts, tb, mtab, ibtab, cup, ring);
-    else
-        thomas_lines<T, 1>(nz, plane, d, d, ts, tb, mtab, ibtab, cup, ring);
+    thomas_body<T, true, false>(g, Ux, Uy, mtab, ibtab, cup, data, conv, blockIdx.x * THOMAS_BLOCK,
+                                (T *)smem_raw);
 }
 
 template <typename T> constexpr size_t thomas_smem() {
@@ -696,34 +837,42 @@ template <typename T> constexpr size_t thomas_smem() {
 }
 
 // u = q' - (dt/rho0) G p on non-wall faces (q' = dt q); wall faces 0.
-// 2 FP64 instructions per face.
+// 2 FP64 instructions per face.  Virtual block: 32 x 8 cells of plane z.
+template <bool CG>
+__device__ __forceinline__ void correct_body(const GridDev &g, const double *p, const double *qx,
+                                             const double *qy, const double *qz, double *u, double *v,
+                                             double *w, VB vb) {
+    const int tid = block_tid();
+    const int i = vb.x * FLUX_BX + (tid & (FLUX_BX - 1));
+    const int j = vb.y * FLUX_BY + tid / FLUX_BX;
+    const int k = vb.z;
+    if (i >= g.nx || j >= g.ny) return;
+    const size_t c = cidx(g, i, j, k);
+    const double pc = ldp<CG>(p + c);
+    double r = 0.0;
+    if (!(g.bcx == BC_NEUMANN && i == g.nx - 1)) {
+        const size_t e = (i == g.nx - 1) ? c - i : c + 1;
+        r = fmaT(-g.cgx, ldp<CG>(p + e) - pc, ldp<CG>(qx + c));
+    }
+    u[c] = r;
+    r = 0.0;
+    if (!(g.bcy == BC_NEUMANN && j == g.ny - 1)) {
+        const size_t nn = (j == g.ny - 1) ? c - (size_t)j * g.nx : c + g.nx;
+        r = fmaT(-g.cgy, ldp<CG>(p + nn) - pc, ldp<CG>(qy + c));
+    }
+    v[c] = r;
+    r = 0.0;
+    if (k < g.nz - 1) r = fmaT(-g.cgz[k], ldp<CG>(p + c + (size_t)g.nx * g.ny) - pc, ldp<CG>(qz + c));
+    w[c] = r;
+}
+
 __global__ void __launch_bounds__(256) k_correct(GridDev g, const double *__restrict__ p,
                                                  const double *__restrict__ qx,
                                                  const double *__restrict__ qy,
                                                  const double *__restrict__ qz,
                                                  double *__restrict__ u, double *__restrict__ v,
                                                  double *__restrict__ w) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const int j = blockIdx.y * blockDim.y + threadIdx.y;
-    const int k = blockIdx.z;
-    if (i >= g.nx || j >= g.ny) return;
-    const size_t c = cidx(g, i, j, k);
-    const double pc = p[c];
-    double r = 0.0;
-    if (!(g.bcx == BC_NEUMANN && i == g.nx - 1)) {
-        const size_t e = (i == g.nx - 1) ? c - i : c + 1;
-        r = fmaT(-g.cgx, p[e] - pc, qx[c]);
-    }
-    u[c] = r;
-    r = 0.0;
-    if (!(g.bcy == BC_NEUMANN && j == g.ny - 1)) {
-        const size_t nn = (j == g.ny - 1) ? c - (size_t)j * g.nx : c + g.nx;
-        r = fmaT(-g.cgy, p[nn] - pc, qy[c]);
-    }
-    v[c] = r;
-    r = 0.0;
-    if (k < g.nz - 1) r = fmaT(-g.cgz[k], p[c + (size_t)g.nx * g.ny] - pc, qz[c]);
-    w[c] = r;
+    correct_body<false>(g, p, qx, qy, qz, u, v, w, vb_of_grid());
 }
 
 // max |D u| (diagnostics).
