@@ -147,6 +147,60 @@ int fizzy_proj_set_timing(fizzy_proj_plan_t p, int enable);
 int fizzy_proj_timing(fizzy_proj_plan_t p, int idx, const char **name, double *ms, int *launches);
 
 /* ------------------------------------------------------------------------
+ * Batched projections.
+ *
+ * Many independent projections of uneven sizes, each described by its own
+ * plan (either precision), run as one persistent kernel launch replayed from
+ * a captured CUDA graph.  The launch works through a list of (instance, pass,
+ * tile) items; an item waits (bounded spin) until every tile of its instance's
+ * previous pass is done.  Results are the same as each plan's own
+ * fizzy_proj_solve (same kernel bodies, same arithmetic per tile).
+ *
+ * arrays: 7*n device pointers, for instance i at 7i..7i+6:
+ *         phi, p_n, p_nm1, u, v, w (u*, in/out), p_np1 -- fixed for the batch
+ *         (the graph is captured with them; write new inputs into the same
+ *         buffers between solves).
+ * A plan in a batch must not be solved elsewhere at the same time (it lends
+ * the batch its workspace and stats); read per-instance stats with
+ * fizzy_proj_get_stats(plans[i]) after fizzy_proj_batch_status().
+ * ------------------------------------------------------------------------ */
+typedef struct fizzy_proj_batch_s *fizzy_proj_batch_t;
+
+typedef struct fizzy_batch_tuning {
+    int ctas_per_sm; /* persistent CTAs per SM; 0 = as many as fit               */
+    int flux_planes; /* z planes per flux tile, multiple of 16; 0 = 16           */
+    int x_lines;     /* x-pass line pairs per tile (1..16); 0 = per-size default */
+    int y_cols;      /* y-pass columns per tile (even, 2..32); 0 = default       */
+    int order;       /* work-list order: 0 pass-major, 1 instance-major          */
+} fizzy_batch_tuning;
+
+/* Build the batch (work list, device descriptors) and capture its graph.
+ * tuning may be NULL (defaults).  Synchronous. */
+int fizzy_proj_batch_create(fizzy_proj_batch_t *out, int n, const fizzy_proj_plan_t *plans,
+                            double *const *arrays, const fizzy_batch_tuning *tuning,
+                            void *stream);
+
+/* Replay the batch graph on stream (asynchronous). */
+int fizzy_proj_batch_solve(fizzy_proj_batch_t b, void *stream);
+
+/* Wait for the stream and return the launch status: FIZZY_OK, or
+ * FIZZY_ERR_TIMEOUT if a dependency wait gave up (outputs then invalid). */
+int fizzy_proj_batch_status(fizzy_proj_batch_t b, void *stream);
+
+/* Time candidate tunings (reps replays each, CUDA events on stream), rebuild
+ * the batch with the fastest and return it in *chosen and its mean time in
+ * *best_ms (either may be NULL).  The candidates vary CTAs per SM, flux
+ * planes per tile, x-pass lines per tile, y-pass columns per tile and the
+ * work-list order.  Overwrites the batch outputs while timing. */
+int fizzy_proj_batch_autotune(fizzy_proj_batch_t b, int reps, fizzy_batch_tuning *chosen,
+                              double *best_ms, void *stream);
+
+/* Work items, persistent grid size and dynamic shared memory of the launch. */
+int fizzy_proj_batch_info(fizzy_proj_batch_t b, int *n_items, int *grid, size_t *smem_bytes);
+
+int fizzy_proj_batch_destroy(fizzy_proj_batch_t b);
+
+/* ------------------------------------------------------------------------
  * Allocation-free projection (FP64 mode, small grids).
  *
  * The paper has no counterpart to this entry point; it exists for callers

@@ -160,6 +160,65 @@ class Plan:
         self.close()
 
 
+class Batch:
+    """Uneven-size projections in one persistent launch under a CUDA graph
+    (fizzy_proj_batch_*).  plans: list of Plan; arrays: per instance the 7
+    float64 CUDA tensors (phi, p_n, p_nm1, u, v, w, p_out), fixed for the
+    batch's lifetime."""
+
+    def __init__(self, plans, arrays, tuning=None, stream=None):
+        n = len(plans)
+        self._plans = list(plans)
+        self._arrays = [t for inst in arrays for t in inst]  # keep tensors alive
+        if len(self._arrays) != 7 * n:
+            raise ValueError("need 7 arrays per instance")
+        hp = (ctypes.c_void_p * n)(*[p._h.value for p in plans])
+        ha = (ctypes.c_void_p * (7 * n))(*[_ptr(t).value for t in self._arrays])
+        tun = None
+        if tuning is not None:
+            tun = _abi.Tuning(**tuning)
+        h = ctypes.c_void_p()
+        rc = _abi.lib().fizzy_proj_batch_create(ctypes.byref(h), n, hp, ha,
+                                                ctypes.byref(tun) if tun else None,
+                                                _stream_handle(stream))
+        if rc != 0:
+            raise FizzyError(rc)
+        self._h = h
+
+    def solve(self, stream=None):
+        rc = _abi.lib().fizzy_proj_batch_solve(self._h, _stream_handle(stream))
+        if rc != 0:
+            raise FizzyError(rc)
+
+    def status(self, stream=None) -> int:
+        return int(_abi.lib().fizzy_proj_batch_status(self._h, _stream_handle(stream)))
+
+    def autotune(self, reps=3, stream=None):
+        t = _abi.Tuning()
+        ms = ctypes.c_double()
+        rc = _abi.lib().fizzy_proj_batch_autotune(self._h, int(reps), ctypes.byref(t),
+                                                  ctypes.byref(ms), _stream_handle(stream))
+        if rc != 0:
+            raise FizzyError(rc)
+        return t.as_dict(), ms.value
+
+    def info(self):
+        n, g, sm = ctypes.c_int(), ctypes.c_int(), ctypes.c_size_t()
+        _abi.lib().fizzy_proj_batch_info(self._h, ctypes.byref(n), ctypes.byref(g), ctypes.byref(sm))
+        return {"items": n.value, "grid": g.value, "smem": sm.value}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _abi.lib().fizzy_proj_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def solve_noalloc(phi, pn, pnm1, u, v, w, p_out, stream=None, **desc):
     """Allocation-free FP64 projection for small grids (fizzy_proj_solve_noalloc).
 

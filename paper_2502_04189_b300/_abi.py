@@ -15,7 +15,9 @@ ERRORS = {-1: "invalid argument", -2: "unsupported size", -3: "out of device mem
 EXPORTED = ("fizzy_proj_plan", "fizzy_proj_workspace_bytes", "fizzy_proj_solve",
             "fizzy_proj_get_stats", "fizzy_proj_solve_host", "fizzy_proj_destroy",
             "fizzy_proj_errstr", "fizzy_proj_last_error", "fizzy_proj_launches_per_solve",
-            "fizzy_proj_set_timing", "fizzy_proj_timing", "fizzy_proj_solve_noalloc")
+            "fizzy_proj_set_timing", "fizzy_proj_timing", "fizzy_proj_solve_noalloc",
+            "fizzy_proj_batch_create", "fizzy_proj_batch_solve", "fizzy_proj_batch_status",
+            "fizzy_proj_batch_autotune", "fizzy_proj_batch_info", "fizzy_proj_batch_destroy")
 NOALLOC_MAX_CELLS = 262144
 
 
@@ -28,6 +30,14 @@ class Desc(ctypes.Structure):
                 ("precision", ctypes.c_int), ("tol", ctypes.c_double),
                 ("max_refine", ctypes.c_int), ("div_tol", ctypes.c_double),
                 ("flags", ctypes.c_uint)]
+
+
+class Tuning(ctypes.Structure):
+    _fields_ = [("ctas_per_sm", ctypes.c_int), ("flux_planes", ctypes.c_int),
+                ("x_lines", ctypes.c_int), ("y_cols", ctypes.c_int), ("order", ctypes.c_int)]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
 
 
 class Stats(ctypes.Structure):
@@ -77,5 +87,20 @@ def lib():
         L.fizzy_proj_timing.restype = ctypes.c_int
         L.fizzy_proj_solve_noalloc.argtypes = [ctypes.POINTER(Desc)] + [vp] * 7 + [vp]
         L.fizzy_proj_solve_noalloc.restype = ctypes.c_int
+        L.fizzy_proj_batch_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int, ctypes.POINTER(vp),
+                                              ctypes.POINTER(vp), ctypes.POINTER(Tuning), vp]
+        L.fizzy_proj_batch_create.restype = ctypes.c_int
+        L.fizzy_proj_batch_solve.argtypes = [vp, vp]
+        L.fizzy_proj_batch_solve.restype = ctypes.c_int
+        L.fizzy_proj_batch_status.argtypes = [vp, vp]
+        L.fizzy_proj_batch_status.restype = ctypes.c_int
+        L.fizzy_proj_batch_autotune.argtypes = [vp, ctypes.c_int, ctypes.POINTER(Tuning),
+                                                ctypes.POINTER(ctypes.c_double), vp]
+        L.fizzy_proj_batch_autotune.restype = ctypes.c_int
+        L.fizzy_proj_batch_info.argtypes = [vp, ctypes.POINTER(ctypes.c_int),
+                                            ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_size_t)]
+        L.fizzy_proj_batch_info.restype = ctypes.c_int
+        L.fizzy_proj_batch_destroy.argtypes = [vp]
+        L.fizzy_proj_batch_destroy.restype = ctypes.c_int
         _lib = L
     return _lib

@@ -18,6 +18,7 @@ FLAGS = ["-O3", "-std=c++17", "-gencode", "arch=compute_103a,code=sm_103a", "-li
 def sources():
     return sorted(glob.glob(os.path.join(HERE, "csrc", "*.cu")) +
                   glob.glob(os.path.join(HERE, "csrc", "*.cuh")) +
+                  glob.glob(os.path.join(HERE, "csrc", "*.inc")) +
                   glob.glob(os.path.join(ROOT, "include", "*.h")))
 
 

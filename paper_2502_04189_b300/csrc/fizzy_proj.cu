@@ -690,6 +690,11 @@ int fizzy_proj_solve_host(fizzy_proj_plan_t p, const double *phi, const double *
 }  // extern "C"
 
 // ===========================================================================
+// Batched projections (fizzy_proj_batch_*)
+// ===========================================================================
+#include "fizzy_batch.inc"
+
+// ===========================================================================
 // Allocation-free projection (fizzy_proj_solve_noalloc): the FP64 kernel
 // sequence of fizzy_proj_solve on tables and workspace kept in one static
 // device array, for callers that cannot allocate device memory.

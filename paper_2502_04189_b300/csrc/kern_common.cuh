@@ -19,6 +19,13 @@ template <> struct C2<float> { typedef float2 t; };
 __device__ __forceinline__ double fmaT(double a, double b, double c) { return __fma_rn(a, b, c); }
 __device__ __forceinline__ float fmaT(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 
+// Products that must not be fused into a following add: the rounding of every
+// kernel body then does not depend on the context it is compiled in (a body
+// gives bit-identical results as a stand-alone kernel and inside the
+// persistent batch kernel).
+__device__ __forceinline__ double mulT(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float mulT(float a, float b) { return __fmul_rn(a, b); }
+
 __device__ __forceinline__ double2 mk2(double x, double y) { return make_double2(x, y); }
 __device__ __forceinline__ float2 mk2(float x, float y) { return make_float2(x, y); }
 

@@ -53,11 +53,11 @@ template <typename T, bool INV>
 __device__ __forceinline__ void twiddle(typename C2<T>::t &x, typename C2<T>::t w) {
     T r, i;
     if (!INV) {
-        r = fmaT(x.x, w.x, -x.y * w.y);
-        i = fmaT(x.x, w.y, x.y * w.x);
+        r = fmaT(x.x, w.x, -mulT(x.y, w.y));
+        i = fmaT(x.x, w.y, mulT(x.y, w.x));
     } else {
-        r = fmaT(x.x, w.x, x.y * w.y);
-        i = fmaT(x.y, w.x, -x.x * w.y);
+        r = fmaT(x.x, w.x, mulT(x.y, w.y));
+        i = fmaT(x.y, w.x, -mulT(x.x, w.y));
     }
     x.x = r;
     x.y = i;
@@ -112,14 +112,14 @@ __device__ __forceinline__ void stockham_stage(const typename C2<T>::t *__restri
             const T h = (T)0.86602540378443864676;  // sqrt(3)/2
             const T sr = x1.x + x2.x, si = x1.y + x2.y;
             const T mr = fmaT((T)-0.5, sr, x0.x), mi = fmaT((T)-0.5, si, x0.y);
-            const T dr = (x1.x - x2.x) * h, di = (x1.y - x2.y) * h;
+            const T dx = x1.x - x2.x, dy = x1.y - x2.y;
             out[0] = mk2(x0.x + sr, x0.y + si);
-            if (!INV) {  // t3 = -i h d
-                out[Ns] = mk2(mr + di, mi - dr);
-                out[2 * Ns] = mk2(mr - di, mi + dr);
+            if (!INV) {  // y1 = m - i h d, y2 = m + i h d
+                out[Ns] = mk2(fmaT(h, dy, mr), fmaT(-h, dx, mi));
+                out[2 * Ns] = mk2(fmaT(-h, dy, mr), fmaT(h, dx, mi));
             } else {
-                out[Ns] = mk2(mr - di, mi + dr);
-                out[2 * Ns] = mk2(mr + di, mi - dr);
+                out[Ns] = mk2(fmaT(-h, dy, mr), fmaT(h, dx, mi));
+                out[2 * Ns] = mk2(fmaT(h, dy, mr), fmaT(-h, dx, mi));
             }
         }
     }
@@ -183,10 +183,10 @@ __device__ __forceinline__ void fwd_separate(const typename C2<T>::t *Z, int n, 
         out(1, n - m, vbi);
     } else {  // X[m] = Re(w V), X[n-m] = -Im(w V), w = c - i s
         const T c = cs[m].x, s = cs[m].y;
-        out(0, m, fmaT(c, var, s * vai));
-        out(0, n - m, fmaT(s, var, -c * vai));
-        out(1, m, fmaT(c, vbr, s * vbi));
-        out(1, n - m, fmaT(s, vbr, -c * vbi));
+        out(0, m, fmaT(c, var, mulT(s, vai)));
+        out(0, n - m, fmaT(s, var, -mulT(c, vai)));
+        out(1, m, fmaT(c, vbr, mulT(s, vbi)));
+        out(1, n - m, fmaT(s, vbr, -mulT(c, vbi)));
     }
 }
 
@@ -213,10 +213,10 @@ __device__ __forceinline__ void inv_combine(typename C2<T>::t *Z, int n, int m, 
     } else {  // V[m] = (c + i s)(X[m] - i X[n-m])
         const T c = cs[m].x, s = cs[m].y;
         const T xa = get(0, m), ya = get(0, n - m), xb = get(1, m), yb = get(1, n - m);
-        ar = fmaT(c, xa, s * ya);
-        ai = fmaT(s, xa, -c * ya);
-        br = fmaT(c, xb, s * yb);
-        bi = fmaT(s, xb, -c * yb);
+        ar = fmaT(c, xa, mulT(s, ya));
+        ai = fmaT(s, xa, -mulT(c, ya));
+        br = fmaT(c, xb, mulT(s, yb));
+        bi = fmaT(s, xb, -mulT(c, yb));
     }
     Z[m] = mk2(ar - bi, ai + br);
     Z[n - m] = mk2(ar + bi, br - ai);

@@ -124,7 +124,7 @@ __device__ __forceinline__ double face_flux(const GridDev &g, double phi_a, doub
     const double k0 = f32_to_f64_shift(tf * rf, 0);
     const double r0 = pos_f32_to_f64(rf);
     const double kappa = fmaT(r0, fmaT(-s, k0, t), k0);
-    return fmaT(dtch, kappa * (ph_b - ph_a), ustar);
+    return fmaT(dtch, mulT(kappa, ph_b - ph_a), ustar);
 }
 
 constexpr int FLUX_BX = 32, FLUX_BY = 8;
@@ -250,7 +250,7 @@ __device__ __forceinline__ double div_q(const GridDev &g, int i, int j, int k, d
                               : (g.bcy == BC_PERIODIC ? ldp<CG>(qy + c + (size_t)(g.ny - 1) * g.nx) : 0.0);
     const double qt = ldp<CG>(qz + c);
     const double qb = (k > 0) ? ldp<CG>(qz + c - (size_t)g.nx * g.ny) : 0.0;
-    return fmaT(cx, qe - qw, fmaT(cy, qn - qs, cz * (qt - qb)));
+    return fmaT(cx, qe - qw, fmaT(cy, qn - qs, mulT(cz, qt - qb)));
 }
 
 // L_h p at one cell in flux (difference) form: each face difference is
@@ -272,7 +272,7 @@ __device__ __forceinline__ double lap(const GridDev &g, int i, int j, int k, con
     const size_t pl = (size_t)g.nx * g.ny;
     const double pt = (k < g.nz - 1) ? ldp<CG>(p + c + pl) : pc;
     const double pb = (k > 0) ? ldp<CG>(p + c - pl) : pc;
-    double acc = ((pe - pc) - (pc - pw)) * g.idx2;
+    double acc = mulT((pe - pc) - (pc - pw), g.idx2);
     acc = fmaT((pn_ - pc) - (pc - ps), g.idy2, acc);
     acc = fmaT(g.lzc[k], pt - pc, acc);
     return fmaT(-g.lza[k], pc - pb, acc);
@@ -624,7 +624,7 @@ __device__ __forceinline__ void thomas_lines(int nz, size_t plane, T *d0, T *d1,
     const T ibt = ibtab[(size_t)(nz - 1) * ts + tb];
 #pragma unroll
     for (int l = 0; l < NL; ++l) {
-        prev[l] = prev[l] * ibt;
+        prev[l] = mulT(prev[l], ibt);
         d[l][(size_t)(nz - 1) * plane] = prev[l];
     }
     // plane k (descending from nz-2) lives in stage (nz-2-k) % S
@@ -646,7 +646,7 @@ __device__ __forceinline__ void thomas_lines(int nz, size_t plane, T *d0, T *d1,
         const T c = cup[k];
 #pragma unroll
         for (int l = 0; l < NL; ++l) {
-            prev[l] = fmaT(-c, prev[l], *slot(st, l)) * ib;
+            prev[l] = mulT(fmaT(-c, prev[l], *slot(st, l)), ib);
             d[l][(size_t)k * plane] = prev[l];
         }
         const int kn = k - THOMAS_S;
@@ -686,17 +686,17 @@ __device__ void singular_line_warp(const GridDev &g, T *d, size_t plane) {
     const int nz = g.nz;
     double s = 0.0;
     for (int k = lane; k < nz; k += 32) s = fmaT(g.dzf[k], (double)ldp<CG>(d + (size_t)k * plane), s);
-    const double fbar = warp_sum(s) * g.inv_lz;
+    const double fbar = mulT(warp_sum(s), g.inv_lz);
     double Fc = 0.0, pc = 0.0, ps = 0.0;
     for (int k0 = 0; k0 < nz; k0 += 32) {
         const int k = k0 + lane;
         double a = 0.0, h = 0.0;
         if (k < nz) {
-            a = g.dzf[k] * ((double)ldp<CG>(d + (size_t)k * plane) - fbar);
+            a = mulT(g.dzf[k], (double)ldp<CG>(d + (size_t)k * plane) - fbar);
             h = g.dzc[k];  // 0 at the top wall
         }
         const double F = warp_inclusive_scan(a, lane) + Fc;  // F_(k+1/2)
-        const double inc = h * F;                             // p_(k+1) - p_k
+        const double inc = mulT(h, F);                        // p_(k+1) - p_k
         const double sc = warp_inclusive_scan(inc, lane);
         const double pk = pc + (sc - inc);                    // exclusive: p_k
         if (k < nz) {
@@ -706,17 +706,15 @@ __device__ void singular_line_warp(const GridDev &g, T *d, size_t plane) {
         Fc = __shfl_sync(0xffffffffu, F, 31);
         pc += __shfl_sync(0xffffffffu, sc, 31);
     }
-    const double pbar = warp_sum(ps) * g.inv_lz;
+    const double pbar = mulT(warp_sum(ps), g.inv_lz);
     for (int k = lane; k < nz; k += 32)
         d[(size_t)k * plane] = (T)((double)ldp<CG>(d + (size_t)k * plane) - pbar);
 }
 
 // Register-prefetch variant of thomas_lines for the persistent batch kernel:
 // THOMAS_U planes of loads (L2-only when CG) are issued ahead of each block of
-// the recurrence.
-constexpr int THOMAS_U = 8;
-
-template <typename T, int NL, bool CG>
+// the recurrence (4 keeps the batch kernel within 80 registers).
+template <typename T, int NL, bool CG, int THOMAS_U>
 __device__ __forceinline__ void thomas_lines_reg(int nz, size_t plane, T *d0, T *d1, size_t ts,
                                                  size_t tb, const T *__restrict__ mtab,
                                                  const T *__restrict__ ibtab,
@@ -753,7 +751,7 @@ __device__ __forceinline__ void thomas_lines_reg(int nz, size_t plane, T *d0, T 
     const T ibt = ibtab[(size_t)(nz - 1) * ts + tb];
 #pragma unroll
     for (int l = 0; l < NL; ++l) {
-        prev[l] = prev[l] * ibt;
+        prev[l] = mulT(prev[l], ibt);
         d[l][(size_t)(nz - 1) * plane] = prev[l];
     }
     k = nz - 2;
@@ -770,7 +768,7 @@ __device__ __forceinline__ void thomas_lines_reg(int nz, size_t plane, T *d0, T 
         for (int q = 0; q < THOMAS_U; ++q)
 #pragma unroll
             for (int l = 0; l < NL; ++l) {
-                prev[l] = fmaT(-cv[q], prev[l], dv[l][q]) * iv[q];
+                prev[l] = mulT(fmaT(-cv[q], prev[l], dv[l][q]), iv[q]);
                 d[l][(size_t)(k - q) * plane] = prev[l];
             }
     }
@@ -778,7 +776,7 @@ __device__ __forceinline__ void thomas_lines_reg(int nz, size_t plane, T *d0, T 
         const T ib = ibtab[(size_t)k * ts + tb], c = cup[k];
 #pragma unroll
         for (int l = 0; l < NL; ++l) {
-            prev[l] = fmaT(-c, prev[l], ldp<CG>(d[l] + (size_t)k * plane)) * ib;
+            prev[l] = mulT(fmaT(-c, prev[l], ldp<CG>(d[l] + (size_t)k * plane)), ib);
             d[l][(size_t)k * plane] = prev[l];
         }
     }
@@ -816,8 +814,8 @@ __device__ __forceinline__ void thomas_body(const GridDev &g, int Ux, int Uy, co
         if (i2 >= 0) thomas_lines<T, 2>(nz, plane, d1, d2, ts, tb, mtab, ibtab, cup, ring);
         else thomas_lines<T, 1>(nz, plane, d1, d1, ts, tb, mtab, ibtab, cup, ring);
     } else {
-        if (i2 >= 0) thomas_lines_reg<T, 2, CG>(nz, plane, d1, d2, ts, tb, mtab, ibtab, cup);
-        else thomas_lines_reg<T, 1, CG>(nz, plane, d1, d1, ts, tb, mtab, ibtab, cup);
+        if (i2 >= 0) thomas_lines_reg<T, 2, CG, 4>(nz, plane, d1, d2, ts, tb, mtab, ibtab, cup);
+        else thomas_lines_reg<T, 1, CG, 4>(nz, plane, d1, d1, ts, tb, mtab, ibtab, cup);
     }
 }
 

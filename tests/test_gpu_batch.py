@@ -1,0 +1,102 @@
+"""Batched projections in one persistent launch (needs a B300).
+
+Each instance solved inside the batch must equal the same plan solved alone
+(the same kernel bodies run per tile), and match the FP64 oracle within the
+mixed-mode tolerance.  The instances are drawn with the uneven-batch recipe
+(sizes 32-192, periodic or wall x/y, 1-20 drops, density ratio 10-1000).
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+import paper_2502_04189_b300 as F
+from paper_2502_04189_b300 import inputs as I
+
+from gpu_util import compare, to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+def small_batch_specs(k=6):
+    specs = I.batch_specs(64)
+    specs.sort(key=lambda s: s.nx * s.ny * s.nz)
+    return specs[:k - 1] + [specs[20]]  # the smallest ones plus one mid-size
+
+
+def run_alone(case, precision):
+    import torch
+    plan = F.Plan.for_case(case, precision=precision)
+    u, v, w = to_dev(case.u), to_dev(case.v), to_dev(case.w)
+    p = torch.empty_like(u)
+    plan.solve(to_dev(case.phi), to_dev(case.pn), to_dev(case.pnm1), u, v, w, p)
+    torch.cuda.synchronize()
+    st = plan.stats()
+    plan.close()
+    return dict(p=p.cpu().numpy(), u=u.cpu().numpy(), v=v.cpu().numpy(), w=w.cpu().numpy(), stats=st)
+
+
+@pytest.mark.parametrize("precision", [F.MIXED, F.FP64], ids=["mixed", "fp64"])
+def test_batch_equals_alone(cuda_ok, precision):
+    import torch
+    cases = [I.make_case(s) for s in small_batch_specs()]
+    alone = [run_alone(c, precision) for c in cases]
+    plans, arrays = [], []
+    for c in cases:
+        plans.append(F.Plan.for_case(c, precision=precision))
+        arrays.append((to_dev(c.phi), to_dev(c.pn), to_dev(c.pnm1), to_dev(c.u), to_dev(c.v),
+                       to_dev(c.w), torch.empty(c.shape, dtype=torch.float64, device="cuda")))
+    batch = F.Batch(plans, arrays)
+    info = batch.info()
+    assert info["items"] > len(cases) and info["grid"] >= 1
+    for rep in range(2):  # replay the graph twice: same answer
+        for c, arr in zip(cases, arrays):
+            arr[3].copy_(to_dev(c.u))
+            arr[4].copy_(to_dev(c.v))
+            arr[5].copy_(to_dev(c.w))
+        batch.solve()
+        assert batch.status() == 0
+        for c, arr, a, plan in zip(cases, arrays, alone, plans):
+            got = dict(p=arr[6].cpu().numpy(), u=arr[3].cpu().numpy(), v=arr[4].cpu().numpy(),
+                       w=arr[5].cpu().numpy())
+            for k in ("p", "u", "v", "w"):
+                assert np.array_equal(got[k], a[k]), (c.spec, k)
+            st = plan.stats()
+            assert st["converged"] == 1
+            assert st["iterations"] == a["stats"]["iterations"]
+    # the largest instance against the oracle
+    c = cases[-1]
+    ref = O.project_case(c)
+    got = dict(p=arrays[-1][6].cpu().numpy(), u=arrays[-1][3].cpu().numpy(),
+               v=arrays[-1][4].cpu().numpy(), w=arrays[-1][5].cpu().numpy())
+    ep, eu = compare(c, got, ref)
+    tol = 1e-9 if precision == F.MIXED else 1e-12
+    assert ep <= tol and eu <= tol, (ep, eu)
+    batch.close()
+    for p in plans:
+        p.close()
+
+
+def test_batch_autotune_keeps_results(cuda_ok):
+    import torch
+    cases = [I.make_case(s) for s in small_batch_specs(4)]
+    plans, arrays = [], []
+    for c in cases:
+        plans.append(F.Plan.for_case(c, precision=F.MIXED))
+        arrays.append((to_dev(c.phi), to_dev(c.pn), to_dev(c.pnm1), to_dev(c.u), to_dev(c.v),
+                       to_dev(c.w), torch.empty(c.shape, dtype=torch.float64, device="cuda")))
+    batch = F.Batch(plans, arrays)
+    tuning, ms = batch.autotune(reps=2)
+    assert ms > 0 and tuning["flux_planes"] in (16, 32)
+    for c, arr in zip(cases, arrays):
+        arr[3].copy_(to_dev(c.u))
+        arr[4].copy_(to_dev(c.v))
+        arr[5].copy_(to_dev(c.w))
+    batch.solve()
+    assert batch.status() == 0
+    for c, arr in zip(cases, arrays):
+        a = run_alone(c, F.MIXED)
+        assert np.array_equal(arr[6].cpu().numpy(), a["p"])
+        assert np.array_equal(arr[3].cpu().numpy(), a["u"])
+    batch.close()
+    for p in plans:
+        p.close()
