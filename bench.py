@@ -411,6 +411,51 @@ def run_batch(args):
     return 0
 
 
+def run_serve(args):
+    """Serving: Poisson arrivals (seeded, mean 2000 req/s) of requests with
+    nx, ny in {64,...,384}, nz in [64, 384], 30 % tanh-stretched z, periodic
+    or wall x/y, density ratio 10-1000, mixed precision refined to 1e-10;
+    admission by a 120 GB HBM budget with plans cached on the device, 100 ms
+    admission deadline.  Inputs are periodic crops of a device-resident
+    256^3 bubble template."""
+    import torch
+    import paper_2502_04189_b300 as F
+    import paper_2502_04189_b300.serve as S
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    n = args.serve_requests
+    arrivals, specs = I.serve_specs(n)
+    tmpl = I.make_case(I.bubbles256_spec())
+    fields = S.TemplateFields(tmpl)
+    reqs = S.requests_from_specs(arrivals, specs, F.MIXED)
+    server = F.Server(120 * (1 << 30), slots=args.serve_slots)
+
+    def fill(r, views, stream):
+        fields.fill(views, r.desc, r.offset, stream)
+
+    # warm-up on a few requests (plan-building code paths, pool growth)
+    S.run(server, [S.Request(i, 0.0, r.desc, r.offset) for i, r in enumerate(reqs[:4])], fill,
+          deadline=60.0)
+    torch.cuda.synchronize()
+    clocks = ClockSampler()
+    clocks.start()
+    out, summ = S.run(server, reqs, fill, deadline=0.1)
+    clk = clocks.stop()
+    info = server.info()
+    server.close()
+    if rank == 0:
+        line = {"metric": METRIC, "value": summ["throughput_pts_s"], "unit": "pts/s",
+                "n_gpus": world, "steps": n, "warmup": 4, "ms_per_step": summ["mean_ms"],
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32+f64", "data": "synthetic",
+                "config": {"workload": "serve", "arrival_rate_per_s": 2000, "requests": n,
+                           "budget_gb": 120, "slots": args.serve_slots, "deadline_ms": 100,
+                           "precision": "mixed", "tol": 1e-10},
+                "serving": summ, "server": info, "clocks": clk}
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -418,7 +463,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="fizzy", choices=["fizzy", "reference"])
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
-    ap.add_argument("--workload", default="bubbles256", choices=list(WORKLOADS) + ["batch64"])
+    ap.add_argument("--workload", default="bubbles256", choices=list(WORKLOADS) + ["batch64", "serve"])
+    ap.add_argument("--serve-requests", type=int, default=4000)
+    ap.add_argument("--serve-slots", type=int, default=8)
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
@@ -426,6 +473,8 @@ def main():
         return run_reference(args)
     if args.workload == "batch64":
         return run_batch(args)
+    if args.workload == "serve":
+        return run_serve(args)
     return run_fizzy(args)
 
 

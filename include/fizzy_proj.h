@@ -62,7 +62,10 @@ enum {
 };
 
 /* flags */
-#define FIZZY_FLAG_CHECK 1u /* also compute u_rms, max|D u| and (FP64 mode) relres into the stats */
+#define FIZZY_FLAG_CHECK 1u       /* also compute u_rms, max|D u| and (FP64 mode) relres into the stats */
+#define FIZZY_FLAG_ASYNC_ALLOC 2u /* allocate the plan's device memory stream-ordered (cudaMallocAsync  */
+                                  /* from the device's default pool) on the plan's stream, and free it  */
+                                  /* the same way in fizzy_proj_destroy (no device synchronisation)     */
 
 /* Maximum x/y extent of one transform line. */
 #define FIZZY_MAX_N 1024
@@ -97,10 +100,14 @@ typedef struct fizzy_proj_stats {
 
 typedef struct fizzy_proj_plan_s *fizzy_proj_plan_t;
 
-/* Build a plan: validates the descriptor, builds the eigenvalue, twiddle and
- * z-factorisation tables on the host and allocates all device tables and the
- * workspace (fizzy_proj_workspace_bytes()).  Grid, densities, dt and precision
- * are fixed per plan.  Synchronous.  On failure *out is NULL. */
+/* Build a plan: validates the descriptor, builds the eigenvalue and twiddle
+ * tables on the host and the z-factorisation tables on the device, and
+ * allocates all device tables and the workspace (fizzy_proj_workspace_bytes()).
+ * Grid and precision are fixed per plan; densities and dt can be rebound with
+ * fizzy_proj_set_physics.  Synchronous, except with FIZZY_FLAG_ASYNC_ALLOC:
+ * then the plan is ready for work queued after it on the same stream (use it
+ * on another stream only after that stream's work has completed).  On
+ * failure *out is NULL. */
 int fizzy_proj_plan(fizzy_proj_plan_t *out, const fizzy_proj_desc *d, void *stream);
 
 /* Device bytes a plan for d would allocate (tables + workspace), 0 if d is invalid. */
@@ -116,6 +123,13 @@ size_t fizzy_proj_workspace_bytes(const fizzy_proj_desc *d);
 int fizzy_proj_solve(fizzy_proj_plan_t p, const double *phi, const double *p_n, const double *p_nm1,
                      double *u, double *v, double *w, double *p_np1, fizzy_proj_stats *st,
                      void *stream);
+
+/* Rebind the densities and time step of a plan (the grid, its transforms and
+ * z-factorisation tables do not depend on them).  Updates four per-plane
+ * tables by an asynchronous copy on stream; solves issued after it on the
+ * same stream use the new values.  Returns FIZZY_ERR_INVALID for rho <= 0 or
+ * dt <= 0. */
+int fizzy_proj_set_physics(fizzy_proj_plan_t p, double rho_l, double rho_g, double dt, void *stream);
 
 /* Read the stats of the last solve issued on p (synchronises stream). */
 int fizzy_proj_get_stats(fizzy_proj_plan_t p, fizzy_proj_stats *st, void *stream);
@@ -199,6 +213,60 @@ int fizzy_proj_batch_autotune(fizzy_proj_batch_t b, int reps, fizzy_batch_tuning
 int fizzy_proj_batch_info(fizzy_proj_batch_t b, int *n_items, int *grid, size_t *smem_bytes);
 
 int fizzy_proj_batch_destroy(fizzy_proj_batch_t b);
+
+/* ------------------------------------------------------------------------
+ * Serving runtime: continuous admission of projection requests.
+ *
+ * A server owns up to max_slots request slots, each with its own CUDA stream,
+ * so requests admitted while others run overlap on the device.  Plans are
+ * cached on the device by geometry (extents, spacings, z faces, boundary
+ * types, precision and refinement settings) and rebound to each request's
+ * densities and dt with fizzy_proj_set_physics, so requests of a geometry
+ * already seen start without building tables.  Device memory of plans
+ * (cached or in use) plus the seven arrays of every occupied slot is kept
+ * within hbm_budget bytes: admission evicts least-recently-used idle plans
+ * and otherwise refuses.  All device memory is stream-ordered
+ * (cudaMallocAsync from the device's default pool, whose release threshold
+ * the server raises to its budget), so admission and release never
+ * synchronise the device.
+ *
+ * Typical use: fizzy_serve_admit -> fill the slot's input arrays on the
+ * slot's stream -> fizzy_serve_launch -> fizzy_serve_poll until it reports
+ * the slot -> read outputs -> fizzy_serve_release.
+ * ------------------------------------------------------------------------ */
+typedef struct fizzy_serve_s *fizzy_serve_t;
+
+#define FIZZY_ERR_BUSY (-7) /* fizzy_serve_admit: no free slot right now */
+
+int fizzy_serve_create(fizzy_serve_t *out, size_t hbm_budget, int max_slots);
+
+/* Admit one request.  On FIZZY_OK, *slot is its slot and arrays[0..6] are
+ * device arrays of d's shape: phi, p_n, p_nm1, u, v, w (u* in, u out), p_np1,
+ * owned by the server until release.  FIZZY_ERR_BUSY: every slot is taken;
+ * FIZZY_ERR_NOMEM: it does not fit the budget now.  Neither changes state. */
+int fizzy_serve_admit(fizzy_serve_t s, const fizzy_proj_desc *d, int *slot, double **arrays);
+
+/* The slot's stream (fill the inputs on it before launch). */
+int fizzy_serve_stream(fizzy_serve_t s, int slot, void **stream);
+
+/* Queue the projection of an admitted slot on its stream. */
+int fizzy_serve_launch(fizzy_serve_t s, int slot);
+
+/* Report up to max launched slots whose projection has finished (without
+ * blocking); returns how many were written to slots[]. */
+int fizzy_serve_poll(fizzy_serve_t s, int *slots, int max);
+
+/* Stats of a finished slot's projection. */
+int fizzy_serve_stats(fizzy_serve_t s, int slot, fizzy_proj_stats *st);
+
+/* Return the slot (its arrays go back to the pool, its plan to the cache). */
+int fizzy_serve_release(fizzy_serve_t s, int slot);
+
+/* Budget in use, cached plans, plans built so far, slots occupied. */
+int fizzy_serve_info(fizzy_serve_t s, size_t *bytes_used, int *plans_cached, int *plans_built,
+                     int *slots_busy);
+
+int fizzy_serve_destroy(fizzy_serve_t s);
 
 /* ------------------------------------------------------------------------
  * Allocation-free projection (FP64 mode, small grids).

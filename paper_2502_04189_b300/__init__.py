@@ -139,6 +139,10 @@ class Plan:
                 out[name.value.decode()] = (ms.value, cnt.value)
         return out
 
+    def set_physics(self, rho_l, rho_g, dt, stream=None):
+        self._check(_abi.lib().fizzy_proj_set_physics(self._h, float(rho_l), float(rho_g), float(dt),
+                                                      _stream_handle(stream)))
+
     def launches_per_solve(self) -> int:
         return int(_abi.lib().fizzy_proj_launches_per_solve(self._h))
 
@@ -210,6 +214,92 @@ class Batch:
     def close(self):
         if getattr(self, "_h", None):
             _abi.lib().fizzy_proj_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class _DevArray:
+    """__cuda_array_interface__ over a raw device pointer (no ownership)."""
+
+    def __init__(self, ptr, shape):
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": "<f8",
+                                         "data": (int(ptr), False), "version": 3, "strides": None}
+
+
+def device_view(ptr, shape):
+    """A float64 CUDA tensor viewing server-owned memory (valid until release)."""
+    import torch
+    return torch.as_tensor(_DevArray(ptr, shape), device="cuda")
+
+
+class Server:
+    """Serving runtime (fizzy_serve_*): request slots on their own streams, a
+    device plan cache keyed by geometry, HBM-budget admission."""
+
+    def __init__(self, hbm_budget_bytes, slots=8):
+        h = ctypes.c_void_p()
+        rc = _abi.lib().fizzy_serve_create(ctypes.byref(h), int(hbm_budget_bytes), int(slots))
+        if rc != 0:
+            raise FizzyError(rc)
+        self._h = h
+        self.slots = int(slots)
+
+    def admit(self, **desc):
+        """Returns (rc, slot, [7 device pointers]); rc 0 admitted, -7 busy, -3 over budget."""
+        d, keep = make_desc(**desc)
+        slot = ctypes.c_int(-1)
+        ptrs = (ctypes.c_void_p * 7)()
+        rc = _abi.lib().fizzy_serve_admit(self._h, ctypes.byref(d), ctypes.byref(slot), ptrs)
+        del keep
+        if rc not in (0, -3, -7):
+            raise FizzyError(rc)
+        return rc, slot.value, [ptrs[i] for i in range(7)]
+
+    def stream(self, slot):
+        import torch
+        st = ctypes.c_void_p()
+        _abi.lib().fizzy_serve_stream(self._h, int(slot), ctypes.byref(st))
+        return torch.cuda.ExternalStream(st.value)
+
+    def launch(self, slot):
+        rc = _abi.lib().fizzy_serve_launch(self._h, int(slot))
+        if rc != 0:
+            raise FizzyError(rc)
+
+    def poll(self):
+        buf = (ctypes.c_int * self.slots)()
+        n = _abi.lib().fizzy_serve_poll(self._h, buf, self.slots)
+        if n < 0:
+            raise FizzyError(n)
+        return [buf[i] for i in range(n)]
+
+    def stats(self, slot):
+        st = Stats()
+        rc = _abi.lib().fizzy_serve_stats(self._h, int(slot), ctypes.byref(st))
+        if rc not in (0, -5):
+            raise FizzyError(rc)
+        return st.as_dict()
+
+    def release(self, slot):
+        rc = _abi.lib().fizzy_serve_release(self._h, int(slot))
+        if rc != 0:
+            raise FizzyError(rc)
+
+    def info(self):
+        used, cached, built, busy = ctypes.c_size_t(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _abi.lib().fizzy_serve_info(self._h, ctypes.byref(used), ctypes.byref(cached),
+                                    ctypes.byref(built), ctypes.byref(busy))
+        return {"bytes_used": used.value, "plans_cached": cached.value, "plans_built": built.value,
+                "slots_busy": busy.value}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _abi.lib().fizzy_serve_destroy(self._h)
             self._h = None
 
     def __del__(self):

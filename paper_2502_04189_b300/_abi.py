@@ -17,7 +17,11 @@ EXPORTED = ("fizzy_proj_plan", "fizzy_proj_workspace_bytes", "fizzy_proj_solve",
             "fizzy_proj_errstr", "fizzy_proj_last_error", "fizzy_proj_launches_per_solve",
             "fizzy_proj_set_timing", "fizzy_proj_timing", "fizzy_proj_solve_noalloc",
             "fizzy_proj_batch_create", "fizzy_proj_batch_solve", "fizzy_proj_batch_status",
-            "fizzy_proj_batch_autotune", "fizzy_proj_batch_info", "fizzy_proj_batch_destroy")
+            "fizzy_proj_batch_autotune", "fizzy_proj_batch_info", "fizzy_proj_batch_destroy",
+            "fizzy_proj_set_physics", "fizzy_serve_create", "fizzy_serve_admit", "fizzy_serve_stream",
+            "fizzy_serve_launch", "fizzy_serve_poll", "fizzy_serve_stats", "fizzy_serve_release",
+            "fizzy_serve_info", "fizzy_serve_destroy")
+ERRORS[-7] = "busy"
 NOALLOC_MAX_CELLS = 262144
 
 
@@ -102,5 +106,28 @@ def lib():
         L.fizzy_proj_batch_info.restype = ctypes.c_int
         L.fizzy_proj_batch_destroy.argtypes = [vp]
         L.fizzy_proj_batch_destroy.restype = ctypes.c_int
+        D = ctypes.c_double
+        L.fizzy_proj_set_physics.argtypes = [vp, D, D, D, vp]
+        L.fizzy_proj_set_physics.restype = ctypes.c_int
+        L.fizzy_serve_create.argtypes = [ctypes.POINTER(vp), ctypes.c_size_t, ctypes.c_int]
+        L.fizzy_serve_create.restype = ctypes.c_int
+        L.fizzy_serve_admit.argtypes = [vp, ctypes.POINTER(Desc), ctypes.POINTER(ctypes.c_int),
+                                        ctypes.POINTER(vp)]
+        L.fizzy_serve_admit.restype = ctypes.c_int
+        L.fizzy_serve_stream.argtypes = [vp, ctypes.c_int, ctypes.POINTER(vp)]
+        L.fizzy_serve_stream.restype = ctypes.c_int
+        L.fizzy_serve_launch.argtypes = [vp, ctypes.c_int]
+        L.fizzy_serve_launch.restype = ctypes.c_int
+        L.fizzy_serve_poll.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.c_int]
+        L.fizzy_serve_poll.restype = ctypes.c_int
+        L.fizzy_serve_stats.argtypes = [vp, ctypes.c_int, ctypes.POINTER(Stats)]
+        L.fizzy_serve_stats.restype = ctypes.c_int
+        L.fizzy_serve_release.argtypes = [vp, ctypes.c_int]
+        L.fizzy_serve_release.restype = ctypes.c_int
+        L.fizzy_serve_info.argtypes = [vp, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_int),
+                                       ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
+        L.fizzy_serve_info.restype = ctypes.c_int
+        L.fizzy_serve_destroy.argtypes = [vp]
+        L.fizzy_serve_destroy.restype = ctypes.c_int
         _lib = L
     return _lib

@@ -52,6 +52,10 @@ struct fizzy_proj_plan_s {
     int Lx = 1, TXy = 2;
     size_t smem_x64 = 0, smem_x32 = 0, smem_y64 = 0, smem_y32 = 0;
     std::string err;
+    // stream-ordered allocation (FIZZY_FLAG_ASYNC_ALLOC)
+    int async_alloc = 0;
+    cudaStream_t alloc_stream = nullptr;
+    double *zt = nullptr;  // per-k tables (physics-dependent rows first)
     // per-kernel timing
     int timing = 0;
     std::vector<cudaEvent_t> ev;        // 2 per recorded launch
@@ -96,7 +100,8 @@ template <typename T> T *dev_alloc(fizzy_proj_plan_t p, size_t count, int *statu
     if (*status) return nullptr;
     void *ptr = nullptr;
     const size_t b = count * sizeof(T);
-    cudaError_t e = cudaMalloc(&ptr, b > 0 ? b : 16);
+    cudaError_t e = p->async_alloc ? cudaMallocAsync(&ptr, b > 0 ? b : 16, p->alloc_stream)
+                                   : cudaMalloc(&ptr, b > 0 ? b : 16);
     if (e != cudaSuccess) {
         (void)cudaGetLastError();
         *status = FIZZY_ERR_NOMEM;
@@ -160,11 +165,11 @@ int build_fft(fizzy_proj_plan_t p, int n, int bc, FFTHost &F, int *status) {
         F.cs32 = dev_alloc<float>(p, cs32.size(), status);
     }
     if (*status) return *status;
-    cudaMemcpy(F.tw64, tw.data(), tw.size() * sizeof(double), cudaMemcpyHostToDevice);
-    cudaMemcpy(F.cs64, cs.data(), cs.size() * sizeof(double), cudaMemcpyHostToDevice);
+    cudaMemcpyAsync(F.tw64, tw.data(), tw.size() * sizeof(double), cudaMemcpyHostToDevice, p->alloc_stream);
+    cudaMemcpyAsync(F.cs64, cs.data(), cs.size() * sizeof(double), cudaMemcpyHostToDevice, p->alloc_stream);
     if (p->mixed) {
-        cudaMemcpy(F.tw32, tw32.data(), tw32.size() * sizeof(float), cudaMemcpyHostToDevice);
-        cudaMemcpy(F.cs32, cs32.data(), cs32.size() * sizeof(float), cudaMemcpyHostToDevice);
+        cudaMemcpyAsync(F.tw32, tw32.data(), tw32.size() * sizeof(float), cudaMemcpyHostToDevice, p->alloc_stream);
+        cudaMemcpyAsync(F.cs32, cs32.data(), cs32.size() * sizeof(float), cudaMemcpyHostToDevice, p->alloc_stream);
     }
     FFTDesc d;
     memset(&d, 0, sizeof(d));
@@ -270,7 +275,13 @@ size_t fizzy_proj_workspace_bytes(const fizzy_proj_desc *d) {
 
 int fizzy_proj_destroy(fizzy_proj_plan_t p) {
     if (!p) return FIZZY_OK;
-    cudaDeviceSynchronize();
+    if (p->async_alloc) {
+        // stream-ordered: frees run after the work already queued on the plan's stream
+        for (void *a : p->allocs) cudaFreeAsync(a, p->alloc_stream);
+        p->allocs.clear();
+    } else {
+        cudaDeviceSynchronize();
+    }
     for (auto &e : p->ev) cudaEventDestroy(e);
     for (void *a : p->allocs) cudaFree(a);
     for (int t = 0; t < 7; ++t)
@@ -287,6 +298,8 @@ int fizzy_proj_plan(fizzy_proj_plan_t *out, const fizzy_proj_desc *d, void *stre
     if (v) return v;
     fizzy_proj_plan_s *p = new fizzy_proj_plan_s();
     p->desc = *d;
+    p->async_alloc = (d->flags & FIZZY_FLAG_ASYNC_ALLOC) ? 1 : 0;
+    p->alloc_stream = (cudaStream_t)stream;
     p->mixed = d->precision == FIZZY_PREC_MIXED;
     p->check = (d->flags & FIZZY_FLAG_CHECK) ? 1 : 0;
     p->tol = d->tol > 0 ? d->tol : 1e-10;
@@ -334,7 +347,8 @@ int fizzy_proj_plan(fizzy_proj_plan_t *out, const fizzy_proj_desc *d, void *stre
         fizzy_proj_destroy(p);
         return st;
     }
-    cudaMemcpy(zt_d, zt.data(), zt.size() * sizeof(double), cudaMemcpyHostToDevice);
+    p->zt = zt_d;
+    cudaMemcpyAsync(zt_d, zt.data(), zt.size() * sizeof(double), cudaMemcpyHostToDevice, p->alloc_stream);
 
     GridDev &g = p->g;
     memset(&g, 0, sizeof(g));
@@ -384,26 +398,10 @@ int fizzy_proj_plan(fizzy_proj_plan_t *out, const fizzy_proj_desc *d, void *stre
     p->Ux = Ux;
     p->Uy = Uy;
     const size_t ts = (size_t)Ux * Uy;
-    std::vector<double> mt(ts * nz, 0.0), ib(ts * nz, 0.0);
-    std::vector<double> lam_x(Ux), lam_y(Uy);
-    for (int u = 0; u < Ux; ++u) lam_x[u] = eig(u, nx, d->dx, d->bc_x);
-    for (int u = 0; u < Uy; ++u) lam_y[u] = eig(u, ny, d->dy, d->bc_y);
-    const double *A = &zt[T_LZA * nz];
+    std::vector<double> lam((size_t)Ux + Uy);
+    for (int u = 0; u < Ux; ++u) lam[u] = eig(u, nx, d->dx, d->bc_x);
+    for (int u = 0; u < Uy; ++u) lam[Ux + u] = eig(u, ny, d->dy, d->bc_y);
     const double *C = &zt[T_LZC * nz];
-#pragma omp parallel for schedule(static)
-    for (long long uu = 0; uu < (long long)ts; ++uu) {
-        const int ux = (int)(uu % Ux), uy = (int)(uu / Ux);
-        if (ux == 0 && uy == 0) continue;  // singular line handled in the kernel
-        const double lam = lam_x[ux] + lam_y[uy];
-        double beta = -(A[0] + C[0]) + lam;
-        ib[uu] = 1.0 / beta;
-        for (int k = 1; k < nz; ++k) {
-            const double m = A[k] / beta;
-            beta = (-(A[k] + C[k]) + lam) - m * C[k - 1];
-            mt[(size_t)k * ts + uu] = m;
-            ib[(size_t)k * ts + uu] = 1.0 / beta;
-        }
-    }
     p->mtab64 = dev_alloc<double>(p, ts * nz, &status);
     p->ibtab64 = dev_alloc<double>(p, ts * nz, &status);
     p->cup64 = dev_alloc<double>(p, nz, &status);
@@ -432,19 +430,27 @@ int fizzy_proj_plan(fizzy_proj_plan_t *out, const fizzy_proj_desc *d, void *stre
         fizzy_proj_destroy(p);
         return st;
     }
-    cudaMemcpy(p->mtab64, mt.data(), mt.size() * sizeof(double), cudaMemcpyHostToDevice);
-    cudaMemcpy(p->ibtab64, ib.data(), ib.size() * sizeof(double), cudaMemcpyHostToDevice);
-    cudaMemcpy(p->cup64, C, nz * sizeof(double), cudaMemcpyHostToDevice);
-    if (p->mixed) {
-        std::vector<float> t32(mt.size());
-        for (size_t t = 0; t < mt.size(); ++t) t32[t] = (float)mt[t];
-        cudaMemcpy(p->mtab32, t32.data(), t32.size() * sizeof(float), cudaMemcpyHostToDevice);
-        for (size_t t = 0; t < ib.size(); ++t) t32[t] = (float)ib[t];
-        cudaMemcpy(p->ibtab32, t32.data(), t32.size() * sizeof(float), cudaMemcpyHostToDevice);
-        std::vector<float> c32(C, C + nz);
-        cudaMemcpy(p->cup32, c32.data(), nz * sizeof(float), cudaMemcpyHostToDevice);
+    // factorisation tables on the device (bitwise the host recurrence)
+    {
+        double *lam_d = dev_alloc<double>(p, lam.size(), &status);
+        if (status) {
+            int st = status;
+            fizzy_proj_destroy(p);
+            return st;
+        }
+        cudaMemcpyAsync(lam_d, lam.data(), lam.size() * sizeof(double), cudaMemcpyHostToDevice, p->alloc_stream);
+        const int blocks = (int)std::min<size_t>((ts + 127) / 128, 4096);
+        k_ztables<<<blocks, 128, 0, p->alloc_stream>>>(Ux, Uy, nz, lam_d, lam_d + Ux, zt_d + T_LZA * nz,
+                                                       zt_d + T_LZC * nz, p->mtab64, p->ibtab64,
+                                                       p->mixed ? p->mtab32 : nullptr,
+                                                       p->mixed ? p->ibtab32 : nullptr);
     }
-    cudaMemset(p->st, 0, sizeof(DevStats));
+    cudaMemcpyAsync(p->cup64, C, nz * sizeof(double), cudaMemcpyHostToDevice, p->alloc_stream);
+    if (p->mixed) {
+        std::vector<float> c32(C, C + nz);
+        cudaMemcpyAsync(p->cup32, c32.data(), nz * sizeof(float), cudaMemcpyHostToDevice, p->alloc_stream);
+    }
+    cudaMemsetAsync(p->st, 0, sizeof(DevStats), p->alloc_stream);
 
     // ---- launch shapes and shared-memory opt-in
     p->Lx = x_lines_per_cta(nx);
@@ -453,6 +459,11 @@ int fizzy_proj_plan(fizzy_proj_plan_t *out, const fizzy_proj_desc *d, void *stre
     p->smem_x32 = pass_smem<float>(nx, p->Lx);
     p->smem_y64 = pass_smem<double>(ny, p->TXy / 2);
     p->smem_y32 = pass_smem<float>(ny, p->TXy / 2);
+    static bool attrs_set[256] = {false};  // opt-in shared-memory limits, once per device
+    int cur_dev = 0;
+    cudaGetDevice(&cur_dev);
+    if (cur_dev < 0 || cur_dev >= 256 || !attrs_set[cur_dev]) {
+    if (cur_dev >= 0 && cur_dev < 256) attrs_set[cur_dev] = true;
     const int big = 200 * 1024;
     cudaFuncSetAttribute(k_xfwd<double, XF_F64_DIVQ>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
     cudaFuncSetAttribute(k_xfwd<float, XF_MIX_DIVQ>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
@@ -464,13 +475,62 @@ int fizzy_proj_plan(fizzy_proj_plan_t *out, const fizzy_proj_desc *d, void *stre
     cudaFuncSetAttribute(k_ypass<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
     cudaFuncSetAttribute(k_ypass<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
     cudaFuncSetAttribute(k_ypass<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-    cudaError_t e = cudaDeviceSynchronize();
+    }
+    // stream-ordered plans are ready for work queued after them on their
+    // stream; other plans are complete on return
+    cudaError_t e = p->async_alloc ? cudaGetLastError() : cudaDeviceSynchronize();
     if (e != cudaSuccess) {
         int st = cuda_err(nullptr, e, "plan");
         fizzy_proj_destroy(p);
         return st;
     }
     *out = p;
+    return FIZZY_OK;
+}
+
+int fizzy_proj_set_physics(fizzy_proj_plan_t p, double rho_l, double rho_g, double dt, void *stream) {
+    if (!p) return FIZZY_ERR_INVALID;
+    if (!(rho_l >= 1e-30 && rho_l <= 1e30) || !(rho_g >= 1e-30 && rho_g <= 1e30) || !(dt > 0) ||
+        !std::isfinite(dt))
+        return set_err(p, FIZZY_ERR_INVALID, "bad densities or dt");
+    const int nx = p->desc.nx, ny = p->desc.ny, nz = p->desc.nz;
+    const double dx = p->desc.dx, dy = p->desc.dy;
+    const double rho0 = std::min(rho_l, rho_g), adrho = std::fabs(rho_l - rho_g);
+    const double sig = p->sigma;
+    // rows 0..3 of the per-k tables: chz, dvz, dvz_s, cgz (see fizzy_proj_plan)
+    std::vector<double> rows(4 * (size_t)nz);
+    for (int k = 0; k < nz; ++k) {
+        const double dzf = p->zf[k + 1] - p->zf[k];
+        const bool top = (k == nz - 1);
+        const double zc0 = 0.5 * (p->zf[k] + p->zf[k + 1]);
+        const double idzc = top ? 0.0 : 1.0 / (0.5 * (p->zf[k + 1] + p->zf[k + 2]) - zc0);
+        rows[0 * (size_t)nz + k] = adrho / rho0 * idzc;
+        rows[1 * (size_t)nz + k] = rho0 / (dt * dzf);
+        rows[2 * (size_t)nz + k] = sig * rho0 / (dt * dzf);
+        rows[3 * (size_t)nz + k] = dt / rho0 * idzc;
+    }
+    const cudaError_t e = cudaMemcpyAsync(p->zt, rows.data(), rows.size() * sizeof(double),
+                                          cudaMemcpyHostToDevice, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_err(p, e, "set_physics");
+    GridDev &g = p->g;
+    g.idt = 1.0 / dt;
+    g.two_rho0 = 2.0 * rho0;
+    g.adrho = adrho;
+    g.chx = adrho / (rho0 * dx);
+    g.chy = adrho / (rho0 * dy);
+    g.dvx = rho0 / (dt * dx);
+    g.dvy = rho0 / (dt * dy);
+    g.dvx_s = sig * rho0 / (dt * dx);
+    g.dvy_s = sig * rho0 / (dt * dy);
+    g.dt = dt;
+    g.cgx = dt / (rho0 * dx);
+    g.cgy = dt / (rho0 * dy);
+    g.div_scale = dt / rho0 * dx;
+    p->desc.rho_l = rho_l;
+    p->desc.rho_g = rho_g;
+    p->desc.dt = dt;
+    (void)nx;
+    (void)ny;
     return FIZZY_OK;
 }
 
@@ -693,6 +753,11 @@ int fizzy_proj_solve_host(fizzy_proj_plan_t p, const double *phi, const double *
 // Batched projections (fizzy_proj_batch_*)
 // ===========================================================================
 #include "fizzy_batch.inc"
+
+// ===========================================================================
+// Serving runtime (fizzy_serve_*)
+// ===========================================================================
+#include "fizzy_serve.inc"
 
 // ===========================================================================
 // Allocation-free projection (fizzy_proj_solve_noalloc): the FP64 kernel

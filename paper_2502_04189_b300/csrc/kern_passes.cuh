@@ -894,4 +894,52 @@ __global__ void __launch_bounds__(256) k_divmax(GridDev g, const double *__restr
     block_max_atomic(mx, &st->divmax_bits);
 }
 
+// z-factorisation tables of a plan, one thread per distinct eigenvalue pair
+// (ux, uy): beta_0 = b_0 + lambda, m_k = a_k / beta_(k-1),
+// beta_k = (b_k + lambda) - m_k c_(k-1), stored as m_k and 1/beta_k (FP64, and
+// rounded to FP32 when t32 is given).  Every operation is an explicit IEEE
+// round-to-nearest operation in the order of that recurrence.  The singular
+// pair (0,0) gets zeros.
+__global__ void k_ztables(int Ux, int Uy, int nz, const double *__restrict__ lamx,
+                          const double *__restrict__ lamy, const double *__restrict__ A,
+                          const double *__restrict__ C, double *mt, double *ib, float *mt32,
+                          float *ib32) {
+    const size_t ts = (size_t)Ux * Uy;
+    for (size_t uu = (size_t)blockIdx.x * blockDim.x + threadIdx.x; uu < ts;
+         uu += (size_t)gridDim.x * blockDim.x) {
+        const int ux = (int)(uu % Ux), uy = (int)(uu / Ux);
+        if (ux == 0 && uy == 0) {
+            for (int k = 0; k < nz; ++k) {
+                mt[(size_t)k * ts + uu] = 0.0;
+                ib[(size_t)k * ts + uu] = 0.0;
+                if (mt32) {
+                    mt32[(size_t)k * ts + uu] = 0.f;
+                    ib32[(size_t)k * ts + uu] = 0.f;
+                }
+            }
+            continue;
+        }
+        const double lam = __dadd_rn(lamx[ux], lamy[uy]);
+        double beta = __dadd_rn(-__dadd_rn(A[0], C[0]), lam);
+        double r = __ddiv_rn(1.0, beta);
+        mt[uu] = 0.0;
+        ib[uu] = r;
+        if (mt32) {
+            mt32[uu] = 0.f;
+            ib32[uu] = __double2float_rn(r);
+        }
+        for (int k = 1; k < nz; ++k) {
+            const double m = __ddiv_rn(A[k], beta);
+            beta = __dsub_rn(__dadd_rn(-__dadd_rn(A[k], C[k]), lam), __dmul_rn(m, C[k - 1]));
+            r = __ddiv_rn(1.0, beta);
+            mt[(size_t)k * ts + uu] = m;
+            ib[(size_t)k * ts + uu] = r;
+            if (mt32) {
+                mt32[(size_t)k * ts + uu] = __double2float_rn(m);
+                ib32[(size_t)k * ts + uu] = __double2float_rn(r);
+            }
+        }
+    }
+}
+
 }  // namespace fz

@@ -1,0 +1,80 @@
+"""Serving runtime on a B300: requests admitted while others run overlap on
+the device, and every served result equals the same request solved alone."""
+import numpy as np
+import pytest
+
+import paper_2502_04189_b300 as F
+import paper_2502_04189_b300.serve as S
+from paper_2502_04189_b300 import inputs as I
+
+from gpu_util import to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+def crop(case, desc, off):
+    """The host-side equivalent of TemplateFields.fill."""
+    nz, ny, nx = desc["nz"], desc["ny"], desc["nx"]
+    Tz, Ty, Tx = case.phi.shape
+    iz = (np.arange(nz) + off[0]) % Tz
+    iy = (np.arange(ny) + off[1]) % Ty
+    ix = (np.arange(nx) + off[2]) % Tx
+    out = [np.ascontiguousarray(a[np.ix_(iz, iy, ix)]) for a in
+           (case.phi, case.pn, case.pnm1, case.u, case.v, case.w)]
+    if desc["bcx"] == 1:
+        out[3][:, :, -1] = 0.0
+    if desc["bcy"] == 1:
+        out[4][:, -1, :] = 0.0
+    out[5][-1] = 0.0
+    return out
+
+
+@pytest.mark.parametrize("budget", [4 << 30, 12 << 20], ids=["roomy", "evicting"])
+def test_served_equals_alone_and_overlaps(cuda_ok, budget):
+    import torch
+    tmpl = I.make_case(I.CaseSpec(nx=48, ny=48, nz=40, n_bubbles=4, radius_cells=5, config=41))
+    fields = S.TemplateFields(tmpl)
+    rng = np.random.default_rng(5)
+    reqs = []
+    for i in range(16):
+        nx, ny = int(rng.choice([32, 48])), int(rng.choice([32, 48]))
+        nz = int(rng.integers(16, 41))
+        if i % 4 == 3:  # repeat a geometry: the plan cache must serve it
+            nx, ny, nz = 32, 32, 24
+        beta = float(rng.uniform(1, 2)) if i % 3 == 0 else 0.0
+        bcx, bcy = int(rng.integers(0, 2)), int(rng.integers(0, 2))
+        desc = dict(nx=nx, ny=ny, nz=nz, dx=1.0 / nx, dy=1.0 / nx, zf=I.z_faces(nz, nz / nx, beta),
+                    bcx=bcx, bcy=bcy, rho_l=1.0, rho_g=1.0 / float(rng.uniform(10, 1000)), dt=1e-4,
+                    precision=F.MIXED)
+        off = tuple(int(rng.integers(0, m)) for m in tmpl.phi.shape)
+        reqs.append(S.Request(i, 0.001 * i, desc, off))
+    server = F.Server(budget, slots=4)
+    served = {}
+
+    def fill(r, views, stream):
+        fields.fill(views, r.desc, r.offset, stream)
+
+    def on_done(r, views):
+        served[r.index] = [views[k].cpu().numpy() for k in (6, 3, 4, 5)]  # p, u, v, w
+
+    out, summ = S.run(server, reqs, fill, deadline=30.0, on_done=on_done)
+    info = server.info()
+    server.close()
+    assert summ["admitted"] == 16 and summ["all_converged"]
+    assert summ["max_inflight"] >= 2
+    if budget > (1 << 30):
+        assert info["plans_built"] < 16  # the repeated geometry is served from the cache
+    else:
+        assert info["plans_cached"] < info["plans_built"]  # plans were evicted
+    for r in reqs:
+        inp = crop(tmpl, r.desc, r.offset)
+        d = dict(r.desc)
+        plan = F.Plan(d["nx"], d["ny"], d["nz"], d["dx"], d["dy"], zf=d["zf"], bcx=d["bcx"],
+                      bcy=d["bcy"], rho_l=d["rho_l"], rho_g=d["rho_g"], dt=d["dt"], precision=F.MIXED)
+        phi, pn, pm, u, v, w = (to_dev(a) for a in inp)
+        p = torch.empty_like(phi)
+        plan.solve(phi, pn, pm, u, v, w, p)
+        torch.cuda.synchronize()
+        plan.close()
+        for got, ref in zip(served[r.index], (p, u, v, w)):
+            assert np.array_equal(got, ref.cpu().numpy()), r.index
