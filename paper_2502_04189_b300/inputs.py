@@ -183,13 +183,14 @@ def pressure_modes(spec: CaseSpec, zf: np.ndarray, rng, n_modes: int = 8) -> np.
     xc = _centres_1d(spec.nx, spec.lx) / spec.lx
     yc = _centres_1d(spec.ny, spec.ly) / spec.ly
     zc = 0.5 * (zf[:-1] + zf[1:]) / spec.lz
-    p = np.zeros((spec.nz, spec.ny, spec.nx))
-    for _ in range(n_modes):
+    zs = np.empty((spec.nz, n_modes))
+    xys = np.empty((n_modes, spec.ny * spec.nx))
+    for m in range(n_modes):
         a, b, c = rng.integers(0, 5, size=3)
         th = rng.random() * 2 * np.pi
-        xy = np.cos(2 * np.pi * (a * xc[None, :] + b * yc[:, None]) + th)
-        p += np.cos(np.pi * c * zc)[:, None, None] * xy[None, :, :]
-    return p
+        xys[m] = np.cos(2 * np.pi * (a * xc[None, :] + b * yc[:, None]) + th).ravel()
+        zs[:, m] = np.cos(np.pi * c * zc)
+    return (zs @ xys).reshape(spec.nz, spec.ny, spec.nx)  # sum over the modes
 
 
 def _random_periodic_field(shape, rng, slope: float = -17.0 / 6.0) -> np.ndarray:
@@ -200,17 +201,20 @@ def _random_periodic_field(shape, rng, slope: float = -17.0 / 6.0) -> np.ndarray
     ky = np.fft.fftfreq(ny) * ny
     kx = np.fft.rfftfreq(nx) * nx
     kmax = min(nx, ny, nz) / 3.0
-    out = np.empty(shape)
-    # build plane by plane in kz to bound memory
+    import os
+    import scipy.fft as sfft
+    # build in chunks of kz planes (the phases are drawn in plane order)
     spec = np.zeros((nz, ny, kx.size), dtype=np.complex128)
     k2xy = ky[:, None] ** 2 + kx[None, :] ** 2
-    for a in range(nz):
-        kk = np.sqrt(kz[a] ** 2 + k2xy)
+    step = max(1, (1 << 22) // max(1, k2xy.size))
+    for a0 in range(0, nz, step):
+        a1 = min(nz, a0 + step)
+        kk = np.sqrt(kz[a0:a1, None, None] ** 2 + k2xy[None])
         amp = np.where((kk > 0) & (kk <= kmax), np.power(np.maximum(kk, 1e-30), slope), 0.0)
         ph = rng.random(kk.shape) * 2 * np.pi
-        spec[a] = amp * np.exp(1j * ph)
-    out[...] = np.fft.irfftn(spec, s=shape, axes=(0, 1, 2))
-    return out
+        spec[a0:a1].real = amp * np.cos(ph)
+        spec[a0:a1].imag = amp * np.sin(ph)
+    return sfft.irfftn(spec, s=shape, axes=(0, 1, 2), workers=os.cpu_count() or 1)
 
 
 def solenoidal_velocity(spec: CaseSpec, dx: float, dy: float, zf: np.ndarray, rng):

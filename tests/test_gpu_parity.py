@@ -151,3 +151,16 @@ def test_bubbles256_fp64_full_size(cuda_ok):
     ep, eu = compare(c, got_m, ref)
     assert got_m["stats"]["relres"] <= 1e-10
     assert ep <= TOLMIX and eu <= TOLMIX, (ep, eu)
+
+
+def test_bubbles512_stretched_mixed_full_size(cuda_ok):
+    """512^3, tanh-stretched z (beta 1.5), 400 drops of radius 6, ratio 1000,
+    mixed precision refined to relres <= 1e-10: the whole field against the
+    FP64 oracle, plus the divergence identity."""
+    c = I.make_case(I.bubbles512_stretched_spec())
+    got = gpu_project(c, F.MIXED)
+    st = got["stats"]
+    assert st["converged"] == 1 and st["relres"] <= 1e-10 and st["div_metric"] <= 1e-10
+    ref = O.project_case(c)
+    ep, eu = compare(c, got, ref)
+    assert ep <= TOLMIX and eu <= TOLMIX, (ep, eu)
