@@ -298,7 +298,7 @@ int fizzy_serve_destroy(fizzy_serve_t s);
  * stats are produced.
  * ------------------------------------------------------------------------ */
 #define FIZZY_NOALLOC_MAX_CELLS 262144
-#define FIZZY_NOALLOC_SCRATCH_BYTES 12935488
+#define FIZZY_NOALLOC_SCRATCH_BYTES 12968256
 int fizzy_proj_solve_noalloc(const fizzy_proj_desc *d, const double *phi, const double *p_n,
                              const double *p_nm1, double *u, double *v, double *w,
                              double *p_np1, void *stream);

@@ -221,12 +221,57 @@ int x_lines_per_cta(int n) {
     if (L > 16) L = 16;
     return L;
 }
-int y_tile_cols(int n) {
-    int L = 1024 / n;
+// y-pass columns per tile: rows of 8 doubles or 16 floats (64 B) at n = 256;
+// the tile holds about 1024 (FP64) or 2048 (FP32) complex values.
+int y_tile_cols(int n, bool fp32 = false) {
+    const int cap = fp32 ? 16 : 8;
+    int L = (fp32 ? 2048 : 1024) / n;
     if (L < 2) L = 2;
-    if (L > 8) L = 8;
+    if (L > cap) L = cap;
     return 2 * L;
 }
+// Physics-dependent scalars of GridDev (densities and dt; spacings dx, dy):
+// shared by fizzy_proj_plan, fizzy_proj_set_physics and the allocation-free
+// entry point.
+void physics_consts(GridDev &g, double rho_l, double rho_g, double dt, double dx, double dy,
+                    double sig) {
+    const double rho0 = std::min(rho_l, rho_g), adrho = std::fabs(rho_l - rho_g);
+    const bool var = adrho > 0.0;
+    g.idt = 1.0 / dt;
+    g.var_rho = var ? 1 : 0;
+    // s'/r' lies in [1, 1 + |drho|/rho0]: centring the seed on half that range
+    g.fsh = var ? (int)std::floor(0.5 * std::log2(1.0 + adrho / rho0)) : 0;
+    g.fax = var ? rho0 * dx / dt : 0.0;
+    g.frx = var ? 2.0 * rho0 * rho0 * dx / (dt * adrho) : 0.0;
+    g.fay = var ? rho0 * dy / dt : 0.0;
+    g.fry = var ? 2.0 * rho0 * rho0 * dy / (dt * adrho) : 0.0;
+    g.dvx = rho0 / (dt * dx);
+    g.dvy = rho0 / (dt * dy);
+    g.dvx_s = sig * rho0 / (dt * dx);
+    g.dvy_s = sig * rho0 / (dt * dy);
+    g.dt = dt;
+    g.cgx = dt / (rho0 * dx);
+    g.cgy = dt / (rho0 * dy);
+    g.div_scale = dt / rho0 * dx;
+}
+
+// The physics rows of the per-k tables at plane k (the first kZPhys rows of
+// the table block): a' and r' of the z face above k, rho0/(dt dzf_k),
+// sigma rho0/(dt dzf_k), dt/(rho0 dzc_(k+1/2)).  dzc is the centre distance
+// to plane k+1 (unused on the top plane).
+constexpr int kZPhys = 5;
+void physics_zrow(double rho_l, double rho_g, double dt, double sig, double dzf, double dzc,
+                  bool top, double *row, size_t stride) {
+    const double rho0 = std::min(rho_l, rho_g), adrho = std::fabs(rho_l - rho_g);
+    const bool face = !top && adrho > 0.0;
+    const double idzc = top ? 0.0 : 1.0 / dzc;
+    row[0 * stride] = face ? rho0 * dzc / dt : 0.0;
+    row[1 * stride] = face ? 2.0 * rho0 * rho0 * dzc / (dt * adrho) : 0.0;
+    row[2 * stride] = rho0 / (dt * dzf);
+    row[3 * stride] = sig * rho0 / (dt * dzf);
+    row[4 * stride] = dt / rho0 * idzc;
+}
+
 template <typename T> size_t pass_smem(int n, int L) {
     return sizeof(typename C2<T>::t) * ((size_t)n + (n / 2 + 2) + 2 * (size_t)L * (n + 1));
 }
@@ -312,7 +357,6 @@ int fizzy_proj_plan(fizzy_proj_plan_t *out, const fizzy_proj_desc *d, void *stre
     p->desc.zf = nullptr;
 
     // ---- grid metrics (host, FP64)
-    const double rho0 = std::min(d->rho_l, d->rho_g);
     std::vector<double> dzf(nz), zc(nz), dzc(nz, 0.0);
     for (int k = 0; k < nz; ++k) {
         dzf[k] = p->zf[k + 1] - p->zf[k];
@@ -323,17 +367,13 @@ int fizzy_proj_plan(fizzy_proj_plan_t *out, const fizzy_proj_desc *d, void *stre
     for (int k = 0; k < nz; ++k) lz += dzf[k];
     p->sigma = 1.0 / (4.0 * (double)nx * (double)ny);
     const double sig = p->sigma;
-    // per-k tables, packed: 11 arrays of nz
-    enum { T_CHZ, T_DVZ, T_DVZS, T_CGZ, T_LZA, T_LZC, T_IZF, T_DZF, T_DZC, T_NTAB };
-    const double adrho = std::fabs(d->rho_l - d->rho_g);
+    // per-k tables, packed: T_NTAB arrays of nz (the physics rows first)
+    enum { T_FAZ, T_FRZ, T_DVZ, T_DVZS, T_CGZ, T_LZA, T_LZC, T_IZF, T_DZF, T_DZC, T_NTAB };
+    static_assert(T_LZA == kZPhys, "physics rows lead the per-k table block");
     std::vector<double> zt((size_t)T_NTAB * nz, 0.0);
     for (int k = 0; k < nz; ++k) {
         const bool top = (k == nz - 1);
-        const double idzc = top ? 0.0 : 1.0 / dzc[k];
-        zt[T_CHZ * nz + k] = adrho / rho0 * idzc;
-        zt[T_DVZ * nz + k] = rho0 / (d->dt * dzf[k]);
-        zt[T_DVZS * nz + k] = sig * rho0 / (d->dt * dzf[k]);
-        zt[T_CGZ * nz + k] = d->dt / rho0 * idzc;
+        physics_zrow(d->rho_l, d->rho_g, d->dt, sig, dzf[k], dzc[k], top, &zt[k], nz);
         zt[T_LZA * nz + k] = (k > 0) ? 1.0 / (dzf[k] * dzc[k - 1]) : 0.0;
         zt[T_LZC * nz + k] = top ? 0.0 : 1.0 / (dzf[k] * dzc[k]);
         zt[T_IZF * nz + k] = 1.0 / dzf[k];
@@ -357,23 +397,13 @@ int fizzy_proj_plan(fizzy_proj_plan_t *out, const fizzy_proj_desc *d, void *stre
     g.nz = nz;
     g.bcx = d->bc_x;
     g.bcy = d->bc_y;
-    g.idt = 1.0 / d->dt;
-    g.two_rho0 = 2.0 * rho0;
-    g.adrho = adrho;
-    g.chx = adrho / (rho0 * d->dx);
-    g.chy = adrho / (rho0 * d->dy);
-    g.dvx = rho0 / (d->dt * d->dx);
-    g.dvy = rho0 / (d->dt * d->dy);
-    g.dvx_s = sig * rho0 / (d->dt * d->dx);
-    g.dvy_s = sig * rho0 / (d->dt * d->dy);
-    g.dt = d->dt;
-    g.cgx = d->dt / (rho0 * d->dx);
-    g.cgy = d->dt / (rho0 * d->dy);
+    physics_consts(g, d->rho_l, d->rho_g, d->dt, d->dx, d->dy, sig);
     g.idx2 = 1.0 / (d->dx * d->dx);
     g.idy2 = 1.0 / (d->dy * d->dy);
     g.idx1 = 1.0 / d->dx;
     g.idy1 = 1.0 / d->dy;
-    g.chz = zt_d + T_CHZ * nz;
+    g.faz = zt_d + T_FAZ * nz;
+    g.frz = zt_d + T_FRZ * nz;
     g.dvz = zt_d + T_DVZ * nz;
     g.dvz_s = zt_d + T_DVZS * nz;
     g.cgz = zt_d + T_CGZ * nz;
@@ -384,7 +414,6 @@ int fizzy_proj_plan(fizzy_proj_plan_t *out, const fizzy_proj_desc *d, void *stre
     g.dzc = zt_d + T_DZC * nz;
     g.inv_lz = 1.0 / lz;
     g.sigma = sig;
-    g.div_scale = d->dt / rho0 * d->dx;
     g.inv_3n = 1.0 / (3.0 * (double)N);
     g.div_tol = p->div_tol;
 
@@ -454,7 +483,7 @@ int fizzy_proj_plan(fizzy_proj_plan_t *out, const fizzy_proj_desc *d, void *stre
 
     // ---- launch shapes and shared-memory opt-in
     p->Lx = x_lines_per_cta(nx);
-    p->TXy = y_tile_cols(ny);
+    p->TXy = y_tile_cols(ny, p->mixed != 0);
     p->smem_x64 = pass_smem<double>(nx, p->Lx);
     p->smem_x32 = pass_smem<float>(nx, p->Lx);
     p->smem_y64 = pass_smem<double>(ny, p->TXy / 2);
@@ -495,37 +524,20 @@ int fizzy_proj_set_physics(fizzy_proj_plan_t p, double rho_l, double rho_g, doub
         return set_err(p, FIZZY_ERR_INVALID, "bad densities or dt");
     const int nx = p->desc.nx, ny = p->desc.ny, nz = p->desc.nz;
     const double dx = p->desc.dx, dy = p->desc.dy;
-    const double rho0 = std::min(rho_l, rho_g), adrho = std::fabs(rho_l - rho_g);
     const double sig = p->sigma;
-    // rows 0..3 of the per-k tables: chz, dvz, dvz_s, cgz (see fizzy_proj_plan)
-    std::vector<double> rows(4 * (size_t)nz);
+    // the physics rows of the per-k tables (see fizzy_proj_plan)
+    std::vector<double> rows(kZPhys * (size_t)nz);
     for (int k = 0; k < nz; ++k) {
         const double dzf = p->zf[k + 1] - p->zf[k];
         const bool top = (k == nz - 1);
         const double zc0 = 0.5 * (p->zf[k] + p->zf[k + 1]);
-        const double idzc = top ? 0.0 : 1.0 / (0.5 * (p->zf[k + 1] + p->zf[k + 2]) - zc0);
-        rows[0 * (size_t)nz + k] = adrho / rho0 * idzc;
-        rows[1 * (size_t)nz + k] = rho0 / (dt * dzf);
-        rows[2 * (size_t)nz + k] = sig * rho0 / (dt * dzf);
-        rows[3 * (size_t)nz + k] = dt / rho0 * idzc;
+        const double dzc = top ? 0.0 : 0.5 * (p->zf[k + 1] + p->zf[k + 2]) - zc0;
+        physics_zrow(rho_l, rho_g, dt, sig, dzf, dzc, top, &rows[k], nz);
     }
     const cudaError_t e = cudaMemcpyAsync(p->zt, rows.data(), rows.size() * sizeof(double),
                                           cudaMemcpyHostToDevice, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_err(p, e, "set_physics");
-    GridDev &g = p->g;
-    g.idt = 1.0 / dt;
-    g.two_rho0 = 2.0 * rho0;
-    g.adrho = adrho;
-    g.chx = adrho / (rho0 * dx);
-    g.chy = adrho / (rho0 * dy);
-    g.dvx = rho0 / (dt * dx);
-    g.dvy = rho0 / (dt * dy);
-    g.dvx_s = sig * rho0 / (dt * dx);
-    g.dvy_s = sig * rho0 / (dt * dy);
-    g.dt = dt;
-    g.cgx = dt / (rho0 * dx);
-    g.cgy = dt / (rho0 * dy);
-    g.div_scale = dt / rho0 * dx;
+    physics_consts(p->g, rho_l, rho_g, dt, dx, dy, sig);
     p->desc.rho_l = rho_l;
     p->desc.rho_g = rho_g;
     p->desc.dt = dt;
@@ -769,9 +781,9 @@ namespace {
 constexpr int kNaMaxCells = FIZZY_NOALLOC_MAX_CELLS;
 constexpr int kNaMaxN = 512;
 constexpr int kNaMaxNz = 4096;
-constexpr int kNaZTabs = 9;  // per-k tables, in the order of the plan's T_* enum
+constexpr int kNaZTabs = 10;  // per-k tables, in the order of the plan's T_* enum
 // layout in doubles: q (3N) | fhat (N) | m table (N) | 1/beta table (N) |
-// per-k tables (9 x nz) | upper z coefficient (nz) | x twiddles | x cos/sin |
+// per-k tables (10 x nz) | upper z coefficient (nz) | x twiddles | x cos/sin |
 // y twiddles | y cos/sin
 constexpr size_t kNaTw = 2 * (size_t)kNaMaxN;
 constexpr size_t kNaCs = 2 * (size_t)(kNaMaxN / 2 + 2);
@@ -845,26 +857,21 @@ extern "C" int fizzy_proj_solve_noalloc(const fizzy_proj_desc *d, const double *
     double *hz = H + 2 * (size_t)kNaMaxCells;       // kNaZTabs x kNaMaxNz
     double *hcup = hz + kNaZTabs * (size_t)kNaMaxNz;
     double *hfft = hcup + kNaMaxNz;                 // tw_x | cs_x | tw_y | cs_y
-    const double rho0 = std::min(d->rho_l, d->rho_g);
-    const double adrho = std::fabs(d->rho_l - d->rho_g);
     static double zf[kNaMaxNz + 1], zc[kNaMaxNz];
     for (int k = 0; k <= nz; ++k) zf[k] = d->zf ? d->zf[k] : d->dz * k;
     for (int k = 0; k < nz; ++k) zc[k] = 0.5 * (zf[k] + zf[k + 1]);
     double lz = 0.0;
     const double sig = 1.0 / (4.0 * (double)nx * (double)ny);
     // per-k tables (same definitions and arithmetic as the plan's)
-    enum { Z_CHZ, Z_DVZ, Z_DVZS, Z_CGZ, Z_LZA, Z_LZC, Z_IZF, Z_DZF, Z_DZC };
+    enum { Z_FAZ, Z_FRZ, Z_DVZ, Z_DVZS, Z_CGZ, Z_LZA, Z_LZC, Z_IZF, Z_DZF, Z_DZC };
+    static_assert(Z_LZA == kZPhys && Z_DZC + 1 == kNaZTabs, "per-k table layout");
     for (int k = 0; k < nz; ++k) lz += zf[k + 1] - zf[k];
     for (int k = 0; k < nz; ++k) {
         const double dzf_k = zf[k + 1] - zf[k];
         const bool top = (k == nz - 1);
         const double dzc_k = top ? 0.0 : zc[k + 1] - zc[k];
         const double dzc_km = (k > 0) ? zc[k] - zc[k - 1] : 0.0;
-        const double idzc = top ? 0.0 : 1.0 / dzc_k;
-        hz[Z_CHZ * kNaMaxNz + k] = adrho / rho0 * idzc;
-        hz[Z_DVZ * kNaMaxNz + k] = rho0 / (d->dt * dzf_k);
-        hz[Z_DVZS * kNaMaxNz + k] = sig * rho0 / (d->dt * dzf_k);
-        hz[Z_CGZ * kNaMaxNz + k] = d->dt / rho0 * idzc;
+        physics_zrow(d->rho_l, d->rho_g, d->dt, sig, dzf_k, dzc_k, top, &hz[k], kNaMaxNz);
         hz[Z_LZA * kNaMaxNz + k] = (k > 0) ? 1.0 / (dzf_k * dzc_km) : 0.0;
         hz[Z_LZC * kNaMaxNz + k] = top ? 0.0 : 1.0 / (dzf_k * dzc_k);
         hz[Z_IZF * kNaMaxNz + k] = 1.0 / dzf_k;
@@ -919,23 +926,13 @@ extern "C" int fizzy_proj_solve_noalloc(const fizzy_proj_desc *d, const double *
     g.nz = nz;
     g.bcx = d->bc_x;
     g.bcy = d->bc_y;
-    g.idt = 1.0 / d->dt;
-    g.two_rho0 = 2.0 * rho0;
-    g.adrho = adrho;
-    g.chx = adrho / (rho0 * d->dx);
-    g.chy = adrho / (rho0 * d->dy);
-    g.dvx = rho0 / (d->dt * d->dx);
-    g.dvy = rho0 / (d->dt * d->dy);
-    g.dvx_s = sig * rho0 / (d->dt * d->dx);
-    g.dvy_s = sig * rho0 / (d->dt * d->dy);
-    g.dt = d->dt;
-    g.cgx = d->dt / (rho0 * d->dx);
-    g.cgy = d->dt / (rho0 * d->dy);
+    physics_consts(g, d->rho_l, d->rho_g, d->dt, d->dx, d->dy, sig);
     g.idx2 = 1.0 / (d->dx * d->dx);
     g.idy2 = 1.0 / (d->dy * d->dy);
     g.idx1 = 1.0 / d->dx;
     g.idy1 = 1.0 / d->dy;
-    g.chz = dz_ + Z_CHZ * kNaMaxNz;
+    g.faz = dz_ + Z_FAZ * kNaMaxNz;
+    g.frz = dz_ + Z_FRZ * kNaMaxNz;
     g.dvz = dz_ + Z_DVZ * kNaMaxNz;
     g.dvz_s = dz_ + Z_DVZS * kNaMaxNz;
     g.cgz = dz_ + Z_CGZ * kNaMaxNz;

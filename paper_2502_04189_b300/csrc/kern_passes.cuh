@@ -31,11 +31,16 @@ enum { BC_PERIODIC = 0, BC_NEUMANN = 1 };
 struct GridDev {
     int nx, ny, nz;
     int bcx, bcy;
-    // flux constants
+    // face-flux constants.  The split-term flux of a face with spacing h is
+    // q' = u* + dt |drho|/(rho0 h) * t/(|drho| t + 2 rho0) * (p^_b - p^_a),
+    // kept here with dt |drho|/(rho0 h) folded into the denominator:
+    // q' = u* + t/(a' t + r') (p^_b - p^_a), a' = rho0 h/dt,
+    // r' = 2 rho0^2 h/(dt |drho|).
     double idt;        // 1/dt
-    double two_rho0;   // 2 rho0
-    double adrho;      // |rho_l - rho_g|
-    double chx, chy;   // |drho| / (rho0 dx), |drho| / (rho0 dy)
+    int var_rho;       // 0: rho_l == rho_g, the split term vanishes (q' = u*)
+    int fsh;           // seed-shift offset floor(log2(1 + |drho|/rho0) / 2)
+    double fax, frx;   // a', r' of x faces
+    double fay, fry;   // a', r' of y faces
     // divergence constants, unscaled (rho0/h) and scaled by sigma = 1/(4 nx ny)
     double dvx, dvy, dvx_s, dvy_s;
     // correction constants
@@ -44,7 +49,8 @@ struct GridDev {
     double idx2, idy2;    // 1/dx^2, 1/dy^2
     double idx1, idy1;    // 1/dx, 1/dy
     // per-k tables (device, FP64, length nz)
-    const double *chz;    // |drho| / (rho0 dzc_(k+1/2))  (0 at k = nz-1)
+    const double *faz;    // a' of the z face above k: rho0 dzc_(k+1/2)/dt  (0 at k = nz-1)
+    const double *frz;    // r' of that face: 2 rho0^2 dzc_(k+1/2)/(dt |drho|)  (0 at k = nz-1)
     const double *dvz;    // rho0/dzf_k
     const double *dvz_s;  // sigma rho0/dzf_k
     const double *cgz;    // dt/(rho0 dzc_(k+1/2))    (0 at k = nz-1)
@@ -107,24 +113,44 @@ template <bool CG, typename T> __device__ __forceinline__ T ldp(const T *p) {
 // in the pure rho0 phase).  With t = psi_a + psi_b and s = rho_a + rho_b =
 // 2 rho0 + |drho| t (so beta_f = 2/s) and kappa = t/s,
 //     q' = dt q = u* - dt gamma_f (phat_b - phat_a)/h = u* + (dt |drho|/(rho0 h)) kappa dphat.
-// kappa comes from an FP32 quotient refined by one Newton step on the
-// quotient in FP64, kappa = k0 + r0 (t - s k0) (r0 the FP32 reciprocal of s),
-// which squares the FP32 error (relative error about 2^-43).
-// 7 FP64 instructions per face (8 when rho0 = rho_l).
+// dt |drho|/(rho0 h) is folded into the denominator: with s' = a' t + r'
+// (a' = rho0 h/dt, r' = 2 rho0^2 h/(dt |drho|)),  q' = u* + (t/s') dphat.
+// t/s' comes from an FP32 quotient refined by one Newton step in FP64,
+// kappa' = k0 + r0 (t - s' k0) (r0 the FP32 reciprocal of s'), which squares
+// the FP32 error (relative error about 2^-43).  The FP32 seed is taken of
+// s' 2^-sh, sh = exponent(r') + fsh, which puts it inside [2^-102, 2^102]
+// for any density ratio the plan accepts; all FP64 <-> FP32 moves are integer
+// operations.  psi = 1 - phi (rho0 = rho_l) is formed once per cell.
+// 6 FP64 instructions per face.
 // ---------------------------------------------------------------------------
-template <bool RHO0_IS_G>
-__device__ __forceinline__ double face_flux(const GridDev &g, double phi_a, double phi_b,
-                                            double ph_a, double ph_b, double ustar, double dtch) {
-    const double sum = phi_a + phi_b;
-    const double t = RHO0_IS_G ? sum : 2.0 - sum;
-    const double s = fmaT(g.adrho, t, g.two_rho0);
+__device__ __forceinline__ int seed_shift(double r, int fsh) {
+    return ((__double2hiint(r) >> 20) & 0x7ff) - 1023 + fsh;
+}
+
+__device__ __forceinline__ double face_flux(double psi_a, double psi_b, double ph_a, double ph_b,
+                                            double ustar, double ap, double rp, int fsh) {
+    const int sh = seed_shift(rp, fsh);
+    const double t = psi_a + psi_b;
+    const double s = fmaT(ap, t, rp);
     const float tf = f64_to_f32_shift(t, 0);
     float rf;
-    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rf) : "f"(pos_f64_to_f32_trunc(s)));
-    const double k0 = f32_to_f64_shift(tf * rf, 0);
-    const double r0 = pos_f32_to_f64(rf);
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rf) : "f"(f64_to_f32_shift(s, sh)));
+    const double k0 = f32_to_f64_shift(tf * rf, -sh);
+    const double r0 = f32_to_f64_shift(rf, -sh);
     const double kappa = fmaT(r0, fmaT(-s, k0, t), k0);
-    return fmaT(dtch, mulT(kappa, ph_b - ph_a), ustar);
+    return fmaT(kappa, ph_b - ph_a, ustar);
+}
+
+// |x| 2^-64 as FP32 (truncated; 0 below 2^-190, FLT_MAX from 2^192 up), by
+// integer operations: the squares of the U statistic of the stopping rule
+// are summed in FP32 (U only scales a threshold).
+__device__ __forceinline__ float abs_scaled_f32(double x) {
+    const unsigned hi = (unsigned)__double2hiint(x) & 0x7fffffffu;
+    const unsigned lo = (unsigned)__double2loint(x);
+    const int e = (int)(hi >> 20) - 64;
+    if (e <= 896) return 0.f;
+    if (e >= 896 + 255) return 3.40282347e38f;
+    return __uint_as_float(((unsigned)(e - 896) << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29));
 }
 
 constexpr int FLUX_BX = 32, FLUX_BY = 8;
@@ -132,7 +158,8 @@ constexpr int FLUX_BX = 32, FLUX_BY = 8;
 // One CTA covers a 32 x 8 (i, j) tile and marches up kc planes; phat and phi
 // of each plane sit in shared memory with a one-cell halo in +x and +y, and
 // the +z neighbour read in one plane is carried as the centre of the next,
-// so phat is evaluated about once per cell.
+// so phat (and psi) is evaluated about once per cell.  The optional sum of
+// u*^2 (for U of the stopping rule) is accumulated in FP32 on |u*| 2^-64.
 template <bool RHO0_IS_G>
 __device__ __forceinline__ void flux_body(const GridDev &g, int kc, VB vb, const double *phi,
                                           const double *pn, const double *pnm1, const double *u,
@@ -164,48 +191,55 @@ __device__ __forceinline__ void flux_body(const GridDev &g, int kc, VB vb, const
         hx = FLUX_BX;
     }
     if (hy >= 0) hoff = (size_t)src_j(j0 + hy) * g.nx + src_i(i0 + hx);
-    const double dtchx = g.dt * g.chx, dtchy = g.dt * g.chy;
-    double ph_c = 0.0, phi_c = 0.0, usq = 0.0;
+    // psi of one cell: phi (rho0 = rho_g) or 1 - phi (rho0 = rho_l)
+    auto psi = [&](size_t at) { return RHO0_IS_G ? phi[at] : 1.0 - phi[at]; };
+    const bool var = g.var_rho != 0;
+    double ph_c = 0.0, psi_c = 0.0;
+    float usq = 0.f;
     for (int k = k0; k < k1; ++k) {
         const size_t base = (size_t)k * plane;
         if (k == k0) {
-            phi_c = phi[base + own];
+            psi_c = psi(base + own);
             ph_c = fmaT(2.0, pn[base + own], -pnm1[base + own]);
         }
         s_ph[ty][tx] = ph_c;
-        s_phi[ty][tx] = phi_c;
+        s_phi[ty][tx] = psi_c;
         if (hy >= 0) {
-            s_phi[hy][hx] = phi[base + hoff];
+            s_phi[hy][hx] = psi(base + hoff);
             s_ph[hy][hx] = fmaT(2.0, pn[base + hoff], -pnm1[base + hoff]);
         }
         __syncthreads();
-        double ph_t = 0.0, phi_t = 0.0;
+        double ph_t = 0.0, psi_t = 0.0;
         if (k + 1 < g.nz) {
-            phi_t = phi[base + plane + own];
+            psi_t = psi(base + plane + own);
             ph_t = fmaT(2.0, pn[base + plane + own], -pnm1[base + plane + own]);
         }
         if (in) {
             const size_t c = base + (size_t)j * g.nx + i;
             const double uc = u[c], vc = v[c], wc = w[c];
-            if (usq_slot) usq = fmaT(uc, uc, fmaT(vc, vc, fmaT(wc, wc, usq)));
+            if (usq_slot) {
+                const float a = abs_scaled_f32(uc), b = abs_scaled_f32(vc), d = abs_scaled_f32(wc);
+                usq = fmaf(a, a, fmaf(b, b, fmaf(d, d, usq)));
+            }
             double q = 0.0;
             if (!(g.bcx == BC_NEUMANN && i == g.nx - 1))
-                q = face_flux<RHO0_IS_G>(g, phi_c, s_phi[ty][tx + 1], ph_c, s_ph[ty][tx + 1], uc, dtchx);
+                q = var ? face_flux(psi_c, s_phi[ty][tx + 1], ph_c, s_ph[ty][tx + 1], uc, g.fax, g.frx, g.fsh) : uc;
             qx[c] = q;
             q = 0.0;
             if (!(g.bcy == BC_NEUMANN && j == g.ny - 1))
-                q = face_flux<RHO0_IS_G>(g, phi_c, s_phi[ty + 1][tx], ph_c, s_ph[ty + 1][tx], vc, dtchy);
+                q = var ? face_flux(psi_c, s_phi[ty + 1][tx], ph_c, s_ph[ty + 1][tx], vc, g.fay, g.fry, g.fsh) : vc;
             qy[c] = q;
             q = 0.0;
-            if (k + 1 < g.nz) q = face_flux<RHO0_IS_G>(g, phi_c, phi_t, ph_c, ph_t, wc, g.dt * g.chz[k]);
+            if (k + 1 < g.nz) q = var ? face_flux(psi_c, psi_t, ph_c, ph_t, wc, g.faz[k], g.frz[k], g.fsh) : wc;
             qz[c] = q;
         }
         ph_c = ph_t;
-        phi_c = phi_t;
+        psi_c = psi_t;
         __syncthreads();
     }
     if (usq_slot) {
-        const double sm = block_sum(usq);
+        // back to FP64 and to the unscaled square (x 2^128), integer-only
+        const double sm = block_sum(f32_to_f64_shift(usq, 128));
         if (tid == 0) *usq_slot = sm;
     }
 }
@@ -322,6 +356,73 @@ __device__ __forceinline__ void xfwd_body(const GridDev &g, const FFTDesc &D, in
     float scale32 = (float)g.sigma;
     if (MODE == XF_MIX_RESID) ef = exp_of_bits(ldp<CG>(&a.st->fmax_bits));
     // 1. source values into the packed complex lines
+    if (MODE == XF_MIX_RESID) {
+        // r = f - L_h p with every x- and y-face difference formed once:
+        //   r = f - idx2 (dE - dW) - idy2 (dN - dS) - c_k dT + a_k dB
+        // (dE = p(i+1) - p(i), dN = p(j+1) - p(j), dT = p(k+1) - p(k),
+        // dB = p(k) - p(k-1); wall faces carry zero difference), folded into
+        // four FMAs.  Thread mapping: G groups of n threads (n <= blockDim),
+        // group g walks a contiguous chunk of the CTA's lines at fixed i, so
+        // the south difference of a line is the north difference the same
+        // thread formed for the previous line; the west difference is the
+        // east difference of the neighbouring lane.  Line and warp starts
+        // form theirs from memory.  Loop trip counts are uniform so the
+        // shuffle runs converged.
+        const int R2 = 2 * L;
+        const int nt = blockDim.x;
+        const int G = (n >= nt) ? 1 : nt / n;
+        const int NI = (n + nt - 1) / nt;
+        const int chunk = (R2 + G - 1) / G;
+        const int grp = (n >= nt) ? 0 : (int)threadIdx.x / n;
+        const int lane = threadIdx.x & 31;
+        const size_t pl = (size_t)g.nx * g.ny;
+        for (int ic = 0; ic < NI; ++ic) {
+            const int i = (n >= nt) ? (int)threadIdx.x + ic * nt : (int)threadIdx.x - grp * n;
+            const bool ion = (i < n) && (grp < G);
+            double dn_prev = 0.0;
+            for (int rr = 0; rr < chunk; ++rr) {
+                const int r = grp * chunk + rr;
+                const int line = line0 + r;
+                const bool on = ion && r < R2 && line < nlines;
+                double pc = 0.0, de = 0.0, dn = 0.0;
+                int j = 0, k = 0;
+                size_t c = 0;
+                if (on) {
+                    j = line % g.ny;
+                    k = line / g.ny;
+                    c = cidx(g, i, j, k);
+                    pc = ldp<CG>(a.p + c);
+                    if (i < g.nx - 1) de = ldp<CG>(a.p + c + 1) - pc;
+                    else if (g.bcx == BC_PERIODIC) de = ldp<CG>(a.p + c - i) - pc;
+                    if (j < g.ny - 1) dn = ldp<CG>(a.p + c + g.nx) - pc;
+                    else if (g.bcy == BC_PERIODIC) dn = ldp<CG>(a.p + c - (size_t)j * g.nx) - pc;
+                }
+                double dw = __shfl_up_sync(0xffffffffu, de, 1);
+                if (on) {
+                    if (i == 0) dw = (g.bcx == BC_PERIODIC) ? pc - ldp<CG>(a.p + c + g.nx - 1) : 0.0;
+                    else if (lane == 0) dw = pc - ldp<CG>(a.p + c - 1);
+                    double ds;
+                    if (j == 0)
+                        ds = (g.bcy == BC_PERIODIC) ? pc - ldp<CG>(a.p + c + (size_t)(g.ny - 1) * g.nx)
+                                                    : 0.0;
+                    else if (rr > 0) ds = dn_prev;
+                    else ds = pc - ldp<CG>(a.p + c - g.nx);
+                    const double dt = (k < g.nz - 1) ? ldp<CG>(a.p + c + pl) - pc : 0.0;
+                    const double db = (k > 0) ? pc - ldp<CG>(a.p + c - pl) : 0.0;
+                    double res = fmaT(-g.idx2, de - dw, ldp<CG>(a.f + c));
+                    res = fmaT(-g.idy2, dn - ds, res);
+                    res = fmaT(-g.lzc[k], dt, res);
+                    res = fmaT(g.lza[k], db, res);
+                    mx = umax64(mx, absbits(res));
+                    ((T *)(A + (r >> 1) * ls))[2 * line_pos(i, n, D.kind) + (r & 1)] =
+                        (T)(f64_to_f32_shift(res, ef) * scale32);
+                } else if (ion && r < R2) {
+                    ((T *)(A + (r >> 1) * ls))[2 * line_pos(i, n, D.kind) + (r & 1)] = (T)0;
+                }
+                dn_prev = dn;
+            }
+        }
+    } else
     for (int idx = threadIdx.x; idx < 2 * L * n; idx += blockDim.x) {
         const int r = idx / n, i = idx - r * n;
         const int line = line0 + r;
@@ -332,15 +433,11 @@ __device__ __forceinline__ void xfwd_body(const GridDev &g, const FFTDesc &D, in
                 const double f = div_q<CG>(g, i, j, k, g.dvx_s, g.dvy_s, g.dvz_s[k], a.qx, a.qy, a.qz);
                 if (a.track_fmax) mx = umax64(mx, absbits(f));
                 val = (T)f;
-            } else if (MODE == XF_MIX_DIVQ) {
+            } else {
                 const double f = div_q<CG>(g, i, j, k, g.dvx, g.dvy, g.dvz[k], a.qx, a.qy, a.qz);
                 a.f_out[cidx(g, i, j, k)] = f;
                 mx = umax64(mx, absbits(f));
                 val = (T)(f64_to_f32_shift(f, 0) * scale32);
-            } else {
-                const double rr = resid<CG>(g, i, j, k, a.f, a.p);
-                mx = umax64(mx, absbits(rr));
-                val = (T)(f64_to_f32_shift(rr, ef) * scale32);
             }
         }
         ((T *)(A + (r >> 1) * ls))[2 * line_pos(i, n, D.kind) + (r & 1)] = val;
