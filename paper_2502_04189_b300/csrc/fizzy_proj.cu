@@ -653,7 +653,7 @@ int fizzy_proj_solve(fizzy_proj_plan_t p, const double *phi, const double *p_n, 
     const int nlines = ny * nz;
     const int xgrid = (nlines + 2 * p->Lx - 1) / (2 * p->Lx);
     const dim3 ygrid((nx + p->TXy - 1) / p->TXy, nz);
-    const int tthreads = (g.bcx == FIZZY_BC_PERIODIC ? nx / 2 + 1 : nx) * ny;
+    const int tthreads = nx * ny;  // one z-line per thread
     const dim3 tgrid((tthreads + THOMAS_BLOCK - 1) / THOMAS_BLOCK);
     XArgs xa;
     memset(&xa, 0, sizeof(xa));
@@ -960,7 +960,7 @@ extern "C" int fizzy_proj_solve_noalloc(const fizzy_proj_desc *d, const double *
     const dim3 cblk(32, 8), cgrd((nx + 31) / 32, (ny + 7) / 8, nz);
     const int xgrid = (ny * nz + 2 * Lx - 1) / (2 * Lx);
     const dim3 ygrid((nx + TXy - 1) / TXy, nz);
-    const int tthreads = (d->bc_x == FIZZY_BC_PERIODIC ? nx / 2 + 1 : nx) * ny;
+    const int tthreads = nx * ny;  // one z-line per thread
     const dim3 tgrid((tthreads + THOMAS_BLOCK - 1) / THOMAS_BLOCK);
     XArgs xa;
     memset(&xa, 0, sizeof(xa));

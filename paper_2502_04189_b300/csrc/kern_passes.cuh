@@ -658,102 +658,112 @@ __global__ void __launch_bounds__(256) k_xinv(GridDev g, FFTDesc D, int L, const
 
 // Tridiagonal z-solves, one per (kx, ky) line, with factorisation tables
 // m_k and 1/beta_k that depend only on the eigenvalue pair and are stored once
-// per distinct pair at index ((k*Uy + uy)*Ux + ux).  In a periodic x
-// direction the half-complex indices i and nx-i share their eigenvalue, so one
-// thread solves both lines against one table read.  The forward sweep keeps
-// its modified right-hand side in place and the backward sweep overwrites it
-// with the solution.  Each thread streams its line values and table entries
-// through a THOMAS_S-stage cp.async ring in shared memory (its own slots:
-// no barrier), so THOMAS_S planes of loads are in flight per thread while the
-// sequential recurrence runs.
+// per distinct pair at index ((k*Uy + uy)*Ux + ux).  In a periodic
+// direction the half-complex indices i and nx-i share their eigenvalue and
+// so their table.  The forward sweep keeps its modified right-hand side in
+// place and the backward sweep overwrites it with the solution.
 // The (0,0) line is singular: its right-hand side mean is removed, the fluxes
 // are integrated from the bottom wall and the result is given zero
 // dzf-weighted mean (the pressure gauge).
-constexpr int THOMAS_S = 16;
+constexpr int THOMAS_S = 16;      // ring stages: planes in flight per line
+constexpr int THOMAS_U = 4;       // planes per block of the recurrence
 constexpr int THOMAS_BLOCK = 64;
 
-template <typename T, int NL>
-__device__ __forceinline__ void thomas_lines(int nz, size_t plane, T *d0, T *d1, size_t ts,
-                                             size_t tb, const T *__restrict__ mtab,
-                                             const T *__restrict__ ibtab,
-                                             const T *__restrict__ cup, T *ring) {
-    // ring slot (stage, item) of this thread: ring[(stage*(NL+1) + item)*THOMAS_BLOCK + tid]
+// One z-line per thread (forward elimination y_k = f_k - m_k y_(k-1), back
+// substitution p_k = (y_k - c_k p_(k+1)) / beta_k, the factors m_k and
+// 1/beta_k read from the per-eigenvalue tables).  The line's data and table
+// values stream through a cp.async ring in shared memory, THOMAS_S planes
+// ahead; the ring is consumed in blocks of THOMAS_U planes (one wait per
+// block, all ring loads issued before the recurrence, the refill issued
+// before the stores), so the dependent chain of a block is THOMAS_U
+// back-to-back FMAs.  Each thread reads only its own ring slots.
+template <typename T>
+__device__ __forceinline__ void thomas_line_ring(int nz, size_t plane, T *d, size_t ts, size_t tb,
+                                                 const T *__restrict__ mtab,
+                                                 const T *__restrict__ ibtab,
+                                                 const T *__restrict__ cup, T *ring) {
+    constexpr int U = THOMAS_U, G = THOMAS_S / THOMAS_U;
+    static_assert(THOMAS_S % THOMAS_U == 0, "ring holds whole blocks");
     const int tid = threadIdx.x;
-    T *d[2] = {d0, d1};
+    // slot (stage, item): item 0 = line value, 1 = table value
     auto slot = [&](int stage, int item) -> T * {
-        return ring + ((size_t)(stage * (NL + 1) + item) * THOMAS_BLOCK + tid);
+        return ring + ((size_t)(stage * 2 + item) * THOMAS_BLOCK + tid);
     };
-    // ---- forward sweep over k = 1 .. nz-1; plane k lives in stage (k-1) % S
-#pragma unroll 1
-    for (int q = 0; q < THOMAS_S; ++q) {
-        const int k = 1 + q;
-        if (k < nz) {
-            cp_async<sizeof(T)>(slot(q, NL), mtab + (size_t)k * ts + tb);
+    const int nb = (nz - 1 + U - 1) / U;  // blocks per sweep (nz - 1 planes each)
+    // ---- forward: block b holds planes 1 + bU + q in stages (b % G) U + q
+    auto issue_f = [&](int b) {
+        const int s0 = (b % G) * U;
 #pragma unroll
-            for (int l = 0; l < NL; ++l) cp_async<sizeof(T)>(slot(q, l), d[l] + (size_t)k * plane);
+        for (int q = 0; q < U; ++q) {
+            const int k = 1 + b * U + q;
+            if (k < nz) {
+                cp_async<sizeof(T)>(slot(s0 + q, 1), mtab + (size_t)k * ts + tb);
+                cp_async<sizeof(T)>(slot(s0 + q, 0), d + (size_t)k * plane);
+            }
         }
         cp_async_commit();
-    }
-    T prev[2];
-#pragma unroll
-    for (int l = 0; l < NL; ++l) prev[l] = d[l][0];
-    int st = 0;
+    };
 #pragma unroll 1
-    for (int k = 1; k < nz; ++k) {
-        cp_async_wait<THOMAS_S - 1>();
-        const T m = *slot(st, NL);
+    for (int b = 0; b < G; ++b) issue_f(b);
+    T prev = d[0];
+#pragma unroll 1
+    for (int b = 0; b < nb; ++b) {
+        cp_async_wait<G - 1>();
+        const int s0 = (b % G) * U, k0 = 1 + b * U;
+        T mv[U], fv[U], out[U];
 #pragma unroll
-        for (int l = 0; l < NL; ++l) {
-            prev[l] = fmaT(-m, prev[l], *slot(st, l));
-            d[l][(size_t)k * plane] = prev[l];
+        for (int q = 0; q < U; ++q) {
+            mv[q] = *slot(s0 + q, 1);
+            fv[q] = *slot(s0 + q, 0);
         }
-        const int kn = k + THOMAS_S;
-        if (kn < nz) {
-            cp_async<sizeof(T)>(slot(st, NL), mtab + (size_t)kn * ts + tb);
 #pragma unroll
-            for (int l = 0; l < NL; ++l) cp_async<sizeof(T)>(slot(st, l), d[l] + (size_t)kn * plane);
+        for (int q = 0; q < U; ++q) {
+            if (k0 + q < nz) prev = fmaT(-mv[q], prev, fv[q]);
+            out[q] = prev;
         }
-        cp_async_commit();
-        st = (st + 1 == THOMAS_S) ? 0 : st + 1;
+        issue_f(b + G);
+#pragma unroll
+        for (int q = 0; q < U; ++q)
+            if (k0 + q < nz) d[(size_t)(k0 + q) * plane] = out[q];
     }
     cp_async_wait<0>();
-    // ---- backward sweep: p_(nz-1) = d_(nz-1)/beta, p_k = (d_k - c_k p_(k+1))/beta_k
-    const T ibt = ibtab[(size_t)(nz - 1) * ts + tb];
+    // ---- backward: p_(nz-1) = y_(nz-1)/beta; block b holds planes nz-2-bU-q
+    prev = mulT(prev, ibtab[(size_t)(nz - 1) * ts + tb]);
+    d[(size_t)(nz - 1) * plane] = prev;
+    auto issue_b = [&](int b) {
+        const int s0 = (b % G) * U;
 #pragma unroll
-    for (int l = 0; l < NL; ++l) {
-        prev[l] = mulT(prev[l], ibt);
-        d[l][(size_t)(nz - 1) * plane] = prev[l];
-    }
-    // plane k (descending from nz-2) lives in stage (nz-2-k) % S
-#pragma unroll 1
-    for (int q = 0; q < THOMAS_S; ++q) {
-        const int k = nz - 2 - q;
-        if (k >= 0) {
-            cp_async<sizeof(T)>(slot(q, NL), ibtab + (size_t)k * ts + tb);
-#pragma unroll
-            for (int l = 0; l < NL; ++l) cp_async<sizeof(T)>(slot(q, l), d[l] + (size_t)k * plane);
+        for (int q = 0; q < U; ++q) {
+            const int k = nz - 2 - b * U - q;
+            if (k >= 0) {
+                cp_async<sizeof(T)>(slot(s0 + q, 1), ibtab + (size_t)k * ts + tb);
+                cp_async<sizeof(T)>(slot(s0 + q, 0), d + (size_t)k * plane);
+            }
         }
         cp_async_commit();
-    }
-    st = 0;
+    };
 #pragma unroll 1
-    for (int k = nz - 2; k >= 0; --k) {
-        cp_async_wait<THOMAS_S - 1>();
-        const T ib = *slot(st, NL);
-        const T c = cup[k];
+    for (int b = 0; b < G; ++b) issue_b(b);
+#pragma unroll 1
+    for (int b = 0; b < nb; ++b) {
+        cp_async_wait<G - 1>();
+        const int s0 = (b % G) * U, k0 = nz - 2 - b * U;
+        T iv[U], dv[U], cv[U], out[U];
 #pragma unroll
-        for (int l = 0; l < NL; ++l) {
-            prev[l] = mulT(fmaT(-c, prev[l], *slot(st, l)), ib);
-            d[l][(size_t)k * plane] = prev[l];
+        for (int q = 0; q < U; ++q) {
+            iv[q] = *slot(s0 + q, 1);
+            dv[q] = *slot(s0 + q, 0);
+            cv[q] = (k0 - q >= 0) ? cup[k0 - q] : (T)0;
         }
-        const int kn = k - THOMAS_S;
-        if (kn >= 0) {
-            cp_async<sizeof(T)>(slot(st, NL), ibtab + (size_t)kn * ts + tb);
 #pragma unroll
-            for (int l = 0; l < NL; ++l) cp_async<sizeof(T)>(slot(st, l), d[l] + (size_t)kn * plane);
+        for (int q = 0; q < U; ++q) {
+            if (k0 - q >= 0) prev = mulT(fmaT(-cv[q], prev, dv[q]), iv[q]);
+            out[q] = prev;
         }
-        cp_async_commit();
-        st = (st + 1 == THOMAS_S) ? 0 : st + 1;
+        issue_b(b + G);
+#pragma unroll
+        for (int q = 0; q < U; ++q)
+            if (k0 - q >= 0) d[(size_t)(k0 - q) * plane] = out[q];
     }
     cp_async_wait<0>();
 }
@@ -808,82 +818,63 @@ __device__ void singular_line_warp(const GridDev &g, T *d, size_t plane) {
         d[(size_t)k * plane] = (T)((double)ldp<CG>(d + (size_t)k * plane) - pbar);
 }
 
-// Register-prefetch variant of thomas_lines for the persistent batch kernel:
-// THOMAS_U planes of loads (L2-only when CG) are issued ahead of each block of
-// the recurrence (4 keeps the batch kernel within 80 registers).
-template <typename T, int NL, bool CG, int THOMAS_U>
-__device__ __forceinline__ void thomas_lines_reg(int nz, size_t plane, T *d0, T *d1, size_t ts,
-                                                 size_t tb, const T *__restrict__ mtab,
-                                                 const T *__restrict__ ibtab,
-                                                 const T *__restrict__ cup) {
-    T *d[2] = {d0, d1};
-    T prev[2];
-#pragma unroll
-    for (int l = 0; l < NL; ++l) prev[l] = ldp<CG>(d[l]);
+// Register-prefetch variant for the persistent batch kernel (no shared-memory
+// ring): THOMAS_U planes of loads (L2-only when CG) are issued ahead of each
+// block of the recurrence.
+template <typename T, bool CG>
+__device__ __forceinline__ void thomas_line_reg(int nz, size_t plane, T *d, size_t ts, size_t tb,
+                                                const T *__restrict__ mtab,
+                                                const T *__restrict__ ibtab,
+                                                const T *__restrict__ cup) {
+    constexpr int U = THOMAS_U;
+    T prev = ldp<CG>(d);
     int k = 1;
-    for (; k + THOMAS_U <= nz; k += THOMAS_U) {
-        T fv[NL][THOMAS_U], mv[THOMAS_U];
+    for (; k + U <= nz; k += U) {
+        T fv[U], mv[U];
 #pragma unroll
-        for (int q = 0; q < THOMAS_U; ++q) {
+        for (int q = 0; q < U; ++q) {
             mv[q] = mtab[(size_t)(k + q) * ts + tb];
-#pragma unroll
-            for (int l = 0; l < NL; ++l) fv[l][q] = ldp<CG>(d[l] + (size_t)(k + q) * plane);
+            fv[q] = ldp<CG>(d + (size_t)(k + q) * plane);
         }
 #pragma unroll
-        for (int q = 0; q < THOMAS_U; ++q)
-#pragma unroll
-            for (int l = 0; l < NL; ++l) {
-                prev[l] = fmaT(-mv[q], prev[l], fv[l][q]);
-                d[l][(size_t)(k + q) * plane] = prev[l];
-            }
+        for (int q = 0; q < U; ++q) {
+            prev = fmaT(-mv[q], prev, fv[q]);
+            d[(size_t)(k + q) * plane] = prev;
+        }
     }
     for (; k < nz; ++k) {
-        const T m = mtab[(size_t)k * ts + tb];
-#pragma unroll
-        for (int l = 0; l < NL; ++l) {
-            prev[l] = fmaT(-m, prev[l], ldp<CG>(d[l] + (size_t)k * plane));
-            d[l][(size_t)k * plane] = prev[l];
-        }
+        prev = fmaT(-mtab[(size_t)k * ts + tb], prev, ldp<CG>(d + (size_t)k * plane));
+        d[(size_t)k * plane] = prev;
     }
-    const T ibt = ibtab[(size_t)(nz - 1) * ts + tb];
-#pragma unroll
-    for (int l = 0; l < NL; ++l) {
-        prev[l] = mulT(prev[l], ibt);
-        d[l][(size_t)(nz - 1) * plane] = prev[l];
-    }
+    prev = mulT(prev, ibtab[(size_t)(nz - 1) * ts + tb]);
+    d[(size_t)(nz - 1) * plane] = prev;
     k = nz - 2;
-    for (; k - THOMAS_U + 1 >= 0; k -= THOMAS_U) {
-        T dv[NL][THOMAS_U], iv[THOMAS_U], cv[THOMAS_U];
+    for (; k - U + 1 >= 0; k -= U) {
+        T dv[U], iv[U], cv[U];
 #pragma unroll
-        for (int q = 0; q < THOMAS_U; ++q) {
+        for (int q = 0; q < U; ++q) {
             iv[q] = ibtab[(size_t)(k - q) * ts + tb];
             cv[q] = cup[k - q];
-#pragma unroll
-            for (int l = 0; l < NL; ++l) dv[l][q] = ldp<CG>(d[l] + (size_t)(k - q) * plane);
+            dv[q] = ldp<CG>(d + (size_t)(k - q) * plane);
         }
 #pragma unroll
-        for (int q = 0; q < THOMAS_U; ++q)
-#pragma unroll
-            for (int l = 0; l < NL; ++l) {
-                prev[l] = mulT(fmaT(-cv[q], prev[l], dv[l][q]), iv[q]);
-                d[l][(size_t)(k - q) * plane] = prev[l];
-            }
+        for (int q = 0; q < U; ++q) {
+            prev = mulT(fmaT(-cv[q], prev, dv[q]), iv[q]);
+            d[(size_t)(k - q) * plane] = prev;
+        }
     }
     for (; k >= 0; --k) {
-        const T ib = ibtab[(size_t)k * ts + tb], c = cup[k];
-#pragma unroll
-        for (int l = 0; l < NL; ++l) {
-            prev[l] = mulT(fmaT(-c, prev[l], ldp<CG>(d[l] + (size_t)k * plane)), ib);
-            d[l][(size_t)k * plane] = prev[l];
-        }
+        prev = mulT(fmaT(-cup[k], prev, ldp<CG>(d + (size_t)k * plane)), ibtab[(size_t)k * ts + tb]);
+        d[(size_t)k * plane] = prev;
     }
 }
 
-// Lines are numbered line = t + TT*j with TT = nx/2+1 x-pairs (periodic x) or
-// nx (wall x); one virtual block covers lines line_base .. line_base +
-// blockDim - 1.  Warp 0 of the block holding line 0 first solves the singular
-// (0,0) line.  ASYNC: cp.async ring in shared memory (ring must hold
-// THOMAS_S*3*blockDim values); otherwise register prefetch.
+// Lines are numbered line = i + nx*j (one thread each); one virtual block
+// covers lines line_base .. line_base + blockDim - 1.  Warp 0 of the block
+// holding line 0 first solves the singular (0,0) line.  Both half-complex
+// slots i and nx-i of a periodic direction use the table of wavenumber
+// min(i, nx-i).  ASYNC: shared-memory ring (THOMAS_S*2*blockDim values);
+// otherwise register prefetch.
 template <typename T, bool ASYNC, bool CG>
 __device__ __forceinline__ void thomas_body(const GridDev &g, int Ux, int Uy, const T *mtab,
                                             const T *ibtab, const T *cup, T *data, const int *conv,
@@ -894,26 +885,16 @@ __device__ __forceinline__ void thomas_body(const GridDev &g, int Ux, int Uy, co
         singular_line_warp<T, CG>(g, data, plane);  // line (0,0)
         if (threadIdx.x == 0) return;
     }
-    const int TT = (g.bcx == BC_PERIODIC) ? g.nx / 2 + 1 : g.nx;
     const int line = line_base + threadIdx.x;
-    if (line >= TT * g.ny) return;
-    const int j = line / TT, t = line - j * TT;
-    int i1 = t, i2 = -1;
-    if (g.bcx == BC_PERIODIC && t > 0 && 2 * t != g.nx) i2 = g.nx - t;
-    const int ux = i1;  // periodic: i1 <= nx/2 is already the distinct index
+    if (line >= g.nx * g.ny) return;
+    const int j = line / g.nx, i = line - j * g.nx;
+    const int ux = (g.bcx == BC_PERIODIC) ? min(i, g.nx - i) : i;
     const int uy = (g.bcy == BC_PERIODIC) ? min(j, g.ny - j) : j;
     const size_t tb = (size_t)uy * Ux + ux;
     const size_t ts = (size_t)Ux * Uy;
-    T *d1 = data + (size_t)j * g.nx + i1;
-    T *d2 = data + (size_t)j * g.nx + (i2 >= 0 ? i2 : i1);
-    const int nz = g.nz;
-    if (ASYNC) {
-        if (i2 >= 0) thomas_lines<T, 2>(nz, plane, d1, d2, ts, tb, mtab, ibtab, cup, ring);
-        else thomas_lines<T, 1>(nz, plane, d1, d1, ts, tb, mtab, ibtab, cup, ring);
-    } else {
-        if (i2 >= 0) thomas_lines_reg<T, 2, CG, 4>(nz, plane, d1, d2, ts, tb, mtab, ibtab, cup);
-        else thomas_lines_reg<T, 1, CG, 4>(nz, plane, d1, d1, ts, tb, mtab, ibtab, cup);
-    }
+    T *d = data + line;
+    if (ASYNC) thomas_line_ring<T>(g.nz, plane, d, ts, tb, mtab, ibtab, cup, ring);
+    else thomas_line_reg<T, CG>(g.nz, plane, d, ts, tb, mtab, ibtab, cup);
 }
 
 template <typename T>
@@ -928,7 +909,7 @@ __global__ void __launch_bounds__(THOMAS_BLOCK) k_thomas(GridDev g, int Ux, int 
 }
 
 template <typename T> constexpr size_t thomas_smem() {
-    return (size_t)THOMAS_S * 3 * THOMAS_BLOCK * sizeof(T);
+    return (size_t)THOMAS_S * 2 * THOMAS_BLOCK * sizeof(T);
 }
 
 // u = q' - (dt/rho0) G p on non-wall faces (q' = dt q); wall faces 0.
