@@ -53,11 +53,12 @@ def measured_peaks():
         return HBM_PEAK_FALLBACK, "fallback"
 
 
-def measured_traffic(kernel):
+def measured_traffic(kernel, mixed):
     """DRAM bytes per launch of a kernel from the committed ncu summaries
     (lines 'traffic_per_launch_bytes <kernel> <bytes>' in profiles/*.md)."""
     import glob
-    name = {"flux": "k_flux", "resid_fwdx": "k_xfwd_resid", "div_fwdx": "k_xfwd"}.get(kernel, kernel)
+    name = {"flux": "k_flux", "resid_fwdx": "k_xfwd_resid",
+            "div_fwdx": "k_xfwd_mix" if mixed else "k_xfwd_f64"}.get(kernel, kernel)
     for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
         for line in open(path):
             parts = line.split()
@@ -69,15 +70,17 @@ def measured_traffic(kernel):
 def algorithmic_per_point(nx, ny, mixed):
     """Algorithmic HBM bytes and FP64 flops (FMA = 2) per grid point of each
     kernel of one projection.  Transform passes use the conventional real-FFT
-    count 2.5 log2(n) flops per point (FP64 passes only)."""
+    count 2.5 log2(n) flops per point (FP64 passes only).  The split-term flux
+    counts 32: per face t, s', the Newton quotient (2 FMA), dphat and the
+    final FMA (10 flops), times 3, plus phat = 2p^n - p^(n-1)."""
     lx, ly = 2.5 * math.log2(nx), 2.5 * math.log2(ny)
     if not mixed:
         return {
-            "flux": (72, 47), "div_fwdx": (32, 8 + lx), "fwd_y": (16, ly), "thomas": (16, 5),
+            "flux": (72, 32), "div_fwdx": (32, 8 + lx), "fwd_y": (16, ly), "thomas": (16, 5),
             "inv_y": (16, ly), "inv_x": (16, lx), "correct": (56, 12)}
     return {
-        "flux": (72, 47), "div_fwdx": (36, 8), "fwd_y": (8, 0), "thomas": (8, 0), "inv_y": (8, 0),
-        "inv_x": (12, 0), "resid_fwdx": (20, 17), "fwd_y_refine": (8, 0), "thomas_refine": (8, 0),
+        "flux": (72, 32), "div_fwdx": (36, 8), "fwd_y": (8, 0), "thomas": (8, 0), "inv_y": (8, 0),
+        "inv_x": (12, 0), "resid_fwdx": (20, 14), "fwd_y_refine": (8, 0), "thomas_refine": (8, 0),
         "inv_y_refine": (8, 0), "inv_x_update": (20, 1), "resid_check": (16, 17), "correct": (56, 12)}
 
 
@@ -216,12 +219,22 @@ def run_fizzy(args):
     stream = torch.cuda.current_stream()
 
     def timed_run(precision, steps, warmup, per_kernel):
+        """W warm-up solves; with per_kernel, a short breakdown run with every
+        kernel bracketed by events picks the dominant kernel; then the timed
+        region of `steps` solves, in which only the dominant kernel's launches
+        carry events (its live average duration feeds the roofline)."""
         plan = F.Plan.for_case(case, precision=precision)
         for _ in range(warmup):
             plan.solve(phi, pn, pnm1, u, v, w, p, stream=stream)
         torch.cuda.synchronize()
+        breakdown, dom = {}, None
         if per_kernel:
             plan.set_timing(True)
+            for _ in range(max(3, steps // 5)):
+                plan.solve(phi, pn, pnm1, u, v, w, p, stream=stream)
+            breakdown = plan.timing()
+            dom = max(breakdown, key=lambda k: breakdown[k][0])
+            plan.set_timing(True, only=dom)
         if dist:
             dist.barrier()
         torch.cuda.synchronize()
@@ -234,15 +247,15 @@ def run_fizzy(args):
         if dist:
             dist.barrier()
         ms = e0.elapsed_time(e1)
-        kern = plan.timing() if per_kernel else {}
+        live = plan.timing().get(dom) if dom else None
         st = plan.stats(stream)
         launches = plan.launches_per_solve() * steps
         plan.close()
-        return ms, kern, st, launches
+        return ms, (breakdown, dom, live, plan.max_refine), st, launches
 
     clocks = ClockSampler()
     clocks.start()
-    ms, kern, st, launches = timed_run(prec, args.steps, args.warmup, True)
+    ms, (kern, dom, live, max_refine), st, launches = timed_run(prec, args.steps, args.warmup, True)
     clk = clocks.stop()
     if dist:
         t = torch.tensor([ms], device="cuda")
@@ -258,17 +271,24 @@ def run_fizzy(args):
     # roofline of the dominant kernel
     hbm_peak, hbm_src = measured_peaks()
     per_pt = algorithmic_per_point(spec.nx, spec.ny, prec == F.MIXED)
-    dom = max(kern, key=lambda k: kern[k][0]) if kern else None
     roof = None
-    if dom:
-        tot_ms, cnt = kern[dom]
+    if dom and live:
+        tot_ms, cnt = live  # the dominant kernel inside the timed region
+        # refinement kernels return at once after convergence: count only the
+        # launches that did the pass (from the solve's sweep count)
+        it, mr = st["iterations"], max_refine
+        per_solve = {"resid_fwdx": min(it + 1, mr), "fwd_y_refine": it, "thomas_refine": it,
+                     "inv_y_refine": it, "inv_x_update": it}.get(dom)
+        if per_solve is not None:
+            cnt = max(1, per_solve * args.steps)
         avg_s = tot_ms / cnt / 1e3
         b_pt, fl_pt = per_pt.get(dom, (0, 0))
         gbs = b_pt * npts / avg_s / 1e9
         tfl = fl_pt * npts / avg_s / 1e12
         t_hbm = b_pt / (hbm_peak * 1e9)
         t_alu = fl_pt / (FP64_PEAK_NOMINAL * 1e12)
-        traffic = measured_traffic(dom) if (spec.nx, spec.ny, spec.nz) == (256, 256, 256) else None
+        traffic = (measured_traffic(dom, prec == F.MIXED)
+                   if (spec.nx, spec.ny, spec.nz) == (256, 256, 256) else None)
         if t_alu > t_hbm:
             roof = {"bound": "alu", "achieved": tfl, "peak": FP64_PEAK_NOMINAL, "unit": "TFLOP/s",
                     "frac": tfl / FP64_PEAK_NOMINAL, "traffic": traffic, "kernel": dom,
@@ -279,6 +299,9 @@ def run_fizzy(args):
             roof = {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
                     "frac": gbs / hbm_peak, "traffic": traffic, "kernel": dom,
                     "algorithmic_bytes": b_pt * npts, "peak_source": hbm_src}
+    if roof:
+        roof["launches_timed"] = cnt
+        roof["duration_ms"] = tot_ms / cnt
     kernels = {k: {"ms_avg": v[0] / v[1], "launches": v[1],
                    "share": v[0] / max(1e-9, sum(x[0] for x in kern.values()))} for k, v in kern.items()}
 

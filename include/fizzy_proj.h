@@ -69,6 +69,7 @@ enum {
 
 /* Maximum x/y extent of one transform line. */
 #define FIZZY_MAX_N 1024
+#define FIZZY_DEFAULT_MAX_REFINE 4  /* refinement sweeps when max_refine = 0 */
 
 /* Plan descriptor.  All fields are read at plan time only. */
 typedef struct fizzy_proj_desc {
@@ -81,7 +82,7 @@ typedef struct fizzy_proj_desc {
     double dt;            /* time step (> 0)                                                    */
     int precision;        /* FIZZY_PREC_FP64 or FIZZY_PREC_MIXED                                */
     double tol;           /* mixed: stop when max|f - L p| / max|f| <= tol (0 -> 1e-10)         */
-    int max_refine;       /* mixed: at most this many refinement sweeps (0 -> 4, max 16)        */
+    int max_refine;       /* mixed: at most this many sweeps (0 -> FIZZY_DEFAULT_MAX_REFINE, max 16) */
     double div_tol;       /* mixed: also stop only when max|D u| dx / U <= div_tol, with U the   */
                           /* rms of u* and D u = (dt/rho0)(f - L p) (0 -> 1e-10; < 0 -> off)    */
     unsigned flags;       /* FIZZY_FLAG_*                                                       */
@@ -151,12 +152,15 @@ const char *fizzy_proj_last_error(fizzy_proj_plan_t p);
 /* Number of kernels one fizzy_proj_solve launches on the plan (for launch accounting). */
 int fizzy_proj_launches_per_solve(fizzy_proj_plan_t p);
 
-/* Per-kernel timing (diagnostics).  While enabled, every kernel launch of a
- * solve is bracketed by CUDA events recorded on the solve's stream (up to 8192
- * launches are kept; later ones are not timed).  fizzy_proj_timing() waits for
- * the recorded events, folds them into per-kernel totals and reports kernel
- * slot idx: its name, total milliseconds and launch count since the last
- * reset (enable = 1 resets).  Returns the number of slots, or a negative code. */
+/* Per-kernel timing (diagnostics).  enable = 1: every kernel launch of a
+ * solve is bracketed by CUDA events recorded on the solve's stream; enable =
+ * 2 + idx: only the launches of kernel slot idx are (two events per launch,
+ * so the rest of the solve runs undisturbed); 0: off.  Up to 8192 launches
+ * are kept; later ones are not timed.  Every call resets the totals.
+ * fizzy_proj_timing() waits for the recorded events, folds them into
+ * per-kernel totals and reports kernel slot idx: its name, total
+ * milliseconds and launch count since the last reset.  Both return the
+ * number of slots (set_timing: FIZZY_OK), or a negative code. */
 int fizzy_proj_set_timing(fizzy_proj_plan_t p, int enable);
 int fizzy_proj_timing(fizzy_proj_plan_t p, int idx, const char **name, double *ms, int *launches);
 

@@ -83,6 +83,7 @@ class Plan:
         if rc != 0:
             raise FizzyError(rc)
         self._h = h
+        self.max_refine = int(max_refine) if max_refine > 0 else _abi.DEFAULT_MAX_REFINE
 
     @classmethod
     def for_case(cls, case, precision=FP64, check=False, **kw):
@@ -123,8 +124,24 @@ class Plan:
         self._check(_abi.lib().fizzy_proj_get_stats(self._h, ctypes.byref(st), _stream_handle(stream)))
         return st.as_dict()
 
-    def set_timing(self, enable: bool):
-        self._check(_abi.lib().fizzy_proj_set_timing(self._h, 1 if enable else 0))
+    def set_timing(self, enable: bool, only: str | None = None):
+        """Per-kernel CUDA-event timing: all kernels, or only the kernel slot
+        named `only` (two events per launch of that kernel)."""
+        mode = 0
+        if enable:
+            mode = 1 if only is None else 2 + self.slot_names().index(only)
+        self._check(_abi.lib().fizzy_proj_set_timing(self._h, mode))
+
+    def slot_names(self):
+        L = _abi.lib()
+        n = L.fizzy_proj_timing(self._h, -1, None, None, None)
+        self._check(min(n, 0))
+        names = []
+        for idx in range(n):
+            name = ctypes.c_char_p()
+            L.fizzy_proj_timing(self._h, idx, ctypes.byref(name), None, None)
+            names.append(name.value.decode())
+        return names
 
     def timing(self):
         """{kernel name: (total ms, launches)} accumulated since set_timing(True)."""

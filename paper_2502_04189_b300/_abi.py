@@ -23,6 +23,7 @@ EXPORTED = ("fizzy_proj_plan", "fizzy_proj_workspace_bytes", "fizzy_proj_solve",
             "fizzy_serve_info", "fizzy_serve_destroy")
 ERRORS[-7] = "busy"
 NOALLOC_MAX_CELLS = 262144
+DEFAULT_MAX_REFINE = 4  # FIZZY_DEFAULT_MAX_REFINE
 
 
 class Desc(ctypes.Structure):

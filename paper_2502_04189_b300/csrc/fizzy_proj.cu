@@ -348,7 +348,7 @@ int fizzy_proj_plan(fizzy_proj_plan_t *out, const fizzy_proj_desc *d, void *stre
     p->mixed = d->precision == FIZZY_PREC_MIXED;
     p->check = (d->flags & FIZZY_FLAG_CHECK) ? 1 : 0;
     p->tol = d->tol > 0 ? d->tol : 1e-10;
-    p->max_refine = d->max_refine > 0 ? d->max_refine : 4;
+    p->max_refine = d->max_refine > 0 ? d->max_refine : FIZZY_DEFAULT_MAX_REFINE;
     p->div_tol = d->div_tol > 0 ? d->div_tol : (d->div_tol < 0 ? -1.0 : 1e-10);
     const int nx = d->nx, ny = d->ny, nz = d->nz;
     const size_t N = (size_t)nx * ny * nz;
@@ -581,7 +581,7 @@ int fizzy_proj_get_stats(fizzy_proj_plan_t p, fizzy_proj_stats *st, void *stream
 }
 
 static inline void tmark(fizzy_proj_plan_t p, int slot, cudaStream_t s, bool begin) {
-    if (!p->timing) return;
+    if (!p->timing || (p->timing >= 2 && slot != p->timing - 2)) return;
     if (begin) {
         if (p->ev_used >= kMaxTimed) return;
         cudaEventRecord(p->ev[2 * p->ev_used], s);
@@ -600,7 +600,7 @@ static inline void tmark(fizzy_proj_plan_t p, int slot, cudaStream_t s, bool beg
     } while (0)
 
 int fizzy_proj_set_timing(fizzy_proj_plan_t p, int enable) {
-    if (!p) return FIZZY_ERR_INVALID;
+    if (!p || enable < 0 || enable >= 2 + KS_N) return FIZZY_ERR_INVALID;
     if (enable && p->ev.empty()) {
         p->ev.resize(2 * kMaxTimed);
         p->ev_slot.assign(kMaxTimed, -1);
@@ -609,7 +609,7 @@ int fizzy_proj_set_timing(fizzy_proj_plan_t p, int enable) {
             if (r != cudaSuccess) return cuda_err(p, r, "event create");
         }
     }
-    p->timing = enable ? 1 : 0;
+    p->timing = enable;
     p->ev_used = 0;
     for (int k = 0; k < KS_N; ++k) {
         p->t_ms[k] = 0.0;

@@ -667,7 +667,7 @@ __global__ void __launch_bounds__(256) k_xinv(GridDev g, FFTDesc D, int L, const
 // dzf-weighted mean (the pressure gauge).
 constexpr int THOMAS_S = 16;      // ring stages: planes in flight per line
 constexpr int THOMAS_U = 4;       // planes per block of the recurrence
-constexpr int THOMAS_BLOCK = 64;
+constexpr int THOMAS_BLOCK = 32;
 
 // One z-line per thread (forward elimination y_k = f_k - m_k y_(k-1), back
 // substitution p_k = (y_k - c_k p_(k+1)) / beta_k, the factors m_k and
