@@ -8,6 +8,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
+#include <cstdint>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -137,27 +138,71 @@ void fill_stages(FFTDesc &d, int n) {
     }
 }
 
-// exp(-2 pi i t / n) and (cos, sin)(pi m / (2n)) in long double, rounded once.
-void make_fft_tables(int n, std::vector<double> &tw, std::vector<double> &cs) {
+// Twiddle table entry t of length n in the form the Stockham stages use
+// (kern_fft.cuh, tw_apply): w = exp(-2 pi i t / n) = c + i s is stored as
+// (m, tau) with w = m (1 + i tau) when |c| >= |s| (R = 0) and
+// w = i m (1 + i tau) otherwise (R = 1); R goes into the lowest mantissa bit
+// of tau.  Computed in long double and rounded once.
+void tw_entry(int n, int t, long double &m, long double &tau, int &R) {
     const long double pi = 3.141592653589793238462643383279502884L;
-    tw.resize(2 * (size_t)n);
+    const long double a = 2.0L * pi * (long double)t / (long double)n;
+    const long double c = cosl(a), sn = -sinl(a);
+    if (fabsl(c) >= fabsl(sn)) {
+        R = 0;
+        m = c;
+        tau = sn / c;
+    } else {
+        R = 1;
+        m = sn;
+        tau = -c / sn;
+    }
+}
+double tw_tau64(long double tau, int R) {
+    double v = (double)tau;
+    uint64_t b;
+    memcpy(&b, &v, 8);
+    b = (b & ~1ull) | (uint64_t)R;
+    memcpy(&v, &b, 8);
+    return v;
+}
+float tw_tau32(long double tau, int R) {
+    float v = (float)tau;
+    uint32_t b;
+    memcpy(&b, &v, 4);
+    b = (b & ~1u) | (uint32_t)R;
+    memcpy(&v, &b, 4);
+    return v;
+}
+
+// Twiddles (n entries (m, tau)) and DCT post-twiddles (cos, sin)(pi m/(2n)),
+// m = 0..n/2 (n/2+2 entries), into caller buffers; tw32/cs32 optional FP32 copies.
+void fill_fft_tables(int n, double *tw, double *cs, float *tw32 = nullptr, float *cs32 = nullptr) {
+    const long double pi = 3.141592653589793238462643383279502884L;
     for (int t = 0; t < n; ++t) {
-        const long double a = 2.0L * pi * (long double)t / (long double)n;
-        tw[2 * t] = (double)cosl(a);
-        tw[2 * t + 1] = (double)(-sinl(a));
+        long double m, tau;
+        int R;
+        tw_entry(n, t, m, tau, R);
+        tw[2 * t] = (double)m;
+        tw[2 * t + 1] = tw_tau64(tau, R);
+        if (tw32) {
+            tw32[2 * t] = (float)m;
+            tw32[2 * t + 1] = tw_tau32(tau, R);
+        }
     }
-    cs.resize(2 * (size_t)(n / 2 + 2), 0.0);
-    for (int m = 0; m <= n / 2; ++m) {
-        const long double a = pi * (long double)m / (2.0L * (long double)n);
-        cs[2 * m] = (double)cosl(a);
-        cs[2 * m + 1] = (double)sinl(a);
+    for (int k = 0; k < n / 2 + 2; ++k) cs[2 * k] = cs[2 * k + 1] = 0.0;
+    for (int k = 0; k <= n / 2; ++k) {
+        const long double a = pi * (long double)k / (2.0L * (long double)n);
+        cs[2 * k] = (double)cosl(a);
+        cs[2 * k + 1] = (double)sinl(a);
     }
+    if (cs32)
+        for (int k = 0; k < 2 * (n / 2 + 2); ++k) cs32[k] = (float)cs[k];
 }
 
 int build_fft(fizzy_proj_plan_t p, int n, int bc, FFTHost &F, int *status) {
-    std::vector<double> tw, cs;
-    make_fft_tables(n, tw, cs);
-    std::vector<float> tw32(tw.begin(), tw.end()), cs32(cs.begin(), cs.end());
+    std::vector<double> tw(2 * (size_t)n), cs(2 * (size_t)(n / 2 + 2));
+    std::vector<float> tw32(tw.size()), cs32(cs.size());
+    fill_fft_tables(n, tw.data(), cs.data(), tw32.data(), cs32.data());
     F.tw64 = dev_alloc<double>(p, tw.size(), status);
     F.cs64 = dev_alloc<double>(p, cs.size(), status);
     if (p->mixed) {
@@ -799,23 +844,6 @@ static double g_noalloc_host[2 * (size_t)kNaMaxCells + (kNaZTabs + 1) * (size_t)
                             2 * (kNaTw + kNaCs)];
 // Device address of the scratch per device ordinal (0 = not looked up yet).
 static double *g_noalloc_dev[256];
-
-// Twiddle and cos/sin tables written straight into a caller buffer (the same
-// values as make_fft_tables, without host heap temporaries).
-void fill_fft_tables(int n, double *tw, double *cs) {
-    const long double pi = 3.141592653589793238462643383279502884L;
-    for (int t = 0; t < n; ++t) {
-        const long double a = 2.0L * pi * (long double)t / (long double)n;
-        tw[2 * t] = (double)cosl(a);
-        tw[2 * t + 1] = (double)(-sinl(a));
-    }
-    for (int m = 0; m < n / 2 + 2; ++m) cs[2 * m] = cs[2 * m + 1] = 0.0;
-    for (int m = 0; m <= n / 2; ++m) {
-        const long double a = pi * (long double)m / (2.0L * (long double)n);
-        cs[2 * m] = (double)cosl(a);
-        cs[2 * m + 1] = (double)sinl(a);
-    }
-}
 
 }  // namespace
 

@@ -15,7 +15,8 @@
 //    folds 1/(4 nx ny) into the right-hand side.
 //  * The complex FFT is a Stockham autosort (self-sorting) mixed-radix
 //    (4, 2, 3) FFT in shared memory with ping-pong buffers and one barrier per
-//    stage; twiddles come from a per-plan table staged into shared memory.
+//    stage; twiddles come from a per-plan table staged into shared memory,
+//    in the FMA-friendly form described at tw_apply.
 #pragma once
 #include "kern_common.cuh"
 
@@ -36,7 +37,7 @@ struct FFTDesc {
     int kind;        // KIND_PERIODIC or KIND_DCT
     int rad[FFT_MAX_STAGES], m[FFT_MAX_STAGES], ns[FFT_MAX_STAGES], twq[FFT_MAX_STAGES];
     unsigned rm[FFT_MAX_STAGES], rns[FFT_MAX_STAGES];
-    const void *tw;  // n complex: exp(-2 pi i t / n)          (T2 of the kernel's type)
+    const void *tw;  // n entries (m, tau) of exp(-2 pi i t / n), see tw_apply (T2)
     const void *cs;  // n/2+1 complex: (cos, sin)(pi m / (2 n)) (T2)
 };
 
@@ -49,18 +50,52 @@ __device__ __forceinline__ int line_pos(int i, int n, int kind) {
     return (kind == KIND_DCT) ? ((i & 1) ? n - 1 - (i >> 1) : (i >> 1)) : i;
 }
 
+// Twiddle factors are stored in an FMA-friendly form: for w = c + i s the
+// table entry is (m, tau) with
+//     w = m (1 + i tau)       (R = 0, |c| >= |s|: m = c, tau = s/c)
+//     w = i m (1 + i tau)     (R = 1, |c| <  |s|: m = s, tau = -c/s)
+// so |tau| <= 1, and R is kept in the lowest mantissa bit of tau (a
+// perturbation of at most one unit in the last place).  Multiplying x by w
+// (or by conj(w) for the inverse) is then z = x (1 +- i tau) (2 FMAs)
+// followed by a scale by m that folds into the FMAs of the butterfly: the
+// product is (mr * za, mi * zb) with (za, zb) = (z.re, z.im) or (z.im, z.re)
+// and (mr, mi) = (+-m, +-m).  A radix-4 butterfly with its three twiddles
+// (w3 = w1 w2: c = w1 (x1 + w2 x3), d = w1 (x1 - w2 x3)) costs 24 FMAs
+// instead of 12 multiply-adds for the twiddles and 16 adds; radix 2 costs 6
+// instead of 8.
+template <typename T> struct TwApplied {
+    T za, zb, mr, mi;  // w x = (mr za, mi zb)
+};
+
+__device__ __forceinline__ bool tw_rot(double tau) { return __double2loint(tau) & 1; }
+__device__ __forceinline__ bool tw_rot(float tau) { return __float_as_uint(tau) & 1u; }
+__device__ __forceinline__ double flip_sign(double v, bool f) {
+    return __hiloint2double(__double2hiint(v) ^ (f ? (int)0x80000000 : 0), __double2loint(v));
+}
+__device__ __forceinline__ float flip_sign(float v, bool f) {
+    return __uint_as_float(__float_as_uint(v) ^ (f ? 0x80000000u : 0u));
+}
+
+// x times w (INV: times conj(w)); w = (m, tau) from the table.
 template <typename T, bool INV>
-__device__ __forceinline__ void twiddle(typename C2<T>::t &x, typename C2<T>::t w) {
-    T r, i;
-    if (!INV) {
-        r = fmaT(x.x, w.x, -mulT(x.y, w.y));
-        i = fmaT(x.x, w.y, mulT(x.y, w.x));
-    } else {
-        r = fmaT(x.x, w.x, mulT(x.y, w.y));
-        i = fmaT(x.y, w.x, -mulT(x.x, w.y));
+__device__ __forceinline__ TwApplied<T> tw_apply(typename C2<T>::t x, typename C2<T>::t w) {
+    const T m = w.x, tau = w.y;
+    const bool R = tw_rot(tau);
+    T zr, zi;
+    if (!INV) {  // x (1 + i tau)
+        zr = fmaT(-tau, x.y, x.x);
+        zi = fmaT(tau, x.x, x.y);
+    } else {     // x (1 - i tau)
+        zr = fmaT(tau, x.y, x.x);
+        zi = fmaT(-tau, x.x, x.y);
     }
-    x.x = r;
-    x.y = i;
+    TwApplied<T> o;
+    o.za = R ? zi : zr;
+    o.zb = R ? zr : zi;
+    // R = 1: i m z = (-m zi, m zr); inverse: -i m z = (m zi, -m zr)
+    o.mr = flip_sign(m, R && !INV);
+    o.mi = flip_sign(m, R && INV);
+    return o;
 }
 
 // One Stockham stage over L lines (line stride ls) from src to dst.
@@ -79,35 +114,63 @@ __device__ __forceinline__ void stockham_stage(const typename C2<T>::t *__restri
         T2 *out = dst + l * ls + (b - j) * R + j;
         const int ts = j * twq;
         if (R == 4) {
-            T2 x0 = in[0], x1 = in[m], x2 = in[2 * m], x3 = in[3 * m];
-            if (Ns > 1) {
-                twiddle<T, INV>(x1, tw[ts]);
-                twiddle<T, INV>(x2, tw[2 * ts]);
-                twiddle<T, INV>(x3, tw[3 * ts]);
-            }
-            const T ar = x0.x + x2.x, ai = x0.y + x2.y;
-            const T br = x0.x - x2.x, bi = x0.y - x2.y;
-            const T cr = x1.x + x3.x, ci = x1.y + x3.y;
-            const T dr = x1.x - x3.x, di = x1.y - x3.y;
-            out[0] = mk2(ar + cr, ai + ci);
-            out[2 * Ns] = mk2(ar - cr, ai - ci);
-            if (!INV) {  // y1 = b - i d, y3 = b + i d
-                out[Ns] = mk2(br + di, bi - dr);
-                out[3 * Ns] = mk2(br - di, bi + dr);
-            } else {     // y1 = b + i d, y3 = b - i d
-                out[Ns] = mk2(br - di, bi + dr);
-                out[3 * Ns] = mk2(br + di, bi - dr);
+            const T2 x0 = in[0], x1 = in[m], x2 = in[2 * m], x3 = in[3 * m];
+            if (Ns == 1) {  // no twiddles
+                const T ar = x0.x + x2.x, ai = x0.y + x2.y;
+                const T br = x0.x - x2.x, bi = x0.y - x2.y;
+                const T cr = x1.x + x3.x, ci = x1.y + x3.y;
+                const T dr = x1.x - x3.x, di = x1.y - x3.y;
+                out[0] = mk2(ar + cr, ai + ci);
+                out[2 * Ns] = mk2(ar - cr, ai - ci);
+                if (!INV) {  // y1 = b - i d, y3 = b + i d
+                    out[Ns] = mk2(br + di, bi - dr);
+                    out[3 * Ns] = mk2(br - di, bi + dr);
+                } else {     // y1 = b + i d, y3 = b - i d
+                    out[Ns] = mk2(br - di, bi + dr);
+                    out[3 * Ns] = mk2(br + di, bi - dr);
+                }
+            } else {
+                const T2 w1 = tw[ts], w2 = tw[2 * ts];
+                // a, b = x0 +- w2 x2;  e, f = x1 +- w2 x3
+                const TwApplied<T> X2 = tw_apply<T, INV>(x2, w2);
+                const T ar = fmaT(X2.mr, X2.za, x0.x), ai = fmaT(X2.mi, X2.zb, x0.y);
+                const T br = fmaT(-X2.mr, X2.za, x0.x), bi = fmaT(-X2.mi, X2.zb, x0.y);
+                const TwApplied<T> X3 = tw_apply<T, INV>(x3, w2);
+                T2 e, f;
+                e.x = fmaT(X3.mr, X3.za, x1.x);
+                e.y = fmaT(X3.mi, X3.zb, x1.y);
+                f.x = fmaT(-X3.mr, X3.za, x1.x);
+                f.y = fmaT(-X3.mi, X3.zb, x1.y);
+                // c = w1 e, d = w1 f;  y0, y2 = a +- c
+                const TwApplied<T> C = tw_apply<T, INV>(e, w1);
+                out[0] = mk2(fmaT(C.mr, C.za, ar), fmaT(C.mi, C.zb, ai));
+                out[2 * Ns] = mk2(fmaT(-C.mr, C.za, ar), fmaT(-C.mi, C.zb, ai));
+                const TwApplied<T> D = tw_apply<T, INV>(f, w1);  // d = (D.mr D.za, D.mi D.zb)
+                if (!INV) {  // y1 = b - i d, y3 = b + i d
+                    out[Ns] = mk2(fmaT(D.mi, D.zb, br), fmaT(-D.mr, D.za, bi));
+                    out[3 * Ns] = mk2(fmaT(-D.mi, D.zb, br), fmaT(D.mr, D.za, bi));
+                } else {     // y1 = b + i d, y3 = b - i d
+                    out[Ns] = mk2(fmaT(-D.mi, D.zb, br), fmaT(D.mr, D.za, bi));
+                    out[3 * Ns] = mk2(fmaT(D.mi, D.zb, br), fmaT(-D.mr, D.za, bi));
+                }
             }
         } else if (R == 2) {
-            T2 x0 = in[0], x1 = in[m];
-            if (Ns > 1) twiddle<T, INV>(x1, tw[ts]);
-            out[0] = mk2(x0.x + x1.x, x0.y + x1.y);
-            out[Ns] = mk2(x0.x - x1.x, x0.y - x1.y);
+            const T2 x0 = in[0], x1 = in[m];
+            if (Ns == 1) {
+                out[0] = mk2(x0.x + x1.x, x0.y + x1.y);
+                out[Ns] = mk2(x0.x - x1.x, x0.y - x1.y);
+            } else {
+                const TwApplied<T> X1 = tw_apply<T, INV>(x1, tw[ts]);
+                out[0] = mk2(fmaT(X1.mr, X1.za, x0.x), fmaT(X1.mi, X1.zb, x0.y));
+                out[Ns] = mk2(fmaT(-X1.mr, X1.za, x0.x), fmaT(-X1.mi, X1.zb, x0.y));
+            }
         } else {  // R == 3
             T2 x0 = in[0], x1 = in[m], x2 = in[2 * m];
             if (Ns > 1) {
-                twiddle<T, INV>(x1, tw[ts]);
-                twiddle<T, INV>(x2, tw[2 * ts]);
+                const TwApplied<T> X1 = tw_apply<T, INV>(x1, tw[ts]);
+                const TwApplied<T> X2 = tw_apply<T, INV>(x2, tw[2 * ts]);
+                x1 = mk2(mulT(X1.mr, X1.za), mulT(X1.mi, X1.zb));
+                x2 = mk2(mulT(X2.mr, X2.za), mulT(X2.mi, X2.zb));
             }
             const T h = (T)0.86602540378443864676;  // sqrt(3)/2
             const T sr = x1.x + x2.x, si = x1.y + x2.y;
