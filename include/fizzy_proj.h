@@ -73,7 +73,9 @@ enum {
 
 /* Plan descriptor.  All fields are read at plan time only. */
 typedef struct fizzy_proj_desc {
-    int nx, ny, nz;       /* cells; nx, ny in [2, FIZZY_MAX_N] with prime factors 2 and 3 only; nz >= 2 */
+    int nx, ny, nz;       /* cells; nx, ny in [2, FIZZY_MAX_N] with prime factors 2 and 3 only;
+                             nz >= 2; nx*ny*nz <= 4e9 and ny*ny*nz < 2^32, else
+                             FIZZY_ERR_UNSUPPORTED                                              */
     double dx, dy;        /* uniform x and y spacing (> 0)                                     */
     double dz;            /* uniform z spacing (> 0), used when zf == NULL                      */
     const double *zf;     /* host array of nz+1 increasing z face coordinates, or NULL          */

@@ -136,6 +136,8 @@ void fill_stages(FFTDesc &d, int n) {
         d.rns[s] = ns > 1 ? (unsigned)((1ull << 32) / (unsigned)ns + 1) : 0u;
         ns *= d.rad[s];
     }
+    d.rn = (unsigned)((1ull << 32) / (unsigned)n + 1);
+    d.rM = (unsigned)((1ull << 32) / (unsigned)(n / 2 + 1) + 1);
 }
 
 // Twiddle table entry t of length n in the form the Stockham stages use
@@ -256,6 +258,9 @@ int validate(const fizzy_proj_desc *d) {
     if (!radix23(d->nx) || !radix23(d->ny)) return FIZZY_ERR_UNSUPPORTED;
     if (d->nx > FIZZY_MAX_N || d->ny > FIZZY_MAX_N) return FIZZY_ERR_UNSUPPORTED;
     if ((double)d->nx * d->ny * d->nz > 4.0e9) return FIZZY_ERR_UNSUPPORTED;
+    // the (y, z) line index is split by a multiply-high division by ny, exact
+    // below 2^32 / ny
+    if ((double)d->ny * d->ny * d->nz >= 4294967296.0) return FIZZY_ERR_UNSUPPORTED;
     return FIZZY_OK;
 }
 
@@ -442,6 +447,7 @@ int fizzy_proj_plan(fizzy_proj_plan_t *out, const fizzy_proj_desc *d, void *stre
     g.nz = nz;
     g.bcx = d->bc_x;
     g.bcy = d->bc_y;
+    g.rny = (unsigned)((1ull << 32) / (unsigned)ny + 1);
     physics_consts(g, d->rho_l, d->rho_g, d->dt, d->dx, d->dy, sig);
     g.idx2 = 1.0 / (d->dx * d->dx);
     g.idy2 = 1.0 / (d->dy * d->dy);
@@ -954,6 +960,7 @@ extern "C" int fizzy_proj_solve_noalloc(const fizzy_proj_desc *d, const double *
     g.nz = nz;
     g.bcx = d->bc_x;
     g.bcy = d->bc_y;
+    g.rny = (unsigned)((1ull << 32) / (unsigned)ny + 1);
     physics_consts(g, d->rho_l, d->rho_g, d->dt, d->dx, d->dy, sig);
     g.idx2 = 1.0 / (d->dx * d->dx);
     g.idy2 = 1.0 / (d->dy * d->dy);

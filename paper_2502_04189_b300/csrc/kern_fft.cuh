@@ -37,12 +37,17 @@ struct FFTDesc {
     int kind;        // KIND_PERIODIC or KIND_DCT
     int rad[FFT_MAX_STAGES], m[FFT_MAX_STAGES], ns[FFT_MAX_STAGES], twq[FFT_MAX_STAGES];
     unsigned rm[FFT_MAX_STAGES], rns[FFT_MAX_STAGES];
+    unsigned rn, rM;  // multiply-high reciprocals of n and M = n/2 + 1
     const void *tw;  // n entries (m, tau) of exp(-2 pi i t / n), see tw_apply (T2)
     const void *cs;  // n/2+1 complex: (cos, sin)(pi m / (2 n)) (T2)
 };
 
 __device__ __forceinline__ int fdiv(int x, int d, unsigned r) {
     return d == 1 ? x : (int)__umulhi((unsigned)x, r);
+}
+// The multiply-high reciprocal of d, for fdiv (exact for 0 <= x < 2^32/d).
+__device__ __forceinline__ unsigned fdiv_recip(int d) {
+    return d > 1 ? 0xffffffffu / (unsigned)d + 1u : 0u;
 }
 
 // position of input sample i inside the (possibly reordered) complex line

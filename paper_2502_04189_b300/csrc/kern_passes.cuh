@@ -31,6 +31,7 @@ enum { BC_PERIODIC = 0, BC_NEUMANN = 1 };
 struct GridDev {
     int nx, ny, nz;
     int bcx, bcy;
+    unsigned rny;      // multiply-high reciprocal of ny (fdiv)
     // face-flux constants.  The split-term flux of a face with spacing h is
     // q' = u* + dt |drho|/(rho0 h) * t/(|drho| t + 2 rho0) * (p^_b - p^_a),
     // kept here with dt |drho|/(rho0 h) folded into the denominator:
@@ -388,8 +389,8 @@ __device__ __forceinline__ void xfwd_body(const GridDev &g, const FFTDesc &D, in
                 int j = 0, k = 0;
                 size_t c = 0;
                 if (on) {
-                    j = line % g.ny;
-                    k = line / g.ny;
+                    k = fdiv(line, g.ny, g.rny);
+                    j = line - k * g.ny;
                     c = cidx(g, i, j, k);
                     pc = ldp<CG>(a.p + c);
                     if (i < g.nx - 1) de = ldp<CG>(a.p + c + 1) - pc;
@@ -424,11 +425,11 @@ __device__ __forceinline__ void xfwd_body(const GridDev &g, const FFTDesc &D, in
         }
     } else
     for (int idx = threadIdx.x; idx < 2 * L * n; idx += blockDim.x) {
-        const int r = idx / n, i = idx - r * n;
+        const int r = fdiv(idx, n, D.rn), i = idx - r * n;
         const int line = line0 + r;
         T val = (T)0;
         if (line < nlines) {
-            const int j = line % g.ny, k = line / g.ny;
+            const int k = fdiv(line, g.ny, g.rny), j = line - k * g.ny;
             if (MODE == XF_F64_DIVQ) {
                 const double f = div_q<CG>(g, i, j, k, g.dvx_s, g.dvy_s, g.dvz_s[k], a.qx, a.qy, a.qz);
                 if (a.track_fmax) mx = umax64(mx, absbits(f));
@@ -452,7 +453,7 @@ __device__ __forceinline__ void xfwd_body(const GridDev &g, const FFTDesc &D, in
     T *out = (T *)a.out;
     const int M = n / 2 + 1;
     for (int t = threadIdx.x; t < L * M; t += blockDim.x) {
-        const int l = t / M, m = t - l * M;
+        const int l = fdiv(t, M, D.rM), m = t - l * M;
         const int la = line0 + 2 * l;
         fwd_separate<T>(Z + l * ls, n, m, D.kind, cs_s, [&](int ab, int ix, T v) {
             const int line = la + ab;
@@ -561,16 +562,17 @@ __device__ __forceinline__ void ypass_body(int nx, int ny, const FFTDesc &D, int
     const int ncols = min(TX, nx - i0);
     T *plane = data + (size_t)kplane * ny * nx + i0;
     const int M = n / 2 + 1;
+    const unsigned rTX = fdiv_recip(TX), rL = fdiv_recip(L);
     if (!INV) {
         for (int idx = threadIdx.x; idx < n * TX; idx += blockDim.x) {
-            const int j = idx / TX, c = idx - j * TX;
+            const int j = fdiv(idx, TX, rTX), c = idx - j * TX;
             const T val = (c < ncols) ? ldp<CG>(plane + (size_t)j * nx + c) : (T)0;
             ((T *)(A + (c >> 1) * ls))[2 * line_pos(j, n, D.kind) + (c & 1)] = val;
         }
         __syncthreads();
         const T2 *Z = fft_lines<T, false>(A, B, L, ls, D, tw_s);
         for (int t = threadIdx.x; t < L * M; t += blockDim.x) {
-            const int m = t / L, l = t - m * L;
+            const int m = fdiv(t, L, rL), l = t - m * L;
             fwd_separate<T>(Z + l * ls, n, m, D.kind, cs_s, [&](int ab, int ix, T v) {
                 const int c = 2 * l + ab;
                 if (c < ncols) plane[(size_t)ix * nx + c] = v;
@@ -579,7 +581,7 @@ __device__ __forceinline__ void ypass_body(int nx, int ny, const FFTDesc &D, int
     } else {
         __syncthreads();
         for (int t = threadIdx.x; t < L * M; t += blockDim.x) {
-            const int m = t / L, l = t - m * L;
+            const int m = fdiv(t, L, rL), l = t - m * L;
             inv_combine<T>(A + l * ls, n, m, D.kind, cs_s, [&](int ab, int ix) -> T {
                 const int c = 2 * l + ab;
                 return (c < ncols) ? ldp<CG>(plane + (size_t)ix * nx + c) : (T)0;
@@ -588,7 +590,7 @@ __device__ __forceinline__ void ypass_body(int nx, int ny, const FFTDesc &D, int
         __syncthreads();
         const T2 *Z = fft_lines<T, true>(A, B, L, ls, D, tw_s);
         for (int idx = threadIdx.x; idx < n * TX; idx += blockDim.x) {
-            const int j = idx / TX, c = idx - j * TX;
+            const int j = fdiv(idx, TX, rTX), c = idx - j * TX;
             if (c < ncols)
                 plane[(size_t)j * nx + c] = ((const T *)(Z + (c >> 1) * ls))[2 * line_pos(j, n, D.kind) + (c & 1)];
         }
@@ -622,7 +624,7 @@ __device__ __forceinline__ void xinv_body(const GridDev &g, const FFTDesc &D, in
     const int M = n / 2 + 1;
     __syncthreads();
     for (int t = threadIdx.x; t < L * M; t += blockDim.x) {
-        const int l = t / M, m = t - l * M;
+        const int l = fdiv(t, M, D.rM), m = t - l * M;
         const int la = line0 + 2 * l;
         inv_combine<T>(A + l * ls, n, m, D.kind, cs_s, [&](int ab, int ix) -> T {
             const int line = la + ab;
@@ -634,7 +636,7 @@ __device__ __forceinline__ void xinv_body(const GridDev &g, const FFTDesc &D, in
     int ef = 0;
     if (MODE == XI_ACCUM) ef = exp_of_bits(ldp<CG>(&st->fmax_bits));
     for (int idx = threadIdx.x; idx < 2 * L * n; idx += blockDim.x) {
-        const int r = idx / n, i = idx - r * n;
+        const int r = fdiv(idx, n, D.rn), i = idx - r * n;
         const int line = line0 + r;
         if (line < nlines) {
             const T v = ((const T *)(Z + (r >> 1) * ls))[2 * line_pos(i, n, D.kind) + (r & 1)];
