@@ -57,7 +57,7 @@ def measured_traffic(kernel, mixed):
     """DRAM bytes per launch of a kernel from the committed ncu summaries
     (lines 'traffic_per_launch_bytes <kernel> <bytes>' in profiles/*.md)."""
     import glob
-    name = {"flux": "k_flux", "resid_fwdx": "k_xfwd_resid",
+    name = {"flux": "k_flux", "resid": "k_resid", "resid_correct": "k_resid_corr",
             "div_fwdx": "k_xfwd_mix" if mixed else "k_xfwd_f64"}.get(kernel, kernel)
     for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
         for line in open(path):
@@ -80,8 +80,9 @@ def algorithmic_per_point(nx, ny, mixed):
             "inv_y": (16, ly), "inv_x": (16, lx), "correct": (56, 12)}
     return {
         "flux": (72, 32), "div_fwdx": (36, 8), "fwd_y": (8, 0), "thomas": (8, 0), "inv_y": (8, 0),
-        "inv_x": (12, 0), "resid_fwdx": (20, 14), "fwd_y_refine": (8, 0), "thomas_refine": (8, 0),
-        "inv_y_refine": (8, 0), "inv_x_update": (20, 1), "resid_check": (16, 17), "correct": (56, 12)}
+        "inv_x": (12, 0), "resid": (20, 14), "fwd_x_refine": (8, 0), "fwd_y_refine": (8, 0),
+        "thomas_refine": (8, 0), "inv_y_refine": (8, 0), "inv_x_update": (20, 1),
+        "resid_correct": (68, 20), "correct": (56, 12)}
 
 
 class ClockSampler:
@@ -277,8 +278,11 @@ def run_fizzy(args):
         # refinement kernels return at once after convergence: count only the
         # launches that did the pass (from the solve's sweep count)
         it, mr = st["iterations"], max_refine
-        per_solve = {"resid_fwdx": min(it + 1, mr), "fwd_y_refine": it, "thomas_refine": it,
-                     "inv_y_refine": it, "inv_x_update": it}.get(dom)
+        per_solve = {"fwd_x_refine": it, "fwd_y_refine": it, "thomas_refine": it,
+                     "inv_y_refine": it, "inv_x_update": it, "resid_correct": it}.get(dom)
+        if prec == F.MIXED and dom == "correct":  # runs only when no fused pass ran
+            per_solve = 1 if it == 0 else 0
+        del mr
         if per_solve is not None:
             cnt = max(1, per_solve * args.steps)
         avg_s = tot_ms / cnt / 1e3

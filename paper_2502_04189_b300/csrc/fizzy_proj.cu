@@ -5,6 +5,7 @@
 #include "fizzy_proj.h"
 #include "kern_passes.cuh"
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -52,6 +53,7 @@ struct fizzy_proj_plan_s {
     // launch shapes
     int Lx = 1, TXy = 2;
     size_t smem_x64 = 0, smem_x32 = 0, smem_y64 = 0, smem_y32 = 0;
+    int cap[24] = {0};  // resident-grid size of each pass kernel (CAP_*)
     std::string err;
     // stream-ordered allocation (FIZZY_FLAG_ASYNC_ALLOC)
     int async_alloc = 0;
@@ -62,19 +64,21 @@ struct fizzy_proj_plan_s {
     std::vector<cudaEvent_t> ev;        // 2 per recorded launch
     std::vector<int> ev_slot;           // kernel slot of each recorded launch
     int ev_used = 0;
-    double t_ms[16] = {0};
-    int t_cnt[16] = {0};
+    double t_ms[24] = {0};
+    int t_cnt[24] = {0};
 };
 
 namespace {
 
 enum {
-    KS_FLUX, KS_XFWD, KS_YFWD, KS_THOMAS, KS_YINV, KS_XINV, KS_XRES, KS_YFWD_R, KS_THOMAS_R,
-    KS_YINV_R, KS_XACC, KS_RESMAX, KS_CORRECT, KS_DIVMAX, KS_SUM, KS_N
+    KS_FLUX, KS_XFWD, KS_YFWD, KS_THOMAS, KS_YINV, KS_XINV, KS_RESID, KS_XFWD_R, KS_YFWD_R,
+    KS_THOMAS_R, KS_YINV_R, KS_XACC, KS_RCORR, KS_RESMAX, KS_CORRECT, KS_DIVMAX, KS_SUM, KS_N
 };
 const char *kSlotName[KS_N] = {"flux", "div_fwdx", "fwd_y", "thomas", "inv_y", "inv_x",
-                               "resid_fwdx", "fwd_y_refine", "thomas_refine", "inv_y_refine",
-                               "inv_x_update", "resid_check", "correct", "div_check", "sum_partials"};
+                               "resid", "fwd_x_refine", "fwd_y_refine", "thomas_refine",
+                               "inv_y_refine", "inv_x_update", "resid_correct", "resid_check",
+                               "correct", "div_check", "sum_partials"};
+static_assert(KS_N <= 24, "timing slot arrays");
 const int kMaxTimed = 8192;
 
 const char *kErrStr[] = {"ok", "invalid argument", "unsupported size", "out of device memory",
@@ -322,8 +326,40 @@ void physics_zrow(double rho_l, double rho_g, double dt, double sig, double dzf,
     row[4 * stride] = dt / rho0 * idzc;
 }
 
+// Grid of a stand-alone pass launch: the CTAs of the kernel the GPU holds
+// resident (occupancy x SM count); the kernel strides over its tiles.
+enum { CAP_XF64, CAP_XF32D, CAP_XF32L, CAP_Y64F, CAP_Y64I, CAP_Y32F, CAP_Y32I, CAP_XI64, CAP_XI32S,
+       CAP_XI32A, CAP_TH64, CAP_TH32, CAP_RM, CAP_RC, CAP_CIF, CAP_N };
+template <typename K> int resident_grid(K kernel, int threads, size_t smem) {
+    int dev = 0, sms = 0, nb = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, threads, smem) != cudaSuccess) {
+        (void)cudaGetLastError();
+        nb = 1;
+    }
+    return std::max(1, nb) * std::max(1, sms);
+}
 template <typename T> size_t pass_smem(int n, int L) {
     return sizeof(typename C2<T>::t) * ((size_t)n + (n / 2 + 2) + 2 * (size_t)L * (n + 1));
+}
+
+void pass_caps(int *cap, size_t sx64, size_t sx32, size_t sy64, size_t sy32) {
+    cap[CAP_XF64] = resident_grid(k_xfwd<double, XF_F64_DIVQ>, 256, sx64);
+    cap[CAP_XF32D] = resident_grid(k_xfwd<float, XF_MIX_DIVQ>, 256, sx32);
+    cap[CAP_XF32L] = resident_grid(k_xfwd<float, XF_MIX_LOAD>, 256, sx32);
+    cap[CAP_Y64F] = resident_grid(k_ypass<double, false>, 256, sy64);
+    cap[CAP_Y64I] = resident_grid(k_ypass<double, true>, 256, sy64);
+    cap[CAP_Y32F] = resident_grid(k_ypass<float, false>, 256, sy32);
+    cap[CAP_Y32I] = resident_grid(k_ypass<float, true>, 256, sy32);
+    cap[CAP_XI64] = resident_grid(k_xinv<double, XI_STORE>, 256, sx64);
+    cap[CAP_XI32S] = resident_grid(k_xinv<float, XI_STORE>, 256, sx32);
+    cap[CAP_XI32A] = resident_grid(k_xinv<float, XI_ACCUM>, 256, sx32);
+    cap[CAP_TH64] = resident_grid(k_thomas<double>, THOMAS_BLOCK, thomas_smem<double>());
+    cap[CAP_TH32] = resident_grid(k_thomas<float>, THOMAS_BLOCK, thomas_smem<float>());
+    cap[CAP_RM] = resident_grid(k_residmax, 256, 0);
+    cap[CAP_RC] = resident_grid(k_resid<true>, 256, 0);
+    cap[CAP_CIF] = resident_grid(k_correct_if, 256, 0);
 }
 
 constexpr int kFluxKc = 16;  // planes marched by one flux CTA
@@ -547,7 +583,7 @@ int fizzy_proj_plan(fizzy_proj_plan_t *out, const fizzy_proj_desc *d, void *stre
     const int big = 200 * 1024;
     cudaFuncSetAttribute(k_xfwd<double, XF_F64_DIVQ>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
     cudaFuncSetAttribute(k_xfwd<float, XF_MIX_DIVQ>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-    cudaFuncSetAttribute(k_xfwd<float, XF_MIX_RESID>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    cudaFuncSetAttribute(k_xfwd<float, XF_MIX_LOAD>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
     cudaFuncSetAttribute(k_xinv<double, XI_STORE>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
     cudaFuncSetAttribute(k_xinv<float, XI_STORE>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
     cudaFuncSetAttribute(k_xinv<float, XI_ACCUM>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
@@ -556,6 +592,7 @@ int fizzy_proj_plan(fizzy_proj_plan_t *out, const fizzy_proj_desc *d, void *stre
     cudaFuncSetAttribute(k_ypass<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
     cudaFuncSetAttribute(k_ypass<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
     }
+    pass_caps(p->cap, p->smem_x64, p->smem_x32, p->smem_y64, p->smem_y32);
     // stream-ordered plans are ready for work queued after them on their
     // stream; other plans are complete on return
     cudaError_t e = p->async_alloc ? cudaGetLastError() : cudaDeviceSynchronize();
@@ -599,7 +636,7 @@ int fizzy_proj_set_physics(fizzy_proj_plan_t p, double rho_l, double rho_g, doub
 
 int fizzy_proj_launches_per_solve(fizzy_proj_plan_t p) {
     if (!p) return 0;
-    int n = p->mixed ? 9 + 5 * p->max_refine : 7;
+    int n = p->mixed ? 9 + 6 * p->max_refine : 7;
     if (p->check) n += p->mixed ? 1 : 3;
     return n;
 }
@@ -702,17 +739,21 @@ int fizzy_proj_solve(fizzy_proj_plan_t p, const double *phi, const double *p_n, 
     const dim3 cblk(32, 8), cgrd((nx + 31) / 32, (ny + 7) / 8, nz);
     const dim3 rblk(256), rgrd((nx + 255) / 256, ny, nz);
     const int nlines = ny * nz;
-    const int xgrid = (nlines + 2 * p->Lx - 1) / (2 * p->Lx);
-    const dim3 ygrid((nx + p->TXy - 1) / p->TXy, nz);
-    const int tthreads = nx * ny;  // one z-line per thread
-    const dim3 tgrid((tthreads + THOMAS_BLOCK - 1) / THOMAS_BLOCK);
+    // tiles of each pass; each stand-alone launch runs min(tiles, resident grid)
+    const int xtiles = (nlines + 2 * p->Lx - 1) / (2 * p->Lx);
+    const int ygx = (nx + p->TXy - 1) / p->TXy, ytiles = ygx * nz;
+    const int ttiles = (nx * ny + THOMAS_BLOCK - 1) / THOMAS_BLOCK;  // one z-line per thread
+    const int rgx = (nx + 255) / 256, rtiles = rgx * ny * nz;
+    // main path: one block per tile; refinement passes that usually find the
+    // solve converged, and the final check: the resident grid
+    auto grid = [&](int tiles, int) { return std::max(1, tiles); };
+    auto rgrid = [&](int tiles, int c) { return std::max(1, std::min(tiles, p->cap[c])); };
     XArgs xa;
     memset(&xa, 0, sizeof(xa));
     xa.qx = p->qx;
     xa.qy = p->qy;
     xa.qz = p->qz;
     xa.st = p->st;
-    xa.tol = p->tol;
     cudaError_t e = cudaSuccess;
     if (p->mixed || p->check) e = cudaMemsetAsync(p->st, 0, sizeof(DevStats), s);
     if (e != cudaSuccess) return cuda_err(p, e, "memset");
@@ -729,42 +770,63 @@ int fizzy_proj_solve(fizzy_proj_plan_t p, const double *phi, const double *p_n, 
         TIMED(KS_SUM, (k_sum_partials<<<1, 1024, 0, s>>>(p->usq_part, p->n_usq_part, p->usq_sum)));
     if (!p->mixed) {
         xa.out = p->fhat64;
-        TIMED(KS_XFWD, (k_xfwd<double, XF_F64_DIVQ><<<xgrid, 256, p->smem_x64, s>>>(g, p->fx.d64, p->Lx, xa)));
-        TIMED(KS_YFWD, (k_ypass<double, false><<<ygrid, 256, p->smem_y64, s>>>(nx, ny, p->fy.d64, p->TXy, p->fhat64, nullptr)));
-        TIMED(KS_THOMAS, (k_thomas<double><<<tgrid, THOMAS_BLOCK, thomas_smem<double>(), s>>>(g, p->Ux, p->Uy, p->mtab64, p->ibtab64, p->cup64, p->fhat64, nullptr)));
-        TIMED(KS_YINV, (k_ypass<double, true><<<ygrid, 256, p->smem_y64, s>>>(nx, ny, p->fy.d64, p->TXy, p->fhat64, nullptr)));
-        TIMED(KS_XINV, (k_xinv<double, XI_STORE><<<xgrid, 256, p->smem_x64, s>>>(g, p->fx.d64, p->Lx, p->fhat64, p_np1, p->st)));
+        TIMED(KS_XFWD, (k_xfwd<double, XF_F64_DIVQ><<<grid(xtiles, CAP_XF64), 256, p->smem_x64, s>>>(g, p->fx.d64, p->Lx, xa, xtiles)));
+        TIMED(KS_YFWD, (k_ypass<double, false><<<grid(ytiles, CAP_Y64F), 256, p->smem_y64, s>>>(nx, ny, p->fy.d64, p->TXy, p->fhat64, nullptr, ygx, ytiles)));
+        TIMED(KS_THOMAS, (k_thomas<double><<<grid(ttiles, CAP_TH64), THOMAS_BLOCK, thomas_smem<double>(), s>>>(g, p->Ux, p->Uy, p->mtab64, p->ibtab64, p->cup64, p->fhat64, nullptr, ttiles)));
+        TIMED(KS_YINV, (k_ypass<double, true><<<grid(ytiles, CAP_Y64I), 256, p->smem_y64, s>>>(nx, ny, p->fy.d64, p->TXy, p->fhat64, nullptr, ygx, ytiles)));
+        TIMED(KS_XINV, (k_xinv<double, XI_STORE><<<grid(xtiles, CAP_XI64), 256, p->smem_x64, s>>>(g, p->fx.d64, p->Lx, p->fhat64, p_np1, p->st, xtiles)));
         if (p->check) {
             XArgs ca = xa;
             ca.p = p_np1;
-            ca.slot = 0;
-            TIMED(KS_RESMAX, (k_residmax<<<rgrd, rblk, 0, s>>>(g, ca, 1)));
+            TIMED(KS_RESMAX, (k_residmax<<<grid(rtiles, CAP_RM), rblk, 0, s>>>(g, ca, rgx, rtiles)));
         }
     } else {
         xa.out = p->fhat32;
         xa.f_out = p->f;
         const int *conv = &p->st->converged;
-        TIMED(KS_XFWD, (k_xfwd<float, XF_MIX_DIVQ><<<xgrid, 256, p->smem_x32, s>>>(g, p->fx.d32, p->Lx, xa)));
-        TIMED(KS_YFWD, (k_ypass<float, false><<<ygrid, 256, p->smem_y32, s>>>(nx, ny, p->fy.d32, p->TXy, p->fhat32, nullptr)));
-        TIMED(KS_THOMAS, (k_thomas<float><<<tgrid, THOMAS_BLOCK, thomas_smem<float>(), s>>>(g, p->Ux, p->Uy, p->mtab32, p->ibtab32, p->cup32, p->fhat32, nullptr)));
-        TIMED(KS_YINV, (k_ypass<float, true><<<ygrid, 256, p->smem_y32, s>>>(nx, ny, p->fy.d32, p->TXy, p->fhat32, nullptr)));
-        TIMED(KS_XINV, (k_xinv<float, XI_STORE><<<xgrid, 256, p->smem_x32, s>>>(g, p->fx.d32, p->Lx, p->fhat32, p_np1, p->st)));
-        XArgs ra = xa;
-        ra.f = p->f;
+        TIMED(KS_XFWD, (k_xfwd<float, XF_MIX_DIVQ><<<grid(xtiles, CAP_XF32D), 256, p->smem_x32, s>>>(g, p->fx.d32, p->Lx, xa, xtiles)));
+        TIMED(KS_YFWD, (k_ypass<float, false><<<grid(ytiles, CAP_Y32F), 256, p->smem_y32, s>>>(nx, ny, p->fy.d32, p->TXy, p->fhat32, nullptr, ygx, ytiles)));
+        TIMED(KS_THOMAS, (k_thomas<float><<<grid(ttiles, CAP_TH32), THOMAS_BLOCK, thomas_smem<float>(), s>>>(g, p->Ux, p->Uy, p->mtab32, p->ibtab32, p->cup32, p->fhat32, nullptr, ttiles)));
+        TIMED(KS_YINV, (k_ypass<float, true><<<grid(ytiles, CAP_Y32I), 256, p->smem_y32, s>>>(nx, ny, p->fy.d32, p->TXy, p->fhat32, nullptr, ygx, ytiles)));
+        TIMED(KS_XINV, (k_xinv<float, XI_STORE><<<grid(xtiles, CAP_XI32S), 256, p->smem_x32, s>>>(g, p->fx.d32, p->Lx, p->fhat32, p_np1, p->st, xtiles)));
+        // residual of the FP32 solution (slot 0), then refinement sweeps
+        // sw = 1..max_refine: transform of the stored residual, FP32 y/z/y^-1,
+        // p += delta, then the residual fused with the correction (slot sw)
+        RArgs ra;
         ra.p = p_np1;
-        ra.f_out = nullptr;
-        for (int sw = 0; sw < p->max_refine; ++sw) {
+        ra.f = p->f;
+        ra.qx = p->qx;
+        ra.qy = p->qy;
+        ra.qz = p->qz;
+        ra.u = u;
+        ra.v = v;
+        ra.w = w;
+        ra.r32 = p->fhat32;
+        ra.st = p->st;
+        ra.tol = p->tol;
+        ra.slot = 0;
+        const dim3 rcb(FLUX_BX, FLUX_BY);
+        const int rtgx = (nx + FLUX_BX - 1) / FLUX_BX, rtgy = (ny + FLUX_BY - 1) / FLUX_BY;
+        const int rctiles = rtgx * rtgy * ((nz + RESID_KC - 1) / RESID_KC);
+        TIMED(KS_RESID, (k_resid<false><<<grid(rctiles, CAP_RC), rcb, 0, s>>>(g, RESID_KC, ra, rtgx, rtgy, rctiles)));
+        XArgs la = xa;  // in-place transform of the stored residual
+        la.f_out = nullptr;
+        for (int sw = 1; sw <= p->max_refine; ++sw) {
+            // a one-sweep solve runs sweep 1; later sweeps usually return at once
+            auto gs = [&](int tiles, int c) { return sw == 1 ? grid(tiles, c) : rgrid(tiles, c); };
+            TIMED(KS_XFWD_R, (k_xfwd<float, XF_MIX_LOAD><<<gs(xtiles, CAP_XF32L), 256, p->smem_x32, s>>>(g, p->fx.d32, p->Lx, la, xtiles)));
+            TIMED(KS_YFWD_R, (k_ypass<float, false><<<gs(ytiles, CAP_Y32F), 256, p->smem_y32, s>>>(nx, ny, p->fy.d32, p->TXy, p->fhat32, conv, ygx, ytiles)));
+            TIMED(KS_THOMAS_R, (k_thomas<float><<<gs(ttiles, CAP_TH32), THOMAS_BLOCK, thomas_smem<float>(), s>>>(g, p->Ux, p->Uy, p->mtab32, p->ibtab32, p->cup32, p->fhat32, conv, ttiles)));
+            TIMED(KS_YINV_R, (k_ypass<float, true><<<gs(ytiles, CAP_Y32I), 256, p->smem_y32, s>>>(nx, ny, p->fy.d32, p->TXy, p->fhat32, conv, ygx, ytiles)));
+            TIMED(KS_XACC, (k_xinv<float, XI_ACCUM><<<gs(xtiles, CAP_XI32A), 256, p->smem_x32, s>>>(g, p->fx.d32, p->Lx, p->fhat32, p_np1, p->st, xtiles)));
             ra.slot = sw;
-            TIMED(KS_XRES, (k_xfwd<float, XF_MIX_RESID><<<xgrid, 256, p->smem_x32, s>>>(g, p->fx.d32, p->Lx, ra)));
-            TIMED(KS_YFWD_R, (k_ypass<float, false><<<ygrid, 256, p->smem_y32, s>>>(nx, ny, p->fy.d32, p->TXy, p->fhat32, conv)));
-            TIMED(KS_THOMAS_R, (k_thomas<float><<<tgrid, THOMAS_BLOCK, thomas_smem<float>(), s>>>(g, p->Ux, p->Uy, p->mtab32, p->ibtab32, p->cup32, p->fhat32, conv)));
-            TIMED(KS_YINV_R, (k_ypass<float, true><<<ygrid, 256, p->smem_y32, s>>>(nx, ny, p->fy.d32, p->TXy, p->fhat32, conv)));
-            TIMED(KS_XACC, (k_xinv<float, XI_ACCUM><<<xgrid, 256, p->smem_x32, s>>>(g, p->fx.d32, p->Lx, p->fhat32, p_np1, p->st)));
+            TIMED(KS_RCORR, (k_resid<true><<<gs(rctiles, CAP_RC), rcb, 0, s>>>(g, RESID_KC, ra, rtgx, rtgy, rctiles)));
         }
-        ra.slot = p->max_refine;
-        TIMED(KS_RESMAX, (k_residmax<<<rgrd, rblk, 0, s>>>(g, ra, 0)));
+        // the correction, unless a fused residual pass has written u
+        const int ctiles = rtgx * rtgy * nz;
+        TIMED(KS_CORRECT, (k_correct_if<<<rgrid(ctiles, CAP_CIF), rcb, 0, s>>>(g, p_np1, p->qx, p->qy, p->qz, u, v, w, p->st, rtgx, rtgy, ctiles)));
     }
-    TIMED(KS_CORRECT, (k_correct<<<cgrd, cblk, 0, s>>>(g, p_np1, p->qx, p->qy, p->qz, u, v, w)));
+    if (!p->mixed) TIMED(KS_CORRECT, (k_correct<<<cgrd, cblk, 0, s>>>(g, p_np1, p->qx, p->qy, p->qz, u, v, w)));
     if (p->check) TIMED(KS_DIVMAX, (k_divmax<<<rgrd, rblk, 0, s>>>(g, u, v, w, p->st)));
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_err(p, e, "solve launch");
@@ -993,10 +1055,10 @@ extern "C" int fizzy_proj_solve_noalloc(const fizzy_proj_desc *d, const double *
     const int Lx = x_lines_per_cta(nx), TXy = y_tile_cols(ny);
     const size_t smx = pass_smem<double>(nx, Lx), smy = pass_smem<double>(ny, TXy / 2);
     const dim3 cblk(32, 8), cgrd((nx + 31) / 32, (ny + 7) / 8, nz);
-    const int xgrid = (ny * nz + 2 * Lx - 1) / (2 * Lx);
-    const dim3 ygrid((nx + TXy - 1) / TXy, nz);
-    const int tthreads = nx * ny;  // one z-line per thread
-    const dim3 tgrid((tthreads + THOMAS_BLOCK - 1) / THOMAS_BLOCK);
+    const int xtiles = (ny * nz + 2 * Lx - 1) / (2 * Lx);
+    const int ygx = (nx + TXy - 1) / TXy, ytiles = ygx * nz;
+    const int ttiles = (nx * ny + THOMAS_BLOCK - 1) / THOMAS_BLOCK;  // one z-line per thread
+    auto grid = [&](int tiles, int) { return std::max(1, tiles); };  // one block per tile
     XArgs xa;
     memset(&xa, 0, sizeof(xa));
     xa.qx = qx;
@@ -1010,11 +1072,11 @@ extern "C" int fizzy_proj_solve_noalloc(const fizzy_proj_desc *d, const double *
         k_flux<true><<<fgrd, fblk, 0, s>>>(g, kFluxKc, phi, p_n, p_nm1, u, v, w, qx, qy, qz, nullptr);
     else
         k_flux<false><<<fgrd, fblk, 0, s>>>(g, kFluxKc, phi, p_n, p_nm1, u, v, w, qx, qy, qz, nullptr);
-    k_xfwd<double, XF_F64_DIVQ><<<xgrid, 256, smx, s>>>(g, Dx, Lx, xa);
-    k_ypass<double, false><<<ygrid, 256, smy, s>>>(nx, ny, Dy, TXy, fhat, nullptr);
-    k_thomas<double><<<tgrid, THOMAS_BLOCK, thomas_smem<double>(), s>>>(g, Ux, Uy, dtab, dtab + kNaMaxCells, dcup, fhat, nullptr);
-    k_ypass<double, true><<<ygrid, 256, smy, s>>>(nx, ny, Dy, TXy, fhat, nullptr);
-    k_xinv<double, XI_STORE><<<xgrid, 256, smx, s>>>(g, Dx, Lx, fhat, p_np1, nullptr);
+    k_xfwd<double, XF_F64_DIVQ><<<grid(xtiles, CAP_XF64), 256, smx, s>>>(g, Dx, Lx, xa, xtiles);
+    k_ypass<double, false><<<grid(ytiles, CAP_Y64F), 256, smy, s>>>(nx, ny, Dy, TXy, fhat, nullptr, ygx, ytiles);
+    k_thomas<double><<<grid(ttiles, CAP_TH64), THOMAS_BLOCK, thomas_smem<double>(), s>>>(g, Ux, Uy, dtab, dtab + kNaMaxCells, dcup, fhat, nullptr, ttiles);
+    k_ypass<double, true><<<grid(ytiles, CAP_Y64I), 256, smy, s>>>(nx, ny, Dy, TXy, fhat, nullptr, ygx, ytiles);
+    k_xinv<double, XI_STORE><<<grid(xtiles, CAP_XI64), 256, smx, s>>>(g, Dx, Lx, fhat, p_np1, nullptr, xtiles);
     k_correct<<<cgrd, cblk, 0, s>>>(g, p_np1, qx, qy, qz, u, v, w);
     e = cudaGetLastError();
     return e == cudaSuccess ? FIZZY_OK : FIZZY_ERR_CUDA;

@@ -21,7 +21,7 @@
 namespace fz {
 
 constexpr int BATCH_THREADS = 256;
-constexpr int BATCH_MAXP = 64;  // passes per instance (9 + 5 * max_refine <= 64)
+constexpr int BATCH_MAXP = 64;  // passes per instance (mixed: 9 + 6 * max_refine <= 64)
 
 enum BatchKind : int {
     BK_FLUX = 0,
@@ -36,12 +36,14 @@ enum BatchKind : int {
     BK_TH32,
     BK_YI32,
     BK_XI32,
-    BK_XRES,
+    BK_RES0,    // residual of the FP32 solution (slot 0)
+    BK_XLOAD,   // transform of the stored residual (sweep s)
     BK_YF32C,
     BK_TH32C,
     BK_YI32C,
     BK_XACC,
-    BK_RESCHK,
+    BK_RCORR,   // residual fused with the correction (slot s)
+    BK_CORRIF,  // the correction, unless a fused residual pass has run
     BK_CORRECT
 };
 
@@ -76,7 +78,6 @@ struct BatchInst {
     // tile decode helpers
     int fgx, fgy;        // flux grid x, y
     int ygx;             // y-pass tiles along x
-    int rgx;             // residual-check tiles along x
     int cgx, cgy;        // correction grid x, y
 };
 
@@ -116,18 +117,14 @@ __device__ __forceinline__ void batch_run_tile(const BatchInst &I, const BatchIt
         break;
     case BK_XFWD64:
     case BK_XFWD_MIX:
-    case BK_XRES: {
+    case BK_XLOAD: {
         XArgs a;
+        memset(&a, 0, sizeof(a));
         a.qx = I.qx;
         a.qy = I.qy;
         a.qz = I.qz;
-        a.f = I.f;
-        a.p = I.p;
         a.f_out = I.f;
         a.st = I.st;
-        a.slot = I.slot[w.pass];
-        a.tol = I.tol;
-        a.track_fmax = 0;
         if (kind == BK_XFWD64) {
             a.out = I.fhat64;
             xfwd_body<double, XF_F64_DIVQ, true>(g, I.fx64, I.Lx, a, tile, I.tiles[w.pass], smem);
@@ -136,8 +133,29 @@ __device__ __forceinline__ void batch_run_tile(const BatchInst &I, const BatchIt
             xfwd_body<float, XF_MIX_DIVQ, true>(g, I.fx32, I.Lx, a, tile, I.tiles[w.pass], smem);
         } else {
             a.out = I.fhat32;
-            xfwd_body<float, XF_MIX_RESID, true>(g, I.fx32, I.Lx, a, tile, I.tiles[w.pass], smem);
+            xfwd_body<float, XF_MIX_LOAD, true>(g, I.fx32, I.Lx, a, tile, I.tiles[w.pass], smem);
         }
+        break;
+    }
+    case BK_RES0:
+    case BK_RCORR: {
+        RArgs a;
+        a.p = I.p;
+        a.f = I.f;
+        a.qx = I.qx;
+        a.qy = I.qy;
+        a.qz = I.qz;
+        a.u = I.u;
+        a.v = I.v;
+        a.w = I.w;
+        a.r32 = I.fhat32;
+        a.st = I.st;
+        a.slot = I.slot[w.pass];
+        a.tol = I.tol;
+        const int txy = I.cgx * I.cgy, z = tile / txy, r = tile - z * txy, y = r / I.cgx;
+        const VB vb{r - y * I.cgx, y, z};
+        if (kind == BK_RES0) resid_body<true, false>(g, RESID_KC, a, vb, I.tiles[w.pass], (double *)smem);
+        else resid_body<true, true>(g, RESID_KC, a, vb, I.tiles[w.pass], (double *)smem);
         break;
     }
     case BK_YF64:
@@ -179,18 +197,9 @@ __device__ __forceinline__ void batch_run_tile(const BatchInst &I, const BatchIt
     case BK_XACC:
         xinv_body<float, XI_ACCUM, true>(g, I.fx32, I.Lx, I.fhat32, I.p, I.st, tile, smem);
         break;
-    case BK_RESCHK: {
-        XArgs a;
-        memset(&a, 0, sizeof(a));
-        a.f = I.f;
-        a.p = I.p;
-        a.st = I.st;
-        a.slot = I.slot[w.pass];
-        a.tol = I.tol;
-        const VB vb{tile % I.rgx, (tile / I.rgx) % g.ny, tile / (I.rgx * g.ny)};
-        residmax_body<true>(g, a, 0, vb, I.tiles[w.pass]);
-        break;
-    }
+    case BK_CORRIF:
+        if (__ldcg(&I.st->n_resid) != 1) break;  // a fused residual pass wrote u
+        [[fallthrough]];
     case BK_CORRECT: {
         const VB vb{tile % I.cgx, (tile / I.cgx) % I.cgy, tile / (I.cgx * I.cgy)};
         correct_body<true>(g, I.p, I.qx, I.qy, I.qz, I.u, I.v, I.w, vb);
@@ -214,8 +223,8 @@ __global__ void __launch_bounds__(BATCH_THREADS, 3) k_batch(BatchArgs A) {
         if (threadIdx.x == 0) {
             int ok = 1;
             const int kind = I.kind[w.pass];
-            const bool refine = kind == BK_XRES || kind == BK_YF32C || kind == BK_TH32C ||
-                                kind == BK_YI32C || kind == BK_XACC || kind == BK_RESCHK;
+            const bool refine = kind == BK_XLOAD || kind == BK_YF32C || kind == BK_TH32C ||
+                                kind == BK_YI32C || kind == BK_XACC || kind == BK_RCORR;
             // refinement work of an instance that has already converged is
             // empty: publish it without waiting (the flag is set once, by the
             // last tile of a residual pass, and never cleared in the launch)

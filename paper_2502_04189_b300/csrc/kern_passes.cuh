@@ -2,13 +2,17 @@
 //
 //   k_flux      : q' = dt q = u* - dt (beta_f - 1/rho0) G phat on every face (FP64)
 //                 (beta_f - 1/rho0 formed without cancellation, see face_flux)
-//   k_xfwd      : f = rho0 D(q)  or  r = f - L_h p, then forward x-transform
+//   k_xfwd      : f = rho0 D(q) (or a stored FP32 residual), then the forward
+//                 x-transform
 //   k_ypass     : forward / inverse y-transform on strided column tiles
 //   k_thomas    : one tridiagonal solve per (kx, ky) z-line (factorised tables)
 //   k_xinv      : inverse x-transform, p = value or p += value
+//   k_resid     : mixed: r = f - L_h p (FP64), stored in FP32 for the next
+//                 sweep, and the convergence decision; fused with the
+//                 correction in the refinement sweeps
 //   k_correct   : u = q' - (dt/rho0) G p^(n+1)                               (FP64)
 //   k_divmax    : max |D u| (diagnostics)
-//   k_residmax  : max |f - L_h p| without a transform (mixed final check)
+//   k_residmax  : max |f - L_h p| without a transform (FP64-mode check)
 //
 // The provisional face flux q = u*/dt - (beta_f - 1/rho0) G phat carries the
 // split: the right-hand side of the constant-coefficient equation is rho0 D(q)
@@ -313,32 +317,22 @@ __device__ __forceinline__ double lap(const GridDev &g, int i, int j, int k, con
     return fmaT(-g.lza[k], pc - pb, acc);
 }
 
-template <bool CG>
-__device__ __forceinline__ double resid(const GridDev &g, int i, int j, int k, const double *f,
-                                        const double *p) {
-    return ldp<CG>(f + cidx(g, i, j, k)) - lap<CG>(g, i, j, k, p);
-}
-
 enum {
     XF_F64_DIVQ = 0,   // FP64 mode: sigma rho0 D(q), FP64 transform
     XF_MIX_DIVQ = 1,   // mixed: f = rho0 D(q) stored (FP64), FP32 transform of sigma f
-    XF_MIX_RESID = 2   // mixed: r = f - L_h p, FP32 transform of sigma 2^-e r
+    XF_MIX_LOAD = 2    // mixed: FP32 transform, in place, of a stored sigma 2^-e r
 };
 
 struct XArgs {
     const double *qx, *qy, *qz;  // divergence sources
-    const double *f;             // residual source f (MIX_RESID)
-    const double *p;             // residual source p (MIX_RESID)
+    const double *p;             // FP64-mode check: the pressure
     double *f_out;               // MIX_DIVQ: f stored here
-    void *out;                   // transformed output (T), [nz][ny][nx]
+    void *out;                   // transformed output (T), [nz][ny][nx]; MIX_LOAD: also the input
     DevStats *st;
-    int slot;                    // residual slot (MIX_RESID)
-    double tol;
     int track_fmax;              // F64_DIVQ: record max|sigma f|
 };
 
 // Forward x-pass: per CTA 2L real x-lines (flattened line index (k, j)).
-// ntiles: number of CTAs of this pass (for the last-block decision).
 template <typename T, int MODE, bool CG>
 __device__ __forceinline__ void xfwd_body(const GridDev &g, const FFTDesc &D, int L, const XArgs &a,
                                           int bx, int ntiles, unsigned char *smem_raw) {
@@ -348,87 +342,21 @@ __device__ __forceinline__ void xfwd_body(const GridDev &g, const FFTDesc &D, in
     T2 *cs_s = tw_s + n;
     T2 *A = cs_s + (n / 2 + 2);
     T2 *B = A + L * ls;
-    if (MODE == XF_MIX_RESID && ldp<CG>(&a.st->converged)) return;
+    if (MODE == XF_MIX_LOAD && ldp<CG>(&a.st->converged)) return;
     load_tables<T>(D, tw_s, cs_s);
     const int nlines = g.ny * g.nz;
     const int line0 = bx * 2 * L;
+    (void)ntiles;
     unsigned long long mx = 0ull;
-    int ef = 0;
-    float scale32 = (float)g.sigma;
-    if (MODE == XF_MIX_RESID) ef = exp_of_bits(ldp<CG>(&a.st->fmax_bits));
+    const float scale32 = (float)g.sigma;
     // 1. source values into the packed complex lines
-    if (MODE == XF_MIX_RESID) {
-        // r = f - L_h p with every x- and y-face difference formed once:
-        //   r = f - idx2 (dE - dW) - idy2 (dN - dS) - c_k dT + a_k dB
-        // (dE = p(i+1) - p(i), dN = p(j+1) - p(j), dT = p(k+1) - p(k),
-        // dB = p(k) - p(k-1); wall faces carry zero difference), folded into
-        // four FMAs.  Thread mapping: G groups of n threads (n <= blockDim),
-        // group g walks a contiguous chunk of the CTA's lines at fixed i, so
-        // the south difference of a line is the north difference the same
-        // thread formed for the previous line; the west difference is the
-        // east difference of the neighbouring lane.  Line and warp starts
-        // form theirs from memory.  Loop trip counts are uniform so the
-        // shuffle runs converged.
-        const int R2 = 2 * L;
-        const int nt = blockDim.x;
-        const int G = (n >= nt) ? 1 : nt / n;
-        const int NI = (n + nt - 1) / nt;
-        const int chunk = (R2 + G - 1) / G;
-        const int grp = (n >= nt) ? 0 : (int)threadIdx.x / n;
-        const int lane = threadIdx.x & 31;
-        const size_t pl = (size_t)g.nx * g.ny;
-        for (int ic = 0; ic < NI; ++ic) {
-            const int i = (n >= nt) ? (int)threadIdx.x + ic * nt : (int)threadIdx.x - grp * n;
-            const bool ion = (i < n) && (grp < G);
-            double dn_prev = 0.0;
-            for (int rr = 0; rr < chunk; ++rr) {
-                const int r = grp * chunk + rr;
-                const int line = line0 + r;
-                const bool on = ion && r < R2 && line < nlines;
-                double pc = 0.0, de = 0.0, dn = 0.0;
-                int j = 0, k = 0;
-                size_t c = 0;
-                if (on) {
-                    k = fdiv(line, g.ny, g.rny);
-                    j = line - k * g.ny;
-                    c = cidx(g, i, j, k);
-                    pc = ldp<CG>(a.p + c);
-                    if (i < g.nx - 1) de = ldp<CG>(a.p + c + 1) - pc;
-                    else if (g.bcx == BC_PERIODIC) de = ldp<CG>(a.p + c - i) - pc;
-                    if (j < g.ny - 1) dn = ldp<CG>(a.p + c + g.nx) - pc;
-                    else if (g.bcy == BC_PERIODIC) dn = ldp<CG>(a.p + c - (size_t)j * g.nx) - pc;
-                }
-                double dw = __shfl_up_sync(0xffffffffu, de, 1);
-                if (on) {
-                    if (i == 0) dw = (g.bcx == BC_PERIODIC) ? pc - ldp<CG>(a.p + c + g.nx - 1) : 0.0;
-                    else if (lane == 0) dw = pc - ldp<CG>(a.p + c - 1);
-                    double ds;
-                    if (j == 0)
-                        ds = (g.bcy == BC_PERIODIC) ? pc - ldp<CG>(a.p + c + (size_t)(g.ny - 1) * g.nx)
-                                                    : 0.0;
-                    else if (rr > 0) ds = dn_prev;
-                    else ds = pc - ldp<CG>(a.p + c - g.nx);
-                    const double dt = (k < g.nz - 1) ? ldp<CG>(a.p + c + pl) - pc : 0.0;
-                    const double db = (k > 0) ? pc - ldp<CG>(a.p + c - pl) : 0.0;
-                    double res = fmaT(-g.idx2, de - dw, ldp<CG>(a.f + c));
-                    res = fmaT(-g.idy2, dn - ds, res);
-                    res = fmaT(-g.lzc[k], dt, res);
-                    res = fmaT(g.lza[k], db, res);
-                    mx = umax64(mx, absbits(res));
-                    ((T *)(A + (r >> 1) * ls))[2 * line_pos(i, n, D.kind) + (r & 1)] =
-                        (T)(f64_to_f32_shift(res, ef) * scale32);
-                } else if (ion && r < R2) {
-                    ((T *)(A + (r >> 1) * ls))[2 * line_pos(i, n, D.kind) + (r & 1)] = (T)0;
-                }
-                dn_prev = dn;
-            }
-        }
-    } else
     for (int idx = threadIdx.x; idx < 2 * L * n; idx += blockDim.x) {
         const int r = fdiv(idx, n, D.rn), i = idx - r * n;
         const int line = line0 + r;
         T val = (T)0;
-        if (line < nlines) {
+        if (line < nlines && MODE == XF_MIX_LOAD) {
+            val = ldp<CG>((const T *)a.out + (size_t)line * n + i);
+        } else if (line < nlines) {
             const int k = fdiv(line, g.ny, g.rny), j = line - k * g.ny;
             if (MODE == XF_F64_DIVQ) {
                 const double f = div_q<CG>(g, i, j, k, g.dvx_s, g.dvy_s, g.dvz_s[k], a.qx, a.qy, a.qz);
@@ -445,7 +373,6 @@ __device__ __forceinline__ void xfwd_body(const GridDev &g, const FFTDesc &D, in
     }
     if (MODE == XF_MIX_DIVQ) block_max_atomic(mx, &a.st->fmax_bits);
     if (MODE == XF_F64_DIVQ && a.track_fmax) block_max_atomic(mx, &a.st->fmax_bits);
-    if (MODE == XF_MIX_RESID) block_max_atomic(mx, &a.st->rmax_bits[a.slot]);
     __syncthreads();
     // 2. complex FFT
     const T2 *Z = fft_lines<T, false>(A, B, L, ls, D, tw_s);
@@ -460,88 +387,63 @@ __device__ __forceinline__ void xfwd_body(const GridDev &g, const FFTDesc &D, in
             if (line < nlines) out[(size_t)line * n + ix] = v;
         });
     }
-    // 4. mixed residual: the last block to finish decides convergence
-    if (MODE == XF_MIX_RESID) {
-        __shared__ int last;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            __threadfence();
-            const unsigned ticket = atomicAdd(&a.st->done_blocks[a.slot], 1u);
-            last = (ticket == (unsigned)ntiles - 1);
-        }
-        __syncthreads();
-        if (last && threadIdx.x == 0) {
-            __threadfence();
-            const unsigned long long rb = atomicMax(&a.st->rmax_bits[a.slot], 0ull);
-            const unsigned long long fb = atomicMax(&a.st->fmax_bits, 0ull);
-            const double rmax = __longlong_as_double((long long)rb);
-            const double fmax = __longlong_as_double((long long)fb);
-            double rel;
-            const bool done = refine_done<CG>(g, rmax, fmax, a.tol, &rel);
-            a.st->relres = rel;
-            a.st->n_resid = a.slot + 1;
-            a.st->iterations = a.slot;
-            if (done) a.st->converged = 1;
-        }
+}
+
+// Stand-alone launches of the pass bodies: the grid strides over the pass's
+// tiles.  Launched with one block per tile on the main path; a refinement
+// pass that is likely to find the solve converged is launched with the
+// resident grid (CTAs per SM x SMs) and reads the flag once per block, so
+// returning at once costs a few hundred block starts, not one per tile.
+// (The flag is set only by the last tile of a residual pass, so no tile of
+// the same launch is pending once it is set.)
+template <typename T, int MODE>
+__global__ void __launch_bounds__(256) k_xfwd(GridDev g, FFTDesc D, int L, XArgs a, int ntiles) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    if (MODE == XF_MIX_LOAD && *(volatile const int *)&a.st->converged) return;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        xfwd_body<T, MODE, false>(g, D, L, a, t, ntiles, smem_raw);
+        __syncthreads();  // shared memory is reused by the next tile
     }
 }
 
-template <typename T, int MODE>
-__global__ void __launch_bounds__(256) k_xfwd(GridDev g, FFTDesc D, int L, XArgs a) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    xfwd_body<T, MODE, false>(g, D, L, a, blockIdx.x, gridDim.x, smem_raw);
-}
-
-// Residual-only check (no transform): max |f - L_h p| into rmax_bits[slot];
-// the last block sets relres/converged.  f_from_q != 0: f = rho0 D(q) on the fly.
+// FP64-mode check (FIZZY_FLAG_CHECK): relres = max|f - L_h p| / max|f| with
+// f = rho0 D(q') recomputed; the last block writes relres.
 // Virtual block: x = tile of 256 cells along x, y = j, z = k.
 template <bool CG>
-__device__ __forceinline__ void residmax_body(const GridDev &g, const XArgs &a, int f_from_q, VB vb,
-                                              int ntiles) {
-    if (!f_from_q && ldp<CG>(&a.st->converged)) return;
+__device__ __forceinline__ void residmax_body(const GridDev &g, const XArgs &a, VB vb, int ntiles) {
     const int i = vb.x * blockDim.x + threadIdx.x;
     const int j = vb.y, k = vb.z;
     unsigned long long mx = 0ull, fm = 0ull;
     if (i < g.nx) {
-        if (f_from_q) {  // FP64-mode check: f recomputed from q
-            const double f = div_q<CG>(g, i, j, k, g.dvx, g.dvy, g.dvz[k], a.qx, a.qy, a.qz);
-            fm = absbits(f);
-            mx = absbits(f - lap<CG>(g, i, j, k, a.p));
-        } else {
-            mx = absbits(resid<CG>(g, i, j, k, a.f, a.p));
-        }
+        const double f = div_q<CG>(g, i, j, k, g.dvx, g.dvy, g.dvz[k], a.qx, a.qy, a.qz);
+        fm = absbits(f);
+        mx = absbits(f - lap<CG>(g, i, j, k, a.p));
     }
-    block_max_atomic(mx, &a.st->rmax_bits[a.slot]);
-    if (f_from_q) block_max_atomic(fm, &a.st->fmax_bits);
+    block_max_atomic(mx, &a.st->rmax_bits[0]);
+    block_max_atomic(fm, &a.st->fmax_bits);
     __shared__ int last;
     __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
-        const unsigned ticket = atomicAdd(&a.st->done_blocks[a.slot], 1u);
+        const unsigned ticket = atomicAdd(&a.st->done_blocks[0], 1u);
         last = (ticket == (unsigned)ntiles - 1);
     }
     __syncthreads();
     if (last && threadIdx.x == 0) {
         __threadfence();
-        const unsigned long long rb = atomicMax(&a.st->rmax_bits[a.slot], 0ull);
-        const unsigned long long fb = atomicMax(&a.st->fmax_bits, 0ull);
-        const double rmax = __longlong_as_double((long long)rb);
-        const double fmax = __longlong_as_double((long long)fb);
-        if (!f_from_q) {
-            double rel;
-            const bool done = refine_done<CG>(g, rmax, fmax, a.tol, &rel);
-            a.st->relres = rel;
-            a.st->n_resid = a.slot + 1;
-            a.st->iterations = a.slot;
-            if (done) a.st->converged = 1;
-        } else {
-            a.st->relres = fmax > 0.0 ? rmax / fmax : rmax;
-        }
+        const double rmax = __longlong_as_double((long long)atomicMax(&a.st->rmax_bits[0], 0ull));
+        const double fmax = __longlong_as_double((long long)atomicMax(&a.st->fmax_bits, 0ull));
+        a.st->relres = fmax > 0.0 ? rmax / fmax : rmax;
     }
 }
 
-__global__ void __launch_bounds__(256) k_residmax(GridDev g, XArgs a, int f_from_q) {
-    residmax_body<false>(g, a, f_from_q, vb_of_grid(), gridDim.x * gridDim.y * gridDim.z);
+// tiles: rgx x-segments of 256 cells per (j, k) row
+__global__ void __launch_bounds__(256) k_residmax(GridDev g, XArgs a, int rgx, int ntiles) {
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int row = t / rgx;
+        residmax_body<false>(g, a, VB{t - row * rgx, row % g.ny, row / g.ny}, ntiles);
+        __syncthreads();
+    }
 }
 
 // Forward / inverse y-pass on a tile of TX columns (tile bx) of plane k (in place).
@@ -597,11 +499,17 @@ __device__ __forceinline__ void ypass_body(int nx, int ny, const FFTDesc &D, int
     }
 }
 
+// tiles: ygx column tiles per plane, nz planes
 template <typename T, bool INV>
 __global__ void __launch_bounds__(256) k_ypass(int nx, int ny, FFTDesc D, int TX, T *data,
-                                               const int *conv) {
+                                               const int *conv, int ygx, int ntiles) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    ypass_body<T, INV, false>(nx, ny, D, TX, data, conv, blockIdx.x, blockIdx.y, smem_raw);
+    if (conv && *(volatile const int *)conv) return;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int k = t / ygx;
+        ypass_body<T, INV, false>(nx, ny, D, TX, data, conv, t - k * ygx, k, smem_raw);
+        __syncthreads();
+    }
 }
 
 enum { XI_STORE = 0, XI_ACCUM = 1 };
@@ -653,9 +561,13 @@ __device__ __forceinline__ void xinv_body(const GridDev &g, const FFTDesc &D, in
 
 template <typename T, int MODE>
 __global__ void __launch_bounds__(256) k_xinv(GridDev g, FFTDesc D, int L, const T *in, double *p,
-                                              const DevStats *st) {
+                                              const DevStats *st, int ntiles) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    xinv_body<T, MODE, false>(g, D, L, in, p, st, blockIdx.x, smem_raw);
+    if (MODE == XI_ACCUM && *(volatile const int *)&st->converged) return;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        xinv_body<T, MODE, false>(g, D, L, in, p, st, t, smem_raw);
+        __syncthreads();
+    }
 }
 
 // Tridiagonal z-solves, one per (kx, ky) line, with factorisation tables
@@ -904,10 +816,12 @@ __global__ void __launch_bounds__(THOMAS_BLOCK) k_thomas(GridDev g, int Ux, int 
                                                          const T *__restrict__ mtab,
                                                          const T *__restrict__ ibtab,
                                                          const T *__restrict__ cup, T *data,
-                                                         const int *conv) {
+                                                         const int *conv, int ntiles) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    thomas_body<T, true, false>(g, Ux, Uy, mtab, ibtab, cup, data, conv, blockIdx.x * THOMAS_BLOCK,
-                                (T *)smem_raw);
+    if (conv && *(volatile const int *)conv) return;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x)
+        thomas_body<T, true, false>(g, Ux, Uy, mtab, ibtab, cup, data, conv, t * THOMAS_BLOCK,
+                                    (T *)smem_raw);
 }
 
 template <typename T> constexpr size_t thomas_smem() {
@@ -951,6 +865,140 @@ __global__ void __launch_bounds__(256) k_correct(GridDev g, const double *__rest
                                                  double *__restrict__ u, double *__restrict__ v,
                                                  double *__restrict__ w) {
     correct_body<false>(g, p, qx, qy, qz, u, v, w, vb_of_grid());
+}
+
+// Mixed-mode residual r = f - L_h p in FP64, stored as sigma 2^-e r in FP32
+// (the right-hand side of the next FP32 solve, e the exponent of max|f|),
+// with max|r| reduced and the last tile deciding convergence (relres and the
+// divergence rule, refine_done).  CORR fuses the correction
+// u = q' - (dt/rho0) G p, which forms the same face differences; a residual
+// pass that converges has then also written the final u.  Every face
+// difference is formed once: dE, dN, dT from the loads, dW from the lane to
+// the left, dS from the row below through shared memory (double-buffered per
+// plane), dB carried from the plane below.  Wall faces carry zero flux.
+// Virtual block: 32 x 8 cells marching kc planes; sdn: 2 x 8 x 32 doubles.
+constexpr int RESID_KC = 16;  // planes marched by one residual tile
+
+struct RArgs {
+    const double *p, *f, *qx, *qy, *qz;
+    double *u, *v, *w;
+    float *r32;
+    DevStats *st;
+    int slot;
+    double tol;
+};
+
+template <bool CG, bool CORR>
+__device__ __forceinline__ void resid_body(const GridDev &g, int kc, const RArgs &a, VB vb,
+                                           int ntiles, double *sdn) {
+    if (ldp<CG>(&a.st->converged)) return;
+    const int tid = block_tid();
+    const int tx = tid & (FLUX_BX - 1), ty = tid / FLUX_BX;
+    const int i = vb.x * FLUX_BX + tx, j = vb.y * FLUX_BY + ty;
+    const int k0 = vb.z * kc, k1 = min(g.nz, k0 + kc);
+    const bool on = i < g.nx && j < g.ny;
+    const size_t pl = (size_t)g.nx * g.ny;
+    const int ef = exp_of_bits(ldp<CG>(&a.st->fmax_bits));
+    const float scale32 = (float)g.sigma;
+    const bool per_x = g.bcx == BC_PERIODIC, per_y = g.bcy == BC_PERIODIC;
+    const bool hasE = i < g.nx - 1 || per_x, hasW = i > 0 || per_x;
+    const bool hasN = j < g.ny - 1 || per_y, hasS = j > 0 || per_y;
+    const long long oE = (i < g.nx - 1) ? 1 : -(long long)i;
+    const long long oW = (i > 0) ? -1 : (long long)(g.nx - 1);
+    const long long oN = (j < g.ny - 1) ? (long long)g.nx : -(long long)j * g.nx;
+    const long long oS = (j > 0) ? -(long long)g.nx : (long long)(g.ny - 1) * g.nx;
+    size_t c = on ? cidx(g, i, j, k0) : 0;
+    double pc = on ? ldp<CG>(a.p + c) : 0.0;
+    double db = (on && k0 > 0) ? pc - ldp<CG>(a.p + c - pl) : 0.0;
+    unsigned long long mx = 0ull;
+    int buf = 0;
+    for (int k = k0; k < k1; ++k) {
+        double de = 0.0, dn = 0.0, dt = 0.0, pt = 0.0;
+        if (on) {
+            if (hasE) de = ldp<CG>(a.p + c + oE) - pc;
+            if (hasN) dn = ldp<CG>(a.p + c + oN) - pc;
+            if (k < g.nz - 1) {
+                pt = ldp<CG>(a.p + c + pl);
+                dt = pt - pc;
+            }
+            if (CORR) {
+                a.u[c] = (g.bcx == BC_NEUMANN && i == g.nx - 1) ? 0.0 : fmaT(-g.cgx, de, ldp<CG>(a.qx + c));
+                a.v[c] = (g.bcy == BC_NEUMANN && j == g.ny - 1) ? 0.0 : fmaT(-g.cgy, dn, ldp<CG>(a.qy + c));
+                a.w[c] = (k < g.nz - 1) ? fmaT(-g.cgz[k], dt, ldp<CG>(a.qz + c)) : 0.0;
+            }
+            sdn[(buf * FLUX_BY + ty) * FLUX_BX + tx] = dn;
+        }
+        double dw = __shfl_up_sync(0xffffffffu, de, 1);
+        __syncthreads();
+        if (on) {
+            if (tx == 0) dw = hasW ? pc - ldp<CG>(a.p + c + oW) : 0.0;
+            const double ds = (ty > 0) ? sdn[(buf * FLUX_BY + ty - 1) * FLUX_BX + tx]
+                                       : (hasS ? pc - ldp<CG>(a.p + c + oS) : 0.0);
+            double res = fmaT(-g.idx2, de - dw, ldp<CG>(a.f + c));
+            res = fmaT(-g.idy2, dn - ds, res);
+            res = fmaT(-g.lzc[k], dt, res);
+            res = fmaT(g.lza[k], db, res);
+            mx = umax64(mx, absbits(res));
+            a.r32[c] = f64_to_f32_shift(res, ef) * scale32;
+        }
+        db = dt;
+        pc = pt;
+        c += pl;
+        buf ^= 1;
+    }
+    block_max_atomic(mx, &a.st->rmax_bits[a.slot]);
+    __shared__ int last;
+    __syncthreads();
+    if (tid == 0) {
+        __threadfence();
+        const unsigned ticket = atomicAdd(&a.st->done_blocks[a.slot], 1u);
+        last = (ticket == (unsigned)ntiles - 1);
+    }
+    __syncthreads();
+    if (last && tid == 0) {
+        __threadfence();
+        const unsigned long long rb = atomicMax(&a.st->rmax_bits[a.slot], 0ull);
+        const unsigned long long fb = atomicMax(&a.st->fmax_bits, 0ull);
+        double rel;
+        const bool done = refine_done<CG>(g, __longlong_as_double((long long)rb),
+                                          __longlong_as_double((long long)fb), a.tol, &rel);
+        a.st->relres = rel;
+        a.st->n_resid = a.slot + 1;
+        a.st->iterations = a.slot;
+        __threadfence();  // the stats are visible before the flag
+        if (done) a.st->converged = 1;
+    }
+}
+
+// One block per tile; tiles of kc planes.
+template <bool CORR>
+__global__ void __launch_bounds__(256) k_resid(GridDev g, int kc, RArgs a, int tgx, int tgy,
+                                               int ntiles) {
+    __shared__ double sdn[2 * FLUX_BY * FLUX_BX];
+    if (*(volatile const int *)&a.st->converged) return;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int txy = tgx * tgy, z = t / txy, r = t - z * txy, y = r / tgx;
+        resid_body<false, CORR>(g, kc, a, VB{r - y * tgx, y, z}, ntiles, sdn);
+        __syncthreads();
+    }
+}
+
+// The correction when no fused residual pass has run (the solve converged
+// at the first residual, or no refinement sweep is allowed): runs only when
+// n_resid == 1; otherwise the fused pass has written u.  Tiles: 32 x 8 cells
+// of one plane.
+__global__ void __launch_bounds__(256) k_correct_if(GridDev g, const double *__restrict__ p,
+                                                    const double *__restrict__ qx,
+                                                    const double *__restrict__ qy,
+                                                    const double *__restrict__ qz,
+                                                    double *__restrict__ u, double *__restrict__ v,
+                                                    double *__restrict__ w, const DevStats *st,
+                                                    int tgx, int tgy, int ntiles) {
+    if (*(volatile const int *)&st->n_resid != 1) return;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int txy = tgx * tgy, z = t / txy, r = t - z * txy, y = r / tgx;
+        correct_body<false>(g, p, qx, qy, qz, u, v, w, VB{r - y * tgx, y, z});
+    }
 }
 
 // max |D u| (diagnostics).
