@@ -332,6 +332,9 @@ struct XArgs {
     int track_fmax;              // F64_DIVQ: record max|sigma f|
 };
 
+constexpr int PASS_U = 4;   // global loads per thread issued together in the pass load loops
+constexpr int PASS_UC = 2;  // spectral pairs per thread loaded together before the inverse combine
+
 // Forward x-pass: per CTA 2L real x-lines (flattened line index (k, j)).
 template <typename T, int MODE, bool CG>
 __device__ __forceinline__ void xfwd_body(const GridDev &g, const FFTDesc &D, int L, const XArgs &a,
@@ -350,13 +353,30 @@ __device__ __forceinline__ void xfwd_body(const GridDev &g, const FFTDesc &D, in
     unsigned long long mx = 0ull;
     const float scale32 = (float)g.sigma;
     // 1. source values into the packed complex lines
+    if (MODE == XF_MIX_LOAD) {  // PASS_U loads per thread in flight
+        const int total = 2 * L * n;
+        for (int base = threadIdx.x; base < total; base += PASS_U * blockDim.x) {
+            T v[PASS_U];
+#pragma unroll
+            for (int u = 0; u < PASS_U; ++u) {
+                const int idx = base + u * blockDim.x;
+                const int r = fdiv(idx, n, D.rn), i = idx - r * n;
+                v[u] = (idx < total && line0 + r < nlines)
+                           ? ldp<CG>((const T *)a.out + (size_t)(line0 + r) * n + i) : (T)0;
+            }
+#pragma unroll
+            for (int u = 0; u < PASS_U; ++u) {
+                const int idx = base + u * blockDim.x;
+                const int r = fdiv(idx, n, D.rn), i = idx - r * n;
+                if (idx < total) ((T *)(A + (r >> 1) * ls))[2 * line_pos(i, n, D.kind) + (r & 1)] = v[u];
+            }
+        }
+    } else
     for (int idx = threadIdx.x; idx < 2 * L * n; idx += blockDim.x) {
         const int r = fdiv(idx, n, D.rn), i = idx - r * n;
         const int line = line0 + r;
         T val = (T)0;
-        if (line < nlines && MODE == XF_MIX_LOAD) {
-            val = ldp<CG>((const T *)a.out + (size_t)line * n + i);
-        } else if (line < nlines) {
+        if (line < nlines) {
             const int k = fdiv(line, g.ny, g.rny), j = line - k * g.ny;
             if (MODE == XF_F64_DIVQ) {
                 const double f = div_q<CG>(g, i, j, k, g.dvx_s, g.dvy_s, g.dvz_s[k], a.qx, a.qy, a.qz);
@@ -466,10 +486,22 @@ __device__ __forceinline__ void ypass_body(int nx, int ny, const FFTDesc &D, int
     const int M = n / 2 + 1;
     const unsigned rTX = fdiv_recip(TX), rL = fdiv_recip(L);
     if (!INV) {
-        for (int idx = threadIdx.x; idx < n * TX; idx += blockDim.x) {
-            const int j = fdiv(idx, TX, rTX), c = idx - j * TX;
-            const T val = (c < ncols) ? ldp<CG>(plane + (size_t)j * nx + c) : (T)0;
-            ((T *)(A + (c >> 1) * ls))[2 * line_pos(j, n, D.kind) + (c & 1)] = val;
+        // PASS_U loads per thread in flight before their shared-memory stores
+        const int total = n * TX;
+        for (int base = threadIdx.x; base < total; base += PASS_U * blockDim.x) {
+            T v[PASS_U];
+#pragma unroll
+            for (int u = 0; u < PASS_U; ++u) {
+                const int idx = base + u * blockDim.x;
+                const int j = fdiv(idx, TX, rTX), c = idx - j * TX;
+                v[u] = (idx < total && c < ncols) ? ldp<CG>(plane + (size_t)j * nx + c) : (T)0;
+            }
+#pragma unroll
+            for (int u = 0; u < PASS_U; ++u) {
+                const int idx = base + u * blockDim.x;
+                const int j = fdiv(idx, TX, rTX), c = idx - j * TX;
+                if (idx < total) ((T *)(A + (c >> 1) * ls))[2 * line_pos(j, n, D.kind) + (c & 1)] = v[u];
+            }
         }
         __syncthreads();
         const T2 *Z = fft_lines<T, false>(A, B, L, ls, D, tw_s);
@@ -482,12 +514,35 @@ __device__ __forceinline__ void ypass_body(int nx, int ny, const FFTDesc &D, int
         }
     } else {
         __syncthreads();
-        for (int t = threadIdx.x; t < L * M; t += blockDim.x) {
-            const int m = fdiv(t, L, rL), l = t - m * L;
-            inv_combine<T>(A + l * ls, n, m, D.kind, cs_s, [&](int ab, int ix) -> T {
-                const int c = 2 * l + ab;
-                return (c < ncols) ? ldp<CG>(plane + (size_t)ix * nx + c) : (T)0;
-            });
+        // the spectral values of PASS_UC pairs (m, n-m) of both lines are
+        // loaded before they are combined
+        const int total = L * M;
+        for (int base = threadIdx.x; base < total; base += PASS_UC * blockDim.x) {
+            T v[PASS_UC][4];
+#pragma unroll
+            for (int u = 0; u < PASS_UC; ++u) {
+                const int t = base + u * blockDim.x;
+                const int m = fdiv(t, L, rL), l = t - m * L;
+                const bool two = m > 0 && 2 * m != n;  // Z[m] and Z[n-m] both read
+#pragma unroll
+                for (int ab = 0; ab < 2; ++ab) {
+                    const int c = 2 * l + ab;
+                    const bool ok = t < total && c < ncols;
+                    v[u][2 * ab] = ok ? ldp<CG>(plane + (size_t)m * nx + c) : (T)0;
+                    v[u][2 * ab + 1] = (ok && two) ? ldp<CG>(plane + (size_t)(n - m) * nx + c) : (T)0;
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < PASS_UC; ++u) {
+                const int t = base + u * blockDim.x;
+                const int m = fdiv(t, L, rL), l = t - m * L;
+                if (t < total)
+                    inv_combine<T>(A + l * ls, n, m, D.kind, cs_s,
+                                   [&](int ab, int ix) -> T {
+                                       return ab == 0 ? (ix == m ? v[u][0] : v[u][1])
+                                                      : (ix == m ? v[u][2] : v[u][3]);
+                                   });
+            }
         }
         __syncthreads();
         const T2 *Z = fft_lines<T, true>(A, B, L, ls, D, tw_s);
@@ -531,29 +586,67 @@ __device__ __forceinline__ void xinv_body(const GridDev &g, const FFTDesc &D, in
     const int line0 = bx * 2 * L;
     const int M = n / 2 + 1;
     __syncthreads();
-    for (int t = threadIdx.x; t < L * M; t += blockDim.x) {
-        const int l = fdiv(t, M, D.rM), m = t - l * M;
-        const int la = line0 + 2 * l;
-        inv_combine<T>(A + l * ls, n, m, D.kind, cs_s, [&](int ab, int ix) -> T {
-            const int line = la + ab;
-            return (line < nlines) ? ldp<CG>(in + (size_t)line * n + ix) : (T)0;
-        });
+    const int total = L * M;
+    for (int base = threadIdx.x; base < total; base += PASS_UC * blockDim.x) {
+        T v[PASS_UC][4];
+#pragma unroll
+        for (int u = 0; u < PASS_UC; ++u) {
+            const int t = base + u * blockDim.x;
+            const int l = fdiv(t, M, D.rM), m = t - l * M;
+            const bool two = m > 0 && 2 * m != n;  // Z[m] and Z[n-m] both read
+#pragma unroll
+            for (int ab = 0; ab < 2; ++ab) {
+                const int line = line0 + 2 * l + ab;
+                const bool ok = t < total && line < nlines;
+                v[u][2 * ab] = ok ? ldp<CG>(in + (size_t)line * n + m) : (T)0;
+                v[u][2 * ab + 1] = (ok && two) ? ldp<CG>(in + (size_t)line * n + (n - m)) : (T)0;
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < PASS_UC; ++u) {
+            const int t = base + u * blockDim.x;
+            const int l = fdiv(t, M, D.rM), m = t - l * M;
+            if (t < total)
+                inv_combine<T>(A + l * ls, n, m, D.kind, cs_s,
+                               [&](int ab, int ix) -> T {
+                                       return ab == 0 ? (ix == m ? v[u][0] : v[u][1])
+                                                      : (ix == m ? v[u][2] : v[u][3]);
+                                   });
+        }
     }
     __syncthreads();
     const T2 *Z = fft_lines<T, true>(A, B, L, ls, D, tw_s);
     int ef = 0;
     if (MODE == XI_ACCUM) ef = exp_of_bits(ldp<CG>(&st->fmax_bits));
-    for (int idx = threadIdx.x; idx < 2 * L * n; idx += blockDim.x) {
-        const int r = fdiv(idx, n, D.rn), i = idx - r * n;
-        const int line = line0 + r;
-        if (line < nlines) {
-            const T v = ((const T *)(Z + (r >> 1) * ls))[2 * line_pos(i, n, D.kind) + (r & 1)];
-            double *dst = p + (size_t)line * n + i;
-            if (MODE == XI_STORE) {
+    if (MODE == XI_STORE) {
+        for (int idx = threadIdx.x; idx < 2 * L * n; idx += blockDim.x) {
+            const int r = fdiv(idx, n, D.rn), i = idx - r * n;
+            const int line = line0 + r;
+            if (line < nlines) {
+                const T v = ((const T *)(Z + (r >> 1) * ls))[2 * line_pos(i, n, D.kind) + (r & 1)];
+                double *dst = p + (size_t)line * n + i;
                 if (sizeof(T) == 8) *dst = (double)v;
                 else *dst = f32_to_f64_shift((float)v, 0);
-            } else {
-                *dst = ldp<CG>(dst) + f32_to_f64_shift((float)v, ef);
+            }
+        }
+    } else {  // p += delta: PASS_U loads of p per thread in flight
+        const int total = 2 * L * n;
+        for (int base = threadIdx.x; base < total; base += PASS_U * blockDim.x) {
+            double pv[PASS_U];
+#pragma unroll
+            for (int u = 0; u < PASS_U; ++u) {
+                const int idx = base + u * blockDim.x;
+                const int r = fdiv(idx, n, D.rn), i = idx - r * n;
+                pv[u] = (idx < total && line0 + r < nlines) ? ldp<CG>(p + (size_t)(line0 + r) * n + i) : 0.0;
+            }
+#pragma unroll
+            for (int u = 0; u < PASS_U; ++u) {
+                const int idx = base + u * blockDim.x;
+                const int r = fdiv(idx, n, D.rn), i = idx - r * n;
+                if (idx < total && line0 + r < nlines) {
+                    const T v = ((const T *)(Z + (r >> 1) * ls))[2 * line_pos(i, n, D.kind) + (r & 1)];
+                    p[(size_t)(line0 + r) * n + i] = pv[u] + f32_to_f64_shift((float)v, ef);
+                }
             }
         }
     }
