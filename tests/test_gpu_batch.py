@@ -76,6 +76,40 @@ def test_batch_equals_alone(cuda_ok, precision):
         p.close()
 
 
+def test_batch_first_residual_convergence_equals_alone(cuda_ok):
+    """Mixed instances with a loose tolerance stop at the residual of the FP32
+    solution, so the batch takes its conditional-correction pass; results
+    stay bitwise equal to each plan solved alone."""
+    import torch
+    cases = [I.make_case(s) for s in small_batch_specs(4)]
+    kw = dict(tol=1e-3, div_tol=1.0)
+    alone = []
+    for c in cases:
+        plan = F.Plan.for_case(c, precision=F.MIXED, **kw)
+        u, v, w = to_dev(c.u), to_dev(c.v), to_dev(c.w)
+        p = torch.empty_like(u)
+        plan.solve(to_dev(c.phi), to_dev(c.pn), to_dev(c.pnm1), u, v, w, p)
+        torch.cuda.synchronize()
+        alone.append(dict(p=p.cpu().numpy(), u=u.cpu().numpy(), v=v.cpu().numpy(),
+                          w=w.cpu().numpy(), stats=plan.stats()))
+        plan.close()
+    assert all(a["stats"]["iterations"] == 0 for a in alone)
+    plans = [F.Plan.for_case(c, precision=F.MIXED, **kw) for c in cases]
+    arrays = [(to_dev(c.phi), to_dev(c.pn), to_dev(c.pnm1), to_dev(c.u), to_dev(c.v), to_dev(c.w),
+               torch.empty(c.shape, dtype=torch.float64, device="cuda")) for c in cases]
+    batch = F.Batch(plans, arrays)
+    batch.solve()
+    assert batch.status() == 0
+    for c, arr, a, plan in zip(cases, arrays, alone, plans):
+        for key, t in (("p", arr[6]), ("u", arr[3]), ("v", arr[4]), ("w", arr[5])):
+            assert np.array_equal(t.cpu().numpy(), a[key]), (c.spec, key)
+        st = plan.stats()
+        assert st["converged"] == 1 and st["iterations"] == 0
+    batch.close()
+    for p in plans:
+        p.close()
+
+
 def test_batch_autotune_keeps_results(cuda_ok):
     import torch
     cases = [I.make_case(s) for s in small_batch_specs(4)]

@@ -117,6 +117,23 @@ def test_not_converged_is_reported(cuda_ok):
     assert ep < 1e-6  # one sweep still lands close
 
 
+def test_mixed_converged_at_first_residual(cuda_ok):
+    """A loose tolerance stops at the residual of the FP32 solution (no
+    refinement sweep): the final correction then runs on its own and u must
+    be the corrected field, within the accuracy of the FP32 solve."""
+    c = I.make_case(CASES["b96x64x33"])
+    got = gpu_project(c, F.MIXED, tol=1e-3, div_tol=1.0)
+    st = got["stats"]
+    assert st["converged"] == 1 and st["iterations"] == 0, st
+    assert 0 < st["relres"] <= 1e-3
+    ref = O.project_case(c)
+    ep, eu = compare(c, got, ref)
+    assert ep < 1e-4 and eu < 1e-4, (ep, eu)
+    # u is not the provisional velocity
+    moved = max(np.max(np.abs(got[k] - getattr(c, k))) for k in "uvw")
+    assert moved > 1e3 * eu * max(np.max(np.abs(ref[k])) for k in "uvw")
+
+
 def test_solve_host_matches_device(cuda_ok):
     c = I.make_case(CASES["b96x64x33"])
     plan = F.Plan.for_case(c, precision=F.FP64)
