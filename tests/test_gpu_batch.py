@@ -110,6 +110,37 @@ def test_batch_first_residual_convergence_equals_alone(cuda_ok):
         p.close()
 
 
+@pytest.mark.parametrize("precision", [F.MIXED, F.FP64], ids=["mixed", "fp64"])
+def test_batch_swapped_density_equals_alone(cuda_ok, precision):
+    """An instance whose lighter phase is the drop phase (rho0 = rho_l, the
+    split term formed from 1 - phi) batched with an ordinary one."""
+    import dataclasses
+    import torch
+    base = small_batch_specs(3)
+    specs = [base[0], dataclasses.replace(base[1], rho_l=base[1].rho_g, rho_g=base[1].rho_l)]
+    assert specs[1].rho_l < specs[1].rho_g
+    cases = [I.make_case(sp) for sp in specs]
+    alone = [run_alone(c, precision) for c in cases]
+    plans = [F.Plan.for_case(c, precision=precision) for c in cases]
+    arrays = [(to_dev(c.phi), to_dev(c.pn), to_dev(c.pnm1), to_dev(c.u), to_dev(c.v), to_dev(c.w),
+               torch.empty(c.shape, dtype=torch.float64, device="cuda")) for c in cases]
+    batch = F.Batch(plans, arrays)
+    batch.solve()
+    assert batch.status() == 0
+    for c, arr, a in zip(cases, arrays, alone):
+        for key, t in (("p", arr[6]), ("u", arr[3]), ("v", arr[4]), ("w", arr[5])):
+            assert np.array_equal(t.cpu().numpy(), a[key]), (c.spec, key)
+    ref = O.project_case(cases[1])
+    got = dict(p=arrays[1][6].cpu().numpy(), u=arrays[1][3].cpu().numpy(),
+               v=arrays[1][4].cpu().numpy(), w=arrays[1][5].cpu().numpy())
+    ep, eu = compare(cases[1], got, ref)
+    tol = 1e-9 if precision == F.MIXED else 1e-12
+    assert ep <= tol and eu <= tol, (ep, eu)
+    batch.close()
+    for p in plans:
+        p.close()
+
+
 def test_batch_autotune_keeps_results(cuda_ok):
     import torch
     cases = [I.make_case(s) for s in small_batch_specs(4)]
