@@ -85,6 +85,37 @@ def algorithmic_per_point(nx, ny, mixed):
         "resid_correct": (68, 20), "correct": (56, 12)}
 
 
+def fft_fp64_instr_per_point(n, dct):
+    """FP64 instructions per real point of one paired real transform of length
+    n, counted from the Stockham stages (radix-4 then 2 then 3; a stage of span
+    1 has no twiddles): radix-4 16 adds or 24 FMAs per butterfly, radix-2 4 or
+    6, radix-3 12 or 20; two real lines share each complex point.  The
+    separation adds 1 per real point, the DCT post-twiddle 2 more."""
+    rad = []
+    m = n
+    for r in (4, 2, 3):
+        while m % r == 0:
+            rad.append(r)
+            m //= r
+    first = {4: 16 / 4, 2: 4 / 2, 3: 12 / 3}
+    later = {4: 24 / 4, 2: 6 / 2, 3: 20 / 3}
+    per_complex = sum(first[r] if i == 0 else later[r] for i, r in enumerate(rad))
+    return per_complex / 2 + 1 + (2 if dct else 0)
+
+
+def fp64_instr_per_point(nx, ny, bcx, bcy, mixed):
+    """FP64 instructions per grid point of each kernel, counted from the code
+    (flux 6 per face + phat; divergence 6; z-solve 3; correction 6; mixed
+    residual 10, fused with the correction 13)."""
+    fx = fft_fp64_instr_per_point(nx, bcx == 1)
+    fy = fft_fp64_instr_per_point(ny, bcy == 1)
+    if not mixed:
+        return {"flux": 19, "div_fwdx": 6 + fx, "fwd_y": fy, "thomas": 3, "inv_y": fy,
+                "inv_x": fx, "correct": 6}
+    return {"flux": 19, "div_fwdx": 6, "resid": 10, "resid_correct": 13, "inv_x_update": 1,
+            "correct": 6}
+
+
 class ClockSampler:
     """nvidia-smi clocks/throttle sampling during the timed region."""
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -306,6 +337,14 @@ def run_fizzy(args):
     if roof:
         roof["launches_timed"] = cnt
         roof["duration_ms"] = tot_ms / cnt
+        # the FP64 issue rate the ALU bound really is: FP64 instructions per
+        # point against the nominal 0.625 T FP64 instructions/s (1.25 TFLOP/s
+        # counts an FMA as two)
+        ipt = fp64_instr_per_point(spec.nx, spec.ny, spec.bcx, spec.bcy, prec == F.MIXED).get(dom)
+        if ipt:
+            ach = ipt * npts / avg_s / 1e12
+            roof["fp64_issue"] = {"instr_per_pt": ipt, "achieved": ach, "peak": FP64_PEAK_NOMINAL / 2,
+                                  "unit": "T instr/s", "frac": ach / (FP64_PEAK_NOMINAL / 2)}
     kernels = {k: {"ms_avg": v[0] / v[1], "launches": v[1],
                    "share": v[0] / max(1e-9, sum(x[0] for x in kern.values()))} for k, v in kern.items()}
 
