@@ -139,11 +139,31 @@ int fizzy_proj_get_stats(fizzy_proj_plan_t p, fizzy_proj_stats *st, void *stream
 
 /* End-to-end variant on HOST buffers (pinned memory recommended): copies the
  * six inputs to plan-owned device buffers, solves, copies u, v, w and p back,
- * and synchronises the stream.  The device staging buffers are allocated on
- * first use and kept by the plan. */
+ * and waits for the copies (fizzy_proj_solve_host_async + fizzy_proj_host_wait).
+ * The device staging buffers are allocated on first use and kept by the plan. */
 int fizzy_proj_solve_host(fizzy_proj_plan_t p, const double *phi, const double *p_n,
                           const double *p_nm1, double *u, double *v, double *w, double *p_np1,
                           fizzy_proj_stats *st, void *stream);
+
+/* Pipelined end-to-end solves on HOST buffers.  Each call queues the copy of
+ * the six inputs (u_in, v_in, w_in hold u*), the solve on stream, and the copy
+ * of u, v, w, p_np1 back, and returns at once.  The plan keeps two device
+ * staging sets and two copy streams of its own: while one call solves, the
+ * next call's inputs and the previous call's results are in transit, so
+ * successive calls overlap their copies with the solves.  Host arrays must be
+ * pinned (cudaHostAlloc / cudaHostRegister) for the copies to run
+ * asynchronously, and must be left untouched (inputs) or unread (outputs)
+ * until fizzy_proj_host_wait returns; the outputs may alias the inputs only
+ * when each call is waited for before the next.  The two staging sets hold
+ * 14 grid fields of device memory (allocated on first use).
+ * fizzy_proj_host_wait blocks until every queued result is in host memory;
+ * fizzy_proj_get_stats then reports the last solve.  Return FIZZY_OK or a
+ * FIZZY_ERR_* code (FIZZY_ERR_NOMEM when the staging cannot be allocated). */
+int fizzy_proj_solve_host_async(fizzy_proj_plan_t p, const double *phi, const double *p_n,
+                                const double *p_nm1, const double *u_in, const double *v_in,
+                                const double *w_in, double *u, double *v, double *w, double *p_np1,
+                                void *stream);
+int fizzy_proj_host_wait(fizzy_proj_plan_t p);
 
 /* Free everything owned by the plan; NULL is a no-op.  Synchronises the device. */
 int fizzy_proj_destroy(fizzy_proj_plan_t p);

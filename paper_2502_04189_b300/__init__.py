@@ -66,6 +66,13 @@ def workspace_bytes(**kw) -> int:
     return int(_abi.lib().fizzy_proj_workspace_bytes(ctypes.byref(d)))
 
 
+def _host_ptr(a):
+    """Address of a host array (CPU tensor or numpy)."""
+    if hasattr(a, "data_ptr"):
+        return ctypes.c_void_p(a.data_ptr())
+    return ctypes.c_void_p(a.ctypes.data)
+
+
 class Plan:
     """A projection plan (fizzy_proj_plan / fizzy_proj_destroy)."""
 
@@ -108,16 +115,26 @@ class Plan:
 
     def solve_host(self, phi, pn, pnm1, u, v, w, p_out, stats=False, stream=None):
         """End-to-end solve on host arrays (numpy or CPU tensors, pinned preferred)."""
-        def hp(a):
-            if hasattr(a, "data_ptr"):
-                return ctypes.c_void_p(a.data_ptr())
-            return ctypes.c_void_p(a.ctypes.data)
+        hp = _host_ptr
         st = Stats() if stats else None
         rc = _abi.lib().fizzy_proj_solve_host(self._h, hp(phi), hp(pn), hp(pnm1), hp(u), hp(v),
                                               hp(w), hp(p_out), ctypes.byref(st) if st else None,
                                               _stream_handle(stream))
         self._check(rc)
         return st.as_dict() if st else None
+
+    def solve_host_async(self, phi, pn, pnm1, u_in, v_in, w_in, u, v, w, p_out, stream=None):
+        """Queue a pipelined end-to-end solve on pinned host arrays (u_in, v_in,
+        w_in hold u*; u, v, w, p_out receive the results); the arrays must stay
+        alive and untouched until host_wait()."""
+        hp = _host_ptr
+        self._check(_abi.lib().fizzy_proj_solve_host_async(
+            self._h, hp(phi), hp(pn), hp(pnm1), hp(u_in), hp(v_in), hp(w_in), hp(u), hp(v), hp(w),
+            hp(p_out), _stream_handle(stream)))
+
+    def host_wait(self):
+        """Block until every queued host solve's results are in host memory."""
+        self._check(_abi.lib().fizzy_proj_host_wait(self._h))
 
     def stats(self, stream=None):
         st = Stats()

@@ -20,7 +20,8 @@ EXPORTED = ("fizzy_proj_plan", "fizzy_proj_workspace_bytes", "fizzy_proj_solve",
             "fizzy_proj_batch_autotune", "fizzy_proj_batch_info", "fizzy_proj_batch_destroy",
             "fizzy_proj_set_physics", "fizzy_serve_create", "fizzy_serve_admit", "fizzy_serve_stream",
             "fizzy_serve_launch", "fizzy_serve_poll", "fizzy_serve_stats", "fizzy_serve_release",
-            "fizzy_serve_info", "fizzy_serve_destroy")
+            "fizzy_serve_info", "fizzy_serve_destroy", "fizzy_proj_solve_host_async",
+            "fizzy_proj_host_wait")
 ERRORS[-7] = "busy"
 NOALLOC_MAX_CELLS = 262144
 DEFAULT_MAX_REFINE = 4  # FIZZY_DEFAULT_MAX_REFINE
@@ -75,6 +76,10 @@ def lib():
         L.fizzy_proj_solve.restype = ctypes.c_int
         L.fizzy_proj_solve_host.argtypes = [vp] + [vp] * 7 + [ctypes.POINTER(Stats), vp]
         L.fizzy_proj_solve_host.restype = ctypes.c_int
+        L.fizzy_proj_solve_host_async.argtypes = [vp] + [vp] * 10 + [vp]
+        L.fizzy_proj_solve_host_async.restype = ctypes.c_int
+        L.fizzy_proj_host_wait.argtypes = [vp]
+        L.fizzy_proj_host_wait.restype = ctypes.c_int
         L.fizzy_proj_get_stats.argtypes = [vp, ctypes.POINTER(Stats), vp]
         L.fizzy_proj_get_stats.restype = ctypes.c_int
         L.fizzy_proj_destroy.argtypes = [vp]

@@ -48,8 +48,13 @@ struct fizzy_proj_plan_s {
     DevStats *st = nullptr;
     double *usq_part = nullptr, *usq_sum = nullptr;
     int n_usq_part = 0;
-    // end-to-end staging (solve_host)
-    double *stage[7] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    // end-to-end staging (solve_host, solve_host_async): two sets of the 7
+    // device fields, two copy streams and their events, made on first use
+    double *stage[2][7] = {};
+    cudaStream_t h2d = nullptr, d2h = nullptr;
+    cudaEvent_t ev_in[2] = {}, ev_done[2] = {}, ev_out[2] = {};
+    bool set_used[2] = {false, false};
+    int host_calls = 0;
     // launch shapes
     int Lx = 1, TXy = 2;
     size_t smem_x64 = 0, smem_x32 = 0, smem_y64 = 0, smem_y32 = 0;
@@ -415,8 +420,15 @@ int fizzy_proj_destroy(fizzy_proj_plan_t p) {
     }
     for (auto &e : p->ev) cudaEventDestroy(e);
     for (void *a : p->allocs) cudaFree(a);
-    for (int t = 0; t < 7; ++t)
-        if (p->stage[t]) cudaFree(p->stage[t]);
+    if (p->d2h) cudaStreamSynchronize(p->d2h);
+    for (int b = 0; b < 2; ++b) {
+        for (int t = 0; t < 7; ++t)
+            if (p->stage[b][t]) cudaFree(p->stage[b][t]);
+        for (cudaEvent_t e : {p->ev_in[b], p->ev_done[b], p->ev_out[b]})
+            if (e) cudaEventDestroy(e);
+    }
+    if (p->h2d) cudaStreamDestroy(p->h2d);
+    if (p->d2h) cudaStreamDestroy(p->d2h);
     delete p;
     return FIZZY_OK;
 }
@@ -834,41 +846,93 @@ int fizzy_proj_solve(fizzy_proj_plan_t p, const double *phi, const double *p_n, 
     return FIZZY_OK;
 }
 
-int fizzy_proj_solve_host(fizzy_proj_plan_t p, const double *phi, const double *p_n,
-                          const double *p_nm1, double *u, double *v, double *w, double *p_np1,
-                          fizzy_proj_stats *st, void *stream) {
-    if (!p) return FIZZY_ERR_INVALID;
-    if (!phi || !p_n || !p_nm1 || !u || !v || !w || !p_np1)
-        return set_err(p, FIZZY_ERR_INVALID, "null array pointer");
-    cudaStream_t s = (cudaStream_t)stream;
-    const size_t N = (size_t)p->desc.nx * p->desc.ny * p->desc.nz;
-    const size_t B = N * sizeof(double);
-    for (int t = 0; t < 7; ++t) {
-        if (!p->stage[t]) {
-            cudaError_t e = cudaMalloc(&p->stage[t], B);
-            if (e != cudaSuccess) {
-                (void)cudaGetLastError();
-                p->stage[t] = nullptr;
-                return set_err(p, FIZZY_ERR_NOMEM, "staging allocation failed");
-            }
-        }
-    }
-    const double *hin[6] = {phi, p_n, p_nm1, u, v, w};
+// Staging for the host-array entry points: both sets, the copy streams and
+// the events, made once.
+static int host_staging(fizzy_proj_plan_t p) {
+    if (p->h2d) return FIZZY_OK;
+    const size_t B = (size_t)p->desc.nx * p->desc.ny * p->desc.nz * sizeof(double);
     cudaError_t e = cudaSuccess;
-    for (int t = 0; t < 6 && e == cudaSuccess; ++t)
-        e = cudaMemcpyAsync(p->stage[t], hin[t], B, cudaMemcpyHostToDevice, s);
-    if (e != cudaSuccess) return cuda_err(p, e, "H2D");
-    int rc = fizzy_proj_solve(p, p->stage[0], p->stage[1], p->stage[2], p->stage[3], p->stage[4],
-                              p->stage[5], p->stage[6], nullptr, stream);
+    for (int b = 0; b < 2 && e == cudaSuccess; ++b)
+        for (int t = 0; t < 7 && e == cudaSuccess; ++t) e = cudaMalloc(&p->stage[b][t], B);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        for (int b = 0; b < 2; ++b)
+            for (int t = 0; t < 7; ++t) {
+                if (p->stage[b][t]) cudaFree(p->stage[b][t]);
+                p->stage[b][t] = nullptr;
+            }
+        return set_err(p, FIZZY_ERR_NOMEM, "staging allocation failed");
+    }
+    for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
+        e = cudaEventCreateWithFlags(&p->ev_in[b], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_done[b], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_out[b], cudaEventDisableTiming);
+    }
+    cudaStream_t h2d = nullptr, d2h = nullptr;
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h2d, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&d2h, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        if (h2d) cudaStreamDestroy(h2d);
+        return cuda_err(p, e, "staging streams");
+    }
+    p->h2d = h2d;
+    p->d2h = d2h;
+    return FIZZY_OK;
+}
+
+int fizzy_proj_solve_host_async(fizzy_proj_plan_t p, const double *phi, const double *p_n,
+                                const double *p_nm1, const double *u_in, const double *v_in,
+                                const double *w_in, double *u, double *v, double *w, double *p_np1,
+                                void *stream) {
+    if (!p) return FIZZY_ERR_INVALID;
+    if (!phi || !p_n || !p_nm1 || !u_in || !v_in || !w_in || !u || !v || !w || !p_np1)
+        return set_err(p, FIZZY_ERR_INVALID, "null array pointer");
+    int rc = host_staging(p);
     if (rc) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t B = (size_t)p->desc.nx * p->desc.ny * p->desc.nz * sizeof(double);
+    const int b = p->host_calls & 1;
+    double *const *d = p->stage[b];
+    // 1. inputs into set b, once its previous results have been copied out
+    cudaError_t e = p->set_used[b] ? cudaStreamWaitEvent(p->h2d, p->ev_out[b], 0) : cudaSuccess;
+    const double *hin[6] = {phi, p_n, p_nm1, u_in, v_in, w_in};
+    for (int t = 0; t < 6 && e == cudaSuccess; ++t)
+        e = cudaMemcpyAsync(d[t], hin[t], B, cudaMemcpyHostToDevice, p->h2d);
+    if (e == cudaSuccess) e = cudaEventRecord(p->ev_in[b], p->h2d);
+    // 2. the solve on the caller's stream
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, p->ev_in[b], 0);
+    if (e != cudaSuccess) return cuda_err(p, e, "H2D");
+    rc = fizzy_proj_solve(p, d[0], d[1], d[2], d[3], d[4], d[5], d[6], nullptr, stream);
+    if (rc) return rc;
+    e = cudaEventRecord(p->ev_done[b], s);
+    // 3. results back
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(p->d2h, p->ev_done[b], 0);
     double *hout[4] = {u, v, w, p_np1};
     const int src[4] = {3, 4, 5, 6};
     for (int t = 0; t < 4 && e == cudaSuccess; ++t)
-        e = cudaMemcpyAsync(hout[t], p->stage[src[t]], B, cudaMemcpyDeviceToHost, s);
+        e = cudaMemcpyAsync(hout[t], d[src[t]], B, cudaMemcpyDeviceToHost, p->d2h);
+    if (e == cudaSuccess) e = cudaEventRecord(p->ev_out[b], p->d2h);
     if (e != cudaSuccess) return cuda_err(p, e, "D2H");
+    p->set_used[b] = true;
+    ++p->host_calls;
+    return FIZZY_OK;
+}
+
+int fizzy_proj_host_wait(fizzy_proj_plan_t p) {
+    if (!p) return FIZZY_ERR_INVALID;
+    if (!p->d2h) return FIZZY_OK;
+    const cudaError_t e = cudaStreamSynchronize(p->d2h);
+    if (e != cudaSuccess) return cuda_err(p, e, "host wait");
+    return FIZZY_OK;
+}
+
+int fizzy_proj_solve_host(fizzy_proj_plan_t p, const double *phi, const double *p_n,
+                          const double *p_nm1, double *u, double *v, double *w, double *p_np1,
+                          fizzy_proj_stats *st, void *stream) {
+    int rc = fizzy_proj_solve_host_async(p, phi, p_n, p_nm1, u, v, w, u, v, w, p_np1, stream);
+    if (rc == FIZZY_OK) rc = fizzy_proj_host_wait(p);
+    if (rc) return rc;
     if (st) return fizzy_proj_get_stats(p, st, stream);
-    e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess) return cuda_err(p, e, "sync");
     return FIZZY_OK;
 }
 
