@@ -11,6 +11,7 @@
 #include <cstdlib>
 #include <cstdint>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -64,6 +65,7 @@ struct fizzy_proj_plan_s {
     int async_alloc = 0;
     cudaStream_t alloc_stream = nullptr;
     double *zt = nullptr;  // per-k tables (physics-dependent rows first)
+    cudaError_t setup_err = cudaSuccess;  // first failed CUDA call while the plan is built
     // per-kernel timing
     int timing = 0;
     std::vector<cudaEvent_t> ev;        // 2 per recorded launch
@@ -99,6 +101,11 @@ bool radix23(int n) {
 int set_err(fizzy_proj_plan_t p, int code, const std::string &msg) {
     if (p) p->err = msg;
     return code;
+}
+
+// Keep the first failing CUDA call of plan construction (checked at its end).
+void note(fizzy_proj_plan_t p, cudaError_t e) {
+    if (e != cudaSuccess && p->setup_err == cudaSuccess) p->setup_err = e;
 }
 
 int cuda_err(fizzy_proj_plan_t p, cudaError_t e, const char *where) {
@@ -221,11 +228,11 @@ int build_fft(fizzy_proj_plan_t p, int n, int bc, FFTHost &F, int *status) {
         F.cs32 = dev_alloc<float>(p, cs32.size(), status);
     }
     if (*status) return *status;
-    cudaMemcpyAsync(F.tw64, tw.data(), tw.size() * sizeof(double), cudaMemcpyHostToDevice, p->alloc_stream);
-    cudaMemcpyAsync(F.cs64, cs.data(), cs.size() * sizeof(double), cudaMemcpyHostToDevice, p->alloc_stream);
+    note(p, cudaMemcpyAsync(F.tw64, tw.data(), tw.size() * sizeof(double), cudaMemcpyHostToDevice, p->alloc_stream));
+    note(p, cudaMemcpyAsync(F.cs64, cs.data(), cs.size() * sizeof(double), cudaMemcpyHostToDevice, p->alloc_stream));
     if (p->mixed) {
-        cudaMemcpyAsync(F.tw32, tw32.data(), tw32.size() * sizeof(float), cudaMemcpyHostToDevice, p->alloc_stream);
-        cudaMemcpyAsync(F.cs32, cs32.data(), cs32.size() * sizeof(float), cudaMemcpyHostToDevice, p->alloc_stream);
+        note(p, cudaMemcpyAsync(F.tw32, tw32.data(), tw32.size() * sizeof(float), cudaMemcpyHostToDevice, p->alloc_stream));
+        note(p, cudaMemcpyAsync(F.cs32, cs32.data(), cs32.size() * sizeof(float), cudaMemcpyHostToDevice, p->alloc_stream));
     }
     FFTDesc d;
     memset(&d, 0, sizeof(d));
@@ -486,7 +493,7 @@ int fizzy_proj_plan(fizzy_proj_plan_t *out, const fizzy_proj_desc *d, void *stre
         return st;
     }
     p->zt = zt_d;
-    cudaMemcpyAsync(zt_d, zt.data(), zt.size() * sizeof(double), cudaMemcpyHostToDevice, p->alloc_stream);
+    note(p, cudaMemcpyAsync(zt_d, zt.data(), zt.size() * sizeof(double), cudaMemcpyHostToDevice, p->alloc_stream));
 
     GridDev &g = p->g;
     memset(&g, 0, sizeof(g));
@@ -566,19 +573,19 @@ int fizzy_proj_plan(fizzy_proj_plan_t *out, const fizzy_proj_desc *d, void *stre
             fizzy_proj_destroy(p);
             return st;
         }
-        cudaMemcpyAsync(lam_d, lam.data(), lam.size() * sizeof(double), cudaMemcpyHostToDevice, p->alloc_stream);
+        note(p, cudaMemcpyAsync(lam_d, lam.data(), lam.size() * sizeof(double), cudaMemcpyHostToDevice, p->alloc_stream));
         const int blocks = (int)std::min<size_t>((ts + 127) / 128, 4096);
         k_ztables<<<blocks, 128, 0, p->alloc_stream>>>(Ux, Uy, nz, lam_d, lam_d + Ux, zt_d + T_LZA * nz,
                                                        zt_d + T_LZC * nz, p->mtab64, p->ibtab64,
                                                        p->mixed ? p->mtab32 : nullptr,
                                                        p->mixed ? p->ibtab32 : nullptr);
     }
-    cudaMemcpyAsync(p->cup64, C, nz * sizeof(double), cudaMemcpyHostToDevice, p->alloc_stream);
+    note(p, cudaMemcpyAsync(p->cup64, C, nz * sizeof(double), cudaMemcpyHostToDevice, p->alloc_stream));
     if (p->mixed) {
         std::vector<float> c32(C, C + nz);
-        cudaMemcpyAsync(p->cup32, c32.data(), nz * sizeof(float), cudaMemcpyHostToDevice, p->alloc_stream);
+        note(p, cudaMemcpyAsync(p->cup32, c32.data(), nz * sizeof(float), cudaMemcpyHostToDevice, p->alloc_stream));
     }
-    cudaMemsetAsync(p->st, 0, sizeof(DevStats), p->alloc_stream);
+    note(p, cudaMemsetAsync(p->st, 0, sizeof(DevStats), p->alloc_stream));
 
     // ---- launch shapes and shared-memory opt-in
     p->Lx = x_lines_per_cta(nx);
@@ -587,27 +594,33 @@ int fizzy_proj_plan(fizzy_proj_plan_t *out, const fizzy_proj_desc *d, void *stre
     p->smem_x32 = pass_smem<float>(nx, p->Lx);
     p->smem_y64 = pass_smem<double>(ny, p->TXy / 2);
     p->smem_y32 = pass_smem<float>(ny, p->TXy / 2);
-    static bool attrs_set[256] = {false};  // opt-in shared-memory limits, once per device
-    int cur_dev = 0;
-    cudaGetDevice(&cur_dev);
-    if (cur_dev < 0 || cur_dev >= 256 || !attrs_set[cur_dev]) {
-    if (cur_dev >= 0 && cur_dev < 256) attrs_set[cur_dev] = true;
-    const int big = 200 * 1024;
-    cudaFuncSetAttribute(k_xfwd<double, XF_F64_DIVQ>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-    cudaFuncSetAttribute(k_xfwd<float, XF_MIX_DIVQ>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-    cudaFuncSetAttribute(k_xfwd<float, XF_MIX_LOAD>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-    cudaFuncSetAttribute(k_xinv<double, XI_STORE>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-    cudaFuncSetAttribute(k_xinv<float, XI_STORE>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-    cudaFuncSetAttribute(k_xinv<float, XI_ACCUM>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-    cudaFuncSetAttribute(k_ypass<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-    cudaFuncSetAttribute(k_ypass<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-    cudaFuncSetAttribute(k_ypass<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-    cudaFuncSetAttribute(k_ypass<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    {  // opt-in shared-memory limits, once per device (plans may be built concurrently)
+        static std::mutex attrs_mu;
+        static bool attrs_set[256] = {false};
+        int cur_dev = 0;
+        note(p, cudaGetDevice(&cur_dev));
+        std::lock_guard<std::mutex> lock(attrs_mu);
+        if (cur_dev < 0 || cur_dev >= 256 || !attrs_set[cur_dev]) {
+            if (cur_dev >= 0 && cur_dev < 256) attrs_set[cur_dev] = true;
+            const int big = 200 * 1024;
+            const cudaFuncAttribute A = cudaFuncAttributeMaxDynamicSharedMemorySize;
+            note(p, cudaFuncSetAttribute(k_xfwd<double, XF_F64_DIVQ>, A, big));
+            note(p, cudaFuncSetAttribute(k_xfwd<float, XF_MIX_DIVQ>, A, big));
+            note(p, cudaFuncSetAttribute(k_xfwd<float, XF_MIX_LOAD>, A, big));
+            note(p, cudaFuncSetAttribute(k_xinv<double, XI_STORE>, A, big));
+            note(p, cudaFuncSetAttribute(k_xinv<float, XI_STORE>, A, big));
+            note(p, cudaFuncSetAttribute(k_xinv<float, XI_ACCUM>, A, big));
+            note(p, cudaFuncSetAttribute(k_ypass<double, false>, A, big));
+            note(p, cudaFuncSetAttribute(k_ypass<double, true>, A, big));
+            note(p, cudaFuncSetAttribute(k_ypass<float, false>, A, big));
+            note(p, cudaFuncSetAttribute(k_ypass<float, true>, A, big));
+        }
     }
     pass_caps(p->cap, p->smem_x64, p->smem_x32, p->smem_y64, p->smem_y32);
     // stream-ordered plans are ready for work queued after them on their
     // stream; other plans are complete on return
     cudaError_t e = p->async_alloc ? cudaGetLastError() : cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = p->setup_err;
     if (e != cudaSuccess) {
         int st = cuda_err(nullptr, e, "plan");
         fizzy_proj_destroy(p);
