@@ -12,7 +12,8 @@ NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 
 FLAGS = ["-O3", "-std=c++17", "-gencode", "arch=compute_103a,code=sm_103a", "-lineinfo",
          "-Xcompiler", "-fPIC,-fopenmp,-O2", "-shared", "-cudart", "shared",
-         "--expt-relaxed-constexpr", "--extended-lambda"]
+         "--expt-relaxed-constexpr", "--extended-lambda",
+         "-Werror", "all-warnings"]  # a warning (e.g. a value used before it is set) fails the build
 
 
 def sources():

@@ -26,6 +26,23 @@ struct FFTHost {
 
 }  // namespace
 
+// Pass kernels of a plan: the length-specialised instance where a direction
+// is periodic with a length the library specialises (256, 512), else the
+// generic one.  The results are the same bit for bit; only the index
+// arithmetic differs.
+typedef void (*XfwdK)(GridDev, FFTDesc, int, XArgs, int);
+typedef void (*Ypass64K)(int, int, FFTDesc, int, double *, const int *, int, int);
+typedef void (*Ypass32K)(int, int, FFTDesc, int, float *, const int *, int, int);
+typedef void (*Xinv64K)(GridDev, FFTDesc, int, const double *, double *, const DevStats *, int);
+typedef void (*Xinv32K)(GridDev, FFTDesc, int, const float *, double *, const DevStats *, int);
+struct PassKernels {
+    XfwdK xf64, xf32d, xf32l;
+    Ypass64K yf64, yi64;
+    Ypass32K yf32, yi32;
+    Xinv64K xi64;
+    Xinv32K xi32s, xi32a;
+};
+
 struct fizzy_proj_plan_s {
     fizzy_proj_desc desc;
     std::vector<double> zf;
@@ -60,6 +77,7 @@ struct fizzy_proj_plan_s {
     int Lx = 1, TXy = 2;
     size_t smem_x64 = 0, smem_x32 = 0, smem_y64 = 0, smem_y32 = 0;
     int cap[24] = {0};  // resident-grid size of each pass kernel (CAP_*)
+    PassKernels kern;   // the pass kernels this plan launches
     std::string err;
     // stream-ordered allocation (FIZZY_FLAG_ASYNC_ALLOC)
     int async_alloc = 0;
@@ -356,17 +374,55 @@ template <typename T> size_t pass_smem(int n, int L) {
     return sizeof(typename C2<T>::t) * ((size_t)n + (n / 2 + 2) + 2 * (size_t)L * (n + 1));
 }
 
-void pass_caps(int *cap, size_t sx64, size_t sx32, size_t sy64, size_t sy32) {
-    cap[CAP_XF64] = resident_grid(k_xfwd<double, XF_F64_DIVQ>, 256, sx64);
-    cap[CAP_XF32D] = resident_grid(k_xfwd<float, XF_MIX_DIVQ>, 256, sx32);
-    cap[CAP_XF32L] = resident_grid(k_xfwd<float, XF_MIX_LOAD>, 256, sx32);
-    cap[CAP_Y64F] = resident_grid(k_ypass<double, false>, 256, sy64);
-    cap[CAP_Y64I] = resident_grid(k_ypass<double, true>, 256, sy64);
-    cap[CAP_Y32F] = resident_grid(k_ypass<float, false>, 256, sy32);
-    cap[CAP_Y32I] = resident_grid(k_ypass<float, true>, 256, sy32);
-    cap[CAP_XI64] = resident_grid(k_xinv<double, XI_STORE>, 256, sx64);
-    cap[CAP_XI32S] = resident_grid(k_xinv<float, XI_STORE>, 256, sx32);
-    cap[CAP_XI32A] = resident_grid(k_xinv<float, XI_ACCUM>, 256, sx32);
+// The specialised length of a direction (0: generic).
+int fixed_len(int n, int bc) { return (bc == FIZZY_BC_PERIODIC && (n == 256 || n == 512)) ? n : 0; }
+
+template <int NX, int NY> PassKernels kernels_for() {
+    PassKernels k;
+    k.xf64 = k_xfwd<double, XF_F64_DIVQ, NX>;
+    k.xf32d = k_xfwd<float, XF_MIX_DIVQ, NX>;
+    k.xf32l = k_xfwd<float, XF_MIX_LOAD, NX>;
+    k.yf64 = k_ypass<double, false, NY>;
+    k.yi64 = k_ypass<double, true, NY>;
+    k.yf32 = k_ypass<float, false, NY>;
+    k.yi32 = k_ypass<float, true, NY>;
+    k.xi64 = k_xinv<double, XI_STORE, NX>;
+    k.xi32s = k_xinv<float, XI_STORE, NX>;
+    k.xi32a = k_xinv<float, XI_ACCUM, NX>;
+    return k;
+}
+template <int NX> PassKernels kernels_for_y(int fy) {
+    return fy == 256 ? kernels_for<NX, 256>() : fy == 512 ? kernels_for<NX, 512>() : kernels_for<NX, 0>();
+}
+PassKernels pick_kernels(int fx, int fy) {
+    return fx == 256 ? kernels_for_y<256>(fy) : fx == 512 ? kernels_for_y<512>(fy) : kernels_for_y<0>(fy);
+}
+
+// Opt every pass kernel instance into large dynamic shared memory.
+void opt_in_smem(fizzy_proj_plan_t p, int bytes) {
+    for (int fx : {0, 256, 512})
+        for (int fy : {0, 256, 512}) {
+            const PassKernels k = pick_kernels(fx, fy);
+            const void *fns[] = {(const void *)k.xf64, (const void *)k.xf32d, (const void *)k.xf32l,
+                                 (const void *)k.yf64, (const void *)k.yi64, (const void *)k.yf32,
+                                 (const void *)k.yi32, (const void *)k.xi64, (const void *)k.xi32s,
+                                 (const void *)k.xi32a};
+            for (const void *f : fns)
+                note(p, cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+        }
+}
+
+void pass_caps(int *cap, const PassKernels &k, size_t sx64, size_t sx32, size_t sy64, size_t sy32) {
+    cap[CAP_XF64] = resident_grid(k.xf64, 256, sx64);
+    cap[CAP_XF32D] = resident_grid(k.xf32d, 256, sx32);
+    cap[CAP_XF32L] = resident_grid(k.xf32l, 256, sx32);
+    cap[CAP_Y64F] = resident_grid(k.yf64, 256, sy64);
+    cap[CAP_Y64I] = resident_grid(k.yi64, 256, sy64);
+    cap[CAP_Y32F] = resident_grid(k.yf32, 256, sy32);
+    cap[CAP_Y32I] = resident_grid(k.yi32, 256, sy32);
+    cap[CAP_XI64] = resident_grid(k.xi64, 256, sx64);
+    cap[CAP_XI32S] = resident_grid(k.xi32s, 256, sx32);
+    cap[CAP_XI32A] = resident_grid(k.xi32a, 256, sx32);
     cap[CAP_TH64] = resident_grid(k_thomas<double>, THOMAS_BLOCK, thomas_smem<double>());
     cap[CAP_TH32] = resident_grid(k_thomas<float>, THOMAS_BLOCK, thomas_smem<float>());
     cap[CAP_RM] = resident_grid(k_residmax, 256, 0);
@@ -602,21 +658,11 @@ int fizzy_proj_plan(fizzy_proj_plan_t *out, const fizzy_proj_desc *d, void *stre
         std::lock_guard<std::mutex> lock(attrs_mu);
         if (cur_dev < 0 || cur_dev >= 256 || !attrs_set[cur_dev]) {
             if (cur_dev >= 0 && cur_dev < 256) attrs_set[cur_dev] = true;
-            const int big = 200 * 1024;
-            const cudaFuncAttribute A = cudaFuncAttributeMaxDynamicSharedMemorySize;
-            note(p, cudaFuncSetAttribute(k_xfwd<double, XF_F64_DIVQ>, A, big));
-            note(p, cudaFuncSetAttribute(k_xfwd<float, XF_MIX_DIVQ>, A, big));
-            note(p, cudaFuncSetAttribute(k_xfwd<float, XF_MIX_LOAD>, A, big));
-            note(p, cudaFuncSetAttribute(k_xinv<double, XI_STORE>, A, big));
-            note(p, cudaFuncSetAttribute(k_xinv<float, XI_STORE>, A, big));
-            note(p, cudaFuncSetAttribute(k_xinv<float, XI_ACCUM>, A, big));
-            note(p, cudaFuncSetAttribute(k_ypass<double, false>, A, big));
-            note(p, cudaFuncSetAttribute(k_ypass<double, true>, A, big));
-            note(p, cudaFuncSetAttribute(k_ypass<float, false>, A, big));
-            note(p, cudaFuncSetAttribute(k_ypass<float, true>, A, big));
+            opt_in_smem(p, 200 * 1024);
         }
     }
-    pass_caps(p->cap, p->smem_x64, p->smem_x32, p->smem_y64, p->smem_y32);
+    p->kern = pick_kernels(fixed_len(nx, d->bc_x), fixed_len(ny, d->bc_y));
+    pass_caps(p->cap, p->kern, p->smem_x64, p->smem_x32, p->smem_y64, p->smem_y32);
     // stream-ordered plans are ready for work queued after them on their
     // stream; other plans are complete on return
     cudaError_t e = p->async_alloc ? cudaGetLastError() : cudaDeviceSynchronize();
@@ -795,11 +841,11 @@ int fizzy_proj_solve(fizzy_proj_plan_t p, const double *phi, const double *p_n, 
         TIMED(KS_SUM, (k_sum_partials<<<1, 1024, 0, s>>>(p->usq_part, p->n_usq_part, p->usq_sum)));
     if (!p->mixed) {
         xa.out = p->fhat64;
-        TIMED(KS_XFWD, (k_xfwd<double, XF_F64_DIVQ><<<grid(xtiles, CAP_XF64), 256, p->smem_x64, s>>>(g, p->fx.d64, p->Lx, xa, xtiles)));
-        TIMED(KS_YFWD, (k_ypass<double, false><<<grid(ytiles, CAP_Y64F), 256, p->smem_y64, s>>>(nx, ny, p->fy.d64, p->TXy, p->fhat64, nullptr, ygx, ytiles)));
+        TIMED(KS_XFWD, (p->kern.xf64<<<grid(xtiles, CAP_XF64), 256, p->smem_x64, s>>>(g, p->fx.d64, p->Lx, xa, xtiles)));
+        TIMED(KS_YFWD, (p->kern.yf64<<<grid(ytiles, CAP_Y64F), 256, p->smem_y64, s>>>(nx, ny, p->fy.d64, p->TXy, p->fhat64, nullptr, ygx, ytiles)));
         TIMED(KS_THOMAS, (k_thomas<double><<<grid(ttiles, CAP_TH64), THOMAS_BLOCK, thomas_smem<double>(), s>>>(g, p->Ux, p->Uy, p->mtab64, p->ibtab64, p->cup64, p->fhat64, nullptr, ttiles)));
-        TIMED(KS_YINV, (k_ypass<double, true><<<grid(ytiles, CAP_Y64I), 256, p->smem_y64, s>>>(nx, ny, p->fy.d64, p->TXy, p->fhat64, nullptr, ygx, ytiles)));
-        TIMED(KS_XINV, (k_xinv<double, XI_STORE><<<grid(xtiles, CAP_XI64), 256, p->smem_x64, s>>>(g, p->fx.d64, p->Lx, p->fhat64, p_np1, p->st, xtiles)));
+        TIMED(KS_YINV, (p->kern.yi64<<<grid(ytiles, CAP_Y64I), 256, p->smem_y64, s>>>(nx, ny, p->fy.d64, p->TXy, p->fhat64, nullptr, ygx, ytiles)));
+        TIMED(KS_XINV, (p->kern.xi64<<<grid(xtiles, CAP_XI64), 256, p->smem_x64, s>>>(g, p->fx.d64, p->Lx, p->fhat64, p_np1, p->st, xtiles)));
         if (p->check) {
             XArgs ca = xa;
             ca.p = p_np1;
@@ -809,11 +855,11 @@ int fizzy_proj_solve(fizzy_proj_plan_t p, const double *phi, const double *p_n, 
         xa.out = p->fhat32;
         xa.f_out = p->f;
         const int *conv = &p->st->converged;
-        TIMED(KS_XFWD, (k_xfwd<float, XF_MIX_DIVQ><<<grid(xtiles, CAP_XF32D), 256, p->smem_x32, s>>>(g, p->fx.d32, p->Lx, xa, xtiles)));
-        TIMED(KS_YFWD, (k_ypass<float, false><<<grid(ytiles, CAP_Y32F), 256, p->smem_y32, s>>>(nx, ny, p->fy.d32, p->TXy, p->fhat32, nullptr, ygx, ytiles)));
+        TIMED(KS_XFWD, (p->kern.xf32d<<<grid(xtiles, CAP_XF32D), 256, p->smem_x32, s>>>(g, p->fx.d32, p->Lx, xa, xtiles)));
+        TIMED(KS_YFWD, (p->kern.yf32<<<grid(ytiles, CAP_Y32F), 256, p->smem_y32, s>>>(nx, ny, p->fy.d32, p->TXy, p->fhat32, nullptr, ygx, ytiles)));
         TIMED(KS_THOMAS, (k_thomas<float><<<grid(ttiles, CAP_TH32), THOMAS_BLOCK, thomas_smem<float>(), s>>>(g, p->Ux, p->Uy, p->mtab32, p->ibtab32, p->cup32, p->fhat32, nullptr, ttiles)));
-        TIMED(KS_YINV, (k_ypass<float, true><<<grid(ytiles, CAP_Y32I), 256, p->smem_y32, s>>>(nx, ny, p->fy.d32, p->TXy, p->fhat32, nullptr, ygx, ytiles)));
-        TIMED(KS_XINV, (k_xinv<float, XI_STORE><<<grid(xtiles, CAP_XI32S), 256, p->smem_x32, s>>>(g, p->fx.d32, p->Lx, p->fhat32, p_np1, p->st, xtiles)));
+        TIMED(KS_YINV, (p->kern.yi32<<<grid(ytiles, CAP_Y32I), 256, p->smem_y32, s>>>(nx, ny, p->fy.d32, p->TXy, p->fhat32, nullptr, ygx, ytiles)));
+        TIMED(KS_XINV, (p->kern.xi32s<<<grid(xtiles, CAP_XI32S), 256, p->smem_x32, s>>>(g, p->fx.d32, p->Lx, p->fhat32, p_np1, p->st, xtiles)));
         // residual of the FP32 solution (slot 0), then refinement sweeps
         // sw = 1..max_refine: transform of the stored residual, FP32 y/z/y^-1,
         // p += delta, then the residual fused with the correction (slot sw)
@@ -839,11 +885,11 @@ int fizzy_proj_solve(fizzy_proj_plan_t p, const double *phi, const double *p_n, 
         for (int sw = 1; sw <= p->max_refine; ++sw) {
             // a one-sweep solve runs sweep 1; later sweeps usually return at once
             auto gs = [&](int tiles, int c) { return sw == 1 ? grid(tiles, c) : rgrid(tiles, c); };
-            TIMED(KS_XFWD_R, (k_xfwd<float, XF_MIX_LOAD><<<gs(xtiles, CAP_XF32L), 256, p->smem_x32, s>>>(g, p->fx.d32, p->Lx, la, xtiles)));
-            TIMED(KS_YFWD_R, (k_ypass<float, false><<<gs(ytiles, CAP_Y32F), 256, p->smem_y32, s>>>(nx, ny, p->fy.d32, p->TXy, p->fhat32, conv, ygx, ytiles)));
+            TIMED(KS_XFWD_R, (p->kern.xf32l<<<gs(xtiles, CAP_XF32L), 256, p->smem_x32, s>>>(g, p->fx.d32, p->Lx, la, xtiles)));
+            TIMED(KS_YFWD_R, (p->kern.yf32<<<gs(ytiles, CAP_Y32F), 256, p->smem_y32, s>>>(nx, ny, p->fy.d32, p->TXy, p->fhat32, conv, ygx, ytiles)));
             TIMED(KS_THOMAS_R, (k_thomas<float><<<gs(ttiles, CAP_TH32), THOMAS_BLOCK, thomas_smem<float>(), s>>>(g, p->Ux, p->Uy, p->mtab32, p->ibtab32, p->cup32, p->fhat32, conv, ttiles)));
-            TIMED(KS_YINV_R, (k_ypass<float, true><<<gs(ytiles, CAP_Y32I), 256, p->smem_y32, s>>>(nx, ny, p->fy.d32, p->TXy, p->fhat32, conv, ygx, ytiles)));
-            TIMED(KS_XACC, (k_xinv<float, XI_ACCUM><<<gs(xtiles, CAP_XI32A), 256, p->smem_x32, s>>>(g, p->fx.d32, p->Lx, p->fhat32, p_np1, p->st, xtiles)));
+            TIMED(KS_YINV_R, (p->kern.yi32<<<gs(ytiles, CAP_Y32I), 256, p->smem_y32, s>>>(nx, ny, p->fy.d32, p->TXy, p->fhat32, conv, ygx, ytiles)));
+            TIMED(KS_XACC, (p->kern.xi32a<<<gs(xtiles, CAP_XI32A), 256, p->smem_x32, s>>>(g, p->fx.d32, p->Lx, p->fhat32, p_np1, p->st, xtiles)));
             ra.slot = sw;
             TIMED(KS_RCORR, (k_resid<true><<<gs(rctiles, CAP_RC), rcb, 0, s>>>(g, RESID_KC, ra, rtgx, rtgy, rctiles)));
         }

@@ -103,8 +103,10 @@ __device__ __forceinline__ TwApplied<T> tw_apply(typename C2<T>::t x, typename C
     return o;
 }
 
-// One Stockham stage over L lines (line stride ls) from src to dst.
-template <typename T, bool INV>
+// One Stockham stage over L lines (line stride ls) from src to dst.  FIXED:
+// the stage constants are compile-time values (a length-specialised
+// transform), so the divisions are written out and fold to shifts.
+template <typename T, bool INV, bool FIXED = false>
 __device__ __forceinline__ void stockham_stage(const typename C2<T>::t *__restrict__ src,
                                                typename C2<T>::t *__restrict__ dst, int L, int ls,
                                                int R, int m, unsigned rm, int Ns, unsigned rns,
@@ -112,9 +114,9 @@ __device__ __forceinline__ void stockham_stage(const typename C2<T>::t *__restri
     typedef typename C2<T>::t T2;
     const int total = L * m;
     for (int t = threadIdx.x; t < total; t += blockDim.x) {
-        const int l = fdiv(t, m, rm);
+        const int l = FIXED ? t / m : fdiv(t, m, rm);
         const int b = t - l * m;
-        const int j = b - fdiv(b, Ns, rns) * Ns;
+        const int j = FIXED ? b % Ns : b - fdiv(b, Ns, rns) * Ns;
         const T2 *in = src + l * ls + b;
         T2 *out = dst + l * ls + (b - j) * R + j;
         const int ts = j * twq;
@@ -208,6 +210,42 @@ __device__ typename C2<T>::t *fft_lines(typename C2<T>::t *a, typename C2<T>::t 
         b = t;
     }
     return a;
+}
+
+// Radix plan of a compile-time length (radix 4 first, then 2, then 3, the
+// order the host uses): number of stages and the constants of stage s.
+constexpr int plan_radix(int n, int s) {
+    for (int k = 0;; ++k) {
+        const int r = (n % 4 == 0) ? 4 : (n % 2 == 0) ? 2 : (n % 3 == 0) ? 3 : 1;
+        if (r == 1) return 1;
+        if (k == s) return r;
+        n /= r;
+    }
+}
+constexpr int plan_nst(int n) {
+    int s = 0;
+    while (plan_radix(n, s) != 1) ++s;
+    return s;
+}
+constexpr int plan_span(int n, int s) {  // product of the radices before stage s
+    int ns = 1;
+    for (int k = 0; k < s; ++k) ns *= plan_radix(n, k);
+    return ns;
+}
+
+// Full complex FFT of L lines of compile-time length N (stages unrolled with
+// constant R, m, Ns and twiddle step); same result as fft_lines.
+template <typename T, bool INV, int N, int S = 0>
+__device__ __forceinline__ typename C2<T>::t *fft_fixed(typename C2<T>::t *a, typename C2<T>::t *b,
+                                                        int L, int ls, const typename C2<T>::t *tw) {
+    if constexpr (S >= plan_nst(N)) {
+        return a;
+    } else {
+        constexpr int R = plan_radix(N, S), NS = plan_span(N, S);
+        stockham_stage<T, INV, true>(a, b, L, ls, R, N / R, 0u, NS, 0u, N / (NS * R), tw);
+        __syncthreads();
+        return fft_fixed<T, INV, N, S + 1>(b, a, L, ls, tw);
+    }
 }
 
 // Stage the twiddle tables of D into shared memory (tw: n entries, cs: n/2+1).

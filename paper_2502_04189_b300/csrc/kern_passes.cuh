@@ -335,12 +335,24 @@ struct XArgs {
 constexpr int PASS_U = 4;   // global loads per thread issued together in the pass load loops
 constexpr int PASS_UC = 2;  // spectral pairs per thread loaded together before the inverse combine
 
+// The transform of a pass: length-specialised when NF != 0 (NF = the length
+// of a periodic direction), else driven by the runtime descriptor.
+template <typename T, bool INV, int NF>
+__device__ __forceinline__ const typename C2<T>::t *fft_any(typename C2<T>::t *a, typename C2<T>::t *b,
+                                                            int L, int ls, const FFTDesc &D,
+                                                            const typename C2<T>::t *tw) {
+    if constexpr (NF != 0) return fft_fixed<T, INV, NF>(a, b, L, ls, tw);
+    else return fft_lines<T, INV>(a, b, L, ls, D, tw);
+}
+
 // Forward x-pass: per CTA 2L real x-lines (flattened line index (k, j)).
-template <typename T, int MODE, bool CG>
+template <typename T, int MODE, bool CG, int NF = 0>
 __device__ __forceinline__ void xfwd_body(const GridDev &g, const FFTDesc &D, int L, const XArgs &a,
                                           int bx, int ntiles, unsigned char *smem_raw) {
     typedef typename C2<T>::t T2;
-    const int n = D.n, ls = n + 1;
+    constexpr bool FX = NF != 0;  // compile-time length (periodic)
+    const int n = FX ? NF : D.n, ls = n + 1;
+    const int kind = FX ? (int)KIND_PERIODIC : D.kind;
     T2 *tw_s = (T2 *)smem_raw;
     T2 *cs_s = tw_s + n;
     T2 *A = cs_s + (n / 2 + 2);
@@ -360,20 +372,20 @@ __device__ __forceinline__ void xfwd_body(const GridDev &g, const FFTDesc &D, in
 #pragma unroll
             for (int u = 0; u < PASS_U; ++u) {
                 const int idx = base + u * blockDim.x;
-                const int r = fdiv(idx, n, D.rn), i = idx - r * n;
+                const int r = (FX ? idx / NF : fdiv(idx, n, D.rn)), i = idx - r * n;
                 v[u] = (idx < total && line0 + r < nlines)
                            ? ldp<CG>((const T *)a.out + (size_t)(line0 + r) * n + i) : (T)0;
             }
 #pragma unroll
             for (int u = 0; u < PASS_U; ++u) {
                 const int idx = base + u * blockDim.x;
-                const int r = fdiv(idx, n, D.rn), i = idx - r * n;
-                if (idx < total) ((T *)(A + (r >> 1) * ls))[2 * line_pos(i, n, D.kind) + (r & 1)] = v[u];
+                const int r = (FX ? idx / NF : fdiv(idx, n, D.rn)), i = idx - r * n;
+                if (idx < total) ((T *)(A + (r >> 1) * ls))[2 * line_pos(i, n, kind) + (r & 1)] = v[u];
             }
         }
     } else
     for (int idx = threadIdx.x; idx < 2 * L * n; idx += blockDim.x) {
-        const int r = fdiv(idx, n, D.rn), i = idx - r * n;
+        const int r = (FX ? idx / NF : fdiv(idx, n, D.rn)), i = idx - r * n;
         const int line = line0 + r;
         T val = (T)0;
         if (line < nlines) {
@@ -389,20 +401,20 @@ __device__ __forceinline__ void xfwd_body(const GridDev &g, const FFTDesc &D, in
                 val = (T)(f64_to_f32_shift(f, 0) * scale32);
             }
         }
-        ((T *)(A + (r >> 1) * ls))[2 * line_pos(i, n, D.kind) + (r & 1)] = val;
+        ((T *)(A + (r >> 1) * ls))[2 * line_pos(i, n, kind) + (r & 1)] = val;
     }
     if (MODE == XF_MIX_DIVQ) block_max_atomic(mx, &a.st->fmax_bits);
     if (MODE == XF_F64_DIVQ && a.track_fmax) block_max_atomic(mx, &a.st->fmax_bits);
     __syncthreads();
     // 2. complex FFT
-    const T2 *Z = fft_lines<T, false>(A, B, L, ls, D, tw_s);
+    const T2 *Z = fft_any<T, false, NF>(A, B, L, ls, D, tw_s);
     // 3. separate and store
     T *out = (T *)a.out;
     const int M = n / 2 + 1;
     for (int t = threadIdx.x; t < L * M; t += blockDim.x) {
-        const int l = fdiv(t, M, D.rM), m = t - l * M;
+        const int l = (FX ? t / (NF / 2 + 1) : fdiv(t, M, D.rM)), m = t - l * M;
         const int la = line0 + 2 * l;
-        fwd_separate<T>(Z + l * ls, n, m, D.kind, cs_s, [&](int ab, int ix, T v) {
+        fwd_separate<T>(Z + l * ls, n, m, kind, cs_s, [&](int ab, int ix, T v) {
             const int line = la + ab;
             if (line < nlines) out[(size_t)line * n + ix] = v;
         });
@@ -416,12 +428,12 @@ __device__ __forceinline__ void xfwd_body(const GridDev &g, const FFTDesc &D, in
 // returning at once costs a few hundred block starts, not one per tile.
 // (The flag is set only by the last tile of a residual pass, so no tile of
 // the same launch is pending once it is set.)
-template <typename T, int MODE>
+template <typename T, int MODE, int NF = 0>
 __global__ void __launch_bounds__(256) k_xfwd(GridDev g, FFTDesc D, int L, XArgs a, int ntiles) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     if (MODE == XF_MIX_LOAD && *(volatile const int *)&a.st->converged) return;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
-        xfwd_body<T, MODE, false>(g, D, L, a, t, ntiles, smem_raw);
+        xfwd_body<T, MODE, false, NF>(g, D, L, a, t, ntiles, smem_raw);
         __syncthreads();  // shared memory is reused by the next tile
     }
 }
@@ -467,13 +479,15 @@ __global__ void __launch_bounds__(256) k_residmax(GridDev g, XArgs a, int rgx, i
 }
 
 // Forward / inverse y-pass on a tile of TX columns (tile bx) of plane k (in place).
-template <typename T, bool INV, bool CG>
+template <typename T, bool INV, bool CG, int NF = 0>
 __device__ __forceinline__ void ypass_body(int nx, int ny, const FFTDesc &D, int TX, T *data,
                                            const int *conv, int bx, int kplane,
                                            unsigned char *smem_raw) {
     typedef typename C2<T>::t T2;
     if (conv && ldp<CG>(conv)) return;
-    const int n = D.n, ls = n + 1;
+    constexpr bool FX = NF != 0;  // compile-time length (periodic)
+    const int n = FX ? NF : D.n, ls = n + 1;
+    const int kind = FX ? (int)KIND_PERIODIC : D.kind;
     const int L = TX / 2;
     T2 *tw_s = (T2 *)smem_raw;
     T2 *cs_s = tw_s + n;
@@ -500,14 +514,14 @@ __device__ __forceinline__ void ypass_body(int nx, int ny, const FFTDesc &D, int
             for (int u = 0; u < PASS_U; ++u) {
                 const int idx = base + u * blockDim.x;
                 const int j = fdiv(idx, TX, rTX), c = idx - j * TX;
-                if (idx < total) ((T *)(A + (c >> 1) * ls))[2 * line_pos(j, n, D.kind) + (c & 1)] = v[u];
+                if (idx < total) ((T *)(A + (c >> 1) * ls))[2 * line_pos(j, n, kind) + (c & 1)] = v[u];
             }
         }
         __syncthreads();
-        const T2 *Z = fft_lines<T, false>(A, B, L, ls, D, tw_s);
+        const T2 *Z = fft_any<T, false, NF>(A, B, L, ls, D, tw_s);
         for (int t = threadIdx.x; t < L * M; t += blockDim.x) {
             const int m = fdiv(t, L, rL), l = t - m * L;
-            fwd_separate<T>(Z + l * ls, n, m, D.kind, cs_s, [&](int ab, int ix, T v) {
+            fwd_separate<T>(Z + l * ls, n, m, kind, cs_s, [&](int ab, int ix, T v) {
                 const int c = 2 * l + ab;
                 if (c < ncols) plane[(size_t)ix * nx + c] = v;
             });
@@ -537,7 +551,7 @@ __device__ __forceinline__ void ypass_body(int nx, int ny, const FFTDesc &D, int
                 const int t = base + u * blockDim.x;
                 const int m = fdiv(t, L, rL), l = t - m * L;
                 if (t < total)
-                    inv_combine<T>(A + l * ls, n, m, D.kind, cs_s,
+                    inv_combine<T>(A + l * ls, n, m, kind, cs_s,
                                    [&](int ab, int ix) -> T {
                                        return ab == 0 ? (ix == m ? v[u][0] : v[u][1])
                                                       : (ix == m ? v[u][2] : v[u][3]);
@@ -545,24 +559,24 @@ __device__ __forceinline__ void ypass_body(int nx, int ny, const FFTDesc &D, int
             }
         }
         __syncthreads();
-        const T2 *Z = fft_lines<T, true>(A, B, L, ls, D, tw_s);
+        const T2 *Z = fft_any<T, true, NF>(A, B, L, ls, D, tw_s);
         for (int idx = threadIdx.x; idx < n * TX; idx += blockDim.x) {
             const int j = fdiv(idx, TX, rTX), c = idx - j * TX;
             if (c < ncols)
-                plane[(size_t)j * nx + c] = ((const T *)(Z + (c >> 1) * ls))[2 * line_pos(j, n, D.kind) + (c & 1)];
+                plane[(size_t)j * nx + c] = ((const T *)(Z + (c >> 1) * ls))[2 * line_pos(j, n, kind) + (c & 1)];
         }
     }
 }
 
 // tiles: ygx column tiles per plane, nz planes
-template <typename T, bool INV>
+template <typename T, bool INV, int NF = 0>
 __global__ void __launch_bounds__(256) k_ypass(int nx, int ny, FFTDesc D, int TX, T *data,
                                                const int *conv, int ygx, int ntiles) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     if (conv && *(volatile const int *)conv) return;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const int k = t / ygx;
-        ypass_body<T, INV, false>(nx, ny, D, TX, data, conv, t - k * ygx, k, smem_raw);
+        ypass_body<T, INV, false, NF>(nx, ny, D, TX, data, conv, t - k * ygx, k, smem_raw);
         __syncthreads();
     }
 }
@@ -570,13 +584,15 @@ __global__ void __launch_bounds__(256) k_ypass(int nx, int ny, FFTDesc D, int TX
 enum { XI_STORE = 0, XI_ACCUM = 1 };
 
 // Inverse x-pass: per CTA 2L real x-lines; writes p (FP64).
-template <typename T, int MODE, bool CG>
+template <typename T, int MODE, bool CG, int NF = 0>
 __device__ __forceinline__ void xinv_body(const GridDev &g, const FFTDesc &D, int L, const T *in,
                                           double *p, const DevStats *st, int bx,
                                           unsigned char *smem_raw) {
     typedef typename C2<T>::t T2;
     if (MODE == XI_ACCUM && ldp<CG>(&st->converged)) return;
-    const int n = D.n, ls = n + 1;
+    constexpr bool FX = NF != 0;  // compile-time length (periodic)
+    const int n = FX ? NF : D.n, ls = n + 1;
+    const int kind = FX ? (int)KIND_PERIODIC : D.kind;
     T2 *tw_s = (T2 *)smem_raw;
     T2 *cs_s = tw_s + n;
     T2 *A = cs_s + (n / 2 + 2);
@@ -592,7 +608,7 @@ __device__ __forceinline__ void xinv_body(const GridDev &g, const FFTDesc &D, in
 #pragma unroll
         for (int u = 0; u < PASS_UC; ++u) {
             const int t = base + u * blockDim.x;
-            const int l = fdiv(t, M, D.rM), m = t - l * M;
+            const int l = (FX ? t / (NF / 2 + 1) : fdiv(t, M, D.rM)), m = t - l * M;
             const bool two = m > 0 && 2 * m != n;  // Z[m] and Z[n-m] both read
 #pragma unroll
             for (int ab = 0; ab < 2; ++ab) {
@@ -605,9 +621,9 @@ __device__ __forceinline__ void xinv_body(const GridDev &g, const FFTDesc &D, in
 #pragma unroll
         for (int u = 0; u < PASS_UC; ++u) {
             const int t = base + u * blockDim.x;
-            const int l = fdiv(t, M, D.rM), m = t - l * M;
+            const int l = (FX ? t / (NF / 2 + 1) : fdiv(t, M, D.rM)), m = t - l * M;
             if (t < total)
-                inv_combine<T>(A + l * ls, n, m, D.kind, cs_s,
+                inv_combine<T>(A + l * ls, n, m, kind, cs_s,
                                [&](int ab, int ix) -> T {
                                        return ab == 0 ? (ix == m ? v[u][0] : v[u][1])
                                                       : (ix == m ? v[u][2] : v[u][3]);
@@ -615,15 +631,15 @@ __device__ __forceinline__ void xinv_body(const GridDev &g, const FFTDesc &D, in
         }
     }
     __syncthreads();
-    const T2 *Z = fft_lines<T, true>(A, B, L, ls, D, tw_s);
+    const T2 *Z = fft_any<T, true, NF>(A, B, L, ls, D, tw_s);
     int ef = 0;
     if (MODE == XI_ACCUM) ef = exp_of_bits(ldp<CG>(&st->fmax_bits));
     if (MODE == XI_STORE) {
         for (int idx = threadIdx.x; idx < 2 * L * n; idx += blockDim.x) {
-            const int r = fdiv(idx, n, D.rn), i = idx - r * n;
+            const int r = (FX ? idx / NF : fdiv(idx, n, D.rn)), i = idx - r * n;
             const int line = line0 + r;
             if (line < nlines) {
-                const T v = ((const T *)(Z + (r >> 1) * ls))[2 * line_pos(i, n, D.kind) + (r & 1)];
+                const T v = ((const T *)(Z + (r >> 1) * ls))[2 * line_pos(i, n, kind) + (r & 1)];
                 double *dst = p + (size_t)line * n + i;
                 if (sizeof(T) == 8) *dst = (double)v;
                 else *dst = f32_to_f64_shift((float)v, 0);
@@ -636,15 +652,15 @@ __device__ __forceinline__ void xinv_body(const GridDev &g, const FFTDesc &D, in
 #pragma unroll
             for (int u = 0; u < PASS_U; ++u) {
                 const int idx = base + u * blockDim.x;
-                const int r = fdiv(idx, n, D.rn), i = idx - r * n;
+                const int r = (FX ? idx / NF : fdiv(idx, n, D.rn)), i = idx - r * n;
                 pv[u] = (idx < total && line0 + r < nlines) ? ldp<CG>(p + (size_t)(line0 + r) * n + i) : 0.0;
             }
 #pragma unroll
             for (int u = 0; u < PASS_U; ++u) {
                 const int idx = base + u * blockDim.x;
-                const int r = fdiv(idx, n, D.rn), i = idx - r * n;
+                const int r = (FX ? idx / NF : fdiv(idx, n, D.rn)), i = idx - r * n;
                 if (idx < total && line0 + r < nlines) {
-                    const T v = ((const T *)(Z + (r >> 1) * ls))[2 * line_pos(i, n, D.kind) + (r & 1)];
+                    const T v = ((const T *)(Z + (r >> 1) * ls))[2 * line_pos(i, n, kind) + (r & 1)];
                     p[(size_t)(line0 + r) * n + i] = pv[u] + f32_to_f64_shift((float)v, ef);
                 }
             }
@@ -652,13 +668,13 @@ __device__ __forceinline__ void xinv_body(const GridDev &g, const FFTDesc &D, in
     }
 }
 
-template <typename T, int MODE>
+template <typename T, int MODE, int NF = 0>
 __global__ void __launch_bounds__(256) k_xinv(GridDev g, FFTDesc D, int L, const T *in, double *p,
                                               const DevStats *st, int ntiles) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     if (MODE == XI_ACCUM && *(volatile const int *)&st->converged) return;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
-        xinv_body<T, MODE, false>(g, D, L, in, p, st, t, smem_raw);
+        xinv_body<T, MODE, false, NF>(g, D, L, in, p, st, t, smem_raw);
         __syncthreads();
     }
 }
