@@ -298,22 +298,6 @@ int validate(const fizzy_proj_desc *d) {
     return FIZZY_OK;
 }
 
-// shapes of the transform passes
-int x_lines_per_cta(int n) {
-    int L = 1024 / n;
-    if (L < 1) L = 1;
-    if (L > 16) L = 16;
-    return L;
-}
-// y-pass columns per tile: rows of 8 doubles or 16 floats (64 B) at n = 256;
-// the tile holds about 1024 (FP64) or 2048 (FP32) complex values.
-int y_tile_cols(int n, bool fp32 = false) {
-    const int cap = fp32 ? 16 : 8;
-    int L = (fp32 ? 2048 : 1024) / n;
-    if (L < 2) L = 2;
-    if (L > cap) L = cap;
-    return 2 * L;
-}
 // Physics-dependent scalars of GridDev (densities and dt; spacings dx, dy):
 // shared by fizzy_proj_plan, fizzy_proj_set_physics and the allocation-free
 // entry point.

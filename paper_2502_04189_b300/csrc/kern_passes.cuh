@@ -332,6 +332,20 @@ struct XArgs {
     int track_fmax;              // F64_DIVQ: record max|sigma f|
 };
 
+// Shapes of the transform passes (host and device): x-pass line pairs per
+// CTA (about 1024 complex values per tile) and y-pass columns per tile
+// (rows of 8 doubles or 16 floats, 64 B, at n = 256; about 1024 (FP64) or
+// 2048 (FP32) complex values per tile).
+constexpr int x_lines_per_cta(int n) {
+    const int L = 1024 / n;
+    return L < 1 ? 1 : (L > 16 ? 16 : L);
+}
+constexpr int y_tile_cols(int n, bool fp32 = false) {
+    const int cap = fp32 ? 16 : 8;
+    const int L = (fp32 ? 2048 : 1024) / n;
+    return 2 * (L < 2 ? 2 : (L > cap ? cap : L));
+}
+
 constexpr int PASS_U = 4;   // global loads per thread issued together in the pass load loops
 constexpr int PASS_UC = 2;  // spectral pairs per thread loaded together before the inverse combine
 
