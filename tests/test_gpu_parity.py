@@ -38,6 +38,9 @@ def small_cases():
                              config=17, velocity="iid"),
         "b81x3x7_nn": I.CaseSpec(nx=81, ny=3, nz=7, bcx=1, bcy=1, beta=2.0, n_bubbles=1,
                                  radius_cells=2, config=18),
+        # periodic x of length 512: the length-specialised x-pass instances
+        "b512x8x5": I.CaseSpec(nx=512, ny=8, nz=5, bcx=0, bcy=1, n_bubbles=1, radius_cells=2,
+                               config=20),
         # light drops in a heavy phase: rho0 = rho_l, split term from 1 - phi
         "b48x32x24_swapped": I.CaseSpec(nx=48, ny=32, nz=24, bcx=0, bcy=1, beta=1.5, n_bubbles=3,
                                         radius_cells=4, rho_l=1e-3, rho_g=1.0, config=19),
@@ -62,7 +65,7 @@ def test_fp64_matches_oracle(cuda_ok, name):
 
 
 @pytest.mark.parametrize("name", ["drop32", "b48x36x20_nx_stretch", "b96x64x33", "b27x18x12_ny",
-                                  "b384x6x5", "b81x3x7_nn", "b48x32x24_swapped"])
+                                  "b384x6x5", "b81x3x7_nn", "b48x32x24_swapped", "b512x8x5"])
 def test_mixed_matches_oracle(cuda_ok, name):
     c = I.make_case(CASES[name])
     ref = O.project_case(c)
