@@ -210,7 +210,12 @@ __device__ __forceinline__ void batch_run_tile(const BatchInst &I, const BatchIt
     }
 }
 
-__global__ void __launch_bounds__(BATCH_THREADS, 3) k_batch(BatchArgs A) {
+// Five resident CTAs per SM (48 registers; about 400 bytes of spills, served
+// by L1): the
+// FP64-bound pass bodies need the warps more than the registers (measured on
+// the 64-instance batch: 3 CTAs 5.29, 4: 5.76, 5: 5.92, 6: 5.94 Gpt/s mixed;
+// FP64 5.28, 5.67, 5.54, 5.46).
+__global__ void __launch_bounds__(BATCH_THREADS, 5) k_batch(BatchArgs A) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int s_item, s_ok;
     for (;;) {
