@@ -184,6 +184,22 @@ def dist_env():
     return world, rank, local
 
 
+def slowest_rank(seconds, dist, device="cuda"):
+    """The job time of N replicas: the maximum over ranks of each rank's time
+    (every rank projects its own batch; no data-path collective)."""
+    if not dist:
+        return seconds
+    import torch
+    t = torch.tensor([float(seconds)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(points_per_rank_step, steps, world, seconds):
+    """Whole-job points per second: all ranks' points over the slowest time."""
+    return points_per_rank_step * steps * world / seconds
+
+
 def oracle_time(case, reps=1):
     """Wall time of the CPU oracle's projection on case (rank 0 host cores)."""
     import oracle as O
@@ -289,11 +305,8 @@ def run_fizzy(args):
     clocks.start()
     ms, (kern, dom, live, max_refine), st, launches = timed_run(prec, args.steps, args.warmup, True)
     clk = clocks.stop()
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = npts * args.steps * world / (ms / 1e3)
+    ms = slowest_rank(ms, dist)
+    value = job_throughput(npts, args.steps, world, ms / 1e3)
 
     # the other precision on the same inputs (context for "mixed vs FP64")
     other = F.FP64 if prec == F.MIXED else F.MIXED
@@ -367,13 +380,9 @@ def run_fizzy(args):
         for _ in range(args.e2e_steps):
             plan.solve_host_async(*hin, *hout, stream=stream)
         plan.host_wait()
-        el = time.perf_counter() - t0
-        if dist:
-            t = torch.tensor([el], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            el = float(t.item())
+        el = slowest_rank(time.perf_counter() - t0, dist)
         plan.close()
-        e2e = {"value": npts * args.e2e_steps * world / el, "unit": "pts/s",
+        e2e = {"value": job_throughput(npts, args.e2e_steps, world, el), "unit": "pts/s",
                "h2d_bytes_per_step": 6 * 8 * npts, "d2h_bytes_per_step": 4 * 8 * npts,
                "ms_per_step": el / args.e2e_steps * 1e3,
                "api": "fizzy_proj_solve_host_async (pipelined, pinned host arrays)"}
