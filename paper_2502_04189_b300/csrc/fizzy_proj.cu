@@ -11,7 +11,9 @@
 #include <cstdlib>
 #include <cstdint>
 #include <cstring>
+#include <map>
 #include <mutex>
+#include <tuple>
 #include <string>
 #include <vector>
 
@@ -236,9 +238,24 @@ void fill_fft_tables(int n, double *tw, double *cs, float *tw32 = nullptr, float
 }
 
 int build_fft(fizzy_proj_plan_t p, int n, int bc, FFTHost &F, int *status) {
-    std::vector<double> tw(2 * (size_t)n), cs(2 * (size_t)(n / 2 + 2));
-    std::vector<float> tw32(tw.size()), cs32(cs.size());
-    fill_fft_tables(n, tw.data(), cs.data(), tw32.data(), cs32.data());
+    // the host tables of each length are computed once per process
+    struct Tabs {
+        std::vector<double> tw, cs;
+        std::vector<float> tw32, cs32;
+    };
+    static std::mutex mu;
+    static std::map<int, Tabs> cache;
+    std::unique_lock<std::mutex> lock(mu);
+    Tabs &T = cache[n];
+    if (T.tw.empty()) {
+        T.tw.resize(2 * (size_t)n);
+        T.cs.resize(2 * (size_t)(n / 2 + 2));
+        T.tw32.resize(T.tw.size());
+        T.cs32.resize(T.cs.size());
+        fill_fft_tables(n, T.tw.data(), T.cs.data(), T.tw32.data(), T.cs32.data());
+    }
+    const std::vector<double> &tw = T.tw, &cs = T.cs;
+    const std::vector<float> &tw32 = T.tw32, &cs32 = T.cs32;
     F.tw64 = dev_alloc<double>(p, tw.size(), status);
     F.cs64 = dev_alloc<double>(p, cs.size(), status);
     if (p->mixed) {
@@ -344,15 +361,29 @@ void physics_zrow(double rho_l, double rho_g, double dt, double sig, double dzf,
 // resident (occupancy x SM count); the kernel strides over its tiles.
 enum { CAP_XF64, CAP_XF32D, CAP_XF32L, CAP_Y64F, CAP_Y64I, CAP_Y32F, CAP_Y32I, CAP_XI64, CAP_XI32S,
        CAP_XI32A, CAP_TH64, CAP_TH32, CAP_RM, CAP_RC, CAP_CIF, CAP_N };
+// Cached per (device, kernel, block size, shared memory): plans are built per
+// request in the serving runtime, and the occupancy queries would dominate.
 template <typename K> int resident_grid(K kernel, int threads, size_t smem) {
-    int dev = 0, sms = 0, nb = 0;
+    static std::mutex mu;
+    static std::map<std::tuple<int, const void *, int, size_t>, int> cache;
+    int dev = 0;
     cudaGetDevice(&dev);
+    const auto key = std::make_tuple(dev, (const void *)kernel, threads, smem);
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        auto it = cache.find(key);
+        if (it != cache.end()) return it->second;
+    }
+    int sms = 0, nb = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, threads, smem) != cudaSuccess) {
         (void)cudaGetLastError();
         nb = 1;
     }
-    return std::max(1, nb) * std::max(1, sms);
+    const int g = std::max(1, nb) * std::max(1, sms);
+    std::lock_guard<std::mutex> lock(mu);
+    cache[key] = g;
+    return g;
 }
 template <typename T> size_t pass_smem(int n, int L) {
     return sizeof(typename C2<T>::t) * ((size_t)n + (n / 2 + 2) + 2 * (size_t)L * (n + 1));

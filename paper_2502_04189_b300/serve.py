@@ -81,6 +81,7 @@ def run(server: Server, requests, fill: Callable, deadline: float = 0.1,
     max_inflight = 0
     t0 = clock()
     n = len(requests)
+    blocked = None  # the head request that could not be admitted, until a slot frees
     while len(outcomes) < n:
         now = clock() - t0
         while nxt < n and requests[nxt].arrival <= now:
@@ -90,11 +91,13 @@ def run(server: Server, requests, fill: Callable, deadline: float = 0.1,
         while pending and now - pending[0].arrival > deadline:
             r = pending.popleft()
             outcomes[r.index] = Outcome(r.index, False)
-        # admit in arrival order while slots and budget allow
-        while pending:
+        # admit in arrival order while slots and budget allow (a refused head
+        # is retried only once a slot has been released or the head changed)
+        while pending and pending[0] is not blocked:
             r = pending[0]
             rc, slot, ptrs = server.admit(**r.desc)
             if rc != 0:
+                blocked = r
                 break
             pending.popleft()
             shape = (r.desc["nz"], r.desc["ny"], r.desc["nx"])
@@ -111,6 +114,7 @@ def run(server: Server, requests, fill: Callable, deadline: float = 0.1,
             if on_done is not None:
                 on_done(r, views)
             server.release(slot)
+            blocked = None
             outcomes[r.index] = Outcome(r.index, True, done - r.arrival, st)
         if spin_sleep:
             time.sleep(spin_sleep)
