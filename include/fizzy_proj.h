@@ -294,6 +294,23 @@ int fizzy_serve_info(fizzy_serve_t s, size_t *bytes_used, int *plans_cached, int
 
 int fizzy_serve_destroy(fizzy_serve_t s);
 
+/* Stage one request's inputs from a device-resident source state: a data
+ * movement helper for serving, not an operation of the method.
+ * src[0..5] (a host array of six device pointers) are phi, p_n, p_nm1, u, v, w
+ * of shape (tz, ty, tx), x fastest; dst[0..5] likewise of shape (nz, ny, nx).
+ * Each output is a periodic crop,
+ *   dst_f[k][j][i] = src_f[(k + oz) mod tz][(j + oy) mod ty][(i + ox) mod tx],
+ * except that the wall faces of the staggered velocity are zero: u at
+ * i = nx-1 when bc_x is FIZZY_BC_NEUMANN, v at j = ny-1 when bc_y is, and w
+ * at k = nz-1 always (the top wall).  One kernel on `stream` (null: the
+ * legacy default stream) moving 96 bytes per output point; dst must not
+ * overlap src.  Returns FIZZY_ERR_INVALID for a null pointer, an extent < 1,
+ * a negative offset or a bc other than the two above, else FIZZY_OK or
+ * FIZZY_ERR_CUDA if the launch failed. */
+int fizzy_crop_fill(const double *const *src, int tx, int ty, int tz, double *const *dst,
+                    int nx, int ny, int nz, int ox, int oy, int oz, int bc_x, int bc_y,
+                    void *stream);
+
 /* ------------------------------------------------------------------------
  * Allocation-free projection (FP64 mode, small grids).
  *

@@ -343,6 +343,25 @@ class Server:
             pass
 
 
+def crop_fill(src, dst, offset, bcx=PERIODIC, bcy=PERIODIC, stream=None):
+    """fizzy_crop_fill: dst[f] (six float64 CUDA tensors, shape (nz, ny, nx))
+    = periodic crop of src[f] (shape (tz, ty, tx)) from offset (oz, oy, ox),
+    with the wall faces of u, v and w zeroed; asynchronous on `stream`."""
+    if len(src) != 6 or len(dst) != 6:
+        raise ValueError("expected six source and six destination fields")
+    tz, ty, tx = src[0].shape
+    nz, ny, nx = dst[0].shape
+    if any(t.shape != (tz, ty, tx) for t in src) or any(t.shape != (nz, ny, nx) for t in dst):
+        raise ValueError("fields of one side must share a shape")
+    sp = (ctypes.c_void_p * 6)(*[_ptr(t).value for t in src])
+    dp = (ctypes.c_void_p * 6)(*[_ptr(t).value for t in dst])
+    oz, oy, ox = (int(o) for o in offset)
+    rc = _abi.lib().fizzy_crop_fill(sp, tx, ty, tz, dp, nx, ny, nz, ox, oy, oz, int(bcx), int(bcy),
+                                    _stream_handle(stream))
+    if rc != 0:
+        raise FizzyError(rc)
+
+
 def solve_noalloc(phi, pn, pnm1, u, v, w, p_out, stream=None, **desc):
     """Allocation-free FP64 projection for small grids (fizzy_proj_solve_noalloc).
 

@@ -21,7 +21,7 @@ EXPORTED = ("fizzy_proj_plan", "fizzy_proj_workspace_bytes", "fizzy_proj_solve",
             "fizzy_proj_set_physics", "fizzy_serve_create", "fizzy_serve_admit", "fizzy_serve_stream",
             "fizzy_serve_launch", "fizzy_serve_poll", "fizzy_serve_stats", "fizzy_serve_release",
             "fizzy_serve_info", "fizzy_serve_destroy", "fizzy_proj_solve_host_async",
-            "fizzy_proj_host_wait")
+            "fizzy_proj_host_wait", "fizzy_crop_fill")
 ERRORS[-7] = "busy"
 NOALLOC_MAX_CELLS = 262144
 DEFAULT_MAX_REFINE = 4  # FIZZY_DEFAULT_MAX_REFINE
@@ -135,5 +135,8 @@ def lib():
         L.fizzy_serve_info.restype = ctypes.c_int
         L.fizzy_serve_destroy.argtypes = [vp]
         L.fizzy_serve_destroy.restype = ctypes.c_int
+        L.fizzy_crop_fill.argtypes = [ctypes.POINTER(vp)] + [ctypes.c_int] * 3 + [ctypes.POINTER(vp)] + \
+            [ctypes.c_int] * 8 + [vp]
+        L.fizzy_crop_fill.restype = ctypes.c_int
         _lib = L
     return _lib

@@ -20,7 +20,7 @@ from typing import Callable, Optional
 
 import numpy as np
 
-from . import Server, device_view
+from . import Server, crop_fill, device_view
 
 
 @dataclasses.dataclass
@@ -51,21 +51,9 @@ class TemplateFields:
         self.shape = case.phi.shape
 
     def fill(self, views, desc, offset, stream):
-        """Write crops of shape (nz, ny, nx) starting at offset into views[0..5]."""
-        import torch
-        nz, ny, nx = desc["nz"], desc["ny"], desc["nx"]
-        Tz, Ty, Tx = self.shape
-        with torch.cuda.stream(stream):
-            iz = (torch.arange(nz, device="cuda") + offset[0]) % Tz
-            iy = (torch.arange(ny, device="cuda") + offset[1]) % Ty
-            ix = (torch.arange(nx, device="cuda") + offset[2]) % Tx
-            for src, dst in zip(self.fields, views[:6]):
-                dst.copy_(src.index_select(0, iz).index_select(1, iy).index_select(2, ix))
-            if desc.get("bcx", 0) == 1:
-                views[3][:, :, -1] = 0.0
-            if desc.get("bcy", 0) == 1:
-                views[4][:, -1, :] = 0.0
-            views[5][-1] = 0.0
+        """Write crops of shape (nz, ny, nx) starting at offset into views[0..5]
+        (one fizzy_crop_fill kernel: 96 bytes of device traffic per point)."""
+        crop_fill(self.fields, views[:6], offset, desc.get("bcx", 0), desc.get("bcy", 0), stream)
 
 
 def run(server: Server, requests, fill: Callable, deadline: float = 0.1,

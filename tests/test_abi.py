@@ -61,6 +61,24 @@ def test_null_plan_calls_are_safe():
     assert L.fizzy_proj_launches_per_solve(None) == 0
 
 
+def test_crop_fill_rejects_bad_arguments():
+    """Argument checks run before any CUDA call."""
+    import ctypes
+    L = _abi.lib()
+    six = (ctypes.c_void_p * 6)(*([8] * 6))
+    ok = dict(tx=4, ty=4, tz=4, nx=2, ny=2, nz=2, ox=0, oy=0, oz=0, bcx=0, bcy=0)
+
+    def call(src=six, dst=six, **kw):
+        a = dict(ok, **kw)
+        return L.fizzy_crop_fill(src, a["tx"], a["ty"], a["tz"], dst, a["nx"], a["ny"], a["nz"],
+                                 a["ox"], a["oy"], a["oz"], a["bcx"], a["bcy"], None)
+    assert call(src=None) == -1
+    assert call(dst=None) == -1
+    assert call(src=(ctypes.c_void_p * 6)(8, 8, 8, None, 8, 8)) == -1
+    for bad in (dict(tx=0), dict(nz=0), dict(oy=-1), dict(bcx=2), dict(bcy=-1)):
+        assert call(**bad) == -1, bad
+
+
 def test_workspace_bytes_scale():
     b1 = F.workspace_bytes(**base())
     b2 = F.workspace_bytes(**base(nz=16))
