@@ -382,9 +382,31 @@ def run_fizzy(args):
         plan.host_wait()
         el = slowest_rank(time.perf_counter() - t0, dist)
         plan.close()
+        # the host link's bound for the same bytes: the step's six input copies
+        # and four output copies alone, on two streams, with no solve
+        dev = [torch.empty(case.shape, dtype=torch.float64, device="cuda") for _ in range(10)]
+        s_in, s_out = torch.cuda.Stream(), torch.cuda.Stream()
+
+        def copies():
+            with torch.cuda.stream(s_in):
+                for h, d in zip(hin, dev[:6]):
+                    d.copy_(h, non_blocking=True)
+            with torch.cuda.stream(s_out):
+                for h, d in zip(hout, dev[6:]):
+                    h.copy_(d, non_blocking=True)
+        copies()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            copies()
+        torch.cuda.synchronize()
+        el_copy = slowest_rank(time.perf_counter() - t0, dist)
+        del dev
         e2e = {"value": job_throughput(npts, args.e2e_steps, world, el), "unit": "pts/s",
                "h2d_bytes_per_step": 6 * 8 * npts, "d2h_bytes_per_step": 4 * 8 * npts,
                "ms_per_step": el / args.e2e_steps * 1e3,
+               "copies_only_ms_per_step": el_copy / args.e2e_steps * 1e3,
+               "link_frac": el_copy / el,
                "api": "fizzy_proj_solve_host_async (pipelined, pinned host arrays)"}
 
     cpu = None

@@ -4,6 +4,7 @@
 // and the stats/error plumbing.
 #include "fizzy_proj.h"
 #include "kern_passes.cuh"
+#include "kern_r16.cuh"
 
 #include <algorithm>
 #include <cmath>
@@ -77,6 +78,7 @@ struct fizzy_proj_plan_s {
     int host_calls = 0;
     // launch shapes
     int Lx = 1, TXy = 2;
+    int x_r16 = 0;  // mixed, periodic nx = 256: register-resident FP32 x-passes
     size_t smem_x64 = 0, smem_x32 = 0, smem_y64 = 0, smem_y32 = 0;
     int cap[24] = {0};  // resident-grid size of each pass kernel (CAP_*)
     PassKernels kern;   // the pass kernels this plan launches
@@ -396,14 +398,27 @@ template <int NX, int NY> PassKernels kernels_for() {
     PassKernels k;
     k.xf64 = k_xfwd<double, XF_F64_DIVQ, NX>;
     k.xf32d = k_xfwd<float, XF_MIX_DIVQ, NX>;
-    k.xf32l = k_xfwd<float, XF_MIX_LOAD, NX>;
+    if constexpr (NX == R16_N)  // register-resident FP32 x-passes
+        k.xf32l = k_xfwd_r16_load;
+    else
+        k.xf32l = k_xfwd<float, XF_MIX_LOAD, NX>;
     k.yf64 = k_ypass<double, false, NY>;
     k.yi64 = k_ypass<double, true, NY>;
-    k.yf32 = k_ypass<float, false, NY>;
-    k.yi32 = k_ypass<float, true, NY>;
+    if constexpr (NY == R16_N) {  // register-resident FP32 y-passes
+        k.yf32 = k_ypass_r16<false>;
+        k.yi32 = k_ypass_r16<true>;
+    } else {
+        k.yf32 = k_ypass<float, false, NY>;
+        k.yi32 = k_ypass<float, true, NY>;
+    }
     k.xi64 = k_xinv<double, XI_STORE, NX>;
-    k.xi32s = k_xinv<float, XI_STORE, NX>;
-    k.xi32a = k_xinv<float, XI_ACCUM, NX>;
+    if constexpr (NX == R16_N) {
+        k.xi32s = k_xinv_r16<XI_STORE>;
+        k.xi32a = k_xinv_r16<XI_ACCUM>;
+    } else {
+        k.xi32s = k_xinv<float, XI_STORE, NX>;
+        k.xi32a = k_xinv<float, XI_ACCUM, NX>;
+    }
     return k;
 }
 template <int NX> PassKernels kernels_for_y(int fy) {
@@ -411,6 +426,13 @@ template <int NX> PassKernels kernels_for_y(int fy) {
 }
 PassKernels pick_kernels(int fx, int fy) {
     return fx == 256 ? kernels_for_y<256>(fy) : fx == 512 ? kernels_for_y<512>(fy) : kernels_for_y<0>(fy);
+}
+
+// The register-resident passes: static shared memory only (no opt-in).
+bool r16_kernel(const void *f) {
+    return f == (const void *)k_ypass_r16<false> || f == (const void *)k_ypass_r16<true> ||
+           f == (const void *)k_xfwd_r16_load || f == (const void *)k_xinv_r16<XI_STORE> ||
+           f == (const void *)k_xinv_r16<XI_ACCUM>;
 }
 
 // Opt every pass kernel instance into large dynamic shared memory.
@@ -423,21 +445,25 @@ void opt_in_smem(fizzy_proj_plan_t p, int bytes) {
                                  (const void *)k.yi32, (const void *)k.xi64, (const void *)k.xi32s,
                                  (const void *)k.xi32a};
             for (const void *f : fns)
-                note(p, cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+                if (!r16_kernel(f))
+                    note(p, cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
         }
 }
 
-void pass_caps(int *cap, const PassKernels &k, size_t sx64, size_t sx32, size_t sy64, size_t sy32) {
+// sx32r: dynamic shared memory of the FP32 load/inverse x-passes (0 for the
+// register-resident ones)
+void pass_caps(int *cap, const PassKernels &k, size_t sx64, size_t sx32, size_t sx32r, size_t sy64,
+               size_t sy32) {
     cap[CAP_XF64] = resident_grid(k.xf64, 256, sx64);
     cap[CAP_XF32D] = resident_grid(k.xf32d, 256, sx32);
-    cap[CAP_XF32L] = resident_grid(k.xf32l, 256, sx32);
+    cap[CAP_XF32L] = resident_grid(k.xf32l, 256, sx32r);
     cap[CAP_Y64F] = resident_grid(k.yf64, 256, sy64);
     cap[CAP_Y64I] = resident_grid(k.yi64, 256, sy64);
     cap[CAP_Y32F] = resident_grid(k.yf32, 256, sy32);
     cap[CAP_Y32I] = resident_grid(k.yi32, 256, sy32);
     cap[CAP_XI64] = resident_grid(k.xi64, 256, sx64);
-    cap[CAP_XI32S] = resident_grid(k.xi32s, 256, sx32);
-    cap[CAP_XI32A] = resident_grid(k.xi32a, 256, sx32);
+    cap[CAP_XI32S] = resident_grid(k.xi32s, 256, sx32r);
+    cap[CAP_XI32A] = resident_grid(k.xi32a, 256, sx32r);
     cap[CAP_TH64] = resident_grid(k_thomas<double>, THOMAS_BLOCK, thomas_smem<double>());
     cap[CAP_TH32] = resident_grid(k_thomas<float>, THOMAS_BLOCK, thomas_smem<float>());
     cap[CAP_RM] = resident_grid(k_residmax, 256, 0);
@@ -660,11 +686,15 @@ int fizzy_proj_plan(fizzy_proj_plan_t *out, const fizzy_proj_desc *d, void *stre
 
     // ---- launch shapes and shared-memory opt-in
     p->Lx = x_lines_per_cta(nx);
-    p->TXy = y_tile_cols(ny, p->mixed != 0);
+    // mixed plans with a periodic y of length 256 run the register-resident
+    // FP32 y-passes: 32 columns per CTA, static shared memory only
+    const bool y_r16 = p->mixed && fixed_len(ny, d->bc_y) == R16_N;
+    p->x_r16 = p->mixed && fixed_len(nx, d->bc_x) == R16_N;
+    p->TXy = y_r16 ? R16_TX : y_tile_cols(ny, p->mixed != 0);
     p->smem_x64 = pass_smem<double>(nx, p->Lx);
     p->smem_x32 = pass_smem<float>(nx, p->Lx);
     p->smem_y64 = pass_smem<double>(ny, p->TXy / 2);
-    p->smem_y32 = pass_smem<float>(ny, p->TXy / 2);
+    p->smem_y32 = y_r16 ? 0 : pass_smem<float>(ny, p->TXy / 2);
     {  // opt-in shared-memory limits, once per device (plans may be built concurrently)
         static std::mutex attrs_mu;
         static bool attrs_set[256] = {false};
@@ -677,7 +707,8 @@ int fizzy_proj_plan(fizzy_proj_plan_t *out, const fizzy_proj_desc *d, void *stre
         }
     }
     p->kern = pick_kernels(fixed_len(nx, d->bc_x), fixed_len(ny, d->bc_y));
-    pass_caps(p->cap, p->kern, p->smem_x64, p->smem_x32, p->smem_y64, p->smem_y32);
+    pass_caps(p->cap, p->kern, p->smem_x64, p->smem_x32, p->x_r16 ? 0 : p->smem_x32, p->smem_y64,
+              p->smem_y32);
     // stream-ordered plans are ready for work queued after them on their
     // stream; other plans are complete on return
     cudaError_t e = p->async_alloc ? cudaGetLastError() : cudaDeviceSynchronize();
@@ -827,6 +858,9 @@ int fizzy_proj_solve(fizzy_proj_plan_t p, const double *phi, const double *p_n, 
     const int nlines = ny * nz;
     // tiles of each pass; each stand-alone launch runs min(tiles, resident grid)
     const int xtiles = (nlines + 2 * p->Lx - 1) / (2 * p->Lx);
+    // the FP32 load/inverse x-passes: 32 lines per tile when register-resident
+    const int xrt = p->x_r16 ? (nlines + 31) / 32 : xtiles;
+    const size_t smx32r = p->x_r16 ? 0 : p->smem_x32;
     const int ygx = (nx + p->TXy - 1) / p->TXy, ytiles = ygx * nz;
     const int ttiles = (nx * ny + THOMAS_BLOCK - 1) / THOMAS_BLOCK;  // one z-line per thread
     const int rgx = (nx + 255) / 256, rtiles = rgx * ny * nz;
@@ -874,7 +908,7 @@ int fizzy_proj_solve(fizzy_proj_plan_t p, const double *phi, const double *p_n, 
         TIMED(KS_YFWD, (p->kern.yf32<<<grid(ytiles, CAP_Y32F), 256, p->smem_y32, s>>>(nx, ny, p->fy.d32, p->TXy, p->fhat32, nullptr, ygx, ytiles)));
         TIMED(KS_THOMAS, (k_thomas<float><<<grid(ttiles, CAP_TH32), THOMAS_BLOCK, thomas_smem<float>(), s>>>(g, p->Ux, p->Uy, p->mtab32, p->ibtab32, p->cup32, p->fhat32, nullptr, ttiles)));
         TIMED(KS_YINV, (p->kern.yi32<<<grid(ytiles, CAP_Y32I), 256, p->smem_y32, s>>>(nx, ny, p->fy.d32, p->TXy, p->fhat32, nullptr, ygx, ytiles)));
-        TIMED(KS_XINV, (p->kern.xi32s<<<grid(xtiles, CAP_XI32S), 256, p->smem_x32, s>>>(g, p->fx.d32, p->Lx, p->fhat32, p_np1, p->st, xtiles)));
+        TIMED(KS_XINV, (p->kern.xi32s<<<grid(xrt, CAP_XI32S), 256, smx32r, s>>>(g, p->fx.d32, p->Lx, p->fhat32, p_np1, p->st, xrt)));
         // residual of the FP32 solution (slot 0), then refinement sweeps
         // sw = 1..max_refine: transform of the stored residual, FP32 y/z/y^-1,
         // p += delta, then the residual fused with the correction (slot sw)
@@ -900,11 +934,11 @@ int fizzy_proj_solve(fizzy_proj_plan_t p, const double *phi, const double *p_n, 
         for (int sw = 1; sw <= p->max_refine; ++sw) {
             // a one-sweep solve runs sweep 1; later sweeps usually return at once
             auto gs = [&](int tiles, int c) { return sw == 1 ? grid(tiles, c) : rgrid(tiles, c); };
-            TIMED(KS_XFWD_R, (p->kern.xf32l<<<gs(xtiles, CAP_XF32L), 256, p->smem_x32, s>>>(g, p->fx.d32, p->Lx, la, xtiles)));
+            TIMED(KS_XFWD_R, (p->kern.xf32l<<<gs(xrt, CAP_XF32L), 256, smx32r, s>>>(g, p->fx.d32, p->Lx, la, xrt)));
             TIMED(KS_YFWD_R, (p->kern.yf32<<<gs(ytiles, CAP_Y32F), 256, p->smem_y32, s>>>(nx, ny, p->fy.d32, p->TXy, p->fhat32, conv, ygx, ytiles)));
             TIMED(KS_THOMAS_R, (k_thomas<float><<<gs(ttiles, CAP_TH32), THOMAS_BLOCK, thomas_smem<float>(), s>>>(g, p->Ux, p->Uy, p->mtab32, p->ibtab32, p->cup32, p->fhat32, conv, ttiles)));
             TIMED(KS_YINV_R, (p->kern.yi32<<<gs(ytiles, CAP_Y32I), 256, p->smem_y32, s>>>(nx, ny, p->fy.d32, p->TXy, p->fhat32, conv, ygx, ytiles)));
-            TIMED(KS_XACC, (p->kern.xi32a<<<gs(xtiles, CAP_XI32A), 256, p->smem_x32, s>>>(g, p->fx.d32, p->Lx, p->fhat32, p_np1, p->st, xtiles)));
+            TIMED(KS_XACC, (p->kern.xi32a<<<gs(xrt, CAP_XI32A), 256, smx32r, s>>>(g, p->fx.d32, p->Lx, p->fhat32, p_np1, p->st, xrt)));
             ra.slot = sw;
             TIMED(KS_RCORR, (k_resid<true><<<gs(rctiles, CAP_RC), rcb, 0, s>>>(g, RESID_KC, ra, rtgx, rtgy, rctiles)));
         }

@@ -41,6 +41,20 @@ def small_cases():
         # periodic x of length 512: the length-specialised x-pass instances
         "b512x8x5": I.CaseSpec(nx=512, ny=8, nz=5, bcx=0, bcy=1, n_bubbles=1, radius_cells=2,
                                config=20),
+        # periodic y of length 256: the register-resident FP32 y-passes of the
+        # mixed mode, with ragged 32-column tiles (even nx: paired loads; odd
+        # nx: single loads and a last line without imaginary part)
+        "b48x256x12": I.CaseSpec(nx=48, ny=256, nz=12, bcx=0, bcy=0, beta=1.5, n_bubbles=2,
+                                 radius_cells=3, config=22),
+        "b27x256x6_wx": I.CaseSpec(nx=27, ny=256, nz=6, bcx=1, bcy=0, n_bubbles=1, radius_cells=3,
+                                   config=23),
+        # periodic x of length 256: the register-resident FP32 x-passes (the
+        # second has an odd number of x-lines, 9 x 5: a last line without
+        # partner)
+        "b256x12x10": I.CaseSpec(nx=256, ny=12, nz=10, bcx=0, bcy=1, beta=1.2, n_bubbles=2,
+                                 radius_cells=3, config=24),
+        "b256x9x5_wy": I.CaseSpec(nx=256, ny=9, nz=5, bcx=0, bcy=1, n_bubbles=1, radius_cells=2,
+                                  config=25),
         # light drops in a heavy phase: rho0 = rho_l, split term from 1 - phi
         "b48x32x24_swapped": I.CaseSpec(nx=48, ny=32, nz=24, bcx=0, bcy=1, beta=1.5, n_bubbles=3,
                                         radius_cells=4, rho_l=1e-3, rho_g=1.0, config=19),
@@ -65,7 +79,8 @@ def test_fp64_matches_oracle(cuda_ok, name):
 
 
 @pytest.mark.parametrize("name", ["drop32", "b48x36x20_nx_stretch", "b96x64x33", "b27x18x12_ny",
-                                  "b384x6x5", "b81x3x7_nn", "b48x32x24_swapped", "b512x8x5"])
+                                  "b384x6x5", "b81x3x7_nn", "b48x32x24_swapped", "b512x8x5",
+                                  "b48x256x12", "b27x256x6_wx", "b256x12x10", "b256x9x5_wy"])
 def test_mixed_matches_oracle(cuda_ok, name):
     c = I.make_case(CASES[name])
     ref = O.project_case(c)
@@ -78,6 +93,21 @@ def test_mixed_matches_oracle(cuda_ok, name):
     assert ep <= TOLMIX, ep
     assert eu <= TOLMIX, eu
     assert st["div_metric"] < 1e-10
+
+
+@pytest.mark.parametrize("name", ["b48x256x12", "b27x256x6_wx", "b256x12x10", "b256x9x5_wy",
+                                  "b96x64x33"])
+def test_fp32_solve_accuracy(cuda_ok, name):
+    """The FP32 solve alone (stopped at its first residual) is accurate to
+    FP32 level, whichever transform kernels it runs (both the Stockham and the
+    register-resident passes leave relres 4e-5 to 6e-5 at n = 256), and
+    at most two refinement sweeps then reach 1e-10."""
+    c = I.make_case(CASES[name])
+    got = gpu_project(c, F.MIXED, tol=1e-3, div_tol=1.0)
+    st = got["stats"]
+    assert st["iterations"] == 0 and 0 < st["relres"] <= 1e-4, st
+    st = gpu_project(c, F.MIXED)["stats"]
+    assert st["converged"] == 1 and 1 <= st["iterations"] <= 2, st
 
 
 def test_equal_density_closed_form(cuda_ok):
