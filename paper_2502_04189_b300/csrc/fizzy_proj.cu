@@ -78,7 +78,7 @@ struct fizzy_proj_plan_s {
     int host_calls = 0;
     // launch shapes
     int Lx = 1, TXy = 2;
-    int x_r16 = 0;  // mixed, periodic nx = 256: register-resident FP32 x-passes
+    int x_r16 = 0;  // mixed, periodic nx = 256 or 512: register-resident FP32 x-passes
     size_t smem_x64 = 0, smem_x32 = 0, smem_y64 = 0, smem_y32 = 0;
     int cap[24] = {0};  // resident-grid size of each pass kernel (CAP_*)
     PassKernels kern;   // the pass kernels this plan launches
@@ -398,23 +398,23 @@ template <int NX, int NY> PassKernels kernels_for() {
     PassKernels k;
     k.xf64 = k_xfwd<double, XF_F64_DIVQ, NX>;
     k.xf32d = k_xfwd<float, XF_MIX_DIVQ, NX>;
-    if constexpr (NX == R16_N)  // register-resident FP32 x-passes
-        k.xf32l = k_xfwd_r16_load;
+    if constexpr (NX != 0)  // register-resident FP32 x-passes
+        k.xf32l = k_xfwd_r_load<NX>;
     else
         k.xf32l = k_xfwd<float, XF_MIX_LOAD, NX>;
     k.yf64 = k_ypass<double, false, NY>;
     k.yi64 = k_ypass<double, true, NY>;
-    if constexpr (NY == R16_N) {  // register-resident FP32 y-passes
-        k.yf32 = k_ypass_r16<false>;
-        k.yi32 = k_ypass_r16<true>;
+    if constexpr (NY != 0) {  // register-resident FP32 y-passes
+        k.yf32 = k_ypass_r<false, NY>;
+        k.yi32 = k_ypass_r<true, NY>;
     } else {
         k.yf32 = k_ypass<float, false, NY>;
         k.yi32 = k_ypass<float, true, NY>;
     }
     k.xi64 = k_xinv<double, XI_STORE, NX>;
-    if constexpr (NX == R16_N) {
-        k.xi32s = k_xinv_r16<XI_STORE>;
-        k.xi32a = k_xinv_r16<XI_ACCUM>;
+    if constexpr (NX != 0) {
+        k.xi32s = k_xinv_r<XI_STORE, NX>;
+        k.xi32a = k_xinv_r<XI_ACCUM, NX>;
     } else {
         k.xi32s = k_xinv<float, XI_STORE, NX>;
         k.xi32a = k_xinv<float, XI_ACCUM, NX>;
@@ -430,9 +430,14 @@ PassKernels pick_kernels(int fx, int fy) {
 
 // The register-resident passes: static shared memory only (no opt-in).
 bool r16_kernel(const void *f) {
-    return f == (const void *)k_ypass_r16<false> || f == (const void *)k_ypass_r16<true> ||
-           f == (const void *)k_xfwd_r16_load || f == (const void *)k_xinv_r16<XI_STORE> ||
-           f == (const void *)k_xinv_r16<XI_ACCUM>;
+    const void *fs[] = {(const void *)k_ypass_r<false, 256>, (const void *)k_ypass_r<true, 256>,
+                        (const void *)k_ypass_r<false, 512>, (const void *)k_ypass_r<true, 512>,
+                        (const void *)k_xfwd_r_load<256>, (const void *)k_xfwd_r_load<512>,
+                        (const void *)k_xinv_r<XI_STORE, 256>, (const void *)k_xinv_r<XI_ACCUM, 256>,
+                        (const void *)k_xinv_r<XI_STORE, 512>, (const void *)k_xinv_r<XI_ACCUM, 512>};
+    for (const void *x : fs)
+        if (f == x) return true;
+    return false;
 }
 
 // Opt every pass kernel instance into large dynamic shared memory.
@@ -686,11 +691,11 @@ int fizzy_proj_plan(fizzy_proj_plan_t *out, const fizzy_proj_desc *d, void *stre
 
     // ---- launch shapes and shared-memory opt-in
     p->Lx = x_lines_per_cta(nx);
-    // mixed plans with a periodic y of length 256 run the register-resident
-    // FP32 y-passes: 32 columns per CTA, static shared memory only
-    const bool y_r16 = p->mixed && fixed_len(ny, d->bc_y) == R16_N;
-    p->x_r16 = p->mixed && fixed_len(nx, d->bc_x) == R16_N;
-    p->TXy = y_r16 ? R16_TX : y_tile_cols(ny, p->mixed != 0);
+    // mixed plans with a periodic direction of length 256 or 512 run the
+    // register-resident FP32 passes along it: static shared memory only
+    const bool y_r16 = p->mixed && fixed_len(ny, d->bc_y) != 0;
+    p->x_r16 = p->mixed && fixed_len(nx, d->bc_x) != 0;
+    p->TXy = y_r16 ? r_tile_cols(ny) : y_tile_cols(ny, p->mixed != 0);
     p->smem_x64 = pass_smem<double>(nx, p->Lx);
     p->smem_x32 = pass_smem<float>(nx, p->Lx);
     p->smem_y64 = pass_smem<double>(ny, p->TXy / 2);
@@ -859,7 +864,7 @@ int fizzy_proj_solve(fizzy_proj_plan_t p, const double *phi, const double *p_n, 
     // tiles of each pass; each stand-alone launch runs min(tiles, resident grid)
     const int xtiles = (nlines + 2 * p->Lx - 1) / (2 * p->Lx);
     // the FP32 load/inverse x-passes: 32 lines per tile when register-resident
-    const int xrt = p->x_r16 ? (nlines + 31) / 32 : xtiles;
+    const int xrt = p->x_r16 ? (nlines + r_tile_lines(nx) - 1) / r_tile_lines(nx) : xtiles;
     const size_t smx32r = p->x_r16 ? 0 : p->smem_x32;
     const int ygx = (nx + p->TXy - 1) / p->TXy, ytiles = ygx * nz;
     const int ttiles = (nx * ny + THOMAS_BLOCK - 1) / THOMAS_BLOCK;  // one z-line per thread

@@ -1,7 +1,8 @@
-// Register-resident FP32 transforms of periodic length 256 (mixed mode).
+// Register-resident FP32 transforms of periodic length 256 and 512 (mixed mode).
 //
-// The y-passes of the FP32 solve (Sec. 3.2: real FFTs along the periodic
-// directions) for ny = 256.  The DFT of length 256 is split as 16 x 16 (the
+// The FP32 transform passes of the mixed-precision solve (Sec. 3.2: real
+// FFTs along the periodic directions) for n = 256 and 512.  The DFT of length
+// 256 is split as 16 x 16 (the
 // four-step form of the Cooley-Tukey factorisation): with n = 16 n1 + n2 and
 // k = k1 + 16 k2,
 //     X[k1 + 16 k2] = sum_n2 W16^(n2 k2) [ W256^(n2 k1) sum_n1 x[16 n1 + n2] W16^(n1 k1) ],
@@ -18,16 +19,20 @@
 // warp access (a load straight into the per-thread order would touch 16 rows
 // per warp instruction).
 //
+// Length 512 first takes one radix-2 step of decimation in frequency,
+//     X[2k]     = DFT256( x[n] + x[n + 256] )[k],
+//     X[2k + 1] = DFT256( (x[n] - x[n + 256]) W512^n )[k],
+// over two groups of 16 threads (a warp per line) that swap their halves
+// with one shuffle; each group then runs the 256-point transform.
+//
 // Same arithmetic as the Stockham passes (about 11 FP32 multiply-adds per
-// real point); what it removes is their per-stage shared-memory round trips,
-// index divisions and the select work of the FMA-form twiddles.
+// real point at n = 256); what it removes is their per-stage shared-memory
+// round trips, index divisions and the select work of the FMA-form twiddles.
 #pragma once
 #include "kern_passes.cuh"
 
 namespace fz {
 
-constexpr int R16_N = 256;
-constexpr int R16_TX = 32;  // real columns of one CTA (16 complex lines x 16 threads)
 
 __device__ __forceinline__ float2 c_add(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ float2 c_sub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
@@ -102,14 +107,25 @@ __device__ __forceinline__ void dft16(float2 (&v)[16]) {
     for (int k = 0; k < 16; ++k) v[k] = o[k];
 }
 
-// Shared memory of one CTA: its 16 complex lines (line stride R16_LS, so
-// that both the row-wise staging and the per-line accesses are free of bank
-// conflicts), reused for the 16 x 16 exchange, and the twiddles W256^(n2 k1)
-// at [k1][n2] (conjugated for the inverse).
-constexpr int R16_LS = R16_N + 1;
+// Launch shape of a length: complex lines per CTA of 256 threads (16
+// threads per line at 256, a warp per line at 512), the line stride in
+// shared memory (padded) and the y-pass tile width in real columns.
+template <int N> struct RShape {
+    static_assert(N == 256 || N == 512, "register-resident lengths");
+    static constexpr int LINES = N == 256 ? 16 : 8;
+    static constexpr int LS = N + 1;
+    static constexpr int TX = 2 * LINES;
+};
+constexpr int r_tile_cols(int n) { return n == 256 ? RShape<256>::TX : RShape<512>::TX; }
+constexpr int r_tile_lines(int n) { return n == 256 ? 2 * RShape<256>::LINES : 2 * RShape<512>::LINES; }
+
+// Shared memory of one CTA: its lines (16 x 257 >= 8 x 513 complex values),
+// reused for the 16 x 16 exchanges; the twiddles W256^(n2 k1) at [k1][n2]
+// and W512^n (n < 256), conjugated for the inverse.
 struct R16Smem {
-    float2 x[16 * R16_LS];
-    float2 tw[R16_N];
+    float2 x[16 * 257];
+    float2 tw[256];
+    float2 tw2[256];
 };
 
 template <bool INV>
@@ -118,19 +134,21 @@ __device__ __forceinline__ void r16_tables(R16Smem &sm) {
     float s, c;
     sincospif(-(float)(n2 * k1) / 128.f, &s, &c);
     sm.tw[threadIdx.x] = make_float2(c, INV ? -s : s);
+    sincospif(-(float)threadIdx.x / 256.f, &s, &c);
+    sm.tw2[threadIdx.x] = make_float2(c, INV ? -s : s);
 }
 
-// Steps 1-3 of the four-step DFT on line X: thread t holds v[n1] =
-// x[16 n1 + t] and ends with v[k2] = X[t + 16 k2].  X is overwritten; all
-// threads must have finished reading X before the call (barriers inside,
-// the last one after the exchange reads).  WARP: every line lives in one
-// warp (the x-passes), so warp barriers suffice.
 template <bool WARP>
 __device__ __forceinline__ void r16_sync() {
     if (WARP) __syncwarp();
     else __syncthreads();
 }
-template <bool INV, bool WARP = false>
+
+// Steps 1-3 of the four-step DFT on the 256 values at X: thread t holds
+// v[n1] = x[16 n1 + t] and ends with v[k2] = X[t + 16 k2].  X is overwritten;
+// its threads must have finished reading X before the call (barriers inside,
+// the last one after the exchange reads).  WARP: X belongs to one warp.
+template <bool INV, bool WARP>
 __device__ __forceinline__ void r16_fft(const R16Smem &sm, float2 *X, int t, float2 (&v)[16]) {
     dft16<INV>(v);
 #pragma unroll
@@ -147,81 +165,142 @@ __device__ __forceinline__ void r16_fft(const R16Smem &sm, float2 *X, int t, flo
     dft16<INV>(v);
 }
 
-// One tile: 32 real columns (bx) of one z-plane of an (nz, 256, nx) FP32
-// array, transformed along y in place.  Forward: real columns -> half-complex
-// spectra scaled by 2 (the convention of the Stockham passes); inverse: the
-// reverse, unscaled.  Rows move between global and shared memory one warp
-// per row (32 columns, one 128-byte segment); column 2l + e of the tile is
-// component e of complex line l.
-template <bool INV>
-__device__ __forceinline__ void ypass_r16_tile(int nx, float *data, int bx, int kplane, R16Smem &sm) {
-    const int ln = threadIdx.x >> 4, t = threadIdx.x & 15;
+// Position of a thread: complex line ln of the CTA, group h (the half of a
+// 512-line), index t in the group.  Its inputs are the samples
+// 16 n1 + t + 256 h, its outputs the indices out_index(k2).
+template <int N> struct RPos {
+    int ln, h, t;
+    __device__ __forceinline__ RPos() {
+        t = threadIdx.x & 15;
+        ln = N == 256 ? threadIdx.x >> 4 : threadIdx.x >> 5;
+        h = N == 256 ? 0 : (threadIdx.x >> 4) & 1;
+    }
+    __device__ __forceinline__ int in_index(int n1) const { return 16 * n1 + t + 256 * h; }
+    __device__ __forceinline__ int out_index(int k2) const {
+        return N == 256 ? t + 16 * k2 : 2 * (t + 16 * k2) + h;
+    }
+};
+
+// The transform of one line: v[n1] = the input at in_index(n1) on entry,
+// v[k2] = the output at out_index(k2) on return.  X: the line's region
+// (N values); warp barriers only (a line never spans warps).
+template <bool INV, int N>
+__device__ __forceinline__ void r_fft(const R16Smem &sm, float2 *X, const RPos<N> &q, float2 (&v)[16]) {
+    if constexpr (N == 512) {  // radix-2 step: group 0 gets lo + hi, group 1 (lo - hi) W512^n
+#pragma unroll
+        for (int n1 = 0; n1 < 16; ++n1) {
+            const float2 own = v[n1];
+            const float2 oth = make_float2(__shfl_xor_sync(0xffffffffu, own.x, 16),
+                                           __shfl_xor_sync(0xffffffffu, own.y, 16));
+            const float2 lo = q.h ? oth : own, hi = q.h ? own : oth;
+            if (q.h == 0) {
+                v[n1] = c_add(lo, hi);
+            } else {
+                const float2 w = sm.tw2[16 * n1 + q.t];
+                v[n1] = c_mul(c_sub(lo, hi), w.x, w.y);
+            }
+        }
+    }
+    r16_fft<INV, true>(sm, X + 256 * q.h, q.t, v);
+}
+
+// Separation of the forward transform of a packed line (two real lines as
+// real and imaginary part): the half-complex spectra, scaled by 2 (the
+// convention of the Stockham passes), through fn(k, a_k, b_k).  X[K] pairs
+// with X[N - K]: at 256 the partner's register 15 - k2 of thread
+// (16 - t) mod 16, or this thread's register (16 - k2) mod 16 (t = 0); at 512
+// the odd outputs pair within group 1 with thread 15 - t, register 15 - k2.
+template <int N, typename F>
+__device__ __forceinline__ void r_separate(const float2 (&v)[16], const RPos<N> &q, F &&fn) {
+    const int lane = threadIdx.x & 31;
+    const int src = (N == 256 || q.h == 0) ? ((lane & 16) | ((16 - q.t) & 15)) : (16 | (15 - q.t));
+    const bool self = q.h == 0 && q.t == 0;
+#pragma unroll
+    for (int k2 = 0; k2 < 16; ++k2) {
+        const float qx = __shfl_sync(0xffffffffu, v[15 - k2].x, src);
+        const float qy = __shfl_sync(0xffffffffu, v[15 - k2].y, src);
+        const float2 z = v[k2];
+        const float2 y = self ? v[(16 - k2) & 15] : make_float2(qx, qy);
+        const int k = q.out_index(k2);
+        // k <= n/2: (Re A_k, Re B_k) x 2; k > n/2: (Im A_m, Im B_m) x 2, m = n - k
+        if (k <= N / 2) fn(k, z.x + y.x, z.y + y.y);
+        else fn(k, y.y - z.y, z.x - y.x);
+    }
+}
+
+// Combination ahead of the inverse transform: v[n1] = Z[in_index(n1)] from
+// the half-complex spectra read through get(k) = (a_k, b_k).
+template <int N, typename G>
+__device__ __forceinline__ void r_combine(float2 (&v)[16], const RPos<N> &q, G &&get) {
+#pragma unroll
+    for (int n1 = 0; n1 < 16; ++n1) {
+        const int k = q.in_index(n1);
+        const float2 o = get(k), p = get((N - k) & (N - 1));  // indices k and n - k
+        if (k == 0 || k == N / 2) v[n1] = o;
+        else if (k < N / 2) v[n1] = make_float2(o.x - p.y, p.x + o.y);
+        else v[n1] = make_float2(p.x + o.y, p.y - o.x);
+    }
+}
+
+// ---- y-passes: one tile = TX real columns (bx) of one z-plane of an
+// (nz, N, nx) FP32 array, transformed along y in place.  Rows move between
+// global and shared memory a warp at a time (32 columns of one row at 256,
+// 16 columns of two rows at 512); column 2l + e of the tile is component e
+// of complex line l.  Forward: real columns -> half-complex spectra scaled
+// by 2; inverse: the reverse, unscaled.
+template <bool INV, int N>
+__device__ __forceinline__ void ypass_r_tile(int nx, float *data, int bx, int kplane, R16Smem &sm) {
+    constexpr int TX = RShape<N>::TX, LS = RShape<N>::LS;
+    constexpr int RPW = 32 / TX;  // rows per warp access
+    const RPos<N> q;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const bool col_ok = bx * R16_TX + lane < nx;
-    float *gcol = data + (size_t)kplane * R16_N * nx + bx * R16_TX + lane;
-    float *scol = (float *)sm.x + (lane >> 1) * (2 * R16_LS) + (lane & 1);
-    float2 *X = sm.x + ln * R16_LS;
-    // 1. stage the tile: warp w moves rows w, w + 8, ... (eight loads in flight)
+    const int col = lane % TX, rsub = lane / TX;
+    const bool col_ok = bx * TX + col < nx;
+    float *gcol = data + (size_t)kplane * N * nx + bx * TX + col;
+    float *scol = (float *)sm.x + (col >> 1) * (2 * LS) + (col & 1);
+    float2 *X = sm.x + q.ln * LS;
+    auto row_of = [&](int i) { return i * (8 * RPW) + warp * RPW + rsub; };  // i < 32
+    // 1. stage the tile (sixteen loads in flight)
 #pragma unroll 1
-    for (int i0 = 0; i0 < R16_N / 8; i0 += 16) {
+    for (int i0 = 0; i0 < 32; i0 += 16) {
         float r[16];
 #pragma unroll
-        for (int u = 0; u < 16; ++u) r[u] = col_ok ? gcol[(size_t)(warp + 8 * (i0 + u)) * nx] : 0.f;
+        for (int u = 0; u < 16; ++u) r[u] = col_ok ? gcol[(size_t)row_of(i0 + u) * nx] : 0.f;
 #pragma unroll
-        for (int u = 0; u < 16; ++u) scol[2 * (warp + 8 * (i0 + u))] = r[u];
+        for (int u = 0; u < 16; ++u) scol[2 * row_of(i0 + u)] = r[u];
     }
     __syncthreads();
     float2 v[16];
     if (!INV) {
 #pragma unroll
-        for (int n1 = 0; n1 < 16; ++n1) v[n1] = X[16 * n1 + t];
+        for (int n1 = 0; n1 < 16; ++n1) v[n1] = X[q.in_index(n1)];
     } else {
-        // combine the half-complex spectra of the two real lines into Z[k]
-#pragma unroll
-        for (int n1 = 0; n1 < 16; ++n1) {
-            const int k = t + 16 * n1;
-            const float2 o = X[k], p = X[(R16_N - k) & (R16_N - 1)];  // rows k and n - k
-            if (k == 0 || k == R16_N / 2) v[n1] = o;
-            else if (k < R16_N / 2) v[n1] = make_float2(o.x - p.y, p.x + o.y);
-            else v[n1] = make_float2(p.x + o.y, p.y - o.x);
-        }
+        r_combine<N>(v, q, [&](int k) { return X[k]; });
     }
-    __syncthreads();
-    r16_fft<INV>(sm, X, t, v);
+    __syncwarp();  // the line's region is the exchange buffer next
+    r_fft<INV, N>(sm, X, q, v);
     if (!INV) {
-        // separation: X[k] pairs with X[256 - k] = the partner's register
-        // 15 - k2 (t != 0) or this thread's register (16 - k2) mod 16 (t = 0)
-        const int src = (threadIdx.x & 16) | ((16 - t) & 15);
-#pragma unroll
-        for (int k2 = 0; k2 < 16; ++k2) {
-            const float qx = __shfl_sync(0xffffffffu, v[15 - k2].x, src);
-            const float qy = __shfl_sync(0xffffffffu, v[15 - k2].y, src);
-            const float2 z = v[k2];
-            const float2 y = (t == 0) ? v[(16 - k2) & 15] : make_float2(qx, qy);
-            const int k = t + 16 * k2;
-            // k <= n/2: (Re A_k, Re B_k) x 2; k > n/2: (Im A_m, Im B_m) x 2, m = n - k
-            X[k] = k <= R16_N / 2 ? make_float2(z.x + y.x, z.y + y.y) : make_float2(y.y - z.y, z.x - y.x);
-        }
+        r_separate<N>(v, q, [&](int k, float a, float b) { X[k] = make_float2(a, b); });
     } else {
 #pragma unroll
-        for (int k2 = 0; k2 < 16; ++k2) X[t + 16 * k2] = v[k2];
+        for (int k2 = 0; k2 < 16; ++k2) X[q.out_index(k2)] = v[k2];
     }
     __syncthreads();
-    // 2. write the tile back, one row per warp
+    // 2. write the tile back
 #pragma unroll
-    for (int i = 0; i < R16_N / 8; ++i) {
-        const int row = warp + 8 * i;
+    for (int i = 0; i < 32; ++i) {
+        const int row = row_of(i);
         if (col_ok) gcol[(size_t)row * nx] = scol[2 * row];
     }
     __syncthreads();  // the buffer is free for the next tile
 }
 
-// y-pass over ntiles = ygx x nz tiles (ygx = ceil(nx / 32)); the signature of
+// y-pass over ntiles = ygx x nz tiles (ygx = ceil(nx / TX)); the signature of
 // k_ypass, so the plan can launch either.  conv: return at once when the
 // refinement has converged.
-template <bool INV>
-__global__ void __launch_bounds__(256, 4) k_ypass_r16(int nx, int ny, FFTDesc D, int TX, float *data,
-                                                   const int *conv, int ygx, int ntiles) {
+template <bool INV, int N>
+__global__ void __launch_bounds__(256, 4) k_ypass_r(int nx, int ny, FFTDesc D, int TX, float *data,
+                                                    const int *conv, int ygx, int ntiles) {
     (void)ny;
     (void)D;
     (void)TX;
@@ -231,80 +310,54 @@ __global__ void __launch_bounds__(256, 4) k_ypass_r16(int nx, int ny, FFTDesc D,
     __syncthreads();
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const int kplane = tile / ygx;
-        ypass_r16_tile<INV>(nx, data, tile - kplane * ygx, kplane, sm);
+        ypass_r_tile<INV, N>(nx, data, tile - kplane * ygx, kplane, sm);
     }
 }
 
-// ---- x-passes (nx = 256): 32 real lines of the [nz][ny] line set per CTA;
-// the warp of complex line l (real lines 2l, 2l + 1 of the tile) loads, transforms
-// and stores it alone, so only warp barriers are needed.  At each register
-// index the 16 threads of a line touch 64 consecutive bytes of each of its
-// two rows.
-
-// Separation of the forward transform (see the y-pass) through fn(k, a, b).
-template <typename F>
-__device__ __forceinline__ void r16_separate(const float2 (&v)[16], int t, F &&fn) {
-    const int src = (threadIdx.x & 16) | ((16 - t) & 15);
-#pragma unroll
-    for (int k2 = 0; k2 < 16; ++k2) {
-        const float qx = __shfl_sync(0xffffffffu, v[15 - k2].x, src);
-        const float qy = __shfl_sync(0xffffffffu, v[15 - k2].y, src);
-        const float2 z = v[k2];
-        const float2 y = (t == 0) ? v[(16 - k2) & 15] : make_float2(qx, qy);
-        const int k = t + 16 * k2;
-        if (k <= R16_N / 2) fn(k, z.x + y.x, z.y + y.y);
-        else fn(k, y.y - z.y, z.x - y.x);
-    }
-}
-
-// Combination of the inverse transform: v[n1] = Z[t + 16 n1] from the
-// half-complex spectra read through get(k) = (a[k], b[k]).
-template <typename G>
-__device__ __forceinline__ void r16_combine(float2 (&v)[16], int t, G &&get) {
-#pragma unroll
-    for (int n1 = 0; n1 < 16; ++n1) {
-        const int k = t + 16 * n1;
-        const float2 o = get(k), p = get((R16_N - k) & (R16_N - 1));
-        if (k == 0 || k == R16_N / 2) v[n1] = o;
-        else if (k < R16_N / 2) v[n1] = make_float2(o.x - p.y, p.x + o.y);
-        else v[n1] = make_float2(p.x + o.y, p.y - o.x);
-    }
-}
+// ---- x-passes: 2 LINES real lines of the [nz][ny] line set per CTA; a
+// line's threads load, transform and store it alone (warp barriers only).
+// At each register index the 16 threads of a group touch 64 consecutive
+// bytes of each of the two rows of their line.
 
 // The transform of the stored FP32 residual (refinement sweeps), in place:
 // the mode XF_MIX_LOAD of k_xfwd.
-__global__ void __launch_bounds__(256, 4) k_xfwd_r16_load(GridDev g, FFTDesc D, int L, XArgs a,
-                                                          int ntiles) {
+template <int N>
+__global__ void __launch_bounds__(256, 4) k_xfwd_r_load(GridDev g, FFTDesc D, int L, XArgs a,
+                                                        int ntiles) {
     (void)D;
     (void)L;
     __shared__ R16Smem sm;
     if (*(volatile const int *)&a.st->converged) return;
     r16_tables<false>(sm);
     __syncthreads();
-    const int nlines = g.ny * g.nz, ln = threadIdx.x >> 4, t = threadIdx.x & 15;
+    const RPos<N> q;
+    const int nlines = g.ny * g.nz;
     float *data = (float *)a.out;
-    float2 *X = sm.x + ln * R16_LS;
+    float2 *X = sm.x + q.ln * RShape<N>::LS;
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const int ra = tile * 32 + 2 * ln;
+        const int ra = tile * r_tile_lines(N) + 2 * q.ln;
         const bool oka = ra < nlines, okb = ra + 1 < nlines;
-        float *la = data + (size_t)ra * R16_N, *lb = la + R16_N;
+        float *la = data + (size_t)ra * N, *lb = la + N;
         float2 v[16];
 #pragma unroll
-        for (int n1 = 0; n1 < 16; ++n1)
-            v[n1] = make_float2(oka ? la[16 * n1 + t] : 0.f, okb ? lb[16 * n1 + t] : 0.f);
-        r16_fft<false, true>(sm, X, t, v);
-        r16_separate(v, t, [&](int k, float va, float vb) {
+        for (int n1 = 0; n1 < 16; ++n1) {
+            const int i = q.in_index(n1);
+            v[n1] = make_float2(oka ? la[i] : 0.f, okb ? lb[i] : 0.f);
+        }
+        r_fft<false, N>(sm, X, q, v);
+        r_separate<N>(v, q, [&](int k, float va, float vb) {
             if (oka) la[k] = va;
             if (okb) lb[k] = vb;
         });
+        __syncwarp();  // every lane has read its line before the next tile
     }
 }
 
 // Inverse x-pass to p (FP64): XI_STORE p = the FP32 solution, XI_ACCUM
 // p += delta 2^e (e: exponent of max|f|); the modes of k_xinv.
-template <int MODE>
-__global__ void __launch_bounds__(256, 4) k_xinv_r16(GridDev g, FFTDesc D, int L, const float *in,
-                                                     double *p, const DevStats *st, int ntiles) {
+template <int MODE, int N>
+__global__ void __launch_bounds__(256, 4) k_xinv_r(GridDev g, FFTDesc D, int L, const float *in,
+                                                   double *p, const DevStats *st, int ntiles) {
     (void)D;
     (void)L;
     __shared__ R16Smem sm;
@@ -312,45 +365,53 @@ __global__ void __launch_bounds__(256, 4) k_xinv_r16(GridDev g, FFTDesc D, int L
     r16_tables<true>(sm);
     __syncthreads();
     const int ef = MODE == XI_ACCUM ? exp_of_bits(*(volatile const unsigned long long *)&st->fmax_bits) : 0;
-    const int nlines = g.ny * g.nz, ln = threadIdx.x >> 4, t = threadIdx.x & 15;
-    float2 *X = sm.x + ln * R16_LS;
+    const RPos<N> q;
+    const int nlines = g.ny * g.nz;
+    constexpr int LS = RShape<N>::LS;
+    float2 *X = sm.x + q.ln * LS;
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const int ra = tile * 32 + 2 * ln;
+        const int ra = tile * r_tile_lines(N) + 2 * q.ln;
         const bool oka = ra < nlines, okb = ra + 1 < nlines;
-        const float *ia = in + (size_t)ra * R16_N, *ib = ia + R16_N;
+        const float *ia = in + (size_t)ra * N, *ib = ia + N;
         float2 v[16];
-        r16_combine(v, t, [&](int k) { return make_float2(oka ? ia[k] : 0.f, okb ? ib[k] : 0.f); });
-        r16_fft<true, true>(sm, X, t, v);
-        double *pa = p + (size_t)ra * R16_N, *pb = pa + R16_N;
+        r_combine<N>(v, q, [&](int k) { return make_float2(oka ? ia[k] : 0.f, okb ? ib[k] : 0.f); });
+        r_fft<true, N>(sm, X, q, v);
         if (MODE == XI_STORE) {
+            double *pa = p + (size_t)ra * N, *pb = pa + N;
 #pragma unroll
             for (int k2 = 0; k2 < 16; ++k2) {
-                const int x = t + 16 * k2;
+                const int x = q.out_index(k2);
                 if (oka) pa[x] = f32_to_f64_shift(v[k2].x, 0);
                 if (okb) pb[x] = f32_to_f64_shift(v[k2].y, 0);
             }
         } else {
-            // delta through the line's exchange buffer, then p += delta row by
-            // row: lane = x mod 32, eight loads of p in flight per lane
+            // delta through the line's region, then p += delta row by row:
+            // lane = x mod 32, eight loads of p in flight per lane
 #pragma unroll
-            for (int k2 = 0; k2 < 16; ++k2) X[t + 16 * k2] = v[k2];
+            for (int k2 = 0; k2 < 16; ++k2) X[q.out_index(k2)] = v[k2];
             __syncwarp();
-            const int lane = threadIdx.x & 31, l0 = ln & ~1;
+            const int lane = threadIdx.x & 31;
+            const int l0 = N == 256 ? (q.ln & ~1) : q.ln;  // the warp's first line
+            constexpr int WROWS = N == 256 ? 4 : 2;         // real rows of the warp
 #pragma unroll 1
-            for (int r = 0; r < 4; ++r) {  // rows a, b of the warp's two lines
-                const int row = tile * 32 + 2 * l0 + r;
+            for (int r = 0; r < WROWS; ++r) {
+                const int row = tile * r_tile_lines(N) + 2 * l0 + r;
                 if (row < nlines) {
-                    double *pr = p + (size_t)row * R16_N + lane;
-                    const float *dr = (const float *)(sm.x + (l0 + (r >> 1)) * R16_LS) + (r & 1) + 2 * lane;
-                    double q[8];
+                    double *pr = p + (size_t)row * N + lane;
+                    const float *dr = (const float *)(sm.x + (l0 + (r >> 1)) * LS) + (r & 1) + 2 * lane;
 #pragma unroll
-                    for (int i = 0; i < 8; ++i) q[i] = pr[32 * i];
+                    for (int i0 = 0; i0 < N / 32; i0 += 8) {
+                        double qv[8];
 #pragma unroll
-                    for (int i = 0; i < 8; ++i) pr[32 * i] = q[i] + f32_to_f64_shift(dr[64 * i], ef);
+                        for (int i = 0; i < 8; ++i) qv[i] = pr[32 * (i0 + i)];
+#pragma unroll
+                        for (int i = 0; i < 8; ++i)
+                            pr[32 * (i0 + i)] = qv[i] + f32_to_f64_shift(dr[64 * (i0 + i)], ef);
+                    }
                 }
             }
-            __syncwarp();  // the buffer is rewritten by the next tile
         }
+        __syncwarp();  // the line's region is rewritten by the next tile
     }
 }
 

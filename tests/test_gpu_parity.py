@@ -55,6 +55,15 @@ def small_cases():
                                  radius_cells=3, config=24),
         "b256x9x5_wy": I.CaseSpec(nx=256, ny=9, nz=5, bcx=0, bcy=1, n_bubbles=1, radius_cells=2,
                                   config=25),
+        # length 512 (radix-2 split ahead of the 16 x 16 transform): periodic
+        # y with ragged 16-column tiles (even and odd nx), periodic x with an
+        # odd number of x-lines
+        "b24x512x8": I.CaseSpec(nx=24, ny=512, nz=8, bcx=1, bcy=0, beta=1.5, n_bubbles=2,
+                                radius_cells=3, config=26),
+        "b9x512x3": I.CaseSpec(nx=9, ny=512, nz=3, bcx=0, bcy=0, n_bubbles=1, radius_cells=2,
+                               config=27),
+        "b512x3x3_wy": I.CaseSpec(nx=512, ny=3, nz=3, bcx=0, bcy=1, n_bubbles=1, radius_cells=1,
+                                  config=28),
         # light drops in a heavy phase: rho0 = rho_l, split term from 1 - phi
         "b48x32x24_swapped": I.CaseSpec(nx=48, ny=32, nz=24, bcx=0, bcy=1, beta=1.5, n_bubbles=3,
                                         radius_cells=4, rho_l=1e-3, rho_g=1.0, config=19),
@@ -80,7 +89,8 @@ def test_fp64_matches_oracle(cuda_ok, name):
 
 @pytest.mark.parametrize("name", ["drop32", "b48x36x20_nx_stretch", "b96x64x33", "b27x18x12_ny",
                                   "b384x6x5", "b81x3x7_nn", "b48x32x24_swapped", "b512x8x5",
-                                  "b48x256x12", "b27x256x6_wx", "b256x12x10", "b256x9x5_wy"])
+                                  "b48x256x12", "b27x256x6_wx", "b256x12x10", "b256x9x5_wy",
+                                  "b6x512x4", "b24x512x8", "b9x512x3", "b512x3x3_wy"])
 def test_mixed_matches_oracle(cuda_ok, name):
     c = I.make_case(CASES[name])
     ref = O.project_case(c)
@@ -96,16 +106,17 @@ def test_mixed_matches_oracle(cuda_ok, name):
 
 
 @pytest.mark.parametrize("name", ["b48x256x12", "b27x256x6_wx", "b256x12x10", "b256x9x5_wy",
-                                  "b96x64x33"])
+                                  "b24x512x8", "b512x8x5", "b96x64x33"])
 def test_fp32_solve_accuracy(cuda_ok, name):
     """The FP32 solve alone (stopped at its first residual) is accurate to
-    FP32 level, whichever transform kernels it runs (both the Stockham and the
-    register-resident passes leave relres 4e-5 to 6e-5 at n = 256), and
-    at most two refinement sweeps then reach 1e-10."""
+    FP32 level, whichever transform kernels it runs: the Stockham and the
+    register-resident passes leave the same relres, 1e-6 to 6e-5 at n = 256
+    and up to 1.8e-4 at n = 512 with stretched z (24 x 512 x 8), and at most
+    two refinement sweeps then reach 1e-10."""
     c = I.make_case(CASES[name])
     got = gpu_project(c, F.MIXED, tol=1e-3, div_tol=1.0)
     st = got["stats"]
-    assert st["iterations"] == 0 and 0 < st["relres"] <= 1e-4, st
+    assert st["iterations"] == 0 and 0 < st["relres"] <= 3e-4, st
     st = gpu_project(c, F.MIXED)["stats"]
     assert st["converged"] == 1 and 1 <= st["iterations"] <= 2, st
 
