@@ -397,7 +397,10 @@ int fixed_len(int n, int bc) { return (bc == FIZZY_BC_PERIODIC && (n == 256 || n
 template <int NX, int NY> PassKernels kernels_for() {
     PassKernels k;
     k.xf64 = k_xfwd<double, XF_F64_DIVQ, NX>;
-    k.xf32d = k_xfwd<float, XF_MIX_DIVQ, NX>;
+    if constexpr (NX != 0)
+        k.xf32d = k_xfwd_r_divq<NX>;
+    else
+        k.xf32d = k_xfwd<float, XF_MIX_DIVQ, NX>;
     if constexpr (NX != 0)  // register-resident FP32 x-passes
         k.xf32l = k_xfwd_r_load<NX>;
     else
@@ -433,6 +436,7 @@ bool r16_kernel(const void *f) {
     const void *fs[] = {(const void *)k_ypass_r<false, 256>, (const void *)k_ypass_r<true, 256>,
                         (const void *)k_ypass_r<false, 512>, (const void *)k_ypass_r<true, 512>,
                         (const void *)k_xfwd_r_load<256>, (const void *)k_xfwd_r_load<512>,
+                        (const void *)k_xfwd_r_divq<256>, (const void *)k_xfwd_r_divq<512>,
                         (const void *)k_xinv_r<XI_STORE, 256>, (const void *)k_xinv_r<XI_ACCUM, 256>,
                         (const void *)k_xinv_r<XI_STORE, 512>, (const void *)k_xinv_r<XI_ACCUM, 512>};
     for (const void *x : fs)
@@ -455,12 +459,12 @@ void opt_in_smem(fizzy_proj_plan_t p, int bytes) {
         }
 }
 
-// sx32r: dynamic shared memory of the FP32 load/inverse x-passes (0 for the
+// sx32r: dynamic shared memory of the FP32 x-passes (0 for the
 // register-resident ones)
 void pass_caps(int *cap, const PassKernels &k, size_t sx64, size_t sx32, size_t sx32r, size_t sy64,
                size_t sy32) {
     cap[CAP_XF64] = resident_grid(k.xf64, 256, sx64);
-    cap[CAP_XF32D] = resident_grid(k.xf32d, 256, sx32);
+    cap[CAP_XF32D] = resident_grid(k.xf32d, 256, sx32r);
     cap[CAP_XF32L] = resident_grid(k.xf32l, 256, sx32r);
     cap[CAP_Y64F] = resident_grid(k.yf64, 256, sy64);
     cap[CAP_Y64I] = resident_grid(k.yi64, 256, sy64);
@@ -863,7 +867,8 @@ int fizzy_proj_solve(fizzy_proj_plan_t p, const double *phi, const double *p_n, 
     const int nlines = ny * nz;
     // tiles of each pass; each stand-alone launch runs min(tiles, resident grid)
     const int xtiles = (nlines + 2 * p->Lx - 1) / (2 * p->Lx);
-    // the FP32 load/inverse x-passes: 32 lines per tile when register-resident
+    // the FP32 x-passes: 32 (n = 256) or 16 (n = 512) lines per tile when
+    // register-resident
     const int xrt = p->x_r16 ? (nlines + r_tile_lines(nx) - 1) / r_tile_lines(nx) : xtiles;
     const size_t smx32r = p->x_r16 ? 0 : p->smem_x32;
     const int ygx = (nx + p->TXy - 1) / p->TXy, ytiles = ygx * nz;
@@ -909,7 +914,7 @@ int fizzy_proj_solve(fizzy_proj_plan_t p, const double *phi, const double *p_n, 
         xa.out = p->fhat32;
         xa.f_out = p->f;
         const int *conv = &p->st->converged;
-        TIMED(KS_XFWD, (p->kern.xf32d<<<grid(xtiles, CAP_XF32D), 256, p->smem_x32, s>>>(g, p->fx.d32, p->Lx, xa, xtiles)));
+        TIMED(KS_XFWD, (p->kern.xf32d<<<grid(xrt, CAP_XF32D), 256, smx32r, s>>>(g, p->fx.d32, p->Lx, xa, xrt)));
         TIMED(KS_YFWD, (p->kern.yf32<<<grid(ytiles, CAP_Y32F), 256, p->smem_y32, s>>>(nx, ny, p->fy.d32, p->TXy, p->fhat32, nullptr, ygx, ytiles)));
         TIMED(KS_THOMAS, (k_thomas<float><<<grid(ttiles, CAP_TH32), THOMAS_BLOCK, thomas_smem<float>(), s>>>(g, p->Ux, p->Uy, p->mtab32, p->ibtab32, p->cup32, p->fhat32, nullptr, ttiles)));
         TIMED(KS_YINV, (p->kern.yi32<<<grid(ytiles, CAP_Y32I), 256, p->smem_y32, s>>>(nx, ny, p->fy.d32, p->TXy, p->fhat32, nullptr, ygx, ytiles)));

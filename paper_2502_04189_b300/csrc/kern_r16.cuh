@@ -353,6 +353,66 @@ __global__ void __launch_bounds__(256, 4) k_xfwd_r_load(GridDev g, FFTDesc D, in
     }
 }
 
+// The first x-pass of the mixed solve (the mode XF_MIX_DIVQ of k_xfwd):
+// f = rho0 D(q') in FP64 (stored, and max|f| recorded), then the forward
+// transform of its FP32 image sigma f.  f is formed row by row (lane = x mod
+// 32, coalesced) into the line's region of shared memory, from which the
+// threads of the line take their inputs.
+template <int N>
+__global__ void __launch_bounds__(256, 4) k_xfwd_r_divq(GridDev g, FFTDesc D, int L, XArgs a,
+                                                        int ntiles) {
+    (void)D;
+    (void)L;
+    __shared__ R16Smem sm;
+    r16_tables<false>(sm);
+    __syncthreads();
+    const RPos<N> q;
+    const int nlines = g.ny * g.nz, lane = threadIdx.x & 31;
+    constexpr int LS = RShape<N>::LS;
+    const int l0 = N == 256 ? (q.ln & ~1) : q.ln;  // the warp's first line
+    constexpr int WROWS = N == 256 ? 4 : 2;         // real rows of the warp
+    const float scale32 = (float)g.sigma;
+    float *out = (float *)a.out;
+    float2 *X = sm.x + q.ln * LS;
+    unsigned long long mx = 0ull;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+#pragma unroll 1
+        for (int r = 0; r < WROWS; ++r) {
+            const int row = tile * r_tile_lines(N) + 2 * l0 + r;
+            float *dr = (float *)(sm.x + (l0 + (r >> 1)) * LS) + (r & 1);
+            if (row < nlines) {
+                const int k = fdiv(row, g.ny, g.rny), j = row - k * g.ny;
+                const double cz = g.dvz[k];
+#pragma unroll 4
+                for (int i = 0; i < N / 32; ++i) {
+                    const int x = lane + 32 * i;
+                    const double f = div_q<false>(g, x, j, k, g.dvx, g.dvy, cz, a.qx, a.qy, a.qz);
+                    a.f_out[(size_t)row * N + x] = f;
+                    mx = umax64(mx, absbits(f));
+                    dr[2 * x] = f64_to_f32_shift(f, 0) * scale32;
+                }
+            } else {
+                for (int i = 0; i < N / 32; ++i) dr[2 * (lane + 32 * i)] = 0.f;
+            }
+        }
+        __syncwarp();
+        float2 v[16];
+#pragma unroll
+        for (int n1 = 0; n1 < 16; ++n1) v[n1] = X[q.in_index(n1)];
+        __syncwarp();  // the line's region is the exchange buffer next
+        r_fft<false, N>(sm, X, q, v);
+        const int ra = tile * r_tile_lines(N) + 2 * q.ln;
+        const bool oka = ra < nlines, okb = ra + 1 < nlines;
+        float *la = out + (size_t)ra * N, *lb = la + N;
+        r_separate<N>(v, q, [&](int kk, float va, float vb) {
+            if (oka) la[kk] = va;
+            if (okb) lb[kk] = vb;
+        });
+        __syncwarp();  // the region is rewritten by the next tile
+    }
+    block_max_atomic(mx, &a.st->fmax_bits);
+}
+
 // Inverse x-pass to p (FP64): XI_STORE p = the FP32 solution, XI_ACCUM
 // p += delta 2^e (e: exponent of max|f|); the modes of k_xinv.
 template <int MODE, int N>
