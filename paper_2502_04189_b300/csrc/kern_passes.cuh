@@ -277,19 +277,33 @@ __global__ void k_sum_partials(const double *__restrict__ part, int n, double *_
 }
 
 // rho0-weighted divergence of q' at one cell; cx, cy, cz are rho0/(dt h) (maybe scaled).
+// (split into its loads and its arithmetic, so that a pass can issue the
+// loads of several cells before their arithmetic)
+struct QFaces {
+    double qe, qw, qn, qs, qt, qb;
+};
+template <bool CG>
+__device__ __forceinline__ QFaces div_q_ld(const GridDev &g, int i, int j, int k, const double *qx,
+                                           const double *qy, const double *qz) {
+    const size_t c = cidx(g, i, j, k);
+    QFaces q;
+    q.qe = ldp<CG>(qx + c);
+    q.qw = (i > 0) ? ldp<CG>(qx + c - 1) : (g.bcx == BC_PERIODIC ? ldp<CG>(qx + c + g.nx - 1) : 0.0);
+    q.qn = ldp<CG>(qy + c);
+    q.qs = (j > 0) ? ldp<CG>(qy + c - g.nx)
+                   : (g.bcy == BC_PERIODIC ? ldp<CG>(qy + c + (size_t)(g.ny - 1) * g.nx) : 0.0);
+    q.qt = ldp<CG>(qz + c);
+    q.qb = (k > 0) ? ldp<CG>(qz + c - (size_t)g.nx * g.ny) : 0.0;
+    return q;
+}
+__device__ __forceinline__ double div_q_eval(const QFaces &q, double cx, double cy, double cz) {
+    return fmaT(cx, q.qe - q.qw, fmaT(cy, q.qn - q.qs, mulT(cz, q.qt - q.qb)));
+}
 template <bool CG>
 __device__ __forceinline__ double div_q(const GridDev &g, int i, int j, int k, double cx, double cy,
                                         double cz, const double *qx, const double *qy,
                                         const double *qz) {
-    const size_t c = cidx(g, i, j, k);
-    const double qe = ldp<CG>(qx + c);
-    const double qw = (i > 0) ? ldp<CG>(qx + c - 1) : (g.bcx == BC_PERIODIC ? ldp<CG>(qx + c + g.nx - 1) : 0.0);
-    const double qn = ldp<CG>(qy + c);
-    const double qs = (j > 0) ? ldp<CG>(qy + c - g.nx)
-                              : (g.bcy == BC_PERIODIC ? ldp<CG>(qy + c + (size_t)(g.ny - 1) * g.nx) : 0.0);
-    const double qt = ldp<CG>(qz + c);
-    const double qb = (k > 0) ? ldp<CG>(qz + c - (size_t)g.nx * g.ny) : 0.0;
-    return fmaT(cx, qe - qw, fmaT(cy, qn - qs, mulT(cz, qt - qb)));
+    return div_q_eval(div_q_ld<CG>(g, i, j, k, qx, qy, qz), cx, cy, cz);
 }
 
 // L_h p at one cell in flux (difference) form: each face difference is
@@ -347,6 +361,7 @@ constexpr int y_tile_cols(int n, bool fp32 = false) {
 }
 
 constexpr int PASS_U = 4;   // global loads per thread issued together in the pass load loops
+constexpr int XDIV_U = 2;   // cells per thread whose six face loads the divergence issues together
 constexpr int PASS_UC = 2;  // spectral pairs per thread loaded together before the inverse combine
 
 // The transform of a pass: length-specialised when NF != 0 (NF = the length
@@ -397,25 +412,45 @@ __device__ __forceinline__ void xfwd_body(const GridDev &g, const FFTDesc &D, in
                 if (idx < total) ((T *)(A + (r >> 1) * ls))[2 * line_pos(i, n, kind) + (r & 1)] = v[u];
             }
         }
-    } else
-    for (int idx = threadIdx.x; idx < 2 * L * n; idx += blockDim.x) {
-        const int r = (FX ? idx / NF : fdiv(idx, n, D.rn)), i = idx - r * n;
-        const int line = line0 + r;
-        T val = (T)0;
-        if (line < nlines) {
-            const int k = fdiv(line, g.ny, g.rny), j = line - k * g.ny;
-            if (MODE == XF_F64_DIVQ) {
-                const double f = div_q<CG>(g, i, j, k, g.dvx_s, g.dvy_s, g.dvz_s[k], a.qx, a.qy, a.qz);
-                if (a.track_fmax) mx = umax64(mx, absbits(f));
-                val = (T)f;
-            } else {
-                const double f = div_q<CG>(g, i, j, k, g.dvx, g.dvy, g.dvz[k], a.qx, a.qy, a.qz);
-                a.f_out[cidx(g, i, j, k)] = f;
-                mx = umax64(mx, absbits(f));
-                val = (T)(f64_to_f32_shift(f, 0) * scale32);
+    } else {  // the divergence: the face loads of UD cells per thread issued together
+        // (one in the persistent batch kernel, whose 48 registers it would spill)
+        constexpr int UD = CG ? 1 : XDIV_U;
+        const int total = 2 * L * n;
+        for (int base = threadIdx.x; base < total; base += UD * blockDim.x) {
+            QFaces qf[UD];
+#pragma unroll
+            for (int u = 0; u < UD; ++u) {
+                const int idx = base + u * blockDim.x;
+                const int r = (FX ? idx / NF : fdiv(idx, n, D.rn)), i = idx - r * n;
+                const int line = line0 + r;
+                if (idx < total && line < nlines) {
+                    const int k = fdiv(line, g.ny, g.rny), j = line - k * g.ny;
+                    qf[u] = div_q_ld<CG>(g, i, j, k, a.qx, a.qy, a.qz);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < UD; ++u) {
+                const int idx = base + u * blockDim.x;
+                if (idx >= total) break;
+                const int r = (FX ? idx / NF : fdiv(idx, n, D.rn)), i = idx - r * n;
+                const int line = line0 + r;
+                T val = (T)0;
+                if (line < nlines) {
+                    const int k = fdiv(line, g.ny, g.rny);
+                    if (MODE == XF_F64_DIVQ) {
+                        const double f = div_q_eval(qf[u], g.dvx_s, g.dvy_s, g.dvz_s[k]);
+                        if (a.track_fmax) mx = umax64(mx, absbits(f));
+                        val = (T)f;
+                    } else {
+                        const double f = div_q_eval(qf[u], g.dvx, g.dvy, g.dvz[k]);
+                        a.f_out[(size_t)line * n + i] = f;
+                        mx = umax64(mx, absbits(f));
+                        val = (T)(f64_to_f32_shift(f, 0) * scale32);
+                    }
+                }
+                ((T *)(A + (r >> 1) * ls))[2 * line_pos(i, n, kind) + (r & 1)] = val;
             }
         }
-        ((T *)(A + (r >> 1) * ls))[2 * line_pos(i, n, kind) + (r & 1)] = val;
     }
     if (MODE == XF_MIX_DIVQ) block_max_atomic(mx, &a.st->fmax_bits);
     if (MODE == XF_F64_DIVQ && a.track_fmax) block_max_atomic(mx, &a.st->fmax_bits);
