@@ -103,6 +103,35 @@ def fft_fp64_instr_per_point(n, dct):
     return per_complex / 2 + 1 + (2 if dct else 0)
 
 
+def path_roofline(value, nx, ny, bcx, bcy, mixed, sweeps, hbm_peak):
+    """The whole projection against its bounds: the algorithmic bytes of the
+    pass sequence (the kernels' per-point bytes summed over the passes that
+    ran; mixed: the refinement passes once per sweep, the stand-alone
+    correction only when no sweep ran), the I/O floor (6 FP64 fields read,
+    4 written: 80 B/pt), and the FP64 instructions per point against the
+    nominal 0.625 T FP64 instructions/s."""
+    per = algorithmic_per_point(nx, ny, mixed)
+    ins = fp64_instr_per_point(nx, ny, bcx, bcy, mixed)
+    if not mixed:
+        b = sum(v[0] for v in per.values())
+        n_ins = sum(ins.values())
+    else:
+        once = ("flux", "div_fwdx", "fwd_y", "thomas", "inv_y", "inv_x", "resid")
+        sweep = ("fwd_x_refine", "fwd_y_refine", "thomas_refine", "inv_y_refine", "inv_x_update",
+                 "resid_correct")
+        b = sum(per[k][0] for k in once) + sweeps * sum(per[k][0] for k in sweep)
+        n_ins = ins["flux"] + ins["div_fwdx"] + ins["resid"] + sweeps * (ins["inv_x_update"] +
+                                                                       ins["resid_correct"])
+        if sweeps == 0:
+            b += per["correct"][0]
+            n_ins += ins["correct"]
+    issue_peak = FP64_PEAK_NOMINAL / 2 * 1e12
+    return {"bytes_per_pt": b, "io_floor_bytes_per_pt": 80, "hbm_gbs": value * b / 1e9,
+            "hbm_frac": value * b / 1e9 / hbm_peak, "io_floor_frac": value * 80 / 1e9 / hbm_peak,
+            "fp64_instr_per_pt": n_ins, "fp64_issue_bound_pts_s": issue_peak / n_ins,
+            "fp64_issue_frac": value * n_ins / issue_peak, "sweeps": sweeps}
+
+
 def fp64_instr_per_point(nx, ny, bcx, bcy, mixed):
     """FP64 instructions per grid point of each kernel, counted from the code
     (flux 6 per face + phat; divergence 6; z-solve 3; correction 6; mixed
@@ -425,7 +454,10 @@ def run_fizzy(args):
                            "precision": args.precision, "bc": "periodic x,y; walls z",
                            "l2": "inputs (6 x %d MiB) larger than L2" % (npts * 8 >> 20),
                            "parallelism": "replicas" if world > 1 else "single"},
-                "gpu_launches": launches, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": launches, "roofline": roof,
+                "path_roofline": path_roofline(value, spec.nx, spec.ny, spec.bcx, spec.bcy,
+                                               prec == F.MIXED, int(st["iterations"]), hbm_peak),
+                "cpu_baseline": cpu, "e2e": e2e,
                 "clocks": clk, "kernels": kernels,
                 "stats": {k: st[k] for k in ("iterations", "converged", "relres")},
                 ("mixed" if other == F.MIXED else "fp64"): {
