@@ -138,17 +138,11 @@ __device__ __forceinline__ void r16_tables(R16Smem &sm) {
     sm.tw2[threadIdx.x] = make_float2(c, INV ? -s : s);
 }
 
-template <bool WARP>
-__device__ __forceinline__ void r16_sync() {
-    if (WARP) __syncwarp();
-    else __syncthreads();
-}
-
 // Steps 1-3 of the four-step DFT on the 256 values at X: thread t holds
 // v[n1] = x[16 n1 + t] and ends with v[k2] = X[t + 16 k2].  X is overwritten;
-// its threads must have finished reading X before the call (barriers inside,
-// the last one after the exchange reads).  WARP: X belongs to one warp.
-template <bool INV, bool WARP>
+// its threads (all in one warp) must have finished reading X before the call
+// (warp barriers inside, the last one after the exchange reads).
+template <bool INV>
 __device__ __forceinline__ void r16_fft(const R16Smem &sm, float2 *X, int t, float2 (&v)[16]) {
     dft16<INV>(v);
 #pragma unroll
@@ -158,10 +152,10 @@ __device__ __forceinline__ void r16_fft(const R16Smem &sm, float2 *X, int t, flo
     }
 #pragma unroll
     for (int k1 = 0; k1 < 16; ++k1) X[k1 * 16 + (t ^ k1)] = v[k1];  // conflict-free both ways
-    r16_sync<WARP>();
+    __syncwarp();
 #pragma unroll
     for (int n2 = 0; n2 < 16; ++n2) v[n2] = X[t * 16 + (n2 ^ t)];
-    r16_sync<WARP>();
+    __syncwarp();
     dft16<INV>(v);
 }
 
@@ -201,7 +195,7 @@ __device__ __forceinline__ void r_fft(const R16Smem &sm, float2 *X, const RPos<N
             }
         }
     }
-    r16_fft<INV, true>(sm, X + 256 * q.h, q.t, v);
+    r16_fft<INV>(sm, X + 256 * q.h, q.t, v);
 }
 
 // Separation of the forward transform of a packed line (two real lines as
