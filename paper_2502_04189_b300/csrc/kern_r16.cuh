@@ -2,15 +2,14 @@
 //
 // The FP32 transform passes of the mixed-precision solve (Sec. 3.2: real
 // FFTs along the periodic directions) for n = 256 and 512.  The DFT of length
-// 256 is split as 16 x 16 (the
-// four-step form of the Cooley-Tukey factorisation): with n = 16 n1 + n2 and
-// k = k1 + 16 k2,
+// 256 is split as 16 x 16 (the four-step form of the Cooley-Tukey
+// factorisation): with n = 16 n1 + n2 and k = k1 + 16 k2,
 //     X[k1 + 16 k2] = sum_n2 W16^(n2 k2) [ W256^(n2 k1) sum_n1 x[16 n1 + n2] W16^(n1 k1) ],
 // W_N = exp(-2 pi i / N) (the inverse uses the conjugates; neither direction
 // is scaled).  A complex line (two real columns, real and imaginary part) is
 // held by 16 threads: thread t first owns the samples x[16 n1 + t],
-// computes their 16-point DFT in
-// registers and applies the twiddles W256^(t k1); one pass through shared
+// computes their 16-point DFT in registers and applies the twiddles
+// W256^(t k1); one pass through shared
 // memory then hands thread t the values of k1 = t, whose 16-point DFT gives
 // X[t + 16 k2].  The separation of the two real spectra (forward) pairs X[k]
 // with X[256 - k], held by thread (16 - t) mod 16 of the same line, through
@@ -32,7 +31,6 @@
 #include "kern_passes.cuh"
 
 namespace fz {
-
 
 __device__ __forceinline__ float2 c_add(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ float2 c_sub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
