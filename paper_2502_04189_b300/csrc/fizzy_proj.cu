@@ -78,7 +78,7 @@ struct fizzy_proj_plan_s {
     int host_calls = 0;
     // launch shapes
     int Lx = 1, TXy = 2;
-    int x_r16 = 0;  // mixed, periodic nx = 256 or 512: register-resident FP32 x-passes
+    int x_r16 = 0;  // mixed, nx = 256 or 512: register-resident FP32 x-passes
     size_t smem_x64 = 0, smem_x32 = 0, smem_y64 = 0, smem_y32 = 0;
     int cap[24] = {0};  // resident-grid size of each pass kernel (CAP_*)
     PassKernels kern;   // the pass kernels this plan launches
@@ -397,31 +397,15 @@ int fixed_len(int n, int bc) { return (bc == FIZZY_BC_PERIODIC && (n == 256 || n
 template <int NX, int NY> PassKernels kernels_for() {
     PassKernels k;
     k.xf64 = k_xfwd<double, XF_F64_DIVQ, NX>;
-    if constexpr (NX != 0)
-        k.xf32d = k_xfwd_r_divq<NX>;
-    else
-        k.xf32d = k_xfwd<float, XF_MIX_DIVQ, NX>;
-    if constexpr (NX != 0)  // register-resident FP32 x-passes
-        k.xf32l = k_xfwd_r_load<NX>;
-    else
-        k.xf32l = k_xfwd<float, XF_MIX_LOAD, NX>;
+    k.xf32d = k_xfwd<float, XF_MIX_DIVQ, NX>;
+    k.xf32l = k_xfwd<float, XF_MIX_LOAD, NX>;
     k.yf64 = k_ypass<double, false, NY>;
     k.yi64 = k_ypass<double, true, NY>;
-    if constexpr (NY != 0) {  // register-resident FP32 y-passes
-        k.yf32 = k_ypass_r<false, NY>;
-        k.yi32 = k_ypass_r<true, NY>;
-    } else {
-        k.yf32 = k_ypass<float, false, NY>;
-        k.yi32 = k_ypass<float, true, NY>;
-    }
+    k.yf32 = k_ypass<float, false, NY>;
+    k.yi32 = k_ypass<float, true, NY>;
     k.xi64 = k_xinv<double, XI_STORE, NX>;
-    if constexpr (NX != 0) {
-        k.xi32s = k_xinv_r<XI_STORE, NX>;
-        k.xi32a = k_xinv_r<XI_ACCUM, NX>;
-    } else {
-        k.xi32s = k_xinv<float, XI_STORE, NX>;
-        k.xi32a = k_xinv<float, XI_ACCUM, NX>;
-    }
+    k.xi32s = k_xinv<float, XI_STORE, NX>;
+    k.xi32a = k_xinv<float, XI_ACCUM, NX>;
     return k;
 }
 template <int NX> PassKernels kernels_for_y(int fy) {
@@ -431,17 +415,28 @@ PassKernels pick_kernels(int fx, int fy) {
     return fx == 256 ? kernels_for_y<256>(fy) : fx == 512 ? kernels_for_y<512>(fy) : kernels_for_y<0>(fy);
 }
 
-// The register-resident passes: static shared memory only (no opt-in).
-bool r16_kernel(const void *f) {
-    const void *fs[] = {(const void *)k_ypass_r<false, 256>, (const void *)k_ypass_r<true, 256>,
-                        (const void *)k_ypass_r<false, 512>, (const void *)k_ypass_r<true, 512>,
-                        (const void *)k_xfwd_r_load<256>, (const void *)k_xfwd_r_load<512>,
-                        (const void *)k_xfwd_r_divq<256>, (const void *)k_xfwd_r_divq<512>,
-                        (const void *)k_xinv_r<XI_STORE, 256>, (const void *)k_xinv_r<XI_ACCUM, 256>,
-                        (const void *)k_xinv_r<XI_STORE, 512>, (const void *)k_xinv_r<XI_ACCUM, 512>};
-    for (const void *x : fs)
-        if (f == x) return true;
-    return false;
+// The length of a direction that has register-resident FP32 passes (any
+// boundary; 0: none).
+int r_len(int n) { return (n == 256 || n == 512) ? n : 0; }
+
+// Mixed plans: the register-resident FP32 passes (static shared memory, no
+// opt-in) replace the Stockham ones along a direction of length 256 or 512.
+template <int N, int KIND> void r_kernels_x(PassKernels &k) {
+    k.xf32d = k_xfwd_r_divq<N, KIND>;
+    k.xf32l = k_xfwd_r_load<N, KIND>;
+    k.xi32s = k_xinv_r<XI_STORE, N, KIND>;
+    k.xi32a = k_xinv_r<XI_ACCUM, N, KIND>;
+}
+template <int N, int KIND> void r_kernels_y(PassKernels &k) {
+    k.yf32 = k_ypass_r<false, N, KIND>;
+    k.yi32 = k_ypass_r<true, N, KIND>;
+}
+void pick_r_kernels(PassKernels &k, int nx, int bcx, int ny, int bcy) {
+    const bool dx = bcx == FIZZY_BC_NEUMANN, dy = bcy == FIZZY_BC_NEUMANN;
+    if (nx == 256) dx ? r_kernels_x<256, KIND_DCT>(k) : r_kernels_x<256, KIND_PERIODIC>(k);
+    if (nx == 512) dx ? r_kernels_x<512, KIND_DCT>(k) : r_kernels_x<512, KIND_PERIODIC>(k);
+    if (ny == 256) dy ? r_kernels_y<256, KIND_DCT>(k) : r_kernels_y<256, KIND_PERIODIC>(k);
+    if (ny == 512) dy ? r_kernels_y<512, KIND_DCT>(k) : r_kernels_y<512, KIND_PERIODIC>(k);
 }
 
 // Opt every pass kernel instance into large dynamic shared memory.
@@ -454,8 +449,7 @@ void opt_in_smem(fizzy_proj_plan_t p, int bytes) {
                                  (const void *)k.yi32, (const void *)k.xi64, (const void *)k.xi32s,
                                  (const void *)k.xi32a};
             for (const void *f : fns)
-                if (!r16_kernel(f))
-                    note(p, cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+                note(p, cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
         }
 }
 
@@ -695,10 +689,10 @@ int fizzy_proj_plan(fizzy_proj_plan_t *out, const fizzy_proj_desc *d, void *stre
 
     // ---- launch shapes and shared-memory opt-in
     p->Lx = x_lines_per_cta(nx);
-    // mixed plans with a periodic direction of length 256 or 512 run the
-    // register-resident FP32 passes along it: static shared memory only
-    const bool y_r16 = p->mixed && fixed_len(ny, d->bc_y) != 0;
-    p->x_r16 = p->mixed && fixed_len(nx, d->bc_x) != 0;
+    // mixed plans with a direction of length 256 or 512 (periodic or walls)
+    // run the register-resident FP32 passes along it: static shared memory only
+    const bool y_r16 = p->mixed && r_len(ny) != 0;
+    p->x_r16 = p->mixed && r_len(nx) != 0;
     p->TXy = y_r16 ? r_tile_cols(ny) : y_tile_cols(ny, p->mixed != 0);
     p->smem_x64 = pass_smem<double>(nx, p->Lx);
     p->smem_x32 = pass_smem<float>(nx, p->Lx);
@@ -716,6 +710,7 @@ int fizzy_proj_plan(fizzy_proj_plan_t *out, const fizzy_proj_desc *d, void *stre
         }
     }
     p->kern = pick_kernels(fixed_len(nx, d->bc_x), fixed_len(ny, d->bc_y));
+    if (p->mixed) pick_r_kernels(p->kern, nx, d->bc_x, ny, d->bc_y);
     pass_caps(p->cap, p->kern, p->smem_x64, p->smem_x32, p->x_r16 ? 0 : p->smem_x32, p->smem_y64,
               p->smem_y32);
     // stream-ordered plans are ready for work queued after them on their

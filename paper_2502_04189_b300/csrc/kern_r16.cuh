@@ -119,14 +119,16 @@ constexpr int r_tile_lines(int n) { return n == 256 ? 2 * RShape<256>::LINES : 2
 
 // Shared memory of one CTA: its lines (16 x 257 >= 8 x 513 complex values),
 // reused for the 16 x 16 exchanges; the twiddles W256^(n2 k1) at [k1][n2]
-// and W512^n (n < 256), conjugated for the inverse.
+// and W512^n (n < 256), conjugated for the inverse; for a DCT direction the
+// post-twiddles (cos, sin)(pi m / (2n)), m < n/2.
 struct R16Smem {
     float2 x[16 * 257];
     float2 tw[256];
     float2 tw2[256];
+    float2 cs[256];
 };
 
-template <bool INV>
+template <bool INV, int N, int KIND>
 __device__ __forceinline__ void r16_tables(R16Smem &sm) {
     const int n2 = threadIdx.x & 15, k1 = threadIdx.x >> 4;
     float s, c;
@@ -134,7 +136,22 @@ __device__ __forceinline__ void r16_tables(R16Smem &sm) {
     sm.tw[threadIdx.x] = make_float2(c, INV ? -s : s);
     sincospif(-(float)threadIdx.x / 256.f, &s, &c);
     sm.tw2[threadIdx.x] = make_float2(c, INV ? -s : s);
+    if (KIND == KIND_DCT && threadIdx.x < N / 2) {
+        sincospif((float)threadIdx.x / (float)(2 * N), &s, &c);
+        sm.cs[threadIdx.x] = make_float2(c, s);
+    }
 }
+
+// The sample held at position p of a packed line: p itself (periodic), or,
+// for the DCT, the even samples forward then the odd ones backward
+// (2p for p < n/2, 2(n - 1 - p) + 1 above), the reordering of Makhoul's
+// DCT-II through one complex FFT.
+template <int N, int KIND>
+__device__ __forceinline__ int r_src(int p) {
+    if (KIND == KIND_PERIODIC) return p;
+    return p < N / 2 ? 2 * p : 2 * (N - 1 - p) + 1;
+}
+constexpr float R_SQRT2 = 1.41421356237309504880f;  // the n/2 term of the DCT (2 cos(pi/4))
 
 // Steps 1-3 of the four-step DFT on the 256 values at X: thread t holds
 // v[n1] = x[16 n1 + t] and ends with v[k2] = X[t + 16 k2].  X is overwritten;
@@ -197,13 +214,16 @@ __device__ __forceinline__ void r_fft(const R16Smem &sm, float2 *X, const RPos<N
 }
 
 // Separation of the forward transform of a packed line (two real lines as
-// real and imaginary part): the half-complex spectra, scaled by 2 (the
-// convention of the Stockham passes), through fn(k, a_k, b_k).  X[K] pairs
-// with X[N - K]: at 256 the partner's register 15 - k2 of thread
-// (16 - t) mod 16, or this thread's register (16 - k2) mod 16 (t = 0); at 512
-// the odd outputs pair within group 1 with thread 15 - t, register 15 - k2.
-template <int N, typename F>
-__device__ __forceinline__ void r_separate(const float2 (&v)[16], const RPos<N> &q, F &&fn) {
+// real and imaginary part): the spectra of both, scaled by 2 (the
+// conventions of the Stockham passes: half-complex for a periodic direction,
+// DCT-II coefficients through the post-twiddle (c, s)_m for a wall), through
+// fn(k, a_k, b_k).  X[K] pairs with X[N - K]: at 256 the partner's register
+// 15 - k2 of thread (16 - t) mod 16, or this thread's register (16 - k2)
+// mod 16 (t = 0); at 512 the odd outputs pair within group 1 with thread
+// 15 - t, register 15 - k2.
+template <int N, int KIND, typename F>
+__device__ __forceinline__ void r_separate(const float2 (&v)[16], const RPos<N> &q,
+                                           const R16Smem &sm, F &&fn) {
     const int lane = threadIdx.x & 31;
     const int src = (N == 256 || q.h == 0) ? ((lane & 16) | ((16 - q.t) & 15)) : (16 | (15 - q.t));
     const bool self = q.h == 0 && q.t == 0;
@@ -214,23 +234,53 @@ __device__ __forceinline__ void r_separate(const float2 (&v)[16], const RPos<N> 
         const float2 z = v[k2];
         const float2 y = self ? v[(16 - k2) & 15] : make_float2(qx, qy);
         const int k = q.out_index(k2);
-        // k <= n/2: (Re A_k, Re B_k) x 2; k > n/2: (Im A_m, Im B_m) x 2, m = n - k
-        if (k <= N / 2) fn(k, z.x + y.x, z.y + y.y);
-        else fn(k, y.y - z.y, z.x - y.x);
+        if (KIND == KIND_PERIODIC) {
+            // k <= n/2: (Re A_k, Re B_k) x 2; k > n/2: (Im A_m, Im B_m) x 2, m = n - k
+            if (k <= N / 2) fn(k, z.x + y.x, z.y + y.y);
+            else fn(k, y.y - z.y, z.x - y.x);
+        } else if (k == 0) {
+            fn(k, z.x + y.x, z.y + y.y);
+        } else if (k == N / 2) {
+            fn(k, R_SQRT2 * z.x, R_SQRT2 * z.y);
+        } else if (k < N / 2) {  // 2 V_k = (var + i vai, vbr + i vbi); X_k = Re(w V_k)
+            const float2 w = sm.cs[k];
+            const float var = z.x + y.x, vai = z.y - y.y, vbr = z.y + y.y, vbi = y.x - z.x;
+            fn(k, fmaf(w.x, var, w.y * vai), fmaf(w.x, vbr, w.y * vbi));
+        } else {  // X_(n-m) = -Im(w V_m), m = n - k (Z_m is the partner's value)
+            const float2 w = sm.cs[N - k];
+            const float var = y.x + z.x, vai = y.y - z.y, vbr = y.y + z.y, vbi = z.x - y.x;
+            fn(k, fmaf(w.y, var, -w.x * vai), fmaf(w.y, vbr, -w.x * vbi));
+        }
     }
 }
 
 // Combination ahead of the inverse transform: v[n1] = Z[in_index(n1)] from
-// the half-complex spectra read through get(k) = (a_k, b_k).
-template <int N, typename G>
-__device__ __forceinline__ void r_combine(float2 (&v)[16], const RPos<N> &q, G &&get) {
+// the spectra of the two real lines read through get(k) = (a_k, b_k)
+// (half-complex, or DCT-II coefficients pre-twiddled by (c, s)_m).
+template <int N, int KIND, typename G>
+__device__ __forceinline__ void r_combine(float2 (&v)[16], const RPos<N> &q, const R16Smem &sm,
+                                          G &&get) {
 #pragma unroll
     for (int n1 = 0; n1 < 16; ++n1) {
         const int k = q.in_index(n1);
         const float2 o = get(k), p = get((N - k) & (N - 1));  // indices k and n - k
-        if (k == 0 || k == N / 2) v[n1] = o;
-        else if (k < N / 2) v[n1] = make_float2(o.x - p.y, p.x + o.y);
-        else v[n1] = make_float2(p.x + o.y, p.y - o.x);
+        if (KIND == KIND_PERIODIC) {
+            if (k == 0 || k == N / 2) v[n1] = o;
+            else if (k < N / 2) v[n1] = make_float2(o.x - p.y, p.x + o.y);
+            else v[n1] = make_float2(p.x + o.y, p.y - o.x);
+        } else if (k == 0) {
+            v[n1] = o;
+        } else if (k == N / 2) {
+            v[n1] = make_float2(R_SQRT2 * o.x, R_SQRT2 * o.y);
+        } else {
+            // m = min(k, n - k); V_m = (c + i s)(X_m - i X_(n-m)) for each line
+            const bool lo = k < N / 2;
+            const float2 w = sm.cs[lo ? k : N - k];
+            const float2 xm = lo ? o : p, xn = lo ? p : o;  // (a, b) at m and at n - m
+            const float ar = fmaf(w.x, xm.x, w.y * xn.x), ai = fmaf(w.y, xm.x, -w.x * xn.x);
+            const float br = fmaf(w.x, xm.y, w.y * xn.y), bi = fmaf(w.y, xm.y, -w.x * xn.y);
+            v[n1] = lo ? make_float2(ar - bi, ai + br) : make_float2(ar + bi, br - ai);
+        }
     }
 }
 
@@ -238,9 +288,10 @@ __device__ __forceinline__ void r_combine(float2 (&v)[16], const RPos<N> &q, G &
 // (nz, N, nx) FP32 array, transformed along y in place.  Rows move between
 // global and shared memory a warp at a time (32 columns of one row at 256,
 // 16 columns of two rows at 512); column 2l + e of the tile is component e
-// of complex line l.  Forward: real columns -> half-complex spectra scaled
-// by 2; inverse: the reverse, unscaled.
-template <bool INV, int N>
+// of complex line l.  Forward: real columns -> spectra scaled by 2
+// (half-complex, or DCT-II for a wall direction); inverse: the reverse,
+// unscaled.
+template <bool INV, int N, int KIND>
 __device__ __forceinline__ void ypass_r_tile(int nx, float *data, int bx, int kplane, R16Smem &sm) {
     constexpr int TX = RShape<N>::TX, LS = RShape<N>::LS;
     constexpr int RPW = 32 / TX;  // rows per warp access
@@ -265,17 +316,17 @@ __device__ __forceinline__ void ypass_r_tile(int nx, float *data, int bx, int kp
     float2 v[16];
     if (!INV) {
 #pragma unroll
-        for (int n1 = 0; n1 < 16; ++n1) v[n1] = X[q.in_index(n1)];
+        for (int n1 = 0; n1 < 16; ++n1) v[n1] = X[r_src<N, KIND>(q.in_index(n1))];
     } else {
-        r_combine<N>(v, q, [&](int k) { return X[k]; });
+        r_combine<N, KIND>(v, q, sm, [&](int k) { return X[k]; });
     }
     __syncwarp();  // the line's region is the exchange buffer next
     r_fft<INV, N>(sm, X, q, v);
     if (!INV) {
-        r_separate<N>(v, q, [&](int k, float a, float b) { X[k] = make_float2(a, b); });
+        r_separate<N, KIND>(v, q, sm, [&](int k, float a, float b) { X[k] = make_float2(a, b); });
     } else {
 #pragma unroll
-        for (int k2 = 0; k2 < 16; ++k2) X[q.out_index(k2)] = v[k2];
+        for (int k2 = 0; k2 < 16; ++k2) X[r_src<N, KIND>(q.out_index(k2))] = v[k2];
     }
     __syncthreads();
     // 2. write the tile back
@@ -290,7 +341,7 @@ __device__ __forceinline__ void ypass_r_tile(int nx, float *data, int bx, int kp
 // y-pass over ntiles = ygx x nz tiles (ygx = ceil(nx / TX)); the signature of
 // k_ypass, so the plan can launch either.  conv: return at once when the
 // refinement has converged.
-template <bool INV, int N>
+template <bool INV, int N, int KIND>
 __global__ void __launch_bounds__(256, 4) k_ypass_r(int nx, int ny, FFTDesc D, int TX, float *data,
                                                     const int *conv, int ygx, int ntiles) {
     (void)ny;
@@ -298,11 +349,11 @@ __global__ void __launch_bounds__(256, 4) k_ypass_r(int nx, int ny, FFTDesc D, i
     (void)TX;
     __shared__ R16Smem sm;
     if (conv && *(volatile const int *)conv) return;
-    r16_tables<INV>(sm);
+    r16_tables<INV, N, KIND>(sm);
     __syncthreads();
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const int kplane = tile / ygx;
-        ypass_r_tile<INV, N>(nx, data, tile - kplane * ygx, kplane, sm);
+        ypass_r_tile<INV, N, KIND>(nx, data, tile - kplane * ygx, kplane, sm);
     }
 }
 
@@ -313,14 +364,14 @@ __global__ void __launch_bounds__(256, 4) k_ypass_r(int nx, int ny, FFTDesc D, i
 
 // The transform of the stored FP32 residual (refinement sweeps), in place:
 // the mode XF_MIX_LOAD of k_xfwd.
-template <int N>
+template <int N, int KIND>
 __global__ void __launch_bounds__(256, 4) k_xfwd_r_load(GridDev g, FFTDesc D, int L, XArgs a,
                                                         int ntiles) {
     (void)D;
     (void)L;
     __shared__ R16Smem sm;
     if (*(volatile const int *)&a.st->converged) return;
-    r16_tables<false>(sm);
+    r16_tables<false, N, KIND>(sm);
     __syncthreads();
     const RPos<N> q;
     const int nlines = g.ny * g.nz;
@@ -333,11 +384,11 @@ __global__ void __launch_bounds__(256, 4) k_xfwd_r_load(GridDev g, FFTDesc D, in
         float2 v[16];
 #pragma unroll
         for (int n1 = 0; n1 < 16; ++n1) {
-            const int i = q.in_index(n1);
+            const int i = r_src<N, KIND>(q.in_index(n1));
             v[n1] = make_float2(oka ? la[i] : 0.f, okb ? lb[i] : 0.f);
         }
         r_fft<false, N>(sm, X, q, v);
-        r_separate<N>(v, q, [&](int k, float va, float vb) {
+        r_separate<N, KIND>(v, q, sm, [&](int k, float va, float vb) {
             if (oka) la[k] = va;
             if (okb) lb[k] = vb;
         });
@@ -350,13 +401,13 @@ __global__ void __launch_bounds__(256, 4) k_xfwd_r_load(GridDev g, FFTDesc D, in
 // transform of its FP32 image sigma f.  f is formed row by row (lane = x mod
 // 32, coalesced) into the line's region of shared memory, from which the
 // threads of the line take their inputs.
-template <int N>
+template <int N, int KIND>
 __global__ void __launch_bounds__(256, 4) k_xfwd_r_divq(GridDev g, FFTDesc D, int L, XArgs a,
                                                         int ntiles) {
     (void)D;
     (void)L;
     __shared__ R16Smem sm;
-    r16_tables<false>(sm);
+    r16_tables<false, N, KIND>(sm);
     __syncthreads();
     const RPos<N> q;
     const int nlines = g.ny * g.nz, lane = threadIdx.x & 31;
@@ -390,13 +441,13 @@ __global__ void __launch_bounds__(256, 4) k_xfwd_r_divq(GridDev g, FFTDesc D, in
         __syncwarp();
         float2 v[16];
 #pragma unroll
-        for (int n1 = 0; n1 < 16; ++n1) v[n1] = X[q.in_index(n1)];
+        for (int n1 = 0; n1 < 16; ++n1) v[n1] = X[r_src<N, KIND>(q.in_index(n1))];
         __syncwarp();  // the line's region is the exchange buffer next
         r_fft<false, N>(sm, X, q, v);
         const int ra = tile * r_tile_lines(N) + 2 * q.ln;
         const bool oka = ra < nlines, okb = ra + 1 < nlines;
         float *la = out + (size_t)ra * N, *lb = la + N;
-        r_separate<N>(v, q, [&](int kk, float va, float vb) {
+        r_separate<N, KIND>(v, q, sm, [&](int kk, float va, float vb) {
             if (oka) la[kk] = va;
             if (okb) lb[kk] = vb;
         });
@@ -407,14 +458,14 @@ __global__ void __launch_bounds__(256, 4) k_xfwd_r_divq(GridDev g, FFTDesc D, in
 
 // Inverse x-pass to p (FP64): XI_STORE p = the FP32 solution, XI_ACCUM
 // p += delta 2^e (e: exponent of max|f|); the modes of k_xinv.
-template <int MODE, int N>
+template <int MODE, int N, int KIND>
 __global__ void __launch_bounds__(256, 4) k_xinv_r(GridDev g, FFTDesc D, int L, const float *in,
                                                    double *p, const DevStats *st, int ntiles) {
     (void)D;
     (void)L;
     __shared__ R16Smem sm;
     if (MODE == XI_ACCUM && *(volatile const int *)&st->converged) return;
-    r16_tables<true>(sm);
+    r16_tables<true, N, KIND>(sm);
     __syncthreads();
     const int ef = MODE == XI_ACCUM ? exp_of_bits(*(volatile const unsigned long long *)&st->fmax_bits) : 0;
     const RPos<N> q;
@@ -426,13 +477,13 @@ __global__ void __launch_bounds__(256, 4) k_xinv_r(GridDev g, FFTDesc D, int L, 
         const bool oka = ra < nlines, okb = ra + 1 < nlines;
         const float *ia = in + (size_t)ra * N, *ib = ia + N;
         float2 v[16];
-        r_combine<N>(v, q, [&](int k) { return make_float2(oka ? ia[k] : 0.f, okb ? ib[k] : 0.f); });
+        r_combine<N, KIND>(v, q, sm, [&](int k) { return make_float2(oka ? ia[k] : 0.f, okb ? ib[k] : 0.f); });
         r_fft<true, N>(sm, X, q, v);
         if (MODE == XI_STORE) {
             double *pa = p + (size_t)ra * N, *pb = pa + N;
 #pragma unroll
             for (int k2 = 0; k2 < 16; ++k2) {
-                const int x = q.out_index(k2);
+                const int x = r_src<N, KIND>(q.out_index(k2));
                 if (oka) pa[x] = f32_to_f64_shift(v[k2].x, 0);
                 if (okb) pb[x] = f32_to_f64_shift(v[k2].y, 0);
             }
@@ -440,7 +491,7 @@ __global__ void __launch_bounds__(256, 4) k_xinv_r(GridDev g, FFTDesc D, int L, 
             // delta through the line's region, then p += delta row by row:
             // lane = x mod 32, eight loads of p in flight per lane
 #pragma unroll
-            for (int k2 = 0; k2 < 16; ++k2) X[q.out_index(k2)] = v[k2];
+            for (int k2 = 0; k2 < 16; ++k2) X[r_src<N, KIND>(q.out_index(k2))] = v[k2];
             __syncwarp();
             const int lane = threadIdx.x & 31;
             const int l0 = N == 256 ? (q.ln & ~1) : q.ln;  // the warp's first line

@@ -64,6 +64,16 @@ def small_cases():
                                config=27),
         "b512x3x3_wy": I.CaseSpec(nx=512, ny=3, nz=3, bcx=0, bcy=1, n_bubbles=1, radius_cells=1,
                                   config=28),
+        # walls (DCT-II) along a direction of length 256 or 512: the
+        # register-resident passes with the reordered packing and post-twiddles
+        "b48x256x12_wy": I.CaseSpec(nx=48, ny=256, nz=12, bcx=0, bcy=1, beta=1.2, n_bubbles=2,
+                                    radius_cells=3, config=30),
+        "b256x12x10_wx": I.CaseSpec(nx=256, ny=12, nz=10, bcx=1, bcy=0, n_bubbles=2, radius_cells=3,
+                                    config=31),
+        "b24x512x8_wxy": I.CaseSpec(nx=24, ny=512, nz=8, bcx=1, bcy=1, beta=1.5, n_bubbles=2,
+                                    radius_cells=3, config=32),
+        "b512x3x3_wxy": I.CaseSpec(nx=512, ny=3, nz=3, bcx=1, bcy=1, n_bubbles=1, radius_cells=1,
+                                   config=33),
         # light drops in a heavy phase: rho0 = rho_l, split term from 1 - phi
         "b48x32x24_swapped": I.CaseSpec(nx=48, ny=32, nz=24, bcx=0, bcy=1, beta=1.5, n_bubbles=3,
                                         radius_cells=4, rho_l=1e-3, rho_g=1.0, config=19),
@@ -90,7 +100,8 @@ def test_fp64_matches_oracle(cuda_ok, name):
 @pytest.mark.parametrize("name", ["drop32", "b48x36x20_nx_stretch", "b96x64x33", "b27x18x12_ny",
                                   "b384x6x5", "b81x3x7_nn", "b48x32x24_swapped", "b512x8x5",
                                   "b48x256x12", "b27x256x6_wx", "b256x12x10", "b256x9x5_wy",
-                                  "b6x512x4", "b24x512x8", "b9x512x3", "b512x3x3_wy"])
+                                  "b6x512x4", "b24x512x8", "b9x512x3", "b512x3x3_wy",
+                                  "b48x256x12_wy", "b256x12x10_wx", "b24x512x8_wxy", "b512x3x3_wxy"])
 def test_mixed_matches_oracle(cuda_ok, name):
     c = I.make_case(CASES[name])
     ref = O.project_case(c)
@@ -106,7 +117,8 @@ def test_mixed_matches_oracle(cuda_ok, name):
 
 
 @pytest.mark.parametrize("name", ["b48x256x12", "b27x256x6_wx", "b256x12x10", "b256x9x5_wy",
-                                  "b24x512x8", "b512x8x5", "b96x64x33"])
+                                  "b24x512x8", "b512x8x5", "b48x256x12_wy", "b256x12x10_wx",
+                                  "b24x512x8_wxy", "b96x64x33"])
 def test_fp32_solve_accuracy(cuda_ok, name):
     """The FP32 solve alone (stopped at its first residual) is accurate to
     FP32 level, whichever transform kernels it runs: the Stockham and the
