@@ -78,7 +78,7 @@ struct fizzy_proj_plan_s {
     int host_calls = 0;
     // launch shapes
     int Lx = 1, TXy = 2;
-    int x_r16 = 0;  // mixed, nx = 256 or 512: register-resident FP32 x-passes
+    int x_r16 = 0;  // mixed, nx = 128, 256 or 512: register-resident FP32 x-passes
     size_t smem_x64 = 0, smem_x32 = 0, smem_y64 = 0, smem_y32 = 0;
     int cap[24] = {0};  // resident-grid size of each pass kernel (CAP_*)
     PassKernels kern;   // the pass kernels this plan launches
@@ -417,10 +417,13 @@ PassKernels pick_kernels(int fx, int fy) {
 
 // The length of a direction that has register-resident FP32 passes (any
 // boundary; 0: none).
-int r_len(int n) { return (n == 256 || n == 512) ? n : 0; }
+// (64 would fit the same transform, 16 x 4, but its 64 lines per CTA leave
+// a 64^3 grid 32 x-pass tiles for 148 SMs: slower than the Stockham passes.)
+int r_len(int n) { return (n == 128 || n == 256 || n == 512) ? n : 0; }
 
 // Mixed plans: the register-resident FP32 passes (static shared memory, no
-// opt-in) replace the Stockham ones along a direction of length 256 or 512.
+// opt-in) replace the Stockham ones along a direction of length 128, 256
+// or 512.
 template <int N, int KIND> void r_kernels_x(PassKernels &k) {
     k.xf32d = k_xfwd_r_divq<N, KIND>;
     k.xf32l = k_xfwd_r_load<N, KIND>;
@@ -433,8 +436,10 @@ template <int N, int KIND> void r_kernels_y(PassKernels &k) {
 }
 void pick_r_kernels(PassKernels &k, int nx, int bcx, int ny, int bcy) {
     const bool dx = bcx == FIZZY_BC_NEUMANN, dy = bcy == FIZZY_BC_NEUMANN;
+    if (nx == 128) dx ? r_kernels_x<128, KIND_DCT>(k) : r_kernels_x<128, KIND_PERIODIC>(k);
     if (nx == 256) dx ? r_kernels_x<256, KIND_DCT>(k) : r_kernels_x<256, KIND_PERIODIC>(k);
     if (nx == 512) dx ? r_kernels_x<512, KIND_DCT>(k) : r_kernels_x<512, KIND_PERIODIC>(k);
+    if (ny == 128) dy ? r_kernels_y<128, KIND_DCT>(k) : r_kernels_y<128, KIND_PERIODIC>(k);
     if (ny == 256) dy ? r_kernels_y<256, KIND_DCT>(k) : r_kernels_y<256, KIND_PERIODIC>(k);
     if (ny == 512) dy ? r_kernels_y<512, KIND_DCT>(k) : r_kernels_y<512, KIND_PERIODIC>(k);
 }
@@ -689,7 +694,7 @@ int fizzy_proj_plan(fizzy_proj_plan_t *out, const fizzy_proj_desc *d, void *stre
 
     // ---- launch shapes and shared-memory opt-in
     p->Lx = x_lines_per_cta(nx);
-    // mixed plans with a direction of length 256 or 512 (periodic or walls)
+    // mixed plans with a direction of length 128 to 512 (periodic or walls)
     // run the register-resident FP32 passes along it: static shared memory only
     const bool y_r16 = p->mixed && r_len(ny) != 0;
     p->x_r16 = p->mixed && r_len(nx) != 0;

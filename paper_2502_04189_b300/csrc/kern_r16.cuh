@@ -105,24 +105,52 @@ __device__ __forceinline__ void dft16(float2 (&v)[16]) {
     for (int k = 0; k < 16; ++k) v[k] = o[k];
 }
 
-// Launch shape of a length: complex lines per CTA of 256 threads (16
-// threads per line at 256, a warp per line at 512), the line stride in
-// shared memory (padded) and the y-pass tile width in real columns.
+// 8-point DFT of v[O..O+7] in place, natural order in and out: 4-point DFTs
+// of the even and the odd samples joined by W8^k (= W16^(2k)).
+template <bool INV, int O>
+__device__ __forceinline__ void dft8(float2 (&v)[16]) {
+    float2 e0 = v[O], e1 = v[O + 2], e2 = v[O + 4], e3 = v[O + 6];
+    float2 o0 = v[O + 1], o1 = v[O + 3], o2 = v[O + 5], o3 = v[O + 7];
+    dft4<INV>(e0, e1, e2, e3);
+    dft4<INV>(o0, o1, o2, o3);
+    o1 = w16<INV, 2>(o1);
+    o2 = w16<INV, 4>(o2);
+    o3 = w16<INV, 6>(o3);
+    v[O] = c_add(e0, o0);
+    v[O + 4] = c_sub(e0, o0);
+    v[O + 1] = c_add(e1, o1);
+    v[O + 5] = c_sub(e1, o1);
+    v[O + 2] = c_add(e2, o2);
+    v[O + 6] = c_sub(e2, o2);
+    v[O + 3] = c_add(e3, o3);
+    v[O + 7] = c_sub(e3, o3);
+}
+
+// Launch shape of a length.  N = 16 M (M = 4, 8, 16): M threads hold a
+// line, 16 values each; N = 512: a warp per line, two 16-thread groups.
+// Complex lines per CTA of 256 threads and per warp, the line stride in
+// shared memory (padded), and the y-pass tile width in real columns.
 template <int N> struct RShape {
-    static_assert(N == 256 || N == 512, "register-resident lengths");
-    static constexpr int LINES = N == 256 ? 16 : 8;
+    static_assert(N == 64 || N == 128 || N == 256 || N == 512, "register-resident lengths");
+    static constexpr int M = N == 512 ? 16 : N / 16;  // threads of one 16 x M transform
+    static constexpr int TPL = N == 512 ? 32 : M;     // threads per line
+    static constexpr int LINES = 256 / TPL;
+    static constexpr int LPW = 32 / TPL;
     static constexpr int LS = N + 1;
     static constexpr int TX = 2 * LINES;
 };
-constexpr int r_tile_cols(int n) { return n == 256 ? RShape<256>::TX : RShape<512>::TX; }
-constexpr int r_tile_lines(int n) { return n == 256 ? 2 * RShape<256>::LINES : 2 * RShape<512>::LINES; }
+constexpr int r_tile_cols(int n) {
+    return n == 64 ? RShape<64>::TX : n == 128 ? RShape<128>::TX : n == 256 ? RShape<256>::TX : RShape<512>::TX;
+}
+constexpr int r_tile_lines(int n) { return r_tile_cols(n); }  // x-passes: real lines per CTA
 
-// Shared memory of one CTA: its lines (16 x 257 >= 8 x 513 complex values),
-// reused for the 16 x 16 exchanges; the twiddles W256^(n2 k1) at [k1][n2]
-// and W512^n (n < 256), conjugated for the inverse; for a DCT direction the
-// post-twiddles (cos, sin)(pi m / (2n)), m < n/2.
+// Shared memory of one CTA: its lines (64 x 65 complex values covers every
+// length's LINES x LS), reused for the 16 x M exchanges; the twiddles
+// W_(16M)^(t k1) at [k1][t] and W512^n (n < 256), conjugated for the
+// inverse; for a DCT direction the post-twiddles (cos, sin)(pi m / (2n)),
+// m < n/2.
 struct R16Smem {
-    float2 x[16 * 257];
+    float2 x[64 * 65];
     float2 tw[256];
     float2 tw2[256];
     float2 cs[256];
@@ -130,12 +158,17 @@ struct R16Smem {
 
 template <bool INV, int N, int KIND>
 __device__ __forceinline__ void r16_tables(R16Smem &sm) {
-    const int n2 = threadIdx.x & 15, k1 = threadIdx.x >> 4;
+    constexpr int M = RShape<N>::M;
     float s, c;
-    sincospif(-(float)(n2 * k1) / 128.f, &s, &c);
-    sm.tw[threadIdx.x] = make_float2(c, INV ? -s : s);
-    sincospif(-(float)threadIdx.x / 256.f, &s, &c);
-    sm.tw2[threadIdx.x] = make_float2(c, INV ? -s : s);
+    if (threadIdx.x < 16 * M) {
+        const int k1 = threadIdx.x / M, t = threadIdx.x % M;
+        sincospif(-(float)(t * k1) / (float)(8 * M), &s, &c);
+        sm.tw[threadIdx.x] = make_float2(c, INV ? -s : s);
+    }
+    if (N == 512) {
+        sincospif(-(float)threadIdx.x / 256.f, &s, &c);
+        sm.tw2[threadIdx.x] = make_float2(c, INV ? -s : s);
+    }
     if (KIND == KIND_DCT && threadIdx.x < N / 2) {
         sincospif((float)threadIdx.x / (float)(2 * N), &s, &c);
         sm.cs[threadIdx.x] = make_float2(c, s);
@@ -153,45 +186,68 @@ __device__ __forceinline__ int r_src(int p) {
 }
 constexpr float R_SQRT2 = 1.41421356237309504880f;  // the n/2 term of the DCT (2 cos(pi/4))
 
-// Steps 1-3 of the four-step DFT on the 256 values at X: thread t holds
-// v[n1] = x[16 n1 + t] and ends with v[k2] = X[t + 16 k2].  X is overwritten;
-// its threads (all in one warp) must have finished reading X before the call
-// (warp barriers inside, the last one after the exchange reads).
-template <bool INV>
-__device__ __forceinline__ void r16_fft(const R16Smem &sm, float2 *X, int t, float2 (&v)[16]) {
+// The 16 x M four-step DFT on the 16 M values at X: thread t holds
+// v[n1] = x[M n1 + t] and ends with v[j M + k2] = X[t + M j + 16 k2]
+// (j < 16/M, k2 < M): a 16-point DFT, the twiddles W_(16M)^(t k1), one
+// swizzled exchange through X (a permutation of M slots both ways), then
+// 16/M M-point DFTs.  X is overwritten; its threads (all in one warp) must
+// have finished reading X before the call (warp barriers inside, the last
+// one after the exchange reads).
+template <bool INV, int M>
+__device__ __forceinline__ void r_core(const R16Smem &sm, float2 *X, int t, float2 (&v)[16]) {
     dft16<INV>(v);
 #pragma unroll
     for (int k1 = 1; k1 < 16; ++k1) {
-        const float2 w = sm.tw[k1 * 16 + t];
+        const float2 w = sm.tw[k1 * M + t];
         v[k1] = c_mul(v[k1], w.x, w.y);
     }
 #pragma unroll
-    for (int k1 = 0; k1 < 16; ++k1) X[k1 * 16 + (t ^ k1)] = v[k1];  // conflict-free both ways
+    for (int k1 = 0; k1 < 16; ++k1) X[k1 * M + (t ^ (k1 & (M - 1)))] = v[k1];
     __syncwarp();
 #pragma unroll
-    for (int n2 = 0; n2 < 16; ++n2) v[n2] = X[t * 16 + (n2 ^ t)];
+    for (int j = 0; j < 16 / M; ++j)
+#pragma unroll
+        for (int n2 = 0; n2 < M; ++n2) v[j * M + n2] = X[(t + M * j) * M + (n2 ^ t)];
     __syncwarp();
-    dft16<INV>(v);
+    if constexpr (M == 16) {
+        dft16<INV>(v);
+    } else if constexpr (M == 8) {
+        dft8<INV, 0>(v);
+        dft8<INV, 8>(v);
+    } else {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) dft4<INV>(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+    }
 }
 
 // Position of a thread: complex line ln of the CTA, group h (the half of a
-// 512-line), index t in the group.  Its inputs are the samples
-// 16 n1 + t + 256 h, its outputs the indices out_index(k2).
+// 512-line), index t in its 16 x M transform.  Its inputs are the samples
+// in_index(n1), its outputs the indices out_index(r).
 template <int N> struct RPos {
+    static constexpr int M = RShape<N>::M;
     int ln, h, t;
     __device__ __forceinline__ RPos() {
-        t = threadIdx.x & 15;
-        ln = N == 256 ? threadIdx.x >> 4 : threadIdx.x >> 5;
-        h = N == 256 ? 0 : (threadIdx.x >> 4) & 1;
+        t = threadIdx.x & (M - 1);
+        ln = threadIdx.x / RShape<N>::TPL;
+        h = N == 512 ? (threadIdx.x >> 4) & 1 : 0;
     }
-    __device__ __forceinline__ int in_index(int n1) const { return 16 * n1 + t + 256 * h; }
-    __device__ __forceinline__ int out_index(int k2) const {
-        return N == 256 ? t + 16 * k2 : 2 * (t + 16 * k2) + h;
+    __device__ __forceinline__ int in_index(int n1) const {
+        return N == 512 ? 16 * n1 + t + 256 * h : M * n1 + t;
+    }
+    __device__ __forceinline__ int out_index(int r) const {
+        return N == 512 ? 2 * (t + 16 * r) + h : t + M * (r / M) + 16 * (r % M);
     }
 };
 
+// The register holding the partner X[N - k] of register r when the thread
+// is its own partner (t = 0, group 0): r = j M + k2 maps to
+// (M - k2) mod M for j = 0, else (16/M - j) M + M - 1 - k2.
+template <int M> constexpr int self_reg(int r) {
+    return r / M == 0 ? (M - r % M) % M : (16 / M - r / M) * M + (M - 1 - r % M);
+}
+
 // The transform of one line: v[n1] = the input at in_index(n1) on entry,
-// v[k2] = the output at out_index(k2) on return.  X: the line's region
+// v[r] = the output at out_index(r) on return.  X: the line's region
 // (N values); warp barriers only (a line never spans warps).
 template <bool INV, int N>
 __device__ __forceinline__ void r_fft(const R16Smem &sm, float2 *X, const RPos<N> &q, float2 (&v)[16]) {
@@ -209,31 +265,35 @@ __device__ __forceinline__ void r_fft(const R16Smem &sm, float2 *X, const RPos<N
                 v[n1] = c_mul(c_sub(lo, hi), w.x, w.y);
             }
         }
+        r_core<INV, 16>(sm, X + 256 * q.h, q.t, v);
+    } else {
+        r_core<INV, RShape<N>::M>(sm, X, q.t, v);
     }
-    r16_fft<INV>(sm, X + 256 * q.h, q.t, v);
 }
 
 // Separation of the forward transform of a packed line (two real lines as
 // real and imaginary part): the spectra of both, scaled by 2 (the
 // conventions of the Stockham passes: half-complex for a periodic direction,
 // DCT-II coefficients through the post-twiddle (c, s)_m for a wall), through
-// fn(k, a_k, b_k).  X[K] pairs with X[N - K]: at 256 the partner's register
-// 15 - k2 of thread (16 - t) mod 16, or this thread's register (16 - k2)
-// mod 16 (t = 0); at 512 the odd outputs pair within group 1 with thread
-// 15 - t, register 15 - k2.
+// fn(k, a_k, b_k).  X[K] pairs with X[N - K], held in register 15 - r of
+// thread (M - t) mod M of the line, or (t = 0) in this thread's register
+// self_reg(r); at 512 the odd outputs pair within group 1 with thread
+// 15 - t, register 15 - r.
 template <int N, int KIND, typename F>
 __device__ __forceinline__ void r_separate(const float2 (&v)[16], const RPos<N> &q,
                                            const R16Smem &sm, F &&fn) {
+    constexpr int M = RShape<N>::M;
     const int lane = threadIdx.x & 31;
-    const int src = (N == 256 || q.h == 0) ? ((lane & 16) | ((16 - q.t) & 15)) : (16 | (15 - q.t));
+    const int src = (N != 512 || q.h == 0) ? ((lane & ~(M - 1)) | ((M - q.t) & (M - 1)))
+                                           : (16 | (15 - q.t));
     const bool self = q.h == 0 && q.t == 0;
 #pragma unroll
-    for (int k2 = 0; k2 < 16; ++k2) {
-        const float qx = __shfl_sync(0xffffffffu, v[15 - k2].x, src);
-        const float qy = __shfl_sync(0xffffffffu, v[15 - k2].y, src);
-        const float2 z = v[k2];
-        const float2 y = self ? v[(16 - k2) & 15] : make_float2(qx, qy);
-        const int k = q.out_index(k2);
+    for (int r = 0; r < 16; ++r) {
+        const float qx = __shfl_sync(0xffffffffu, v[15 - r].x, src);
+        const float qy = __shfl_sync(0xffffffffu, v[15 - r].y, src);
+        const float2 z = v[r];
+        const float2 y = self ? v[self_reg<M>(r)] : make_float2(qx, qy);
+        const int k = q.out_index(r);
         if (KIND == KIND_PERIODIC) {
             // k <= n/2: (Re A_k, Re B_k) x 2; k > n/2: (Im A_m, Im B_m) x 2, m = n - k
             if (k <= N / 2) fn(k, z.x + y.x, z.y + y.y);
@@ -285,32 +345,60 @@ __device__ __forceinline__ void r_combine(float2 (&v)[16], const RPos<N> &q, con
 }
 
 // ---- y-passes: one tile = TX real columns (bx) of one z-plane of an
-// (nz, N, nx) FP32 array, transformed along y in place.  Rows move between
-// global and shared memory a warp at a time (32 columns of one row at 256,
-// 16 columns of two rows at 512); column 2l + e of the tile is component e
-// of complex line l.  Forward: real columns -> spectra scaled by 2
-// (half-complex, or DCT-II for a wall direction); inverse: the reverse,
-// unscaled.
+// (nz, N, nx) FP32 array, transformed along y in place.  The N x TX tile
+// (8192 values at every length) moves between global and shared memory as
+// elements e = lane + 32 (warp + 8 i): each warp access is 32 consecutive
+// columns (TX >= 32) or two rows of 16 (TX = 16).  Column 2l + c of the tile
+// is component c of complex line l.  Forward: real columns -> spectra
+// scaled by 2 (half-complex, or DCT-II for a wall direction); inverse: the
+// reverse, unscaled.
 template <bool INV, int N, int KIND>
 __device__ __forceinline__ void ypass_r_tile(int nx, float *data, int bx, int kplane, R16Smem &sm) {
     constexpr int TX = RShape<N>::TX, LS = RShape<N>::LS;
-    constexpr int RPW = 32 / TX;  // rows per warp access
+    static_assert(N * TX == 32 * 256, "one tile is 32 values per thread");
     const RPos<N> q;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int col = lane % TX, rsub = lane / TX;
-    const bool col_ok = bx * TX + col < nx;
-    float *gcol = data + (size_t)kplane * N * nx + bx * TX + col;
-    float *scol = (float *)sm.x + (col >> 1) * (2 * LS) + (col & 1);
+    const int c0 = bx * TX;
+    float *plane = data + (size_t)kplane * N * nx + c0;
+    float *sf = (float *)sm.x;
     float2 *X = sm.x + q.ln * LS;
-    auto row_of = [&](int i) { return i * (8 * RPW) + warp * RPW + rsub; };  // i < 32
+    // element i of this thread: (row, col) of e = lane + 32 (warp + 8 i); for
+    // TX <= 32 the column is the thread's own (one pointer per thread)
+    auto rc = [&](int i, int &row, int &col) {
+        const int e = lane + 32 * (warp + 8 * i);
+        row = e / TX;
+        col = e % TX;
+    };
+    // one column per thread (TX <= 32): its pointers and the rows linear in i
+    constexpr int RPW = TX <= 32 ? 32 / TX : 1;
+    const int tcol = lane % TX, rsub = lane / TX;
+    const bool tcol_ok = c0 + tcol < nx;
+    float *gcol = plane + tcol;
+    float *scol = sf + (tcol >> 1) * (2 * LS) + (tcol & 1);
+    auto row_of = [&](int i) { return i * (8 * RPW) + warp * RPW + rsub; };
     // 1. stage the tile (sixteen loads in flight)
 #pragma unroll 1
     for (int i0 = 0; i0 < 32; i0 += 16) {
         float r[16];
+        if constexpr (TX <= 32) {
 #pragma unroll
-        for (int u = 0; u < 16; ++u) r[u] = col_ok ? gcol[(size_t)row_of(i0 + u) * nx] : 0.f;
+            for (int u = 0; u < 16; ++u) r[u] = tcol_ok ? gcol[(size_t)row_of(i0 + u) * nx] : 0.f;
 #pragma unroll
-        for (int u = 0; u < 16; ++u) scol[2 * row_of(i0 + u)] = r[u];
+            for (int u = 0; u < 16; ++u) scol[2 * row_of(i0 + u)] = r[u];
+        } else {
+#pragma unroll
+            for (int u = 0; u < 16; ++u) {
+                int row, col;
+                rc(i0 + u, row, col);
+                r[u] = c0 + col < nx ? plane[(size_t)row * nx + col] : 0.f;
+            }
+#pragma unroll
+            for (int u = 0; u < 16; ++u) {
+                int row, col;
+                rc(i0 + u, row, col);
+                sf[(col >> 1) * (2 * LS) + 2 * row + (col & 1)] = r[u];
+            }
+        }
     }
     __syncthreads();
     float2 v[16];
@@ -326,14 +414,20 @@ __device__ __forceinline__ void ypass_r_tile(int nx, float *data, int bx, int kp
         r_separate<N, KIND>(v, q, sm, [&](int k, float a, float b) { X[k] = make_float2(a, b); });
     } else {
 #pragma unroll
-        for (int k2 = 0; k2 < 16; ++k2) X[r_src<N, KIND>(q.out_index(k2))] = v[k2];
+        for (int r = 0; r < 16; ++r) X[r_src<N, KIND>(q.out_index(r))] = v[r];
     }
     __syncthreads();
     // 2. write the tile back
 #pragma unroll
     for (int i = 0; i < 32; ++i) {
-        const int row = row_of(i);
-        if (col_ok) gcol[(size_t)row * nx] = scol[2 * row];
+        if constexpr (TX <= 32) {
+            const int row = row_of(i);
+            if (tcol_ok) gcol[(size_t)row * nx] = scol[2 * row];
+        } else {
+            int row, col;
+            rc(i, row, col);
+            if (c0 + col < nx) plane[(size_t)row * nx + col] = sf[(col >> 1) * (2 * LS) + 2 * row + (col & 1)];
+        }
     }
     __syncthreads();  // the buffer is free for the next tile
 }
@@ -357,10 +451,68 @@ __global__ void __launch_bounds__(256, 4) k_ypass_r(int nx, int ny, FFTDesc D, i
     }
 }
 
-// ---- x-passes: 2 LINES real lines of the [nz][ny] line set per CTA; a
-// line's threads load, transform and store it alone (warp barriers only).
-// At each register index the 16 threads of a group touch 64 consecutive
-// bytes of each of the two rows of their line.
+// ---- x-passes: 2 LINES real lines of the [nz][ny] line set per CTA.  A
+// warp owns LPW complex lines (2 LPW real rows, rows 2l and 2l + 1 packed as
+// line l); it stages them row by row through their shared-memory regions
+// (lane = x mod 32: 128-byte accesses), transforms them and writes them back
+// the same way, with warp barriers only.
+
+// The warp's first line (of the CTA).
+template <int N> __device__ __forceinline__ int r_warp_line() {
+    return (threadIdx.x >> 5) * RShape<N>::LPW;
+}
+
+// A warp's rows hold 2 LPW x N = 32 x 32 values at every length: slot s
+// (s < 32) of a lane is row s / (N/32), x = lane + 32 (s mod N/32).
+template <int N> __device__ __forceinline__ int r_slot_row(int s) { return s / (N / 32); }
+template <int N> __device__ __forceinline__ int r_slot_x(int s) {
+    return (threadIdx.x & 31) + 32 * (s % (N / 32));
+}
+// The shared-memory float of (row r of the warp, x): line l0 + r/2, component r & 1.
+template <int N> __device__ __forceinline__ int r_slot_f(int r, int x) {
+    return (r_warp_line<N>() + (r >> 1)) * (2 * RShape<N>::LS) + 2 * x + (r & 1);
+}
+
+// Rows of the warp from an FP32 array [nlines][N] into the line regions
+// (zeros past the last line), all 32 loads of a lane in flight.
+template <int N>
+__device__ __forceinline__ void r_rows_in(const float *src, int row0, int nlines, R16Smem &sm) {
+    float *sf = (float *)sm.x;
+    float x[32];
+#pragma unroll
+    for (int s = 0; s < 32; ++s) {
+        const int row = row0 + r_slot_row<N>(s);
+        x[s] = row < nlines ? src[(size_t)row * N + r_slot_x<N>(s)] : 0.f;
+    }
+#pragma unroll
+    for (int s = 0; s < 32; ++s) sf[r_slot_f<N>(r_slot_row<N>(s), r_slot_x<N>(s))] = x[s];
+    __syncwarp();
+}
+
+// Rows of the warp from the line regions back to an FP32 array.
+template <int N>
+__device__ __forceinline__ void r_rows_out(float *dst, int row0, int nlines, const R16Smem &sm) {
+    const float *sf = (const float *)sm.x;
+    __syncwarp();
+#pragma unroll
+    for (int s = 0; s < 32; ++s) {
+        const int row = row0 + r_slot_row<N>(s);
+        if (row < nlines) dst[(size_t)row * N + r_slot_x<N>(s)] = sf[r_slot_f<N>(r_slot_row<N>(s), r_slot_x<N>(s))];
+    }
+    __syncwarp();
+}
+
+// Forward transform of the staged lines: inputs from the line region X,
+// the spectra back into it.
+template <int N, int KIND>
+__device__ __forceinline__ void r_forward_line(const R16Smem &sm, float2 *X, const RPos<N> &q) {
+    float2 v[16];
+#pragma unroll
+    for (int n1 = 0; n1 < 16; ++n1) v[n1] = X[r_src<N, KIND>(q.in_index(n1))];
+    __syncwarp();  // the line's region is the exchange buffer next
+    r_fft<false, N>(sm, X, q, v);
+    r_separate<N, KIND>(v, q, sm, [&](int k, float a, float b) { X[k] = make_float2(a, b); });
+}
 
 // The transform of the stored FP32 residual (refinement sweeps), in place:
 // the mode XF_MIX_LOAD of k_xfwd.
@@ -378,29 +530,37 @@ __global__ void __launch_bounds__(256, 4) k_xfwd_r_load(GridDev g, FFTDesc D, in
     float *data = (float *)a.out;
     float2 *X = sm.x + q.ln * RShape<N>::LS;
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const int ra = tile * r_tile_lines(N) + 2 * q.ln;
-        const bool oka = ra < nlines, okb = ra + 1 < nlines;
-        float *la = data + (size_t)ra * N, *lb = la + N;
-        float2 v[16];
+        const int row0 = tile * r_tile_lines(N) + 2 * r_warp_line<N>();
+        if constexpr (N >= 256) {
+            // a 16-thread group reads and writes 64 consecutive bytes of each
+            // of its line's two rows at a time: direct global access
+            const int ra = tile * r_tile_lines(N) + 2 * q.ln;
+            const bool oka = ra < nlines, okb = ra + 1 < nlines;
+            float *la = data + (size_t)ra * N, *lb = la + N;
+            float2 v[16];
 #pragma unroll
-        for (int n1 = 0; n1 < 16; ++n1) {
-            const int i = r_src<N, KIND>(q.in_index(n1));
-            v[n1] = make_float2(oka ? la[i] : 0.f, okb ? lb[i] : 0.f);
+            for (int n1 = 0; n1 < 16; ++n1) {
+                const int i = r_src<N, KIND>(q.in_index(n1));
+                v[n1] = make_float2(oka ? la[i] : 0.f, okb ? lb[i] : 0.f);
+            }
+            r_fft<false, N>(sm, X, q, v);
+            r_separate<N, KIND>(v, q, sm, [&](int k, float va, float vb) {
+                if (oka) la[k] = va;
+                if (okb) lb[k] = vb;
+            });
+            __syncwarp();  // every lane has read its line before the next tile
+        } else {
+            r_rows_in<N>(data, row0, nlines, sm);
+            r_forward_line<N, KIND>(sm, X, q);
+            r_rows_out<N>(data, row0, nlines, sm);
         }
-        r_fft<false, N>(sm, X, q, v);
-        r_separate<N, KIND>(v, q, sm, [&](int k, float va, float vb) {
-            if (oka) la[k] = va;
-            if (okb) lb[k] = vb;
-        });
-        __syncwarp();  // every lane has read its line before the next tile
     }
 }
 
 // The first x-pass of the mixed solve (the mode XF_MIX_DIVQ of k_xfwd):
 // f = rho0 D(q') in FP64 (stored, and max|f| recorded), then the forward
 // transform of its FP32 image sigma f.  f is formed row by row (lane = x mod
-// 32, coalesced) into the line's region of shared memory, from which the
-// threads of the line take their inputs.
+// 32, coalesced) into the line regions.
 template <int N, int KIND>
 __global__ void __launch_bounds__(256, 4) k_xfwd_r_divq(GridDev g, FFTDesc D, int L, XArgs a,
                                                         int ntiles) {
@@ -410,48 +570,70 @@ __global__ void __launch_bounds__(256, 4) k_xfwd_r_divq(GridDev g, FFTDesc D, in
     r16_tables<false, N, KIND>(sm);
     __syncthreads();
     const RPos<N> q;
-    const int nlines = g.ny * g.nz, lane = threadIdx.x & 31;
+    const int nlines = g.ny * g.nz, l0 = r_warp_line<N>();
     constexpr int LS = RShape<N>::LS;
-    const int l0 = N == 256 ? (q.ln & ~1) : q.ln;  // the warp's first line
-    constexpr int WROWS = N == 256 ? 4 : 2;         // real rows of the warp
     const float scale32 = (float)g.sigma;
     float *out = (float *)a.out;
+    float *sf = (float *)sm.x;
     float2 *X = sm.x + q.ln * LS;
     unsigned long long mx = 0ull;
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int row0 = tile * r_tile_lines(N) + 2 * l0;
+        if constexpr (N >= 256) {  // rows of N/32 >= 8 cells per lane: per-row constants once
+            const int lane = threadIdx.x & 31;
 #pragma unroll 1
-        for (int r = 0; r < WROWS; ++r) {
-            const int row = tile * r_tile_lines(N) + 2 * l0 + r;
-            float *dr = (float *)(sm.x + (l0 + (r >> 1)) * LS) + (r & 1);
-            if (row < nlines) {
-                const int k = fdiv(row, g.ny, g.rny), j = row - k * g.ny;
-                const double cz = g.dvz[k];
+            for (int r = 0; r < 2 * RShape<N>::LPW; ++r) {
+                const int row = row0 + r;
+                float *dr = sf + r_slot_f<N>(r, 0);
+                if (row < nlines) {
+                    const int k = fdiv(row, g.ny, g.rny), j = row - k * g.ny;
+                    const double cz = g.dvz[k];
 #pragma unroll 4
-                for (int i = 0; i < N / 32; ++i) {
-                    const int x = lane + 32 * i;
-                    const double f = div_q<false>(g, x, j, k, g.dvx, g.dvy, cz, a.qx, a.qy, a.qz);
+                    for (int i = 0; i < N / 32; ++i) {
+                        const int x = lane + 32 * i;
+                        const double f = div_q<false>(g, x, j, k, g.dvx, g.dvy, cz, a.qx, a.qy, a.qz);
+                        a.f_out[(size_t)row * N + x] = f;
+                        mx = umax64(mx, absbits(f));
+                        dr[2 * x] = f64_to_f32_shift(f, 0) * scale32;
+                    }
+                } else {
+                    for (int i = 0; i < N / 32; ++i) dr[2 * (lane + 32 * i)] = 0.f;
+                }
+            }
+        } else {  // short rows: the warp's 32 slots per lane
+#pragma unroll 4
+            for (int s = 0; s < 32; ++s) {
+                const int r = r_slot_row<N>(s), x = r_slot_x<N>(s), row = row0 + r;
+                float val = 0.f;
+                if (row < nlines) {
+                    const int k = fdiv(row, g.ny, g.rny), j = row - k * g.ny;
+                    const double f = div_q<false>(g, x, j, k, g.dvx, g.dvy, g.dvz[k], a.qx, a.qy, a.qz);
                     a.f_out[(size_t)row * N + x] = f;
                     mx = umax64(mx, absbits(f));
-                    dr[2 * x] = f64_to_f32_shift(f, 0) * scale32;
+                    val = f64_to_f32_shift(f, 0) * scale32;
                 }
-            } else {
-                for (int i = 0; i < N / 32; ++i) dr[2 * (lane + 32 * i)] = 0.f;
+                sf[r_slot_f<N>(r, x)] = val;
             }
         }
         __syncwarp();
-        float2 v[16];
+        if constexpr (N >= 256) {  // the spectra straight to global memory
+            float2 v[16];
 #pragma unroll
-        for (int n1 = 0; n1 < 16; ++n1) v[n1] = X[r_src<N, KIND>(q.in_index(n1))];
-        __syncwarp();  // the line's region is the exchange buffer next
-        r_fft<false, N>(sm, X, q, v);
-        const int ra = tile * r_tile_lines(N) + 2 * q.ln;
-        const bool oka = ra < nlines, okb = ra + 1 < nlines;
-        float *la = out + (size_t)ra * N, *lb = la + N;
-        r_separate<N, KIND>(v, q, sm, [&](int kk, float va, float vb) {
-            if (oka) la[kk] = va;
-            if (okb) lb[kk] = vb;
-        });
-        __syncwarp();  // the region is rewritten by the next tile
+            for (int n1 = 0; n1 < 16; ++n1) v[n1] = X[r_src<N, KIND>(q.in_index(n1))];
+            __syncwarp();  // the line's region is the exchange buffer next
+            r_fft<false, N>(sm, X, q, v);
+            const int ra = tile * r_tile_lines(N) + 2 * q.ln;
+            const bool oka = ra < nlines, okb = ra + 1 < nlines;
+            float *la = out + (size_t)ra * N, *lb = la + N;
+            r_separate<N, KIND>(v, q, sm, [&](int kk, float va, float vb) {
+                if (oka) la[kk] = va;
+                if (okb) lb[kk] = vb;
+            });
+            __syncwarp();  // the region is rewritten by the next tile
+        } else {
+            r_forward_line<N, KIND>(sm, X, q);
+            r_rows_out<N>(out, row0, nlines, sm);
+        }
     }
     block_max_atomic(mx, &a.st->fmax_bits);
 }
@@ -469,52 +651,39 @@ __global__ void __launch_bounds__(256, 4) k_xinv_r(GridDev g, FFTDesc D, int L, 
     __syncthreads();
     const int ef = MODE == XI_ACCUM ? exp_of_bits(*(volatile const unsigned long long *)&st->fmax_bits) : 0;
     const RPos<N> q;
-    const int nlines = g.ny * g.nz;
-    constexpr int LS = RShape<N>::LS;
-    float2 *X = sm.x + q.ln * LS;
+    const int nlines = g.ny * g.nz, l0 = r_warp_line<N>();
+    float2 *X = sm.x + q.ln * RShape<N>::LS;
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const int ra = tile * r_tile_lines(N) + 2 * q.ln;
-        const bool oka = ra < nlines, okb = ra + 1 < nlines;
-        const float *ia = in + (size_t)ra * N, *ib = ia + N;
+        const int row0 = tile * r_tile_lines(N) + 2 * l0;
+        r_rows_in<N>(in, row0, nlines, sm);
         float2 v[16];
-        r_combine<N, KIND>(v, q, sm, [&](int k) { return make_float2(oka ? ia[k] : 0.f, okb ? ib[k] : 0.f); });
+        r_combine<N, KIND>(v, q, sm, [&](int k) { return X[k]; });
+        __syncwarp();  // the line's region is the exchange buffer next
         r_fft<true, N>(sm, X, q, v);
-        if (MODE == XI_STORE) {
-            double *pa = p + (size_t)ra * N, *pb = pa + N;
 #pragma unroll
-            for (int k2 = 0; k2 < 16; ++k2) {
-                const int x = r_src<N, KIND>(q.out_index(k2));
-                if (oka) pa[x] = f32_to_f64_shift(v[k2].x, 0);
-                if (okb) pb[x] = f32_to_f64_shift(v[k2].y, 0);
-            }
-        } else {
-            // delta through the line's region, then p += delta row by row:
-            // lane = x mod 32, eight loads of p in flight per lane
+        for (int r = 0; r < 16; ++r) X[r_src<N, KIND>(q.out_index(r))] = v[r];
+        __syncwarp();
+        // p (or p += delta) by slots (lane = x mod 32), eight values of p in
+        // flight per lane
+        const float *sf = (const float *)sm.x;
 #pragma unroll
-            for (int k2 = 0; k2 < 16; ++k2) X[r_src<N, KIND>(q.out_index(k2))] = v[k2];
-            __syncwarp();
-            const int lane = threadIdx.x & 31;
-            const int l0 = N == 256 ? (q.ln & ~1) : q.ln;  // the warp's first line
-            constexpr int WROWS = N == 256 ? 4 : 2;         // real rows of the warp
-#pragma unroll 1
-            for (int r = 0; r < WROWS; ++r) {
-                const int row = tile * r_tile_lines(N) + 2 * l0 + r;
-                if (row < nlines) {
-                    double *pr = p + (size_t)row * N + lane;
-                    const float *dr = (const float *)(sm.x + (l0 + (r >> 1)) * LS) + (r & 1) + 2 * lane;
+        for (int s0 = 0; s0 < 32; s0 += 8) {
+            double qv[8];
+            if (MODE == XI_ACCUM) {
 #pragma unroll
-                    for (int i0 = 0; i0 < N / 32; i0 += 8) {
-                        double qv[8];
-#pragma unroll
-                        for (int i = 0; i < 8; ++i) qv[i] = pr[32 * (i0 + i)];
-#pragma unroll
-                        for (int i = 0; i < 8; ++i)
-                            pr[32 * (i0 + i)] = qv[i] + f32_to_f64_shift(dr[64 * (i0 + i)], ef);
-                    }
+                for (int u = 0; u < 8; ++u) {
+                    const int row = row0 + r_slot_row<N>(s0 + u);
+                    qv[u] = row < nlines ? p[(size_t)row * N + r_slot_x<N>(s0 + u)] : 0.0;
                 }
             }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int r = r_slot_row<N>(s0 + u), x = r_slot_x<N>(s0 + u), row = row0 + r;
+                const double d = f32_to_f64_shift(sf[r_slot_f<N>(r, x)], ef);
+                if (row < nlines) p[(size_t)row * N + x] = MODE == XI_ACCUM ? qv[u] + d : d;
+            }
         }
-        __syncwarp();  // the line's region is rewritten by the next tile
+        __syncwarp();  // the line regions are rewritten by the next tile
     }
 }
 

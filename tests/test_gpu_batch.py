@@ -1,9 +1,14 @@
 """Batched projections in one persistent launch (needs a B300).
 
-Each instance solved inside the batch must equal the same plan solved alone
-(the same kernel bodies run per tile), and match the FP64 oracle within the
-mixed-mode tolerance.  The instances are drawn with the uneven-batch recipe
-(sizes 32-192, periodic or wall x/y, 1-20 drops, density ratio 10-1000).
+Each instance solved inside the batch must equal the same plan solved alone,
+bit for bit (the same kernel bodies run per tile), and match the FP64 oracle
+within the mixed-mode tolerance.  "Alone" is the plain solve, except for
+mixed instances with an x or y length of 128, 256 or 512: plain mixed
+solves run register-resident FP32 transform passes there while the batch
+keeps the Stockham bodies, so such an instance is compared with the same
+instance batched alone, and with the plain solve within the mixed tolerance.
+The instances are drawn with the uneven-batch recipe (sizes 32-192, periodic
+or wall x/y, 1-20 drops, density ratio 10-1000).
 """
 import numpy as np
 import pytest
@@ -23,9 +28,17 @@ def small_batch_specs(k=6):
     return specs[:k - 1] + [specs[20]]  # the smallest ones plus one mid-size
 
 
-def run_alone(case, precision):
+R_LENGTHS = (128, 256, 512)  # register-resident FP32 passes in plain mixed solves
+
+
+def plain_differs(case, precision):
+    s = case.spec
+    return precision == F.MIXED and (s.nx in R_LENGTHS or s.ny in R_LENGTHS)
+
+
+def run_plain(case, precision, **kw):
     import torch
-    plan = F.Plan.for_case(case, precision=precision)
+    plan = F.Plan.for_case(case, precision=precision, **kw)
     u, v, w = to_dev(case.u), to_dev(case.v), to_dev(case.w)
     p = torch.empty_like(u)
     plan.solve(to_dev(case.phi), to_dev(case.pn), to_dev(case.pnm1), u, v, w, p)
@@ -33,6 +46,28 @@ def run_alone(case, precision):
     st = plan.stats()
     plan.close()
     return dict(p=p.cpu().numpy(), u=u.cpu().numpy(), v=v.cpu().numpy(), w=w.cpu().numpy(), stats=st)
+
+
+def run_batched_alone(case, precision, **kw):
+    import torch
+    plan = F.Plan.for_case(case, precision=precision, **kw)
+    arr = (to_dev(case.phi), to_dev(case.pn), to_dev(case.pnm1), to_dev(case.u), to_dev(case.v),
+           to_dev(case.w), torch.empty(case.shape, dtype=torch.float64, device="cuda"))
+    batch = F.Batch([plan], [arr])
+    batch.solve()
+    assert batch.status() == 0
+    out = dict(p=arr[6].cpu().numpy(), u=arr[3].cpu().numpy(), v=arr[4].cpu().numpy(),
+               w=arr[5].cpu().numpy(), stats=plan.stats())
+    batch.close()
+    plan.close()
+    return out
+
+
+def run_alone(case, precision, **kw):
+    """The instance solved by itself with the passes the batch runs."""
+    if plain_differs(case, precision):
+        return run_batched_alone(case, precision, **kw)
+    return run_plain(case, precision, **kw)
 
 
 @pytest.mark.parametrize("precision", [F.MIXED, F.FP64], ids=["mixed", "fp64"])
@@ -79,20 +114,11 @@ def test_batch_equals_alone(cuda_ok, precision):
 def test_batch_first_residual_convergence_equals_alone(cuda_ok):
     """Mixed instances with a loose tolerance stop at the residual of the FP32
     solution, so the batch takes its conditional-correction pass; results
-    stay bitwise equal to each plan solved alone."""
+    stay bitwise equal to each instance solved alone."""
     import torch
     cases = [I.make_case(s) for s in small_batch_specs(4)]
     kw = dict(tol=1e-3, div_tol=1.0)
-    alone = []
-    for c in cases:
-        plan = F.Plan.for_case(c, precision=F.MIXED, **kw)
-        u, v, w = to_dev(c.u), to_dev(c.v), to_dev(c.w)
-        p = torch.empty_like(u)
-        plan.solve(to_dev(c.phi), to_dev(c.pn), to_dev(c.pnm1), u, v, w, p)
-        torch.cuda.synchronize()
-        alone.append(dict(p=p.cpu().numpy(), u=u.cpu().numpy(), v=v.cpu().numpy(),
-                          w=w.cpu().numpy(), stats=plan.stats()))
-        plan.close()
+    alone = [run_alone(c, F.MIXED, **kw) for c in cases]
     assert all(a["stats"]["iterations"] == 0 for a in alone)
     plans = [F.Plan.for_case(c, precision=F.MIXED, **kw) for c in cases]
     arrays = [(to_dev(c.phi), to_dev(c.pn), to_dev(c.pnm1), to_dev(c.u), to_dev(c.v), to_dev(c.w),
@@ -162,6 +188,35 @@ def test_batch_autotune_keeps_results(cuda_ok):
         a = run_alone(c, F.MIXED)
         assert np.array_equal(arr[6].cpu().numpy(), a["p"])
         assert np.array_equal(arr[3].cpu().numpy(), a["u"])
+    batch.close()
+    for p in plans:
+        p.close()
+
+
+def test_batch_mixed_matches_plain_within_tolerance(cuda_ok):
+    """Mixed instances whose plain solves run the register-resident FP32
+    passes: the batched result (Stockham FP32 passes) and the plain one both
+    converge to relres <= 1e-10 and agree within the mixed tolerance."""
+    import torch
+    specs = sorted((s for s in I.batch_specs(64) if s.nx in R_LENGTHS or s.ny in R_LENGTHS),
+                   key=lambda s: s.nx * s.ny * s.nz)[:3]
+    assert specs
+    cases = [I.make_case(s) for s in specs]
+    assert all(plain_differs(c, F.MIXED) for c in cases)
+    plans = [F.Plan.for_case(c, precision=F.MIXED) for c in cases]
+    arrays = [(to_dev(c.phi), to_dev(c.pn), to_dev(c.pnm1), to_dev(c.u), to_dev(c.v), to_dev(c.w),
+               torch.empty(c.shape, dtype=torch.float64, device="cuda")) for c in cases]
+    batch = F.Batch(plans, arrays)
+    batch.solve()
+    assert batch.status() == 0
+    for c, arr, plan in zip(cases, arrays, plans):
+        assert plan.stats()["converged"] == 1
+        a = run_plain(c, F.MIXED)
+        assert a["stats"]["converged"] == 1 and a["stats"]["relres"] <= 1e-10
+        got = dict(p=arr[6].cpu().numpy(), u=arr[3].cpu().numpy(), v=arr[4].cpu().numpy(),
+                   w=arr[5].cpu().numpy())
+        ep, eu = compare(c, got, a)
+        assert ep <= 1e-9 and eu <= 1e-9, (c.spec, ep, eu)
     batch.close()
     for p in plans:
         p.close()

@@ -74,6 +74,18 @@ def small_cases():
                                     radius_cells=3, config=32),
         "b512x3x3_wxy": I.CaseSpec(nx=512, ny=3, nz=3, bcx=1, bcy=1, n_bubbles=1, radius_cells=1,
                                    config=33),
+        # length 128 (the 16 x 8 transform, 4 lines per warp) and 64 (the
+        # Stockham passes): walls and periodic, odd nx, ragged y tiles, odd
+        # line counts
+        "b27x64x9_wy": I.CaseSpec(nx=27, ny=64, nz=9, bcx=0, bcy=1, beta=1.3, n_bubbles=1,
+                                  radius_cells=3, config=34),
+        "b36x128x10": I.CaseSpec(nx=36, ny=128, nz=10, bcx=1, bcy=0, n_bubbles=2, radius_cells=3,
+                                 config=35),
+        "b64x9x7": I.CaseSpec(nx=64, ny=9, nz=7, bcx=0, bcy=1, n_bubbles=1, radius_cells=2, config=36),
+        "b128x6x5_wx": I.CaseSpec(nx=128, ny=6, nz=5, bcx=1, bcy=0, beta=1.5, n_bubbles=1,
+                                  radius_cells=2, config=37),
+        "b64x128x16_w": I.CaseSpec(nx=64, ny=128, nz=16, bcx=1, bcy=1, n_bubbles=2, radius_cells=4,
+                                   config=38),
         # light drops in a heavy phase: rho0 = rho_l, split term from 1 - phi
         "b48x32x24_swapped": I.CaseSpec(nx=48, ny=32, nz=24, bcx=0, bcy=1, beta=1.5, n_bubbles=3,
                                         radius_cells=4, rho_l=1e-3, rho_g=1.0, config=19),
@@ -101,7 +113,9 @@ def test_fp64_matches_oracle(cuda_ok, name):
                                   "b384x6x5", "b81x3x7_nn", "b48x32x24_swapped", "b512x8x5",
                                   "b48x256x12", "b27x256x6_wx", "b256x12x10", "b256x9x5_wy",
                                   "b6x512x4", "b24x512x8", "b9x512x3", "b512x3x3_wy",
-                                  "b48x256x12_wy", "b256x12x10_wx", "b24x512x8_wxy", "b512x3x3_wxy"])
+                                  "b48x256x12_wy", "b256x12x10_wx", "b24x512x8_wxy", "b512x3x3_wxy",
+                                  "b27x64x9_wy", "b36x128x10", "b64x9x7", "b128x6x5_wx",
+                                  "b64x128x16_w"])
 def test_mixed_matches_oracle(cuda_ok, name):
     c = I.make_case(CASES[name])
     ref = O.project_case(c)
@@ -118,7 +132,8 @@ def test_mixed_matches_oracle(cuda_ok, name):
 
 @pytest.mark.parametrize("name", ["b48x256x12", "b27x256x6_wx", "b256x12x10", "b256x9x5_wy",
                                   "b24x512x8", "b512x8x5", "b48x256x12_wy", "b256x12x10_wx",
-                                  "b24x512x8_wxy", "b96x64x33"])
+                                  "b24x512x8_wxy", "b27x64x9_wy", "b128x6x5_wx", "b64x128x16_w",
+                                  "b96x64x33"])
 def test_fp32_solve_accuracy(cuda_ok, name):
     """The FP32 solve alone (stopped at its first residual) is accurate to
     FP32 level, whichever transform kernels it runs: the Stockham and the
