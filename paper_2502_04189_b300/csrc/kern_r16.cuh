@@ -1,22 +1,22 @@
-// Register-resident FP32 transforms of periodic length 256 and 512 (mixed mode).
+// Register-resident FP32 transforms of length 128, 256 and 512 (mixed mode).
 //
 // The FP32 transform passes of the mixed-precision solve (Sec. 3.2: real
-// FFTs along the periodic directions) for n = 256 and 512.  The DFT of length
-// 256 is split as 16 x 16 (the four-step form of the Cooley-Tukey
-// factorisation): with n = 16 n1 + n2 and k = k1 + 16 k2,
-//     X[k1 + 16 k2] = sum_n2 W16^(n2 k2) [ W256^(n2 k1) sum_n1 x[16 n1 + n2] W16^(n1 k1) ],
+// FFTs, or DCT-II for wall directions, along x and y).  A DFT of length
+// N = 16 M (M = 8, 16; 4 builds too) is split 16 x M, the four-step form of
+// the Cooley-Tukey factorisation: with n = M n1 + n2 and k = k1 + 16 k2,
+//     X[k1 + 16 k2] = sum_n2 WM^(n2 k2) [ WN^(n2 k1) sum_n1 x[M n1 + n2] W16^(n1 k1) ],
 // W_N = exp(-2 pi i / N) (the inverse uses the conjugates; neither direction
-// is scaled).  A complex line (two real columns, real and imaginary part) is
-// held by 16 threads: thread t first owns the samples x[16 n1 + t],
-// computes their 16-point DFT in registers and applies the twiddles
-// W256^(t k1); one pass through shared
-// memory then hands thread t the values of k1 = t, whose 16-point DFT gives
-// X[t + 16 k2].  The separation of the two real spectra (forward) pairs X[k]
-// with X[256 - k], held by thread (16 - t) mod 16 of the same line, through
-// warp shuffles; the inverse combination reads both rows of a pair.  The
-// tile is staged through shared memory with one 128-byte row segment per
-// warp access (a load straight into the per-thread order would touch 16 rows
-// per warp instruction).
+// is scaled).  A complex line (two real lines as real and imaginary part) is
+// held by M threads: thread t owns the samples x[M n1 + t], computes their
+// 16-point DFT in registers and applies the twiddles WN^(t k1); one pass
+// through shared memory then hands it the values of k1 = t + M j, whose
+// M-point DFTs give X[t + M j + 16 k2].  The separation of the two real
+// spectra (forward) pairs X[k] with X[N - k], held in register 15 - r of
+// thread (M - t) mod M of the same line, through warp shuffles; the inverse
+// combination reads both values of a pair.  A wall direction keeps
+// Makhoul's packing of the DCT-II (even samples forward, odd backward) and
+// applies the post-twiddles (cos, sin)(pi m / (2N)) in the separation and
+// combination.
 //
 // Length 512 first takes one radix-2 step of decimation in frequency,
 //     X[2k]     = DFT256( x[n] + x[n + 256] )[k],
