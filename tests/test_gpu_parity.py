@@ -86,6 +86,10 @@ def small_cases():
                                   radius_cells=2, config=37),
         "b64x128x16_w": I.CaseSpec(nx=64, ny=128, nz=16, bcx=1, bcy=1, n_bubbles=2, radius_cells=4,
                                    config=38),
+        "b128x3x3_odd": I.CaseSpec(nx=128, ny=3, nz=3, bcx=0, bcy=1, n_bubbles=1, radius_cells=1,
+                                   config=39),
+        "b27x128x5_wy": I.CaseSpec(nx=27, ny=128, nz=5, bcx=1, bcy=1, beta=1.8, n_bubbles=1,
+                                   radius_cells=2, config=42),
         # light drops in a heavy phase: rho0 = rho_l, split term from 1 - phi
         "b48x32x24_swapped": I.CaseSpec(nx=48, ny=32, nz=24, bcx=0, bcy=1, beta=1.5, n_bubbles=3,
                                         radius_cells=4, rho_l=1e-3, rho_g=1.0, config=19),
@@ -115,7 +119,7 @@ def test_fp64_matches_oracle(cuda_ok, name):
                                   "b6x512x4", "b24x512x8", "b9x512x3", "b512x3x3_wy",
                                   "b48x256x12_wy", "b256x12x10_wx", "b24x512x8_wxy", "b512x3x3_wxy",
                                   "b27x64x9_wy", "b36x128x10", "b64x9x7", "b128x6x5_wx",
-                                  "b64x128x16_w"])
+                                  "b64x128x16_w", "b128x3x3_odd", "b27x128x5_wy"])
 def test_mixed_matches_oracle(cuda_ok, name):
     c = I.make_case(CASES[name])
     ref = O.project_case(c)
