@@ -75,16 +75,23 @@ struct GridDev {
 
 // Mixed-mode stopping rule, evaluated by one thread once max|r| is known:
 // relres <= tol and, unless disabled, the divergence the correction will
-// leave, max|D u| dx / U = (dt/rho0) max|r| dx / U, <= div_tol.
+// leave, max|D u| dx / U = (dt/rho0) max|r| dx / U, <= div_tol.  The
+// divergence rule is a bound through the FP64 residual, whose own rounding
+// (about eps max|p| / h^2 of the stencil terms) can exceed div_tol U when U
+// is small against the pressure correction; once a sweep no longer halves
+// max|r| (rmax_prev >= 0: the previous evaluation) the residual is at that
+// floor and further sweeps cannot lower it, so the solve stops there (the
+// divergence it reached is measured after the correction, div_metric).
 template <bool CG>
 __device__ __forceinline__ bool refine_done(const GridDev &g, double rmax, double fmax, double tol,
-                                            double *rel_out) {
+                                            double rmax_prev, double *rel_out) {
     const double rel = fmax > 0.0 ? rmax / fmax : rmax;
     *rel_out = rel;
     if (!(rel <= tol)) return false;
     if (g.div_tol < 0.0) return true;
     const double U = sqrt((CG ? __ldcg(g.usq) : *g.usq) * g.inv_3n);
-    return U > 0.0 ? rmax * g.div_scale / U <= g.div_tol : rmax == 0.0;
+    if (U > 0.0 ? rmax * g.div_scale / U <= g.div_tol : rmax == 0.0) return true;
+    return rmax_prev >= 0.0 && rmax > 0.5 * rmax_prev;  // stagnated at the evaluation floor
 }
 
 __device__ __forceinline__ size_t cidx(const GridDev &g, int i, int j, int k) {
@@ -1118,8 +1125,11 @@ __device__ __forceinline__ void resid_body(const GridDev &g, int kc, const RArgs
         const unsigned long long rb = atomicMax(&a.st->rmax_bits[a.slot], 0ull);
         const unsigned long long fb = atomicMax(&a.st->fmax_bits, 0ull);
         double rel;
+        const double prev = a.slot > 0
+                                ? __longlong_as_double((long long)atomicMax(&a.st->rmax_bits[a.slot - 1], 0ull))
+                                : -1.0;
         const bool done = refine_done<CG>(g, __longlong_as_double((long long)rb),
-                                          __longlong_as_double((long long)fb), a.tol, &rel);
+                                          __longlong_as_double((long long)fb), a.tol, prev, &rel);
         a.st->relres = rel;
         a.st->n_resid = a.slot + 1;
         a.st->iterations = a.slot;

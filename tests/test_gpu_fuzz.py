@@ -1,0 +1,78 @@
+"""Seeded random configurations against the FP64 oracle (needs a B300).
+
+Sizes are products of 2 and 3 (including the register-resident length 128
+and odd lengths such as 3, 9, 27), boundaries, stretching, density ratio,
+drop count, velocity recipe and the phase that is light all drawn at random;
+every case must meet the same bars as the named parity cases: FP64 <= 1e-12,
+mixed <= 1e-9 after refinement, divergence <= 1e-10.
+
+Some draws are pressure-dominated: the correction (dt/rho0) G p is up to
+1e3 times max|u| (a 2-cell direction with a weak velocity field).  A p that
+agrees with the oracle to round-off then moves u by (dt/rho0) 2 eps max|p| /
+h_min through the gradient, which can exceed 1e-12 of max|u| for any FP64
+solver; the velocity bar is the larger of 1e-12 and ten times that floor,
+computed from the oracle's fields (the floor is reported beside the error)."""
+import numpy as np
+import pytest
+
+import oracle as O
+import paper_2502_04189_b300 as F
+from paper_2502_04189_b300 import inputs as I
+
+from gpu_util import compare, gpu_project
+
+pytestmark = pytest.mark.gpu
+
+LENGTHS = (2, 3, 4, 6, 8, 9, 12, 16, 18, 24, 27, 32, 36, 48, 54, 64, 72, 96, 128)
+
+
+def fuzz_specs(n=24, seed=2024):
+    rng = np.random.default_rng(seed)
+    out = []
+    while len(out) < n:
+        nx, ny = int(rng.choice(LENGTHS)), int(rng.choice(LENGTHS))
+        nz = int(rng.integers(2, 41))
+        if nx * ny * nz > 160_000:  # keep the oracle to a fraction of a second
+            continue
+        light_drops = bool(rng.random() < 0.7)
+        ratio = float(10 ** rng.uniform(0, 3))
+        rho_g, rho_l = (1.0 / ratio, 1.0) if light_drops else (1.0, 1.0 / ratio)
+        out.append(I.CaseSpec(
+            nx=nx, ny=ny, nz=nz, bcx=int(rng.integers(0, 2)), bcy=int(rng.integers(0, 2)),
+            beta=float(rng.uniform(0.5, 2.0)) if rng.random() < 0.5 else 0.0,
+            n_bubbles=int(rng.integers(1, 4)), radius_cells=float(rng.uniform(0.5, 4.0)),
+            rho_l=rho_l, rho_g=rho_g, dt=float(10 ** rng.uniform(-4, -2)),
+            velocity="iid" if rng.random() < 0.3 else "solenoidal",
+            config=60, instance=len(out)))
+    return out
+
+
+SPECS = fuzz_specs()
+
+
+def velocity_floor(case, ref):
+    """Relative velocity change caused by a one-ulp change of p."""
+    s = case.spec
+    g = O.Grid.of_case(case)
+    rho0 = min(s.rho_l, s.rho_g)
+    pmax = np.max(np.abs(ref["p"] - O.weighted_mean(g, ref["p"])))
+    hmin = min(case.dx, case.dy, float(np.diff(case.zf).min()))
+    umax = max(np.max(np.abs(ref[k])) for k in "uvw")
+    return s.dt / rho0 * 2 * np.finfo(np.float64).eps * pmax / hmin / umax
+
+
+@pytest.mark.parametrize("i", range(len(SPECS)))
+def test_fuzz_matches_oracle(cuda_ok, i):
+    c = I.make_case(SPECS[i])
+    ref = O.project_case(c)
+    floor = velocity_floor(c, ref)
+    got = gpu_project(c, F.FP64)
+    ep, eu = compare(c, got, ref)
+    assert ep <= 1e-12 and eu <= max(1e-12, 10 * floor), (SPECS[i], ep, eu, floor)
+    assert got["stats"]["div_metric"] <= 1e-10, SPECS[i]
+    got = gpu_project(c, F.MIXED)
+    st = got["stats"]
+    assert st["converged"] == 1 and st["relres"] <= 1e-10, (SPECS[i], st)
+    ep, eu = compare(c, got, ref)
+    assert ep <= 1e-9 and eu <= max(1e-9, 10 * floor), (SPECS[i], ep, eu, floor)
+    assert st["div_metric"] <= 1e-10, SPECS[i]
