@@ -40,3 +40,47 @@ def compare(case, got, ref):
     ug = np.concatenate([got[k].ravel() for k in "uvw"])
     ur = np.concatenate([ref[k].ravel() for k in "uvw"])
     return relerr(pg, pr), relerr(ug, ur)
+
+
+# ---- one instance solved alone, as the batched executor solves it
+
+R_LENGTHS = (128, 256, 512)  # register-resident FP32 passes in plain mixed solves
+
+
+def plain_differs(case, precision):
+    s = case.spec
+    return precision == F.MIXED and (s.nx in R_LENGTHS or s.ny in R_LENGTHS)
+
+
+def run_plain(case, precision, **kw):
+    import torch
+    plan = F.Plan.for_case(case, precision=precision, **kw)
+    u, v, w = to_dev(case.u), to_dev(case.v), to_dev(case.w)
+    p = torch.empty_like(u)
+    plan.solve(to_dev(case.phi), to_dev(case.pn), to_dev(case.pnm1), u, v, w, p)
+    torch.cuda.synchronize()
+    st = plan.stats()
+    plan.close()
+    return dict(p=p.cpu().numpy(), u=u.cpu().numpy(), v=v.cpu().numpy(), w=w.cpu().numpy(), stats=st)
+
+
+def run_batched_alone(case, precision, **kw):
+    import torch
+    plan = F.Plan.for_case(case, precision=precision, **kw)
+    arr = (to_dev(case.phi), to_dev(case.pn), to_dev(case.pnm1), to_dev(case.u), to_dev(case.v),
+           to_dev(case.w), torch.empty(case.shape, dtype=torch.float64, device="cuda"))
+    batch = F.Batch([plan], [arr])
+    batch.solve()
+    assert batch.status() == 0
+    out = dict(p=arr[6].cpu().numpy(), u=arr[3].cpu().numpy(), v=arr[4].cpu().numpy(),
+               w=arr[5].cpu().numpy(), stats=plan.stats())
+    batch.close()
+    plan.close()
+    return out
+
+
+def run_alone(case, precision, **kw):
+    """The instance solved by itself with the passes the batch runs."""
+    if plain_differs(case, precision):
+        return run_batched_alone(case, precision, **kw)
+    return run_plain(case, precision, **kw)

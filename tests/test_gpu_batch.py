@@ -17,7 +17,7 @@ import oracle as O
 import paper_2502_04189_b300 as F
 from paper_2502_04189_b300 import inputs as I
 
-from gpu_util import compare, to_dev
+from gpu_util import R_LENGTHS, compare, plain_differs, run_alone, run_plain, to_dev
 
 pytestmark = pytest.mark.gpu
 
@@ -26,48 +26,6 @@ def small_batch_specs(k=6):
     specs = I.batch_specs(64)
     specs.sort(key=lambda s: s.nx * s.ny * s.nz)
     return specs[:k - 1] + [specs[20]]  # the smallest ones plus one mid-size
-
-
-R_LENGTHS = (128, 256, 512)  # register-resident FP32 passes in plain mixed solves
-
-
-def plain_differs(case, precision):
-    s = case.spec
-    return precision == F.MIXED and (s.nx in R_LENGTHS or s.ny in R_LENGTHS)
-
-
-def run_plain(case, precision, **kw):
-    import torch
-    plan = F.Plan.for_case(case, precision=precision, **kw)
-    u, v, w = to_dev(case.u), to_dev(case.v), to_dev(case.w)
-    p = torch.empty_like(u)
-    plan.solve(to_dev(case.phi), to_dev(case.pn), to_dev(case.pnm1), u, v, w, p)
-    torch.cuda.synchronize()
-    st = plan.stats()
-    plan.close()
-    return dict(p=p.cpu().numpy(), u=u.cpu().numpy(), v=v.cpu().numpy(), w=w.cpu().numpy(), stats=st)
-
-
-def run_batched_alone(case, precision, **kw):
-    import torch
-    plan = F.Plan.for_case(case, precision=precision, **kw)
-    arr = (to_dev(case.phi), to_dev(case.pn), to_dev(case.pnm1), to_dev(case.u), to_dev(case.v),
-           to_dev(case.w), torch.empty(case.shape, dtype=torch.float64, device="cuda"))
-    batch = F.Batch([plan], [arr])
-    batch.solve()
-    assert batch.status() == 0
-    out = dict(p=arr[6].cpu().numpy(), u=arr[3].cpu().numpy(), v=arr[4].cpu().numpy(),
-               w=arr[5].cpu().numpy(), stats=plan.stats())
-    batch.close()
-    plan.close()
-    return out
-
-
-def run_alone(case, precision, **kw):
-    """The instance solved by itself with the passes the batch runs."""
-    if plain_differs(case, precision):
-        return run_batched_alone(case, precision, **kw)
-    return run_plain(case, precision, **kw)
 
 
 @pytest.mark.parametrize("precision", [F.MIXED, F.FP64], ids=["mixed", "fp64"])

@@ -19,7 +19,7 @@ import oracle as O
 import paper_2502_04189_b300 as F
 from paper_2502_04189_b300 import inputs as I
 
-from gpu_util import compare, gpu_project
+from gpu_util import compare, gpu_project, run_alone, to_dev
 
 pytestmark = pytest.mark.gpu
 
@@ -76,3 +76,26 @@ def test_fuzz_matches_oracle(cuda_ok, i):
     ep, eu = compare(c, got, ref)
     assert ep <= 1e-9 and eu <= max(1e-9, 10 * floor), (SPECS[i], ep, eu, floor)
     assert st["div_metric"] <= 1e-10, SPECS[i]
+
+
+@pytest.mark.parametrize("precision", [F.FP64, F.MIXED], ids=["fp64", "mixed"])
+@pytest.mark.parametrize("seed", [7, 8])
+def test_fuzz_batch_equals_alone(cuda_ok, precision, seed):
+    """Random mixes of eight of these instances in one persistent launch:
+    each equals the same instance solved alone, bit for bit."""
+    import torch
+    specs = fuzz_specs(8, seed=seed)
+    cases = [I.make_case(s) for s in specs]
+    alone = [run_alone(c, precision) for c in cases]
+    plans = [F.Plan.for_case(c, precision=precision) for c in cases]
+    arrays = [(to_dev(c.phi), to_dev(c.pn), to_dev(c.pnm1), to_dev(c.u), to_dev(c.v), to_dev(c.w),
+               torch.empty(c.shape, dtype=torch.float64, device="cuda")) for c in cases]
+    batch = F.Batch(plans, arrays)
+    batch.solve()
+    assert batch.status() == 0
+    for c, arr, a in zip(cases, arrays, alone):
+        for key, t in (("p", arr[6]), ("u", arr[3]), ("v", arr[4]), ("w", arr[5])):
+            assert np.array_equal(t.cpu().numpy(), a[key]), (c.spec, key)
+    batch.close()
+    for p in plans:
+        p.close()
