@@ -227,6 +227,17 @@ int fizzy_proj_batch_solve(fizzy_proj_batch_t b, void *stream);
  * FIZZY_ERR_TIMEOUT if a dependency wait gave up (outputs then invalid). */
 int fizzy_proj_batch_status(fizzy_proj_batch_t b, void *stream);
 
+/* Test support for the timeout path (no GPU fault): rebuild the batch graph
+ * so that the first dependency wait of instance inst (0 <= inst < n) can
+ * never be met, and every dependency wait gives up after spin_limit polls
+ * (each about 64 ns; 1 <= spin_limit <= 2^26).  The next solve then ends
+ * normally and fizzy_proj_batch_status returns FIZZY_ERR_TIMEOUT (outputs of
+ * that solve invalid); the context stays usable.  inst = -1 and
+ * spin_limit = 0 restore the defaults (no stall, 2^26 polls).  Returns
+ * FIZZY_ERR_INVALID for a null batch or out-of-range arguments, else the
+ * status of the rebuild. */
+int fizzy_proj_batch_inject_stall(fizzy_proj_batch_t b, int inst, long long spin_limit);
+
 /* Time candidate tunings (reps replays each, CUDA events on stream), rebuild
  * the batch with the fastest and return it in *chosen and its mean time in
  * *best_ms (either may be NULL).  The candidates vary CTAs per SM, flux

@@ -240,6 +240,14 @@ class Batch:
             raise FizzyError(rc)
         return t.as_dict(), ms.value
 
+    def inject_stall(self, inst=-1, spin_limit=0):
+        """Test support (fizzy_proj_batch_inject_stall): instance inst's first
+        dependency wait never completes and every wait gives up after
+        spin_limit polls; inject_stall() restores the defaults."""
+        rc = _abi.lib().fizzy_proj_batch_inject_stall(self._h, int(inst), int(spin_limit))
+        if rc != 0:
+            raise FizzyError(rc)
+
     def info(self):
         n, g, sm = ctypes.c_int(), ctypes.c_int(), ctypes.c_size_t()
         _abi.lib().fizzy_proj_batch_info(self._h, ctypes.byref(n), ctypes.byref(g), ctypes.byref(sm))

@@ -21,7 +21,7 @@ EXPORTED = ("fizzy_proj_plan", "fizzy_proj_workspace_bytes", "fizzy_proj_solve",
             "fizzy_proj_set_physics", "fizzy_serve_create", "fizzy_serve_admit", "fizzy_serve_stream",
             "fizzy_serve_launch", "fizzy_serve_poll", "fizzy_serve_stats", "fizzy_serve_release",
             "fizzy_serve_info", "fizzy_serve_destroy", "fizzy_proj_solve_host_async",
-            "fizzy_proj_host_wait", "fizzy_crop_fill")
+            "fizzy_proj_host_wait", "fizzy_crop_fill", "fizzy_proj_batch_inject_stall")
 ERRORS[-7] = "busy"
 NOALLOC_MAX_CELLS = 262144
 DEFAULT_MAX_REFINE = 4  # FIZZY_DEFAULT_MAX_REFINE
@@ -110,6 +110,8 @@ def lib():
         L.fizzy_proj_batch_info.argtypes = [vp, ctypes.POINTER(ctypes.c_int),
                                             ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_size_t)]
         L.fizzy_proj_batch_info.restype = ctypes.c_int
+        L.fizzy_proj_batch_inject_stall.argtypes = [vp, ctypes.c_int, ctypes.c_longlong]
+        L.fizzy_proj_batch_inject_stall.restype = ctypes.c_int
         L.fizzy_proj_batch_destroy.argtypes = [vp]
         L.fizzy_proj_batch_destroy.restype = ctypes.c_int
         D = ctypes.c_double

@@ -96,6 +96,7 @@ struct BatchArgs {
     int *done;       // [n_inst][BATCH_MAXP] completed tiles
     int *status;     // 0 or FIZZY-style negative code
     long long spin_limit;
+    int stall_inst;  // test support: this instance's first dependency never completes (-1: none)
 };
 
 __device__ __forceinline__ void batch_run_tile(const BatchInst &I, const BatchItem &w, int tile,
@@ -235,7 +236,7 @@ __global__ void __launch_bounds__(BATCH_THREADS, 5) k_batch(BatchArgs A) {
             // last tile of a residual pass, and never cleared in the launch)
             if (refine && *(const volatile int *)&I.st->converged) ok = 0;
             else if (w.pass > 0) {
-                const int need = I.tiles[w.pass - 1];
+                const int need = (w.inst == A.stall_inst && w.pass == 1) ? INT_MAX : I.tiles[w.pass - 1];
                 const volatile int *cnt = A.done + (size_t)w.inst * BATCH_MAXP + (w.pass - 1);
                 long long spins = 0;
                 while (*cnt < need) {

@@ -79,6 +79,10 @@ def test_crop_fill_rejects_bad_arguments():
         assert call(**bad) == -1, bad
 
 
+def test_inject_stall_rejects_a_null_batch():
+    assert _abi.lib().fizzy_proj_batch_inject_stall(None, 0, 1) == -1
+
+
 def test_workspace_bytes_scale():
     b1 = F.workspace_bytes(**base())
     b2 = F.workspace_bytes(**base(nz=16))

@@ -178,3 +178,32 @@ def test_batch_mixed_matches_plain_within_tolerance(cuda_ok):
     batch.close()
     for p in plans:
         p.close()
+
+
+def test_batch_wait_timeout_is_reported_and_recoverable(cuda_ok):
+    """A dependency wait that can never be met gives up after its poll limit:
+    the launch ends, the status is FIZZY_ERR_TIMEOUT, and after restoring the
+    defaults the same batch solves correctly (no GPU fault, context usable)."""
+    import torch
+    cases = [I.make_case(s) for s in small_batch_specs(3)]
+    alone = [run_alone(c, F.FP64) for c in cases]
+    plans = [F.Plan.for_case(c, precision=F.FP64) for c in cases]
+    arrays = [(to_dev(c.phi), to_dev(c.pn), to_dev(c.pnm1), to_dev(c.u), to_dev(c.v), to_dev(c.w),
+               torch.empty(c.shape, dtype=torch.float64, device="cuda")) for c in cases]
+    batch = F.Batch(plans, arrays)
+    batch.inject_stall(inst=1, spin_limit=1 << 12)
+    batch.solve()
+    assert batch.status() == -6  # FIZZY_ERR_TIMEOUT
+    batch.inject_stall()
+    for c, arr in zip(cases, arrays):
+        arr[3].copy_(to_dev(c.u))
+        arr[4].copy_(to_dev(c.v))
+        arr[5].copy_(to_dev(c.w))
+    batch.solve()
+    assert batch.status() == 0
+    for c, arr, a in zip(cases, arrays, alone):
+        for key, t in (("p", arr[6]), ("u", arr[3]), ("v", arr[4]), ("w", arr[5])):
+            assert np.array_equal(t.cpu().numpy(), a[key]), (c.spec, key)
+    batch.close()
+    for p in plans:
+        p.close()
