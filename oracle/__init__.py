@@ -51,7 +51,7 @@ def lib():
                 L = ctypes.CDLL(_LIB)
             d = ctypes.POINTER(ctypes.c_double)
             I, D = ctypes.c_int, ctypes.c_double
-            g = [I, I, I, D, D, d, I, I]
+            g = [I, I, I, D, D, d, I, I, I]  # nx ny nz dx dy zf bcx bcy bcz
             L.ora_grad.argtypes = g + [d, d, d, d]
             L.ora_div.argtypes = g + [d, d, d, d]
             L.ora_apply_L.argtypes = g + [d, d]
@@ -81,26 +81,29 @@ def _c(a):
 
 
 class Grid:
-    """Grid of nx*ny*nz cells; zf = nz+1 z face coordinates; bcx/bcy 0 periodic, 1 walls."""
+    """Grid of nx*ny*nz cells; zf = nz+1 z face coordinates; bcx/bcy/bcz 0 periodic,
+    1 walls (z defaults to walls)."""
 
-    def __init__(self, nx, ny, nz, dx, dy, zf, bcx=PERIODIC, bcy=PERIODIC):
+    def __init__(self, nx, ny, nz, dx, dy, zf, bcx=PERIODIC, bcy=PERIODIC, bcz=NEUMANN):
         self.nx, self.ny, self.nz = int(nx), int(ny), int(nz)
         self.dx, self.dy = float(dx), float(dy)
         self.zf = _c(zf)
         assert self.zf.shape == (self.nz + 1,)
-        self.bcx, self.bcy = int(bcx), int(bcy)
+        self.bcx, self.bcy, self.bcz = int(bcx), int(bcy), int(bcz)
 
     @property
     def shape(self):
         return (self.nz, self.ny, self.nx)
 
     def args(self):
-        return (self.nx, self.ny, self.nz, self.dx, self.dy, _p(self.zf), self.bcx, self.bcy)
+        return (self.nx, self.ny, self.nz, self.dx, self.dy, _p(self.zf), self.bcx, self.bcy,
+                self.bcz)
 
     @classmethod
     def of_case(cls, case):
         s = case.spec
-        return cls(s.nx, s.ny, s.nz, case.dx, case.dy, case.zf, s.bcx, s.bcy)
+        return cls(s.nx, s.ny, s.nz, case.dx, case.dy, case.zf, s.bcx, s.bcy,
+                   getattr(s, "bcz", NEUMANN))
 
 
 def grad(g: Grid, q):

@@ -20,11 +20,11 @@ from fractions import Fraction as Q
 
 
 class ExactGrid:
-    def __init__(self, nx, ny, nz, dx, dy, zf, bcx, bcy):
+    def __init__(self, nx, ny, nz, dx, dy, zf, bcx, bcy, bcz=1):
         self.nx, self.ny, self.nz = nx, ny, nz
         self.dx, self.dy = Q(dx), Q(dy)
         self.zf = [Q(z) for z in zf]
-        self.bcx, self.bcy = bcx, bcy
+        self.bcx, self.bcy, self.bcz = bcx, bcy, bcz
 
     def dzf(self, k):
         return self.zf[k + 1] - self.zf[k]
@@ -32,7 +32,9 @@ class ExactGrid:
     def zc(self, k):
         return (self.zf[k] + self.zf[k + 1]) / 2
 
-    def dzc(self, k):  # spacing at z-face k+1/2
+    def dzc(self, k):  # spacing at z-face k+1/2 (k = nz-1: across the periodic boundary)
+        if k == self.nz - 1:
+            return (self.dzf(0) + self.dzf(self.nz - 1)) / 2
         return self.zc(k + 1) - self.zc(k)
 
     def cells(self):
@@ -57,7 +59,10 @@ def _grad(g, q):
             gy[(i, j, k)] = (q[(i, j + 1, k)] - c) / g.dy
         else:
             gy[(i, j, k)] = (q[(i, 0, k)] - c) / g.dy if g.bcy == 0 else Q(0)
-        gz[(i, j, k)] = (q[(i, j, k + 1)] - c) / g.dzc(k) if k < g.nz - 1 else Q(0)
+        if k < g.nz - 1:
+            gz[(i, j, k)] = (q[(i, j, k + 1)] - c) / g.dzc(k)
+        else:
+            gz[(i, j, k)] = (q[(i, j, 0)] - c) / g.dzc(k) if g.bcz == 0 else Q(0)
     return gx, gy, gz
 
 
@@ -74,8 +79,11 @@ def _div(g, u, v, w):
             vs = v[(i, j - 1, k)]
         else:
             vs = v[(i, g.ny - 1, k)] if g.bcy == 0 else Q(0)
-        wt = Q(0) if k == g.nz - 1 else w[(i, j, k)]
-        wb = w[(i, j, k - 1)] if k > 0 else Q(0)
+        wt = Q(0) if (g.bcz == 1 and k == g.nz - 1) else w[(i, j, k)]
+        if k > 0:
+            wb = w[(i, j, k - 1)]
+        else:
+            wb = w[(i, j, g.nz - 1)] if g.bcz == 0 else Q(0)
         out[(i, j, k)] = (ue - uw) / g.dx + (vn - vs) / g.dy + (wt - wb) / g.dzf(k)
     return out
 
@@ -90,7 +98,8 @@ def _beta(g, rho_l, rho_g, phi):
         jn = j + 1 if j < g.ny - 1 else (0 if g.bcy == 0 else None)
         bx[c] = 1 / ((rho(c) + rho((ie, j, k))) / 2) if ie is not None else Q(0)
         by[c] = 1 / ((rho(c) + rho((i, jn, k))) / 2) if jn is not None else Q(0)
-        bz[c] = 1 / ((rho(c) + rho((i, j, k + 1))) / 2) if k < g.nz - 1 else Q(0)
+        kt = k + 1 if k < g.nz - 1 else (0 if g.bcz == 0 else None)
+        bz[c] = 1 / ((rho(c) + rho((i, j, kt))) / 2) if kt is not None else Q(0)
     return bx, by, bz
 
 
@@ -155,6 +164,6 @@ def project(g: ExactGrid, rho_l, rho_g, dt, phi, pn, pnm1, u, v, w):
             uo[c] = u[c] - dt * (px[c] / rho0 + (bx[c] - 1 / rho0) * gx[c])
         if not (g.bcy == 1 and j == g.ny - 1):
             vo[c] = v[c] - dt * (py[c] / rho0 + (by[c] - 1 / rho0) * gy[c])
-        if k < g.nz - 1:
+        if not (g.bcz == 1 and k == g.nz - 1):
             wo[c] = w[c] - dt * (pz[c] / rho0 + (bz[c] - 1 / rho0) * gz[c])
     return f, p, uo, vo, wo

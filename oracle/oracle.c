@@ -22,6 +22,10 @@
  *   u     = u* - dt [G p / rho0 + (beta_f - 1/rho0) G phat]   on every non-wall face
  *
  * G: centre-to-face gradient, D: face-to-centre divergence; wall faces are 0.
+ * A periodic z direction (the triperiodic domains of the paper's
+ * "Numerical experiments", e.g. the emulsion in homogeneous isotropic
+ * turbulence) couples plane nz-1 to plane 0 through the face nz-1/2, whose
+ * centre distance is (dzf_0 + dzf_(nz-1))/2.
  *
  * The Poisson solve is deliberately a *different* algorithm from the GPU's:
  *   - full complex DFTs in x and y by a plain recursive mixed-radix
@@ -29,14 +33,16 @@
  *   - a Neumann (wall) direction is handled by even extension to a periodic
  *     problem of twice the length, solved the same way and restricted back;
  *   - each (kx, ky) z-line is solved by Gaussian elimination with partial
- *     pivoting on the tridiagonal band; the singular (0,0) line by dense
- *     Gaussian elimination with the gauge row sum_k dzf_k p_k = 0;
+ *     pivoting on the tridiagonal band (walls in z), or by dense Gaussian
+ *     elimination of the assembled cyclic matrix (periodic z); the singular
+ *     (0,0) line by dense Gaussian elimination with the gauge row
+ *     sum_k dzf_k p_k = 0;
  *   - small grids also have a dense LU path on the assembled operator.
  *
  * Layout: double arrays [nz][ny][nx], x fastest.  u[k][j][i] is the x-face
  * i+1/2, v the y-face j+1/2, w the z-face k+1/2.  bc = 0 periodic, 1 Neumann
- * (walls); z is always wall-bounded.  In a wall direction the last face is the
- * far wall and the near wall face is implicit; both are treated as 0.
+ * (walls), in x, y and z alike.  In a wall direction the last face is the far
+ * wall and the near wall face is implicit; both are treated as 0.
  */
 #include <complex.h>
 #include <math.h>
@@ -49,21 +55,26 @@ typedef struct {
     int nx, ny, nz;
     double dx, dy;
     const double *zf; /* nz+1 face coordinates */
-    int bcx, bcy;
+    int bcx, bcy, bcz;
 } grid_t;
 
 #define IDX(g, i, j, k) (((size_t)(k) * (g)->ny + (size_t)(j)) * (g)->nx + (size_t)(i))
 
 static grid_t mkgrid(int nx, int ny, int nz, double dx, double dy, const double *zf, int bcx,
-                     int bcy) {
-    grid_t g = {nx, ny, nz, dx, dy, zf, bcx, bcy};
+                     int bcy, int bcz) {
+    grid_t g = {nx, ny, nz, dx, dy, zf, bcx, bcy, bcz};
     return g;
 }
 
 static double dzf(const grid_t *g, int k) { return g->zf[k + 1] - g->zf[k]; }
 static double zc(const grid_t *g, int k) { return 0.5 * (g->zf[k] + g->zf[k + 1]); }
-/* distance between centres k and k+1 (the spacing at z-face k+1/2) */
-static double dzc(const grid_t *g, int k) { return zc(g, k + 1) - zc(g, k); }
+/* distance between centres k and k+1 (the spacing at z-face k+1/2); for
+ * k = nz-1 in a periodic z direction, the distance from centre nz-1 across the
+ * periodic boundary to centre 0 */
+static double dzc(const grid_t *g, int k) {
+    if (k == g->nz - 1) return 0.5 * (dzf(g, 0) + dzf(g, g->nz - 1));
+    return zc(g, k + 1) - zc(g, k);
+}
 
 /* ------------------------------------------------------------------ */
 /* Staggered operators                                                  */
@@ -88,7 +99,10 @@ static void grad(const grid_t *g, const double *q, double *gx, double *gy, doubl
                 else
                     gy[c] = g->bcy == 0 ? (q[IDX(g, i, 0, k)] - q[c]) / g->dy : 0.0;
                 /* z-face k+1/2 */
-                gz[c] = (k < nz - 1) ? (q[IDX(g, i, j, k + 1)] - q[c]) / dzc(g, k) : 0.0;
+                if (k < nz - 1)
+                    gz[c] = (q[IDX(g, i, j, k + 1)] - q[c]) / dzc(g, k);
+                else
+                    gz[c] = g->bcz == 0 ? (q[IDX(g, i, j, 0)] - q[c]) / dzc(g, k) : 0.0;
             }
 }
 
@@ -107,8 +121,9 @@ static void divergence(const grid_t *g, const double *u, const double *v, const 
                 double vn = (g->bcy == 1 && j == ny - 1) ? 0.0 : v[c];
                 double vs = (j > 0) ? v[IDX(g, i, j - 1, k)]
                                     : (g->bcy == 0 ? v[IDX(g, i, ny - 1, k)] : 0.0);
-                double wt = (k == nz - 1) ? 0.0 : w[c];
-                double wb = (k > 0) ? w[IDX(g, i, j, k - 1)] : 0.0;
+                double wt = (g->bcz == 1 && k == nz - 1) ? 0.0 : w[c];
+                double wb = (k > 0) ? w[IDX(g, i, j, k - 1)]
+                                    : (g->bcz == 0 ? w[IDX(g, i, j, nz - 1)] : 0.0);
                 out[c] = (ue - uw) / g->dx + (vn - vs) / g->dy + (wt - wb) / dzf(g, k);
             }
 }
@@ -135,8 +150,9 @@ static void face_beta(const grid_t *g, double rho_l, double rho_g, const double 
                     by[c] = 1.0 / (0.5 * (rc + rn));
                 } else
                     by[c] = 0.0;
-                if (k < nz - 1) {
-                    double rt = rho_g + phi[IDX(g, i, j, k + 1)] * (rho_l - rho_g);
+                int kt = (k < nz - 1) ? k + 1 : (g->bcz == 0 ? 0 : -1);
+                if (kt >= 0) {
+                    double rt = rho_g + phi[IDX(g, i, j, kt)] * (rho_l - rho_g);
                     bz[c] = 1.0 / (0.5 * (rc + rt));
                 } else
                     bz[c] = 0.0;
@@ -166,21 +182,21 @@ static void remove_weighted_mean(const grid_t *g, double *a) {
 /* ------------------------------------------------------------------ */
 
 void ora_grad(int nx, int ny, int nz, double dx, double dy, const double *zf, int bcx, int bcy,
-              const double *q, double *gx, double *gy, double *gz) {
-    grid_t g = mkgrid(nx, ny, nz, dx, dy, zf, bcx, bcy);
+              int bcz, const double *q, double *gx, double *gy, double *gz) {
+    grid_t g = mkgrid(nx, ny, nz, dx, dy, zf, bcx, bcy, bcz);
     grad(&g, q, gx, gy, gz);
 }
 
 void ora_div(int nx, int ny, int nz, double dx, double dy, const double *zf, int bcx, int bcy,
-             const double *u, const double *v, const double *w, double *out) {
-    grid_t g = mkgrid(nx, ny, nz, dx, dy, zf, bcx, bcy);
+             int bcz, const double *u, const double *v, const double *w, double *out) {
+    grid_t g = mkgrid(nx, ny, nz, dx, dy, zf, bcx, bcy, bcz);
     divergence(&g, u, v, w, out);
 }
 
 /* L_h p = D(G p) */
 void ora_apply_L(int nx, int ny, int nz, double dx, double dy, const double *zf, int bcx, int bcy,
-                 const double *p, double *out) {
-    grid_t g = mkgrid(nx, ny, nz, dx, dy, zf, bcx, bcy);
+                 int bcz, const double *p, double *out) {
+    grid_t g = mkgrid(nx, ny, nz, dx, dy, zf, bcx, bcy, bcz);
     size_t n = (size_t)nx * ny * nz;
     double *gx = malloc(n * sizeof(double)), *gy = malloc(n * sizeof(double)),
            *gz = malloc(n * sizeof(double));
@@ -192,16 +208,16 @@ void ora_apply_L(int nx, int ny, int nz, double dx, double dy, const double *zf,
 }
 
 double ora_weighted_mean(int nx, int ny, int nz, const double *zf, const double *a) {
-    grid_t g = mkgrid(nx, ny, nz, 1.0, 1.0, zf, 0, 0);
+    grid_t g = mkgrid(nx, ny, nz, 1.0, 1.0, zf, 0, 0, 1);
     return weighted_mean(&g, a);
 }
 
 /* Split right-hand side: f = (rho0/dt) D(u*) + D[(1 - rho0 beta_f) G phat], then the
  * dzf-weighted mean is removed. */
 void ora_rhs(int nx, int ny, int nz, double dx, double dy, const double *zf, int bcx, int bcy,
-             double rho_l, double rho_g, double dt, const double *phi, const double *pn,
+             int bcz, double rho_l, double rho_g, double dt, const double *phi, const double *pn,
              const double *pnm1, const double *u, const double *v, const double *w, double *f) {
-    grid_t g = mkgrid(nx, ny, nz, dx, dy, zf, bcx, bcy);
+    grid_t g = mkgrid(nx, ny, nz, dx, dy, zf, bcx, bcy, bcz);
     size_t n = (size_t)nx * ny * nz;
     double rho0 = rho_l < rho_g ? rho_l : rho_g;
     double *ph = malloc(n * sizeof(double));
@@ -234,9 +250,9 @@ void ora_rhs(int nx, int ny, int nz, double dx, double dy, const double *zf, int
 
 /* u = u* - dt [G p / rho0 + (beta_f - 1/rho0) G phat] on non-wall faces (in place). */
 void ora_correct(int nx, int ny, int nz, double dx, double dy, const double *zf, int bcx, int bcy,
-                 double rho_l, double rho_g, double dt, const double *phi, const double *pn,
+                 int bcz, double rho_l, double rho_g, double dt, const double *phi, const double *pn,
                  const double *pnm1, const double *p, double *u, double *v, double *w) {
-    grid_t g = mkgrid(nx, ny, nz, dx, dy, zf, bcx, bcy);
+    grid_t g = mkgrid(nx, ny, nz, dx, dy, zf, bcx, bcy, bcz);
     size_t n = (size_t)nx * ny * nz;
     double rho0 = rho_l < rho_g ? rho_l : rho_g;
     double *ph = malloc(n * sizeof(double));
@@ -258,7 +274,8 @@ void ora_correct(int nx, int ny, int nz, double dx, double dy, const double *zf,
                     u[c] -= dt * (px[c] / rho0 + (bx[c] - 1.0 / rho0) * hx[c]);
                 if (!(bcy == 1 && j == ny - 1))
                     v[c] -= dt * (py[c] / rho0 + (by[c] - 1.0 / rho0) * hy[c]);
-                if (k < nz - 1) w[c] -= dt * (pz[c] / rho0 + (bz[c] - 1.0 / rho0) * hz[c]);
+                if (!(g.bcz == 1 && k == nz - 1))
+                    w[c] -= dt * (pz[c] / rho0 + (bz[c] - 1.0 / rho0) * hz[c]);
             }
     free(ph);
     free(px);
@@ -450,13 +467,27 @@ static int dense_gepp(int n, double *A, cplx *b) {
 /* Poisson solve D G p = f                                               */
 /* ------------------------------------------------------------------ */
 
+/* Assemble A_z + lam I (nz x nz, row major) from the coupling coefficients:
+ * row k has -(lo_k + up_k) + lam on the diagonal, lo_k in column k-1 and up_k
+ * in column k+1, both taken cyclically (lo_0 and up_(nz-1) are 0 with walls,
+ * so the wrapped entries only appear for periodic z; for nz = 2 the two
+ * couplings of a row land in the same column and add). */
+static void z_matrix(int nz, const double *lo, const double *up, double lam, double *A) {
+    memset(A, 0, sizeof(double) * (size_t)nz * nz);
+    for (int k = 0; k < nz; ++k) {
+        A[(size_t)k * nz + k] += -(lo[k] + up[k]) + lam;
+        A[(size_t)k * nz + (k + nz - 1) % nz] += lo[k];
+        A[(size_t)k * nz + (k + 1) % nz] += up[k];
+    }
+}
+
 /* Source index of extended position e in a direction of n cells:
  * periodic -> e; Neumann (extended to 2n by even reflection) -> mirror. */
 static int ext_src(int e, int n, int bc) { return (bc == 0 || e < n) ? e : 2 * n - 1 - e; }
 
 int ora_poisson_fft(int nx, int ny, int nz, double dx, double dy, const double *zf, int bcx,
-                    int bcy, const double *f, double *p) {
-    grid_t g = mkgrid(nx, ny, nz, dx, dy, zf, bcx, bcy);
+                    int bcy, int bcz, const double *f, double *p) {
+    grid_t g = mkgrid(nx, ny, nz, dx, dy, zf, bcx, bcy, bcz);
     int mx = bcx == 0 ? nx : 2 * nx; /* extent of the periodic problem */
     int my = bcy == 0 ? ny : 2 * ny;
     size_t plane = (size_t)mx * my;
@@ -506,29 +537,42 @@ int ora_poisson_fft(int nx, int ny, int nz, double dx, double dy, const double *
         double s = sin(M_PI * (double)b / (double)my);
         lam_y[b] = -4.0 / (dy * dy) * s * s;
     }
+    /* z coefficients: lo[k] couples p_k to p_(k-1), up[k] to p_(k+1); with
+       periodic z, lo[0] couples plane 0 to plane nz-1 and up[nz-1] plane nz-1
+       to plane 0 (both through the face nz-1/2), with walls both are 0 */
     double *lo = malloc(sizeof(double) * nz), *up = malloc(sizeof(double) * nz);
     for (int k = 0; k < nz; ++k) {
-        lo[k] = (k > 0) ? 1.0 / (dzf(&g, k) * dzc(&g, k - 1)) : 0.0;
-        up[k] = (k < nz - 1) ? 1.0 / (dzf(&g, k) * dzc(&g, k)) : 0.0;
+        int per = g.bcz == 0;
+        lo[k] = (k > 0) ? 1.0 / (dzf(&g, k) * dzc(&g, k - 1))
+                        : (per ? 1.0 / (dzf(&g, 0) * dzc(&g, nz - 1)) : 0.0);
+        up[k] = (k < nz - 1 || per) ? 1.0 / (dzf(&g, k) * dzc(&g, k)) : 0.0;
     }
 
 #pragma omp parallel
     {
         double *dl = malloc(sizeof(double) * nz), *d = malloc(sizeof(double) * nz),
                *du = malloc(sizeof(double) * nz), *du2 = malloc(sizeof(double) * nz);
+        double *A = g.bcz == 0 ? malloc(sizeof(double) * (size_t)nz * nz) : NULL;
         cplx *rhs = malloc(sizeof(cplx) * nz);
 #pragma omp for schedule(static) collapse(2)
         for (int b = 0; b < my; ++b)
             for (int a = 0; a < mx; ++a) {
                 if (a == 0 && b == 0) continue;
                 double lam = lam_x[a] + lam_y[b];
-                for (int k = 0; k < nz; ++k) {
-                    dl[k] = lo[k];
-                    du[k] = up[k];
-                    d[k] = -(lo[k] + up[k]) + lam;
-                    rhs[k] = F[(size_t)k * plane + (size_t)b * mx + a];
+                for (int k = 0; k < nz; ++k) rhs[k] = F[(size_t)k * plane + (size_t)b * mx + a];
+                int bad;
+                if (A) {
+                    z_matrix(nz, lo, up, lam, A);
+                    bad = dense_gepp(nz, A, rhs);
+                } else {
+                    for (int k = 0; k < nz; ++k) {
+                        dl[k] = lo[k];
+                        du[k] = up[k];
+                        d[k] = -(lo[k] + up[k]) + lam;
+                    }
+                    bad = tri_gepp(nz, dl, d, du, du2, rhs);
                 }
-                if (tri_gepp(nz, dl, d, du, du2, rhs) != 0) {
+                if (bad != 0) {
 #pragma omp atomic write
                     status = -1;
                 }
@@ -538,18 +582,15 @@ int ora_poisson_fft(int nx, int ny, int nz, double dx, double dy, const double *
         free(d);
         free(du);
         free(du2);
+        free(A);
         free(rhs);
     }
     /* (0,0): singular; rows 0..nz-2 of A_z plus the gauge row sum_k dzf_k p_k = 0 */
     {
-        double *A = calloc((size_t)nz * nz, sizeof(double));
+        double *A = malloc(sizeof(double) * (size_t)nz * nz);
         cplx *rhs = malloc(sizeof(cplx) * nz);
-        for (int k = 0; k < nz - 1; ++k) {
-            if (k > 0) A[(size_t)k * nz + k - 1] = lo[k];
-            A[(size_t)k * nz + k] = -(lo[k] + up[k]);
-            A[(size_t)k * nz + k + 1] = up[k];
-            rhs[k] = F[(size_t)k * plane];
-        }
+        z_matrix(nz, lo, up, 0.0, A);
+        for (int k = 0; k < nz - 1; ++k) rhs[k] = F[(size_t)k * plane];
         for (int k = 0; k < nz; ++k) A[(size_t)(nz - 1) * nz + k] = dzf(&g, k);
         rhs[nz - 1] = 0.0;
         if (nz == 1) A[0] = 1.0;
@@ -599,8 +640,8 @@ int ora_poisson_fft(int nx, int ny, int nz, double dx, double dy, const double *
 /* Dense path for small grids: assemble L_h column by column from ora_apply_L,
  * replace the last row by the gauge row (weights dzf_k), solve by dense GEPP. */
 int ora_poisson_dense(int nx, int ny, int nz, double dx, double dy, const double *zf, int bcx,
-                      int bcy, const double *f, double *p) {
-    grid_t g = mkgrid(nx, ny, nz, dx, dy, zf, bcx, bcy);
+                      int bcy, int bcz, const double *f, double *p) {
+    grid_t g = mkgrid(nx, ny, nz, dx, dy, zf, bcx, bcy, bcz);
     size_t n = (size_t)nx * ny * nz;
     if (n > 4096) return -2;
     double *A = calloc(n * n, sizeof(double));
@@ -608,7 +649,7 @@ int ora_poisson_dense(int nx, int ny, int nz, double dx, double dy, const double
     cplx *b = malloc(n * sizeof(cplx));
     for (size_t c = 0; c < n; ++c) {
         e[c] = 1.0;
-        ora_apply_L(nx, ny, nz, dx, dy, zf, bcx, bcy, e, col);
+        ora_apply_L(nx, ny, nz, dx, dy, zf, bcx, bcy, bcz, e, col);
         for (size_t r = 0; r < n; ++r) A[r * n + c] = col[r];
         e[c] = 0.0;
     }
@@ -645,21 +686,21 @@ static double maxabs(const double *a, size_t n) {
  * receives the right-hand side.  diag (optional, 3 doubles) receives
  * [relres = max|f - L p| / max|f|, max|D u|, max|f|].  Returns 0 on success. */
 int ora_project(int nx, int ny, int nz, double dx, double dy, const double *zf, int bcx, int bcy,
-                double rho_l, double rho_g, double dt, const double *phi, const double *pn,
+                int bcz, double rho_l, double rho_g, double dt, const double *phi, const double *pn,
                 const double *pnm1, double *u, double *v, double *w, double *p, double *f_out,
                 double *diag, int dense) {
     size_t n = (size_t)nx * ny * nz;
     double *f = malloc(n * sizeof(double)), *t = malloc(n * sizeof(double));
-    ora_rhs(nx, ny, nz, dx, dy, zf, bcx, bcy, rho_l, rho_g, dt, phi, pn, pnm1, u, v, w, f);
-    int st = dense ? ora_poisson_dense(nx, ny, nz, dx, dy, zf, bcx, bcy, f, p)
-                   : ora_poisson_fft(nx, ny, nz, dx, dy, zf, bcx, bcy, f, p);
-    ora_correct(nx, ny, nz, dx, dy, zf, bcx, bcy, rho_l, rho_g, dt, phi, pn, pnm1, p, u, v, w);
+    ora_rhs(nx, ny, nz, dx, dy, zf, bcx, bcy, bcz, rho_l, rho_g, dt, phi, pn, pnm1, u, v, w, f);
+    int st = dense ? ora_poisson_dense(nx, ny, nz, dx, dy, zf, bcx, bcy, bcz, f, p)
+                   : ora_poisson_fft(nx, ny, nz, dx, dy, zf, bcx, bcy, bcz, f, p);
+    ora_correct(nx, ny, nz, dx, dy, zf, bcx, bcy, bcz, rho_l, rho_g, dt, phi, pn, pnm1, p, u, v, w);
     if (diag) {
-        ora_apply_L(nx, ny, nz, dx, dy, zf, bcx, bcy, p, t);
+        ora_apply_L(nx, ny, nz, dx, dy, zf, bcx, bcy, bcz, p, t);
         for (size_t c = 0; c < n; ++c) t[c] = f[c] - t[c];
         double fm = maxabs(f, n);
         diag[0] = fm > 0 ? maxabs(t, n) / fm : maxabs(t, n);
-        ora_div(nx, ny, nz, dx, dy, zf, bcx, bcy, u, v, w, t);
+        ora_div(nx, ny, nz, dx, dy, zf, bcx, bcy, bcz, u, v, w, t);
         diag[1] = maxabs(t, n);
         diag[2] = fm;
     }

@@ -57,6 +57,7 @@ class CaseSpec:
     noise: float = 0.01
     config: int = 0            # seed namespace
     instance: int = 0
+    bcz: int = NEUMANN         # z: walls (default) or periodic (triperiodic boxes)
 
 
 @dataclasses.dataclass
@@ -108,8 +109,8 @@ def _place_bubbles(spec: CaseSpec, R: float, eps: float, rng) -> np.ndarray:
     lo = np.array([0.0, 0.0, 0.0])
     hi = np.array([spec.lx, spec.ly, spec.lz])
     margin = R + 2 * eps
-    # keep away from walls (z always walls; x/y when Neumann)
-    walls = [spec.bcx == NEUMANN, spec.bcy == NEUMANN, True]
+    # keep away from walls
+    walls = [spec.bcx == NEUMANN, spec.bcy == NEUMANN, spec.bcz == NEUMANN]
     for d in range(3):
         if walls[d]:
             lo[d] += margin
@@ -117,7 +118,8 @@ def _place_bubbles(spec: CaseSpec, R: float, eps: float, rng) -> np.ndarray:
         if hi[d] <= lo[d]:                    # too small: pin to the middle
             lo[d] = hi[d] = 0.5 * (lo[d] + hi[d])
     per = np.array([spec.lx if spec.bcx == PERIODIC else 0.0,
-                    spec.ly if spec.bcy == PERIODIC else 0.0, 0.0])
+                    spec.ly if spec.bcy == PERIODIC else 0.0,
+                    spec.lz if spec.bcz == PERIODIC else 0.0])
     dmin = 2 * R + 4 * eps
     centres = []
     tries = 0
@@ -161,6 +163,8 @@ def phase_field(spec: CaseSpec, dx: float, dy: float, zf: np.ndarray, rng) -> np
         if spec.bcy == PERIODIC:
             ddy -= spec.ly * np.round(ddy / spec.ly)
         ddz = zc - c[2]
+        if spec.bcz == PERIODIC:
+            ddz -= spec.lz * np.round(ddz / spec.lz)
         # only the box around the bubble matters (tanh saturates beyond ~20 eps)
         reach = R + 20 * eps
         ix = np.nonzero(np.abs(ddx) < reach)[0]
@@ -179,7 +183,9 @@ def phase_field(spec: CaseSpec, dx: float, dy: float, zf: np.ndarray, rng) -> np
 def pressure_modes(spec: CaseSpec, zf: np.ndarray, rng, n_modes: int = 8) -> np.ndarray:
     """Sum of 8 seeded Fourier modes of amplitude 1:
     sum_m cos(2 pi (a_m x/lx + b_m y/ly) + theta_m) cos(pi c_m z / lz),
-    a_m, b_m, c_m integers in [0, 4], theta_m uniform in [0, 2 pi)."""
+    a_m, b_m, c_m integers in [0, 4], theta_m uniform in [0, 2 pi); with
+    periodic z the z factor is cos(2 pi c_m z / lz)."""
+    zk = 2.0 if spec.bcz == PERIODIC else 1.0
     xc = _centres_1d(spec.nx, spec.lx) / spec.lx
     yc = _centres_1d(spec.ny, spec.ly) / spec.ly
     zc = 0.5 * (zf[:-1] + zf[1:]) / spec.lz
@@ -189,7 +195,7 @@ def pressure_modes(spec: CaseSpec, zf: np.ndarray, rng, n_modes: int = 8) -> np.
         a, b, c = rng.integers(0, 5, size=3)
         th = rng.random() * 2 * np.pi
         xys[m] = np.cos(2 * np.pi * (a * xc[None, :] + b * yc[:, None]) + th).ravel()
-        zs[:, m] = np.cos(np.pi * c * zc)
+        zs[:, m] = np.cos(zk * np.pi * c * zc)
     return (zs @ xys).reshape(spec.nz, spec.ny, spec.nx)  # sum over the modes
 
 
@@ -223,7 +229,8 @@ def solenoidal_velocity(spec: CaseSpec, dx: float, dy: float, zf: np.ndarray, rn
     A_x lives on x-edges (i, j+1/2, k+1/2), A_y on y-edges (i+1/2, j, k+1/2),
     A_z on z-edges (i+1/2, j+1/2, k); the staggered curl of such a potential
     has zero discrete divergence.  Envelopes sin(pi s / L) make the potential
-    vanish on wall edges so the normal velocity is exactly 0 on every wall.
+    vanish on wall edges so the normal velocity is exactly 0 on every wall
+    (none along a periodic direction).
     """
     nz, ny, nx = spec.nz, spec.ny, spec.nx
     shape = (nz, ny, nx)
@@ -231,10 +238,12 @@ def solenoidal_velocity(spec: CaseSpec, dx: float, dy: float, zf: np.ndarray, rn
     Ay = _random_periodic_field(shape, rng)
     Az = _random_periodic_field(shape, rng)
     zfe = zf[1:]                              # z of edge k+1/2
-    envz = np.sin(np.pi * zfe / spec.lz)
-    envz[-1] = 0.0
-    Ax *= envz[:, None, None]
-    Ay *= envz[:, None, None]
+    pz = spec.bcz == PERIODIC
+    if not pz:                                # A_x, A_y vanish on z walls
+        envz = np.sin(np.pi * zfe / spec.lz)
+        envz[-1] = 0.0
+        Ax *= envz[:, None, None]
+        Ay *= envz[:, None, None]
     if spec.bcx == NEUMANN:                   # A_y, A_z vanish on x walls
         xe = (np.arange(nx) + 1.0) / nx
         envx = np.sin(np.pi * xe)
@@ -264,9 +273,9 @@ def solenoidal_velocity(spec: CaseSpec, dx: float, dy: float, zf: np.ndarray, rn
     px = spec.bcx == PERIODIC
     py = spec.bcy == PERIODIC
     # u(i+1/2, j, k) = dAz/dy - dAy/dz
-    u = (Az - shm(Az, 1, py)) / dy - (Ay - shm(Ay, 0, False)) / dzf[:, None, None]
+    u = (Az - shm(Az, 1, py)) / dy - (Ay - shm(Ay, 0, pz)) / dzf[:, None, None]
     # v(i, j+1/2, k) = dAx/dz - dAz/dx
-    v = (Ax - shm(Ax, 0, False)) / dzf[:, None, None] - (Az - shm(Az, 2, px)) / dx
+    v = (Ax - shm(Ax, 0, pz)) / dzf[:, None, None] - (Az - shm(Az, 2, px)) / dx
     # w(i, j, k+1/2) = dAy/dx - dAx/dy
     w = (Ay - shm(Ay, 2, px)) / dx - (Ax - shm(Ax, 1, py)) / dy
     return u, v, w
@@ -277,7 +286,8 @@ def zero_walls(spec: CaseSpec, u, v, w):
         u[:, :, -1] = 0.0
     if spec.bcy == NEUMANN:
         v[:, -1, :] = 0.0
-    w[-1, :, :] = 0.0
+    if spec.bcz == NEUMANN:
+        w[-1, :, :] = 0.0
 
 
 def make_case(spec: CaseSpec) -> Case:

@@ -28,6 +28,13 @@ CASES = [
          zf=["0", "1/8", "1/2", "7/8", "1"], bcx=1, bcy=0, rho_l="1/8", rho_g="1", dt="1/16", seed=23),
     dict(name="p2x3x3_nn_stretched", nx=2, ny=3, nz=3, dx="1/2", dy="1/4",
          zf=["0", "1/4", "1/2", "1"], bcx=1, bcy=1, rho_l="1", rho_g="1/4", dt="1/8", seed=37),
+    # periodic z (triperiodic boxes; bcz = 0)
+    dict(name="p3x2x4_ppp_uniform", nx=3, ny=2, nz=4, dx="1/4", dy="1/2",
+         zf=["0", "1/4", "1/2", "3/4", "1"], bcx=0, bcy=0, bcz=0, rho_l="1/8", rho_g="1",
+         dt="1/16", seed=41),
+    dict(name="p2x3x4_npp_stretched", nx=2, ny=3, nz=4, dx="1/2", dy="1/4",
+         zf=["0", "1/8", "3/8", "1/2", "1"], bcx=1, bcy=0, bcz=0, rho_l="1", rho_g="1/4",
+         dt="1/8", seed=53),
 ]
 
 
@@ -40,8 +47,9 @@ def lcg(seed):
 
 def make(case):
     nx, ny, nz = case["nx"], case["ny"], case["nz"]
+    bcz = case.get("bcz", 1)
     g = exact.ExactGrid(nx, ny, nz, Q(case["dx"]), Q(case["dy"]), [Q(z) for z in case["zf"]],
-                        case["bcx"], case["bcy"])
+                        case["bcx"], case["bcy"], bcz)
     r = lcg(case["seed"])
     cells = list(g.cells())
     phi = {c: Q(next(r) % 17, 16) for c in cells}
@@ -55,7 +63,7 @@ def make(case):
             u[(i, j, k)] = Q(0)
         if case["bcy"] == 1 and j == ny - 1:
             v[(i, j, k)] = Q(0)
-        if k == nz - 1:
+        if bcz == 1 and k == nz - 1:
             w[(i, j, k)] = Q(0)
     f, p, uo, vo, wo = exact.project(g, Q(case["rho_l"]), Q(case["rho_g"]), Q(case["dt"]), phi,
                                      pn, pnm1, u, v, w)

@@ -17,7 +17,8 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, "oracle", "oracle.c")
 
 PINS = ("exact_rational or eigenmodes or apply_then_solve or divergence_free or "
-        "constant_density or dense_solves or stretched_z or correction_identity")
+        "constant_density or dense_solves or stretched_z or correction_identity or "
+        "triperiodic or rotation_commutes")
 
 MUTATIONS = [
     ("grad_sign", "gx[c] = (q[IDX(g, i + 1, j, k)] - q[c]) / g->dx;",
@@ -40,14 +41,29 @@ MUTATIONS = [
      "w[c] -= dt * (hz[c] / rho0 + (bz[c] - 1.0 / rho0) * pz[c]);"),
     ("eigen_angle", "double s = sin(M_PI * (double)a / (double)mx);",
      "double s = sin(2.0 * M_PI * (double)a / (double)mx);"),
-    ("z_coeff_index", "lo[k] = (k > 0) ? 1.0 / (dzf(&g, k) * dzc(&g, k - 1)) : 0.0;",
-     "lo[k] = (k > 0) ? 1.0 / (dzf(&g, k) * dzc(&g, k > 1 ? k - 2 : 0)) : 0.0;"),
+    ("z_coeff_index", "lo[k] = (k > 0) ? 1.0 / (dzf(&g, k) * dzc(&g, k - 1))",
+     "lo[k] = (k > 0) ? 1.0 / (dzf(&g, k) * dzc(&g, k > 1 ? k - 2 : 0))"),
     ("inverse_scale", "double scale = 1.0 / ((double)mx * (double)my);", "double scale = 1.0 / (double)mx;"),
     ("correct_no_extrapolation",
      "for (size_t c = 0; c < n; ++c) ph[c] = 2.0 * pn[c] - pnm1[c];\n    grad(&g, p, px, py, pz);",
      "for (size_t c = 0; c < n; ++c) ph[c] = pn[c];\n    grad(&g, p, px, py, pz);"),
-    ("z_coeff_upper", "up[k] = (k < nz - 1) ? 1.0 / (dzf(&g, k) * dzc(&g, k)) : 0.0;",
-     "up[k] = (k < nz - 1) ? 1.0 / (dzc(&g, k) * dzc(&g, k)) : 0.0;"),
+    ("z_coeff_upper", "up[k] = (k < nz - 1 || per) ? 1.0 / (dzf(&g, k) * dzc(&g, k)) : 0.0;",
+     "up[k] = (k < nz - 1 || per) ? 1.0 / (dzc(&g, k) * dzc(&g, k)) : 0.0;"),
+    # periodic z
+    ("z_seam_spacing", "if (k == g->nz - 1) return 0.5 * (dzf(g, 0) + dzf(g, g->nz - 1));",
+     "if (k == g->nz - 1) return dzf(g, g->nz - 1);"),
+    ("grad_z_seam_sign", "gz[c] = g->bcz == 0 ? (q[IDX(g, i, j, 0)] - q[c]) / dzc(g, k) : 0.0;",
+     "gz[c] = g->bcz == 0 ? (q[c] - q[IDX(g, i, j, 0)]) / dzc(g, k) : 0.0;"),
+    ("div_z_seam_index", "(g->bcz == 0 ? w[IDX(g, i, j, nz - 1)] : 0.0)",
+     "(g->bcz == 0 ? w[IDX(g, i, j, 0)] : 0.0)"),
+    ("face_density_z_seam", "int kt = (k < nz - 1) ? k + 1 : (g->bcz == 0 ? 0 : -1);",
+     "int kt = (k < nz - 1) ? k + 1 : (g->bcz == 0 ? k : -1);"),
+    ("correct_skips_z_seam", "if (!(g.bcz == 1 && k == nz - 1))\n                    w[c]",
+     "if (k < nz - 1)\n                    w[c]"),
+    ("z_solve_seam_coupling", "(per ? 1.0 / (dzf(&g, 0) * dzc(&g, nz - 1)) : 0.0)",
+     "(per ? 1.0 / (dzf(&g, nz - 1) * dzc(&g, nz - 1)) : 0.0)"),
+    ("z_matrix_wrap_column", "A[(size_t)k * nz + (k + nz - 1) % nz] += lo[k];",
+     "A[(size_t)k * nz + (k + nz - 2) % nz] += lo[k];"),
     ("neumann_extension", "return (bc == 0 || e < n) ? e : 2 * n - 1 - e;",
      "return (bc == 0 || e < n) ? e : 2 * n - e - (e == 2 * n - 1 ? 1 : 0) - 0;"),
 ]

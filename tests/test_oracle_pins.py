@@ -56,7 +56,8 @@ def test_projection_matches_exact_rational(path, dense):
     nx, ny, nz = d["nx"], d["ny"], d["nz"]
     shape = (nz, ny, nx)
     zf = np.array([float(Q(z)) for z in d["zf"]])
-    g = O.Grid(nx, ny, nz, float(Q(d["dx"])), float(Q(d["dy"])), zf, d["bcx"], d["bcy"])
+    g = O.Grid(nx, ny, nz, float(Q(d["dx"])), float(Q(d["dy"])), zf, d["bcx"], d["bcy"],
+               d.get("bcz", I.NEUMANN))
     inp = {k: np.array(v).reshape(shape) for k, v in d["inputs"].items()}
     exp = {k: np.array(v).reshape(shape) for k, v in d["expected"].items()}
     r = O.project(g, float(Q(d["rho_l"])), float(Q(d["rho_g"])), float(Q(d["dt"])), inp["phi"],
@@ -101,6 +102,73 @@ def test_eigenmodes_closed_form(nx, ny, nz, bcx, bcy):
             assert relerr(p, q0) < 1e-12
 
 
+@pytest.mark.parametrize("nx,ny,nz,bcx,bcy", [
+    (16, 12, 10, 0, 0), (12, 16, 9, 1, 0), (9, 8, 12, 1, 1), (8, 6, 2, 0, 1), (6, 8, 3, 1, 0)])
+def test_eigenmodes_closed_form_periodic_z(nx, ny, nz, bcx, bcy):
+    """Periodic z (triperiodic boxes of the paper's emulsion case): the z
+    factor is a Fourier mode of the periodic second difference."""
+    dx, dy, dz = 1.0 / nx, 0.7 / ny, 1.3 / nz
+    g = O.Grid(nx, ny, nz, dx, dy, uniform_zf(nz, 1.3), bcx, bcy, I.PERIODIC)
+    rng = np.random.default_rng(nx * 100 + ny + 7)
+    modes = [(0, 0, 1), (1, 0, 0), (0, 1, 1), (nx // 2, ny // 2, nz // 2), (1, 2, 1),
+             (nx - 1, 1, nz - 1), (2, ny - 1, 0)]
+    for a, b, c in modes:
+        X, lx = _mode_1d(nx, dx, a, bcx, rng.random() * 6.28)
+        Y, ly = _mode_1d(ny, dy, b, bcy, rng.random() * 6.28)
+        Z, lz = _mode_1d(nz, dz, c, I.PERIODIC, rng.random() * 6.28)
+        q = Z[:, None, None] * Y[None, :, None] * X[None, None, :]
+        lam = lx + ly + lz
+        Lq = O.apply_L(g, q)
+        assert np.max(np.abs(Lq - lam * q)) < 1e-12 * max(1.0, abs(lam))
+        if abs(lam) > 0 and np.max(np.abs(q)) > 1e-12:
+            p = O.poisson(g, lam * q)
+            q0 = q - O.weighted_mean(g, q)
+            assert relerr(p, q0) < 1e-12
+
+
+def test_triperiodic_poisson_matches_numpy_fft():
+    """Uniform triperiodic grid: D G is diagonal in the 3-D discrete Fourier
+    basis, so numpy's FFT with the closed-form eigenvalues solves it exactly
+    (an independent library routine against the oracle's z-line solves)."""
+    nx, ny, nz = 12, 10, 16
+    dx, dy, dz = 1.0 / nx, 0.8 / ny, 1.2 / nz
+    g = O.Grid(nx, ny, nz, dx, dy, uniform_zf(nz, 1.2), I.PERIODIC, I.PERIODIC, I.PERIODIC)
+    f = np.random.default_rng(4).standard_normal(g.shape)
+    f -= f.mean()
+    lam = (-4 / dz ** 2 * np.sin(np.pi * np.arange(nz) / nz) ** 2)[:, None, None] + \
+          (-4 / dy ** 2 * np.sin(np.pi * np.arange(ny) / ny) ** 2)[None, :, None] + \
+          (-4 / dx ** 2 * np.sin(np.pi * np.arange(nx) / nx) ** 2)[None, None, :]
+    F = np.fft.fftn(f)
+    lam[0, 0, 0] = 1.0
+    F /= lam
+    F[0, 0, 0] = 0.0
+    p_np = np.real(np.fft.ifftn(F))
+    assert relerr(O.poisson(g, f), p_np) < 1e-12
+    assert relerr(O.apply_L(g, p_np), f) < 1e-12
+
+
+def test_periodic_z_rotation_commutes_stretched():
+    """A periodic z direction has no distinguished plane: rotating the cell
+    spacings and every field by s planes (so the periodic seam moves inside
+    the domain, where the centre distance is formed from the neighbouring
+    centres) must rotate the projection's results."""
+    spec = I.CaseSpec(nx=10, ny=8, nz=12, beta=1.8, n_bubbles=2, radius_cells=2.0, config=12,
+                      bcz=I.PERIODIC)
+    c = I.make_case(spec)
+    g0 = O.Grid.of_case(c)
+    r0 = O.project_case(c)
+    for sh in (1, 5):
+        dzf = np.roll(np.diff(c.zf), sh)
+        zf1 = np.concatenate([[0.0], np.cumsum(dzf)])
+        g1 = O.Grid(spec.nx, spec.ny, spec.nz, c.dx, c.dy, zf1, spec.bcx, spec.bcy, I.PERIODIC)
+        rl = lambda a: np.roll(a, sh, axis=0)
+        r1 = O.project(g1, spec.rho_l, spec.rho_g, spec.dt, rl(c.phi), rl(c.pn), rl(c.pnm1),
+                       rl(c.u), rl(c.v), rl(c.w))
+        for key in ("p", "u", "v", "w"):
+            assert relerr(r1[key], rl(r0[key])) < 1e-11, (sh, key)
+    assert abs(O.weighted_mean(g0, r0["p"])) < 1e-12 * np.max(np.abs(r0["p"]))
+
+
 # --------------------------------------------------------------------------
 # Stretched z: closed-form action on linear and quadratic profiles
 # --------------------------------------------------------------------------
@@ -128,11 +196,12 @@ def test_stretched_z_operator_closed_form(beta):
 # --------------------------------------------------------------------------
 # T3: apply-then-solve on random fields (uniform and stretched, all BCs)
 # --------------------------------------------------------------------------
-@pytest.mark.parametrize("nx,ny,nz,bcx,bcy,beta", [
-    (16, 16, 16, 0, 0, 0.0), (12, 18, 10, 1, 0, 1.5), (18, 8, 13, 0, 1, 2.0),
-    (6, 9, 24, 1, 1, 1.0), (32, 24, 20, 0, 0, 1.5)])
-def test_apply_then_solve(nx, ny, nz, bcx, bcy, beta):
-    g = O.Grid(nx, ny, nz, 1.0 / nx, 1.1 / ny, I.z_faces(nz, 0.9, beta), bcx, bcy)
+@pytest.mark.parametrize("nx,ny,nz,bcx,bcy,beta,bcz", [
+    (16, 16, 16, 0, 0, 0.0, 1), (12, 18, 10, 1, 0, 1.5, 1), (18, 8, 13, 0, 1, 2.0, 1),
+    (6, 9, 24, 1, 1, 1.0, 1), (32, 24, 20, 0, 0, 1.5, 1),
+    (16, 12, 16, 0, 0, 0.0, 0), (12, 8, 11, 1, 0, 1.5, 0), (8, 6, 3, 0, 1, 0.0, 0)])
+def test_apply_then_solve(nx, ny, nz, bcx, bcy, beta, bcz):
+    g = O.Grid(nx, ny, nz, 1.0 / nx, 1.1 / ny, I.z_faces(nz, 0.9, beta), bcx, bcy, bcz)
     q = np.random.default_rng(7).standard_normal(g.shape)
     p = O.poisson(g, O.apply_L(g, q))
     q0 = q - O.weighted_mean(g, q)
@@ -143,13 +212,14 @@ def test_apply_then_solve(nx, ny, nz, bcx, bcy, beta):
 # --------------------------------------------------------------------------
 # T2: dense solves (oracle's own dense path and an independent numpy matrix)
 # --------------------------------------------------------------------------
-def _numpy_laplacian(nx, ny, nz, dx, dy, zf, bcx, bcy):
-    """7-point operator assembled independently from the stencil weights."""
+def _numpy_laplacian(nx, ny, nz, dx, dy, zf, bcx, bcy, bcz=I.NEUMANN):
+    """7-point operator assembled independently from the stencil weights; with
+    periodic z the seam face joins centre nz-1 to centre 0 + lz."""
     n = nx * ny * nz
     A = np.zeros((n, n))
     dzf = np.diff(zf)
     zc = 0.5 * (zf[:-1] + zf[1:])
-    dzc = np.diff(zc)
+    dzc = np.diff(np.concatenate([zc, [zc[0] + (zf[-1] - zf[0])]]))  # dzc[nz-1]: the seam
 
     def ix(i, j, k):
         return (k * ny + j) * nx + i
@@ -168,21 +238,22 @@ def _numpy_laplacian(nx, ny, nz, dx, dy, zf, bcx, bcy):
                     if 0 <= jj < ny or bcy == I.PERIODIC:
                         A[r, ix(i, jj % ny, k)] += 1 / dy ** 2
                         A[r, r] -= 1 / dy ** 2
-                if k + 1 < nz:
-                    A[r, ix(i, j, k + 1)] += 1 / (dzf[k] * dzc[k])
+                if k + 1 < nz or bcz == I.PERIODIC:
+                    A[r, ix(i, j, (k + 1) % nz)] += 1 / (dzf[k] * dzc[k])
                     A[r, r] -= 1 / (dzf[k] * dzc[k])
-                if k - 1 >= 0:
-                    A[r, ix(i, j, k - 1)] += 1 / (dzf[k] * dzc[k - 1])
+                if k - 1 >= 0 or bcz == I.PERIODIC:
+                    A[r, ix(i, j, (k - 1) % nz)] += 1 / (dzf[k] * dzc[k - 1])
                     A[r, r] -= 1 / (dzf[k] * dzc[k - 1])
     return A
 
 
-@pytest.mark.parametrize("nx,ny,nz,bcx,bcy,beta", [
-    (8, 8, 8, 0, 0, 0.0), (8, 6, 10, 1, 0, 1.5), (6, 8, 7, 0, 1, 1.0), (4, 6, 8, 1, 1, 2.0)])
-def test_dense_solves(nx, ny, nz, bcx, bcy, beta):
+@pytest.mark.parametrize("nx,ny,nz,bcx,bcy,beta,bcz", [
+    (8, 8, 8, 0, 0, 0.0, 1), (8, 6, 10, 1, 0, 1.5, 1), (6, 8, 7, 0, 1, 1.0, 1), (4, 6, 8, 1, 1, 2.0, 1),
+    (8, 6, 8, 0, 0, 0.0, 0), (6, 8, 9, 1, 0, 1.5, 0), (4, 6, 2, 0, 1, 0.0, 0), (6, 4, 7, 1, 1, 2.0, 0)])
+def test_dense_solves(nx, ny, nz, bcx, bcy, beta, bcz):
     zf = I.z_faces(nz, 1.0, beta)
-    g = O.Grid(nx, ny, nz, 1.0 / nx, 1.0 / ny, zf, bcx, bcy)
-    A = _numpy_laplacian(nx, ny, nz, g.dx, g.dy, zf, bcx, bcy)
+    g = O.Grid(nx, ny, nz, 1.0 / nx, 1.0 / ny, zf, bcx, bcy, bcz)
+    A = _numpy_laplacian(nx, ny, nz, g.dx, g.dy, zf, bcx, bcy, bcz)
     q = np.random.default_rng(3).standard_normal(g.shape)
     # the oracle's operator is the independently assembled matrix
     assert np.max(np.abs(O.apply_L(g, q).ravel() - A @ q.ravel())) < 1e-9 * np.max(np.abs(A))
@@ -203,8 +274,14 @@ def test_dense_solves(nx, ny, nz, bcx, bcy, beta):
 @pytest.mark.parametrize("spec", [I.drop32_spec(),
                                   I.bubbles_spec(24, 3, 3.0, 1.5, config=1),
                                   I.CaseSpec(nx=16, ny=24, nz=20, bcx=1, bcy=0, n_bubbles=2,
-                                             radius_cells=3, beta=1.0, config=3)],
-                         ids=["drop32", "bubbles24_stretched", "neumann_x"])
+                                             radius_cells=3, beta=1.0, config=3),
+                                  I.CaseSpec(nx=20, ny=16, nz=18, n_bubbles=3, radius_cells=3,
+                                             config=13, bcz=I.PERIODIC),
+                                  I.CaseSpec(nx=12, ny=16, nz=14, bcx=1, n_bubbles=2,
+                                             radius_cells=2.5, beta=1.5, config=14,
+                                             bcz=I.PERIODIC)],
+                         ids=["drop32", "bubbles24_stretched", "neumann_x", "triperiodic",
+                              "periodic_z_stretched"])
 def test_divergence_free(spec):
     c = I.make_case(spec)
     g = O.Grid.of_case(c)
@@ -217,7 +294,8 @@ def test_divergence_free(spec):
     # wall faces untouched (zero)
     if spec.bcx == I.NEUMANN:
         assert np.all(r["u"][:, :, -1] == 0)
-    assert np.all(r["w"][-1] == 0)
+    if spec.bcz == I.NEUMANN:
+        assert np.all(r["w"][-1] == 0)
 
 
 # --------------------------------------------------------------------------
