@@ -88,6 +88,14 @@ typedef struct fizzy_proj_desc {
     double div_tol;       /* mixed: also stop only when max|D u| dx / U <= div_tol, with U the   */
                           /* rms of u* and D u = (dt/rho0)(f - L p) (0 -> 1e-10; < 0 -> off)    */
     unsigned flags;       /* FIZZY_FLAG_*                                                       */
+    int periodic_z;       /* 0: walls at z = zf[0] and zf[nz] (w[nz-1] is the top wall, 0);    */
+                          /* 1: periodic z (triperiodic boxes with bc_x = bc_y = periodic, as  */
+                          /* the paper's emulsion in homogeneous isotropic turbulence): the     */
+                          /* seam face nz-1/2 joins plane nz-1 to plane 0, centre distance      */
+                          /* (dzf_0 + dzf_(nz-1))/2, w[nz-1] is its velocity.  Each z-line is a */
+                          /* cyclic tridiagonal system (Sherman-Morrison).  Not accepted by     */
+                          /* fizzy_proj_solve_noalloc or the batched executor                   */
+                          /* (FIZZY_ERR_UNSUPPORTED).  Other values: FIZZY_ERR_INVALID.         */
 } fizzy_proj_desc;
 
 /* Diagnostics of the last solve (host memory). */

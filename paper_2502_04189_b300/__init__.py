@@ -43,7 +43,8 @@ def _ptr(t):
 
 
 def make_desc(nx, ny, nz, dx, dy, zf=None, dz=None, bcx=PERIODIC, bcy=PERIODIC, rho_l=1.0,
-              rho_g=1e-3, dt=1e-4, precision=FP64, tol=0.0, max_refine=0, flags=0, div_tol=0.0):
+              rho_g=1e-3, dt=1e-4, precision=FP64, tol=0.0, max_refine=0, flags=0, div_tol=0.0,
+              periodic_z=False):
     d = _abi.Desc()
     d.nx, d.ny, d.nz = int(nx), int(ny), int(nz)
     d.dx, d.dy = float(dx), float(dy)
@@ -58,6 +59,7 @@ def make_desc(nx, ny, nz, dx, dy, zf=None, dz=None, bcx=PERIODIC, bcy=PERIODIC, 
     d.rho_l, d.rho_g, d.dt = float(rho_l), float(rho_g), float(dt)
     d.precision, d.tol, d.max_refine, d.flags = int(precision), float(tol), int(max_refine), int(flags)
     d.div_tol = float(div_tol)
+    d.periodic_z = 1 if periodic_z else 0
     return d, keep
 
 
@@ -78,11 +80,11 @@ class Plan:
 
     def __init__(self, nx, ny, nz, dx, dy, zf=None, dz=None, bcx=PERIODIC, bcy=PERIODIC,
                  rho_l=1.0, rho_g=1e-3, dt=1e-4, precision=FP64, tol=0.0, max_refine=0,
-                 check=False, stream=None, div_tol=0.0):
+                 check=False, stream=None, div_tol=0.0, periodic_z=False):
         self.shape = (int(nz), int(ny), int(nx))
         self.precision = precision
         d, keep = make_desc(nx, ny, nz, dx, dy, zf, dz, bcx, bcy, rho_l, rho_g, dt, precision,
-                            tol, max_refine, FLAG_CHECK if check else 0, div_tol)
+                            tol, max_refine, FLAG_CHECK if check else 0, div_tol, periodic_z)
         h = ctypes.c_void_p()
         rc = _abi.lib().fizzy_proj_plan(ctypes.byref(h), ctypes.byref(d),
                                         ctypes.c_void_p(0) if stream is None else _stream_handle(stream))
@@ -96,7 +98,8 @@ class Plan:
     def for_case(cls, case, precision=FP64, check=False, **kw):
         s = case.spec
         return cls(s.nx, s.ny, s.nz, case.dx, case.dy, zf=case.zf, bcx=s.bcx, bcy=s.bcy,
-                   rho_l=s.rho_l, rho_g=s.rho_g, dt=s.dt, precision=precision, check=check, **kw)
+                   rho_l=s.rho_l, rho_g=s.rho_g, dt=s.dt, precision=precision, check=check,
+                   periodic_z=getattr(s, "bcz", NEUMANN) == PERIODIC, **kw)
 
     def _check(self, rc):
         if rc not in (0, -5):

@@ -35,7 +35,7 @@ class Desc(ctypes.Structure):
                 ("rho_l", ctypes.c_double), ("rho_g", ctypes.c_double), ("dt", ctypes.c_double),
                 ("precision", ctypes.c_int), ("tol", ctypes.c_double),
                 ("max_refine", ctypes.c_int), ("div_tol", ctypes.c_double),
-                ("flags", ctypes.c_uint)]
+                ("flags", ctypes.c_uint), ("periodic_z", ctypes.c_int)]
 
 
 class Tuning(ctypes.Structure):

@@ -62,6 +62,9 @@ struct fizzy_proj_plan_s {
     int Ux = 0, Uy = 0;
     double *mtab64 = nullptr, *ibtab64 = nullptr, *cup64 = nullptr;
     float *mtab32 = nullptr, *ibtab32 = nullptr, *cup32 = nullptr;
+    // periodic z: Sherman-Morrison weights and correction vector (k_ztables_cyc)
+    double *wtab64 = nullptr, *qtab64 = nullptr;
+    float *wtab32 = nullptr, *qtab32 = nullptr;
     double *qx = nullptr, *qy = nullptr, *qz = nullptr;
     double *fhat64 = nullptr;
     float *fhat32 = nullptr;
@@ -300,6 +303,7 @@ int validate(const fizzy_proj_desc *d) {
     if (!d->zf && !(d->dz > 0)) return FIZZY_ERR_INVALID;
     if (d->bc_x != FIZZY_BC_PERIODIC && d->bc_x != FIZZY_BC_NEUMANN) return FIZZY_ERR_INVALID;
     if (d->bc_y != FIZZY_BC_PERIODIC && d->bc_y != FIZZY_BC_NEUMANN) return FIZZY_ERR_INVALID;
+    if (d->periodic_z != 0 && d->periodic_z != 1) return FIZZY_ERR_INVALID;
     if (!(d->rho_l >= 1e-30 && d->rho_l <= 1e30) || !(d->rho_g >= 1e-30 && d->rho_g <= 1e30))
         return FIZZY_ERR_INVALID;
     if (!(d->dt > 0) || !std::isfinite(d->dt)) return FIZZY_ERR_INVALID;
@@ -362,7 +366,7 @@ void physics_zrow(double rho_l, double rho_g, double dt, double sig, double dzf,
 // Grid of a stand-alone pass launch: the CTAs of the kernel the GPU holds
 // resident (occupancy x SM count); the kernel strides over its tiles.
 enum { CAP_XF64, CAP_XF32D, CAP_XF32L, CAP_Y64F, CAP_Y64I, CAP_Y32F, CAP_Y32I, CAP_XI64, CAP_XI32S,
-       CAP_XI32A, CAP_TH64, CAP_TH32, CAP_RM, CAP_RC, CAP_CIF, CAP_N };
+       CAP_XI32A, CAP_TH64, CAP_TH32, CAP_TH64C, CAP_TH32C, CAP_RM, CAP_RC, CAP_CIF, CAP_N };
 // Cached per (device, kernel, block size, shared memory): plans are built per
 // request in the serving runtime, and the occupancy queries would dominate.
 template <typename K> int resident_grid(K kernel, int threads, size_t smem) {
@@ -474,6 +478,8 @@ void pass_caps(int *cap, const PassKernels &k, size_t sx64, size_t sx32, size_t 
     cap[CAP_XI32A] = resident_grid(k.xi32a, 256, sx32r);
     cap[CAP_TH64] = resident_grid(k_thomas<double>, THOMAS_BLOCK, thomas_smem<double>());
     cap[CAP_TH32] = resident_grid(k_thomas<float>, THOMAS_BLOCK, thomas_smem<float>());
+    cap[CAP_TH64C] = resident_grid(k_thomas_cyc<double>, THOMAS_BLOCK, thomas_cyc_smem<double>());
+    cap[CAP_TH32C] = resident_grid(k_thomas_cyc<float>, THOMAS_BLOCK, thomas_cyc_smem<float>());
     cap[CAP_RM] = resident_grid(k_residmax, 256, 0);
     cap[CAP_RC] = resident_grid(k_resid<true>, 256, 0);
     cap[CAP_CIF] = resident_grid(k_correct_if, 256, 0);
@@ -497,8 +503,9 @@ size_t plan_bytes(const fizzy_proj_desc *d) {
     size_t b = 0;
     b += 3 * N * 8;                   // q
     b += mixed ? N * 4 + N * 8 : N * 8;  // spectral workspace (+ f in mixed)
-    b += 2 * tab * 8;                 // FP64 factorisation tables
-    if (mixed) b += 2 * tab * 4;      // FP32 factorisation tables
+    const size_t ntab = d->periodic_z ? 4 : 2;  // periodic z: + weights and correction vector
+    b += ntab * tab * 8;              // FP64 factorisation tables
+    if (mixed) b += ntab * tab * 4;   // FP32 factorisation tables
     b += 16 * (size_t)d->nz * 8;      // per-k tables
     b += 4 * (size_t)(d->nx + d->ny + 4) * 16;  // twiddles
     b += usq_blocks(d) * 8 + 4096;    // partials + stats
@@ -573,6 +580,8 @@ int fizzy_proj_plan(fizzy_proj_plan_t *out, const fizzy_proj_desc *d, void *stre
         zc[k] = 0.5 * (p->zf[k] + p->zf[k + 1]);
     }
     for (int k = 0; k + 1 < nz; ++k) dzc[k] = zc[k + 1] - zc[k];
+    const bool perz = d->periodic_z != 0;
+    if (perz) dzc[nz - 1] = 0.5 * (dzf[0] + dzf[nz - 1]);  // the seam face nz-1/2
     double lz = 0.0;
     for (int k = 0; k < nz; ++k) lz += dzf[k];
     p->sigma = 1.0 / (4.0 * (double)nx * (double)ny);
@@ -582,10 +591,11 @@ int fizzy_proj_plan(fizzy_proj_plan_t *out, const fizzy_proj_desc *d, void *stre
     static_assert(T_LZA == kZPhys, "physics rows lead the per-k table block");
     std::vector<double> zt((size_t)T_NTAB * nz, 0.0);
     for (int k = 0; k < nz; ++k) {
-        const bool top = (k == nz - 1);
+        const bool top = (k == nz - 1) && !perz;
         physics_zrow(d->rho_l, d->rho_g, d->dt, sig, dzf[k], dzc[k], top, &zt[k], nz);
-        zt[T_LZA * nz + k] = (k > 0) ? 1.0 / (dzf[k] * dzc[k - 1]) : 0.0;
-        zt[T_LZC * nz + k] = top ? 0.0 : 1.0 / (dzf[k] * dzc[k]);
+        zt[T_LZA * nz + k] = (k > 0) ? 1.0 / (dzf[k] * dzc[k - 1])
+                                     : (perz ? 1.0 / (dzf[0] * dzc[nz - 1]) : 0.0);
+        zt[T_LZC * nz + k] = top ? 0.0 : 1.0 / (dzf[k] * dzc[k]);  // periodic z: the seam at nz-1
         zt[T_IZF * nz + k] = 1.0 / dzf[k];
         zt[T_DZF * nz + k] = dzf[k];
         zt[T_DZC * nz + k] = dzc[k];
@@ -607,6 +617,7 @@ int fizzy_proj_plan(fizzy_proj_plan_t *out, const fizzy_proj_desc *d, void *stre
     g.nz = nz;
     g.bcx = d->bc_x;
     g.bcy = d->bc_y;
+    g.perz = d->periodic_z ? 1 : 0;
     g.rny = (unsigned)((1ull << 32) / (unsigned)ny + 1);
     physics_consts(g, d->rho_l, d->rho_g, d->dt, d->dx, d->dy, sig);
     g.idx2 = 1.0 / (d->dx * d->dx);
@@ -650,6 +661,14 @@ int fizzy_proj_plan(fizzy_proj_plan_t *out, const fizzy_proj_desc *d, void *stre
         p->ibtab32 = dev_alloc<float>(p, ts * nz, &status);
         p->cup32 = dev_alloc<float>(p, nz, &status);
     }
+    if (perz) {
+        p->wtab64 = dev_alloc<double>(p, ts * nz, &status);
+        p->qtab64 = dev_alloc<double>(p, ts * nz, &status);
+        if (p->mixed) {
+            p->wtab32 = dev_alloc<float>(p, ts * nz, &status);
+            p->qtab32 = dev_alloc<float>(p, ts * nz, &status);
+        }
+    }
     // ---- workspace
     p->qx = dev_alloc<double>(p, N, &status);
     p->qy = dev_alloc<double>(p, N, &status);
@@ -680,10 +699,17 @@ int fizzy_proj_plan(fizzy_proj_plan_t *out, const fizzy_proj_desc *d, void *stre
         }
         note(p, cudaMemcpyAsync(lam_d, lam.data(), lam.size() * sizeof(double), cudaMemcpyHostToDevice, p->alloc_stream));
         const int blocks = (int)std::min<size_t>((ts + 127) / 128, 4096);
-        k_ztables<<<blocks, 128, 0, p->alloc_stream>>>(Ux, Uy, nz, lam_d, lam_d + Ux, zt_d + T_LZA * nz,
-                                                       zt_d + T_LZC * nz, p->mtab64, p->ibtab64,
-                                                       p->mixed ? p->mtab32 : nullptr,
-                                                       p->mixed ? p->ibtab32 : nullptr);
+        if (perz)
+            k_ztables_cyc<<<blocks, 128, 0, p->alloc_stream>>>(
+                Ux, Uy, nz, lam_d, lam_d + Ux, zt_d + T_LZA * nz, zt_d + T_LZC * nz, p->mtab64,
+                p->ibtab64, p->wtab64, p->qtab64, p->mixed ? p->mtab32 : nullptr,
+                p->mixed ? p->ibtab32 : nullptr, p->mixed ? p->wtab32 : nullptr,
+                p->mixed ? p->qtab32 : nullptr);
+        else
+            k_ztables<<<blocks, 128, 0, p->alloc_stream>>>(Ux, Uy, nz, lam_d, lam_d + Ux, zt_d + T_LZA * nz,
+                                                           zt_d + T_LZC * nz, p->mtab64, p->ibtab64,
+                                                           p->mixed ? p->mtab32 : nullptr,
+                                                           p->mixed ? p->ibtab32 : nullptr);
     }
     note(p, cudaMemcpyAsync(p->cup64, C, nz * sizeof(double), cudaMemcpyHostToDevice, p->alloc_stream));
     if (p->mixed) {
@@ -743,9 +769,11 @@ int fizzy_proj_set_physics(fizzy_proj_plan_t p, double rho_l, double rho_g, doub
     std::vector<double> rows(kZPhys * (size_t)nz);
     for (int k = 0; k < nz; ++k) {
         const double dzf = p->zf[k + 1] - p->zf[k];
-        const bool top = (k == nz - 1);
+        const bool last = (k == nz - 1), top = last && !p->g.perz;
         const double zc0 = 0.5 * (p->zf[k] + p->zf[k + 1]);
-        const double dzc = top ? 0.0 : 0.5 * (p->zf[k + 1] + p->zf[k + 2]) - zc0;
+        const double dzc = top ? 0.0
+                           : last ? 0.5 * ((p->zf[1] - p->zf[0]) + dzf)  // periodic z: the seam
+                                  : 0.5 * (p->zf[k + 1] + p->zf[k + 2]) - zc0;
         physics_zrow(rho_l, rho_g, dt, sig, dzf, dzc, top, &rows[k], nz);
     }
     const cudaError_t e = cudaMemcpyAsync(p->zt, rows.data(), rows.size() * sizeof(double),
@@ -902,7 +930,10 @@ int fizzy_proj_solve(fizzy_proj_plan_t p, const double *phi, const double *p_n, 
         xa.out = p->fhat64;
         TIMED(KS_XFWD, (p->kern.xf64<<<grid(xtiles, CAP_XF64), 256, p->smem_x64, s>>>(g, p->fx.d64, p->Lx, xa, xtiles)));
         TIMED(KS_YFWD, (p->kern.yf64<<<grid(ytiles, CAP_Y64F), 256, p->smem_y64, s>>>(nx, ny, p->fy.d64, p->TXy, p->fhat64, nullptr, ygx, ytiles)));
-        TIMED(KS_THOMAS, (k_thomas<double><<<grid(ttiles, CAP_TH64), THOMAS_BLOCK, thomas_smem<double>(), s>>>(g, p->Ux, p->Uy, p->mtab64, p->ibtab64, p->cup64, p->fhat64, nullptr, ttiles)));
+        if (g.perz)
+            TIMED(KS_THOMAS, (k_thomas_cyc<double><<<grid(ttiles, CAP_TH64C), THOMAS_BLOCK, thomas_cyc_smem<double>(), s>>>(g, p->Ux, p->Uy, p->mtab64, p->ibtab64, p->cup64, p->wtab64, p->qtab64, p->fhat64, nullptr, ttiles)));
+        else
+            TIMED(KS_THOMAS, (k_thomas<double><<<grid(ttiles, CAP_TH64), THOMAS_BLOCK, thomas_smem<double>(), s>>>(g, p->Ux, p->Uy, p->mtab64, p->ibtab64, p->cup64, p->fhat64, nullptr, ttiles)));
         TIMED(KS_YINV, (p->kern.yi64<<<grid(ytiles, CAP_Y64I), 256, p->smem_y64, s>>>(nx, ny, p->fy.d64, p->TXy, p->fhat64, nullptr, ygx, ytiles)));
         TIMED(KS_XINV, (p->kern.xi64<<<grid(xtiles, CAP_XI64), 256, p->smem_x64, s>>>(g, p->fx.d64, p->Lx, p->fhat64, p_np1, p->st, xtiles)));
         if (p->check) {
@@ -916,7 +947,10 @@ int fizzy_proj_solve(fizzy_proj_plan_t p, const double *phi, const double *p_n, 
         const int *conv = &p->st->converged;
         TIMED(KS_XFWD, (p->kern.xf32d<<<grid(xrt, CAP_XF32D), 256, smx32r, s>>>(g, p->fx.d32, p->Lx, xa, xrt)));
         TIMED(KS_YFWD, (p->kern.yf32<<<grid(ytiles, CAP_Y32F), 256, p->smem_y32, s>>>(nx, ny, p->fy.d32, p->TXy, p->fhat32, nullptr, ygx, ytiles)));
-        TIMED(KS_THOMAS, (k_thomas<float><<<grid(ttiles, CAP_TH32), THOMAS_BLOCK, thomas_smem<float>(), s>>>(g, p->Ux, p->Uy, p->mtab32, p->ibtab32, p->cup32, p->fhat32, nullptr, ttiles)));
+        if (g.perz)
+            TIMED(KS_THOMAS, (k_thomas_cyc<float><<<grid(ttiles, CAP_TH32C), THOMAS_BLOCK, thomas_cyc_smem<float>(), s>>>(g, p->Ux, p->Uy, p->mtab32, p->ibtab32, p->cup32, p->wtab32, p->qtab32, p->fhat32, nullptr, ttiles)));
+        else
+            TIMED(KS_THOMAS, (k_thomas<float><<<grid(ttiles, CAP_TH32), THOMAS_BLOCK, thomas_smem<float>(), s>>>(g, p->Ux, p->Uy, p->mtab32, p->ibtab32, p->cup32, p->fhat32, nullptr, ttiles)));
         TIMED(KS_YINV, (p->kern.yi32<<<grid(ytiles, CAP_Y32I), 256, p->smem_y32, s>>>(nx, ny, p->fy.d32, p->TXy, p->fhat32, nullptr, ygx, ytiles)));
         TIMED(KS_XINV, (p->kern.xi32s<<<grid(xrt, CAP_XI32S), 256, smx32r, s>>>(g, p->fx.d32, p->Lx, p->fhat32, p_np1, p->st, xrt)));
         // residual of the FP32 solution (slot 0), then refinement sweeps
@@ -946,7 +980,10 @@ int fizzy_proj_solve(fizzy_proj_plan_t p, const double *phi, const double *p_n, 
             auto gs = [&](int tiles, int c) { return sw == 1 ? grid(tiles, c) : rgrid(tiles, c); };
             TIMED(KS_XFWD_R, (p->kern.xf32l<<<gs(xrt, CAP_XF32L), 256, smx32r, s>>>(g, p->fx.d32, p->Lx, la, xrt)));
             TIMED(KS_YFWD_R, (p->kern.yf32<<<gs(ytiles, CAP_Y32F), 256, p->smem_y32, s>>>(nx, ny, p->fy.d32, p->TXy, p->fhat32, conv, ygx, ytiles)));
-            TIMED(KS_THOMAS_R, (k_thomas<float><<<gs(ttiles, CAP_TH32), THOMAS_BLOCK, thomas_smem<float>(), s>>>(g, p->Ux, p->Uy, p->mtab32, p->ibtab32, p->cup32, p->fhat32, conv, ttiles)));
+            if (g.perz)
+                TIMED(KS_THOMAS_R, (k_thomas_cyc<float><<<gs(ttiles, CAP_TH32C), THOMAS_BLOCK, thomas_cyc_smem<float>(), s>>>(g, p->Ux, p->Uy, p->mtab32, p->ibtab32, p->cup32, p->wtab32, p->qtab32, p->fhat32, conv, ttiles)));
+            else
+                TIMED(KS_THOMAS_R, (k_thomas<float><<<gs(ttiles, CAP_TH32), THOMAS_BLOCK, thomas_smem<float>(), s>>>(g, p->Ux, p->Uy, p->mtab32, p->ibtab32, p->cup32, p->fhat32, conv, ttiles)));
             TIMED(KS_YINV_R, (p->kern.yi32<<<gs(ytiles, CAP_Y32I), 256, p->smem_y32, s>>>(nx, ny, p->fy.d32, p->TXy, p->fhat32, conv, ygx, ytiles)));
             TIMED(KS_XACC, (p->kern.xi32a<<<gs(xrt, CAP_XI32A), 256, smx32r, s>>>(g, p->fx.d32, p->Lx, p->fhat32, p_np1, p->st, xrt)));
             ra.slot = sw;
@@ -1104,6 +1141,7 @@ extern "C" int fizzy_proj_solve_noalloc(const fizzy_proj_desc *d, const double *
     if (vrc) return vrc;
     if (!phi || !p_n || !p_nm1 || !u || !v || !w || !p_np1) return FIZZY_ERR_INVALID;
     if (d->precision != FIZZY_PREC_FP64 || d->flags != 0) return FIZZY_ERR_INVALID;
+    if (d->periodic_z) return FIZZY_ERR_UNSUPPORTED;  // walls in z only
     const int nx = d->nx, ny = d->ny, nz = d->nz;
     if ((long long)nx * ny * nz > kNaMaxCells || nx > kNaMaxN || ny > kNaMaxN || nz > kNaMaxNz)
         return FIZZY_ERR_UNSUPPORTED;
@@ -1204,6 +1242,7 @@ extern "C" int fizzy_proj_solve_noalloc(const fizzy_proj_desc *d, const double *
     g.nz = nz;
     g.bcx = d->bc_x;
     g.bcy = d->bc_y;
+    g.perz = d->periodic_z ? 1 : 0;
     g.rny = (unsigned)((1ull << 32) / (unsigned)ny + 1);
     physics_consts(g, d->rho_l, d->rho_g, d->dt, d->dx, d->dy, sig);
     g.idx2 = 1.0 / (d->dx * d->dx);

@@ -35,6 +35,7 @@ enum { BC_PERIODIC = 0, BC_NEUMANN = 1 };
 struct GridDev {
     int nx, ny, nz;
     int bcx, bcy;
+    int perz;          // 1: periodic z (plane nz-1 joins plane 0 through the seam face nz-1/2)
     unsigned rny;      // multiply-high reciprocal of ny (fdiv)
     // face-flux constants.  The split-term flux of a face with spacing h is
     // q' = u* + dt |drho|/(rho0 h) * t/(|drho| t + 2 rho0) * (p^_b - p^_a),
@@ -53,7 +54,10 @@ struct GridDev {
     // Laplacian / divergence constants
     double idx2, idy2;    // 1/dx^2, 1/dy^2
     double idx1, idy1;    // 1/dx, 1/dy
-    // per-k tables (device, FP64, length nz)
+    // per-k tables (device, FP64, length nz).  "0 at k = nz-1" holds for z
+    // walls; with periodic z that entry belongs to the seam face, whose centre
+    // distance is dzc_(nz-1/2) = (dzf_0 + dzf_(nz-1))/2, and a_0 couples plane
+    // 0 to plane nz-1 through it.
     const double *faz;    // a' of the z face above k: rho0 dzc_(k+1/2)/dt  (0 at k = nz-1)
     const double *frz;    // r' of that face: 2 rho0^2 dzc_(k+1/2)/(dt |drho|)  (0 at k = nz-1)
     const double *dvz;    // rho0/dzf_k
@@ -222,9 +226,11 @@ __device__ __forceinline__ void flux_body(const GridDev &g, int kc, VB vb, const
         }
         __syncthreads();
         double ph_t = 0.0, psi_t = 0.0;
-        if (k + 1 < g.nz) {
-            psi_t = psi(base + plane + own);
-            ph_t = fmaT(2.0, pn[base + plane + own], -pnm1[base + plane + own]);
+        const bool top_face = k + 1 < g.nz || g.perz;  // periodic z: the seam joins plane 0
+        if (top_face) {
+            const size_t nxt = (k + 1 < g.nz) ? base + plane : 0;
+            psi_t = psi(nxt + own);
+            ph_t = fmaT(2.0, pn[nxt + own], -pnm1[nxt + own]);
         }
         if (in) {
             const size_t c = base + (size_t)j * g.nx + i;
@@ -242,7 +248,7 @@ __device__ __forceinline__ void flux_body(const GridDev &g, int kc, VB vb, const
                 q = var ? face_flux(psi_c, s_phi[ty + 1][tx], ph_c, s_ph[ty + 1][tx], vc, g.fay, g.fry, g.fsh) : vc;
             qy[c] = q;
             q = 0.0;
-            if (k + 1 < g.nz) q = var ? face_flux(psi_c, psi_t, ph_c, ph_t, wc, g.faz[k], g.frz[k], g.fsh) : wc;
+            if (top_face) q = var ? face_flux(psi_c, psi_t, ph_c, ph_t, wc, g.faz[k], g.frz[k], g.fsh) : wc;
             qz[c] = q;
         }
         ph_c = ph_t;
@@ -300,7 +306,8 @@ __device__ __forceinline__ QFaces div_q_ld(const GridDev &g, int i, int j, int k
     q.qs = (j > 0) ? ldp<CG>(qy + c - g.nx)
                    : (g.bcy == BC_PERIODIC ? ldp<CG>(qy + c + (size_t)(g.ny - 1) * g.nx) : 0.0);
     q.qt = ldp<CG>(qz + c);
-    q.qb = (k > 0) ? ldp<CG>(qz + c - (size_t)g.nx * g.ny) : 0.0;
+    q.qb = (k > 0) ? ldp<CG>(qz + c - (size_t)g.nx * g.ny)
+                   : (g.perz ? ldp<CG>(qz + c + (size_t)(g.nz - 1) * g.nx * g.ny) : 0.0);
     return q;
 }
 __device__ __forceinline__ double div_q_eval(const QFaces &q, double cx, double cy, double cz) {
@@ -330,8 +337,8 @@ __device__ __forceinline__ double lap(const GridDev &g, int i, int j, int k, con
     if (j > 0) ps = ldp<CG>(p + c - g.nx);
     else ps = (g.bcy == BC_PERIODIC) ? ldp<CG>(p + c + (size_t)(g.ny - 1) * g.nx) : pc;
     const size_t pl = (size_t)g.nx * g.ny;
-    const double pt = (k < g.nz - 1) ? ldp<CG>(p + c + pl) : pc;
-    const double pb = (k > 0) ? ldp<CG>(p + c - pl) : pc;
+    const double pt = (k < g.nz - 1) ? ldp<CG>(p + c + pl) : (g.perz ? ldp<CG>(p + c - k * pl) : pc);
+    const double pb = (k > 0) ? ldp<CG>(p + c - pl) : (g.perz ? ldp<CG>(p + c + (g.nz - 1) * pl) : pc);
     double acc = mulT((pe - pc) - (pc - pw), g.idx2);
     acc = fmaT((pn_ - pc) - (pc - ps), g.idy2, acc);
     acc = fmaT(g.lzc[k], pt - pc, acc);
@@ -847,13 +854,133 @@ __device__ __forceinline__ void thomas_line_ring(int nz, size_t plane, T *d, siz
     cp_async_wait<0>();
 }
 
+// Periodic z: each (kx, ky) line is a cyclic tridiagonal system A p = f (the
+// seam couples row 0 to p_(nz-1) by a_0 and row nz-1 to p_0 by c_(nz-1)).
+// It is solved with the Sherman-Morrison formula: A = B + u v^T with
+// u = (gamma, 0, ..., 0, c_(nz-1)), v = (1, 0, ..., 0, a_0/gamma),
+// gamma = -b_0, B tridiagonal with its first and last diagonal entries
+// changed; then p = y - (v^T y) q with B y = f and q = B^(-1) u / (1 + v^T B^(-1) u).
+// The tables hold B's factorisation (m_k, 1/beta_k), q_k, and the weights w_k
+// for which v^T y = sum_k w_k g_k, g the forward-eliminated right-hand side
+// (back substitution makes y_0 a fixed combination of the g_k), so v^T y is
+// accumulated during the forward sweep and the back substitution writes
+// p_k = y_k - (v^T y) q_k directly: 5 instructions per point instead of 3,
+// one ring item more per stage, and no extra sweep.
+template <typename T>
+__device__ __forceinline__ void thomas_line_ring_cyc(int nz, size_t plane, T *d, size_t ts, size_t tb,
+                                                     const T *__restrict__ mtab,
+                                                     const T *__restrict__ ibtab,
+                                                     const T *__restrict__ cup,
+                                                     const T *__restrict__ wtab,
+                                                     const T *__restrict__ qtab, T *ring) {
+    constexpr int U = THOMAS_U, G = THOMAS_S / THOMAS_U;
+    const int tid = threadIdx.x;
+    // slot (stage, item): item 0 = line value, 1 = m_k or 1/beta_k, 2 = w_k or q_k
+    auto slot = [&](int stage, int item) -> T * {
+        return ring + ((size_t)(stage * 3 + item) * THOMAS_BLOCK + tid);
+    };
+    const int nb = (nz - 1 + U - 1) / U;
+    auto issue_f = [&](int b) {
+        const int s0 = (b % G) * U;
+#pragma unroll
+        for (int q = 0; q < U; ++q) {
+            const int k = 1 + b * U + q;
+            if (k < nz) {
+                cp_async<sizeof(T)>(slot(s0 + q, 1), mtab + (size_t)k * ts + tb);
+                cp_async<sizeof(T)>(slot(s0 + q, 2), wtab + (size_t)k * ts + tb);
+                cp_async<sizeof(T)>(slot(s0 + q, 0), d + (size_t)k * plane);
+            }
+        }
+        cp_async_commit();
+    };
+#pragma unroll 1
+    for (int b = 0; b < G; ++b) issue_f(b);
+    T prev = d[0];
+    T acc = mulT(wtab[tb], prev);  // v^T y, accumulated over k
+#pragma unroll 1
+    for (int b = 0; b < nb; ++b) {
+        cp_async_wait<G - 1>();
+        const int s0 = (b % G) * U, k0 = 1 + b * U;
+        T mv[U], wv[U], fv[U], out[U];
+#pragma unroll
+        for (int q = 0; q < U; ++q) {
+            mv[q] = *slot(s0 + q, 1);
+            wv[q] = *slot(s0 + q, 2);
+            fv[q] = *slot(s0 + q, 0);
+        }
+#pragma unroll
+        for (int q = 0; q < U; ++q) {
+            if (k0 + q < nz) {
+                prev = fmaT(-mv[q], prev, fv[q]);
+                acc = fmaT(wv[q], prev, acc);
+            }
+            out[q] = prev;
+        }
+        issue_f(b + G);
+#pragma unroll
+        for (int q = 0; q < U; ++q)
+            if (k0 + q < nz) d[(size_t)(k0 + q) * plane] = out[q];
+    }
+    cp_async_wait<0>();
+    const T sv = acc;
+    // ---- backward: y carried, p_k = y_k - (v^T y) q_k stored
+    prev = mulT(prev, ibtab[(size_t)(nz - 1) * ts + tb]);
+    d[(size_t)(nz - 1) * plane] = fmaT(-sv, qtab[(size_t)(nz - 1) * ts + tb], prev);
+    auto issue_b = [&](int b) {
+        const int s0 = (b % G) * U;
+#pragma unroll
+        for (int q = 0; q < U; ++q) {
+            const int k = nz - 2 - b * U - q;
+            if (k >= 0) {
+                cp_async<sizeof(T)>(slot(s0 + q, 1), ibtab + (size_t)k * ts + tb);
+                cp_async<sizeof(T)>(slot(s0 + q, 2), qtab + (size_t)k * ts + tb);
+                cp_async<sizeof(T)>(slot(s0 + q, 0), d + (size_t)k * plane);
+            }
+        }
+        cp_async_commit();
+    };
+#pragma unroll 1
+    for (int b = 0; b < G; ++b) issue_b(b);
+#pragma unroll 1
+    for (int b = 0; b < nb; ++b) {
+        cp_async_wait<G - 1>();
+        const int s0 = (b % G) * U, k0 = nz - 2 - b * U;
+        T iv[U], qv[U], dv[U], cv[U], out[U];
+#pragma unroll
+        for (int q = 0; q < U; ++q) {
+            iv[q] = *slot(s0 + q, 1);
+            qv[q] = *slot(s0 + q, 2);
+            dv[q] = *slot(s0 + q, 0);
+            cv[q] = (k0 - q >= 0) ? cup[k0 - q] : (T)0;
+        }
+#pragma unroll
+        for (int q = 0; q < U; ++q) {
+            if (k0 - q >= 0) {
+                prev = mulT(fmaT(-cv[q], prev, dv[q]), iv[q]);
+                out[q] = fmaT(-sv, qv[q], prev);
+            } else {
+                out[q] = prev;
+            }
+        }
+        issue_b(b + G);
+#pragma unroll
+        for (int q = 0; q < U; ++q)
+            if (k0 - q >= 0) d[(size_t)(k0 - q) * plane] = out[q];
+    }
+    cp_async_wait<0>();
+}
+
 // The singular (0,0) line, solved by one warp.  With a_k = dzf_k (f_k - fbar)
 // (fbar the dzf-weighted mean, removed so the line is compatible), the flux
 // through face k+1/2 is the inclusive prefix sum F_(k+1/2) = sum_(k'<=k) a_k'
 // (zero flux through the bottom wall) and the pressure is the exclusive prefix
 // sum p_k = sum_(k'<k) dzc_(k'+1/2) F_(k'+1/2) (p_0 = 0); both sums run as warp
 // scans over chunks of 32 planes.  Finally the dzf-weighted mean of p is
-// removed (the pressure gauge).
+// removed (the pressure gauge).  With periodic z the flux through the seam is
+// not zero but a constant C added to every face flux, F_(k+1/2) = C + S_k;
+// going once around the periodic line must return to the same pressure,
+// sum_k dzc_(k+1/2) F_(k+1/2) = 0, so C = -sum_k dzc_(k+1/2) S_k / sum_k dzc_(k+1/2),
+// found by a first scan over the line.
 __device__ __forceinline__ double warp_sum(double v) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
@@ -874,6 +1001,22 @@ __device__ void singular_line_warp(const GridDev &g, T *d, size_t plane) {
     for (int k = lane; k < nz; k += 32) s = fmaT(g.dzf[k], (double)ldp<CG>(d + (size_t)k * plane), s);
     const double fbar = mulT(warp_sum(s), g.inv_lz);
     double Fc = 0.0, pc = 0.0, ps = 0.0;
+    if (g.perz) {
+        double Sc = 0.0, num = 0.0, den = 0.0;
+        for (int k0 = 0; k0 < nz; k0 += 32) {
+            const int k = k0 + lane;
+            double a = 0.0, h = 0.0;
+            if (k < nz) {
+                a = mulT(g.dzf[k], (double)ldp<CG>(d + (size_t)k * plane) - fbar);
+                h = g.dzc[k];  // the seam at k = nz-1
+            }
+            const double S = warp_inclusive_scan(a, lane) + Sc;
+            num = fmaT(h, S, num);
+            den += h;
+            Sc = __shfl_sync(0xffffffffu, S, 31);
+        }
+        Fc = -warp_sum(num) / warp_sum(den);
+    }
     for (int k0 = 0; k0 < nz; k0 += 32) {
         const int k = k0 + lane;
         double a = 0.0, h = 0.0;
@@ -992,6 +1135,9 @@ __global__ void __launch_bounds__(THOMAS_BLOCK) k_thomas(GridDev g, int Ux, int 
 template <typename T> constexpr size_t thomas_smem() {
     return (size_t)THOMAS_S * 2 * THOMAS_BLOCK * sizeof(T);
 }
+template <typename T> constexpr size_t thomas_cyc_smem() {
+    return (size_t)THOMAS_S * 3 * THOMAS_BLOCK * sizeof(T);
+}
 
 // u = q' - (dt/rho0) G p on non-wall faces (q' = dt q); wall faces 0.
 // 2 FP64 instructions per face.  Virtual block: 32 x 8 cells of plane z.
@@ -1019,7 +1165,11 @@ __device__ __forceinline__ void correct_body(const GridDev &g, const double *p, 
     }
     v[c] = r;
     r = 0.0;
-    if (k < g.nz - 1) r = fmaT(-g.cgz[k], ldp<CG>(p + c + (size_t)g.nx * g.ny) - pc, ldp<CG>(qz + c));
+    if (k < g.nz - 1 || g.perz) {
+        const size_t pl = (size_t)g.nx * g.ny;
+        const size_t t = (k < g.nz - 1) ? c + pl : c - (size_t)k * pl;  // periodic z: the seam
+        r = fmaT(-g.cgz[k], ldp<CG>(p + t) - pc, ldp<CG>(qz + c));
+    }
     w[c] = r;
 }
 
@@ -1074,7 +1224,9 @@ __device__ __forceinline__ void resid_body(const GridDev &g, int kc, const RArgs
     const long long oS = (j > 0) ? -(long long)g.nx : (long long)(g.ny - 1) * g.nx;
     size_t c = on ? cidx(g, i, j, k0) : 0;
     double pc = on ? ldp<CG>(a.p + c) : 0.0;
-    double db = (on && k0 > 0) ? pc - ldp<CG>(a.p + c - pl) : 0.0;
+    double db = 0.0;
+    if (on && k0 > 0) db = pc - ldp<CG>(a.p + c - pl);
+    else if (on && g.perz) db = pc - ldp<CG>(a.p + c + (size_t)(g.nz - 1) * pl);  // seam
     unsigned long long mx = 0ull;
     int buf = 0;
     for (int k = k0; k < k1; ++k) {
@@ -1085,11 +1237,13 @@ __device__ __forceinline__ void resid_body(const GridDev &g, int kc, const RArgs
             if (k < g.nz - 1) {
                 pt = ldp<CG>(a.p + c + pl);
                 dt = pt - pc;
+            } else if (g.perz) {
+                dt = ldp<CG>(a.p + c - (size_t)k * pl) - pc;  // seam to plane 0
             }
             if (CORR) {
                 a.u[c] = (g.bcx == BC_NEUMANN && i == g.nx - 1) ? 0.0 : fmaT(-g.cgx, de, ldp<CG>(a.qx + c));
                 a.v[c] = (g.bcy == BC_NEUMANN && j == g.ny - 1) ? 0.0 : fmaT(-g.cgy, dn, ldp<CG>(a.qy + c));
-                a.w[c] = (k < g.nz - 1) ? fmaT(-g.cgz[k], dt, ldp<CG>(a.qz + c)) : 0.0;
+                a.w[c] = (k < g.nz - 1 || g.perz) ? fmaT(-g.cgz[k], dt, ldp<CG>(a.qz + c)) : 0.0;
             }
             sdn[(buf * FLUX_BY + ty) * FLUX_BX + tx] = dn;
         }
@@ -1169,6 +1323,36 @@ __global__ void __launch_bounds__(256) k_correct_if(GridDev g, const double *__r
     }
 }
 
+// Periodic z: the cyclic z-solves (thomas_line_ring_cyc), lines as in
+// k_thomas; the singular (0,0) line takes its periodic branch.
+template <typename T>
+__global__ void __launch_bounds__(THOMAS_BLOCK) k_thomas_cyc(GridDev g, int Ux, int Uy,
+                                                             const T *__restrict__ mtab,
+                                                             const T *__restrict__ ibtab,
+                                                             const T *__restrict__ cup,
+                                                             const T *__restrict__ wtab,
+                                                             const T *__restrict__ qtab, T *data,
+                                                             const int *conv, int ntiles) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    if (conv && *(volatile const int *)conv) return;
+    const size_t plane = (size_t)g.nx * g.ny;
+    const size_t ts = (size_t)Ux * Uy;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int line_base = t * THOMAS_BLOCK;
+        if (line_base == 0 && threadIdx.x < 32) {
+            singular_line_warp<T, false>(g, data, plane);  // line (0,0)
+            if (threadIdx.x == 0) continue;
+        }
+        const int line = line_base + threadIdx.x;
+        if (line >= g.nx * g.ny) continue;
+        const int j = line / g.nx, i = line - j * g.nx;
+        const int ux = (g.bcx == BC_PERIODIC) ? min(i, g.nx - i) : i;
+        const int uy = (g.bcy == BC_PERIODIC) ? min(j, g.ny - j) : j;
+        thomas_line_ring_cyc<T>(g.nz, plane, data + line, ts, (size_t)uy * Ux + ux, mtab, ibtab, cup,
+                                wtab, qtab, (T *)smem_raw);
+    }
+}
+
 // max |D u| (diagnostics).
 __global__ void __launch_bounds__(256) k_divmax(GridDev g, const double *__restrict__ u,
                                                 const double *__restrict__ v,
@@ -1182,8 +1366,9 @@ __global__ void __launch_bounds__(256) k_divmax(GridDev g, const double *__restr
         const double uw = (i > 0) ? u[c - 1] : (g.bcx == BC_PERIODIC ? u[c + g.nx - 1] : 0.0);
         const double vn = (g.bcy == BC_NEUMANN && j == g.ny - 1) ? 0.0 : v[c];
         const double vs = (j > 0) ? v[c - g.nx] : (g.bcy == BC_PERIODIC ? v[c + (size_t)(g.ny - 1) * g.nx] : 0.0);
-        const double wt = (k == g.nz - 1) ? 0.0 : w[c];
-        const double wb = (k > 0) ? w[c - (size_t)g.nx * g.ny] : 0.0;
+        const double wt = (k == g.nz - 1 && !g.perz) ? 0.0 : w[c];
+        const double wb = (k > 0) ? w[c - (size_t)g.nx * g.ny]
+                                  : (g.perz ? w[c + (size_t)(g.nz - 1) * g.nx * g.ny] : 0.0);
         const double d = fmaT(ue - uw, g.idx1, fmaT(vn - vs, g.idy1, (wt - wb) * g.izf[k]));
         mx = absbits(d);
     }
@@ -1233,6 +1418,83 @@ __global__ void k_ztables(int Ux, int Uy, int nz, const double *__restrict__ lam
             if (mt32) {
                 mt32[(size_t)k * ts + uu] = __double2float_rn(m);
                 ib32[(size_t)k * ts + uu] = __double2float_rn(r);
+            }
+        }
+    }
+}
+
+// Periodic-z tables (Sherman-Morrison form of the cyclic z-solve, see
+// thomas_line_ring_cyc), one thread per eigenvalue pair.  With b_k the
+// diagonal -(a_k + c_k) + lambda, gamma = -b_0, alpha = a_0 (row 0's seam
+// coupling) and beta_c = c_(nz-1) (row nz-1's): B has diagonal b_0 - gamma,
+// b_1, ..., b_(nz-2), b_(nz-1) - alpha beta_c / gamma; m_k and 1/beta_k factor
+// B as in k_ztables; w_k = (1/beta_k) prod_(j<k) (-c_j / beta_j), plus
+// (alpha/gamma)/beta_(nz-1) at k = nz-1; q = B^(-1) (gamma, 0, ..., 0, beta_c),
+// divided by 1 + q_0 + (alpha/gamma) q_(nz-1).  Explicit round-to-nearest
+// operations; FP32 copies rounded from the FP64 values.  The singular pair
+// (0,0) gets zeros.
+__global__ void k_ztables_cyc(int Ux, int Uy, int nz, const double *__restrict__ lamx,
+                              const double *__restrict__ lamy, const double *__restrict__ A,
+                              const double *__restrict__ C, double *mt, double *ib, double *wt,
+                              double *qt, float *mt32, float *ib32, float *wt32, float *qt32) {
+    const size_t ts = (size_t)Ux * Uy;
+    for (size_t uu = (size_t)blockIdx.x * blockDim.x + threadIdx.x; uu < ts;
+         uu += (size_t)gridDim.x * blockDim.x) {
+        const int ux = (int)(uu % Ux), uy = (int)(uu / Ux);
+        auto at = [&](int k) { return (size_t)k * ts + uu; };
+        if (ux == 0 && uy == 0) {
+            for (int k = 0; k < nz; ++k) {
+                mt[at(k)] = ib[at(k)] = wt[at(k)] = qt[at(k)] = 0.0;
+                if (mt32) mt32[at(k)] = ib32[at(k)] = wt32[at(k)] = qt32[at(k)] = 0.f;
+            }
+            continue;
+        }
+        const double lam = __dadd_rn(lamx[ux], lamy[uy]);
+        const double b0 = __dadd_rn(-__dadd_rn(A[0], C[0]), lam);
+        const double gam = -b0;
+        const double ag = __ddiv_rn(A[0], gam);                 // alpha / gamma
+        const double corner = __dmul_rn(ag, C[nz - 1]);          // alpha beta_c / gamma
+        // factorisation of B
+        double beta = __dsub_rn(b0, gam);
+        mt[at(0)] = 0.0;
+        ib[at(0)] = __ddiv_rn(1.0, beta);
+        for (int k = 1; k < nz; ++k) {
+            const double m = __ddiv_rn(A[k], beta);
+            double bk = __dadd_rn(-__dadd_rn(A[k], C[k]), lam);
+            if (k == nz - 1) bk = __dsub_rn(bk, corner);
+            beta = __dsub_rn(bk, __dmul_rn(m, C[k - 1]));
+            mt[at(k)] = m;
+            ib[at(k)] = __ddiv_rn(1.0, beta);
+        }
+        // weights of y_0 in the forward-eliminated right-hand side
+        double P = 1.0;
+        for (int k = 0; k < nz; ++k) {
+            if (k > 0) P = __dmul_rn(P, __dmul_rn(-C[k - 1], ib[at(k - 1)]));
+            wt[at(k)] = __dmul_rn(ib[at(k)], P);
+        }
+        wt[at(nz - 1)] = __dadd_rn(wt[at(nz - 1)], __dmul_rn(ag, ib[at(nz - 1)]));
+        // q = B^(-1) u: forward elimination into qt, then back substitution in place
+        double g = gam;
+        qt[at(0)] = g;
+        for (int k = 1; k < nz; ++k) {
+            const double uk = (k == nz - 1) ? C[nz - 1] : 0.0;
+            g = __dsub_rn(uk, __dmul_rn(mt[at(k)], g));
+            qt[at(k)] = g;
+        }
+        double y = __dmul_rn(qt[at(nz - 1)], ib[at(nz - 1)]);
+        qt[at(nz - 1)] = y;
+        for (int k = nz - 2; k >= 0; --k) {
+            y = __dmul_rn(__dsub_rn(qt[at(k)], __dmul_rn(C[k], y)), ib[at(k)]);
+            qt[at(k)] = y;
+        }
+        const double iden = __ddiv_rn(1.0, __dadd_rn(1.0, __dadd_rn(qt[at(0)], __dmul_rn(ag, qt[at(nz - 1)]))));
+        for (int k = 0; k < nz; ++k) {
+            qt[at(k)] = __dmul_rn(qt[at(k)], iden);
+            if (mt32) {
+                mt32[at(k)] = __double2float_rn(mt[at(k)]);
+                ib32[at(k)] = __double2float_rn(ib[at(k)]);
+                wt32[at(k)] = __double2float_rn(wt[at(k)]);
+                qt32[at(k)] = __double2float_rn(qt[at(k)]);
             }
         }
     }

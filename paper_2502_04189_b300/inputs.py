@@ -351,6 +351,24 @@ def bubbles512_stretched_spec() -> CaseSpec:
     return bubbles_spec(512, 400, 6.0, 1.5, config=2)
 
 
+def emulsion_spec(n: int = 256, n_drops: int = 400, radius_cells: float = 8.0,
+                  config: int = 5) -> CaseSpec:
+    """n^3 unit triperiodic box (periodic x, y and z), standing in for the
+    paper's liquid-liquid emulsion in forced homogeneous isotropic turbulence
+    (its weak-scaling case): n_drops drops of the given radius (cells; 400 of
+    radius 8 fill about 5 % of 256^3), drops of density 0.8 in a carrier of
+    density 1 (an oil-in-water-like ratio; rho0 is then the drop density), a
+    k^-5/3 solenoidal u* of rms 1 with no wall envelope plus
+    uniform[-0.01, 0.01] noise, dt = 1e-4."""
+    return CaseSpec(nx=n, ny=n, nz=n, n_bubbles=n_drops, radius_cells=radius_cells,
+                    rho_l=0.8, rho_g=1.0, dt=1e-4, velocity="solenoidal", noise=0.01,
+                    config=config, bcz=PERIODIC)
+
+
+def emulsion256_spec() -> CaseSpec:
+    return emulsion_spec(256, 400, 8.0, config=5)
+
+
 BATCH_XY = (32, 48, 64, 96, 128, 192)
 SERVE_XY = (64, 96, 128, 192, 256, 384)
 

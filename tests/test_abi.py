@@ -83,6 +83,21 @@ def test_inject_stall_rejects_a_null_batch():
     assert _abi.lib().fizzy_proj_batch_inject_stall(None, 0, 1) == -1
 
 
+def test_periodic_z_descriptor_checks():
+    """periodic_z must be 0 or 1; it adds the Sherman-Morrison tables to the
+    plan's footprint; the allocation-free entry point refuses it before any
+    CUDA call."""
+    d, keep = F.make_desc(**base())
+    d.periodic_z = 2
+    h = ctypes.c_void_p()
+    assert _abi.lib().fizzy_proj_plan(ctypes.byref(h), ctypes.byref(d), None) == -1
+    assert not h.value
+    assert F.workspace_bytes(**base(periodic_z=True)) > F.workspace_bytes(**base())
+    d, keep = F.make_desc(**base(periodic_z=True))
+    fake = [ctypes.c_void_p(8)] * 7
+    assert _abi.lib().fizzy_proj_solve_noalloc(ctypes.byref(d), *fake, None) == -2
+
+
 def test_workspace_bytes_scale():
     b1 = F.workspace_bytes(**base())
     b2 = F.workspace_bytes(**base(nz=16))
