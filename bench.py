@@ -40,6 +40,7 @@ WORKLOADS = {
     "bubbles256": I.bubbles256_spec,
     "drop32": I.drop32_spec,
     "bubbles512_stretched": I.bubbles512_stretched_spec,
+    "emulsion256": I.emulsion256_spec,
 }
 
 
@@ -103,7 +104,7 @@ def fft_fp64_instr_per_point(n, dct):
     return per_complex / 2 + 1 + (2 if dct else 0)
 
 
-def path_roofline(value, nx, ny, bcx, bcy, mixed, sweeps, hbm_peak):
+def path_roofline(value, nx, ny, bcx, bcy, mixed, sweeps, hbm_peak, bcz=1):
     """The whole projection against its bounds: the algorithmic bytes of the
     pass sequence (the kernels' per-point bytes summed over the passes that
     ran; mixed: the refinement passes once per sweep, the stand-alone
@@ -111,7 +112,7 @@ def path_roofline(value, nx, ny, bcx, bcy, mixed, sweeps, hbm_peak):
     4 written: 80 B/pt), and the FP64 instructions per point against the
     nominal 0.625 T FP64 instructions/s."""
     per = algorithmic_per_point(nx, ny, mixed)
-    ins = fp64_instr_per_point(nx, ny, bcx, bcy, mixed)
+    ins = fp64_instr_per_point(nx, ny, bcx, bcy, mixed, bcz)
     if not mixed:
         b = sum(v[0] for v in per.values())
         n_ins = sum(ins.values())
@@ -132,14 +133,15 @@ def path_roofline(value, nx, ny, bcx, bcy, mixed, sweeps, hbm_peak):
             "fp64_issue_frac": value * n_ins / issue_peak, "sweeps": sweeps}
 
 
-def fp64_instr_per_point(nx, ny, bcx, bcy, mixed):
+def fp64_instr_per_point(nx, ny, bcx, bcy, mixed, bcz=1):
     """FP64 instructions per grid point of each kernel, counted from the code
-    (flux 6 per face + phat; divergence 6; z-solve 3; correction 6; mixed
+    (flux 6 per face + phat; divergence 6; z-solve 3, or 5 with periodic z
+    (the Sherman-Morrison dot product and correction); correction 6; mixed
     residual 10, fused with the correction 13)."""
     fx = fft_fp64_instr_per_point(nx, bcx == 1)
     fy = fft_fp64_instr_per_point(ny, bcy == 1)
     if not mixed:
-        return {"flux": 19, "div_fwdx": 6 + fx, "fwd_y": fy, "thomas": 3, "inv_y": fy,
+        return {"flux": 19, "div_fwdx": 6 + fx, "fwd_y": fy, "thomas": 5 if bcz == 0 else 3, "inv_y": fy,
                 "inv_x": fx, "correct": 6}
     return {"flux": 19, "div_fwdx": 6, "resid": 10, "resid_correct": 13, "inv_x_update": 1,
             "correct": 6}
@@ -229,6 +231,15 @@ def job_throughput(points_per_rank_step, steps, world, seconds):
     return points_per_rank_step * steps * world / seconds
 
 
+def slab_spec(spec, nz=32):
+    """A bounded sample of a workload for the CPU oracle: the same recipe on a
+    slab of nz planes (same x/y transform lengths and spacing, z length and
+    drop count scaled)."""
+    k = min(spec.nz, nz)
+    return I.CaseSpec(**{**spec.__dict__, "nz": k, "lz": spec.lz * k / spec.nz,
+                         "n_bubbles": max(1, spec.n_bubbles * k // spec.nz)})
+
+
 def oracle_time(case, reps=1):
     """Wall time of the CPU oracle's projection on case (rank 0 host cores)."""
     import oracle as O
@@ -248,8 +259,7 @@ def run_reference(args):
         return 0
     import oracle as O
     spec = WORKLOADS[args.workload]()
-    sample_spec = I.CaseSpec(**{**spec.__dict__, "nz": min(spec.nz, 32), "lz": spec.lz * min(spec.nz, 32) / spec.nz,
-                                "n_bubbles": max(1, spec.n_bubbles * min(spec.nz, 32) // spec.nz)})
+    sample_spec = slab_spec(spec)
     case = I.make_case(sample_spec)
     for _ in range(args.warmup):
         O.project_case(case)
@@ -365,7 +375,7 @@ def run_fizzy(args):
         t_hbm = b_pt / (hbm_peak * 1e9)
         t_alu = fl_pt / (FP64_PEAK_NOMINAL * 1e12)
         traffic = (measured_traffic(dom, prec == F.MIXED)
-                   if (spec.nx, spec.ny, spec.nz) == (256, 256, 256) else None)
+                   if args.workload == "bubbles256" else None)
         if t_alu > t_hbm:
             roof = {"bound": "alu", "achieved": tfl, "peak": FP64_PEAK_NOMINAL, "unit": "TFLOP/s",
                     "frac": tfl / FP64_PEAK_NOMINAL, "traffic": traffic, "kernel": dom,
@@ -382,7 +392,8 @@ def run_fizzy(args):
         # the FP64 issue rate the ALU bound really is: FP64 instructions per
         # point against the nominal 0.625 T FP64 instructions/s (1.25 TFLOP/s
         # counts an FMA as two)
-        ipt = fp64_instr_per_point(spec.nx, spec.ny, spec.bcx, spec.bcy, prec == F.MIXED).get(dom)
+        ipt = fp64_instr_per_point(spec.nx, spec.ny, spec.bcx, spec.bcy, prec == F.MIXED,
+                                   spec.bcz).get(dom)
         if ipt:
             ach = ipt * npts / avg_s / 1e12
             roof["fp64_issue"] = {"instr_per_pt": ipt, "achieved": ach, "peak": FP64_PEAK_NOMINAL / 2,
@@ -440,9 +451,14 @@ def run_fizzy(args):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        t_or, cores = oracle_time(case, reps=2)
-        cpu = {"value": npts / t_or, "unit": "pts/s", "cores": cores, "kind": "oracle",
-               "sample": "one full %dx%dx%d projection (best of 2)" % (spec.nx, spec.ny, spec.nz)}
+        # periodic z: the oracle's dense cyclic z-line solves grow as nz^3, so
+        # it is timed on a 32-plane slab of the same recipe
+        ocase = case if spec.bcz == I.NEUMANN else I.make_case(slab_spec(spec))
+        t_or, cores = oracle_time(ocase, reps=2)
+        os_ = ocase.spec
+        cpu = {"value": ocase.npts / t_or, "unit": "pts/s", "cores": cores, "kind": "oracle",
+               "sample": "one full %dx%dx%d projection (best of 2)%s" % (
+                   os_.nx, os_.ny, os_.nz, "" if ocase is case else ", a slab of the workload")}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "pts/s", "n_gpus": world,
@@ -451,12 +467,14 @@ def run_fizzy(args):
                 "dtype": "f64" if prec == F.FP64 else "f32+f64",
                 "data": "synthetic",
                 "config": {"workload": args.workload, "grid": [spec.nx, spec.ny, spec.nz],
-                           "precision": args.precision, "bc": "periodic x,y; walls z",
+                           "precision": args.precision, "bc": "%s x, %s y, %s z" % tuple(
+                               "periodic" if b == I.PERIODIC else "walls" for b in (spec.bcx, spec.bcy, spec.bcz)),
                            "l2": "inputs (6 x %d MiB) larger than L2" % (npts * 8 >> 20),
                            "parallelism": "replicas" if world > 1 else "single"},
                 "gpu_launches": launches, "roofline": roof,
                 "path_roofline": path_roofline(value, spec.nx, spec.ny, spec.bcx, spec.bcy,
-                                               prec == F.MIXED, int(st["iterations"]), hbm_peak),
+                                               prec == F.MIXED, int(st["iterations"]), hbm_peak,
+                                               spec.bcz),
                 "cpu_baseline": cpu, "e2e": e2e,
                 "clocks": clk, "kernels": kernels,
                 "stats": {k: st[k] for k in ("iterations", "converged", "relres")},

@@ -94,8 +94,8 @@ typedef struct fizzy_proj_desc {
                           /* seam face nz-1/2 joins plane nz-1 to plane 0, centre distance      */
                           /* (dzf_0 + dzf_(nz-1))/2, w[nz-1] is its velocity.  Each z-line is a */
                           /* cyclic tridiagonal system (Sherman-Morrison).  Not accepted by     */
-                          /* fizzy_proj_solve_noalloc or the batched executor                   */
-                          /* (FIZZY_ERR_UNSUPPORTED).  Other values: FIZZY_ERR_INVALID.         */
+                          /* fizzy_proj_solve_noalloc (FIZZY_ERR_UNSUPPORTED).  Other values:   */
+                          /* FIZZY_ERR_INVALID.                                                 */
 } fizzy_proj_desc;
 
 /* Diagnostics of the last solve (host memory). */

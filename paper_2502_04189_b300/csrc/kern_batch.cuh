@@ -66,7 +66,9 @@ struct BatchInst {
     float *fhat32;
     double *f;
     const double *mtab64, *ibtab64, *cup64;
+    const double *wtab64, *qtab64;  // periodic z (else null)
     const float *mtab32, *ibtab32, *cup32;
+    const float *wtab32, *qtab32;
     DevStats *st;
     double *usq_part, *usq_sum;
     int n_usq_part;
@@ -181,13 +183,13 @@ __device__ __forceinline__ void batch_run_tile(const BatchInst &I, const BatchIt
         break;
     case BK_TH64:
         thomas_body<double, false, true>(g, I.Ux, I.Uy, I.mtab64, I.ibtab64, I.cup64, I.fhat64,
-                                         nullptr, tile * BATCH_THREADS, nullptr);
+                                         nullptr, tile * BATCH_THREADS, nullptr, I.wtab64, I.qtab64);
         break;
     case BK_TH32:
     case BK_TH32C:
         thomas_body<float, false, true>(g, I.Ux, I.Uy, I.mtab32, I.ibtab32, I.cup32, I.fhat32,
                                         kind == BK_TH32C ? &I.st->converged : nullptr,
-                                        tile * BATCH_THREADS, nullptr);
+                                        tile * BATCH_THREADS, nullptr, I.wtab32, I.qtab32);
         break;
     case BK_XI64:
         xinv_body<double, XI_STORE, true>(g, I.fx64, I.Lx, I.fhat64, I.p, I.st, tile, smem);

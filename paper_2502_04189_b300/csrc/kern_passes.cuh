@@ -1091,16 +1091,76 @@ __device__ __forceinline__ void thomas_line_reg(int nz, size_t plane, T *d, size
     }
 }
 
+// Periodic-z form of thomas_line_reg (the cyclic solve of
+// thomas_line_ring_cyc with register prefetch), for the persistent batch kernel.
+template <typename T, bool CG>
+__device__ __forceinline__ void thomas_line_reg_cyc(int nz, size_t plane, T *d, size_t ts, size_t tb,
+                                                    const T *__restrict__ mtab,
+                                                    const T *__restrict__ ibtab,
+                                                    const T *__restrict__ cup,
+                                                    const T *__restrict__ wtab,
+                                                    const T *__restrict__ qtab) {
+    constexpr int U = THOMAS_U;
+    T prev = ldp<CG>(d);
+    T acc = mulT(wtab[tb], prev);
+    int k = 1;
+    for (; k + U <= nz; k += U) {
+        T fv[U], mv[U], wv[U];
+#pragma unroll
+        for (int q = 0; q < U; ++q) {
+            mv[q] = mtab[(size_t)(k + q) * ts + tb];
+            wv[q] = wtab[(size_t)(k + q) * ts + tb];
+            fv[q] = ldp<CG>(d + (size_t)(k + q) * plane);
+        }
+#pragma unroll
+        for (int q = 0; q < U; ++q) {
+            prev = fmaT(-mv[q], prev, fv[q]);
+            acc = fmaT(wv[q], prev, acc);
+            d[(size_t)(k + q) * plane] = prev;
+        }
+    }
+    for (; k < nz; ++k) {
+        prev = fmaT(-mtab[(size_t)k * ts + tb], prev, ldp<CG>(d + (size_t)k * plane));
+        acc = fmaT(wtab[(size_t)k * ts + tb], prev, acc);
+        d[(size_t)k * plane] = prev;
+    }
+    const T sv = acc;
+    prev = mulT(prev, ibtab[(size_t)(nz - 1) * ts + tb]);
+    d[(size_t)(nz - 1) * plane] = fmaT(-sv, qtab[(size_t)(nz - 1) * ts + tb], prev);
+    k = nz - 2;
+    for (; k - U + 1 >= 0; k -= U) {
+        T dv[U], iv[U], cv[U], qv[U];
+#pragma unroll
+        for (int q = 0; q < U; ++q) {
+            iv[q] = ibtab[(size_t)(k - q) * ts + tb];
+            qv[q] = qtab[(size_t)(k - q) * ts + tb];
+            cv[q] = cup[k - q];
+            dv[q] = ldp<CG>(d + (size_t)(k - q) * plane);
+        }
+#pragma unroll
+        for (int q = 0; q < U; ++q) {
+            prev = mulT(fmaT(-cv[q], prev, dv[q]), iv[q]);
+            d[(size_t)(k - q) * plane] = fmaT(-sv, qv[q], prev);
+        }
+    }
+    for (; k >= 0; --k) {
+        prev = mulT(fmaT(-cup[k], prev, ldp<CG>(d + (size_t)k * plane)), ibtab[(size_t)k * ts + tb]);
+        d[(size_t)k * plane] = fmaT(-sv, qtab[(size_t)k * ts + tb], prev);
+    }
+}
+
 // Lines are numbered line = i + nx*j (one thread each); one virtual block
 // covers lines line_base .. line_base + blockDim - 1.  Warp 0 of the block
 // holding line 0 first solves the singular (0,0) line.  Both half-complex
 // slots i and nx-i of a periodic direction use the table of wavenumber
-// min(i, nx-i).  ASYNC: shared-memory ring (THOMAS_S*2*blockDim values);
-// otherwise register prefetch.
+// min(i, nx-i).  ASYNC: shared-memory ring (THOMAS_S*2*blockDim values;
+// walls in z only, periodic z has k_thomas_cyc); otherwise register prefetch,
+// with the cyclic solve when g.perz (tables wtab, qtab).
 template <typename T, bool ASYNC, bool CG>
 __device__ __forceinline__ void thomas_body(const GridDev &g, int Ux, int Uy, const T *mtab,
                                             const T *ibtab, const T *cup, T *data, const int *conv,
-                                            int line_base, T *ring) {
+                                            int line_base, T *ring, const T *wtab = nullptr,
+                                            const T *qtab = nullptr) {
     if (conv && ldp<CG>(conv)) return;
     const size_t plane = (size_t)g.nx * g.ny;
     if (line_base == 0 && threadIdx.x < 32) {
@@ -1116,6 +1176,7 @@ __device__ __forceinline__ void thomas_body(const GridDev &g, int Ux, int Uy, co
     const size_t ts = (size_t)Ux * Uy;
     T *d = data + line;
     if (ASYNC) thomas_line_ring<T>(g.nz, plane, d, ts, tb, mtab, ibtab, cup, ring);
+    else if (g.perz) thomas_line_reg_cyc<T, CG>(g.nz, plane, d, ts, tb, mtab, ibtab, cup, wtab, qtab);
     else thomas_line_reg<T, CG>(g.nz, plane, d, ts, tb, mtab, ibtab, cup);
 }
 

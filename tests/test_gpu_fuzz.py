@@ -26,7 +26,9 @@ pytestmark = pytest.mark.gpu
 LENGTHS = (2, 3, 4, 6, 8, 9, 12, 16, 18, 24, 27, 32, 36, 48, 54, 64, 72, 96, 128, 256, 512)
 
 
-def fuzz_specs(n=32, seed=2024):
+def fuzz_specs(n=32, seed=2024, bcz_mix=False):
+    """n random specs; with bcz_mix each draw also picks walls or periodic z
+    (the draws of the wall-only lists stay as they were)."""
     rng = np.random.default_rng(seed)
     out = []
     while len(out) < n:
@@ -37,17 +39,20 @@ def fuzz_specs(n=32, seed=2024):
         light_drops = bool(rng.random() < 0.7)
         ratio = float(10 ** rng.uniform(0, 3))
         rho_g, rho_l = (1.0 / ratio, 1.0) if light_drops else (1.0, 1.0 / ratio)
+        bcz = int(rng.integers(0, 2)) if bcz_mix else I.NEUMANN
         out.append(I.CaseSpec(
             nx=nx, ny=ny, nz=nz, bcx=int(rng.integers(0, 2)), bcy=int(rng.integers(0, 2)),
             beta=float(rng.uniform(0.5, 2.0)) if rng.random() < 0.5 else 0.0,
             n_bubbles=int(rng.integers(1, 4)), radius_cells=float(rng.uniform(0.5, 4.0)),
             rho_l=rho_l, rho_g=rho_g, dt=float(10 ** rng.uniform(-4, -2)),
             velocity="iid" if rng.random() < 0.3 else "solenoidal",
-            config=60, instance=len(out)))
+            config=60, instance=len(out), bcz=bcz))
     return out
 
 
 SPECS = fuzz_specs()
+# walls or periodic z drawn per case (triperiodic boxes among them)
+PZ_SPECS = fuzz_specs(24, seed=2025, bcz_mix=True)
 
 
 def velocity_floor(case, ref):
@@ -61,30 +66,40 @@ def velocity_floor(case, ref):
     return s.dt / rho0 * 2 * np.finfo(np.float64).eps * pmax / hmin / umax
 
 
-@pytest.mark.parametrize("i", range(len(SPECS)))
-def test_fuzz_matches_oracle(cuda_ok, i):
-    c = I.make_case(SPECS[i])
+def check_against_oracle(spec):
+    c = I.make_case(spec)
     ref = O.project_case(c)
     floor = velocity_floor(c, ref)
     got = gpu_project(c, F.FP64)
     ep, eu = compare(c, got, ref)
-    assert ep <= 1e-12 and eu <= max(1e-12, 10 * floor), (SPECS[i], ep, eu, floor)
-    assert got["stats"]["div_metric"] <= 1e-10, SPECS[i]
+    assert ep <= 1e-12 and eu <= max(1e-12, 10 * floor), (spec, ep, eu, floor)
+    assert got["stats"]["div_metric"] <= 1e-10, spec
     got = gpu_project(c, F.MIXED)
     st = got["stats"]
-    assert st["converged"] == 1 and st["relres"] <= 1e-10, (SPECS[i], st)
+    assert st["converged"] == 1 and st["relres"] <= 1e-10, (spec, st)
     ep, eu = compare(c, got, ref)
-    assert ep <= 1e-9 and eu <= max(1e-9, 10 * floor), (SPECS[i], ep, eu, floor)
-    assert st["div_metric"] <= 1e-10, SPECS[i]
+    assert ep <= 1e-9 and eu <= max(1e-9, 10 * floor), (spec, ep, eu, floor)
+    assert st["div_metric"] <= 1e-10, spec
+
+
+@pytest.mark.parametrize("i", range(len(SPECS)))
+def test_fuzz_matches_oracle(cuda_ok, i):
+    check_against_oracle(SPECS[i])
+
+
+@pytest.mark.parametrize("i", range(len(PZ_SPECS)))
+def test_fuzz_periodic_z_matches_oracle(cuda_ok, i):
+    check_against_oracle(PZ_SPECS[i])
 
 
 @pytest.mark.parametrize("precision", [F.FP64, F.MIXED], ids=["fp64", "mixed"])
-@pytest.mark.parametrize("seed", [7, 8])
-def test_fuzz_batch_equals_alone(cuda_ok, precision, seed):
-    """Random mixes of eight of these instances in one persistent launch:
-    each equals the same instance solved alone, bit for bit."""
+@pytest.mark.parametrize("seed,bcz_mix", [(7, False), (8, False), (9, True)])
+def test_fuzz_batch_equals_alone(cuda_ok, precision, seed, bcz_mix):
+    """Random mixes of eight of these instances in one persistent launch
+    (the last mix with periodic z drawn per instance): each equals the same
+    instance solved alone, bit for bit."""
     import torch
-    specs = fuzz_specs(8, seed=seed)
+    specs = fuzz_specs(8, seed=seed, bcz_mix=bcz_mix)
     cases = [I.make_case(s) for s in specs]
     alone = [run_alone(c, precision) for c in cases]
     plans = [F.Plan.for_case(c, precision=precision) for c in cases]

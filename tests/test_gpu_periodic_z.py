@@ -15,7 +15,7 @@ import oracle as O
 import paper_2502_04189_b300 as F
 from paper_2502_04189_b300 import inputs as I
 
-from gpu_util import compare, gpu_project, relerr, to_dev
+from gpu_util import compare, gpu_project, relerr, run_alone, to_dev
 
 pytestmark = pytest.mark.gpu
 
@@ -121,14 +121,40 @@ def test_periodic_z_seam_rotation(cuda_ok):
     assert relerr(b["p"] - O.weighted_mean(g, b["p"]), pa - O.weighted_mean(g, pa)) < TOL64
 
 
-def test_periodic_z_is_refused_by_the_batch(cuda_ok):
-    c = I.make_case(CASES["t32_ppp"])
-    plan = F.Plan.for_case(c, precision=F.FP64)
-    arrays = tuple(to_dev(a) for a in (c.phi, c.pn, c.pnm1, c.u, c.v, c.w, c.phi))
-    with pytest.raises(F.FizzyError) as e:
-        F.Batch([plan], [arrays])
-    assert e.value.code == -2
-    plan.close()
+@pytest.mark.parametrize("precision", [F.FP64, F.MIXED])
+def test_periodic_z_in_the_batch(cuda_ok, precision):
+    """Periodic-z instances in one persistent batch launch, next to a
+    wall-bounded one: each equals the instance solved alone with the same
+    passes (bit for bit) and the oracle within the bar."""
+    specs = [CASES["t48x36x20_npp_stretch"], CASES["t27x18x13_pnp"], CASES["t16x12x2"],
+             I.CaseSpec(nx=36, ny=24, nz=20, bcx=1, beta=1.2, n_bubbles=2, radius_cells=3,
+                        config=70)]
+    cs = [I.make_case(sp) for sp in specs]
+    plans = [F.Plan.for_case(c, precision=precision) for c in cs]
+    arrays = [(to_dev(c.phi), to_dev(c.pn), to_dev(c.pnm1), to_dev(c.u), to_dev(c.v), to_dev(c.w),
+               torch_empty(c.shape)) for c in cs]
+    batch = F.Batch(plans, arrays)
+    batch.solve()
+    assert batch.status() == 0
+    bar = TOL64 if precision == F.FP64 else TOLMIX
+    for c, a, pl in zip(cs, arrays, plans):
+        got = dict(p=a[6].cpu().numpy(), u=a[3].cpu().numpy(), v=a[4].cpu().numpy(),
+                   w=a[5].cpu().numpy())
+        alone = run_alone(c, precision)
+        for k in ("p", "u", "v", "w"):
+            assert np.array_equal(got[k], alone[k]), k
+        ep, eu = compare(c, got, O.project_case(c))
+        assert ep <= bar and eu <= bar, (ep, eu)
+        if precision == F.MIXED:
+            assert pl.stats()["converged"] == 1
+    batch.close()
+    for pl in plans:
+        pl.close()
+
+
+def torch_empty(shape):
+    import torch
+    return torch.empty(shape, dtype=torch.float64, device="cuda")
 
 
 def test_emulsion_full_size_properties(cuda_ok):
