@@ -63,6 +63,9 @@ def lib():
             L.ora_poisson_dense.restype = I
             L.ora_project.argtypes = g + [D, D, D, d, d, d, d, d, d, d, d, d, I]
             L.ora_project.restype = I
+            L.ora_apply_vc.argtypes = g + [D, D, d, d, d]
+            L.ora_project_vc.argtypes = g + [D, D, D, d, d, d, d, d, d]
+            L.ora_project_vc.restype = I
             L.ora_fft.argtypes = [I, d, d, d, d, I]
             L.ora_dft.argtypes = [I, d, d, d, d, I]
             L.ora_weighted_mean.argtypes = [I, I, I, d, d]
@@ -175,6 +178,29 @@ def project_case(case, dense: bool = False):
     s = case.spec
     return project(Grid.of_case(case), s.rho_l, s.rho_g, s.dt, case.phi, case.pn, case.pnm1,
                    case.u, case.v, case.w, dense=dense)
+
+
+def apply_vc(g: Grid, rho_l, rho_g, phi, p):
+    """D(beta_f G p), beta_f = 1/rho_f (the unsplit variable-coefficient operator)."""
+    phi, p = _c(phi), _c(p)
+    out = np.empty(g.shape)
+    lib().ora_apply_vc(*g.args(), rho_l, rho_g, _p(phi), _p(p), _p(out))
+    return out
+
+
+def project_vc(g: Grid, rho_l, rho_g, dt, phi, u, v, w):
+    """Variable-coefficient projection without splitting, dense (<= 4096 cells):
+    D(beta_f G p) = D(u*)/dt, u = u* - dt beta_f G p.
+    Returns dict(p, u, v, w, relres, divmax)."""
+    phi = _c(phi)
+    uo, vo, wo = (np.array(a, dtype=np.float64, copy=True, order="C") for a in (u, v, w))
+    p = np.empty(g.shape)
+    diag = np.zeros(2)
+    st = lib().ora_project_vc(*g.args(), rho_l, rho_g, dt, _p(phi), _p(uo), _p(vo), _p(wo), _p(p),
+                              _p(diag))
+    if st != 0:
+        raise RuntimeError("oracle variable-coefficient projection failed with status %d" % st)
+    return dict(p=p, u=uo, v=vo, w=wo, relres=diag[0], divmax=diag[1])
 
 
 def fft(x, sign=-1):

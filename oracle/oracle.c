@@ -710,6 +710,117 @@ int ora_project(int nx, int ny, int nz, double dx, double dy, const double *zf, 
     return st;
 }
 
+/* ------------------------------------------------------------------ */
+/* Variable-coefficient projection (no splitting)                       */
+/* ------------------------------------------------------------------ */
+/* The pressure equation before the constant-coefficient splitting (the
+ * paper's "Methods and Implementation strategy": the variable-coefficient
+ * Poisson equation that the splitting replaces; the Hypre path of the code
+ * solves it directly):
+ *     D(beta_f G p) = D(u*)/dt,   u = u* - dt beta_f G p,
+ * with beta_f = 1/rho_f as in face_beta (wall faces 0).  p has zero
+ * dzf-weighted mean. */
+
+/* out = D(beta_f G p) */
+void ora_apply_vc(int nx, int ny, int nz, double dx, double dy, const double *zf, int bcx, int bcy,
+                  int bcz, double rho_l, double rho_g, const double *phi, const double *p,
+                  double *out) {
+    grid_t g = mkgrid(nx, ny, nz, dx, dy, zf, bcx, bcy, bcz);
+    size_t n = (size_t)nx * ny * nz;
+    double *gx = malloc(n * sizeof(double)), *gy = malloc(n * sizeof(double)),
+           *gz = malloc(n * sizeof(double));
+    double *bx = malloc(n * sizeof(double)), *by = malloc(n * sizeof(double)),
+           *bz = malloc(n * sizeof(double));
+    grad(&g, p, gx, gy, gz);
+    face_beta(&g, rho_l, rho_g, phi, bx, by, bz);
+    for (size_t c = 0; c < n; ++c) {
+        gx[c] *= bx[c];
+        gy[c] *= by[c];
+        gz[c] *= bz[c];
+    }
+    divergence(&g, gx, gy, gz, out);
+    free(gx);
+    free(gy);
+    free(gz);
+    free(bx);
+    free(by);
+    free(bz);
+}
+
+/* Whole variable-coefficient projection on a small grid (n <= 4096 cells):
+ * the operator is assembled column by column from ora_apply_vc, its last row
+ * replaced by the gauge row (weights dzf_k), and solved by dense Gaussian
+ * elimination with partial pivoting.  u, v, w hold u* on entry and u on
+ * exit.  diag (optional, 2 doubles): [max|b - A p| / max|b|, max|D u|].
+ * Returns 0, -2 if the grid is too large, -1 on a zero pivot. */
+int ora_project_vc(int nx, int ny, int nz, double dx, double dy, const double *zf, int bcx,
+                   int bcy, int bcz, double rho_l, double rho_g, double dt, const double *phi,
+                   double *u, double *v, double *w, double *p, double *diag) {
+    grid_t g = mkgrid(nx, ny, nz, dx, dy, zf, bcx, bcy, bcz);
+    size_t n = (size_t)nx * ny * nz;
+    if (n > 4096) return -2;
+    double *A = calloc(n * n, sizeof(double));
+    double *e = calloc(n, sizeof(double)), *col = malloc(n * sizeof(double));
+    double *rhs = malloc(n * sizeof(double));
+    cplx *b = malloc(n * sizeof(cplx));
+    for (size_t c = 0; c < n; ++c) {
+        e[c] = 1.0;
+        ora_apply_vc(nx, ny, nz, dx, dy, zf, bcx, bcy, bcz, rho_l, rho_g, phi, e, col);
+        for (size_t r = 0; r < n; ++r) A[r * n + c] = col[r];
+        e[c] = 0.0;
+    }
+    divergence(&g, u, v, w, rhs);
+    for (size_t c = 0; c < n; ++c) rhs[c] /= dt;
+    remove_weighted_mean(&g, rhs);
+    for (size_t r = 0; r < n; ++r) b[r] = rhs[r];
+    for (int k = 0; k < nz; ++k)
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i < nx; ++i) A[(n - 1) * n + IDX(&g, i, j, k)] = dzf(&g, k);
+    b[n - 1] = 0.0;
+    int st = dense_gepp((int)n, A, b);
+    for (size_t r = 0; r < n; ++r) p[r] = creal(b[r]);
+    remove_weighted_mean(&g, p);
+    /* u = u* - dt beta_f G p on non-wall faces */
+    double *gx = malloc(n * sizeof(double)), *gy = malloc(n * sizeof(double)),
+           *gz = malloc(n * sizeof(double));
+    double *bx = malloc(n * sizeof(double)), *by = malloc(n * sizeof(double)),
+           *bz = malloc(n * sizeof(double));
+    grad(&g, p, gx, gy, gz);
+    face_beta(&g, rho_l, rho_g, phi, bx, by, bz);
+    for (int k = 0; k < nz; ++k)
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i < nx; ++i) {
+                size_t c = IDX(&g, i, j, k);
+                if (!(bcx == 1 && i == nx - 1)) u[c] -= dt * bx[c] * gx[c];
+                if (!(bcy == 1 && j == ny - 1)) v[c] -= dt * by[c] * gy[c];
+                if (!(bcz == 1 && k == nz - 1)) w[c] -= dt * bz[c] * gz[c];
+            }
+    if (diag) {
+        ora_apply_vc(nx, ny, nz, dx, dy, zf, bcx, bcy, bcz, rho_l, rho_g, phi, p, col);
+        double rm = 0.0, bm = 0.0;
+        for (size_t c = 0; c < n; ++c) {
+            double d = fabs(rhs[c] - col[c]);
+            if (d > rm) rm = d;
+            if (fabs(rhs[c]) > bm) bm = fabs(rhs[c]);
+        }
+        diag[0] = bm > 0 ? rm / bm : rm;
+        divergence(&g, u, v, w, col);
+        diag[1] = maxabs(col, n);
+    }
+    free(A);
+    free(e);
+    free(col);
+    free(rhs);
+    free(b);
+    free(gx);
+    free(gy);
+    free(gz);
+    free(bx);
+    free(by);
+    free(bz);
+    return st;
+}
+
 int ora_num_threads(void) {
 #ifdef _OPENMP
     extern int omp_get_max_threads(void);

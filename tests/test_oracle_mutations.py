@@ -18,7 +18,7 @@ SRC = os.path.join(ROOT, "oracle", "oracle.c")
 
 PINS = ("exact_rational or eigenmodes or apply_then_solve or divergence_free or "
         "constant_density or dense_solves or stretched_z or correction_identity or "
-        "triperiodic or rotation_commutes")
+        "triperiodic or rotation_commutes or vc_")
 
 MUTATIONS = [
     ("grad_sign", "gx[c] = (q[IDX(g, i + 1, j, k)] - q[c]) / g->dx;",
@@ -62,6 +62,13 @@ MUTATIONS = [
      "if (k < nz - 1)\n                    w[c]"),
     ("z_solve_seam_coupling", "(per ? 1.0 / (dzf(&g, 0) * dzc(&g, nz - 1)) : 0.0)",
      "(per ? 1.0 / (dzf(&g, nz - 1) * dzc(&g, nz - 1)) : 0.0)"),
+    # variable-coefficient projection
+    ("vc_beta_dropped_x", "        gx[c] *= bx[c];\n        gy[c] *= by[c];",
+     "        gx[c] *= 1.0;\n        gy[c] *= by[c];"),
+    ("vc_correct_sign", "if (!(bcx == 1 && i == nx - 1)) u[c] -= dt * bx[c] * gx[c];",
+     "if (!(bcx == 1 && i == nx - 1)) u[c] += dt * bx[c] * gx[c];"),
+    ("vc_rhs_dt", "for (size_t c = 0; c < n; ++c) rhs[c] /= dt;",
+     "for (size_t c = 0; c < n; ++c) rhs[c] *= dt;"),
     ("z_matrix_wrap_column", "A[(size_t)k * nz + (k + nz - 1) % nz] += lo[k];",
      "A[(size_t)k * nz + (k + nz - 2) % nz] += lo[k];"),
     ("neumann_extension", "return (bc == 0 || e < n) ? e : 2 * n - 1 - e;",
