@@ -135,6 +135,27 @@ int fizzy_proj_solve(fizzy_proj_plan_t p, const double *phi, const double *p_n, 
                      double *u, double *v, double *w, double *p_np1, fizzy_proj_stats *st,
                      void *stream);
 
+/* Variable-coefficient projection WITHOUT the constant-coefficient splitting
+ * (the equation the splitting replaces; the paper's Hypre path solves it):
+ *     D(beta_f G p) = D(u*)/dt,   u = u* - dt beta_f G p,   beta_f = 1/rho_f,
+ * with the same grid, staggering, face densities and boundaries as
+ * fizzy_proj_solve.  Solved by conjugate gradients preconditioned with the
+ * plan's constant-coefficient FFT/tridiagonal solve; stops when
+ * max|D(u*)/dt - D(beta_f G p)| / max|D(u*)/dt| <= tol (0 -> 1e-10) or after
+ * max_iter iterations (1 .. 100000).
+ *   phi        : in, cell centred (densities and dt from the plan).
+ *   u, v, w    : in u* (wall faces 0), out u.
+ *   p_np1      : out p with zero dzf-weighted mean (the full pressure; no p^n
+ *                enters); must not alias the inputs.
+ *   st         : NULL or host stats (iterations = CG iterations, relres,
+ *                f_max = max|D(u*)/dt|, div_max, u_rms, div_metric).
+ * Needs an FP64 plan (else FIZZY_ERR_UNSUPPORTED).  Allocates 7 fields of
+ * workspace on first use (kept with the plan).  Synchronises the stream
+ * every 4 iterations to test convergence (not graph-capturable).  Returns
+ * FIZZY_ERR_NOT_CONVERGED (outputs written) if tol was not reached. */
+int fizzy_proj_solve_vc(fizzy_proj_plan_t p, const double *phi, double *u, double *v, double *w,
+                        double *p_np1, int max_iter, double tol, fizzy_proj_stats *st, void *stream);
+
 /* Rebind the densities and time step of a plan (the grid, its transforms and
  * z-factorisation tables do not depend on them).  Updates four per-plane
  * tables by an asynchronous copy on stream; solves issued after it on the

@@ -139,6 +139,20 @@ class Plan:
         """Block until every queued host solve's results are in host memory."""
         self._check(_abi.lib().fizzy_proj_host_wait(self._h))
 
+    def solve_vc(self, phi, u, v, w, p_out, max_iter=500, tol=0.0, stream=None):
+        """Variable-coefficient projection WITHOUT the splitting
+        (fizzy_proj_solve_vc): D(beta_f G p) = D(u*)/dt by conjugate gradients
+        preconditioned with this plan's constant-coefficient solve; u, v, w
+        are overwritten with u.  Needs an FP64 plan.  Returns the stats dict
+        (iterations = CG iterations); raises unless converged."""
+        st = Stats()
+        rc = _abi.lib().fizzy_proj_solve_vc(self._h, _ptr(phi), _ptr(u), _ptr(v), _ptr(w), _ptr(p_out),
+                                            int(max_iter), float(tol), ctypes.byref(st),
+                                            _stream_handle(stream))
+        if rc != 0:
+            raise FizzyError(rc, _abi.lib().fizzy_proj_last_error(self._h).decode())
+        return st.as_dict()
+
     def stats(self, stream=None):
         st = Stats()
         self._check(_abi.lib().fizzy_proj_get_stats(self._h, ctypes.byref(st), _stream_handle(stream)))

@@ -5,6 +5,7 @@
 #include "fizzy_proj.h"
 #include "kern_passes.cuh"
 #include "kern_r16.cuh"
+#include "kern_vc.cuh"
 
 #include <algorithm>
 #include <cmath>
@@ -40,6 +41,7 @@ typedef void (*Xinv64K)(GridDev, FFTDesc, int, const double *, double *, const D
 typedef void (*Xinv32K)(GridDev, FFTDesc, int, const float *, double *, const DevStats *, int);
 struct PassKernels {
     XfwdK xf64, xf32d, xf32l;
+    XfwdK xl64;  // FP64 transform of a stored right-hand side (the preconditioner of fizzy_proj_solve_vc)
     Ypass64K yf64, yi64;
     Ypass32K yf32, yi32;
     Xinv64K xi64;
@@ -65,6 +67,11 @@ struct fizzy_proj_plan_s {
     // periodic z: Sherman-Morrison weights and correction vector (k_ztables_cyc)
     double *wtab64 = nullptr, *qtab64 = nullptr;
     float *wtab32 = nullptr, *qtab32 = nullptr;
+    // variable-coefficient solve (fizzy_proj_solve_vc), allocated on first use:
+    // face beta x, y, z, r, z, d, A d; partial sums; iteration state
+    double *vc[7] = {};
+    double *vc_part = nullptr;
+    VcState *vc_state = nullptr;
     double *qx = nullptr, *qy = nullptr, *qz = nullptr;
     double *fhat64 = nullptr;
     float *fhat32 = nullptr;
@@ -403,6 +410,7 @@ template <int NX, int NY> PassKernels kernels_for() {
     k.xf64 = k_xfwd<double, XF_F64_DIVQ, NX>;
     k.xf32d = k_xfwd<float, XF_MIX_DIVQ, NX>;
     k.xf32l = k_xfwd<float, XF_MIX_LOAD, NX>;
+    k.xl64 = k_xfwd<double, XF_MIX_LOAD, NX>;
     k.yf64 = k_ypass<double, false, NY>;
     k.yi64 = k_ypass<double, true, NY>;
     k.yf32 = k_ypass<float, false, NY>;
@@ -454,6 +462,7 @@ void opt_in_smem(fizzy_proj_plan_t p, int bytes) {
         for (int fy : {0, 256, 512}) {
             const PassKernels k = pick_kernels(fx, fy);
             const void *fns[] = {(const void *)k.xf64, (const void *)k.xf32d, (const void *)k.xf32l,
+                                 (const void *)k.xl64,
                                  (const void *)k.yf64, (const void *)k.yi64, (const void *)k.yf32,
                                  (const void *)k.yi32, (const void *)k.xi64, (const void *)k.xi32s,
                                  (const void *)k.xi32a};
@@ -1097,6 +1106,11 @@ int fizzy_proj_solve_host(fizzy_proj_plan_t p, const double *phi, const double *
 // Batched projections (fizzy_proj_batch_*)
 // ===========================================================================
 #include "fizzy_batch.inc"
+
+// ===========================================================================
+// Variable-coefficient projection without splitting (fizzy_proj_solve_vc)
+// ===========================================================================
+#include "fizzy_vc.inc"
 
 // ===========================================================================
 // Serving runtime (fizzy_serve_*)

@@ -348,7 +348,9 @@ __device__ __forceinline__ double lap(const GridDev &g, int i, int j, int k, con
 enum {
     XF_F64_DIVQ = 0,   // FP64 mode: sigma rho0 D(q), FP64 transform
     XF_MIX_DIVQ = 1,   // mixed: f = rho0 D(q) stored (FP64), FP32 transform of sigma f
-    XF_MIX_LOAD = 2    // mixed: FP32 transform, in place, of a stored sigma 2^-e r
+    XF_MIX_LOAD = 2    // transform, in place, of a stored right-hand side: mixed mode's FP32
+                       // sigma 2^-e r; with T = double the preconditioner of the
+                       // variable-coefficient solve (sigma r)
 };
 
 struct XArgs {

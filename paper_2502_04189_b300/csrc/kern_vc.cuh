@@ -1,0 +1,252 @@
+// Variable-coefficient projection without splitting (sm_103a):
+//     D(beta_f G p) = D(u*)/dt,   u = u* - dt beta_f G p,
+// beta_f = 1/rho_f (face mean of rho = rho_g + phi (rho_l - rho_g)).  This is
+// the pressure equation that the constant-coefficient splitting replaces (the
+// paper's Hypre path solves it directly).  Here it is solved by conjugate
+// gradients preconditioned with the constant-coefficient FFT/tridiagonal
+// solve L^-1 of the projection's own passes: A = D beta G and L = D G are
+// both symmetric in the cell-volume (dzf-weighted) inner product and
+// negative semi-definite with the constants as null space, so CG on
+// (-A) x = -b with the preconditioner (-L)^-1 runs with the same formulas as
+// on A x = b:
+//     r = b - A x,  z = L^-1 r,  rho = <r, z>,  d = z + (rho / rho_old) d,
+//     alpha = rho / <d, A d>,  x += alpha d,  r -= alpha A d,
+// stopped when max|r| / max|b| <= tol.  Every dot product is a fixed-order
+// reduction (grid-stride partial per block, then one block), so a solve is
+// bitwise repeatable.  The iteration's scalars live in device memory
+// (VcState); the kernels of an iteration return at once after convergence.
+#pragma once
+#include "kern_passes.cuh"
+
+namespace fz {
+
+struct VcState {
+    double rho;       // <r, z> of the current residual
+    double alpha, beta;
+    double usq;       // sum of u*^2 over all face values
+    unsigned long long bmax_bits;  // max|b|
+    unsigned long long rmax_bits;  // max|r| of the current iteration
+    unsigned int done;             // last-block ticket of the update kernel
+    int iters;                     // CG iterations run
+};
+
+constexpr int VC_THREADS = 256;
+constexpr int VC_MAX_BLOCKS = 2048;  // partial-sum slots
+
+// rho at a cell centre
+__device__ __forceinline__ double vc_rho(double rho_l, double rho_g, double phi) {
+    return fmaT(phi, rho_l - rho_g, rho_g);
+}
+
+// Face beta_f = 1/rho_f on the +x, +y, +z faces of every cell (0 on walls),
+// b = D(u*)/dt, r = b, x = d = 0, the preconditioner's input sigma r in the
+// spectral workspace, max|b| and the partial sums of u*^2.
+__global__ void __launch_bounds__(VC_THREADS) k_vc_init(GridDev g, double rho_l, double rho_g, double dt,
+                                                       const double *__restrict__ phi,
+                                                       const double *__restrict__ u,
+                                                       const double *__restrict__ v,
+                                                       const double *__restrict__ w,
+                                                       double *__restrict__ bx, double *__restrict__ by,
+                                                       double *__restrict__ bz, double *__restrict__ r,
+                                                       double *__restrict__ x, double *__restrict__ d,
+                                                       double *__restrict__ spec,
+                                                       double *__restrict__ part, VcState *vs) {
+    const size_t n = (size_t)g.nx * g.ny * g.nz, pl = (size_t)g.nx * g.ny;
+    const double idt = 1.0 / dt, cx = g.idx1 * idt, cy = g.idy1 * idt;
+    unsigned long long mx = 0ull;
+    double usq = 0.0;
+    for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (size_t)gridDim.x * blockDim.x) {
+        const int k = (int)(c / pl);
+        const size_t rem = c - (size_t)k * pl;
+        const int j = (int)(rem / g.nx), i = (int)(rem - (size_t)j * g.nx);
+        const double rc = vc_rho(rho_l, rho_g, phi[c]);
+        double b = 0.0;
+        if (!(g.bcx == BC_NEUMANN && i == g.nx - 1))
+            b = 2.0 / (rc + vc_rho(rho_l, rho_g, phi[i < g.nx - 1 ? c + 1 : c - i]));
+        bx[c] = b;
+        b = 0.0;
+        if (!(g.bcy == BC_NEUMANN && j == g.ny - 1))
+            b = 2.0 / (rc + vc_rho(rho_l, rho_g, phi[j < g.ny - 1 ? c + g.nx : c - (size_t)j * g.nx]));
+        by[c] = b;
+        b = 0.0;
+        if (k < g.nz - 1 || g.perz)
+            b = 2.0 / (rc + vc_rho(rho_l, rho_g, phi[k < g.nz - 1 ? c + pl : c - (size_t)k * pl]));
+        bz[c] = b;
+        const double f = div_q<false>(g, i, j, k, cx, cy, mulT(g.izf[k], idt), u, v, w);
+        r[c] = f;
+        x[c] = 0.0;
+        d[c] = 0.0;
+        spec[c] = mulT(f, g.sigma);
+        mx = umax64(mx, absbits(f));
+        usq = fmaT(u[c], u[c], fmaT(v[c], v[c], fmaT(w[c], w[c], usq)));
+    }
+    block_max_atomic(mx, &vs->bmax_bits);
+    const double s = block_sum(usq);
+    if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+// u*^2 total (one block, fixed order); resets the iteration state.
+__global__ void __launch_bounds__(1024) k_vc_init_sum(const double *__restrict__ part, int nparts,
+                                                      VcState *vs) {
+    double s = 0.0;
+    for (int t = threadIdx.x; t < nparts; t += blockDim.x) s += part[t];
+    s = block_sum(s);
+    if (threadIdx.x == 0) {
+        vs->usq = s;
+        vs->rho = 0.0;
+        vs->iters = 0;
+    }
+}
+
+// Partial sums of <a, b> = sum dzf_k a b (one per block).
+__global__ void __launch_bounds__(VC_THREADS) k_vc_dot(GridDev g, const double *__restrict__ a,
+                                                      const double *__restrict__ b,
+                                                      double *__restrict__ part, const DevStats *st) {
+    if (*(volatile const int *)&st->converged) return;
+    const size_t n = (size_t)g.nx * g.ny * g.nz, pl = (size_t)g.nx * g.ny;
+    double s = 0.0;
+    for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (size_t)gridDim.x * blockDim.x)
+        s = fmaT(mulT(g.dzf[c / pl], a[c]), b[c], s);
+    s = block_sum(s);
+    if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+// rho = <r, z>; beta = rho / rho_old (0 on the first iteration).
+__global__ void __launch_bounds__(1024) k_vc_beta(const double *__restrict__ part, int nparts, VcState *vs,
+                                                  const DevStats *st) {
+    if (*(volatile const int *)&st->converged) return;
+    double s = 0.0;
+    for (int t = threadIdx.x; t < nparts; t += blockDim.x) s += part[t];
+    s = block_sum(s);
+    if (threadIdx.x == 0) {
+        vs->beta = vs->iters == 0 ? 0.0 : s / vs->rho;
+        vs->rho = s;
+    }
+}
+
+// d = z + beta d
+__global__ void __launch_bounds__(VC_THREADS) k_vc_dir(GridDev g, const double *__restrict__ z,
+                                                      double *__restrict__ d, const VcState *vs,
+                                                      const DevStats *st) {
+    if (*(volatile const int *)&st->converged) return;
+    const size_t n = (size_t)g.nx * g.ny * g.nz;
+    const double beta = vs->beta;
+    for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (size_t)gridDim.x * blockDim.x)
+        d[c] = fmaT(beta, d[c], z[c]);
+}
+
+// q = A d = D(beta_f G d) in flux form (each face flux beta (d_nbr - d_c)/h
+// formed once per face and cell side), partial sums of <d, q>.
+__global__ void __launch_bounds__(VC_THREADS) k_vc_apply(GridDev g, const double *__restrict__ d,
+                                                        const double *__restrict__ bx,
+                                                        const double *__restrict__ by,
+                                                        const double *__restrict__ bz,
+                                                        double *__restrict__ q, double *__restrict__ part,
+                                                        const DevStats *st) {
+    if (*(volatile const int *)&st->converged) return;
+    const size_t n = (size_t)g.nx * g.ny * g.nz, pl = (size_t)g.nx * g.ny;
+    double s = 0.0;
+    for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (size_t)gridDim.x * blockDim.x) {
+        const int k = (int)(c / pl);
+        const size_t rem = c - (size_t)k * pl;
+        const int j = (int)(rem / g.nx), i = (int)(rem - (size_t)j * g.nx);
+        const double dc = d[c];
+        // east / west faces (beta 0 on walls)
+        const size_t e = i < g.nx - 1 ? c + 1 : c - i;
+        const size_t wst = i > 0 ? c - 1 : c + g.nx - 1;
+        const double bw = (i > 0 || g.bcx == BC_PERIODIC) ? bx[wst] : 0.0;
+        double acc = mulT(fmaT(bx[c], d[e] - dc, -mulT(bw, dc - d[wst])), g.idx2);
+        const size_t nn = j < g.ny - 1 ? c + g.nx : c - (size_t)j * g.nx;
+        const size_t ss = j > 0 ? c - g.nx : c + (size_t)(g.ny - 1) * g.nx;
+        const double bs = (j > 0 || g.bcy == BC_PERIODIC) ? by[ss] : 0.0;
+        acc = fmaT(fmaT(by[c], d[nn] - dc, -mulT(bs, dc - d[ss])), g.idy2, acc);
+        const size_t t = k < g.nz - 1 ? c + pl : c - (size_t)k * pl;
+        const size_t b = k > 0 ? c - pl : c + (size_t)(g.nz - 1) * pl;
+        const double bt = bz[c];  // 0 on the top wall
+        const double bb = (k > 0 || g.perz) ? bz[b] : 0.0;
+        acc = fmaT(mulT(bt, g.lzc[k]), d[t] - dc, acc);
+        acc = fmaT(-mulT(bb, g.lza[k]), dc - d[b], acc);
+        q[c] = acc;
+        s = fmaT(mulT(g.dzf[k], dc), acc, s);
+    }
+    s = block_sum(s);
+    if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+// alpha = rho / <d, A d>; resets the update kernel's max and ticket.
+__global__ void __launch_bounds__(1024) k_vc_alpha(const double *__restrict__ part, int nparts, VcState *vs,
+                                                   const DevStats *st) {
+    if (*(volatile const int *)&st->converged) return;
+    double s = 0.0;
+    for (int t = threadIdx.x; t < nparts; t += blockDim.x) s += part[t];
+    s = block_sum(s);
+    if (threadIdx.x == 0) {
+        vs->alpha = vs->rho / s;
+        vs->rmax_bits = 0ull;
+        vs->done = 0u;
+    }
+}
+
+// x += alpha d, r -= alpha q, sigma r into the spectral workspace, max|r|;
+// the last block decides convergence.
+__global__ void __launch_bounds__(VC_THREADS) k_vc_update(GridDev g, double *__restrict__ x,
+                                                         double *__restrict__ r,
+                                                         const double *__restrict__ d,
+                                                         const double *__restrict__ q,
+                                                         double *__restrict__ spec, VcState *vs,
+                                                         DevStats *st, double tol) {
+    if (*(volatile const int *)&st->converged) return;
+    const size_t n = (size_t)g.nx * g.ny * g.nz;
+    const double alpha = vs->alpha;
+    unsigned long long mx = 0ull;
+    for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (size_t)gridDim.x * blockDim.x) {
+        x[c] = fmaT(alpha, d[c], x[c]);
+        const double rv = fmaT(-alpha, q[c], r[c]);
+        r[c] = rv;
+        spec[c] = mulT(rv, g.sigma);
+        mx = umax64(mx, absbits(rv));
+    }
+    block_max_atomic(mx, &vs->rmax_bits);
+    __shared__ int last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last = atomicAdd(&vs->done, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (last && threadIdx.x == 0) {
+        __threadfence();
+        const double rm = __longlong_as_double((long long)atomicMax(&vs->rmax_bits, 0ull));
+        const double bm = __longlong_as_double((long long)vs->bmax_bits);
+        const double rel = bm > 0.0 ? rm / bm : rm;
+        vs->iters += 1;
+        st->iterations = vs->iters;
+        st->relres = rel;
+        if (rel <= tol) st->converged = 1;
+    }
+}
+
+// u = u* - dt beta_f G x on every non-wall face (in place).
+__global__ void __launch_bounds__(VC_THREADS) k_vc_correct(GridDev g, double dt, const double *__restrict__ x,
+                                                          const double *__restrict__ bx,
+                                                          const double *__restrict__ by,
+                                                          const double *__restrict__ bz,
+                                                          double *__restrict__ u, double *__restrict__ v,
+                                                          double *__restrict__ w) {
+    const size_t n = (size_t)g.nx * g.ny * g.nz, pl = (size_t)g.nx * g.ny;
+    for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (size_t)gridDim.x * blockDim.x) {
+        const int k = (int)(c / pl);
+        const size_t rem = c - (size_t)k * pl;
+        const int j = (int)(rem / g.nx), i = (int)(rem - (size_t)j * g.nx);
+        const double xc = x[c];
+        if (!(g.bcx == BC_NEUMANN && i == g.nx - 1))
+            u[c] = fmaT(-mulT(mulT(dt, bx[c]), g.idx1), x[i < g.nx - 1 ? c + 1 : c - i] - xc, u[c]);
+        if (!(g.bcy == BC_NEUMANN && j == g.ny - 1))
+            v[c] = fmaT(-mulT(mulT(dt, by[c]), g.idy1), x[j < g.ny - 1 ? c + g.nx : c - (size_t)j * g.nx] - xc,
+                        v[c]);
+        if (k < g.nz - 1 || g.perz)
+            w[c] = fmaT(-mulT(dt, bz[c]) / g.dzc[k], x[k < g.nz - 1 ? c + pl : c - (size_t)k * pl] - xc, w[c]);
+    }
+}
+
+}  // namespace fz

@@ -546,3 +546,22 @@ def test_vc_layered_closed_form():
     p = np.concatenate([[0.0], np.cumsum(dp)])
     p -= np.sum(np.diff(zf) * p) / np.sum(np.diff(zf))
     assert relerr(r["p"][:, 1, 2], p) < 1e-12
+
+
+@pytest.mark.parametrize("bcz", [1, 0])
+def test_vc_is_the_split_fixed_point(bcz):
+    """The split projection with phat = p equals the unsplit one: if p solves
+    D(beta_f G p) = D(u*)/dt, then with p^n = p^(n-1) = p (so phat = p) the
+    split right-hand side (rho0/dt) D u* + D[(1 - rho0 beta_f) G p] equals
+    D G p (multiply the unsplit equation by rho0 and add D G p to both sides),
+    so the split solve returns p and the same u.  This ties the two oracle
+    paths to each other at density ratio 1000."""
+    spec = I.CaseSpec(nx=12, ny=10, nz=9, bcx=1, beta=1.4, n_bubbles=2, radius_cells=2.0,
+                      rho_l=1.0, rho_g=1e-3, dt=1e-3, config=83, bcz=bcz)
+    c = I.make_case(spec)
+    g = O.Grid.of_case(c)
+    r = O.project_vc(g, spec.rho_l, spec.rho_g, spec.dt, c.phi, c.u, c.v, c.w)
+    s = O.project(g, spec.rho_l, spec.rho_g, spec.dt, c.phi, r["p"], r["p"], c.u, c.v, c.w)
+    assert relerr(s["p"], r["p"]) < 1e-10
+    for k in "uvw":
+        assert relerr(s[k], r[k]) < 1e-10, k
