@@ -625,7 +625,8 @@ def run_vc(args):
         return torch.from_numpy(np.ascontiguousarray(a)).cuda()
 
     phi = dev(case.phi)
-    plan = F.Plan.for_case(case, precision=F.FP64)
+    prec = F.MIXED if args.precision == "mixed" else F.FP64  # mixed: FP32 preconditioner
+    plan = F.Plan.for_case(case, precision=prec)
     p = torch.empty_like(phi)
     stream = torch.cuda.current_stream()
     times, st = [], None
@@ -658,10 +659,11 @@ def run_vc(args):
     if rank == 0:
         line = {"metric": METRIC, "value": npts / (ms / 1e3), "unit": "pts/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
-                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-                "data": "synthetic",
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32+f64" if prec == F.MIXED else "f64", "data": "synthetic",
                 "config": {"workload": args.workload, "grid": [spec.nx, spec.ny, spec.nz],
                            "form": "variable-coefficient projection, preconditioned CG",
+                           "preconditioner": "FP32 solve, flexible CG" if prec == F.MIXED else "FP64 solve",
                            "tol": args.vc_tol, "density_ratio": max(spec.rho_l, spec.rho_g) / min(spec.rho_l, spec.rho_g)},
                 "stats": {k: st[k] for k in ("iterations", "converged", "relres", "div_metric")},
                 "ms_per_iteration": ms / max(1, st["iterations"]),

@@ -149,8 +149,11 @@ int fizzy_proj_solve(fizzy_proj_plan_t p, const double *phi, const double *p_n, 
  *                enters); must not alias the inputs.
  *   st         : NULL or host stats (iterations = CG iterations, relres,
  *                f_max = max|D(u*)/dt|, div_max, u_rms, div_metric).
- * Needs an FP64 plan (else FIZZY_ERR_UNSUPPORTED).  Allocates 7 fields of
- * workspace on first use (kept with the plan).  Synchronises the stream
+ * On an FP64 plan the preconditioner is the FP64 solve; on a mixed plan it is
+ * the FP32 solve (applied to r 2^-e, e the exponent of max|b|) with the
+ * flexible (Polak-Ribiere) direction update; residuals, the operator and p
+ * are FP64 in both.  Allocates 7 fields of workspace on first use (kept
+ * with the plan); a mixed plan also uses its FP64 right-hand-side buffer.  Synchronises the stream
  * every 4 iterations to test convergence (not graph-capturable).  Returns
  * FIZZY_ERR_NOT_CONVERGED (outputs written) if tol was not reached. */
 int fizzy_proj_solve_vc(fizzy_proj_plan_t p, const double *phi, double *u, double *v, double *w,

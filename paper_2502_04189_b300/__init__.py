@@ -143,8 +143,9 @@ class Plan:
         """Variable-coefficient projection WITHOUT the splitting
         (fizzy_proj_solve_vc): D(beta_f G p) = D(u*)/dt by conjugate gradients
         preconditioned with this plan's constant-coefficient solve; u, v, w
-        are overwritten with u.  Needs an FP64 plan.  Returns the stats dict
-        (iterations = CG iterations); raises unless converged."""
+        are overwritten with u.  A mixed plan preconditions with its FP32
+        solve (flexible CG); an FP64 plan with its FP64 solve.  Returns the
+        stats dict (iterations = CG iterations); raises unless converged."""
         st = Stats()
         rc = _abi.lib().fizzy_proj_solve_vc(self._h, _ptr(phi), _ptr(u), _ptr(v), _ptr(w), _ptr(p_out),
                                             int(max_iter), float(tol), ctypes.byref(st),

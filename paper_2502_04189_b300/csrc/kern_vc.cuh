@@ -11,7 +11,13 @@
 // on A x = b:
 //     r = b - A x,  z = L^-1 r,  rho = <r, z>,  d = z + (rho / rho_old) d,
 //     alpha = rho / <d, A d>,  x += alpha d,  r -= alpha A d,
-// stopped when max|r| / max|b| <= tol.  Every dot product is a fixed-order
+// stopped when max|r| / max|b| <= tol.  On a mixed plan the preconditioner
+// is the FP32 solve (the register-resident passes where the lengths allow),
+// applied to r 2^-e (e the exponent of max|b|, a fixed scale), and the
+// direction update is the flexible (Polak-Ribiere) form
+// beta = (<z, r> - <z, r_prev>) / rho_old, which tolerates the FP32 rounding
+// of the preconditioner; residuals, the operator and x stay FP64.
+// Every dot product is a fixed-order
 // reduction (grid-stride partial per block, then one block), so a solve is
 // bitwise repeatable.  The iteration's scalars live in device memory
 // (VcState); the kernels of an iteration return at once after convergence.
@@ -24,6 +30,7 @@ struct VcState {
     double rho;       // <r, z> of the current residual
     double alpha, beta;
     double usq;       // sum of u*^2 over all face values
+    double rz_prev;   // flexible form: <z, r_prev>
     unsigned long long bmax_bits;  // max|b|
     unsigned long long rmax_bits;  // max|r| of the current iteration
     unsigned int done;             // last-block ticket of the update kernel
@@ -76,7 +83,7 @@ __global__ void __launch_bounds__(VC_THREADS) k_vc_init(GridDev g, double rho_l,
         r[c] = f;
         x[c] = 0.0;
         d[c] = 0.0;
-        spec[c] = mulT(f, g.sigma);
+        if (spec) spec[c] = mulT(f, g.sigma);
         mx = umax64(mx, absbits(f));
         usq = fmaT(u[c], u[c], fmaT(v[c], v[c], fmaT(w[c], w[c], usq)));
     }
@@ -98,30 +105,59 @@ __global__ void __launch_bounds__(1024) k_vc_init_sum(const double *__restrict__
     }
 }
 
-// Partial sums of <a, b> = sum dzf_k a b (one per block).
+// Partial sums of <a, b> = sum dzf_k a b (one per block); FLEX also
+// <a, b2> into part2.
+template <bool FLEX>
 __global__ void __launch_bounds__(VC_THREADS) k_vc_dot(GridDev g, const double *__restrict__ a,
                                                       const double *__restrict__ b,
-                                                      double *__restrict__ part, const DevStats *st) {
+                                                      const double *__restrict__ b2,
+                                                      double *__restrict__ part, double *__restrict__ part2,
+                                                      const DevStats *st) {
     if (*(volatile const int *)&st->converged) return;
     const size_t n = (size_t)g.nx * g.ny * g.nz, pl = (size_t)g.nx * g.ny;
-    double s = 0.0;
-    for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (size_t)gridDim.x * blockDim.x)
-        s = fmaT(mulT(g.dzf[c / pl], a[c]), b[c], s);
+    double s = 0.0, s2 = 0.0;
+    for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (size_t)gridDim.x * blockDim.x) {
+        const double wa = mulT(g.dzf[c / pl], a[c]);
+        s = fmaT(wa, b[c], s);
+        if (FLEX) s2 = fmaT(wa, b2[c], s2);
+    }
     s = block_sum(s);
     if (threadIdx.x == 0) part[blockIdx.x] = s;
+    if (FLEX) {
+        s2 = block_sum(s2);
+        if (threadIdx.x == 0) part2[blockIdx.x] = s2;
+    }
 }
 
-// rho = <r, z>; beta = rho / rho_old (0 on the first iteration).
-__global__ void __launch_bounds__(1024) k_vc_beta(const double *__restrict__ part, int nparts, VcState *vs,
-                                                  const DevStats *st) {
+// rho = <r, z>; beta = rho / rho_old, or (rho - <z, r_prev>) / rho_old in the
+// flexible form (0 on the first iteration).
+template <bool FLEX>
+__global__ void __launch_bounds__(1024) k_vc_beta(const double *__restrict__ part,
+                                                  const double *__restrict__ part2, int nparts,
+                                                  VcState *vs, const DevStats *st) {
     if (*(volatile const int *)&st->converged) return;
-    double s = 0.0;
-    for (int t = threadIdx.x; t < nparts; t += blockDim.x) s += part[t];
+    double s = 0.0, s2 = 0.0;
+    for (int t = threadIdx.x; t < nparts; t += blockDim.x) {
+        s += part[t];
+        if (FLEX) s2 += part2[t];
+    }
     s = block_sum(s);
+    if (FLEX) s2 = block_sum(s2);
     if (threadIdx.x == 0) {
-        vs->beta = vs->iters == 0 ? 0.0 : s / vs->rho;
+        const double num = FLEX ? s - s2 : s;
+        vs->beta = vs->iters == 0 ? 0.0 : num / vs->rho;
         vs->rho = s;
     }
+}
+
+// Mixed plans: the first preconditioner input, r 2^-e sigma in FP32.
+__global__ void __launch_bounds__(VC_THREADS) k_vc_spec32(GridDev g, const double *__restrict__ r,
+                                                         float *__restrict__ spec, const VcState *vs) {
+    const size_t n = (size_t)g.nx * g.ny * g.nz;
+    const int eb = exp_of_bits(vs->bmax_bits);
+    const float sc = (float)g.sigma;
+    for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (size_t)gridDim.x * blockDim.x)
+        spec[c] = f64_to_f32_shift(r[c], eb) * sc;
 }
 
 // d = z + beta d
@@ -187,23 +223,33 @@ __global__ void __launch_bounds__(1024) k_vc_alpha(const double *__restrict__ pa
     }
 }
 
-// x += alpha d, r -= alpha q, sigma r into the spectral workspace, max|r|;
-// the last block decides convergence.
+// x += alpha d, r -= alpha q, the next preconditioner input in the spectral
+// workspace (sigma r in FP64; mixed: r 2^-e sigma in FP32, and r_prev = the
+// old r for the flexible update), max|r|; the last block decides convergence.
+template <bool MIX>
 __global__ void __launch_bounds__(VC_THREADS) k_vc_update(GridDev g, double *__restrict__ x,
                                                          double *__restrict__ r,
                                                          const double *__restrict__ d,
                                                          const double *__restrict__ q,
-                                                         double *__restrict__ spec, VcState *vs,
-                                                         DevStats *st, double tol) {
+                                                         void *__restrict__ spec, double *__restrict__ r_prev,
+                                                         VcState *vs, DevStats *st, double tol) {
     if (*(volatile const int *)&st->converged) return;
     const size_t n = (size_t)g.nx * g.ny * g.nz;
     const double alpha = vs->alpha;
+    const int eb = MIX ? exp_of_bits(vs->bmax_bits) : 0;
+    const float sc = (float)g.sigma;
     unsigned long long mx = 0ull;
     for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (size_t)gridDim.x * blockDim.x) {
         x[c] = fmaT(alpha, d[c], x[c]);
-        const double rv = fmaT(-alpha, q[c], r[c]);
+        const double ro = r[c];
+        const double rv = fmaT(-alpha, q[c], ro);
         r[c] = rv;
-        spec[c] = mulT(rv, g.sigma);
+        if (MIX) {
+            r_prev[c] = ro;
+            ((float *)spec)[c] = f64_to_f32_shift(rv, eb) * sc;
+        } else {
+            ((double *)spec)[c] = mulT(rv, g.sigma);
+        }
         mx = umax64(mx, absbits(rv));
     }
     block_max_atomic(mx, &vs->rmax_bits);

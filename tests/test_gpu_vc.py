@@ -43,10 +43,9 @@ def cases():
 CASES = cases()
 
 
-def gpu_vc(case, max_iter=2000, tol=1e-12):
+def gpu_vc(case, max_iter=2000, tol=1e-12, precision=F.FP64):
     import torch
-    s = case.spec
-    plan = F.Plan.for_case(case, precision=F.FP64)
+    plan = F.Plan.for_case(case, precision=precision)
     u, v, w = to_dev(case.u), to_dev(case.v), to_dev(case.w)
     p = torch.empty_like(u)
     st = plan.solve_vc(to_dev(case.phi), u, v, w, p, max_iter=max_iter, tol=tol)
@@ -55,13 +54,16 @@ def gpu_vc(case, max_iter=2000, tol=1e-12):
     return dict(p=p.cpu().numpy(), u=u.cpu().numpy(), v=v.cpu().numpy(), w=w.cpu().numpy(), stats=st)
 
 
+@pytest.mark.parametrize("precision", [F.FP64, F.MIXED], ids=["fp64_precond", "fp32_precond"])
 @pytest.mark.parametrize("name", list(CASES))
-def test_vc_matches_dense_oracle(cuda_ok, name):
+def test_vc_matches_dense_oracle(cuda_ok, name, precision):
+    """FP64 plans precondition with the FP64 solve, mixed plans with the FP32
+    solve (flexible CG); both reach the same FP64 residual bar."""
     c = I.make_case(CASES[name])
     s = c.spec
     g = O.Grid.of_case(c)
     ref = O.project_vc(g, s.rho_l, s.rho_g, s.dt, c.phi, c.u, c.v, c.w)
-    got = gpu_vc(c)
+    got = gpu_vc(c, precision=precision)
     st = got["stats"]
     assert st["converged"] == 1 and st["relres"] <= 1e-12, st
     pg = got["p"] - O.weighted_mean(g, got["p"])
@@ -89,15 +91,16 @@ def test_vc_constant_density_is_the_split_projection(cuda_ok):
         assert relerr(a[k], b[k]) < 1e-11, k
 
 
+@pytest.mark.parametrize("precision", [F.FP64, F.MIXED], ids=["fp64_precond", "fp32_precond"])
 @pytest.mark.parametrize("bcz", [I.NEUMANN, P])
-def test_vc_properties_at_64(cuda_ok, bcz):
+def test_vc_properties_at_64(cuda_ok, bcz, precision):
     """64^3, density ratio 1000: through the oracle's O(N) operators, the
     GPU's p solves D(beta_f G p) = D(u*)/dt to the reported relres, u is
     divergence-free and u = u* - dt beta_f G p face by face."""
     spec = I.CaseSpec(nx=64, ny=64, nz=64, n_bubbles=6, radius_cells=5, config=96, bcz=bcz)
     c = I.make_case(spec)
     g = O.Grid.of_case(c)
-    got = gpu_vc(c, max_iter=3000, tol=1e-11)
+    got = gpu_vc(c, max_iter=3000, tol=1e-11, precision=precision)
     st = got["stats"]
     assert st["converged"] == 1
     b = O.div(g, c.u, c.v, c.w) / spec.dt
@@ -126,11 +129,6 @@ def test_vc_not_converged_is_reported(cuda_ok):
         plan.solve_vc(to_dev(c.phi), u, v, w, p, max_iter=3, tol=1e-14)
     assert e.value.code == -5
     plan.close()
-    mplan = F.Plan.for_case(c, precision=F.MIXED)
-    with pytest.raises(F.FizzyError) as e:
-        mplan.solve_vc(to_dev(c.phi), u, v, w, p)
-    assert e.value.code == -2
-    mplan.close()
 
 
 @pytest.mark.parametrize("bcz", [I.NEUMANN, P])
