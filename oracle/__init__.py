@@ -66,6 +66,7 @@ def lib():
             L.ora_apply_vc.argtypes = g + [D, D, d, d, d]
             L.ora_project_vc.argtypes = g + [D, D, D, d, d, d, d, d, d]
             L.ora_project_vc.restype = I
+            L.ora_acdi_rhs.argtypes = g + [D, D, D, d, d, d, d, d]
             L.ora_fft.argtypes = [I, d, d, d, d, I]
             L.ora_dft.argtypes = [I, d, d, d, d, I]
             L.ora_weighted_mean.argtypes = [I, I, I, d, d]
@@ -201,6 +202,15 @@ def project_vc(g: Grid, rho_l, rho_g, dt, phi, u, v, w):
     if st != 0:
         raise RuntimeError("oracle variable-coefficient projection failed with status %d" % st)
     return dict(p=p, u=uo, v=vo, w=wo, relres=diag[0], divmax=diag[1])
+
+
+def acdi_rhs(g: Grid, eps, gam, phi, u, v, w, delta=1e-100):
+    """Right-hand side of the ACDI phase-field transport (Jain 2022) in
+    conservative face-flux form: d phi/dt = rhs."""
+    arrs = [_c(a) for a in (phi, u, v, w)]
+    out = np.empty(g.shape)
+    lib().ora_acdi_rhs(*g.args(), eps, gam, delta, *[_p(a) for a in arrs], _p(out))
+    return out
 
 
 def fft(x, sign=-1):

@@ -821,6 +821,131 @@ int ora_project_vc(int nx, int ny, int nz, double dx, double dy, const double *z
     return st;
 }
 
+/* ------------------------------------------------------------------ */
+/* ACDI phase-field transport (the step that produces phi)              */
+/* ------------------------------------------------------------------ */
+/* The paper advances the phase field with the accurate conservative
+ * diffuse-interface (ACDI) model of Jain (2022):
+ *   d phi/dt + div(u phi) = div{ Gamma [ eps grad phi
+ *                                        - 1/4 (1 - tanh^2(psi/(2 eps))) n ] },
+ *   psi = eps ln((phi + delta)/(1 - phi + delta)),   n = grad psi / |grad psi|.
+ * Discretised in conservative (face-flux) form on the staggered grid:
+ *   psi and n at cell centres (n from central differences of psi, a wall
+ *   mirrors psi, |grad psi| = 0 gives n = 0);
+ *   on a face between cells a and b: F = u_f (phi_a + phi_b)/2
+ *       - Gamma [ eps (phi_b - phi_a)/h_ab
+ *                 - 1/4 (1 - tanh^2((psi_a + psi_b)/(4 eps))) (n_a + n_b)/2 ],
+ *   h_ab the centre distance, n the face-normal component; wall faces carry
+ *   no flux;
+ *   rhs = -D F;  one forward-Euler stage phi + dt rhs (stages of any explicit
+ *   scheme are made of these). */
+
+static double acdi_psi(double phi, double eps, double delta) {
+    return eps * log((phi + delta) / (1.0 - phi + delta));
+}
+
+/* rhs = -D F for the ACDI face fluxes F (see above). */
+void ora_acdi_rhs(int nx, int ny, int nz, double dx, double dy, const double *zf, int bcx, int bcy,
+                  int bcz, double eps, double gam, double delta, const double *phi, const double *u,
+                  const double *v, const double *w, double *rhs) {
+    grid_t g = mkgrid(nx, ny, nz, dx, dy, zf, bcx, bcy, bcz);
+    size_t n = (size_t)nx * ny * nz;
+    double *psi = malloc(n * sizeof(double));
+    double *nxv = malloc(n * sizeof(double)), *nyv = malloc(n * sizeof(double)),
+           *nzv = malloc(n * sizeof(double));
+    double *fx = malloc(n * sizeof(double)), *fy = malloc(n * sizeof(double)),
+           *fz = malloc(n * sizeof(double));
+    for (size_t c = 0; c < n; ++c) psi[c] = acdi_psi(phi[c], eps, delta);
+    /* unit normals at centres: central differences; at a wall the missing
+     * neighbour mirrors the cell (psi_ghost = psi_cell, ghost centre mirrored
+     * across the wall face) */
+#pragma omp parallel for schedule(static)
+    for (int k = 0; k < nz; ++k)
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i < nx; ++i) {
+                size_t c = IDX(&g, i, j, k);
+                int ip = i + 1, im = i - 1, jp = j + 1, jm = j - 1;
+                double pxp, pxm, pyp, pym, pzp, pzm;
+                if (ip == nx) ip = bcx == 0 ? 0 : -1;
+                if (im < 0) im = bcx == 0 ? nx - 1 : -1;
+                if (jp == ny) jp = bcy == 0 ? 0 : -1;
+                if (jm < 0) jm = bcy == 0 ? ny - 1 : -1;
+                pxp = ip >= 0 ? psi[IDX(&g, ip, j, k)] : psi[c];
+                pxm = im >= 0 ? psi[IDX(&g, im, j, k)] : psi[c];
+                pyp = jp >= 0 ? psi[IDX(&g, i, jp, k)] : psi[c];
+                pym = jm >= 0 ? psi[IDX(&g, i, jm, k)] : psi[c];
+                double gx = (pxp - pxm) / (2.0 * dx), gy = (pyp - pym) / (2.0 * dy);
+                /* z: centre distance between the two neighbours used */
+                double zlo, zhi;
+                if (k + 1 < nz) {
+                    pzp = psi[IDX(&g, i, j, k + 1)];
+                    zhi = zc(&g, k + 1);
+                } else if (bcz == 0) {
+                    pzp = psi[IDX(&g, i, j, 0)];
+                    zhi = zc(&g, 0) + (zf[nz] - zf[0]);
+                } else {
+                    pzp = psi[c];
+                    zhi = 2.0 * zf[nz] - zc(&g, k);
+                }
+                if (k > 0) {
+                    pzm = psi[IDX(&g, i, j, k - 1)];
+                    zlo = zc(&g, k - 1);
+                } else if (bcz == 0) {
+                    pzm = psi[IDX(&g, i, j, nz - 1)];
+                    zlo = zc(&g, nz - 1) - (zf[nz] - zf[0]);
+                } else {
+                    pzm = psi[c];
+                    zlo = 2.0 * zf[0] - zc(&g, 0);
+                }
+                double gz = (pzp - pzm) / (zhi - zlo);
+                double mag = sqrt(gx * gx + gy * gy + gz * gz);
+                nxv[c] = mag > 0 ? gx / mag : 0.0;
+                nyv[c] = mag > 0 ? gy / mag : 0.0;
+                nzv[c] = mag > 0 ? gz / mag : 0.0;
+            }
+    /* face fluxes on the +x, +y, +z face of every cell (0 on walls) */
+#pragma omp parallel for schedule(static)
+    for (int k = 0; k < nz; ++k)
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i < nx; ++i) {
+                size_t c = IDX(&g, i, j, k);
+                int ie = (i < nx - 1) ? i + 1 : (bcx == 0 ? 0 : -1);
+                int jn = (j < ny - 1) ? j + 1 : (bcy == 0 ? 0 : -1);
+                int kt = (k < nz - 1) ? k + 1 : (bcz == 0 ? 0 : -1);
+                fx[c] = fy[c] = fz[c] = 0.0;
+                if (ie >= 0) {
+                    size_t b = IDX(&g, ie, j, k);
+                    double t = tanh((psi[c] + psi[b]) / (4.0 * eps));
+                    fx[c] = u[c] * 0.5 * (phi[c] + phi[b]) -
+                            gam * (eps * (phi[b] - phi[c]) / dx -
+                                   0.25 * (1.0 - t * t) * 0.5 * (nxv[c] + nxv[b]));
+                }
+                if (jn >= 0) {
+                    size_t b = IDX(&g, i, jn, k);
+                    double t = tanh((psi[c] + psi[b]) / (4.0 * eps));
+                    fy[c] = v[c] * 0.5 * (phi[c] + phi[b]) -
+                            gam * (eps * (phi[b] - phi[c]) / dy -
+                                   0.25 * (1.0 - t * t) * 0.5 * (nyv[c] + nyv[b]));
+                }
+                if (kt >= 0) {
+                    size_t b = IDX(&g, i, j, kt);
+                    double t = tanh((psi[c] + psi[b]) / (4.0 * eps));
+                    fz[c] = w[c] * 0.5 * (phi[c] + phi[b]) -
+                            gam * (eps * (phi[b] - phi[c]) / dzc(&g, k) -
+                                   0.25 * (1.0 - t * t) * 0.5 * (nzv[c] + nzv[b]));
+                }
+            }
+    divergence(&g, fx, fy, fz, rhs);
+    for (size_t c = 0; c < n; ++c) rhs[c] = -rhs[c];
+    free(psi);
+    free(nxv);
+    free(nyv);
+    free(nzv);
+    free(fx);
+    free(fy);
+    free(fz);
+}
+
 int ora_num_threads(void) {
 #ifdef _OPENMP
     extern int omp_get_max_threads(void);

@@ -18,7 +18,7 @@ SRC = os.path.join(ROOT, "oracle", "oracle.c")
 
 PINS = ("exact_rational or eigenmodes or apply_then_solve or divergence_free or "
         "constant_density or dense_solves or stretched_z or correction_identity or "
-        "triperiodic or rotation_commutes or vc_")
+        "triperiodic or rotation_commutes or vc_ or acdi_")
 
 MUTATIONS = [
     ("grad_sign", "gx[c] = (q[IDX(g, i + 1, j, k)] - q[c]) / g->dx;",
@@ -69,6 +69,15 @@ MUTATIONS = [
      "if (!(bcx == 1 && i == nx - 1)) u[c] += dt * bx[c] * gx[c];"),
     ("vc_rhs_dt", "for (size_t c = 0; c < n; ++c) rhs[c] /= dt;",
      "for (size_t c = 0; c < n; ++c) rhs[c] *= dt;"),
+    # ACDI transport
+    ("acdi_quarter", "0.25 * (1.0 - t * t) * 0.5 * (nxv[c] + nxv[b])",
+     "0.5 * (1.0 - t * t) * 0.5 * (nxv[c] + nxv[b])"),
+    ("acdi_tanh_width", "double t = tanh((psi[c] + psi[b]) / (4.0 * eps));",
+     "double t = tanh((psi[c] + psi[b]) / (2.0 * eps));"),
+    ("acdi_normal_one_sided", "0.5 * (nxv[c] + nxv[b])", "nxv[c]"),
+    ("acdi_advect_upwind", "fx[c] = u[c] * 0.5 * (phi[c] + phi[b])", "fx[c] = u[c] * phi[c]"),
+    ("acdi_psi_sign", "return eps * log((phi + delta) / (1.0 - phi + delta));",
+     "return eps * log((1.0 - phi + delta) / (phi + delta));"),
     ("z_matrix_wrap_column", "A[(size_t)k * nz + (k + nz - 1) % nz] += lo[k];",
      "A[(size_t)k * nz + (k + nz - 2) % nz] += lo[k];"),
     ("neumann_extension", "return (bc == 0 || e < n) ? e : 2 * n - 1 - e;",

@@ -565,3 +565,77 @@ def test_vc_is_the_split_fixed_point(bcz):
     assert relerr(s["p"], r["p"]) < 1e-10
     for k in "uvw":
         assert relerr(s[k], r[k]) < 1e-10, k
+
+
+# --------------------------------------------------------------------------
+# ACDI phase-field transport (Jain 2022), conservative face-flux form
+# --------------------------------------------------------------------------
+def _acdi_case(bcx, bcy, bcz, beta, config, noise=0.0):
+    spec = I.CaseSpec(nx=14, ny=12, nz=10, bcx=bcx, bcy=bcy, bcz=bcz, beta=beta, n_bubbles=2,
+                      radius_cells=3.0, noise=noise, config=config)
+    return spec, I.make_case(spec)
+
+
+@pytest.mark.parametrize("bcx,bcy,bcz,beta", [(0, 0, 1, 0.0), (1, 0, 1, 1.5), (0, 1, 0, 1.2),
+                                              (1, 1, 0, 0.0)])
+def test_acdi_conserves_mass(bcx, bcy, bcz, beta):
+    """The face-flux form telescopes: sum_c dV_c rhs_c = 0 (walls carry no
+    flux, periodic faces appear twice with opposite signs)."""
+    spec, c = _acdi_case(bcx, bcy, bcz, beta, 84, noise=0.1)
+    g = O.Grid.of_case(c)
+    r = O.acdi_rhs(g, c.dx, 1.3, c.phi, c.u, c.v, c.w)
+    dv = np.diff(c.zf)[:, None, None] * c.dx * c.dy
+    assert abs(np.sum(dv * r)) <= 1e-13 * np.sum(np.abs(dv * r))
+    assert np.max(np.abs(r)) > 0
+
+
+@pytest.mark.parametrize("bcz", [1, 0])
+def test_acdi_central_advection_conserves_phi_squared(bcz):
+    """Gamma = 0 and a discretely divergence-free u (the staggered curl of
+    the input recipe): sum_c dV phi rhs = -1/2 sum_c dV phi^2 D u = 0."""
+    spec, c = _acdi_case(0, 1, bcz, 1.3, 85)
+    g = O.Grid.of_case(c)
+    assert np.max(np.abs(O.div(g, c.u, c.v, c.w))) < 1e-10 * np.max(np.abs(c.u)) / c.dx
+    phi = np.random.default_rng(3).uniform(0.05, 0.95, g.shape)
+    r = O.acdi_rhs(g, c.dx, 0.0, phi, c.u, c.v, c.w)
+    dv = np.diff(c.zf)[:, None, None]
+    assert abs(np.sum(dv * phi * r)) <= 1e-12 * np.sum(np.abs(dv * phi * r))
+    # and a constant phi does not move
+    r0 = O.acdi_rhs(g, c.dx, 0.0, np.full(g.shape, 0.3), c.u, c.v, c.w)
+    assert np.max(np.abs(r0)) <= 1e-10 * np.max(np.abs(c.u)) / c.dx
+
+
+def test_acdi_equilibrium_profile_second_order():
+    """u = 0 and the kernel profile phi = 1/2 (1 + tanh((x - x0)/(2 eps))):
+    psi is then the signed distance x - x0, |n| = 1 and the diffusive and
+    sharpening fluxes cancel in the continuum, so the discrete rhs is pure
+    truncation error.  Halving dx at fixed eps divides it by about 4."""
+    eps, x0 = 0.04, 0.5 + 1e-3
+    errs = []
+    for nx in (64, 128, 256):
+        dx = 1.0 / nx
+        g = O.Grid(nx, 2, 2, dx, dx, np.array([0.0, dx, 2 * dx]), I.NEUMANN, I.PERIODIC, I.PERIODIC)
+        xc = (np.arange(nx) + 0.5) * dx
+        phi = np.broadcast_to(0.5 * (1 + np.tanh((xc - x0) / (2 * eps))), g.shape).copy()
+        z = np.zeros(g.shape)
+        r = O.acdi_rhs(g, eps, 1.0, phi, z, z, z)
+        errs.append(np.max(np.abs(r)))
+    assert 3.3 < errs[0] / errs[1] < 4.7 and 3.3 < errs[1] / errs[2] < 4.7, errs
+    # a profile of the wrong width is not in equilibrium
+    g = O.Grid(128, 2, 2, 1 / 128, 1 / 128, np.array([0.0, 1 / 128, 2 / 128]), I.NEUMANN, 0, 0)
+    xc = (np.arange(128) + 0.5) / 128
+    phi = np.broadcast_to(0.5 * (1 + np.tanh((xc - x0) / (4 * eps))), g.shape).copy()
+    z = np.zeros(g.shape)
+    assert np.max(np.abs(O.acdi_rhs(g, eps, 1.0, phi, z, z, z))) > 30 * errs[1]
+
+
+def test_acdi_axis_swap_symmetry():
+    """On a square x-y grid, swapping x and y (and u with v) swaps the rhs."""
+    spec = I.CaseSpec(nx=12, ny=12, nz=8, bcx=1, bcy=1, beta=1.2, n_bubbles=2, radius_cells=2.5,
+                      config=86, noise=0.05)
+    c = I.make_case(spec)
+    g = O.Grid.of_case(c)
+    r = O.acdi_rhs(g, c.dx, 0.8, c.phi, c.u, c.v, c.w)
+    sw = lambda a: np.ascontiguousarray(np.swapaxes(a, 1, 2))
+    r2 = O.acdi_rhs(g, c.dx, 0.8, sw(c.phi), sw(c.v), sw(c.u), sw(c.w))
+    assert relerr(r2, sw(r)) < 1e-13
