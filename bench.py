@@ -675,6 +675,58 @@ def run_vc(args):
     return 0
 
 
+def run_acdi(args):
+    """One explicit stage of the ACDI phase-field transport (fizzy_acdi_step)
+    on a workload: time per stage with inputs resident in HBM, against the
+    algorithmic bytes of its four passes (psi: 16 B/pt; normals: 32; face
+    fluxes: phi, psi, 3 normals, u, v, w in, 3 fluxes out = 88; update:
+    phi, 3 fluxes in, phi out = 40; 176 B/pt)."""
+    import torch
+    import paper_2502_04189_b300 as F
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    spec = WORKLOADS[args.workload]()
+    case = I.make_case(spec)
+    npts = case.npts
+
+    def dev(a):
+        return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+    phi, u, v, w = dev(case.phi), dev(case.u), dev(case.v), dev(case.w)
+    out = torch.empty_like(phi)
+    plan = F.Plan.for_case(case, precision=F.FP64)
+    eps, gam, dt = case.dx, 1.0, 1e-4
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        plan.acdi_step(phi, u, v, w, eps, gam, dt, phi_out=out)
+    clocks = ClockSampler()
+    clocks.start()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        plan.acdi_step(phi, u, v, w, eps, gam, dt, phi_out=out)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    plan.close()
+    hbm_peak, hbm_src = measured_peaks()
+    gbs = 176 * npts / (ms / 1e3) / 1e9
+    if rank == 0:
+        line = {"metric": "grid pts/s per ACDI stage", "value": npts / (ms / 1e3), "unit": "pts/s",
+                "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic",
+                "config": {"workload": args.workload, "grid": [spec.nx, spec.ny, spec.nz],
+                           "form": "ACDI phase-field stage (4 kernels)", "eps": "dx", "gamma": gam},
+                "hbm": {"algorithmic_bytes_per_pt": 176, "achieved_gbs": gbs, "peak": hbm_peak,
+                        "frac": gbs / hbm_peak, "peak_source": hbm_src},
+                "gpu_launches": 4 * args.steps, "clocks": clk}
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -690,6 +742,7 @@ def main():
     ap.add_argument("--vc", action="store_true",
                     help="time the variable-coefficient projection without splitting instead")
     ap.add_argument("--vc-tol", type=float, default=1e-10)
+    ap.add_argument("--acdi", action="store_true", help="time the ACDI phase-field stage instead")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -699,6 +752,8 @@ def main():
         return run_serve(args)
     if args.vc:
         return run_vc(args)
+    if args.acdi:
+        return run_acdi(args)
     return run_fizzy(args)
 
 

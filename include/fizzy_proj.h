@@ -159,6 +159,29 @@ int fizzy_proj_solve(fizzy_proj_plan_t p, const double *phi, const double *p_n, 
 int fizzy_proj_solve_vc(fizzy_proj_plan_t p, const double *phi, double *u, double *v, double *w,
                         double *p_np1, int max_iter, double tol, fizzy_proj_stats *st, void *stream);
 
+/* One explicit stage of the ACDI phase-field transport (Jain 2022; the
+ * paper's phase-field model), the step that produces phi before a
+ * projection, on the plan's grid and boundaries:
+ *     d phi/dt = rhs = -div(u phi) + div{ gamma [ eps grad phi
+ *                        - 1/4 (1 - tanh^2(psi/(2 eps))) grad psi/|grad psi| ] },
+ *     psi = eps ln((phi + 1e-100)/(1 - phi + 1e-100)),
+ * in conservative face-flux form: psi and its unit gradient at the centres
+ * (central differences, a wall mirrors psi, a zero gradient gives 0), face
+ * values as the mean of the two cells, wall faces carry no flux (mass is
+ * conserved to round-off).
+ *   phi          : in, cell centred.
+ *   u, v, w      : in, face velocities (the projection's layout; wall faces 0).
+ *   eps, gamma   : interface thickness (> 0) and velocity scale (>= 0).
+ *   dt           : stage step; phi_out = phi + dt rhs.
+ *   rhs_out      : out rhs, or NULL.
+ *   phi_out      : out, or NULL; may alias phi (not u, v, w, rhs_out).
+ * Asynchronous on stream.  Uses the plan's face-flux buffers as scratch
+ * (a projection queued after it on the same stream is unaffected) and
+ * allocates 4 fields on first use.  FP64 in either precision mode. */
+int fizzy_acdi_step(fizzy_proj_plan_t p, const double *phi, const double *u, const double *v,
+                    const double *w, double eps, double gamma, double dt, double *rhs_out,
+                    double *phi_out, void *stream);
+
 /* Rebind the densities and time step of a plan (the grid, its transforms and
  * z-factorisation tables do not depend on them).  Updates four per-plane
  * tables by an asynchronous copy on stream; solves issued after it on the

@@ -154,6 +154,18 @@ class Plan:
             raise FizzyError(rc, _abi.lib().fizzy_proj_last_error(self._h).decode())
         return st.as_dict()
 
+    def acdi_step(self, phi, u, v, w, eps, gamma, dt=0.0, rhs_out=None, phi_out=None, stream=None):
+        """One explicit stage of the ACDI phase-field transport
+        (fizzy_acdi_step) on this plan's grid: rhs_out = d phi/dt,
+        phi_out = phi + dt rhs (either may be None; phi_out may be phi)."""
+        nul = ctypes.c_void_p(0)
+        rc = _abi.lib().fizzy_acdi_step(self._h, _ptr(phi), _ptr(u), _ptr(v), _ptr(w), float(eps),
+                                        float(gamma), float(dt),
+                                        nul if rhs_out is None else _ptr(rhs_out),
+                                        nul if phi_out is None else _ptr(phi_out), _stream_handle(stream))
+        if rc != 0:
+            raise FizzyError(rc, _abi.lib().fizzy_proj_last_error(self._h).decode())
+
     def stats(self, stream=None):
         st = Stats()
         self._check(_abi.lib().fizzy_proj_get_stats(self._h, ctypes.byref(st), _stream_handle(stream)))

@@ -22,7 +22,7 @@ EXPORTED = ("fizzy_proj_plan", "fizzy_proj_workspace_bytes", "fizzy_proj_solve",
             "fizzy_serve_launch", "fizzy_serve_poll", "fizzy_serve_stats", "fizzy_serve_release",
             "fizzy_serve_info", "fizzy_serve_destroy", "fizzy_proj_solve_host_async",
             "fizzy_proj_host_wait", "fizzy_crop_fill", "fizzy_proj_batch_inject_stall",
-            "fizzy_proj_solve_vc")
+            "fizzy_proj_solve_vc", "fizzy_acdi_step")
 ERRORS[-7] = "busy"
 NOALLOC_MAX_CELLS = 262144
 DEFAULT_MAX_REFINE = 4  # FIZZY_DEFAULT_MAX_REFINE
@@ -78,6 +78,8 @@ def lib():
         L.fizzy_proj_solve_vc.argtypes = [vp] + [vp] * 5 + [ctypes.c_int, ctypes.c_double,
                                                              ctypes.POINTER(Stats), vp]
         L.fizzy_proj_solve_vc.restype = ctypes.c_int
+        L.fizzy_acdi_step.argtypes = [vp] + [vp] * 4 + [ctypes.c_double] * 3 + [vp, vp, vp]
+        L.fizzy_acdi_step.restype = ctypes.c_int
         L.fizzy_proj_solve_host.argtypes = [vp] + [vp] * 7 + [ctypes.POINTER(Stats), vp]
         L.fizzy_proj_solve_host.restype = ctypes.c_int
         L.fizzy_proj_solve_host_async.argtypes = [vp] + [vp] * 10 + [vp]

@@ -6,6 +6,7 @@
 #include "kern_passes.cuh"
 #include "kern_r16.cuh"
 #include "kern_vc.cuh"
+#include "kern_acdi.cuh"
 
 #include <algorithm>
 #include <cmath>
@@ -72,6 +73,8 @@ struct fizzy_proj_plan_s {
     double *vc[7] = {};
     double *vc_part = nullptr;
     VcState *vc_state = nullptr;
+    // ACDI step (fizzy_acdi_step), allocated on first use: psi and the unit normal
+    double *acdi[4] = {};
     double *qx = nullptr, *qy = nullptr, *qz = nullptr;
     double *fhat64 = nullptr;
     float *fhat32 = nullptr;
@@ -1111,6 +1114,11 @@ int fizzy_proj_solve_host(fizzy_proj_plan_t p, const double *phi, const double *
 // Variable-coefficient projection without splitting (fizzy_proj_solve_vc)
 // ===========================================================================
 #include "fizzy_vc.inc"
+
+// ===========================================================================
+// ACDI phase-field step (fizzy_acdi_step)
+// ===========================================================================
+#include "fizzy_acdi.inc"
 
 // ===========================================================================
 // Serving runtime (fizzy_serve_*)
