@@ -678,9 +678,9 @@ def run_vc(args):
 def run_acdi(args):
     """One explicit stage of the ACDI phase-field transport (fizzy_acdi_step)
     on a workload: time per stage with inputs resident in HBM, against the
-    algorithmic bytes of its four passes (psi: 16 B/pt; normals: 32; face
-    fluxes: phi, psi, 3 normals, u, v, w in, 3 fluxes out = 88; update:
-    phi, 3 fluxes in, phi out = 40; 176 B/pt)."""
+    algorithmic bytes of its four passes (psi and r: 24 B/pt; normals: 32;
+    face fluxes: phi, r, 3 normals, u, v, w in, 3 fluxes out = 88; update:
+    phi, 3 fluxes in, phi out = 40; 184 B/pt)."""
     import torch
     import paper_2502_04189_b300 as F
     world, rank, local = dist_env()
@@ -712,7 +712,7 @@ def run_acdi(args):
     ms = e0.elapsed_time(e1) / args.steps
     plan.close()
     hbm_peak, hbm_src = measured_peaks()
-    gbs = 176 * npts / (ms / 1e3) / 1e9
+    gbs = 184 * npts / (ms / 1e3) / 1e9
     if rank == 0:
         line = {"metric": "grid pts/s per ACDI stage", "value": npts / (ms / 1e3), "unit": "pts/s",
                 "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
@@ -720,7 +720,7 @@ def run_acdi(args):
                 "data": "synthetic",
                 "config": {"workload": args.workload, "grid": [spec.nx, spec.ny, spec.nz],
                            "form": "ACDI phase-field stage (4 kernels)", "eps": "dx", "gamma": gam},
-                "hbm": {"algorithmic_bytes_per_pt": 176, "achieved_gbs": gbs, "peak": hbm_peak,
+                "hbm": {"algorithmic_bytes_per_pt": 184, "achieved_gbs": gbs, "peak": hbm_peak,
                         "frac": gbs / hbm_peak, "peak_source": hbm_src},
                 "gpu_launches": 4 * args.steps, "clocks": clk}
         print(json.dumps(line), flush=True)

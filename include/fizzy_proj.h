@@ -177,7 +177,7 @@ int fizzy_proj_solve_vc(fizzy_proj_plan_t p, const double *phi, double *u, doubl
  *   phi_out      : out, or NULL; may alias phi (not u, v, w, rhs_out).
  * Asynchronous on stream.  Uses the plan's face-flux buffers as scratch
  * (a projection queued after it on the same stream is unaffected) and
- * allocates 4 fields on first use.  FP64 in either precision mode. */
+ * allocates 5 fields on first use.  FP64 in either precision mode. */
 int fizzy_acdi_step(fizzy_proj_plan_t p, const double *phi, const double *u, const double *v,
                     const double *w, double eps, double gamma, double dt, double *rhs_out,
                     double *phi_out, void *stream);

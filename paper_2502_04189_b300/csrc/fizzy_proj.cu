@@ -73,8 +73,9 @@ struct fizzy_proj_plan_s {
     double *vc[7] = {};
     double *vc_part = nullptr;
     VcState *vc_state = nullptr;
-    // ACDI step (fizzy_acdi_step), allocated on first use: psi and the unit normal
-    double *acdi[4] = {};
+    // ACDI step (fizzy_acdi_step), allocated on first use: psi, the unit
+    // normal, sqrt((phi + delta)/(1 - phi + delta))
+    double *acdi[5] = {};
     double *qx = nullptr, *qy = nullptr, *qz = nullptr;
     double *fhat64 = nullptr;
     float *fhat32 = nullptr;

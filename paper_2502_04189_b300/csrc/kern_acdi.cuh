@@ -5,7 +5,8 @@
 //                                        - 1/4 (1 - tanh^2(psi/(2 eps))) n ] },
 //   psi = eps ln((phi + delta)/(1 - phi + delta)),   n = grad psi / |grad psi|,
 // in conservative face-flux form on the staggered grid (FP64):
-//   k_acdi_psi    : psi at the centres (one log per cell);
+//   k_acdi_psi    : r = (phi + delta)/(1 - phi + delta), psi = eps ln r and
+//                   q = sqrt(r) at the centres (one log per cell);
 //   k_acdi_normal : n at the centres from central differences of psi (a wall
 //                   mirrors psi; the centre distances are the sums of the two
 //                   half spacings, so stretched and periodic z need nothing
@@ -15,6 +16,11 @@
 //                       - 1/4 (1 - tanh^2((psi_a + psi_b)/(4 eps))) (n_a + n_b)/2 ],
 //                   0 on walls;
 //   k_acdi_update : rhs = -D F, phi_out = phi + dt rhs.
+// The face coefficient 1 - tanh^2(x), x = (psi_a + psi_b)/(4 eps), is formed
+// without the tanh: psi/eps = ln r gives e^(2x) = sqrt(r_a r_b) = q_a q_b = S,
+// so tanh x = (S - 1)/(S + 1) and 1 - tanh^2 x = 4 S/(1 + S)^2 exactly (one
+// multiply and one division per face instead of an FP64 tanh, and no
+// cancellation where tanh x is near +-1; S stays within [1e-100, 1e100]).
 // Mass is conserved to round-off: every face flux enters two cells with
 // opposite signs (walls carry none).
 #pragma once
@@ -33,11 +39,13 @@ __device__ __forceinline__ void acdi_ijk(const GridDev &g, size_t c, int &i, int
 }
 
 __global__ void __launch_bounds__(256) k_acdi_psi(GridDev g, double eps, const double *__restrict__ phi,
-                                                  double *__restrict__ psi) {
+                                                  double *__restrict__ psi, double *__restrict__ rr) {
     const size_t n = (size_t)g.nx * g.ny * g.nz;
     for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (size_t)gridDim.x * blockDim.x) {
         const double f = phi[c];
-        psi[c] = eps * log((f + ACDI_DELTA) / (1.0 - f + ACDI_DELTA));
+        const double r = (f + ACDI_DELTA) / (1.0 - f + ACDI_DELTA);
+        rr[c] = sqrt(r);
+        psi[c] = eps * log(r);
     }
 }
 
@@ -79,25 +87,26 @@ __global__ void __launch_bounds__(256) k_acdi_normal(GridDev g, const double *__
             dn = g.dzf[0];
         }
         const double gx = (pe - pw) * hx, gy = (pn - ps) * hy, gz = (pt - pb) / (up + dn);
-        const double mag = sqrt(fmaT(gx, gx, fmaT(gy, gy, mulT(gz, gz))));
-        const double inv = mag > 0.0 ? 1.0 / mag : 0.0;
+        const double m2 = fmaT(gx, gx, fmaT(gy, gy, mulT(gz, gz)));
+        const double inv = m2 > 0.0 ? rsqrt(m2) : 0.0;
         nxo[c] = gx * inv;
         nyo[c] = gy * inv;
         nzo[c] = gz * inv;
     }
 }
 
-// One face: advective plus diffusive-sharpening flux between cells a and b.
-__device__ __forceinline__ double acdi_face(double ua, double fa, double fb, double sa, double sb, double na,
-                                            double nb, double ih, double eps, double gam, double i4eps) {
-    const double t = tanh((sa + sb) * i4eps);
-    const double sharp = 0.25 * (1.0 - t * t) * (0.5 * (na + nb));
+// One face: advective plus diffusive-sharpening flux between cells a and b;
+// 1/4 (1 - tanh^2) = S/(1 + S)^2 with S = q_a q_b.
+__device__ __forceinline__ double acdi_face(double ua, double fa, double fb, double qa, double qb, double na,
+                                            double nb, double ih, double eps, double gam) {
+    const double S = qa * qb, S1 = 1.0 + S;
+    const double sharp = S / (S1 * S1) * (0.5 * (na + nb));
     return fmaT(ua, 0.5 * (fa + fb), -gam * (eps * (fb - fa) * ih - sharp));
 }
 
 __global__ void __launch_bounds__(256) k_acdi_flux(GridDev g, double eps, double gam,
                                                    const double *__restrict__ phi,
-                                                   const double *__restrict__ psi,
+                                                   const double *__restrict__ rr,
                                                    const double *__restrict__ nxv,
                                                    const double *__restrict__ nyv,
                                                    const double *__restrict__ nzv,
@@ -106,27 +115,26 @@ __global__ void __launch_bounds__(256) k_acdi_flux(GridDev g, double eps, double
                                                    const double *__restrict__ w, double *__restrict__ fx,
                                                    double *__restrict__ fy, double *__restrict__ fz) {
     const size_t n = (size_t)g.nx * g.ny * g.nz, pl = (size_t)g.nx * g.ny;
-    const double i4eps = 0.25 / eps;
     for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (size_t)gridDim.x * blockDim.x) {
         int i, j, k;
         acdi_ijk(g, c, i, j, k);
-        const double fc = phi[c], sc = psi[c];
+        const double fc = phi[c], sc = rr[c];
         double q = 0.0;
         if (i < g.nx - 1 || g.bcx == BC_PERIODIC) {
             const size_t b = i < g.nx - 1 ? c + 1 : c - i;
-            q = acdi_face(u[c], fc, phi[b], sc, psi[b], nxv[c], nxv[b], g.idx1, eps, gam, i4eps);
+            q = acdi_face(u[c], fc, phi[b], sc, rr[b], nxv[c], nxv[b], g.idx1, eps, gam);
         }
         fx[c] = q;
         q = 0.0;
         if (j < g.ny - 1 || g.bcy == BC_PERIODIC) {
             const size_t b = j < g.ny - 1 ? c + g.nx : c - (size_t)j * g.nx;
-            q = acdi_face(v[c], fc, phi[b], sc, psi[b], nyv[c], nyv[b], g.idy1, eps, gam, i4eps);
+            q = acdi_face(v[c], fc, phi[b], sc, rr[b], nyv[c], nyv[b], g.idy1, eps, gam);
         }
         fy[c] = q;
         q = 0.0;
         if (k < g.nz - 1 || g.perz) {
             const size_t b = k < g.nz - 1 ? c + pl : c - (size_t)k * pl;
-            q = acdi_face(w[c], fc, phi[b], sc, psi[b], nzv[c], nzv[b], 1.0 / g.dzc[k], eps, gam, i4eps);
+            q = acdi_face(w[c], fc, phi[b], sc, rr[b], nzv[c], nzv[b], 1.0 / g.dzc[k], eps, gam);
         }
         fz[c] = q;
     }
