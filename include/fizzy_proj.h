@@ -368,7 +368,8 @@ int fizzy_serve_destroy(fizzy_serve_t s);
  *   dst_f[k][j][i] = src_f[(k + oz) mod tz][(j + oy) mod ty][(i + ox) mod tx],
  * except that the wall faces of the staggered velocity are zero: u at
  * i = nx-1 when bc_x is FIZZY_BC_NEUMANN, v at j = ny-1 when bc_y is, and w
- * at k = nz-1 always (the top wall).  One kernel on `stream` (null: the
+ * at k = nz-1 always (the top wall; for a periodic-z request that face is
+ * the seam and must be staged by a plain copy instead).  One kernel on `stream` (null: the
  * legacy default stream) moving 96 bytes per output point; dst must not
  * overlap src.  Returns FIZZY_ERR_INVALID for a null pointer, an extent < 1,
  * a negative offset or a bc other than the two above, else FIZZY_OK or
