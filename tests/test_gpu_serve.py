@@ -100,3 +100,55 @@ def test_served_equals_alone_and_overlaps(cuda_ok, budget):
         plan.close()
         for got, ref in zip(served[r.index], (p, u, v, w)):
             assert np.array_equal(got, ref.cpu().numpy()), r.index
+
+
+def test_served_periodic_z_requests(cuda_ok):
+    """Periodic-z requests through the serving runtime, next to a
+    wall-bounded request of the same grid (the plan cache keys on the z
+    boundary): each result equals the same request solved alone, bit for bit,
+    and the periodic ones match the oracle within the mixed bar."""
+    import torch
+    import oracle as O
+    from gpu_util import compare
+    specs = [I.CaseSpec(nx=32, ny=24, nz=20, n_bubbles=2, radius_cells=3, config=110, bcz=I.PERIODIC),
+             I.CaseSpec(nx=32, ny=24, nz=20, n_bubbles=2, radius_cells=3, config=111),
+             I.CaseSpec(nx=48, ny=32, nz=18, bcx=1, beta=1.3, n_bubbles=2, radius_cells=3, config=112,
+                        bcz=I.PERIODIC)]
+    cases = [I.make_case(s) for s in specs]
+    reqs = []
+    for i, c in enumerate(cases):
+        s = c.spec
+        desc = dict(nx=s.nx, ny=s.ny, nz=s.nz, dx=c.dx, dy=c.dy, zf=c.zf, bcx=s.bcx, bcy=s.bcy,
+                    rho_l=s.rho_l, rho_g=s.rho_g, dt=s.dt, precision=F.MIXED,
+                    periodic_z=s.bcz == I.PERIODIC)
+        reqs.append(S.Request(i, 0.0, desc, (0, 0, 0)))
+    server = F.Server(4 << 30, slots=4)
+    served = {}
+
+    def fill(r, views, stream):
+        c = cases[r.index]
+        with torch.cuda.stream(stream):
+            for k, a in enumerate((c.phi, c.pn, c.pnm1, c.u, c.v, c.w)):
+                views[k].copy_(torch.from_numpy(np.ascontiguousarray(a)), non_blocking=False)
+
+    def on_done(r, views):
+        served[r.index] = [views[k].cpu().numpy() for k in (6, 3, 4, 5)]
+
+    out, summ = S.run(server, reqs, fill, deadline=30.0, on_done=on_done)
+    info = server.info()
+    server.close()
+    assert summ["admitted"] == 3 and summ["all_converged"]
+    assert info["plans_built"] == 3  # same grid, different z boundary: two plans
+    for i, c in enumerate(cases):
+        plan = F.Plan.for_case(c, precision=F.MIXED)
+        phi, pn, pm, u, v, w = (to_dev(a) for a in (c.phi, c.pn, c.pnm1, c.u, c.v, c.w))
+        p = torch.empty_like(phi)
+        plan.solve(phi, pn, pm, u, v, w, p)
+        torch.cuda.synchronize()
+        plan.close()
+        for got, ref in zip(served[i], (p, u, v, w)):
+            assert np.array_equal(got, ref.cpu().numpy()), i
+        if c.spec.bcz == I.PERIODIC:
+            got = dict(p=served[i][0], u=served[i][1], v=served[i][2], w=served[i][3])
+            ep, eu = compare(c, got, O.project_case(c))
+            assert ep <= 1e-9 and eu <= 1e-9, (i, ep, eu)
