@@ -139,8 +139,9 @@ int fizzy_proj_solve(fizzy_proj_plan_t p, const double *phi, const double *p_n, 
  * (the equation the splitting replaces; the paper's Hypre path solves it):
  *     D(beta_f G p) = D(u*)/dt,   u = u* - dt beta_f G p,   beta_f = 1/rho_f,
  * with the same grid, staggering, face densities and boundaries as
- * fizzy_proj_solve.  Solved by conjugate gradients preconditioned with the
- * plan's constant-coefficient FFT/tridiagonal solve; stops when
+ * fizzy_proj_solve.  Solved by conjugate gradients preconditioned with
+ * M^-1 = L^-1 D(rho_f G) L^-1, L^-1 the plan's constant-coefficient
+ * FFT/tridiagonal solve (exact for a constant density); stops when
  * max|D(u*)/dt - D(beta_f G p)| / max|D(u*)/dt| <= tol (0 -> 1e-10) or after
  * max_iter iterations (1 .. 100000).
  *   phi        : in, cell centred (densities and dt from the plan).
@@ -151,8 +152,8 @@ int fizzy_proj_solve(fizzy_proj_plan_t p, const double *phi, const double *p_n, 
  *                f_max = max|D(u*)/dt|, div_max, u_rms, div_metric).
  * On an FP64 plan the preconditioner is the FP64 solve; on a mixed plan it is
  * the FP32 solve (applied to r 2^-e, e the exponent of max|b|) with the
- * flexible (Polak-Ribiere) direction update; residuals, the operator and p
- * are FP64 in both.  Allocates 7 fields of workspace on first use (kept
+ * flexible (Polak-Ribiere) direction update; residuals, the operators and p
+ * are FP64 in both.  Allocates 10 fields of workspace on first use (kept
  * with the plan); a mixed plan also uses its FP64 right-hand-side buffer.  Synchronises the stream
  * every 4 iterations to test convergence (not graph-capturable).  Returns
  * FIZZY_ERR_NOT_CONVERGED (outputs written) if tol was not reached. */

@@ -69,8 +69,8 @@ struct fizzy_proj_plan_s {
     double *wtab64 = nullptr, *qtab64 = nullptr;
     float *wtab32 = nullptr, *qtab32 = nullptr;
     // variable-coefficient solve (fizzy_proj_solve_vc), allocated on first use:
-    // face beta x, y, z, r, z, d, A d; partial sums; iteration state
-    double *vc[7] = {};
+    // face beta x, y, z, r, z, d, A d, face rho x, y, z; partial sums; iteration state
+    double *vc[10] = {};
     double *vc_part = nullptr;
     VcState *vc_state = nullptr;
     // ACDI step (fizzy_acdi_step), allocated on first use: psi, the unit

@@ -3,12 +3,15 @@
 // beta_f = 1/rho_f (face mean of rho = rho_g + phi (rho_l - rho_g)).  This is
 // the pressure equation that the constant-coefficient splitting replaces (the
 // paper's Hypre path solves it directly).  Here it is solved by conjugate
-// gradients preconditioned with the constant-coefficient FFT/tridiagonal
-// solve L^-1 of the projection's own passes: A = D beta G and L = D G are
-// both symmetric in the cell-volume (dzf-weighted) inner product and
-// negative semi-definite with the constants as null space, so CG on
-// (-A) x = -b with the preconditioner (-L)^-1 runs with the same formulas as
-// on A x = b:
+// gradients preconditioned with M^-1 = L^-1 D(rho_f G) L^-1, two
+// constant-coefficient FFT/tridiagonal solves L^-1 of the projection's own
+// passes around the density-weighted operator (exact for a constant density,
+// where A = L / rho; with the plain L^-1 instead, the iterations grow with
+// the density ratio: 383 against 41 at ratio 1000 in a 32^3 model).
+// A = D beta G, L = D G and D rho G are symmetric in the cell-volume
+// (dzf-weighted) inner product and negative semi-definite with the constants
+// as null space, so CG on (-A) x = -b with the preconditioner -M^-1 runs with
+// the same formulas as on A x = b:
 //     r = b - A x,  z = L^-1 r,  rho = <r, z>,  d = z + (rho / rho_old) d,
 //     alpha = rho / <d, A d>,  x += alpha d,  r -= alpha A d,
 // stopped when max|r| / max|b| <= tol.  On a mixed plan the preconditioner
@@ -45,7 +48,7 @@ __device__ __forceinline__ double vc_rho(double rho_l, double rho_g, double phi)
     return fmaT(phi, rho_l - rho_g, rho_g);
 }
 
-// Face beta_f = 1/rho_f on the +x, +y, +z faces of every cell (0 on walls),
+// Face beta_f = 1/rho_f and rho_f on the +x, +y, +z faces of every cell (0 on walls),
 // b = D(u*)/dt, r = b, x = d = 0, the preconditioner's input sigma r in the
 // spectral workspace, max|b| and the partial sums of u*^2.
 __global__ void __launch_bounds__(VC_THREADS) k_vc_init(GridDev g, double rho_l, double rho_g, double dt,
@@ -54,7 +57,9 @@ __global__ void __launch_bounds__(VC_THREADS) k_vc_init(GridDev g, double rho_l,
                                                        const double *__restrict__ v,
                                                        const double *__restrict__ w,
                                                        double *__restrict__ bx, double *__restrict__ by,
-                                                       double *__restrict__ bz, double *__restrict__ r,
+                                                       double *__restrict__ bz,
+                                                       double *__restrict__ rx, double *__restrict__ ry,
+                                                       double *__restrict__ rzf, double *__restrict__ r,
                                                        double *__restrict__ x, double *__restrict__ d,
                                                        double *__restrict__ spec,
                                                        double *__restrict__ part, VcState *vs) {
@@ -67,18 +72,27 @@ __global__ void __launch_bounds__(VC_THREADS) k_vc_init(GridDev g, double rho_l,
         const size_t rem = c - (size_t)k * pl;
         const int j = (int)(rem / g.nx), i = (int)(rem - (size_t)j * g.nx);
         const double rc = vc_rho(rho_l, rho_g, phi[c]);
-        double b = 0.0;
-        if (!(g.bcx == BC_NEUMANN && i == g.nx - 1))
-            b = 2.0 / (rc + vc_rho(rho_l, rho_g, phi[i < g.nx - 1 ? c + 1 : c - i]));
+        double b = 0.0, s = 0.0;
+        if (!(g.bcx == BC_NEUMANN && i == g.nx - 1)) {
+            s = rc + vc_rho(rho_l, rho_g, phi[i < g.nx - 1 ? c + 1 : c - i]);
+            b = 2.0 / s;
+        }
         bx[c] = b;
-        b = 0.0;
-        if (!(g.bcy == BC_NEUMANN && j == g.ny - 1))
-            b = 2.0 / (rc + vc_rho(rho_l, rho_g, phi[j < g.ny - 1 ? c + g.nx : c - (size_t)j * g.nx]));
+        rx[c] = 0.5 * s;
+        b = s = 0.0;
+        if (!(g.bcy == BC_NEUMANN && j == g.ny - 1)) {
+            s = rc + vc_rho(rho_l, rho_g, phi[j < g.ny - 1 ? c + g.nx : c - (size_t)j * g.nx]);
+            b = 2.0 / s;
+        }
         by[c] = b;
-        b = 0.0;
-        if (k < g.nz - 1 || g.perz)
-            b = 2.0 / (rc + vc_rho(rho_l, rho_g, phi[k < g.nz - 1 ? c + pl : c - (size_t)k * pl]));
+        ry[c] = 0.5 * s;
+        b = s = 0.0;
+        if (k < g.nz - 1 || g.perz) {
+            s = rc + vc_rho(rho_l, rho_g, phi[k < g.nz - 1 ? c + pl : c - (size_t)k * pl]);
+            b = 2.0 / s;
+        }
         bz[c] = b;
+        rzf[c] = 0.5 * s;
         const double f = div_q<false>(g, i, j, k, cx, cy, mulT(g.izf[k], idt), u, v, w);
         r[c] = f;
         x[c] = 0.0;
@@ -171,13 +185,18 @@ __global__ void __launch_bounds__(VC_THREADS) k_vc_dir(GridDev g, const double *
         d[c] = fmaT(beta, d[c], z[c]);
 }
 
-// q = A d = D(beta_f G d) in flux form (each face flux beta (d_nbr - d_c)/h
-// formed once per face and cell side), partial sums of <d, q>.
+// q = D(c_f G d) in flux form (each face flux c (d_nbr - d_c)/h formed once
+// per face and cell side) for face coefficients c_f: beta_f (the operator A,
+// OUT = VC_OUT_Q: q and the partial sums of <d, q>) or rho_f (the middle of
+// the preconditioner, OUT = VC_OUT_SPEC64 / VC_OUT_SPEC32: q written as the
+// next FFT solve's input, sigma q in FP64 or FP32).
+enum { VC_OUT_Q = 0, VC_OUT_SPEC64 = 1, VC_OUT_SPEC32 = 2 };
+template <int OUT>
 __global__ void __launch_bounds__(VC_THREADS) k_vc_apply(GridDev g, const double *__restrict__ d,
                                                         const double *__restrict__ bx,
                                                         const double *__restrict__ by,
                                                         const double *__restrict__ bz,
-                                                        double *__restrict__ q, double *__restrict__ part,
+                                                        void *__restrict__ q, double *__restrict__ part,
                                                         const DevStats *st) {
     if (*(volatile const int *)&st->converged) return;
     const size_t n = (size_t)g.nx * g.ny * g.nz, pl = (size_t)g.nx * g.ny;
@@ -202,11 +221,19 @@ __global__ void __launch_bounds__(VC_THREADS) k_vc_apply(GridDev g, const double
         const double bb = (k > 0 || g.perz) ? bz[b] : 0.0;
         acc = fmaT(mulT(bt, g.lzc[k]), d[t] - dc, acc);
         acc = fmaT(-mulT(bb, g.lza[k]), dc - d[b], acc);
-        q[c] = acc;
-        s = fmaT(mulT(g.dzf[k], dc), acc, s);
+        if (OUT == VC_OUT_Q) {
+            ((double *)q)[c] = acc;
+            s = fmaT(mulT(g.dzf[k], dc), acc, s);
+        } else if (OUT == VC_OUT_SPEC64) {
+            ((double *)q)[c] = mulT(acc, g.sigma);
+        } else {
+            ((float *)q)[c] = f64_to_f32_shift(acc, 0) * (float)g.sigma;
+        }
     }
-    s = block_sum(s);
-    if (threadIdx.x == 0) part[blockIdx.x] = s;
+    if (OUT == VC_OUT_Q) {
+        s = block_sum(s);
+        if (threadIdx.x == 0) part[blockIdx.x] = s;
+    }
 }
 
 // alpha = rho / <d, A d>; resets the update kernel's max and ticket.
