@@ -78,6 +78,8 @@ MUTATIONS = [
     ("acdi_advect_upwind", "fx[c] = u[c] * 0.5 * (phi[c] + phi[b])", "fx[c] = u[c] * phi[c]"),
     ("acdi_psi_sign", "return eps * log((phi + delta) / (1.0 - phi + delta));",
      "return eps * log((1.0 - phi + delta) / (phi + delta));"),
+    ("acdi_z_wall_ghost", "zhi = 2.0 * zf[nz] - zc(&g, k);", "zhi = zf[nz];"),
+    ("acdi_z_seam_distance", "zlo = zc(&g, nz - 1) - (zf[nz] - zf[0]);", "zlo = zc(&g, nz - 1);"),
     ("z_matrix_wrap_column", "A[(size_t)k * nz + (k + nz - 1) % nz] += lo[k];",
      "A[(size_t)k * nz + (k + nz - 2) % nz] += lo[k];"),
     ("neumann_extension", "return (bc == 0 || e < n) ? e : 2 * n - 1 - e;",
