@@ -48,7 +48,10 @@ __device__ __forceinline__ double vc_rho(double rho_l, double rho_g, double phi)
     return fmaT(phi, rho_l - rho_g, rho_g);
 }
 
-// Face beta_f = 1/rho_f and rho_f on the +x, +y, +z faces of every cell (0 on walls;
+// Face coefficients on the +x, +y, +z faces of every cell, stored pre-scaled
+// for the flux form of the operators: beta_f/dx^2, beta_f/dy^2 and the z
+// conductance beta_f/dzc (the divergence then multiplies by 1/dzf), and the
+// same for rho_f (0 on walls;
 // beta_f = 2/(rho_a + rho_b) by the FP32-seeded Newton reciprocal, relative
 // error about 2^-44: the operator and the correction use the same stored
 // beta_f, so u stays divergence-free to round-off; rho_a + rho_b lies within
@@ -81,22 +84,23 @@ __global__ void __launch_bounds__(VC_THREADS) k_vc_init(GridDev g, double rho_l,
             s = rc + vc_rho(rho_l, rho_g, phi[i < g.nx - 1 ? c + 1 : c - i]);
             b = 2.0 * rcp_pos_nr1(s);
         }
-        bx[c] = b;
-        rx[c] = 0.5 * s;
+        bx[c] = mulT(b, g.idx2);
+        rx[c] = mulT(0.5 * s, g.idx2);
         b = s = 0.0;
         if (!(g.bcy == BC_NEUMANN && j == g.ny - 1)) {
             s = rc + vc_rho(rho_l, rho_g, phi[j < g.ny - 1 ? c + g.nx : c - (size_t)j * g.nx]);
             b = 2.0 * rcp_pos_nr1(s);
         }
-        by[c] = b;
-        ry[c] = 0.5 * s;
+        by[c] = mulT(b, g.idy2);
+        ry[c] = mulT(0.5 * s, g.idy2);
         b = s = 0.0;
         if (k < g.nz - 1 || g.perz) {
             s = rc + vc_rho(rho_l, rho_g, phi[k < g.nz - 1 ? c + pl : c - (size_t)k * pl]);
             b = 2.0 * rcp_pos_nr1(s);
         }
-        bz[c] = b;
-        rzf[c] = 0.5 * s;
+        const double idzc = mulT(g.lzc[k], g.dzf[k]);  // 1/dzc_(k+1/2) (0 on the top wall)
+        bz[c] = mulT(b, idzc);
+        rzf[c] = mulT(0.5 * s, idzc);
         const double f = div_q<false>(g, i, j, k, cx, cy, mulT(g.izf[k], idt), u, v, w);
         r[c] = f;
         x[c] = 0.0;
@@ -210,21 +214,23 @@ __global__ void __launch_bounds__(VC_THREADS) k_vc_apply(GridDev g, const double
         const size_t rem = c - (size_t)k * pl;
         const int j = (int)(rem / g.nx), i = (int)(rem - (size_t)j * g.nx);
         const double dc = d[c];
-        // east / west faces (beta 0 on walls)
+        // sum over the six faces of c_f (d_nbr - d_c), coefficients 0 on walls
         const size_t e = i < g.nx - 1 ? c + 1 : c - i;
         const size_t wst = i > 0 ? c - 1 : c + g.nx - 1;
-        const double bw = (i > 0 || g.bcx == BC_PERIODIC) ? bx[wst] : 0.0;
-        double acc = mulT(fmaT(bx[c], d[e] - dc, -mulT(bw, dc - d[wst])), g.idx2);
+        const double cw = (i > 0 || g.bcx == BC_PERIODIC) ? bx[wst] : 0.0;
+        double acc = mulT(bx[c], d[e] - dc);
+        acc = fmaT(cw, d[wst] - dc, acc);
         const size_t nn = j < g.ny - 1 ? c + g.nx : c - (size_t)j * g.nx;
         const size_t ss = j > 0 ? c - g.nx : c + (size_t)(g.ny - 1) * g.nx;
-        const double bs = (j > 0 || g.bcy == BC_PERIODIC) ? by[ss] : 0.0;
-        acc = fmaT(fmaT(by[c], d[nn] - dc, -mulT(bs, dc - d[ss])), g.idy2, acc);
+        const double cs = (j > 0 || g.bcy == BC_PERIODIC) ? by[ss] : 0.0;
+        acc = fmaT(by[c], d[nn] - dc, acc);
+        acc = fmaT(cs, d[ss] - dc, acc);
         const size_t t = k < g.nz - 1 ? c + pl : c - (size_t)k * pl;
         const size_t b = k > 0 ? c - pl : c + (size_t)(g.nz - 1) * pl;
-        const double bt = bz[c];  // 0 on the top wall
-        const double bb = (k > 0 || g.perz) ? bz[b] : 0.0;
-        acc = fmaT(mulT(bt, g.lzc[k]), d[t] - dc, acc);
-        acc = fmaT(-mulT(bb, g.lza[k]), dc - d[b], acc);
+        const double cb = (k > 0 || g.perz) ? bz[b] : 0.0;
+        double az = mulT(bz[c], d[t] - dc);  // 0 on the top wall
+        az = fmaT(cb, d[b] - dc, az);
+        acc = fmaT(g.izf[k], az, acc);
         if (OUT == VC_OUT_Q) {
             ((double *)q)[c] = acc;
             s = fmaT(mulT(g.dzf[k], dc), acc, s);
@@ -303,8 +309,10 @@ __global__ void __launch_bounds__(VC_THREADS) k_vc_update(GridDev g, double *__r
     }
 }
 
-// u = u* - dt beta_f G x on every non-wall face (in place).
-__global__ void __launch_bounds__(VC_THREADS) k_vc_correct(GridDev g, double dt, const double *__restrict__ x,
+// u = u* - dt beta_f G x on every non-wall face (in place); dtx = dt dx,
+// dty = dt dy.
+__global__ void __launch_bounds__(VC_THREADS) k_vc_correct(GridDev g, double dt, double dtx, double dty,
+                                                          const double *__restrict__ x,
                                                           const double *__restrict__ bx,
                                                           const double *__restrict__ by,
                                                           const double *__restrict__ bz,
@@ -316,13 +324,13 @@ __global__ void __launch_bounds__(VC_THREADS) k_vc_correct(GridDev g, double dt,
         const size_t rem = c - (size_t)k * pl;
         const int j = (int)(rem / g.nx), i = (int)(rem - (size_t)j * g.nx);
         const double xc = x[c];
+        // beta/h = (beta/h^2) h in x and y; the z coefficient is beta/dzc already
         if (!(g.bcx == BC_NEUMANN && i == g.nx - 1))
-            u[c] = fmaT(-mulT(mulT(dt, bx[c]), g.idx1), x[i < g.nx - 1 ? c + 1 : c - i] - xc, u[c]);
+            u[c] = fmaT(-mulT(dtx, bx[c]), x[i < g.nx - 1 ? c + 1 : c - i] - xc, u[c]);
         if (!(g.bcy == BC_NEUMANN && j == g.ny - 1))
-            v[c] = fmaT(-mulT(mulT(dt, by[c]), g.idy1), x[j < g.ny - 1 ? c + g.nx : c - (size_t)j * g.nx] - xc,
-                        v[c]);
+            v[c] = fmaT(-mulT(dty, by[c]), x[j < g.ny - 1 ? c + g.nx : c - (size_t)j * g.nx] - xc, v[c]);
         if (k < g.nz - 1 || g.perz)
-            w[c] = fmaT(-mulT(dt, bz[c]) / g.dzc[k], x[k < g.nz - 1 ? c + pl : c - (size_t)k * pl] - xc, w[c]);
+            w[c] = fmaT(-mulT(dt, bz[c]), x[k < g.nz - 1 ? c + pl : c - (size_t)k * pl] - xc, w[c]);
     }
 }
 
