@@ -24,11 +24,12 @@
  * ---------------------------------------
  *  - Arrays are double, C order [nz][ny][nx] (x fastest), caller-owned.
  *  - Staggering: u[k][j][i] is the x-face i+1/2, v[k][j][i] the y-face j+1/2,
- *    w[k][j][i] the z-face k+1/2.  z is always wall-bounded (homogeneous
- *    Neumann p); x and y are periodic or wall-bounded.  In a wall direction
- *    the last face (i = nx-1, j = ny-1, k = nz-1) is the far wall and must
- *    hold 0 on input; the near wall face is implicit.  Wall faces are 0 on
- *    output.
+ *    w[k][j][i] the z-face k+1/2.  x and y are periodic or wall-bounded
+ *    (bc_x, bc_y); z is wall-bounded (homogeneous Neumann p) unless the
+ *    descriptor sets periodic_z, in which case w[nz-1] is the seam face
+ *    joining plane nz-1 to plane 0.  In a wall direction the last face
+ *    (i = nx-1, j = ny-1, k = nz-1) is the far wall and must hold 0 on
+ *    input; the near wall face is implicit.  Wall faces are 0 on output.
  *  - "stream" is a cudaStream_t passed as void* (NULL = legacy default
  *    stream).  Device work is asynchronous on it unless stated otherwise.
  *  - Return codes: FIZZY_OK (0) or a negative FIZZY_ERR_* value; no entry
@@ -165,11 +166,13 @@ int fizzy_proj_solve_vc(fizzy_proj_plan_t p, const double *phi, double *u, doubl
  * projection, on the plan's grid and boundaries:
  *     d phi/dt = rhs = -div(u phi) + div{ gamma [ eps grad phi
  *                        - 1/4 (1 - tanh^2(psi/(2 eps))) grad psi/|grad psi| ] },
- *     psi = eps ln((phi + 1e-100)/(1 - phi + 1e-100)),
+ *     psi = eps ln(max(phi + 1e-100, 1e-100)/max(1 - phi + 1e-100, 1e-100)),
  * in conservative face-flux form: psi and its unit gradient at the centres
  * (central differences, a wall mirrors psi, a zero gradient gives 0), face
  * values as the mean of the two cells, wall faces carry no flux (mass is
- * conserved to round-off).
+ * conserved to round-off).  The bounds inside the logarithm keep psi finite
+ * (saturated near +-230 eps) where phi has left [0, 1] by an undershoot or
+ * overshoot; for phi in [0, 1] they change nothing.
  *   phi          : in, cell centred.
  *   u, v, w      : in, face velocities (the projection's layout; wall faces 0).
  *   eps, gamma   : interface thickness (> 0) and velocity scale (>= 0).

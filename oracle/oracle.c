@@ -828,7 +828,8 @@ int ora_project_vc(int nx, int ny, int nz, double dx, double dy, const double *z
  * diffuse-interface (ACDI) model of Jain (2022):
  *   d phi/dt + div(u phi) = div{ Gamma [ eps grad phi
  *                                        - 1/4 (1 - tanh^2(psi/(2 eps))) n ] },
- *   psi = eps ln((phi + delta)/(1 - phi + delta)),   n = grad psi / |grad psi|.
+ *   psi = eps ln((phi + delta)/(1 - phi + delta)),   n = grad psi / |grad psi|
+ *   (each side of the quotient bounded below by delta, see acdi_psi).
  * Discretised in conservative (face-flux) form on the staggered grid:
  *   psi and n at cell centres (n from central differences of psi, a wall
  *   mirrors psi, |grad psi| = 0 gives n = 0);
@@ -840,8 +841,16 @@ int ora_project_vc(int nx, int ny, int nz, double dx, double dy, const double *z
  *   rhs = -D F;  one forward-Euler stage phi + dt rhs (stages of any explicit
  *   scheme are made of these). */
 
+/* Jain's psi is defined for phi inside (0, 1).  A discrete phi can leave
+ * [0, 1] by a small undershoot or overshoot (central advection does when the
+ * velocity scale Gamma is below max|u|), and the plain quotient would then be
+ * negative and its logarithm NaN.  Reading taken here: each side of the
+ * quotient is bounded below by delta, so psi saturates (near -230 eps below
+ * phi = 0, +230 eps above phi = 1) and stays finite; inside [0, 1] nothing
+ * changes. */
 static double acdi_psi(double phi, double eps, double delta) {
-    return eps * log((phi + delta) / (1.0 - phi + delta));
+    const double a = phi + delta, b = 1.0 - phi + delta;
+    return eps * log((a > delta ? a : delta) / (b > delta ? b : delta));
 }
 
 /* rhs = -D F for the ACDI face fluxes F (see above). */

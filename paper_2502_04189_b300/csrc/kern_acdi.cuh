@@ -5,8 +5,11 @@
 //                                        - 1/4 (1 - tanh^2(psi/(2 eps))) n ] },
 //   psi = eps ln((phi + delta)/(1 - phi + delta)),   n = grad psi / |grad psi|,
 // in conservative face-flux form on the staggered grid (FP64):
-//   k_acdi_psi    : r = (phi + delta)/(1 - phi + delta), psi = eps ln r and
-//                   q = sqrt(r) at the centres (one log per cell);
+//   k_acdi_psi    : r = max(phi + delta, delta)/max(1 - phi + delta, delta),
+//                   psi = eps ln r and q = sqrt(r) at the centres (one log
+//                   per cell; the bounds keep r > 0 for any phi, so a phi
+//                   slightly outside [0, 1] saturates psi near +-230 eps
+//                   instead of giving NaN; inside [0, 1] r is unchanged);
 //   k_acdi_normal : n at the centres from central differences of psi (a wall
 //                   mirrors psi; the centre distances are the sums of the two
 //                   half spacings, so stretched and periodic z need nothing
@@ -43,7 +46,10 @@ __global__ void __launch_bounds__(256) k_acdi_psi(GridDev g, double eps, const d
     const size_t n = (size_t)g.nx * g.ny * g.nz;
     for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (size_t)gridDim.x * blockDim.x) {
         const double f = phi[c];
-        const double r = (f + ACDI_DELTA) / (1.0 - f + ACDI_DELTA);
+        // both sides bounded below by delta: a phi that advection has pushed
+        // slightly outside [0, 1] still gives a finite psi (saturated at
+        // about +-230 eps) instead of the logarithm of a negative number
+        const double r = fmax(f + ACDI_DELTA, ACDI_DELTA) / fmax(1.0 - f + ACDI_DELTA, ACDI_DELTA);
         rr[c] = sqrt(r);
         psi[c] = eps * log(r);
     }

@@ -1,7 +1,7 @@
 // Register-resident FP32 transforms of length 128, 256 and 512 (mixed mode).
 //
-// The FP32 transform passes of the mixed-precision solve (Sec. 3.2: real
-// FFTs, or DCT-II for wall directions, along x and y).  A DFT of length
+// The FP32 transform passes of the mixed-precision solve (the fast direct
+// solver's real FFTs, or DCT-II for wall directions, along x and y).  A DFT of length
 // N = 16 M (M = 8, 16; 4 builds too) is split 16 x M, the four-step form of
 // the Cooley-Tukey factorisation: with n = M n1 + n2 and k = k1 + 16 k2,
 //     X[k1 + 16 k2] = sum_n2 WM^(n2 k2) [ WN^(n2 k1) sum_n1 x[M n1 + n2] W16^(n1 k1) ],

@@ -1,10 +1,13 @@
 """ACDI phase-field step on the GPU (fizzy_acdi_step) against the FP64 CPU
 oracle (needs a B300).
 
-Element by element, rhs within 1e-11 of max|rhs| (the logarithm and tanh
-of the two sides round differently in the last place; the sharpening term
-is a smooth function of them), phi + dt rhs likewise; mass conserved to
-round-off on the GPU too.
+Element by element, rhs within 1e-12 of max|rhs|, phi + dt rhs likewise;
+mass conserved to round-off on the GPU too.  The two sides form the
+sharpening coefficient differently (the oracle's tanh, the kernels'
+4S/(1+S)^2 with rsqrt normals); an FP64 numpy restatement measures the
+spread of those two forms at under 8e-16 of max|rhs| on these recipes
+(tests/test_oracle_pins.py, test_acdi_form_floor_is_measured), so 1e-12
+leaves three orders of magnitude for the kernels' own rounding.
 """
 import numpy as np
 import pytest
@@ -18,7 +21,7 @@ from gpu_util import relerr, to_dev
 pytestmark = pytest.mark.gpu
 
 P = I.PERIODIC
-TOL = 1e-11
+TOL = 1e-12
 
 
 def cases():
@@ -87,3 +90,21 @@ def test_acdi_rejects_bad_arguments(cuda_ok):
     with pytest.raises(F.FizzyError):  # no output requested
         plan.acdi_step(phi, u, u, u, 1.0, 1.0, 0.1)
     plan.close()
+
+
+def test_acdi_phi_outside_unit_interval(cuda_ok):
+    """phi pushed slightly outside [0, 1] (and a few points far outside):
+    the bounded logarithm keeps every output finite, and the GPU still
+    matches the oracle element by element."""
+    c = I.make_case(CASES["a48x36x20_wx_stretch"])
+    g = O.Grid.of_case(c)
+    rng = np.random.default_rng(11)
+    phi = c.phi + rng.uniform(-2e-3, 2e-3, g.shape)
+    flat = phi.reshape(-1)
+    flat[rng.choice(flat.size, 6, replace=False)] = [-0.4, -1e-12, 1.0 + 1e-12, 1.5, -3.0, 4.0]
+    c.phi = phi
+    eps, gam, dt = c.dx, 0.7, 1e-3
+    ref = O.acdi_rhs(g, eps, gam, phi, c.u, c.v, c.w)
+    rhs, out, _ = gpu_acdi(c, eps, gam, dt)
+    assert np.all(np.isfinite(rhs)) and np.all(np.isfinite(out))
+    assert relerr(rhs, ref) <= TOL

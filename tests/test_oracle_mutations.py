@@ -76,8 +76,10 @@ MUTATIONS = [
      "double t = tanh((psi[c] + psi[b]) / (2.0 * eps));"),
     ("acdi_normal_one_sided", "0.5 * (nxv[c] + nxv[b])", "nxv[c]"),
     ("acdi_advect_upwind", "fx[c] = u[c] * 0.5 * (phi[c] + phi[b])", "fx[c] = u[c] * phi[c]"),
-    ("acdi_psi_sign", "return eps * log((phi + delta) / (1.0 - phi + delta));",
-     "return eps * log((1.0 - phi + delta) / (phi + delta));"),
+    ("acdi_psi_sign", "return eps * log((a > delta ? a : delta) / (b > delta ? b : delta));",
+     "return eps * log((b > delta ? b : delta) / (a > delta ? a : delta));"),
+    ("acdi_psi_unbounded", "return eps * log((a > delta ? a : delta) / (b > delta ? b : delta));",
+     "return eps * log(a / b);"),
     ("acdi_z_wall_ghost", "zhi = 2.0 * zf[nz] - zc(&g, k);", "zhi = zf[nz];"),
     ("acdi_z_seam_distance", "zlo = zc(&g, nz - 1) - (zf[nz] - zf[0]);", "zlo = zc(&g, nz - 1);"),
     ("z_matrix_wrap_column", "A[(size_t)k * nz + (k + nz - 1) % nz] += lo[k];",

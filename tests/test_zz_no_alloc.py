@@ -64,3 +64,42 @@ def test_noalloc_matches_plan_solve_twice_in_a_row(cuda_ok):
         torch.cuda.synchronize()
         for a, b in ((p2, p1), (u2, u1), (v2, v1), (w2, w1)):
             assert relerr(a.cpu().numpy(), b.cpu().numpy()) <= TOL64
+
+
+@pytest.mark.gpu
+def test_noalloc_at_capacity_matches_oracle(cuda_ok):
+    """Grids at the scratch limit (nx * ny * nz = FIZZY_NOALLOC_MAX_CELLS) with
+    a 512-length x direction, where the generic transform path stands in for
+    the plan's length-specialised one: periodic x, then walls in x (the
+    DCT-II path), two calls in a row.  Each call is compared element by
+    element with the FP64 oracle (p with its gauge removed, u, v, w) and with
+    the plan-based solve."""
+    import torch
+    import oracle as O
+    from gpu_util import compare
+
+    assert 512 * 32 * 16 == _abi.NOALLOC_MAX_CELLS
+
+    def dev(a):
+        return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+    for bcx, bcy, cfg in ((I.PERIODIC, I.NEUMANN, 33), (I.NEUMANN, I.PERIODIC, 34)):
+        spec = I.CaseSpec(nx=512, ny=32, nz=16, bcx=bcx, bcy=bcy, lx=1.0, ly=32 / 512,
+                          lz=16 / 512, beta=1.2, n_bubbles=3, radius_cells=4, config=cfg)
+        case = I.make_case(spec)
+        ref = O.project_case(case)
+        u, v, w = dev(case.u), dev(case.v), dev(case.w)
+        p = torch.empty_like(u)
+        F.solve_noalloc(dev(case.phi), dev(case.pn), dev(case.pnm1), u, v, w, p, **desc_of(case))
+        torch.cuda.synchronize()
+        got = dict(p=p.cpu().numpy(), u=u.cpu().numpy(), v=v.cpu().numpy(), w=w.cpu().numpy())
+        ep, eu = compare(case, got, ref)
+        assert ep <= TOL64 and eu <= TOL64, (bcx, ep, eu)
+        plan = F.Plan.for_case(case, precision=F.FP64)
+        u1, v1, w1 = dev(case.u), dev(case.v), dev(case.w)
+        p1 = torch.empty_like(u1)
+        plan.solve(dev(case.phi), dev(case.pn), dev(case.pnm1), u1, v1, w1, p1)
+        torch.cuda.synchronize()
+        plan.close()
+        for a, b in ((p, p1), (u, u1), (v, v1), (w, w1)):
+            assert relerr(a.cpu().numpy(), b.cpu().numpy()) <= TOL64
