@@ -2,13 +2,23 @@
 """Benchmark of the variable-density pressure-correction projection on B300.
 
 Metric: grid points per second of one projection (right-hand side, FFT/DCT +
-z-tridiagonal Poisson solve, variable-density correction) on the 256^3
-bubble-laden workload: periodic x/y, walls in z, uniform grid, 40 drops of
-radius 8 cells, density ratio 1000, k^-5/3 solenoidal u* (rms 1) plus 1 %
-noise, two 8-mode pressure fields, dt = 1e-4; FP64 mode (the mixed
-FP32/FP64-refinement mode is reported beside it).
+z-tridiagonal Poisson solve, variable-density correction), mixed FP32/FP64
+refinement against the plain FP64 form on the same inputs, both refined or
+solved to a relative residual of 1e-10.  Default workload: 512^3 cells,
+periodic x/y, walls in z with tanh-stretched spacing (beta = 1.5), 400 drops
+of radius 6 cells, density ratio 1000, k^-5/3 solenoidal u* (rms 1) plus 1 %
+noise, two 8-mode pressure fields, dt = 1e-4.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl fizzy|reference]
+                  [--workload NAME] [--precision mixed|fp64]
+
+Every timed solve starts from the workload's u* (restored from a pristine
+device copy before each solve, outside the solve's CUDA events).  The line
+states the error of both results against the FP64 CPU oracle on the same
+inputs, the roofline of the dominant kernel against peaks measured in the
+same run, the oracle's own throughput on the host cores, an end-to-end
+number through the host-buffer entry point, and short runs of the 64-instance
+uneven batch and of the serving loop.
 
 One JSON line is printed by rank 0.  Under torchrun every rank runs an
 independent replica on its own GPU (the projection does not shard in this
@@ -34,14 +44,15 @@ from paper_2502_04189_b300 import inputs as I  # noqa: E402
 
 METRIC = "grid pts/s per projection, mixed vs FP64 at 1e-10 residual; HBM %; p50/p99 ms"
 HBM_PEAK_FALLBACK = 6400.0        # GB/s, recipe fallback
-FP64_PEAK_NOMINAL = 1.25          # TFLOP/s, nominal B300 FP64 (recipe table)
+FP64_PEAK_NOMINAL = 1.25          # TFLOP/s, nominal B300 FP64 (recipe table), context only
 
 WORKLOADS = {
+    "bubbles512_stretched": I.bubbles512_stretched_spec,
     "bubbles256": I.bubbles256_spec,
     "drop32": I.drop32_spec,
-    "bubbles512_stretched": I.bubbles512_stretched_spec,
     "emulsion256": I.emulsion256_spec,
 }
+DEFAULT_WORKLOAD = "bubbles512_stretched"
 
 
 def measured_peaks():
@@ -49,23 +60,26 @@ def measured_peaks():
     try:
         with open(path) as fh:
             d = json.load(fh)
-        return float(d["hbm_gbs"]), "measured"
+        return float(d["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs)"
     except Exception:
         return HBM_PEAK_FALLBACK, "fallback"
 
 
-def measured_traffic(kernel, mixed):
-    """DRAM bytes per launch of a kernel from the committed ncu summaries
-    (lines 'traffic_per_launch_bytes <kernel> <bytes>' in profiles/*.md)."""
+def measured_traffic(workload, precision, kernel):
+    """DRAM bytes per grid point of one launch of a kernel, from the committed
+    ncu summaries: lines 'traffic_per_point <workload> <precision> <kernel>
+    <bytes per point> <captured grid>' in profiles/*.md.  Returns (bytes per
+    point, source) or (None, None)."""
     import glob
-    name = {"flux": "k_flux", "resid": "k_resid", "resid_correct": "k_resid_corr",
-            "div_fwdx": "k_xfwd_mix" if mixed else "k_xfwd_f64"}.get(kernel, kernel)
     for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
         for line in open(path):
             parts = line.split()
-            if len(parts) == 3 and parts[0] == "traffic_per_launch_bytes" and parts[1] == name:
-                return int(parts[2])
-    return None
+            if (len(parts) >= 5 and parts[0] == "traffic_per_point" and parts[1] == workload
+                    and parts[2] == precision and parts[3] == kernel):
+                src = "%s (ncu capture%s)" % (os.path.basename(path),
+                                              ", " + parts[5] if len(parts) > 5 else "")
+                return float(parts[4]), src
+    return None, None
 
 
 def algorithmic_per_point(nx, ny, mixed):
@@ -104,13 +118,27 @@ def fft_fp64_instr_per_point(n, dct):
     return per_complex / 2 + 1 + (2 if dct else 0)
 
 
-def path_roofline(value, nx, ny, bcx, bcy, mixed, sweeps, hbm_peak, bcz=1):
+def fp64_instr_per_point(nx, ny, bcx, bcy, mixed, bcz=1):
+    """FP64 instructions per grid point of each kernel, counted from the code
+    (flux 6 per face + phat; divergence 6; z-solve 3, or 5 with periodic z
+    (the Sherman-Morrison dot product and correction); correction 6; mixed
+    residual 10, fused with the correction 13)."""
+    fx = fft_fp64_instr_per_point(nx, bcx == 1)
+    fy = fft_fp64_instr_per_point(ny, bcy == 1)
+    if not mixed:
+        return {"flux": 19, "div_fwdx": 6 + fx, "fwd_y": fy, "thomas": 5 if bcz == 0 else 3, "inv_y": fy,
+                "inv_x": fx, "correct": 6}
+    return {"flux": 19, "div_fwdx": 6, "resid": 10, "resid_correct": 13, "inv_x_update": 1,
+            "correct": 6}
+
+
+def path_roofline(value, nx, ny, bcx, bcy, mixed, sweeps, hbm_peak, fp64_issue_peak, bcz=1):
     """The whole projection against its bounds: the algorithmic bytes of the
     pass sequence (the kernels' per-point bytes summed over the passes that
     ran; mixed: the refinement passes once per sweep, the stand-alone
     correction only when no sweep ran), the I/O floor (6 FP64 fields read,
     4 written: 80 B/pt), and the FP64 instructions per point against the
-    nominal 0.625 T FP64 instructions/s."""
+    FP64 FMA issue rate measured in the same run."""
     per = algorithmic_per_point(nx, ny, mixed)
     ins = fp64_instr_per_point(nx, ny, bcx, bcy, mixed, bcz)
     if not mixed:
@@ -126,25 +154,11 @@ def path_roofline(value, nx, ny, bcx, bcy, mixed, sweeps, hbm_peak, bcz=1):
         if sweeps == 0:
             b += per["correct"][0]
             n_ins += ins["correct"]
-    issue_peak = FP64_PEAK_NOMINAL / 2 * 1e12
     return {"bytes_per_pt": b, "io_floor_bytes_per_pt": 80, "hbm_gbs": value * b / 1e9,
             "hbm_frac": value * b / 1e9 / hbm_peak, "io_floor_frac": value * 80 / 1e9 / hbm_peak,
-            "fp64_instr_per_pt": n_ins, "fp64_issue_bound_pts_s": issue_peak / n_ins,
-            "fp64_issue_frac": value * n_ins / issue_peak, "sweeps": sweeps}
-
-
-def fp64_instr_per_point(nx, ny, bcx, bcy, mixed, bcz=1):
-    """FP64 instructions per grid point of each kernel, counted from the code
-    (flux 6 per face + phat; divergence 6; z-solve 3, or 5 with periodic z
-    (the Sherman-Morrison dot product and correction); correction 6; mixed
-    residual 10, fused with the correction 13)."""
-    fx = fft_fp64_instr_per_point(nx, bcx == 1)
-    fy = fft_fp64_instr_per_point(ny, bcy == 1)
-    if not mixed:
-        return {"flux": 19, "div_fwdx": 6 + fx, "fwd_y": fy, "thomas": 5 if bcz == 0 else 3, "inv_y": fy,
-                "inv_x": fx, "correct": 6}
-    return {"flux": 19, "div_fwdx": 6, "resid": 10, "resid_correct": 13, "inv_x_update": 1,
-            "correct": 6}
+            "fp64_instr_per_pt": n_ins, "fp64_issue_peak_instr_s": fp64_issue_peak,
+            "fp64_issue_bound_pts_s": fp64_issue_peak / n_ins,
+            "fp64_issue_frac": value * n_ins / fp64_issue_peak, "sweeps": sweeps}
 
 
 class ClockSampler:
@@ -232,28 +246,66 @@ def job_throughput(points_per_rank_step, steps, world, seconds):
 
 
 def slab_spec(spec, nz=32):
-    """A bounded sample of a workload for the CPU oracle: the same recipe on a
-    slab of nz planes (same x/y transform lengths and spacing, z length and
-    drop count scaled)."""
+    """A bounded sample of a workload: the same recipe on a slab of nz planes
+    (same x/y transform lengths and spacing, z length and drop count scaled;
+    a stretched z keeps its tanh law over the slab)."""
     k = min(spec.nz, nz)
     return I.CaseSpec(**{**spec.__dict__, "nz": k, "lz": spec.lz * k / spec.nz,
                          "n_bubbles": max(1, spec.n_bubbles * k // spec.nz)})
 
 
 def oracle_time(case, reps=1):
-    """Wall time of the CPU oracle's projection on case (rank 0 host cores)."""
+    """Wall time of the CPU oracle's projection on case (rank 0 host cores);
+    returns (best seconds, threads, the last result)."""
     import oracle as O
-    best = []
+    best, res = [], None
     for _ in range(reps):
         t0 = time.perf_counter()
-        O.project_case(case)
+        res = O.project_case(case)
         best.append(time.perf_counter() - t0)
-    return min(best), O.num_threads()
+    return min(best), O.num_threads(), res
+
+
+def errors_vs_oracle(case, got, ref):
+    """spec error definitions: max|x - x_oracle| / max|x_oracle| for p
+    (the dzf-weighted mean removed on both sides) and for u, v, w together
+    (one shared max); plus the divergence metric max|D u| dx / U of the
+    result, U the rms of u* over all faces, evaluated by the oracle's D."""
+    import oracle as O
+    g = O.Grid.of_case(case)
+    pg = got["p"] - O.weighted_mean(g, got["p"])
+    pr = ref["p"] - O.weighted_mean(g, ref["p"])
+    ep = float(np.max(np.abs(pg - pr)) / np.max(np.abs(pr)))
+    num = max(float(np.max(np.abs(got[k] - ref[k]))) for k in "uvw")
+    den = max(float(np.max(np.abs(ref[k]))) for k in "uvw")
+    U = math.sqrt(sum(float(np.sum(getattr(case, k) ** 2)) for k in "uvw") / (3 * case.npts))
+    dmax = float(np.max(np.abs(O.div(g, got["u"], got["v"], got["w"]))))
+    return {"p": ep, "u": num / den, "div_metric": dmax * case.dx / U}
+
+
+def probe_peaks(F, stream, target_ms=150.0):
+    """In-run FMA issue-rate probes (fizzy_probe_fma_rate): DFMA and FFMA
+    chains (8 independent chains per thread, a resident grid), each launch
+    calibrated to about target_ms, best of three, with the SM clock sampled
+    during the probes."""
+    out = {}
+    clocks = ClockSampler()
+    clocks.start()
+    for prec, name, it0 in ((F.FP64, "dfma", 2000), (F.MIXED, "ffma", 100000)):
+        _, ms = F.probe_fma_rate(prec, it0, stream=stream)
+        it = max(1, int(it0 * target_ms / max(ms, 1e-3)))
+        runs = [F.probe_fma_rate(prec, it, stream=stream) for _ in range(3)]
+        rate, ms = max(runs)
+        out[name] = {"instr_per_s": rate, "ms": ms, "iters": it, "chains_per_thread": 8}
+    clk = clocks.stop()
+    out["clocks"] = clk
+    return out
 
 
 def run_reference(args):
-    """The oracle on the host cores: each step = one projection of a 256 x 256 x 32
-    slab drawn with the same recipe (same x/y transform lengths and spacing)."""
+    """The oracle on the host cores: each step = one projection of a 32-plane
+    slab drawn with the workload's recipe (same x/y transform lengths and
+    spacing)."""
     world, rank, _ = dist_env()
     if rank != 0:
         return 0
@@ -275,12 +327,185 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": args.workload, "grid": [spec.nx, spec.ny, spec.nz],
-                                             "precision": "fp64", "l2": "inputs larger than L2"},
+                                             "precision": args.precision,
+                                             "l2": "inputs larger than L2"},
             "cpu_baseline": {"value": value, "unit": "pts/s", "cores": O.num_threads(),
                              "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "pts/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
+
+
+def dominant_roofline(dom, live, st, steps, mixed, max_refine, spec, npts, hbm_peak, hbm_src,
+                      dfma, workload):
+    """Roofline object of the dominant kernel from its live CUDA-event time in
+    the timed region.  FP64-bound kernels report "alu": algorithmic FP64 flops
+    (FMA = 2) per launch over the launch time, against twice the DFMA issue
+    rate measured in the same run; the FP64 instruction rate against that
+    issue rate and the HBM rate against the measured copy bandwidth sit
+    beside it."""
+    tot_ms, cnt = live
+    # refinement kernels return at once after convergence: count only the
+    # launches that did the pass (from the solve's sweep count)
+    it = st["iterations"]
+    per_solve = {"fwd_x_refine": it, "fwd_y_refine": it, "thomas_refine": it,
+                 "inv_y_refine": it, "inv_x_update": it, "resid_correct": it}.get(dom)
+    if mixed and dom == "correct":  # runs only when no fused pass ran
+        per_solve = 1 if it == 0 else 0
+    if per_solve is not None:
+        cnt = max(1, per_solve * steps)
+    avg_s = tot_ms / cnt / 1e3
+    per_pt = algorithmic_per_point(spec.nx, spec.ny, mixed)
+    b_pt, fl_pt = per_pt.get(dom, (0, 0))
+    ipt = fp64_instr_per_point(spec.nx, spec.ny, spec.bcx, spec.bcy, mixed, spec.bcz).get(dom, 0)
+    gbs = b_pt * npts / avg_s / 1e9
+    tpt, tsrc = measured_traffic(workload, "mixed" if mixed else "fp64", dom)
+    traffic = tpt * npts if tpt is not None else None
+    issue = ipt * npts / avg_s
+    if ipt and ipt / dfma > b_pt / (hbm_peak * 1e9):
+        peak = 2.0 * dfma / 1e12
+        tfl = fl_pt * npts / avg_s / 1e12
+        roof = {"bound": "alu", "achieved": tfl, "peak": peak, "unit": "TFLOP/s", "frac": tfl / peak,
+                "peak_source": "measured in this run: 2 x DFMA issue rate (fizzy_probe_fma_rate)",
+                "nominal_peak": FP64_PEAK_NOMINAL}
+    else:
+        roof = {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
+                "frac": gbs / hbm_peak, "peak_source": hbm_src}
+    roof.update({"traffic": traffic, "traffic_source": tsrc, "kernel": dom,
+                 "algorithmic_bytes": b_pt * npts, "algorithmic_fp64_flops": fl_pt * npts,
+                 "hbm_gbs": gbs, "hbm_frac": gbs / hbm_peak, "hbm_peak_source": hbm_src,
+                 "launches_timed": cnt, "duration_ms": tot_ms / cnt})
+    if ipt:
+        roof["fp64_issue"] = {"instr_per_pt": ipt, "achieved": issue / 1e12, "peak": dfma / 1e12,
+                              "unit": "T instr/s", "frac": issue / dfma,
+                              "peak_source": "DFMA issue rate measured in this run"}
+    return roof
+
+
+def run_batch_forms(args, F, torch, steps, warmup, reps=3):
+    """The 64-instance uneven batch: the mixed batched form (one persistent
+    launch replayed from a CUDA graph, autotuned), the FP64 batched form and
+    the plain FP64 form (one fizzy_proj_solve per instance).  Each instance's
+    outputs are checked against its own plain FP64 solve (max relative p error
+    with the gauge removed, and u error)."""
+    specs = I.batch_specs(64)
+    cases = [I.make_case(s) for s in specs]
+    npts = sum(c.npts for c in cases)
+
+    def dev(a):
+        return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+    inputs = [(dev(c.phi), dev(c.pn), dev(c.pnm1)) for c in cases]
+    ustar = [(dev(c.u), dev(c.v), dev(c.w)) for c in cases]
+    work = [tuple(torch.empty_like(t) for t in us) for us in ustar]
+    outs = [torch.empty(c.shape, dtype=torch.float64, device="cuda") for c in cases]
+    stream = torch.cuda.current_stream()
+
+    def restore():
+        for wk, us in zip(work, ustar):
+            for a, b in zip(wk, us):
+                a.copy_(b)
+
+    def results():
+        return [(o.clone(), *[t.clone() for t in wk]) for o, wk in zip(outs, work)]
+
+    forms = {}
+    finals = {}
+    for prec, name in ((F.MIXED, "mixed_batched"), (F.FP64, "fp64_batched")):
+        plans = [F.Plan.for_case(c, precision=prec) for c in cases]
+        arrays = [inp + wk + (o,) for inp, wk, o in zip(inputs, work, outs)]
+        batch = F.Batch(plans, arrays)
+        restore()
+        tuning, tuned_ms = batch.autotune(reps=reps)
+        for _ in range(warmup):
+            restore()
+            batch.solve()
+        torch.cuda.synchronize()
+        tot = 0.0
+        for _ in range(steps):
+            restore()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            batch.solve()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            tot += e0.elapsed_time(e1)
+        ms = tot / steps
+        status = batch.status()
+        st = [p.stats() for p in plans]
+        finals[name] = results()
+        forms[name] = {"value": npts / (ms / 1e3), "ms_per_batch": ms, "tuning": tuning,
+                       "status": status, "items": batch.info()["items"],
+                       "max_relres": max(x["relres"] for x in st),
+                       "sweeps_max": max(x["iterations"] for x in st) if prec == F.MIXED else 0,
+                       "all_converged": all(x["converged"] for x in st)}
+        batch.close()
+        for p in plans:
+            p.close()
+    # plain FP64 form: one stand-alone solve per instance
+    plans = [F.Plan.for_case(c, precision=F.FP64) for c in cases]
+
+    def plain():
+        for pl, inp, wk, o in zip(plans, inputs, work, outs):
+            pl.solve(*inp, *wk, o)
+    for _ in range(warmup):
+        restore()
+        plain()
+    torch.cuda.synchronize()
+    tot = 0.0
+    for _ in range(steps):
+        restore()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        plain()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        tot += e0.elapsed_time(e1)
+    ms = tot / steps
+    ref = results()
+    forms["fp64_plain_loop"] = {"value": npts / (ms / 1e3), "ms_per_batch": ms}
+    for p in plans:
+        p.close()
+    # accuracy of the batched forms against the plain FP64 solves
+    for name in ("mixed_batched", "fp64_batched"):
+        ep = eu = 0.0
+        for (pb, ub, vb, wb), (pr, ur, vr, wr) in zip(finals[name], ref):
+            pb = pb - pb.mean()
+            pr = pr - pr.mean()  # uniform cells here: the plain mean is the gauge difference
+            ep = max(ep, float((pb - pr).abs().max() / pr.abs().max()))
+            m = max(float(t.abs().max()) for t in (ur, vr, wr))
+            eu = max(eu, max(float((a - b).abs().max()) for a, b in ((ub, ur), (vb, vr), (wb, wr))) / m)
+        forms[name]["err_vs_plain_fp64"] = {"p": ep, "u": eu}
+    return {"instances": len(cases), "points": npts, "forms": forms,
+            "mixed_over_plain_fp64": forms["mixed_batched"]["value"] / forms["fp64_plain_loop"]["value"]}
+
+
+def run_serve_loop(args, F, torch, n_requests, slots):
+    """Serving: Poisson arrivals (seeded, mean 2000 req/s) of requests with
+    nx, ny in {64,...,384}, nz in [64, 384], 30 % tanh-stretched z, periodic
+    or wall x/y, density ratio 10-1000, mixed precision refined to 1e-10;
+    admission by a 120 GB HBM budget with plans cached on the device, 100 ms
+    admission deadline.  Inputs are periodic crops of a device-resident
+    256^3 bubble template."""
+    import paper_2502_04189_b300.serve as S
+    arrivals, specs = I.serve_specs(n_requests)
+    tmpl = I.make_case(I.bubbles256_spec())
+    fields = S.TemplateFields(tmpl)
+    reqs = S.requests_from_specs(arrivals, specs, F.MIXED)
+    server = F.Server(120 * (1 << 30), slots=slots)
+
+    def fill(r, views, stream):
+        fields.fill(views, r.desc, r.offset, stream)
+
+    # warm-up on a few requests (plan-building code paths, pool growth)
+    S.run(server, [S.Request(i, 0.0, r.desc, r.offset) for i, r in enumerate(reqs[:4])], fill,
+          deadline=60.0)
+    torch.cuda.synchronize()
+    out, summ = S.run(server, reqs, fill, deadline=0.1)
+    info = server.info()
+    server.close()
+    del fields
+    return summ, info
 
 
 def run_fizzy(args):
@@ -293,111 +518,97 @@ def run_fizzy(args):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     spec = WORKLOADS[args.workload]()
+    if args.nz:
+        spec = slab_spec(spec, args.nz)
     case = I.make_case(spec)
     npts = case.npts
     prec = F.MIXED if args.precision == "mixed" else F.FP64
+    other = F.FP64 if prec == F.MIXED else F.MIXED
+    mixed = prec == F.MIXED
 
     def dev(a):
         return torch.from_numpy(np.ascontiguousarray(a)).cuda()
 
     phi, pn, pnm1 = dev(case.phi), dev(case.pn), dev(case.pnm1)
-    u, v, w = dev(case.u), dev(case.v), dev(case.w)
+    u0, v0, w0 = dev(case.u), dev(case.v), dev(case.w)  # the workload's u*, kept pristine
+    u, v, w = torch.empty_like(u0), torch.empty_like(v0), torch.empty_like(w0)
     p = torch.empty_like(phi)
     stream = torch.cuda.current_stream()
+
+    def restore():
+        u.copy_(u0)
+        v.copy_(v0)
+        w.copy_(w0)
+
+    # peaks of this GPU, measured before the timed region
+    peaks = probe_peaks(F, stream) if not args.no_probe else None
+    dfma = peaks["dfma"]["instr_per_s"] if peaks else FP64_PEAK_NOMINAL / 2 * 1e12
 
     def timed_run(precision, steps, warmup, per_kernel):
         """W warm-up solves; with per_kernel, a short breakdown run with every
         kernel bracketed by events picks the dominant kernel; then the timed
-        region of `steps` solves, in which only the dominant kernel's launches
+        region of `steps` solves, each from the restored u* and bracketed by
+        its own CUDA events, in which only the dominant kernel's launches also
         carry events (its live average duration feeds the roofline)."""
         plan = F.Plan.for_case(case, precision=precision)
         for _ in range(warmup):
+            restore()
             plan.solve(phi, pn, pnm1, u, v, w, p, stream=stream)
         torch.cuda.synchronize()
         breakdown, dom = {}, None
         if per_kernel:
             plan.set_timing(True)
-            for _ in range(max(3, steps // 5)):
+            for _ in range(3):
+                restore()
                 plan.solve(phi, pn, pnm1, u, v, w, p, stream=stream)
             breakdown = plan.timing()
             dom = max(breakdown, key=lambda k: breakdown[k][0])
             plan.set_timing(True, only=dom)
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(steps)]
         if dist:
             dist.barrier()
         torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(steps):
+        t0 = time.perf_counter()
+        for e0, e1 in evs:
+            restore()
+            e0.record(stream)
             plan.solve(phi, pn, pnm1, u, v, w, p, stream=stream)
-        e1.record(stream)
+            e1.record(stream)
         torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
         if dist:
             dist.barrier()
-        ms = e0.elapsed_time(e1)
+        per = [e0.elapsed_time(e1) for e0, e1 in evs]
         live = plan.timing().get(dom) if dom else None
         st = plan.stats(stream)
         launches = plan.launches_per_solve() * steps
+        mr = plan.max_refine
         plan.close()
-        return ms, (breakdown, dom, live, plan.max_refine), st, launches
+        # the last solve started from the workload's u*: its outputs
+        out = {"p": p.cpu().numpy(), "u": u.cpu().numpy(), "v": v.cpu().numpy(), "w": w.cpu().numpy()}
+        return {"ms": sum(per), "ms_each": per, "wall_s": wall, "breakdown": breakdown, "dom": dom,
+                "live": live, "stats": st, "launches": launches, "max_refine": mr, "out": out}
 
     clocks = ClockSampler()
     clocks.start()
-    ms, (kern, dom, live, max_refine), st, launches = timed_run(prec, args.steps, args.warmup, True)
+    R = timed_run(prec, args.steps, args.warmup, True)
     clk = clocks.stop()
-    ms = slowest_rank(ms, dist)
+    ms = slowest_rank(R["ms"], dist)
     value = job_throughput(npts, args.steps, world, ms / 1e3)
+    st = R["stats"]
 
-    # the other precision on the same inputs (context for "mixed vs FP64")
-    other = F.FP64 if prec == F.MIXED else F.MIXED
-    ms_o, _, st_o, _ = timed_run(other, max(3, args.steps // 4), args.warmup, False)
-    value_o = npts * max(3, args.steps // 4) / (ms_o / 1e3)
+    # the other precision on the same inputs (the "mixed vs FP64" comparison)
+    k_o = max(3, args.steps // 4)
+    Ro = timed_run(other, k_o, args.warmup, False)
+    value_o = npts * k_o / (Ro["ms"] / 1e3)
 
-    # roofline of the dominant kernel
     hbm_peak, hbm_src = measured_peaks()
-    per_pt = algorithmic_per_point(spec.nx, spec.ny, prec == F.MIXED)
     roof = None
-    if dom and live:
-        tot_ms, cnt = live  # the dominant kernel inside the timed region
-        # refinement kernels return at once after convergence: count only the
-        # launches that did the pass (from the solve's sweep count)
-        it, mr = st["iterations"], max_refine
-        per_solve = {"fwd_x_refine": it, "fwd_y_refine": it, "thomas_refine": it,
-                     "inv_y_refine": it, "inv_x_update": it, "resid_correct": it}.get(dom)
-        if prec == F.MIXED and dom == "correct":  # runs only when no fused pass ran
-            per_solve = 1 if it == 0 else 0
-        del mr
-        if per_solve is not None:
-            cnt = max(1, per_solve * args.steps)
-        avg_s = tot_ms / cnt / 1e3
-        b_pt, fl_pt = per_pt.get(dom, (0, 0))
-        gbs = b_pt * npts / avg_s / 1e9
-        tfl = fl_pt * npts / avg_s / 1e12
-        t_hbm = b_pt / (hbm_peak * 1e9)
-        t_alu = fl_pt / (FP64_PEAK_NOMINAL * 1e12)
-        traffic = (measured_traffic(dom, prec == F.MIXED)
-                   if args.workload == "bubbles256" else None)
-        if t_alu > t_hbm:
-            roof = {"bound": "alu", "achieved": tfl, "peak": FP64_PEAK_NOMINAL, "unit": "TFLOP/s",
-                    "frac": tfl / FP64_PEAK_NOMINAL, "traffic": traffic, "kernel": dom,
-                    "peak_source": "nominal FP64 (recipe table)",
-                    "algorithmic_bytes": b_pt * npts, "hbm_gbs": gbs,
-                    "hbm_frac": gbs / hbm_peak, "hbm_peak_source": hbm_src}
-        else:
-            roof = {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
-                    "frac": gbs / hbm_peak, "traffic": traffic, "kernel": dom,
-                    "algorithmic_bytes": b_pt * npts, "peak_source": hbm_src}
-    if roof:
-        roof["launches_timed"] = cnt
-        roof["duration_ms"] = tot_ms / cnt
-        # the FP64 issue rate the ALU bound really is: FP64 instructions per
-        # point against the nominal 0.625 T FP64 instructions/s (1.25 TFLOP/s
-        # counts an FMA as two)
-        ipt = fp64_instr_per_point(spec.nx, spec.ny, spec.bcx, spec.bcy, prec == F.MIXED,
-                                   spec.bcz).get(dom)
-        if ipt:
-            ach = ipt * npts / avg_s / 1e12
-            roof["fp64_issue"] = {"instr_per_pt": ipt, "achieved": ach, "peak": FP64_PEAK_NOMINAL / 2,
-                                  "unit": "T instr/s", "frac": ach / (FP64_PEAK_NOMINAL / 2)}
+    if R["dom"] and R["live"]:
+        roof = dominant_roofline(R["dom"], R["live"], st, args.steps, mixed, R["max_refine"], spec, npts,
+                                 hbm_peak, hbm_src, dfma, args.workload if not args.nz else None)
+    kern = R["breakdown"]
     kernels = {k: {"ms_avg": v[0] / v[1], "launches": v[1],
                    "share": v[0] / max(1e-9, sum(x[0] for x in kern.values()))} for k, v in kern.items()}
 
@@ -424,15 +635,15 @@ def run_fizzy(args):
         plan.close()
         # the host link's bound for the same bytes: the step's six input copies
         # and four output copies alone, on two streams, with no solve
-        dev = [torch.empty(case.shape, dtype=torch.float64, device="cuda") for _ in range(10)]
+        devs = [torch.empty(case.shape, dtype=torch.float64, device="cuda") for _ in range(10)]
         s_in, s_out = torch.cuda.Stream(), torch.cuda.Stream()
 
         def copies():
             with torch.cuda.stream(s_in):
-                for h, d in zip(hin, dev[:6]):
+                for h, d in zip(hin, devs[:6]):
                     d.copy_(h, non_blocking=True)
             with torch.cuda.stream(s_out):
-                for h, d in zip(hout, dev[6:]):
+                for h, d in zip(hout, devs[6:]):
                     h.copy_(d, non_blocking=True)
         copies()
         torch.cuda.synchronize()
@@ -441,46 +652,85 @@ def run_fizzy(args):
             copies()
         torch.cuda.synchronize()
         el_copy = slowest_rank(time.perf_counter() - t0, dist)
-        del dev
+        del devs, hin, hout
         e2e = {"value": job_throughput(npts, args.e2e_steps, world, el), "unit": "pts/s",
                "h2d_bytes_per_step": 6 * 8 * npts, "d2h_bytes_per_step": 4 * 8 * npts,
                "ms_per_step": el / args.e2e_steps * 1e3,
                "copies_only_ms_per_step": el_copy / args.e2e_steps * 1e3,
                "link_frac": el_copy / el,
                "api": "fizzy_proj_solve_host_async (pipelined, pinned host arrays)"}
+    del phi, pn, pnm1, u0, v0, w0, u, v, w, p
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
 
-    cpu = None
+    # the FP64 CPU oracle on the same inputs: its time is the CPU baseline,
+    # its result the reference both GPU results are measured against
+    cpu, err = None, None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         # periodic z: the oracle's dense cyclic z-line solves grow as nz^3, so
-        # it is timed on a 32-plane slab of the same recipe
-        ocase = case if spec.bcz == I.NEUMANN else I.make_case(slab_spec(spec))
-        t_or, cores = oracle_time(ocase, reps=2)
+        # it runs on a 32-plane slab of the same recipe (errors then unmeasured)
+        full = spec.bcz == I.NEUMANN
+        ocase = case if full else I.make_case(slab_spec(spec))
+        t_or, cores, ref = oracle_time(ocase, reps=1)
         os_ = ocase.spec
         cpu = {"value": ocase.npts / t_or, "unit": "pts/s", "cores": cores, "kind": "oracle",
-               "sample": "one full %dx%dx%d projection (best of 2)%s" % (
-                   os_.nx, os_.ny, os_.nz, "" if ocase is case else ", a slab of the workload")}
+               "sample": "one full %dx%dx%d projection of the same inputs%s" % (
+                   os_.nx, os_.ny, os_.nz, "" if full else " (a 32-plane slab of the workload)"),
+               "seconds": t_or}
+        if full:
+            name_m = "mixed" if mixed else "fp64"
+            name_o = "fp64" if mixed else "mixed"
+            err = {name_m: errors_vs_oracle(case, R["out"], ref),
+                   name_o: errors_vs_oracle(case, Ro["out"], ref),
+                   "definition": "max|x - x_oracle| / max|x_oracle|; p with the dzf-weighted mean "
+                                 "removed on both sides; u, v, w with one shared max; div_metric = "
+                                 "max|D u| dx / rms(u*)",
+                   "bars": {"fp64": 1e-12, "mixed": 1e-9, "div_metric": 1e-10}}
+        del ref
+    R["out"] = Ro["out"] = None
+
+    batch = serve = None
+    if rank == 0 and not args.no_sub:
+        batch = run_batch_forms(args, F, torch, steps=5, warmup=2, reps=2)
+        torch.cuda.empty_cache()
+        summ, info = run_serve_loop(args, F, torch, args.sub_serve_requests, args.serve_slots)
+        serve = {"requests": summ["requests"], "arrival_rate_per_s": 2000, "budget_gb": 120,
+                 "slots": args.serve_slots, "deadline_ms": 100, "throughput_pts_s": summ["throughput_pts_s"],
+                 "p50_ms": summ["p50_ms"], "p99_ms": summ["p99_ms"],
+                 "rejected_fraction": summ["rejected_fraction"], "requests_per_s": summ["requests_per_s"],
+                 "all_converged": summ["all_converged"], "max_relres": summ["max_relres"],
+                 "plans_built": info.get("plans_built")}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "pts/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-                "dtype": "f64" if prec == F.FP64 else "f32+f64",
+                "dtype": "f32+f64" if mixed else "f64",
                 "data": "synthetic",
                 "config": {"workload": args.workload, "grid": [spec.nx, spec.ny, spec.nz],
-                           "precision": args.precision, "bc": "%s x, %s y, %s z" % tuple(
+                           "precision": args.precision, "tol": 1e-10,
+                           "z_stretch_beta": spec.beta,
+                           "bc": "%s x, %s y, %s z" % tuple(
                                "periodic" if b == I.PERIODIC else "walls" for b in (spec.bcx, spec.bcy, spec.bcz)),
                            "l2": "inputs (6 x %d MiB) larger than L2" % (npts * 8 >> 20),
+                           "timing": "each solve from the workload's u*, restored from a pristine device "
+                                     "copy before it, outside its own CUDA events; value = points / sum "
+                                     "of the solves' event times",
                            "parallelism": "replicas" if world > 1 else "single"},
-                "gpu_launches": launches, "roofline": roof,
-                "path_roofline": path_roofline(value, spec.nx, spec.ny, spec.bcx, spec.bcy,
-                                               prec == F.MIXED, int(st["iterations"]), hbm_peak,
-                                               spec.bcz),
+                "gpu_launches": R["launches"], "roofline": roof,
+                "path_roofline": path_roofline(value, spec.nx, spec.ny, spec.bcx, spec.bcy, mixed,
+                                               int(st["iterations"]), hbm_peak, dfma, spec.bcz),
+                "peaks_measured": peaks,
+                "err_vs_oracle": err,
                 "cpu_baseline": cpu, "e2e": e2e,
                 "clocks": clk, "kernels": kernels,
                 "stats": {k: st[k] for k in ("iterations", "converged", "relres")},
-                ("mixed" if other == F.MIXED else "fp64"): {
-                    "value": value_o, "unit": "pts/s", "ms_per_step": ms_o / max(3, args.steps // 4),
-                    "iterations": st_o["iterations"], "relres": st_o["relres"]}}
+                "timed_wall_s_incl_restores": R["wall_s"],
+                ("fp64" if mixed else "mixed"): {
+                    "value": value_o, "unit": "pts/s", "ms_per_step": Ro["ms"] / k_o, "steps": k_o,
+                    "iterations": Ro["stats"]["iterations"], "relres": Ro["stats"]["relres"]},
+                "mixed_over_fp64": (value / value_o) if mixed else (value_o / value),
+                "batch64": batch, "serve": serve}
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
@@ -488,120 +738,47 @@ def run_fizzy(args):
 
 
 def run_batch(args):
-    """Uneven batch: 64 projections (nx, ny in {32..192}, nz in [32, 192],
-    periodic or wall x/y, 1-20 drops, density ratio 10-1000), mixed precision,
-    one persistent launch replayed from a CUDA graph with autotuned tiles;
-    compared with the plain FP64 form (one fizzy_proj_solve per instance)."""
+    """Uneven batch alone: 64 projections (nx, ny in {32..192}, nz in
+    [32, 192], periodic or wall x/y, 1-20 drops, density ratio 10-1000),
+    mixed precision, one persistent launch replayed from a CUDA graph with
+    autotuned tiles; compared with the plain FP64 form (one fizzy_proj_solve
+    per instance)."""
     import torch
     import paper_2502_04189_b300 as F
     world, rank, local = dist_env()
     torch.cuda.set_device(local)
-    specs = I.batch_specs(64)
-    cases = [I.make_case(s) for s in specs]
-    npts = sum(c.npts for c in cases)
-
-    def dev(a):
-        return torch.from_numpy(np.ascontiguousarray(a)).cuda()
-
-    inputs = [(dev(c.phi), dev(c.pn), dev(c.pnm1), dev(c.u), dev(c.v), dev(c.w)) for c in cases]
-    outs = [torch.empty(c.shape, dtype=torch.float64, device="cuda") for c in cases]
-    stream = torch.cuda.current_stream()
-    results = {}
-    for prec, name in ((F.MIXED, "mixed_batched"), (F.FP64, "fp64_batched")):
-        plans = [F.Plan.for_case(c, precision=prec) for c in cases]
-        arrays = [inp + (o,) for inp, o in zip(inputs, outs)]
-        batch = F.Batch(plans, arrays)
-        tuning, tuned_ms = batch.autotune(reps=3)
-        for _ in range(args.warmup):
-            batch.solve()
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(args.steps):
-            batch.solve()
-        e1.record(stream)
-        torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1) / args.steps
-        status = batch.status()
-        st = [p.stats() for p in plans]
-        results[name] = {"value": npts / (ms / 1e3), "ms_per_batch": ms, "tuning": tuning,
-                         "status": status, "items": batch.info()["items"],
-                         "max_relres": max(x["relres"] for x in st),
-                         "sweeps": [x["iterations"] for x in st] if prec == F.MIXED else None,
-                         "all_converged": all(x["converged"] for x in st)}
-        batch.close()
-        for p in plans:
-            p.close()
-    # plain FP64 form: one stand-alone solve per instance
-    plans = [F.Plan.for_case(c, precision=F.FP64) for c in cases]
-    for _ in range(args.warmup):
-        for pl, inp, o in zip(plans, inputs, outs):
-            pl.solve(*inp, o)
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(args.steps):
-        for pl, inp, o in zip(plans, inputs, outs):
-            pl.solve(*inp, o)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / args.steps
-    results["fp64_plain_loop"] = {"value": npts / (ms / 1e3), "ms_per_batch": ms}
-    for p in plans:
-        p.close()
+    res = run_batch_forms(args, F, torch, steps=args.steps, warmup=args.warmup, reps=3)
     if rank == 0:
-        r = results["mixed_batched"]
+        r = res["forms"]["mixed_batched"]
         line = {"metric": METRIC, "value": r["value"], "unit": "pts/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms_per_batch"],
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "f32+f64", "data": "synthetic",
-                "config": {"workload": "batch64", "instances": len(cases), "points": npts,
+                "config": {"workload": "batch64", "instances": res["instances"], "points": res["points"],
                            "precision": "mixed", "tol": 1e-10},
-                "forms": results}
+                "forms": res["forms"], "mixed_over_plain_fp64": res["mixed_over_plain_fp64"]}
         print(json.dumps(line), flush=True)
     return 0
 
 
 def run_serve(args):
-    """Serving: Poisson arrivals (seeded, mean 2000 req/s) of requests with
-    nx, ny in {64,...,384}, nz in [64, 384], 30 % tanh-stretched z, periodic
-    or wall x/y, density ratio 10-1000, mixed precision refined to 1e-10;
-    admission by a 120 GB HBM budget with plans cached on the device, 100 ms
-    admission deadline.  Inputs are periodic crops of a device-resident
-    256^3 bubble template."""
+    """Serving alone (see run_serve_loop) with nvidia-smi clock sampling."""
     import torch
     import paper_2502_04189_b300 as F
-    import paper_2502_04189_b300.serve as S
     world, rank, local = dist_env()
     torch.cuda.set_device(local)
-    n = args.serve_requests
-    arrivals, specs = I.serve_specs(n)
-    tmpl = I.make_case(I.bubbles256_spec())
-    fields = S.TemplateFields(tmpl)
-    reqs = S.requests_from_specs(arrivals, specs, F.MIXED)
-    server = F.Server(120 * (1 << 30), slots=args.serve_slots)
-
-    def fill(r, views, stream):
-        fields.fill(views, r.desc, r.offset, stream)
-
-    # warm-up on a few requests (plan-building code paths, pool growth)
-    S.run(server, [S.Request(i, 0.0, r.desc, r.offset) for i, r in enumerate(reqs[:4])], fill,
-          deadline=60.0)
-    torch.cuda.synchronize()
     clocks = ClockSampler()
     clocks.start()
-    out, summ = S.run(server, reqs, fill, deadline=0.1)
+    summ, info = run_serve_loop(args, F, torch, args.serve_requests, args.serve_slots)
     clk = clocks.stop()
-    info = server.info()
-    server.close()
     if rank == 0:
         line = {"metric": METRIC, "value": summ["throughput_pts_s"], "unit": "pts/s",
-                "n_gpus": world, "steps": n, "warmup": 4, "ms_per_step": summ["mean_ms"],
+                "n_gpus": world, "steps": summ["requests"], "warmup": 4, "ms_per_step": summ["mean_ms"],
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "f32+f64", "data": "synthetic",
-                "config": {"workload": "serve", "arrival_rate_per_s": 2000, "requests": n,
-                           "budget_gb": 120, "slots": args.serve_slots, "deadline_ms": 100,
-                           "precision": "mixed", "tol": 1e-10},
+                "config": {"workload": "serve", "arrival_rate_per_s": 2000,
+                           "requests": summ["requests"], "budget_gb": 120, "slots": args.serve_slots,
+                           "deadline_ms": 100, "precision": "mixed", "tol": 1e-10},
                 "serving": summ, "server": info, "clocks": clk}
         print(json.dumps(line), flush=True)
     return 0
@@ -730,15 +907,21 @@ def run_acdi(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="fizzy", choices=["fizzy", "reference"])
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
-    ap.add_argument("--workload", default="bubbles256", choices=list(WORKLOADS) + ["batch64", "serve"])
+    ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=list(WORKLOADS) + ["batch64", "serve"])
+    ap.add_argument("--nz", type=int, default=0,
+                    help="run a slab of the workload with this many z planes (profiling captures)")
     ap.add_argument("--serve-requests", type=int, default=4000)
+    ap.add_argument("--sub-serve-requests", type=int, default=1000,
+                    help="requests of the serving run embedded in the default line")
     ap.add_argument("--serve-slots", type=int, default=8)
-    ap.add_argument("--e2e-steps", type=int, default=8)
+    ap.add_argument("--e2e-steps", type=int, default=6)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-sub", action="store_true", help="skip the embedded batch and serving runs")
+    ap.add_argument("--no-probe", action="store_true", help="skip the FMA-rate probes")
     ap.add_argument("--vc", action="store_true",
                     help="time the variable-coefficient projection without splitting instead")
     ap.add_argument("--vc-tol", type=float, default=1e-10)

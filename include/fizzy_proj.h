@@ -382,6 +382,19 @@ int fizzy_crop_fill(const double *const *src, int tx, int ty, int tz, double *co
                     int nx, int ny, int nz, int ox, int oy, int oz, int bc_x, int bc_y,
                     void *stream);
 
+/* Measurement support (no counterpart in the paper): the fused multiply-add
+ * issue rate of the GPU, the peak the FP64-bound projection kernels are
+ * measured against.  precision FIZZY_PREC_FP64 times DFMA, FIZZY_PREC_MIXED
+ * FFMA.  One launch of a resident grid (CTAs per SM x SMs, 256 threads),
+ * each thread running 8 independent FMA chains for 32 x iters FMAs; timed
+ * with CUDA events on stream, which the call synchronises.  *instr_per_s
+ * receives FMA instructions (per lane) per second, *elapsed_ms (nullable)
+ * the kernel time.  Choose iters so the launch lasts 100 ms or more.
+ * Returns FIZZY_ERR_INVALID for iters < 1, a null instr_per_s or another
+ * precision, FIZZY_ERR_CUDA if the launch fails. */
+int fizzy_probe_fma_rate(int precision, int iters, double *instr_per_s, double *elapsed_ms,
+                         void *stream);
+
 /* ------------------------------------------------------------------------
  * Allocation-free projection (FP64 mode, small grids).
  *

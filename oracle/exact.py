@@ -167,3 +167,83 @@ def project(g: ExactGrid, rho_l, rho_g, dt, phi, pn, pnm1, u, v, w):
         if not (g.bcz == 1 and k == g.nz - 1):
             wo[c] = w[c] - dt * (pz[c] / rho0 + (bz[c] - 1 / rho0) * gz[c])
     return f, p, uo, vo, wo
+
+
+# ---------------------------------------------------------------------------
+# The Poisson problem alone with the CaNS solver's boundary kinds in x and y:
+# 0 periodic, 1 Neumann at both ends, 2 Dirichlet at both ends (p = 0 on the
+# boundary faces), 3 Neumann near / Dirichlet far, 4 Dirichlet near /
+# Neumann far.  Beyond a Neumann face the ghost value equals the cell value,
+# beyond a Dirichlet face it is its negative.
+# ---------------------------------------------------------------------------
+def _ghost(bc, side, qc):
+    dirichlet = bc == 2 or (bc == 3 and side == 1) or (bc == 4 and side == 0)
+    return -qc if dirichlet else qc
+
+
+def lap_bc(g: ExactGrid, q):
+    """L_h q written out cell by cell: (neighbour - centre)/h on every face,
+    ghost values beyond boundary faces, z faces as in the projection."""
+    out = {}
+    for i, j, k in g.cells():
+        qc = q[(i, j, k)]
+        if i < g.nx - 1:
+            qe = q[(i + 1, j, k)]
+        else:
+            qe = q[(0, j, k)] if g.bcx == 0 else _ghost(g.bcx, 1, qc)
+        if i > 0:
+            qw = q[(i - 1, j, k)]
+        else:
+            qw = q[(g.nx - 1, j, k)] if g.bcx == 0 else _ghost(g.bcx, 0, qc)
+        if j < g.ny - 1:
+            qn = q[(i, j + 1, k)]
+        else:
+            qn = q[(i, 0, k)] if g.bcy == 0 else _ghost(g.bcy, 1, qc)
+        if j > 0:
+            qs = q[(i, j - 1, k)]
+        else:
+            qs = q[(i, g.ny - 1, k)] if g.bcy == 0 else _ghost(g.bcy, 0, qc)
+        if k < g.nz - 1:
+            wt = (q[(i, j, k + 1)] - qc) / g.dzc(k)
+        else:
+            wt = (q[(i, j, 0)] - qc) / g.dzc(k) if g.bcz == 0 else Q(0)
+        if k > 0:
+            wb = (qc - q[(i, j, k - 1)]) / g.dzc(k - 1)
+        else:
+            wb = (qc - q[(i, j, g.nz - 1)]) / g.dzc(g.nz - 1) if g.bcz == 0 else Q(0)
+        out[(i, j, k)] = (((qe - qc) - (qc - qw)) / g.dx / g.dx + ((qn - qc) - (qc - qs)) / g.dy / g.dy
+                          + (wt - wb) / g.dzf(k))
+    return out
+
+
+def poisson_bc(g: ExactGrid, f):
+    """Exact solution of L_h p = f.  Singular (no Dirichlet face in x or y):
+    the last equation is replaced by the gauge row sum dzf_k p = 0 and f is
+    taken as given (the caller passes a compatible f).  Otherwise p is
+    unique."""
+    cells = list(g.cells())
+    n = len(cells)
+    cols = []
+    for c in cells:
+        e = {d: Q(0) for d in cells}
+        e[c] = Q(1)
+        cols.append(lap_bc(g, e))
+    A = [[cols[ci][r] for ci in range(n)] for r in cells]
+    b = [f[r] for r in cells]
+    if g.bcx <= 1 and g.bcy <= 1:
+        A[n - 1] = [g.dzf(c[2]) for c in cells]
+        b[n - 1] = Q(0)
+    for k in range(n):
+        piv = next(r for r in range(k, n) if A[r][k] != 0)
+        A[k], A[piv] = A[piv], A[k]
+        b[k], b[piv] = b[piv], b[k]
+        for r in range(k + 1, n):
+            if A[r][k] != 0:
+                m = A[r][k] / A[k][k]
+                A[r] = [A[r][c] - m * A[k][c] for c in range(n)]
+                b[r] -= m * b[k]
+    x = [Q(0)] * n
+    for k in range(n - 1, -1, -1):
+        s = b[k] - sum(A[k][c] * x[c] for c in range(k + 1, n))
+        x[k] = s / A[k][k]
+    return {cells[i]: x[i] for i in range(n)}

@@ -43,6 +43,17 @@
  * i+1/2, v the y-face j+1/2, w the z-face k+1/2.  bc = 0 periodic, 1 Neumann
  * (walls), in x, y and z alike.  In a wall direction the last face is the far
  * wall and the near wall face is implicit; both are treated as 0.
+ *
+ * The Poisson solve alone (ora_apply_L, ora_poisson_fft, ora_poisson_dense)
+ * also takes the boundary kinds of the CaNS fast solver in x and y:
+ * bc = 2 Dirichlet (p = 0 on both boundary faces), 3 Neumann at the near end
+ * and Dirichlet at the far end, 4 Dirichlet near and Neumann far.  The ghost
+ * value beyond a Neumann face mirrors the cell (zero flux), beyond a
+ * Dirichlet face it mirrors it with the opposite sign (zero face value).
+ * The FFT path extends such a direction to a periodic problem by reflection:
+ * odd about both faces (length 2n), or even about the Neumann face and odd
+ * about the Dirichlet face (the quarter-wave extension, length 4n).  With a
+ * Dirichlet face in x or y the problem is not singular: no gauge, p unique.
  */
 #include <complex.h>
 #include <math.h>
@@ -193,10 +204,56 @@ void ora_div(int nx, int ny, int nz, double dx, double dy, const double *zf, int
     divergence(&g, u, v, w, out);
 }
 
+/* Ghost rule of an x or y direction of kind bc (>= 1) at its near (side 0)
+ * or far (side 1) boundary face: +1 mirrors the cell (Neumann), -1 mirrors
+ * it with the opposite sign (Dirichlet). */
+static double ghost_sign(int bc, int side) {
+    int dir = (bc == 2) || (bc == 3 && side == 1) || (bc == 4 && side == 0);
+    return dir ? -1.0 : 1.0;
+}
+
+/* L_h p with the boundary kinds 0..4 in x and y: every face gradient
+ * (neighbour - centre)/h, the neighbour beyond a boundary face being the
+ * ghost value; z as in grad(). */
+static void lap_bc(const grid_t *g, const double *q, double *out) {
+    int nx = g->nx, ny = g->ny, nz = g->nz;
+#pragma omp parallel for schedule(static)
+    for (int k = 0; k < nz; ++k)
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i < nx; ++i) {
+                size_t c = IDX(g, i, j, k);
+                double qc = q[c], qe, qw, qn, qs;
+                if (i < nx - 1) qe = q[IDX(g, i + 1, j, k)];
+                else qe = g->bcx == 0 ? q[IDX(g, 0, j, k)] : ghost_sign(g->bcx, 1) * qc;
+                if (i > 0) qw = q[IDX(g, i - 1, j, k)];
+                else qw = g->bcx == 0 ? q[IDX(g, nx - 1, j, k)] : ghost_sign(g->bcx, 0) * qc;
+                if (j < ny - 1) qn = q[IDX(g, i, j + 1, k)];
+                else qn = g->bcy == 0 ? q[IDX(g, i, 0, k)] : ghost_sign(g->bcy, 1) * qc;
+                if (j > 0) qs = q[IDX(g, i, j - 1, k)];
+                else qs = g->bcy == 0 ? q[IDX(g, i, ny - 1, k)] : ghost_sign(g->bcy, 0) * qc;
+                double ue = (qe - qc) / g->dx, uw = (qc - qw) / g->dx;
+                double vn = (qn - qc) / g->dy, vs = (qc - qs) / g->dy;
+                double wt, wb;
+                if (k < nz - 1) wt = (q[IDX(g, i, j, k + 1)] - qc) / dzc(g, k);
+                else wt = g->bcz == 0 ? (q[IDX(g, i, j, 0)] - qc) / dzc(g, k) : 0.0;
+                if (k > 0) wb = (qc - q[IDX(g, i, j, k - 1)]) / dzc(g, k - 1);
+                else wb = g->bcz == 0 ? (qc - q[IDX(g, i, j, nz - 1)]) / dzc(g, nz - 1) : 0.0;
+                out[c] = (ue - uw) / g->dx + (vn - vs) / g->dy + (wt - wb) / dzf(g, k);
+            }
+}
+
+/* The Poisson problem is singular (constants in its null space) unless a
+ * Dirichlet face bounds x or y. */
+static int singular(const grid_t *g) { return g->bcx <= 1 && g->bcy <= 1; }
+
 /* L_h p = D(G p) */
 void ora_apply_L(int nx, int ny, int nz, double dx, double dy, const double *zf, int bcx, int bcy,
                  int bcz, const double *p, double *out) {
     grid_t g = mkgrid(nx, ny, nz, dx, dy, zf, bcx, bcy, bcz);
+    if (bcx > 1 || bcy > 1) {
+        lap_bc(&g, p, out);
+        return;
+    }
     size_t n = (size_t)nx * ny * nz;
     double *gx = malloc(n * sizeof(double)), *gy = malloc(n * sizeof(double)),
            *gz = malloc(n * sizeof(double));
@@ -485,23 +542,61 @@ static void z_matrix(int nz, const double *lo, const double *up, double lam, dou
  * periodic -> e; Neumann (extended to 2n by even reflection) -> mirror. */
 static int ext_src(int e, int n, int bc) { return (bc == 0 || e < n) ? e : 2 * n - 1 - e; }
 
+/* Length of the periodic problem a direction of kind bc extends to. */
+static int ext_len(int n, int bc) { return bc == 0 ? n : (bc <= 2 ? 2 * n : 4 * n); }
+
+/* Source cell and sign of extended position e (0 <= e < ext_len).  Neumann:
+ * even about the far face (period 2n).  Dirichlet: odd about the far face
+ * (period 2n, hence odd about the near face too).  Neumann near, Dirichlet
+ * far: the first 2n positions odd about face n-1/2, the next 2n their even
+ * mirror about face -1/2 (period 4n).  Dirichlet near, Neumann far: the first
+ * 2n even about face n-1/2, the next 2n their odd mirror about face -1/2. */
+static int ext_map(int e, int n, int bc, double *sign) {
+    *sign = 1.0;
+    if (bc == 0 || e < n) return e;
+    if (bc == 1) return 2 * n - 1 - e;
+    if (bc == 2) {
+        *sign = -1.0;
+        return 2 * n - 1 - e;
+    }
+    double s2 = 1.0;
+    int e2 = e;
+    if (e >= 2 * n) {          /* mirror about face -1/2 of the first 2n positions */
+        e2 = 4 * n - 1 - e;
+        s2 = bc == 3 ? 1.0 : -1.0;
+    }
+    if (e2 < n) {
+        *sign = s2;
+        return e2;
+    }
+    *sign = s2 * (bc == 3 ? -1.0 : 1.0);  /* reflection about face n-1/2 */
+    return 2 * n - 1 - e2;
+}
+
 int ora_poisson_fft(int nx, int ny, int nz, double dx, double dy, const double *zf, int bcx,
                     int bcy, int bcz, const double *f, double *p) {
     grid_t g = mkgrid(nx, ny, nz, dx, dy, zf, bcx, bcy, bcz);
-    int mx = bcx == 0 ? nx : 2 * nx; /* extent of the periodic problem */
-    int my = bcy == 0 ? ny : 2 * ny;
+    int mx = ext_len(nx, bcx); /* extent of the periodic problem */
+    int my = ext_len(ny, bcy);
+    const int sing = singular(&g);
     size_t plane = (size_t)mx * my;
     cplx *F = malloc(sizeof(cplx) * plane * nz);
     if (!F) return -3;
     int status = 0;
 
-    /* even extension in wall directions */
+    /* even extension in wall directions (odd or quarter-wave with Dirichlet faces) */
 #pragma omp parallel for schedule(static)
     for (int k = 0; k < nz; ++k)
         for (int b = 0; b < my; ++b)
-            for (int a = 0; a < mx; ++a)
-                F[(size_t)k * plane + (size_t)b * mx + a] =
-                    f[IDX(&g, ext_src(a, nx, bcx), ext_src(b, ny, bcy), k)];
+            for (int a = 0; a < mx; ++a) {
+                double sa, sb;
+                int ia = (bcx <= 1) ? ext_src(a, nx, bcx) : ext_map(a, nx, bcx, &sa);
+                int ib = (bcy <= 1) ? ext_src(b, ny, bcy) : ext_map(b, ny, bcy, &sb);
+                double v = f[IDX(&g, ia, ib, k)];
+                if (bcx > 1) v *= sa;
+                if (bcy > 1) v *= sb;
+                F[(size_t)k * plane + (size_t)b * mx + a] = v;
+            }
 
     /* forward complex FFTs along x then y */
     cplx *wxf = roots_table(mx, -1), *wyf = roots_table(my, -1);
@@ -585,8 +680,12 @@ int ora_poisson_fft(int nx, int ny, int nz, double dx, double dy, const double *
         free(A);
         free(rhs);
     }
-    /* (0,0): singular; rows 0..nz-2 of A_z plus the gauge row sum_k dzf_k p_k = 0 */
-    {
+    /* (0,0): singular; rows 0..nz-2 of A_z plus the gauge row sum_k dzf_k p_k = 0.
+       With a Dirichlet face in x or y the extension has no mean: that mode
+       is exactly zero. */
+    if (!sing) {
+        for (int k = 0; k < nz; ++k) F[(size_t)k * plane] = 0.0;
+    } else {
         double *A = malloc(sizeof(double) * (size_t)nz * nz);
         cplx *rhs = malloc(sizeof(cplx) * nz);
         z_matrix(nz, lo, up, 0.0, A);
@@ -624,7 +723,7 @@ int ora_poisson_fft(int nx, int ny, int nz, double dx, double dy, const double *
         for (int j = 0; j < ny; ++j)
             for (int i = 0; i < nx; ++i)
                 p[IDX(&g, i, j, k)] = creal(F[(size_t)k * plane + (size_t)j * mx + i]) * scale;
-    remove_weighted_mean(&g, p);
+    if (sing) remove_weighted_mean(&g, p);
     free(wxf);
     free(wyf);
     free(wxb);
@@ -638,7 +737,8 @@ int ora_poisson_fft(int nx, int ny, int nz, double dx, double dy, const double *
 }
 
 /* Dense path for small grids: assemble L_h column by column from ora_apply_L,
- * replace the last row by the gauge row (weights dzf_k), solve by dense GEPP. */
+ * replace the last row by the gauge row (weights dzf_k) when the problem is
+ * singular, solve by dense GEPP. */
 int ora_poisson_dense(int nx, int ny, int nz, double dx, double dy, const double *zf, int bcx,
                       int bcy, int bcz, const double *f, double *p) {
     grid_t g = mkgrid(nx, ny, nz, dx, dy, zf, bcx, bcy, bcz);
@@ -653,14 +753,16 @@ int ora_poisson_dense(int nx, int ny, int nz, double dx, double dy, const double
         for (size_t r = 0; r < n; ++r) A[r * n + c] = col[r];
         e[c] = 0.0;
     }
-    for (int k = 0; k < nz; ++k)
-        for (int j = 0; j < ny; ++j)
-            for (int i = 0; i < nx; ++i) A[(n - 1) * n + IDX(&g, i, j, k)] = dzf(&g, k);
+    const int sing = singular(&g);
+    if (sing)
+        for (int k = 0; k < nz; ++k)
+            for (int j = 0; j < ny; ++j)
+                for (int i = 0; i < nx; ++i) A[(n - 1) * n + IDX(&g, i, j, k)] = dzf(&g, k);
     for (size_t r = 0; r < n; ++r) b[r] = f[r];
-    b[n - 1] = 0.0;
+    if (sing) b[n - 1] = 0.0;
     int st = dense_gepp((int)n, A, b);
     for (size_t r = 0; r < n; ++r) p[r] = creal(b[r]);
-    remove_weighted_mean(&g, p);
+    if (sing) remove_weighted_mean(&g, p);
     free(A);
     free(e);
     free(col);

@@ -415,3 +415,15 @@ def solve_noalloc(phi, pn, pnm1, u, v, w, p_out, stream=None, **desc):
     del keep
     if rc != 0:
         raise FizzyError(rc)
+
+
+def probe_fma_rate(precision=FP64, iters=20000, stream=None):
+    """FMA issue rate of the GPU (fizzy_probe_fma_rate): precision FP64 times
+    DFMA chains, MIXED FFMA chains.  Returns (FMA instructions per second,
+    kernel milliseconds)."""
+    rate, ms = ctypes.c_double(), ctypes.c_double()
+    rc = _abi.lib().fizzy_probe_fma_rate(int(precision), int(iters), ctypes.byref(rate),
+                                         ctypes.byref(ms), _stream_handle(stream))
+    if rc != 0:
+        raise FizzyError(rc)
+    return rate.value, ms.value

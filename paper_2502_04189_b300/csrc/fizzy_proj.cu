@@ -7,6 +7,7 @@
 #include "kern_r16.cuh"
 #include "kern_vc.cuh"
 #include "kern_acdi.cuh"
+#include "kern_probe.cuh"
 
 #include <algorithm>
 #include <cmath>
@@ -1083,6 +1084,41 @@ int fizzy_proj_solve_host_async(fizzy_proj_plan_t p, const double *phi, const do
     if (e != cudaSuccess) return cuda_err(p, e, "D2H");
     p->set_used[b] = true;
     ++p->host_calls;
+    return FIZZY_OK;
+}
+
+int fizzy_probe_fma_rate(int precision, int iters, double *instr_per_s, double *elapsed_ms,
+                         void *stream) {
+    if (iters < 1 || !instr_per_s) return FIZZY_ERR_INVALID;
+    if (precision != FIZZY_PREC_FP64 && precision != FIZZY_PREC_MIXED) return FIZZY_ERR_INVALID;
+    cudaStream_t s = (cudaStream_t)stream;
+    const bool f64 = precision == FIZZY_PREC_FP64;
+    const void *fn = f64 ? (const void *)k_fma_probe<double> : (const void *)k_fma_probe<float>;
+    int dev = 0, sms = 0, nb = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, 256, 0);
+    if (e != cudaSuccess) return FIZZY_ERR_CUDA;
+    const int grid = std::max(1, nb) * std::max(1, sms);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+    if (e == cudaSuccess) {
+        if (f64) k_fma_probe<double><<<grid, 256, 0, s>>>(iters, 0.9999999, 1e-7);
+        else k_fma_probe<float><<<grid, 256, 0, s>>>(iters, 0.9999f, 1e-4f);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (e != cudaSuccess || !(ms > 0.f)) return FIZZY_ERR_CUDA;
+    const double instr = (double)grid * 256.0 * (double)iters * 4.0 * PROBE_CHAINS;
+    *instr_per_s = instr / (ms * 1e-3);
+    if (elapsed_ms) *elapsed_ms = ms;
     return FIZZY_OK;
 }
 

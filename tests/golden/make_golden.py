@@ -78,10 +78,52 @@ def make(case):
     return out
 
 
+# The Poisson problem alone with Dirichlet and mixed x/y boundaries (bc 2 DD,
+# 3 Neumann near / Dirichlet far, 4 Dirichlet near / Neumann far): the
+# boundary kinds of the CaNS fast solver the paper's "Methods and
+# Implementation strategy" builds on.
+CITATION_POISSON = ("Paper, 'Methods and Implementation strategy': staggered second-order finite "
+                    "differences, fast direct FFT-based Poisson solver of CaNS (Costa 2018) with "
+                    "Dirichlet and mixed boundary kinds.  Values: exact rational solution of the "
+                    "discrete equations (oracle/exact.py, poisson_bc), rounded to binary64.")
+
+POISSON_CASES = [
+    dict(name="dd_p_uniform", nx=4, ny=3, nz=3, dx="1/4", dy="1/3", zf=["0", "1/3", "2/3", "1"],
+         bcx=2, bcy=0, bcz=1, seed=61),
+    dict(name="nd_dn_stretched", nx=3, ny=4, nz=4, dx="1/2", dy="1/4",
+         zf=["0", "1/8", "1/2", "7/8", "1"], bcx=3, bcy=4, bcz=1, seed=67),
+    dict(name="dn_n_periodic_z", nx=4, ny=2, nz=3, dx="1/4", dy="1/2", zf=["0", "1/4", "5/8", "1"],
+         bcx=4, bcy=1, bcz=0, seed=71),
+    dict(name="dd_dd_uniform", nx=3, ny=3, nz=2, dx="1/3", dy="1/3", zf=["0", "1/2", "1"],
+         bcx=2, bcy=2, bcz=1, seed=73),
+]
+
+
+def make_poisson(case):
+    nx, ny, nz = case["nx"], case["ny"], case["nz"]
+    g = exact.ExactGrid(nx, ny, nz, Q(case["dx"]), Q(case["dy"]), [Q(z) for z in case["zf"]],
+                        case["bcx"], case["bcy"], case["bcz"])
+    r = lcg(case["seed"])
+    cells = list(g.cells())
+    f = {c: Q(next(r) % 65 - 32, 8) for c in cells}
+    p = exact.poisson_bc(g, f)
+    out = dict(case)
+    out.update(citation=CITATION_POISSON, layout="[nz][ny][nx], x fastest",
+               inputs=dict(f=[float(f[c]) for c in cells]),
+               expected=dict(p=[float(p[c]) for c in cells]))
+    return out
+
+
 if __name__ == "__main__":
     for case in CASES:
         data = make(case)
         path = os.path.join(HERE, "exact_%s.json" % case["name"])
+        with open(path, "w") as fh:
+            json.dump(data, fh, indent=1)
+        print("wrote", path)
+    for case in POISSON_CASES:
+        data = make_poisson(case)
+        path = os.path.join(HERE, "poisson_%s.json" % case["name"])
         with open(path, "w") as fh:
             json.dump(data, fh, indent=1)
         print("wrote", path)

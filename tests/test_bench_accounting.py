@@ -26,16 +26,16 @@ def test_fp64_mode_path_totals():
     ins = bench.fp64_instr_per_point(256, 256, 0, 0, mixed=False)
     assert sum(v[0] for v in per.values()) == 224
     assert sum(ins.values()) == 82  # 19 + (6 + 12) + 12 + 3 + 12 + 12 + 6
-    r = bench.path_roofline(1e9, 256, 256, 0, 0, False, 0, 6504.1)
+    r = bench.path_roofline(1e9, 256, 256, 0, 0, False, 0, 6504.1, 0.625e12)
     assert r["bytes_per_pt"] == 224 and r["fp64_instr_per_pt"] == 82
     assert r["hbm_gbs"] == pytest.approx(224.0)
     assert r["fp64_issue_frac"] == pytest.approx(82e9 / 0.625e12)
 
 
 def test_mixed_path_counts_each_sweep():
-    one = bench.path_roofline(1e9, 256, 256, 0, 0, True, 1, 6504.1)
-    two = bench.path_roofline(1e9, 256, 256, 0, 0, True, 2, 6504.1)
-    none = bench.path_roofline(1e9, 256, 256, 0, 0, True, 0, 6504.1)
+    one = bench.path_roofline(1e9, 256, 256, 0, 0, True, 1, 6504.1, 0.6e12)
+    two = bench.path_roofline(1e9, 256, 256, 0, 0, True, 2, 6504.1, 0.6e12)
+    none = bench.path_roofline(1e9, 256, 256, 0, 0, True, 0, 6504.1, 0.6e12)
     per = bench.algorithmic_per_point(256, 256, mixed=True)
     sweep = sum(per[k][0] for k in ("fwd_x_refine", "fwd_y_refine", "thomas_refine",
                                     "inv_y_refine", "inv_x_update", "resid_correct"))
@@ -45,3 +45,28 @@ def test_mixed_path_counts_each_sweep():
     assert one["fp64_instr_per_pt"] == 19 + 6 + 10 + 1 + 13
     assert none["fp64_instr_per_pt"] == 19 + 6 + 10 + 6
     assert one["io_floor_bytes_per_pt"] == 80
+
+
+def test_dominant_roofline_against_measured_dfma_rate():
+    """The dominant kernel's roofline divides by the DFMA issue rate measured
+    in the run: an FP64-bound flux launch is "alu", its flop fraction is the
+    algorithmic flops over twice that rate, and its issue fraction the
+    counted FP64 instructions over the rate itself."""
+    from paper_2502_04189_b300 import inputs as I
+    spec = I.bubbles256_spec()
+    n = spec.nx * spec.ny * spec.nz
+    dfma = 0.6e12
+    t_ms = 0.6  # per launch
+    st = {"iterations": 1}
+    r = bench.dominant_roofline("flux", (t_ms * 20, 20), st, 20, True, 4, spec, n, 6504.1, "m", dfma,
+                                "no-such-workload")
+    assert r["bound"] == "alu" and r["kernel"] == "flux"
+    assert r["achieved"] == pytest.approx(32 * n / (t_ms * 1e-3) / 1e12)
+    assert r["peak"] == pytest.approx(2 * dfma / 1e12)
+    assert r["fp64_issue"]["frac"] == pytest.approx(19 * n / (t_ms * 1e-3) / dfma)
+    assert r["hbm_gbs"] == pytest.approx(72 * n / (t_ms * 1e-3) / 1e9)
+    assert r["traffic"] is None
+    # a refinement kernel counts only the launches of sweeps that ran
+    r2 = bench.dominant_roofline("thomas_refine", (1.0, 80), st, 20, True, 4, spec, n, 6504.1, "m",
+                                 dfma, "no-such-workload")
+    assert r2["bound"] == "hbm" and r2["launches_timed"] == 20

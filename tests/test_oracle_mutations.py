@@ -18,7 +18,7 @@ SRC = os.path.join(ROOT, "oracle", "oracle.c")
 
 PINS = ("exact_rational or eigenmodes or apply_then_solve or divergence_free or "
         "constant_density or dense_solves or stretched_z or correction_identity or "
-        "triperiodic or rotation_commutes or vc_ or acdi_")
+        "triperiodic or rotation_commutes or vc_ or acdi_ or poisson_bc")
 
 MUTATIONS = [
     ("grad_sign", "gx[c] = (q[IDX(g, i + 1, j, k)] - q[c]) / g->dx;",
@@ -82,6 +82,16 @@ MUTATIONS = [
      "return eps * log(a / b);"),
     ("acdi_z_wall_ghost", "zhi = 2.0 * zf[nz] - zc(&g, k);", "zhi = zf[nz];"),
     ("acdi_z_seam_distance", "zlo = zc(&g, nz - 1) - (zf[nz] - zf[0]);", "zlo = zc(&g, nz - 1);"),
+    # Dirichlet and mixed x/y boundary kinds of the Poisson solve
+    ("bc_ghost_sign", "    return dir ? -1.0 : 1.0;", "    return dir ? 1.0 : -1.0;"),
+    ("bc_mixed_side", "int dir = (bc == 2) || (bc == 3 && side == 1) || (bc == 4 && side == 0);",
+     "int dir = (bc == 2) || (bc == 3 && side == 0) || (bc == 4 && side == 1);"),
+    ("bc_quarter_wave_length", "static int ext_len(int n, int bc) { return bc == 0 ? n : (bc <= 2 ? 2 * n : 4 * n); }",
+     "static int ext_len(int n, int bc) { return bc == 0 ? n : 2 * n; }"),
+    ("bc_odd_extension_sign", "    if (bc == 2) {\n        *sign = -1.0;", "    if (bc == 2) {\n        *sign = 1.0;"),
+    ("bc_quarter_wave_mirror_sign", "        s2 = bc == 3 ? 1.0 : -1.0;", "        s2 = bc == 3 ? -1.0 : 1.0;"),
+    ("bc_gauge_when_regular", "    if (sing) remove_weighted_mean(&g, p);\n    free(wxf);",
+     "    remove_weighted_mean(&g, p);\n    free(wxf);"),
     ("z_matrix_wrap_column", "A[(size_t)k * nz + (k + nz - 1) % nz] += lo[k];",
      "A[(size_t)k * nz + (k + nz - 2) % nz] += lo[k];"),
     ("neumann_extension", "return (bc == 0 || e < n) ? e : 2 * n - 1 - e;",

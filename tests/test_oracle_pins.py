@@ -793,3 +793,141 @@ def test_acdi_phi_outside_unit_interval_stays_finite():
     # the unbounded quotient would give NaN here
     with np.errstate(invalid="ignore"):
         assert np.isnan(np.log((phi + 1e-100) / (1 - phi + 1e-100))).any()
+
+
+# --------------------------------------------------------------------------
+# The Poisson solve with Dirichlet and mixed x/y boundary kinds (bc 2: p = 0
+# on both boundary faces; 3: Neumann near, Dirichlet far; 4: Dirichlet near,
+# Neumann far), the boundary kinds of the CaNS fast solver
+# --------------------------------------------------------------------------
+def _poisson_golden():
+    return sorted(glob.glob(os.path.join(GOLDEN, "poisson_*.json")))
+
+
+@pytest.mark.parametrize("path", _poisson_golden(), ids=lambda p: os.path.basename(p))
+@pytest.mark.parametrize("dense", [False, True])
+def test_poisson_bc_matches_exact_rational(path, dense):
+    d = json.load(open(path))
+    nx, ny, nz = d["nx"], d["ny"], d["nz"]
+    shape = (nz, ny, nx)
+    zf = np.array([float(Q(z)) for z in d["zf"]])
+    g = O.Grid(nx, ny, nz, float(Q(d["dx"])), float(Q(d["dy"])), zf, d["bcx"], d["bcy"], d["bcz"])
+    f = np.array(d["inputs"]["f"]).reshape(shape)
+    p = O.poisson(g, f, dense=dense)
+    assert relerr(p, np.array(d["expected"]["p"]).reshape(shape)) < 1e-13
+
+
+def _mode_bc(n, h, m, bc):
+    """Closed-form eigenvector of the second difference of kind bc at the
+    cell centres, and its eigenvalue."""
+    x = np.arange(n) + 0.5
+    if bc == 2:    # p = 0 on both faces: sin(pi (m+1) x / n)
+        return np.sin(np.pi * (m + 1) * x / n), -4 / h ** 2 * np.sin(np.pi * (m + 1) / (2 * n)) ** 2
+    if bc == 3:    # zero flux near, p = 0 far: cos(pi (m + 1/2) x / n)
+        return np.cos(np.pi * (m + 0.5) * x / n), -4 / h ** 2 * np.sin(np.pi * (m + 0.5) / (2 * n)) ** 2
+    if bc == 4:    # p = 0 near, zero flux far: sin(pi (m + 1/2) x / n)
+        return np.sin(np.pi * (m + 0.5) * x / n), -4 / h ** 2 * np.sin(np.pi * (m + 0.5) / (2 * n)) ** 2
+    if bc == 1:
+        return np.cos(np.pi * m * x / n), -4 / h ** 2 * np.sin(np.pi * m / (2 * n)) ** 2
+    i = np.arange(n)
+    return np.cos(2 * np.pi * m * i / n), -4 / h ** 2 * np.sin(np.pi * m / n) ** 2
+
+
+@pytest.mark.parametrize("bcx,bcy,bcz", [(2, 0, 1), (3, 2, 1), (4, 1, 1), (2, 3, 0), (1, 4, 0),
+                                         (3, 3, 1), (4, 4, 0), (2, 2, 1)])
+def test_poisson_bc_eigenmodes_closed_form(bcx, bcy, bcz):
+    """Products of closed-form eigenvectors are solved exactly (to round-off)
+    by both oracle paths, and L_h maps them to lambda times themselves."""
+    nx, ny, nz = 12, 9, 8
+    dx, dy, lz = 1.0 / nx, 0.7 / ny, 1.3
+    g = O.Grid(nx, ny, nz, dx, dy, uniform_zf(nz, lz), bcx, bcy, bcz)
+    for mx, my, mz in ((0, 0, 0), (0, 1, 0), (3, 2, 1), (nx - 1, ny - 1, nz - 1), (5, 4, 2)):
+        qx, lx = _mode_bc(nx, dx, mx, bcx)
+        qy, ly = _mode_bc(ny, dy, my, bcy)
+        if bcz == 1:
+            qz, lzv = _mode_bc(nz, lz / nz, mz, 1)
+        else:
+            qz, lzv = _mode_bc(nz, lz / nz, mz, 0)
+        q = qz[:, None, None] * qy[None, :, None] * qx[None, None, :]
+        lam = lx + ly + lzv
+        if lam == 0:
+            continue
+        f = lam * q
+        assert relerr(O.apply_L(g, q), f) < 1e-13
+        for dense in (False, True):
+            assert relerr(O.poisson(g, f, dense=dense), q) < 1e-12, (mx, my, mz, dense)
+
+
+def _lap1d_bc(n, h, bc):
+    """Dense second-difference matrix of one direction from its ghost rules
+    (numpy; independent of the oracle's loops)."""
+    A = np.zeros((n, n))
+    for i in range(n):
+        A[i, i] -= 2
+        for s in (-1, 1):
+            j = i + s
+            if 0 <= j < n:
+                A[i, j] += 1
+            elif bc == 0:
+                A[i, j % n] += 1
+            else:
+                side = 0 if j < 0 else 1
+                dirichlet = bc == 2 or (bc == 3 and side == 1) or (bc == 4 and side == 0)
+                A[i, i] += -1 if dirichlet else 1
+    return A / h ** 2
+
+
+@pytest.mark.parametrize("bcx,bcy", [(2, 0), (3, 1), (4, 2), (2, 4), (3, 3)])
+def test_poisson_bc_operator_and_solve_match_numpy_assembly(bcx, bcy):
+    """The operator against a Kronecker-sum assembly of 1-D matrices built
+    from the ghost rules, and both oracle solves against numpy's dense solve
+    of that matrix (a non-singular system: no gauge)."""
+    nx, ny, nz = 6, 5, 4
+    dx, dy, dz = 0.3, 0.25, 0.2
+    g = O.Grid(nx, ny, nz, dx, dy, uniform_zf(nz, nz * dz), bcx, bcy, I.NEUMANN)
+    Ax, Ay, Az = _lap1d_bc(nx, dx, bcx), _lap1d_bc(ny, dy, bcy), _lap1d_bc(nz, dz, 1)
+    Ix, Iy, Iz = np.eye(nx), np.eye(ny), np.eye(nz)
+    L = np.kron(Iz, np.kron(Iy, Ax)) + np.kron(Iz, np.kron(Ay, Ix)) + np.kron(Az, np.kron(Iy, Ix))
+    rng = np.random.default_rng(bcx * 10 + bcy)
+    q = rng.standard_normal((nz, ny, nx))
+    assert relerr(O.apply_L(g, q), (L @ q.ravel()).reshape(q.shape)) < 1e-14
+    f = rng.standard_normal((nz, ny, nx))
+    ref = np.linalg.solve(L, f.ravel()).reshape(f.shape)
+    for dense in (False, True):
+        assert relerr(O.poisson(g, f, dense=dense), ref) < 1e-12
+
+
+@pytest.mark.parametrize("bcx,bcy,bcz,beta", [(2, 0, 1, 1.4), (3, 4, 0, 0.0), (4, 2, 1, 1.2),
+                                              (1, 3, 0, 1.1)])
+def test_poisson_bc_apply_then_solve(bcx, bcy, bcz, beta):
+    """f := L_h q for a random q on stretched and periodic z: the solve
+    returns q itself (p is unique with a Dirichlet face, no gauge)."""
+    nx, ny, nz = 12, 8, 10
+    zf = I.z_faces(nz, 1.0, beta)
+    g = O.Grid(nx, ny, nz, 1.0 / nx, 0.8 / ny, zf, bcx, bcy, bcz)
+    q = np.random.default_rng(5 + bcx).standard_normal(g.shape)
+    f = O.apply_L(g, q)
+    assert relerr(O.poisson(g, f), q) < 1e-12
+    assert relerr(O.poisson(g, f, dense=True), q) < 1e-12
+
+
+def test_poisson_bc_one_dimensional_against_scipy_transforms():
+    """A right-hand side constant in y and in z (periodic y, walls in z)
+    reduces the solve to one x-line: p = T^-1 [T(f) / lambda] with T scipy's
+    DST-II (p = 0 on both faces), DCT-IV (zero flux near, p = 0 far) or
+    DST-IV (p = 0 near, zero flux far), an independent library routine."""
+    import scipy.fft as sf
+    nx, ny, nz, dx = 16, 4, 3, 1.0 / 16
+    f1 = np.random.default_rng(9).standard_normal(nx)
+    f = np.broadcast_to(f1, (nz, ny, nx)).copy()
+    m = np.arange(nx)
+    for bc, kind, fwd, inv, lam in (
+            (2, "dst", 2, 3, -4 / dx ** 2 * np.sin(np.pi * (m + 1) / (2 * nx)) ** 2),
+            (3, "dct", 4, 4, -4 / dx ** 2 * np.sin(np.pi * (m + 0.5) / (2 * nx)) ** 2),
+            (4, "dst", 4, 4, -4 / dx ** 2 * np.sin(np.pi * (m + 0.5) / (2 * nx)) ** 2)):
+        T = getattr(sf, kind)
+        ref = T(T(f1, type=fwd, norm="ortho") / lam, type=inv, norm="ortho")
+        g = O.Grid(nx, ny, nz, dx, 0.25, uniform_zf(nz), bc, I.PERIODIC, I.NEUMANN)
+        p = O.poisson(g, f)
+        assert relerr(p[1, 2], ref) < 1e-13, bc
+        assert relerr(p, np.broadcast_to(ref, p.shape)) < 1e-13
