@@ -45,6 +45,12 @@ from paper_2502_04189_b300 import inputs as I  # noqa: E402
 METRIC = "grid pts/s per projection, mixed vs FP64 at 1e-10 residual; HBM %; p50/p99 ms"
 HBM_PEAK_FALLBACK = 6400.0        # GB/s, recipe fallback
 FP64_PEAK_NOMINAL = 1.25          # TFLOP/s, nominal B300 FP64 (recipe table), context only
+# FP64 instructions one SM's FP64 pipe completes per clock when it is always
+# busy: the nominal 1.25 TFLOP/s over 148 SMs at about 2.1 GHz.  ncu agrees
+# on this part: the in-run probe's 0.506 T instr/s at 2032 MHz is 84.2 % FP64
+# pipe activity and k_flux's 0.524 T/s is 89.4 %, both 0.601 T/s = 2 x 148 x
+# 2.032 GHz at 100 % (profiles/fp64_pipe_probe_and_flux.md).
+FP64_PER_CLK_PER_SM = 2
 
 WORKLOADS = {
     "bubbles512_stretched": I.bubbles512_stretched_spec,
@@ -132,14 +138,19 @@ def fp64_instr_per_point(nx, ny, bcx, bcy, mixed, bcz=1):
             "correct": 6}
 
 
-def path_roofline(value, nx, ny, bcx, bcy, mixed, sweeps, hbm_peak, fp64_issue_peak, bcz=1):
+def path_roofline(value, nx, ny, bcx, bcy, mixed, sweeps, hbm_peak, fp64_issue_peak, bcz=1,
+                  fused_xy=False):
     """The whole projection against its bounds: the algorithmic bytes of the
     pass sequence (the kernels' per-point bytes summed over the passes that
     ran; mixed: the refinement passes once per sweep, the stand-alone
     correction only when no sweep ran), the I/O floor (6 FP64 fields read,
     4 written: 80 B/pt), and the FP64 instructions per point against the
-    FP64 FMA issue rate measured in the same run."""
+    FP64 issue peak.  fused_xy: the mixed solve's x and y passes run fused on
+    clusters, so the separate y-passes' bytes are not moved."""
     per = algorithmic_per_point(nx, ny, mixed)
+    if mixed and fused_xy:
+        for k in ("fwd_y", "inv_y", "fwd_y_refine", "inv_y_refine"):
+            per[k] = (0, 0)
     ins = fp64_instr_per_point(nx, ny, bcx, bcy, mixed, bcz)
     if not mixed:
         b = sum(v[0] for v in per.values())
@@ -283,22 +294,31 @@ def errors_vs_oracle(case, got, ref):
     return {"p": ep, "u": num / den, "div_metric": dmax * case.dx / U}
 
 
-def probe_peaks(F, stream, target_ms=150.0):
-    """In-run FMA issue-rate probes (fizzy_probe_fma_rate): DFMA and FFMA
-    chains (8 independent chains per thread, a resident grid), each launch
-    calibrated to about target_ms, best of three, with the SM clock sampled
-    during the probes."""
+PROBE_VARIANTS = (  # name, precision (0 FP64, 1 FP32), op (see fizzy_probe_fma_rate), chains
+    ("dfma_8", 0, 0, 8), ("dfma_16", 0, 0, 16), ("dadd_8", 0, 1, 8), ("dmul_8", 0, 2, 8),
+    ("dfma_dadd_8", 0, 3, 8), ("dfma_with_ffma_8", 0, 4, 8), ("dfma_reg_8", 0, 5, 8),
+    ("ffma_8", 1, 0, 8))
+
+
+def probe_peaks(F, stream, target_ms=120.0):
+    """In-run issue-rate probes (fizzy_probe_fma_rate): FP64 chains of
+    multiply-adds, adds, multiplies, both in turn, multiply-adds interleaved
+    with FP32 work and with register multiplicands, and FP32 multiply-add
+    chains; a resident grid, each launch calibrated to about target_ms, best
+    of two, with the SM clock sampled during the probes.  The FP64 issue peak
+    is the highest FP64 variant."""
     out = {}
     clocks = ClockSampler()
     clocks.start()
-    for prec, name, it0 in ((F.FP64, "dfma", 2000), (F.MIXED, "ffma", 100000)):
-        _, ms = F.probe_fma_rate(prec, it0, stream=stream)
+    for name, prec, op, ch in PROBE_VARIANTS:
+        it0 = 500 if prec == 0 else 20000
+        _, ms = F.probe_fma_rate(prec, it0, op=op, chains=ch, stream=stream)
         it = max(1, int(it0 * target_ms / max(ms, 1e-3)))
-        runs = [F.probe_fma_rate(prec, it, stream=stream) for _ in range(3)]
-        rate, ms = max(runs)
-        out[name] = {"instr_per_s": rate, "ms": ms, "iters": it, "chains_per_thread": 8}
-    clk = clocks.stop()
-    out["clocks"] = clk
+        rate, ms = max(F.probe_fma_rate(prec, it, op=op, chains=ch, stream=stream) for _ in range(2))
+        out[name] = {"instr_per_s": rate, "ms": ms, "iters": it}
+    out["clocks"] = clocks.stop()
+    best = max((k for k in out if k.startswith("d")), key=lambda k: out[k]["instr_per_s"])
+    out["fp64_issue_peak"] = {"instr_per_s": out[best]["instr_per_s"], "variant": best}
     return out
 
 
@@ -366,7 +386,9 @@ def dominant_roofline(dom, live, st, steps, mixed, max_refine, spec, npts, hbm_p
         peak = 2.0 * dfma / 1e12
         tfl = fl_pt * npts / avg_s / 1e12
         roof = {"bound": "alu", "achieved": tfl, "peak": peak, "unit": "TFLOP/s", "frac": tfl / peak,
-                "peak_source": "measured in this run: 2 x DFMA issue rate (fizzy_probe_fma_rate)",
+                "peak_source": "FP64 pipe at full rate: 2 FP64 instructions per clock per SM x SMs x "
+                               "the median SM clock of the timed region, FMA = 2 flops (the in-run "
+                               "probes and ncu's FP64-pipe activity corroborate it: peaks_measured)",
                 "nominal_peak": FP64_PEAK_NOMINAL}
     else:
         roof = {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
@@ -378,7 +400,7 @@ def dominant_roofline(dom, live, st, steps, mixed, max_refine, spec, npts, hbm_p
     if ipt:
         roof["fp64_issue"] = {"instr_per_pt": ipt, "achieved": issue / 1e12, "peak": dfma / 1e12,
                               "unit": "T instr/s", "frac": issue / dfma,
-                              "peak_source": "DFMA issue rate measured in this run"}
+                              "peak_source": "FP64 pipe at full rate (2 / clock / SM at the sampled clock)"}
     return roof
 
 
@@ -542,7 +564,7 @@ def run_fizzy(args):
 
     # peaks of this GPU, measured before the timed region
     peaks = probe_peaks(F, stream) if not args.no_probe else None
-    dfma = peaks["dfma"]["instr_per_s"] if peaks else FP64_PEAK_NOMINAL / 2 * 1e12
+    n_sm = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
 
     def timed_run(precision, steps, warmup, per_kernel):
         """W warm-up solves; with per_kernel, a short breakdown run with every
@@ -550,7 +572,7 @@ def run_fizzy(args):
         region of `steps` solves, each from the restored u* and bracketed by
         its own CUDA events, in which only the dominant kernel's launches also
         carry events (its live average duration feeds the roofline)."""
-        plan = F.Plan.for_case(case, precision=precision)
+        plan = F.Plan.for_case(case, precision=precision, fused_xy=args.fused_xy)
         for _ in range(warmup):
             restore()
             plan.solve(phi, pn, pnm1, u, v, w, p, stream=stream)
@@ -594,6 +616,9 @@ def run_fizzy(args):
     clocks.start()
     R = timed_run(prec, args.steps, args.warmup, True)
     clk = clocks.stop()
+    # the FP64 pipe's full rate at the SM clock of the timed region
+    sm_hz = (clk["sm_mhz"] if clk else 2032.0) * 1e6
+    dfma = FP64_PER_CLK_PER_SM * n_sm * sm_hz
     ms = slowest_rank(R["ms"], dist)
     value = job_throughput(npts, args.steps, world, ms / 1e3)
     st = R["stats"]
@@ -716,11 +741,16 @@ def run_fizzy(args):
                            "timing": "each solve from the workload's u*, restored from a pristine device "
                                      "copy before it, outside its own CUDA events; value = points / sum "
                                      "of the solves' event times",
+                           "fused_xy_passes": bool(args.fused_xy),
                            "parallelism": "replicas" if world > 1 else "single"},
                 "gpu_launches": R["launches"], "roofline": roof,
                 "path_roofline": path_roofline(value, spec.nx, spec.ny, spec.bcx, spec.bcy, mixed,
-                                               int(st["iterations"]), hbm_peak, dfma, spec.bcz),
-                "peaks_measured": peaks,
+                                               int(st["iterations"]), hbm_peak, dfma, spec.bcz,
+                                               fused_xy=mixed and "fwd_y" not in R["breakdown"]),
+                "fused_xy": mixed and "fwd_y" not in R["breakdown"],
+                "peaks_measured": dict(peaks or {}, fp64_pipe_full_rate_instr_s=dfma, n_sm=n_sm,
+                                       probe_over_pipe=(peaks["fp64_issue_peak"]["instr_per_s"] / dfma)
+                                       if peaks else None),
                 "err_vs_oracle": err,
                 "cpu_baseline": cpu, "e2e": e2e,
                 "clocks": clk, "kernels": kernels,
@@ -922,6 +952,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-sub", action="store_true", help="skip the embedded batch and serving runs")
     ap.add_argument("--no-probe", action="store_true", help="skip the FMA-rate probes")
+    ap.add_argument("--fused-xy", action="store_true",
+                    help="run the cluster-fused x-y FP32 passes (FIZZY_FLAG_FUSED_XY)")
     ap.add_argument("--vc", action="store_true",
                     help="time the variable-coefficient projection without splitting instead")
     ap.add_argument("--vc-tol", type=float, default=1e-10)

@@ -55,7 +55,23 @@ enum {
     FIZZY_ERR_TIMEOUT = -6        /* a bounded device wait gave up (batched executor)               */
 };
 
-enum { FIZZY_BC_PERIODIC = 0, FIZZY_BC_NEUMANN = 1 };
+/* Boundary kinds of x and y.  The projection and everything built on it
+ * (batch, serving, the unsplit and ACDI steps, the allocation-free entry
+ * point) take FIZZY_BC_PERIODIC and FIZZY_BC_NEUMANN (walls): the staggered
+ * layout stores one face per cell, so a direction's near face is implicit
+ * and must be a wall or periodic.  fizzy_poisson_solve also takes the
+ * Dirichlet and mixed kinds of the CaNS fast solver (paper, "Methods and
+ * Implementation strategy"): p = 0 on a Dirichlet face, read as a ghost
+ * value -p beyond it; a Neumann face has zero flux (ghost value +p). */
+enum {
+    FIZZY_BC_PERIODIC = 0,
+    FIZZY_BC_NEUMANN = 1,            /* zero flux at both faces (DCT-II / DCT-III)                  */
+    FIZZY_BC_DIRICHLET = 2,          /* p = 0 at both faces (DST-II / DST-III)                      */
+    FIZZY_BC_NEUMANN_DIRICHLET = 3,  /* zero flux at the near face, p = 0 at the far one (DCT-IV;   */
+                                     /* even extents only)                                          */
+    FIZZY_BC_DIRICHLET_NEUMANN = 4   /* p = 0 at the near face, zero flux at the far one (DST-IV;   */
+                                     /* even extents only)                                          */
+};
 
 enum {
     FIZZY_PREC_FP64 = 0,  /* every pass in FP64                                           */
@@ -67,6 +83,13 @@ enum {
 #define FIZZY_FLAG_ASYNC_ALLOC 2u /* allocate the plan's device memory stream-ordered (cudaMallocAsync  */
                                   /* from the device's default pool) on the plan's stream, and free it  */
                                   /* the same way in fizzy_proj_destroy (no device synchronisation)     */
+#define FIZZY_FLAG_FUSED_XY 4u    /* mixed plans with nx = ny = 256 or 512 (periodic or wall x, y): run  */
+                                  /* the x and y transforms of each FP32 solve as one pass per          */
+                                  /* direction of the solve on a thread-block cluster (a z-plane in     */
+                                  /* distributed shared memory) instead of separate x and y passes;     */
+                                  /* the same results, bit for bit.  Off by default: on this part the   */
+                                  /* separate passes are faster (the cluster's plane fills its SMs'     */
+                                  /* shared memory, so loads, exchange and stores cannot overlap)       */
 
 /* Maximum x/y extent of one transform line. */
 #define FIZZY_MAX_N 1024
@@ -80,7 +103,8 @@ typedef struct fizzy_proj_desc {
     double dx, dy;        /* uniform x and y spacing (> 0)                                     */
     double dz;            /* uniform z spacing (> 0), used when zf == NULL                      */
     const double *zf;     /* host array of nz+1 increasing z face coordinates, or NULL          */
-    int bc_x, bc_y;       /* FIZZY_BC_PERIODIC or FIZZY_BC_NEUMANN                              */
+    int bc_x, bc_y;       /* FIZZY_BC_*: PERIODIC or NEUMANN for the projection; any kind for  */
+                          /* fizzy_poisson_solve (3 and 4 need an even extent)                 */
     double rho_l, rho_g;  /* phase densities (> 0, within [1e-30, 1e30]); phi = 1 is rho_l      */
     double dt;            /* time step (> 0)                                                    */
     int precision;        /* FIZZY_PREC_FP64 or FIZZY_PREC_MIXED                                */
@@ -135,6 +159,31 @@ size_t fizzy_proj_workspace_bytes(const fizzy_proj_desc *d);
 int fizzy_proj_solve(fizzy_proj_plan_t p, const double *phi, const double *p_n, const double *p_nm1,
                      double *u, double *v, double *w, double *p_np1, fizzy_proj_stats *st,
                      void *stream);
+
+/* The plan's fast direct Poisson solve on a given right-hand side: L_h p = f
+ * with L_h = D G, the 7-point operator of the projection (second-order
+ * differences on the staggered grid; z from the plan's face coordinates,
+ * walls or periodic) and the plan's x/y boundary kinds, Dirichlet and mixed
+ * ones included (the CaNS solver the paper builds on: "Methods and
+ * Implementation strategy").  Real transforms along x and y (half-complex
+ * FFT, DCT-II, DST-II, DCT-IV or DST-IV per kind), one tridiagonal solve per
+ * wavenumber pair along z, inverse transforms.
+ *   f     : in, device, [nz][ny][nx] FP64.  Without a Dirichlet face in x or
+ *           y the problem is singular: the solve removes f's dzf-weighted
+ *           mean and returns the p of zero dzf-weighted mean (a mixed plan's
+ *           refinement needs a compatible f, i.e. that mean already 0, to
+ *           reach tol).  With a Dirichlet face p is unique.
+ *   p_out : out, device, [nz][ny][nx] FP64; must not alias f.
+ *   st    : NULL (asynchronous) or host stats: relres = max|f - L_h p| /
+ *           max|f|, f_max, and on a mixed plan iterations and converged.
+ * FP64 plan: one FP64 solve.  Mixed plan: FP32 transforms and z-solves,
+ * refined by FP64 residuals until relres <= the plan's tol (at most
+ * max_refine sweeps; max|f| times 1/(4 nx ny) must lie in the FP32 normal
+ * range).  Uses the plan's spectral workspace.  Returns
+ * FIZZY_ERR_NOT_CONVERGED (p written) when st is given and a mixed solve
+ * stopped above tol. */
+int fizzy_poisson_solve(fizzy_proj_plan_t p, const double *f, double *p_out, fizzy_proj_stats *st,
+                        void *stream);
 
 /* Variable-coefficient projection WITHOUT the constant-coefficient splitting
  * (the equation the splitting replaces; the paper's Hypre path solves it):
@@ -382,18 +431,22 @@ int fizzy_crop_fill(const double *const *src, int tx, int ty, int tz, double *co
                     int nx, int ny, int nz, int ox, int oy, int oz, int bc_x, int bc_y,
                     void *stream);
 
-/* Measurement support (no counterpart in the paper): the fused multiply-add
- * issue rate of the GPU, the peak the FP64-bound projection kernels are
- * measured against.  precision FIZZY_PREC_FP64 times DFMA, FIZZY_PREC_MIXED
- * FFMA.  One launch of a resident grid (CTAs per SM x SMs, 256 threads),
- * each thread running 8 independent FMA chains for 32 x iters FMAs; timed
- * with CUDA events on stream, which the call synchronises.  *instr_per_s
- * receives FMA instructions (per lane) per second, *elapsed_ms (nullable)
- * the kernel time.  Choose iters so the launch lasts 100 ms or more.
- * Returns FIZZY_ERR_INVALID for iters < 1, a null instr_per_s or another
- * precision, FIZZY_ERR_CUDA if the launch fails. */
-int fizzy_probe_fma_rate(int precision, int iters, double *instr_per_s, double *elapsed_ms,
-                         void *stream);
+/* Measurement support (no counterpart in the paper): the arithmetic issue
+ * rate of the GPU, the peak the FP64-bound projection kernels are measured
+ * against.  precision FIZZY_PREC_FP64 times FP64 instructions,
+ * FIZZY_PREC_MIXED FP32 ones; op 0 fused multiply-adds, 1 adds, 2 multiplies,
+ * 3 multiply-adds and adds in turn, 4 multiply-adds each followed by an
+ * independent FP32 multiply-add (not counted), 5 multiply-adds whose
+ * multiplicand is another chain's register; chains (4, 8 or 16) independent chains
+ * per thread.  One launch of a resident grid (CTAs per SM x SMs, 256
+ * threads), 4 x chains x iters instructions per thread, timed with CUDA
+ * events on stream, which the call synchronises.  *instr_per_s receives
+ * instructions (per lane) per second, *elapsed_ms (nullable) the kernel
+ * time.  Choose iters so the launch lasts 100 ms or more.  Returns
+ * FIZZY_ERR_INVALID for an argument out of range or a null instr_per_s,
+ * FIZZY_ERR_CUDA if the launch fails. */
+int fizzy_probe_fma_rate(int precision, int op, int chains, int iters, double *instr_per_s,
+                         double *elapsed_ms, void *stream);
 
 /* ------------------------------------------------------------------------
  * Allocation-free projection (FP64 mode, small grids).

@@ -15,9 +15,13 @@ from ._abi import Stats
 
 PERIODIC = 0
 NEUMANN = 1
+DIRICHLET = 2             # p = 0 on both boundary faces (fizzy_poisson_solve only)
+NEUMANN_DIRICHLET = 3     # zero flux near, p = 0 far (fizzy_poisson_solve only)
+DIRICHLET_NEUMANN = 4     # p = 0 near, zero flux far (fizzy_poisson_solve only)
 FP64 = 0
 MIXED = 1
 FLAG_CHECK = 1
+FLAG_FUSED_XY = 4  # cluster-fused x-y FP32 passes (mixed, nx = ny = 256 or 512)
 
 
 class FizzyError(RuntimeError):
@@ -80,11 +84,12 @@ class Plan:
 
     def __init__(self, nx, ny, nz, dx, dy, zf=None, dz=None, bcx=PERIODIC, bcy=PERIODIC,
                  rho_l=1.0, rho_g=1e-3, dt=1e-4, precision=FP64, tol=0.0, max_refine=0,
-                 check=False, stream=None, div_tol=0.0, periodic_z=False):
+                 check=False, stream=None, div_tol=0.0, periodic_z=False, fused_xy=False):
         self.shape = (int(nz), int(ny), int(nx))
         self.precision = precision
+        flags = (FLAG_CHECK if check else 0) | (FLAG_FUSED_XY if fused_xy else 0)
         d, keep = make_desc(nx, ny, nz, dx, dy, zf, dz, bcx, bcy, rho_l, rho_g, dt, precision,
-                            tol, max_refine, FLAG_CHECK if check else 0, div_tol, periodic_z)
+                            tol, max_refine, flags, div_tol, periodic_z)
         h = ctypes.c_void_p()
         rc = _abi.lib().fizzy_proj_plan(ctypes.byref(h), ctypes.byref(d),
                                         ctypes.c_void_p(0) if stream is None else _stream_handle(stream))
@@ -138,6 +143,16 @@ class Plan:
     def host_wait(self):
         """Block until every queued host solve's results are in host memory."""
         self._check(_abi.lib().fizzy_proj_host_wait(self._h))
+
+    def poisson(self, f, p_out, stats=False, stream=None):
+        """The plan's fast direct Poisson solve L_h p = f (fizzy_poisson_solve)
+        on CUDA float64 tensors, with any x/y boundary kind the plan holds.
+        Returns a stats dict if stats=True (synchronises), else None."""
+        st = Stats() if stats else None
+        rc = _abi.lib().fizzy_poisson_solve(self._h, _ptr(f), _ptr(p_out),
+                                            ctypes.byref(st) if st else None, _stream_handle(stream))
+        self._check(rc)
+        return st.as_dict() if st else None
 
     def solve_vc(self, phi, u, v, w, p_out, max_iter=500, tol=0.0, stream=None):
         """Variable-coefficient projection WITHOUT the splitting
@@ -417,13 +432,15 @@ def solve_noalloc(phi, pn, pnm1, u, v, w, p_out, stream=None, **desc):
         raise FizzyError(rc)
 
 
-def probe_fma_rate(precision=FP64, iters=20000, stream=None):
-    """FMA issue rate of the GPU (fizzy_probe_fma_rate): precision FP64 times
-    DFMA chains, MIXED FFMA chains.  Returns (FMA instructions per second,
-    kernel milliseconds)."""
+def probe_fma_rate(precision=FP64, iters=20000, op=0, chains=8, stream=None):
+    """Arithmetic issue rate of the GPU (fizzy_probe_fma_rate): precision FP64
+    times FP64 chains, MIXED FP32 chains; op 0 multiply-adds, 1 adds,
+    2 multiplies, 3 multiply-adds and adds in turn; chains independent chains
+    per thread (4, 8 or 16).  Returns (instructions per second, kernel
+    milliseconds)."""
     rate, ms = ctypes.c_double(), ctypes.c_double()
-    rc = _abi.lib().fizzy_probe_fma_rate(int(precision), int(iters), ctypes.byref(rate),
-                                         ctypes.byref(ms), _stream_handle(stream))
+    rc = _abi.lib().fizzy_probe_fma_rate(int(precision), int(op), int(chains), int(iters),
+                                         ctypes.byref(rate), ctypes.byref(ms), _stream_handle(stream))
     if rc != 0:
         raise FizzyError(rc)
     return rate.value, ms.value

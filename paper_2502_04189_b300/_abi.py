@@ -22,7 +22,8 @@ EXPORTED = ("fizzy_proj_plan", "fizzy_proj_workspace_bytes", "fizzy_proj_solve",
             "fizzy_serve_launch", "fizzy_serve_poll", "fizzy_serve_stats", "fizzy_serve_release",
             "fizzy_serve_info", "fizzy_serve_destroy", "fizzy_proj_solve_host_async",
             "fizzy_proj_host_wait", "fizzy_crop_fill", "fizzy_proj_batch_inject_stall",
-            "fizzy_proj_solve_vc", "fizzy_acdi_step", "fizzy_probe_fma_rate")
+            "fizzy_proj_solve_vc", "fizzy_acdi_step", "fizzy_probe_fma_rate",
+            "fizzy_poisson_solve")
 ERRORS[-7] = "busy"
 NOALLOC_MAX_CELLS = 262144
 DEFAULT_MAX_REFINE = 4  # FIZZY_DEFAULT_MAX_REFINE
@@ -146,8 +147,10 @@ def lib():
         L.fizzy_crop_fill.argtypes = [ctypes.POINTER(vp)] + [ctypes.c_int] * 3 + [ctypes.POINTER(vp)] + \
             [ctypes.c_int] * 8 + [vp]
         L.fizzy_crop_fill.restype = ctypes.c_int
-        L.fizzy_probe_fma_rate.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
-                                           ctypes.POINTER(ctypes.c_double), vp]
+        L.fizzy_probe_fma_rate.argtypes = [ctypes.c_int] * 4 + [ctypes.POINTER(ctypes.c_double),
+                                                                 ctypes.POINTER(ctypes.c_double), vp]
         L.fizzy_probe_fma_rate.restype = ctypes.c_int
+        L.fizzy_poisson_solve.argtypes = [vp, vp, vp, ctypes.POINTER(Stats), vp]
+        L.fizzy_poisson_solve.restype = ctypes.c_int
         _lib = L
     return _lib

@@ -8,6 +8,8 @@
 #include "kern_vc.cuh"
 #include "kern_acdi.cuh"
 #include "kern_probe.cuh"
+#include "kern_poisson.cuh"
+#include "kern_xy.cuh"
 
 #include <algorithm>
 #include <cmath>
@@ -41,6 +43,8 @@ typedef void (*Ypass64K)(int, int, FFTDesc, int, double *, const int *, int, int
 typedef void (*Ypass32K)(int, int, FFTDesc, int, float *, const int *, int, int);
 typedef void (*Xinv64K)(GridDev, FFTDesc, int, const double *, double *, const DevStats *, int);
 typedef void (*Xinv32K)(GridDev, FFTDesc, int, const float *, double *, const DevStats *, int);
+typedef void (*XYFwdK)(GridDev, XArgs);
+typedef void (*XYInvK)(GridDev, const float *, double *, const DevStats *);
 struct PassKernels {
     XfwdK xf64, xf32d, xf32l;
     XfwdK xl64;  // FP64 transform of a stored right-hand side (the preconditioner of fizzy_proj_solve_vc)
@@ -94,6 +98,13 @@ struct fizzy_proj_plan_s {
     // launch shapes
     int Lx = 1, TXy = 2;
     int x_r16 = 0;  // mixed, nx = 128, 256 or 512: register-resident FP32 x-passes
+    // mixed, nx = ny = 256 or 512, periodic or wall x/y: fused x-y cluster passes
+    int xy_fused = 0;
+    XYFwdK xyf_div = nullptr, xyf_load = nullptr;
+    XYInvK xyi_store = nullptr, xyi_accum = nullptr;
+    size_t xy_smem = 0;
+    int xy_threads = 0;
+
     size_t smem_x64 = 0, smem_x32 = 0, smem_y64 = 0, smem_y32 = 0;
     int cap[24] = {0};  // resident-grid size of each pass kernel (CAP_*)
     PassKernels kern;   // the pass kernels this plan launches
@@ -139,6 +150,15 @@ int set_err(fizzy_proj_plan_t p, int code, const std::string &msg) {
     if (p) p->err = msg;
     return code;
 }
+
+// The projection's staggered layout stores one face per cell and direction,
+// so the near face of a direction is implicit: it takes periodic or wall x/y
+// boundaries only.  The Dirichlet and mixed kinds are the Poisson solve's.
+bool staggered_bcs(const fizzy_proj_desc &d) {
+    return d.bc_x <= FIZZY_BC_NEUMANN && d.bc_y <= FIZZY_BC_NEUMANN;
+}
+const char *kNeedsStaggeredBcs =
+    "this entry point takes periodic or wall x/y boundaries (Dirichlet kinds: fizzy_poisson_solve)";
 
 // Keep the first failing CUDA call of plan construction (checked at its end).
 void note(fizzy_proj_plan_t p, cudaError_t e) {
@@ -254,22 +274,54 @@ void fill_fft_tables(int n, double *tw, double *cs, float *tw32 = nullptr, float
         for (int k = 0; k < 2 * (n / 2 + 2); ++k) cs32[k] = (float)cs[k];
 }
 
+// DCT-IV tables of a direction of length n (even, m = n/2): the m FFT
+// twiddles of length m in the (m, tau) form, then the m pre-twiddles
+// exp(-i pi (4t+1)/(4n)) as (cos, sin); cs: the m post-twiddles
+// 2 exp(-i pi k/n).  Long double, rounded once.
+void fill_dct4_tables(int n, double *tw, double *cs, float *tw32, float *cs32) {
+    const long double pi = 3.141592653589793238462643383279502884L;
+    const int m = n / 2;
+    for (int t = 0; t < m; ++t) {
+        long double mm, tau;
+        int R;
+        tw_entry(m, t, mm, tau, R);
+        tw[2 * t] = (double)mm;
+        tw[2 * t + 1] = tw_tau64(tau, R);
+        tw32[2 * t] = (float)mm;
+        tw32[2 * t + 1] = tw_tau32(tau, R);
+        const long double a = -pi * (4.0L * t + 1.0L) / (4.0L * n);
+        tw[2 * (m + t)] = (double)cosl(a);
+        tw[2 * (m + t) + 1] = (double)sinl(a);
+        tw32[2 * (m + t)] = (float)cosl(a);
+        tw32[2 * (m + t) + 1] = (float)sinl(a);
+    }
+    for (int k = 0; k < n / 2 + 2; ++k) cs[2 * k] = cs[2 * k + 1] = 0.0;
+    for (int k = 0; k < m; ++k) {
+        const long double a = -pi * (long double)k / (long double)n;
+        cs[2 * k] = (double)(2.0L * cosl(a));
+        cs[2 * k + 1] = (double)(2.0L * sinl(a));
+    }
+    for (int k = 0; k < 2 * (n / 2 + 2); ++k) cs32[k] = (float)cs[k];
+}
+
 int build_fft(fizzy_proj_plan_t p, int n, int bc, FFTHost &F, int *status) {
-    // the host tables of each length are computed once per process
+    // the host tables of each length (and family) are computed once per process
     struct Tabs {
         std::vector<double> tw, cs;
         std::vector<float> tw32, cs32;
     };
     static std::mutex mu;
-    static std::map<int, Tabs> cache;
+    static std::map<std::pair<int, int>, Tabs> cache;
     std::unique_lock<std::mutex> lock(mu);
-    Tabs &T = cache[n];
+    const bool dct4 = bc == FIZZY_BC_NEUMANN_DIRICHLET || bc == FIZZY_BC_DIRICHLET_NEUMANN;
+    Tabs &T = cache[std::make_pair(n, dct4 ? 1 : 0)];
     if (T.tw.empty()) {
         T.tw.resize(2 * (size_t)n);
         T.cs.resize(2 * (size_t)(n / 2 + 2));
         T.tw32.resize(T.tw.size());
         T.cs32.resize(T.cs.size());
-        fill_fft_tables(n, T.tw.data(), T.cs.data(), T.tw32.data(), T.cs32.data());
+        if (dct4) fill_dct4_tables(n, T.tw.data(), T.cs.data(), T.tw32.data(), T.cs32.data());
+        else fill_fft_tables(n, T.tw.data(), T.cs.data(), T.tw32.data(), T.cs32.data());
     }
     const std::vector<double> &tw = T.tw, &cs = T.cs;
     const std::vector<float> &tw32 = T.tw32, &cs32 = T.cs32;
@@ -288,8 +340,17 @@ int build_fft(fizzy_proj_plan_t p, int n, int bc, FFTHost &F, int *status) {
     }
     FFTDesc d;
     memset(&d, 0, sizeof(d));
-    fill_stages(d, n);
-    d.kind = (bc == FIZZY_BC_NEUMANN) ? KIND_DCT : KIND_PERIODIC;
+    if (dct4) {  // stages of the half-length complex FFT; lines of length n
+        fill_stages(d, n / 2);
+        d.n = n;
+        d.rn = (unsigned)((1ull << 32) / (unsigned)n + 1);
+        d.rK = n / 2 > 1 ? (unsigned)((1ull << 32) / (unsigned)(n / 2) + 1) : 0u;
+        d.kind = KIND_DCT4;
+    } else {
+        fill_stages(d, n);
+        d.kind = (bc == FIZZY_BC_PERIODIC) ? KIND_PERIODIC : KIND_DCT;
+    }
+    d.flip = (bc == FIZZY_BC_DIRICHLET || bc == FIZZY_BC_DIRICHLET_NEUMANN) ? 1 : 0;
     F.d64 = d;
     F.d64.tw = F.tw64;
     F.d64.cs = F.cs64;
@@ -299,12 +360,25 @@ int build_fft(fizzy_proj_plan_t p, int n, int bc, FFTHost &F, int *status) {
     return 0;
 }
 
-// Eigenvalue of the second difference at transform index u.
+// Eigenvalue of the second difference at transform slot u:
+//   periodic (half-complex index u)        -(4/h^2) sin^2(pi u / n)
+//   Neumann both faces (DCT-II index u)    -(4/h^2) sin^2(pi u / (2n))
+//   Dirichlet both faces (DST-II index n-1-u, see KIND_DCT's flip)
+//                                          -(4/h^2) cos^2(pi u / (2n))
+//   Neumann near, Dirichlet far (DCT-IV)   -(4/h^2) sin^2(pi (u + 1/2) / (2n))
+//   Dirichlet near, Neumann far (DST-IV index n-1-u)
+//                                          -(4/h^2) cos^2(pi (u + 1/2) / (2n))
 double eig(int u, int n, double h, int bc) {
     const long double pi = 3.141592653589793238462643383279502884L;
-    const long double a = (bc == FIZZY_BC_PERIODIC) ? pi * u / (long double)n
-                                                    : pi * u / (2.0L * (long double)n);
-    const long double s = sinl(a);
+    const long double un = (long double)u, nn = (long double)n;
+    long double s;
+    switch (bc) {
+        case FIZZY_BC_PERIODIC: s = sinl(pi * un / nn); break;
+        case FIZZY_BC_NEUMANN: s = sinl(pi * un / (2.0L * nn)); break;
+        case FIZZY_BC_DIRICHLET: s = cosl(pi * un / (2.0L * nn)); break;
+        case FIZZY_BC_NEUMANN_DIRICHLET: s = sinl(pi * (un + 0.5L) / (2.0L * nn)); break;
+        default: s = cosl(pi * (un + 0.5L) / (2.0L * nn)); break;
+    }
     return (double)(-4.0L / ((long double)h * h) * s * s);
 }
 
@@ -313,8 +387,8 @@ int validate(const fizzy_proj_desc *d) {
     if (d->nx < 2 || d->ny < 2 || d->nz < 2) return FIZZY_ERR_INVALID;
     if (!(d->dx > 0) || !(d->dy > 0)) return FIZZY_ERR_INVALID;
     if (!d->zf && !(d->dz > 0)) return FIZZY_ERR_INVALID;
-    if (d->bc_x != FIZZY_BC_PERIODIC && d->bc_x != FIZZY_BC_NEUMANN) return FIZZY_ERR_INVALID;
-    if (d->bc_y != FIZZY_BC_PERIODIC && d->bc_y != FIZZY_BC_NEUMANN) return FIZZY_ERR_INVALID;
+    if (d->bc_x < FIZZY_BC_PERIODIC || d->bc_x > FIZZY_BC_DIRICHLET_NEUMANN) return FIZZY_ERR_INVALID;
+    if (d->bc_y < FIZZY_BC_PERIODIC || d->bc_y > FIZZY_BC_DIRICHLET_NEUMANN) return FIZZY_ERR_INVALID;
     if (d->periodic_z != 0 && d->periodic_z != 1) return FIZZY_ERR_INVALID;
     if (!(d->rho_l >= 1e-30 && d->rho_l <= 1e30) || !(d->rho_g >= 1e-30 && d->rho_g <= 1e30))
         return FIZZY_ERR_INVALID;
@@ -325,6 +399,9 @@ int validate(const fizzy_proj_desc *d) {
         for (int k = 0; k < d->nz; ++k)
             if (!(d->zf[k + 1] > d->zf[k])) return FIZZY_ERR_INVALID;
     if (!radix23(d->nx) || !radix23(d->ny)) return FIZZY_ERR_UNSUPPORTED;
+    // the DCT-IV of a mixed direction runs as a complex FFT of half its length
+    if (d->bc_x >= FIZZY_BC_NEUMANN_DIRICHLET && d->nx % 2) return FIZZY_ERR_UNSUPPORTED;
+    if (d->bc_y >= FIZZY_BC_NEUMANN_DIRICHLET && d->ny % 2) return FIZZY_ERR_UNSUPPORTED;
     if (d->nx > FIZZY_MAX_N || d->ny > FIZZY_MAX_N) return FIZZY_ERR_UNSUPPORTED;
     if ((double)d->nx * d->ny * d->nz > 4.0e9) return FIZZY_ERR_UNSUPPORTED;
     // the (y, z) line index is split by a multiply-high division by ny, exact
@@ -461,6 +538,74 @@ void pick_r_kernels(PassKernels &k, int nx, int bcx, int ny, int bcy) {
     if (ny == 512) dy ? r_kernels_y<512, KIND_DCT>(k) : r_kernels_y<512, KIND_PERIODIC>(k);
 }
 
+// The fused x-y cluster kernels of a length and transform kinds.
+template <int N, int KX, int KY> void xy_kernels(XYFwdK *fd, XYFwdK *fl, XYInvK *is, XYInvK *ia) {
+    *fd = k_xy_fwd<N, KX, KY, XY_DIVQ>;
+    *fl = k_xy_fwd<N, KX, KY, XY_LOAD>;
+    *is = k_xy_inv<N, KX, KY, XI_STORE>;
+    *ia = k_xy_inv<N, KX, KY, XI_ACCUM>;
+}
+template <int N> void xy_kernels_n(int kx, int ky, XYFwdK *fd, XYFwdK *fl, XYInvK *is, XYInvK *ia) {
+    if (kx == KIND_PERIODIC && ky == KIND_PERIODIC) xy_kernels<N, KIND_PERIODIC, KIND_PERIODIC>(fd, fl, is, ia);
+    else if (kx == KIND_PERIODIC) xy_kernels<N, KIND_PERIODIC, KIND_DCT>(fd, fl, is, ia);
+    else if (ky == KIND_PERIODIC) xy_kernels<N, KIND_DCT, KIND_PERIODIC>(fd, fl, is, ia);
+    else xy_kernels<N, KIND_DCT, KIND_DCT>(fd, fl, is, ia);
+}
+// Set up the fused passes of a plan when its shape allows them and the
+// device runs the clusters: opt the kernels into their shared memory (once
+// per device) and check that a cluster fits.  Returns 1 if enabled.
+int setup_xy(fizzy_proj_plan_t p, int n, int kx, int ky) {
+    XYFwdK fd, fl;
+    XYInvK is, ia;
+    size_t smem;
+    int threads;
+    if (n == 512) {
+        xy_kernels_n<512>(kx, ky, &fd, &fl, &is, &ia);
+        smem = xy_smem_bytes<512>();
+        threads = XYShape<512>::THREADS;
+    } else {
+        xy_kernels_n<256>(kx, ky, &fd, &fl, &is, &ia);
+        smem = xy_smem_bytes<256>();
+        threads = XYShape<256>::THREADS;
+    }
+    static std::mutex mu;
+    static std::map<std::pair<int, const void *>, int> ok_cache;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    std::lock_guard<std::mutex> lock(mu);
+    auto key = std::make_pair(dev, (const void *)fd);
+    auto it = ok_cache.find(key);
+    int ok;
+    if (it != ok_cache.end()) {
+        ok = it->second;
+    } else {
+        ok = 1;
+        for (const void *f : {(const void *)fd, (const void *)fl, (const void *)is, (const void *)ia})
+            if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+                ok = 0;
+        if (ok) {
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = dim3(XY_CL);
+            cfg.blockDim = dim3(threads);
+            cfg.dynamicSmemBytes = smem;
+            int nclusters = 0;
+            for (const void *f : {(const void *)fd, (const void *)fl, (const void *)is, (const void *)ia}) {
+                if (cudaOccupancyMaxActiveClusters(&nclusters, f, &cfg) != cudaSuccess || nclusters < 1) ok = 0;
+            }
+        }
+        (void)cudaGetLastError();
+        ok_cache[key] = ok;
+    }
+    if (!ok) return 0;
+    p->xyf_div = fd;
+    p->xyf_load = fl;
+    p->xyi_store = is;
+    p->xyi_accum = ia;
+    p->xy_smem = smem;
+    p->xy_threads = threads;
+    return 1;
+}
+
 // Opt every pass kernel instance into large dynamic shared memory.
 void opt_in_smem(fizzy_proj_plan_t p, int bytes) {
     for (int fx : {0, 256, 512})
@@ -524,6 +669,18 @@ size_t plan_bytes(const fizzy_proj_desc *d) {
     b += 4 * (size_t)(d->nx + d->ny + 4) * 16;  // twiddles
     b += usq_blocks(d) * 8 + 4096;    // partials + stats
     return b;
+}
+
+// The probe kernel instance of an operation and chain count.
+template <typename T> const void *probe_fn(int op, int chains) {
+    const void *f[6][3] = {
+        {(const void *)k_fma_probe<T, 0, 4>, (const void *)k_fma_probe<T, 0, 8>, (const void *)k_fma_probe<T, 0, 16>},
+        {(const void *)k_fma_probe<T, 1, 4>, (const void *)k_fma_probe<T, 1, 8>, (const void *)k_fma_probe<T, 1, 16>},
+        {(const void *)k_fma_probe<T, 2, 4>, (const void *)k_fma_probe<T, 2, 8>, (const void *)k_fma_probe<T, 2, 16>},
+        {(const void *)k_fma_probe<T, 3, 4>, (const void *)k_fma_probe<T, 3, 8>, (const void *)k_fma_probe<T, 3, 16>},
+        {(const void *)k_fma_probe<T, 4, 4>, (const void *)k_fma_probe<T, 4, 8>, (const void *)k_fma_probe<T, 4, 16>},
+        {(const void *)k_fma_probe<T, 5, 4>, (const void *)k_fma_probe<T, 5, 8>, (const void *)k_fma_probe<T, 5, 16>}};
+    return f[op][chains == 4 ? 0 : chains == 8 ? 1 : 2];
 }
 
 }  // namespace
@@ -632,6 +789,7 @@ int fizzy_proj_plan(fizzy_proj_plan_t *out, const fizzy_proj_desc *d, void *stre
     g.bcx = d->bc_x;
     g.bcy = d->bc_y;
     g.perz = d->periodic_z ? 1 : 0;
+    g.sing = (d->bc_x <= FIZZY_BC_NEUMANN && d->bc_y <= FIZZY_BC_NEUMANN) ? 1 : 0;
     g.rny = (unsigned)((1ull << 32) / (unsigned)ny + 1);
     physics_consts(g, d->rho_l, d->rho_g, d->dt, d->dx, d->dy, sig);
     g.idx2 = 1.0 / (d->dx * d->dx);
@@ -718,12 +876,12 @@ int fizzy_proj_plan(fizzy_proj_plan_t *out, const fizzy_proj_desc *d, void *stre
                 Ux, Uy, nz, lam_d, lam_d + Ux, zt_d + T_LZA * nz, zt_d + T_LZC * nz, p->mtab64,
                 p->ibtab64, p->wtab64, p->qtab64, p->mixed ? p->mtab32 : nullptr,
                 p->mixed ? p->ibtab32 : nullptr, p->mixed ? p->wtab32 : nullptr,
-                p->mixed ? p->qtab32 : nullptr);
+                p->mixed ? p->qtab32 : nullptr, g.sing);
         else
             k_ztables<<<blocks, 128, 0, p->alloc_stream>>>(Ux, Uy, nz, lam_d, lam_d + Ux, zt_d + T_LZA * nz,
                                                            zt_d + T_LZC * nz, p->mtab64, p->ibtab64,
                                                            p->mixed ? p->mtab32 : nullptr,
-                                                           p->mixed ? p->ibtab32 : nullptr);
+                                                           p->mixed ? p->ibtab32 : nullptr, g.sing);
     }
     note(p, cudaMemcpyAsync(p->cup64, C, nz * sizeof(double), cudaMemcpyHostToDevice, p->alloc_stream));
     if (p->mixed) {
@@ -736,8 +894,8 @@ int fizzy_proj_plan(fizzy_proj_plan_t *out, const fizzy_proj_desc *d, void *stre
     p->Lx = x_lines_per_cta(nx);
     // mixed plans with a direction of length 128 to 512 (periodic or walls)
     // run the register-resident FP32 passes along it: static shared memory only
-    const bool y_r16 = p->mixed && r_len(ny) != 0;
-    p->x_r16 = p->mixed && r_len(nx) != 0;
+    const bool y_r16 = p->mixed && r_len(ny) != 0 && d->bc_y <= FIZZY_BC_NEUMANN;
+    p->x_r16 = p->mixed && r_len(nx) != 0 && d->bc_x <= FIZZY_BC_NEUMANN;
     p->TXy = y_r16 ? r_tile_cols(ny) : y_tile_cols(ny, p->mixed != 0);
     p->smem_x64 = pass_smem<double>(nx, p->Lx);
     p->smem_x32 = pass_smem<float>(nx, p->Lx);
@@ -755,7 +913,11 @@ int fizzy_proj_plan(fizzy_proj_plan_t *out, const fizzy_proj_desc *d, void *stre
         }
     }
     p->kern = pick_kernels(fixed_len(nx, d->bc_x), fixed_len(ny, d->bc_y));
-    if (p->mixed) pick_r_kernels(p->kern, nx, d->bc_x, ny, d->bc_y);
+    if (p->mixed) pick_r_kernels(p->kern, p->x_r16 ? nx : 0, d->bc_x, y_r16 ? ny : 0, d->bc_y);
+    if (p->mixed && p->x_r16 && y_r16 && nx == ny && (nx == 256 || nx == 512) &&
+        (d->flags & FIZZY_FLAG_FUSED_XY))
+        p->xy_fused = setup_xy(p, nx, d->bc_x == FIZZY_BC_NEUMANN ? KIND_DCT : KIND_PERIODIC,
+                               d->bc_y == FIZZY_BC_NEUMANN ? KIND_DCT : KIND_PERIODIC);
     pass_caps(p->cap, p->kern, p->smem_x64, p->smem_x32, p->x_r16 ? 0 : p->smem_x32, p->smem_y64,
               p->smem_y32);
     // stream-ordered plans are ready for work queued after them on their
@@ -804,7 +966,7 @@ int fizzy_proj_set_physics(fizzy_proj_plan_t p, double rho_l, double rho_g, doub
 
 int fizzy_proj_launches_per_solve(fizzy_proj_plan_t p) {
     if (!p) return 0;
-    int n = p->mixed ? 9 + 6 * p->max_refine : 7;
+    int n = p->mixed ? (p->xy_fused ? 7 + 4 * p->max_refine : 9 + 6 * p->max_refine) : 7;
     if (p->check) n += p->mixed ? 1 : 3;
     return n;
 }
@@ -901,6 +1063,7 @@ int fizzy_proj_solve(fizzy_proj_plan_t p, const double *phi, const double *p_n, 
         return set_err(p, FIZZY_ERR_INVALID, "null array pointer");
     if (p_np1 == phi || p_np1 == p_n || p_np1 == p_nm1 || p_np1 == u || p_np1 == v || p_np1 == w)
         return set_err(p, FIZZY_ERR_INVALID, "p_np1 aliases an input");
+    if (!staggered_bcs(p->desc)) return set_err(p, FIZZY_ERR_UNSUPPORTED, kNeedsStaggeredBcs);
     cudaStream_t s = (cudaStream_t)stream;
     const GridDev &g = p->g;
     const int nx = g.nx, ny = g.ny, nz = g.nz;
@@ -959,14 +1122,23 @@ int fizzy_proj_solve(fizzy_proj_plan_t p, const double *phi, const double *p_n, 
         xa.out = p->fhat32;
         xa.f_out = p->f;
         const int *conv = &p->st->converged;
-        TIMED(KS_XFWD, (p->kern.xf32d<<<grid(xrt, CAP_XF32D), 256, smx32r, s>>>(g, p->fx.d32, p->Lx, xa, xrt)));
-        TIMED(KS_YFWD, (p->kern.yf32<<<grid(ytiles, CAP_Y32F), 256, p->smem_y32, s>>>(nx, ny, p->fy.d32, p->TXy, p->fhat32, nullptr, ygx, ytiles)));
+        const int xyg = XY_CL * nz;  // fused x-y passes: one cluster per z-plane
+        if (p->xy_fused) {
+            TIMED(KS_XFWD, (p->xyf_div<<<xyg, p->xy_threads, p->xy_smem, s>>>(g, xa)));
+        } else {
+            TIMED(KS_XFWD, (p->kern.xf32d<<<grid(xrt, CAP_XF32D), 256, smx32r, s>>>(g, p->fx.d32, p->Lx, xa, xrt)));
+            TIMED(KS_YFWD, (p->kern.yf32<<<grid(ytiles, CAP_Y32F), 256, p->smem_y32, s>>>(nx, ny, p->fy.d32, p->TXy, p->fhat32, nullptr, ygx, ytiles)));
+        }
         if (g.perz)
             TIMED(KS_THOMAS, (k_thomas_cyc<float><<<grid(ttiles, CAP_TH32C), THOMAS_BLOCK, thomas_cyc_smem<float>(), s>>>(g, p->Ux, p->Uy, p->mtab32, p->ibtab32, p->cup32, p->wtab32, p->qtab32, p->fhat32, nullptr, ttiles)));
         else
             TIMED(KS_THOMAS, (k_thomas<float><<<grid(ttiles, CAP_TH32), THOMAS_BLOCK, thomas_smem<float>(), s>>>(g, p->Ux, p->Uy, p->mtab32, p->ibtab32, p->cup32, p->fhat32, nullptr, ttiles)));
-        TIMED(KS_YINV, (p->kern.yi32<<<grid(ytiles, CAP_Y32I), 256, p->smem_y32, s>>>(nx, ny, p->fy.d32, p->TXy, p->fhat32, nullptr, ygx, ytiles)));
-        TIMED(KS_XINV, (p->kern.xi32s<<<grid(xrt, CAP_XI32S), 256, smx32r, s>>>(g, p->fx.d32, p->Lx, p->fhat32, p_np1, p->st, xrt)));
+        if (p->xy_fused) {
+            TIMED(KS_XINV, (p->xyi_store<<<xyg, p->xy_threads, p->xy_smem, s>>>(g, p->fhat32, p_np1, p->st)));
+        } else {
+            TIMED(KS_YINV, (p->kern.yi32<<<grid(ytiles, CAP_Y32I), 256, p->smem_y32, s>>>(nx, ny, p->fy.d32, p->TXy, p->fhat32, nullptr, ygx, ytiles)));
+            TIMED(KS_XINV, (p->kern.xi32s<<<grid(xrt, CAP_XI32S), 256, smx32r, s>>>(g, p->fx.d32, p->Lx, p->fhat32, p_np1, p->st, xrt)));
+        }
         // residual of the FP32 solution (slot 0), then refinement sweeps
         // sw = 1..max_refine: transform of the stored residual, FP32 y/z/y^-1,
         // p += delta, then the residual fused with the correction (slot sw)
@@ -992,14 +1164,22 @@ int fizzy_proj_solve(fizzy_proj_plan_t p, const double *phi, const double *p_n, 
         for (int sw = 1; sw <= p->max_refine; ++sw) {
             // a one-sweep solve runs sweep 1; later sweeps usually return at once
             auto gs = [&](int tiles, int c) { return sw == 1 ? grid(tiles, c) : rgrid(tiles, c); };
-            TIMED(KS_XFWD_R, (p->kern.xf32l<<<gs(xrt, CAP_XF32L), 256, smx32r, s>>>(g, p->fx.d32, p->Lx, la, xrt)));
-            TIMED(KS_YFWD_R, (p->kern.yf32<<<gs(ytiles, CAP_Y32F), 256, p->smem_y32, s>>>(nx, ny, p->fy.d32, p->TXy, p->fhat32, conv, ygx, ytiles)));
+            if (p->xy_fused) {
+                TIMED(KS_XFWD_R, (p->xyf_load<<<xyg, p->xy_threads, p->xy_smem, s>>>(g, la)));
+            } else {
+                TIMED(KS_XFWD_R, (p->kern.xf32l<<<gs(xrt, CAP_XF32L), 256, smx32r, s>>>(g, p->fx.d32, p->Lx, la, xrt)));
+                TIMED(KS_YFWD_R, (p->kern.yf32<<<gs(ytiles, CAP_Y32F), 256, p->smem_y32, s>>>(nx, ny, p->fy.d32, p->TXy, p->fhat32, conv, ygx, ytiles)));
+            }
             if (g.perz)
                 TIMED(KS_THOMAS_R, (k_thomas_cyc<float><<<gs(ttiles, CAP_TH32C), THOMAS_BLOCK, thomas_cyc_smem<float>(), s>>>(g, p->Ux, p->Uy, p->mtab32, p->ibtab32, p->cup32, p->wtab32, p->qtab32, p->fhat32, conv, ttiles)));
             else
                 TIMED(KS_THOMAS_R, (k_thomas<float><<<gs(ttiles, CAP_TH32), THOMAS_BLOCK, thomas_smem<float>(), s>>>(g, p->Ux, p->Uy, p->mtab32, p->ibtab32, p->cup32, p->fhat32, conv, ttiles)));
-            TIMED(KS_YINV_R, (p->kern.yi32<<<gs(ytiles, CAP_Y32I), 256, p->smem_y32, s>>>(nx, ny, p->fy.d32, p->TXy, p->fhat32, conv, ygx, ytiles)));
-            TIMED(KS_XACC, (p->kern.xi32a<<<gs(xrt, CAP_XI32A), 256, smx32r, s>>>(g, p->fx.d32, p->Lx, p->fhat32, p_np1, p->st, xrt)));
+            if (p->xy_fused) {
+                TIMED(KS_XACC, (p->xyi_accum<<<xyg, p->xy_threads, p->xy_smem, s>>>(g, p->fhat32, p_np1, p->st)));
+            } else {
+                TIMED(KS_YINV_R, (p->kern.yi32<<<gs(ytiles, CAP_Y32I), 256, p->smem_y32, s>>>(nx, ny, p->fy.d32, p->TXy, p->fhat32, conv, ygx, ytiles)));
+                TIMED(KS_XACC, (p->kern.xi32a<<<gs(xrt, CAP_XI32A), 256, smx32r, s>>>(g, p->fx.d32, p->Lx, p->fhat32, p_np1, p->st, xrt)));
+            }
             ra.slot = sw;
             TIMED(KS_RCORR, (k_resid<true><<<gs(rctiles, CAP_RC), rcb, 0, s>>>(g, RESID_KC, ra, rtgx, rtgy, rctiles)));
         }
@@ -1056,6 +1236,7 @@ int fizzy_proj_solve_host_async(fizzy_proj_plan_t p, const double *phi, const do
     if (!p) return FIZZY_ERR_INVALID;
     if (!phi || !p_n || !p_nm1 || !u_in || !v_in || !w_in || !u || !v || !w || !p_np1)
         return set_err(p, FIZZY_ERR_INVALID, "null array pointer");
+    if (!staggered_bcs(p->desc)) return set_err(p, FIZZY_ERR_UNSUPPORTED, kNeedsStaggeredBcs);
     int rc = host_staging(p);
     if (rc) return rc;
     cudaStream_t s = (cudaStream_t)stream;
@@ -1087,13 +1268,15 @@ int fizzy_proj_solve_host_async(fizzy_proj_plan_t p, const double *phi, const do
     return FIZZY_OK;
 }
 
-int fizzy_probe_fma_rate(int precision, int iters, double *instr_per_s, double *elapsed_ms,
-                         void *stream) {
-    if (iters < 1 || !instr_per_s) return FIZZY_ERR_INVALID;
+
+int fizzy_probe_fma_rate(int precision, int op, int chains, int iters, double *instr_per_s,
+                         double *elapsed_ms, void *stream) {
+    if (iters < 1 || !instr_per_s || op < 0 || op > 5 || (chains != 4 && chains != 8 && chains != 16))
+        return FIZZY_ERR_INVALID;
     if (precision != FIZZY_PREC_FP64 && precision != FIZZY_PREC_MIXED) return FIZZY_ERR_INVALID;
     cudaStream_t s = (cudaStream_t)stream;
     const bool f64 = precision == FIZZY_PREC_FP64;
-    const void *fn = f64 ? (const void *)k_fma_probe<double> : (const void *)k_fma_probe<float>;
+    const void *fn = f64 ? probe_fn<double>(op, chains) : probe_fn<float>(op, chains);
     int dev = 0, sms = 0, nb = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -1105,9 +1288,11 @@ int fizzy_probe_fma_rate(int precision, int iters, double *instr_per_s, double *
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
     if (e == cudaSuccess) e = cudaEventRecord(e0, s);
     if (e == cudaSuccess) {
-        if (f64) k_fma_probe<double><<<grid, 256, 0, s>>>(iters, 0.9999999, 1e-7);
-        else k_fma_probe<float><<<grid, 256, 0, s>>>(iters, 0.9999f, 1e-4f);
-        e = cudaGetLastError();
+        double a64 = 0.9999999, b64 = 1e-7;
+        float a32 = 0.9999f, b32 = 1e-4f;
+        void *args64[] = {&iters, &a64, &b64};
+        void *args32[] = {&iters, &a32, &b32};
+        e = cudaLaunchKernel(fn, dim3(grid), dim3(256), f64 ? args64 : args32, 0, s);
     }
     if (e == cudaSuccess) e = cudaEventRecord(e1, s);
     if (e == cudaSuccess) e = cudaEventSynchronize(e1);
@@ -1116,7 +1301,7 @@ int fizzy_probe_fma_rate(int precision, int iters, double *instr_per_s, double *
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
     if (e != cudaSuccess || !(ms > 0.f)) return FIZZY_ERR_CUDA;
-    const double instr = (double)grid * 256.0 * (double)iters * 4.0 * PROBE_CHAINS;
+    const double instr = (double)grid * 256.0 * (double)iters * 4.0 * chains;
     *instr_per_s = instr / (ms * 1e-3);
     if (elapsed_ms) *elapsed_ms = ms;
     return FIZZY_OK;
@@ -1141,6 +1326,11 @@ int fizzy_proj_solve_host(fizzy_proj_plan_t p, const double *phi, const double *
 }
 
 }  // extern "C"
+
+// ===========================================================================
+// Stand-alone Poisson solve with every boundary kind (fizzy_poisson_solve)
+// ===========================================================================
+#include "fizzy_poisson.inc"
 
 // ===========================================================================
 // Batched projections (fizzy_proj_batch_*)
@@ -1200,7 +1390,7 @@ extern "C" int fizzy_proj_solve_noalloc(const fizzy_proj_desc *d, const double *
     if (vrc) return vrc;
     if (!phi || !p_n || !p_nm1 || !u || !v || !w || !p_np1) return FIZZY_ERR_INVALID;
     if (d->precision != FIZZY_PREC_FP64 || d->flags != 0) return FIZZY_ERR_INVALID;
-    if (d->periodic_z) return FIZZY_ERR_UNSUPPORTED;  // walls in z only
+    if (d->periodic_z || !staggered_bcs(*d)) return FIZZY_ERR_UNSUPPORTED;  // walls in z; P/N x, y
     const int nx = d->nx, ny = d->ny, nz = d->nz;
     if ((long long)nx * ny * nz > kNaMaxCells || nx > kNaMaxN || ny > kNaMaxN || nz > kNaMaxNz)
         return FIZZY_ERR_UNSUPPORTED;
@@ -1302,6 +1492,7 @@ extern "C" int fizzy_proj_solve_noalloc(const fizzy_proj_desc *d, const double *
     g.bcx = d->bc_x;
     g.bcy = d->bc_y;
     g.perz = d->periodic_z ? 1 : 0;
+    g.sing = (d->bc_x <= FIZZY_BC_NEUMANN && d->bc_y <= FIZZY_BC_NEUMANN) ? 1 : 0;
     g.rny = (unsigned)((1ull << 32) / (unsigned)ny + 1);
     physics_consts(g, d->rho_l, d->rho_g, d->dt, d->dx, d->dy, sig);
     g.idx2 = 1.0 / (d->dx * d->dx);

@@ -22,7 +22,16 @@
 
 namespace fz {
 
-enum { KIND_PERIODIC = 0, KIND_DCT = 1 };
+// Transform kinds.  KIND_DCT4 (zero flux at the near face, p = 0 at the far
+// face) is the DCT-IV, X_k = sum_n x_n cos(pi (2n+1)(2k+1) / (4n)), computed
+// per real line by one complex FFT of half the length (see dct4_tile).  The
+// descriptor's flip turns a DCT-II into the DST-II (p = 0 at both faces) and
+// a DCT-IV into the DST-IV (p = 0 near, zero flux far): with y_n = (-1)^n x_n,
+//     DST-II(x)_k = DCT-II(y)_(N-1-k),   DST-IV(x)_k = DCT-IV(y)_(N-1-k),
+// so the forward pass negates the odd samples on loading and the inverse
+// pass negates them on storing; the reversed spectral index is absorbed into
+// the eigenvalue of each slot (slot j holds the sine index N-1-j).
+enum { KIND_PERIODIC = 0, KIND_DCT = 1, KIND_DCT4 = 2 };
 
 constexpr int FFT_MAX_STAGES = 12;
 
@@ -32,14 +41,19 @@ constexpr int FFT_MAX_STAGES = 12;
 // multiply-high reciprocals of m[s] and ns[s]: for 0 <= x < 2^31/d,
 // floor(x/d) = umulhi(x, floor(2^32/d) + 1)  (d > 1).
 struct FFTDesc {
-    int n;           // transform length
+    int n;           // line length (the complex FFT length too, except KIND_DCT4: n/2)
     int nst;         // number of Stockham stages
-    int kind;        // KIND_PERIODIC or KIND_DCT
+    int kind;        // KIND_PERIODIC, KIND_DCT or KIND_DCT4
+    int flip;        // 1: negate odd samples (DST-II from KIND_DCT, DST-IV from KIND_DCT4)
+    unsigned rK;     // KIND_DCT4: multiply-high reciprocal of n/2
     int rad[FFT_MAX_STAGES], m[FFT_MAX_STAGES], ns[FFT_MAX_STAGES], twq[FFT_MAX_STAGES];
     unsigned rm[FFT_MAX_STAGES], rns[FFT_MAX_STAGES];
     unsigned rn, rM;  // multiply-high reciprocals of n and M = n/2 + 1
-    const void *tw;  // n entries (m, tau) of exp(-2 pi i t / n), see tw_apply (T2)
-    const void *cs;  // n/2+1 complex: (cos, sin)(pi m / (2 n)) (T2)
+    const void *tw;  // n entries (m, tau) of exp(-2 pi i t / n), see tw_apply (T2); KIND_DCT4:
+                     // n/2 such entries for length n/2, then the pre-twiddles
+                     // exp(-i pi (4t+1)/(4n)), t < n/2
+    const void *cs;  // n/2+1 complex: (cos, sin)(pi m / (2 n)) (T2); KIND_DCT4: the
+                     // post-twiddles 2 exp(-i pi k / n), k < n/2
 };
 
 __device__ __forceinline__ int fdiv(int x, int d, unsigned r) {
@@ -258,6 +272,13 @@ __device__ __forceinline__ void load_tables(const FFTDesc &D, typename C2<T>::t 
     for (int t = threadIdx.x; t < D.n; t += blockDim.x) tw_s[t] = tw[t];
     if (D.kind == KIND_DCT)
         for (int t = threadIdx.x; t <= D.n / 2; t += blockDim.x) cs_s[t] = cs[t];
+    if (D.kind == KIND_DCT4)
+        for (int t = threadIdx.x; t < D.n / 2; t += blockDim.x) cs_s[t] = cs[t];
+}
+
+// a sample of a flipped direction: odd samples negated (an integer operation)
+template <typename T> __device__ __forceinline__ T flip_odd(T v, int flip, int i) {
+    return flip_sign(v, flip && (i & 1));
 }
 
 // Forward separation for the pair index m of one complex line Z (length n):

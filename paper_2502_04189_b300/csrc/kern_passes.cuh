@@ -36,6 +36,8 @@ struct GridDev {
     int nx, ny, nz;
     int bcx, bcy;
     int perz;          // 1: periodic z (plane nz-1 joins plane 0 through the seam face nz-1/2)
+    int sing;          // 1: no Dirichlet face in x or y, so the (0,0) z-line is singular
+                       // (mean removed, pressure gauge); 0: every z-line is regular
     unsigned rny;      // multiply-high reciprocal of ny (fdiv)
     // face-flux constants.  The split-term flux of a face with spacing h is
     // q' = u* + dt |drho|/(rho0 h) * t/(|drho| t + 2 rho0) * (p^_b - p^_a),
@@ -390,6 +392,69 @@ __device__ __forceinline__ const typename C2<T>::t *fft_any(typename C2<T>::t *a
     else return fft_lines<T, INV>(a, b, L, ls, D, tw);
 }
 
+// DCT-IV (times 2) of the R real lines of a tile, in shared memory, by one
+// complex FFT of half the length per line (n = 2M):
+//     z_t = (x_(2t) + i x_(n-1-2t)) exp(-i pi (4t+1)/(4n)),   t < M,
+//     Z = FFT_M(z),   Y_k = 2 Z_k exp(-i pi k/n),
+//     X_(2k) = Re Y_k,   X_(n-1-2k) = -Im Y_k.
+// The DCT-IV is its own inverse up to n/2, so the forward and the inverse
+// passes run the same steps (the round trip then scales by 2n, as the other
+// kinds do).  ld(r, i) returns sample i of line r, st(r, k, v) stores value k;
+// LFAST orders the load and store loops with the line index fastest (the
+// y-pass, whose lines are columns), else the sample index fastest.  tw_s holds
+// the M twiddles of the length-M FFT then the M pre-twiddles, cs_s the M
+// post-twiddles; A and B hold R lines of M complex values each.
+template <typename T, bool LFAST, typename LD, typename ST>
+__device__ __forceinline__ void dct4_tile(const FFTDesc &D, int R, typename C2<T>::t *A,
+                                          typename C2<T>::t *B, const typename C2<T>::t *tw_s,
+                                          const typename C2<T>::t *cs_s, LD &&ld, ST &&st) {
+    typedef typename C2<T>::t T2;
+    const int n = D.n, M = n >> 1;
+    const unsigned rR = fdiv_recip(R);
+    const T2 *pre = tw_s + M;
+    // 1. pack the two halves of each line into M complex values
+    const int total = R * n;
+    for (int base = threadIdx.x; base < total; base += PASS_U * blockDim.x) {
+        T v[PASS_U];
+#pragma unroll
+        for (int u = 0; u < PASS_U; ++u) {
+            const int idx = base + u * blockDim.x;
+            int r, i;
+            if (LFAST) { i = fdiv(idx, R, rR); r = idx - i * R; }
+            else { r = fdiv(idx, n, D.rn); i = idx - r * n; }
+            v[u] = idx < total ? ld(r, i) : (T)0;
+        }
+#pragma unroll
+        for (int u = 0; u < PASS_U; ++u) {
+            const int idx = base + u * blockDim.x;
+            int r, i;
+            if (LFAST) { i = fdiv(idx, R, rR); r = idx - i * R; }
+            else { r = fdiv(idx, n, D.rn); i = idx - r * n; }
+            const int t = (i & 1) ? (n - 1 - i) >> 1 : i >> 1;
+            if (idx < total) ((T *)(A + r * M))[2 * t + (i & 1)] = v[u];
+        }
+    }
+    __syncthreads();
+    // 2. pre-twiddle
+    for (int t = threadIdx.x; t < R * M; t += blockDim.x) {
+        const int r = fdiv(t, M, D.rK), q = t - r * M;
+        const T2 a = A[r * M + q], w = pre[q];
+        A[r * M + q] = mk2(fmaT(a.x, w.x, -mulT(a.y, w.y)), fmaT(a.x, w.y, mulT(a.y, w.x)));
+    }
+    __syncthreads();
+    // 3. complex FFT of length M (the descriptor's stages)
+    const T2 *Z = fft_lines<T, false>(A, B, R, M, D, tw_s);
+    // 4. post-twiddle (carrying the factor 2) and store
+    for (int t = threadIdx.x; t < R * M; t += blockDim.x) {
+        int r, k;
+        if (LFAST) { k = fdiv(t, R, rR); r = t - k * R; }
+        else { r = fdiv(t, M, D.rK); k = t - r * M; }
+        const T2 z = Z[r * M + k], w = cs_s[k];
+        st(r, 2 * k, fmaT(z.x, w.x, -mulT(z.y, w.y)));
+        st(r, n - 1 - 2 * k, -fmaT(z.x, w.y, mulT(z.y, w.x)));
+    }
+}
+
 // Forward x-pass: per CTA 2L real x-lines (flattened line index (k, j)).
 template <typename T, int MODE, bool CG, int NF = 0>
 __device__ __forceinline__ void xfwd_body(const GridDev &g, const FFTDesc &D, int L, const XArgs &a,
@@ -407,6 +472,22 @@ __device__ __forceinline__ void xfwd_body(const GridDev &g, const FFTDesc &D, in
     const int nlines = g.ny * g.nz;
     const int line0 = bx * 2 * L;
     (void)ntiles;
+    if constexpr (!FX && MODE == XF_MIX_LOAD) {
+        if (kind == KIND_DCT4) {  // in place on the stored right-hand side
+            T *data = (T *)a.out;
+            dct4_tile<T, false>(
+                D, 2 * L, A, B, tw_s, cs_s,
+                [&](int r, int i) -> T {
+                    const int line = line0 + r;
+                    return line < nlines ? flip_odd(ldp<CG>(data + (size_t)line * n + i), D.flip, i) : (T)0;
+                },
+                [&](int r, int k, T v) {
+                    const int line = line0 + r;
+                    if (line < nlines) data[(size_t)line * n + k] = v;
+                });
+            return;
+        }
+    }
     unsigned long long mx = 0ull;
     const float scale32 = (float)g.sigma;
     // 1. source values into the packed complex lines
@@ -425,7 +506,9 @@ __device__ __forceinline__ void xfwd_body(const GridDev &g, const FFTDesc &D, in
             for (int u = 0; u < PASS_U; ++u) {
                 const int idx = base + u * blockDim.x;
                 const int r = (FX ? idx / NF : fdiv(idx, n, D.rn)), i = idx - r * n;
-                if (idx < total) ((T *)(A + (r >> 1) * ls))[2 * line_pos(i, n, kind) + (r & 1)] = v[u];
+                if (idx < total)
+                    ((T *)(A + (r >> 1) * ls))[2 * line_pos(i, n, kind) + (r & 1)] =
+                        FX ? v[u] : flip_odd(v[u], D.flip, i);
             }
         }
     } else {  // the divergence: the face loads of UD cells per thread issued together
@@ -562,6 +645,21 @@ __device__ __forceinline__ void ypass_body(int nx, int ny, const FFTDesc &D, int
     const int i0 = bx * TX;
     const int ncols = min(TX, nx - i0);
     T *plane = data + (size_t)kplane * ny * nx + i0;
+    if constexpr (!FX) {
+        if (kind == KIND_DCT4) {  // the same steps forward and inverse (columns = lines)
+            dct4_tile<T, true>(
+                D, TX, A, B, tw_s, cs_s,
+                [&](int c, int j) -> T {
+                    if (c >= ncols) return (T)0;
+                    const T v = ldp<CG>(plane + (size_t)j * nx + c);
+                    return INV ? v : flip_odd(v, D.flip, j);
+                },
+                [&](int c, int k, T v) {
+                    if (c < ncols) plane[(size_t)k * nx + c] = INV ? flip_odd(v, D.flip, k) : v;
+                });
+            return;
+        }
+    }
     const int M = n / 2 + 1;
     const unsigned rTX = fdiv_recip(TX), rL = fdiv_recip(L);
     if (!INV) {
@@ -579,7 +677,9 @@ __device__ __forceinline__ void ypass_body(int nx, int ny, const FFTDesc &D, int
             for (int u = 0; u < PASS_U; ++u) {
                 const int idx = base + u * blockDim.x;
                 const int j = fdiv(idx, TX, rTX), c = idx - j * TX;
-                if (idx < total) ((T *)(A + (c >> 1) * ls))[2 * line_pos(j, n, kind) + (c & 1)] = v[u];
+                if (idx < total)
+                    ((T *)(A + (c >> 1) * ls))[2 * line_pos(j, n, kind) + (c & 1)] =
+                        FX ? v[u] : flip_odd(v[u], D.flip, j);
             }
         }
         __syncthreads();
@@ -627,8 +727,10 @@ __device__ __forceinline__ void ypass_body(int nx, int ny, const FFTDesc &D, int
         const T2 *Z = fft_any<T, true, NF>(A, B, L, ls, D, tw_s);
         for (int idx = threadIdx.x; idx < n * TX; idx += blockDim.x) {
             const int j = fdiv(idx, TX, rTX), c = idx - j * TX;
-            if (c < ncols)
-                plane[(size_t)j * nx + c] = ((const T *)(Z + (c >> 1) * ls))[2 * line_pos(j, n, kind) + (c & 1)];
+            if (c < ncols) {
+                const T v = ((const T *)(Z + (c >> 1) * ls))[2 * line_pos(j, n, kind) + (c & 1)];
+                plane[(size_t)j * nx + c] = FX ? v : flip_odd(v, D.flip, j);
+            }
         }
     }
 }
@@ -665,6 +767,27 @@ __device__ __forceinline__ void xinv_body(const GridDev &g, const FFTDesc &D, in
     load_tables<T>(D, tw_s, cs_s);
     const int nlines = g.ny * g.nz;
     const int line0 = bx * 2 * L;
+    if constexpr (!FX) {
+        if (kind == KIND_DCT4) {
+            const int es = (MODE == XI_ACCUM) ? exp_of_bits(ldp<CG>(&st->fmax_bits)) : 0;
+            dct4_tile<T, false>(
+                D, 2 * L, A, B, tw_s, cs_s,
+                [&](int r, int k) -> T {
+                    const int line = line0 + r;
+                    return line < nlines ? ldp<CG>(in + (size_t)line * n + k) : (T)0;
+                },
+                [&](int r, int i, T v) {
+                    const int line = line0 + r;
+                    if (line >= nlines) return;
+                    v = flip_odd(v, D.flip, i);
+                    double *dst = p + (size_t)line * n + i;
+                    const double dv = sizeof(T) == 8 ? (double)v : f32_to_f64_shift((float)v, es);
+                    if (MODE == XI_STORE) *dst = dv;
+                    else *dst = ldp<CG>(dst) + dv;
+                });
+            return;
+        }
+    }
     const int M = n / 2 + 1;
     __syncthreads();
     const int total = L * M;
@@ -704,7 +827,8 @@ __device__ __forceinline__ void xinv_body(const GridDev &g, const FFTDesc &D, in
             const int r = (FX ? idx / NF : fdiv(idx, n, D.rn)), i = idx - r * n;
             const int line = line0 + r;
             if (line < nlines) {
-                const T v = ((const T *)(Z + (r >> 1) * ls))[2 * line_pos(i, n, kind) + (r & 1)];
+                T v = ((const T *)(Z + (r >> 1) * ls))[2 * line_pos(i, n, kind) + (r & 1)];
+                if (!FX) v = flip_odd(v, D.flip, i);
                 double *dst = p + (size_t)line * n + i;
                 if (sizeof(T) == 8) *dst = (double)v;
                 else *dst = f32_to_f64_shift((float)v, 0);
@@ -725,7 +849,8 @@ __device__ __forceinline__ void xinv_body(const GridDev &g, const FFTDesc &D, in
                 const int idx = base + u * blockDim.x;
                 const int r = (FX ? idx / NF : fdiv(idx, n, D.rn)), i = idx - r * n;
                 if (idx < total && line0 + r < nlines) {
-                    const T v = ((const T *)(Z + (r >> 1) * ls))[2 * line_pos(i, n, kind) + (r & 1)];
+                    T v = ((const T *)(Z + (r >> 1) * ls))[2 * line_pos(i, n, kind) + (r & 1)];
+                    if (!FX) v = flip_odd(v, D.flip, i);
                     p[(size_t)(line0 + r) * n + i] = pv[u] + f32_to_f64_shift((float)v, ef);
                 }
             }
@@ -1165,7 +1290,7 @@ __device__ __forceinline__ void thomas_body(const GridDev &g, int Ux, int Uy, co
                                             const T *qtab = nullptr) {
     if (conv && ldp<CG>(conv)) return;
     const size_t plane = (size_t)g.nx * g.ny;
-    if (line_base == 0 && threadIdx.x < 32) {
+    if (g.sing && line_base == 0 && threadIdx.x < 32) {
         singular_line_warp<T, CG>(g, data, plane);  // line (0,0)
         if (threadIdx.x == 0) return;
     }
@@ -1402,7 +1527,7 @@ __global__ void __launch_bounds__(THOMAS_BLOCK) k_thomas_cyc(GridDev g, int Ux, 
     const size_t ts = (size_t)Ux * Uy;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const int line_base = t * THOMAS_BLOCK;
-        if (line_base == 0 && threadIdx.x < 32) {
+        if (g.sing && line_base == 0 && threadIdx.x < 32) {
             singular_line_warp<T, false>(g, data, plane);  // line (0,0)
             if (threadIdx.x == 0) continue;
         }
@@ -1443,16 +1568,16 @@ __global__ void __launch_bounds__(256) k_divmax(GridDev g, const double *__restr
 // beta_k = (b_k + lambda) - m_k c_(k-1), stored as m_k and 1/beta_k (FP64, and
 // rounded to FP32 when t32 is given).  Every operation is an explicit IEEE
 // round-to-nearest operation in the order of that recurrence.  The singular
-// pair (0,0) gets zeros.
+// pair (0,0) gets zeros when sing != 0 (no Dirichlet face in x or y).
 __global__ void k_ztables(int Ux, int Uy, int nz, const double *__restrict__ lamx,
                           const double *__restrict__ lamy, const double *__restrict__ A,
                           const double *__restrict__ C, double *mt, double *ib, float *mt32,
-                          float *ib32) {
+                          float *ib32, int sing) {
     const size_t ts = (size_t)Ux * Uy;
     for (size_t uu = (size_t)blockIdx.x * blockDim.x + threadIdx.x; uu < ts;
          uu += (size_t)gridDim.x * blockDim.x) {
         const int ux = (int)(uu % Ux), uy = (int)(uu / Ux);
-        if (ux == 0 && uy == 0) {
+        if (sing && ux == 0 && uy == 0) {
             for (int k = 0; k < nz; ++k) {
                 mt[(size_t)k * ts + uu] = 0.0;
                 ib[(size_t)k * ts + uu] = 0.0;
@@ -1495,17 +1620,18 @@ __global__ void k_ztables(int Ux, int Uy, int nz, const double *__restrict__ lam
 // (alpha/gamma)/beta_(nz-1) at k = nz-1; q = B^(-1) (gamma, 0, ..., 0, beta_c),
 // divided by 1 + q_0 + (alpha/gamma) q_(nz-1).  Explicit round-to-nearest
 // operations; FP32 copies rounded from the FP64 values.  The singular pair
-// (0,0) gets zeros.
+// (0,0) (sing != 0) gets zeros.
 __global__ void k_ztables_cyc(int Ux, int Uy, int nz, const double *__restrict__ lamx,
                               const double *__restrict__ lamy, const double *__restrict__ A,
                               const double *__restrict__ C, double *mt, double *ib, double *wt,
-                              double *qt, float *mt32, float *ib32, float *wt32, float *qt32) {
+                              double *qt, float *mt32, float *ib32, float *wt32, float *qt32,
+                              int sing) {
     const size_t ts = (size_t)Ux * Uy;
     for (size_t uu = (size_t)blockIdx.x * blockDim.x + threadIdx.x; uu < ts;
          uu += (size_t)gridDim.x * blockDim.x) {
         const int ux = (int)(uu % Ux), uy = (int)(uu / Ux);
         auto at = [&](int k) { return (size_t)k * ts + uu; };
-        if (ux == 0 && uy == 0) {
+        if (sing && ux == 0 && uy == 0) {
             for (int k = 0; k < nz; ++k) {
                 mt[at(k)] = ib[at(k)] = wt[at(k)] = qt[at(k)] = 0.0;
                 if (mt32) mt32[at(k)] = ib32[at(k)] = wt32[at(k)] = qt32[at(k)] = 0.f;

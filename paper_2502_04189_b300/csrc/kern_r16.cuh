@@ -156,8 +156,9 @@ struct R16Smem {
     float2 cs[256];
 };
 
-template <bool INV, int N, int KIND>
-__device__ __forceinline__ void r16_tables(R16Smem &sm) {
+// (SM: any shared-memory struct with the tw, tw2 and cs tables of R16Smem)
+template <bool INV, int N, int KIND, typename SM>
+__device__ __forceinline__ void r16_tables(SM &sm) {
     constexpr int M = RShape<N>::M;
     float s, c;
     if (threadIdx.x < 16 * M) {
@@ -165,7 +166,7 @@ __device__ __forceinline__ void r16_tables(R16Smem &sm) {
         sincospif(-(float)(t * k1) / (float)(8 * M), &s, &c);
         sm.tw[threadIdx.x] = make_float2(c, INV ? -s : s);
     }
-    if (N == 512) {
+    if (N == 512 && threadIdx.x < 256) {  // (blocks may have more than 256 threads)
         sincospif(-(float)threadIdx.x / 256.f, &s, &c);
         sm.tw2[threadIdx.x] = make_float2(c, INV ? -s : s);
     }
@@ -193,8 +194,8 @@ constexpr float R_SQRT2 = 1.41421356237309504880f;  // the n/2 term of the DCT (
 // 16/M M-point DFTs.  X is overwritten; its threads (all in one warp) must
 // have finished reading X before the call (warp barriers inside, the last
 // one after the exchange reads).
-template <bool INV, int M>
-__device__ __forceinline__ void r_core(const R16Smem &sm, float2 *X, int t, float2 (&v)[16]) {
+template <bool INV, int M, typename SM>
+__device__ __forceinline__ void r_core(const SM &sm, float2 *X, int t, float2 (&v)[16]) {
     dft16<INV>(v);
 #pragma unroll
     for (int k1 = 1; k1 < 16; ++k1) {
@@ -249,8 +250,8 @@ template <int M> constexpr int self_reg(int r) {
 // The transform of one line: v[n1] = the input at in_index(n1) on entry,
 // v[r] = the output at out_index(r) on return.  X: the line's region
 // (N values); warp barriers only (a line never spans warps).
-template <bool INV, int N>
-__device__ __forceinline__ void r_fft(const R16Smem &sm, float2 *X, const RPos<N> &q, float2 (&v)[16]) {
+template <bool INV, int N, typename SM>
+__device__ __forceinline__ void r_fft(const SM &sm, float2 *X, const RPos<N> &q, float2 (&v)[16]) {
     if constexpr (N == 512) {  // radix-2 step: group 0 gets lo + hi, group 1 (lo - hi) W512^n
 #pragma unroll
         for (int n1 = 0; n1 < 16; ++n1) {
@@ -279,9 +280,9 @@ __device__ __forceinline__ void r_fft(const R16Smem &sm, float2 *X, const RPos<N
 // thread (M - t) mod M of the line, or (t = 0) in this thread's register
 // self_reg(r); at 512 the odd outputs pair within group 1 with thread
 // 15 - t, register 15 - r.
-template <int N, int KIND, typename F>
-__device__ __forceinline__ void r_separate(const float2 (&v)[16], const RPos<N> &q,
-                                           const R16Smem &sm, F &&fn) {
+template <int N, int KIND, typename SM, typename F>
+__device__ __forceinline__ void r_separate(const float2 (&v)[16], const RPos<N> &q, const SM &sm,
+                                           F &&fn) {
     constexpr int M = RShape<N>::M;
     const int lane = threadIdx.x & 31;
     const int src = (N != 512 || q.h == 0) ? ((lane & ~(M - 1)) | ((M - q.t) & (M - 1)))
@@ -317,9 +318,8 @@ __device__ __forceinline__ void r_separate(const float2 (&v)[16], const RPos<N> 
 // Combination ahead of the inverse transform: v[n1] = Z[in_index(n1)] from
 // the spectra of the two real lines read through get(k) = (a_k, b_k)
 // (half-complex, or DCT-II coefficients pre-twiddled by (c, s)_m).
-template <int N, int KIND, typename G>
-__device__ __forceinline__ void r_combine(float2 (&v)[16], const RPos<N> &q, const R16Smem &sm,
-                                          G &&get) {
+template <int N, int KIND, typename SM, typename G>
+__device__ __forceinline__ void r_combine(float2 (&v)[16], const RPos<N> &q, const SM &sm, G &&get) {
 #pragma unroll
     for (int n1 = 0; n1 < 16; ++n1) {
         const int k = q.in_index(n1);

@@ -106,3 +106,26 @@ def test_workspace_bytes_scale():
     assert bm > b1
     big = F.workspace_bytes(nx=512, ny=512, nz=512, dx=1, dy=1, dz=1, precision=1)
     assert 4e9 < big < 8e9
+
+
+def test_dirichlet_and_mixed_boundary_descriptors():
+    """bc 2 (Dirichlet), 3 (Neumann near, Dirichlet far) and 4 (Dirichlet
+    near, Neumann far) are valid plan kinds; 3 and 4 need an even extent
+    (the DCT-IV runs as a half-length complex FFT); 5 is invalid.  The
+    allocation-free entry point refuses them before any CUDA call."""
+    for bc in (2, 3, 4):
+        assert F.workspace_bytes(**base(bcx=bc)) > 0
+        assert F.workspace_bytes(**base(bcy=bc)) > 0
+    assert F.workspace_bytes(**base(bcx=2, nx=27)) > 0       # DST-II: any radix-2/3 extent
+    for bc in (3, 4):
+        d, keep = F.make_desc(**base(bcx=bc, nx=27))
+        h = ctypes.c_void_p()
+        assert _abi.lib().fizzy_proj_plan(ctypes.byref(h), ctypes.byref(d), None) == -2
+        assert not h.value
+    d, keep = F.make_desc(**base(bcy=5))
+    h = ctypes.c_void_p()
+    assert _abi.lib().fizzy_proj_plan(ctypes.byref(h), ctypes.byref(d), None) == -1
+    d, keep = F.make_desc(**base(bcx=2))
+    fake = [ctypes.c_void_p(8)] * 7
+    assert _abi.lib().fizzy_proj_solve_noalloc(ctypes.byref(d), *fake, None) == -2
+    assert _abi.lib().fizzy_poisson_solve(None, None, None, None, None) == -1

@@ -11,7 +11,12 @@ Some draws are pressure-dominated: the correction (dt/rho0) G p is up to
 agrees with the oracle to round-off then moves u by (dt/rho0) 2 eps max|p| /
 h_min through the gradient, which can exceed 1e-12 of max|u| for any FP64
 solver; the velocity bar is the larger of 1e-12 and ten times that floor,
-computed from the oracle's fields (the floor is reported beside the error)."""
+computed from the oracle's fields (the floor is reported beside the error).
+test_fuzz_floor_report, the last test of this file, lists every draw whose
+velocity error exceeded the plain bar and passed on that floor, with the
+largest floor seen."""
+import warnings
+
 import numpy as np
 import pytest
 
@@ -66,30 +71,42 @@ def velocity_floor(case, ref):
     return s.dt / rho0 * 2 * np.finfo(np.float64).eps * pmax / hmin / umax
 
 
-def check_against_oracle(spec):
+# (draw, precision, velocity error, floor) of every draw that needed the floor,
+# and the largest floor over all draws
+FLOOR_LOG = []
+FLOOR_MAX = [0.0, None]
+
+
+def check_against_oracle(spec, label):
     c = I.make_case(spec)
     ref = O.project_case(c)
     floor = velocity_floor(c, ref)
+    if floor > FLOOR_MAX[0]:
+        FLOOR_MAX[:] = [floor, label]
     got = gpu_project(c, F.FP64)
     ep, eu = compare(c, got, ref)
     assert ep <= 1e-12 and eu <= max(1e-12, 10 * floor), (spec, ep, eu, floor)
+    if eu > 1e-12:
+        FLOOR_LOG.append((label, "fp64", eu, floor))
     assert got["stats"]["div_metric"] <= 1e-10, spec
     got = gpu_project(c, F.MIXED)
     st = got["stats"]
     assert st["converged"] == 1 and st["relres"] <= 1e-10, (spec, st)
     ep, eu = compare(c, got, ref)
     assert ep <= 1e-9 and eu <= max(1e-9, 10 * floor), (spec, ep, eu, floor)
+    if eu > 1e-9:
+        FLOOR_LOG.append((label, "mixed", eu, floor))
     assert st["div_metric"] <= 1e-10, spec
 
 
 @pytest.mark.parametrize("i", range(len(SPECS)))
 def test_fuzz_matches_oracle(cuda_ok, i):
-    check_against_oracle(SPECS[i])
+    check_against_oracle(SPECS[i], "walls-z draw %d" % i)
 
 
 @pytest.mark.parametrize("i", range(len(PZ_SPECS)))
 def test_fuzz_periodic_z_matches_oracle(cuda_ok, i):
-    check_against_oracle(PZ_SPECS[i])
+    check_against_oracle(PZ_SPECS[i], "mixed-z draw %d" % i)
 
 
 @pytest.mark.parametrize("precision", [F.FP64, F.MIXED], ids=["fp64", "mixed"])
@@ -114,3 +131,14 @@ def test_fuzz_batch_equals_alone(cuda_ok, precision, seed, bcz_mix):
     batch.close()
     for p in plans:
         p.close()
+
+
+def test_fuzz_floor_report(cuda_ok):
+    """The draws that passed only on the velocity floor (error above the
+    plain bar, below ten times the floor) and the largest floor seen,
+    reported as a warning (pytest prints it in its summary)."""
+    lines = ["%s (%s): velocity error %.2e, floor %.2e" % d for d in FLOOR_LOG]
+    warnings.warn("fuzz draws passing on the R14 floor: %d%s; largest floor %.2e (%s)" % (
+        len(FLOOR_LOG), "".join("\n  " + x for x in lines), FLOOR_MAX[0], FLOOR_MAX[1]))
+    for _, prec, eu, floor in FLOOR_LOG:
+        assert eu <= 10 * floor, (prec, eu, floor)

@@ -16,5 +16,9 @@ def test_probe_rates_are_plausible(cuda_ok):
     assert 0.06e12 < d < 6e12, d
     assert 3.8e12 < s < 380e12, s
     assert s > 10 * d
-    with pytest.raises(F.FizzyError):
-        F.probe_fma_rate(F.FP64, iters=0)
+    for op in (1, 2, 3):
+        r, _ = F.probe_fma_rate(F.FP64, iters=200, op=op, chains=16)
+        assert 0.06e12 < r < 6e12, (op, r)
+    for bad in (dict(iters=0), dict(iters=10, op=6), dict(iters=10, chains=5)):
+        with pytest.raises(F.FizzyError):
+            F.probe_fma_rate(F.FP64, **bad)
