@@ -298,11 +298,16 @@ int fizzy_proj_timing(fizzy_proj_plan_t p, int idx, const char **name, double *m
  * Batched projections.
  *
  * Many independent projections of uneven sizes, each described by its own
- * plan (either precision), run as one persistent kernel launch replayed from
- * a captured CUDA graph.  The launch works through a list of (instance, pass,
- * tile) items; an item waits (bounded spin) until every tile of its instance's
- * previous pass is done.  Results are the same as each plan's own
- * fizzy_proj_solve (same kernel bodies, same arithmetic per tile).
+ * plan (either precision), replayed from a captured CUDA graph in one of two
+ * forms.  Persistent form: one kernel launch works through a list of
+ * (instance, pass, tile) items; an item waits (bounded spin) until every tile
+ * of its instance's previous pass is done.  Grouped form: one ordinary launch
+ * per pass covers that pass of every instance (of a chain), so launch order
+ * carries the dependencies.  Results are the same in both forms and equal
+ * each plan's own fizzy_proj_solve (same kernel bodies, same arithmetic per
+ * tile; a mixed plan with an x or y length of 128, 256 or 512 solved alone
+ * runs register-resident FP32 transform passes instead, within the mixed
+ * tolerance).
  *
  * arrays: 7*n device pointers, for instance i at 7i..7i+6:
  *         phi, p_n, p_nm1, u, v, w (u*, in/out), p_np1 -- fixed for the batch
@@ -315,11 +320,20 @@ int fizzy_proj_timing(fizzy_proj_plan_t p, int idx, const char **name, double *m
 typedef struct fizzy_proj_batch_s *fizzy_proj_batch_t;
 
 typedef struct fizzy_batch_tuning {
-    int ctas_per_sm; /* persistent CTAs per SM; 0 = as many as fit               */
+    int ctas_per_sm; /* resident CTAs per SM (256-thread kernels); 0 = as many
+                        as fit                                                  */
     int flux_planes; /* z planes per flux tile, multiple of 16; 0 = 16           */
     int x_lines;     /* x-pass line pairs per tile (1..16); 0 = per-size default */
     int y_cols;      /* y-pass columns per tile (even, 2..32); 0 = default       */
-    int order;       /* work-list order: 0 pass-major, 1 instance-major          */
+    int order;       /* persistent form's work-list order: 0 pass-major,
+                        1 instance-major, 2 staggered (half of the instances,
+                        alternate by size, four passes behind the other half)  */
+    int form;        /* 0 persistent launch; 1 grouped: one ordinary launch per
+                        pass index and pass kind, covering the tiles of every
+                        instance at that pass (no dependency waits)            */
+    int chains;      /* grouped form: instances split (by size, round robin)
+                        into this many independent launch chains that the
+                        graph runs concurrently (1..8); 0 = 1                  */
 } fizzy_batch_tuning;
 
 /* Build the batch (work list, device descriptors) and capture its graph.
@@ -342,19 +356,24 @@ int fizzy_proj_batch_status(fizzy_proj_batch_t b, void *stream);
  * normally and fizzy_proj_batch_status returns FIZZY_ERR_TIMEOUT (outputs of
  * that solve invalid); the context stays usable.  inst = -1 and
  * spin_limit = 0 restore the defaults (no stall, 2^26 polls).  Returns
- * FIZZY_ERR_INVALID for a null batch or out-of-range arguments, else the
- * status of the rebuild. */
+ * FIZZY_ERR_INVALID for a null batch or out-of-range arguments,
+ * FIZZY_ERR_UNSUPPORTED for a batch built in the grouped form (it has no
+ * dependency waits), else the status of the rebuild. */
 int fizzy_proj_batch_inject_stall(fizzy_proj_batch_t b, int inst, long long spin_limit);
 
 /* Time candidate tunings (reps replays each, CUDA events on stream), rebuild
  * the batch with the fastest and return it in *chosen and its mean time in
- * *best_ms (either may be NULL).  The candidates vary CTAs per SM, flux
- * planes per tile, x-pass lines per tile, y-pass columns per tile and the
- * work-list order.  Overwrites the batch outputs while timing. */
+ * *best_ms (either may be NULL).  The candidates cover both forms: the
+ * persistent launch with varied CTAs per SM, flux planes per tile, x-pass
+ * lines per tile, y-pass columns per tile and work-list order, and the
+ * grouped launches with 2, 4 or 8 chains.  Overwrites the batch outputs while
+ * timing. */
 int fizzy_proj_batch_autotune(fizzy_proj_batch_t b, int reps, fizzy_batch_tuning *chosen,
                               double *best_ms, void *stream);
 
-/* Work items, persistent grid size and dynamic shared memory of the launch. */
+/* Persistent form: work items, grid size and dynamic shared memory of the
+ * launch.  Grouped form: launches per solve, the largest grid and the largest
+ * dynamic shared memory of one launch. */
 int fizzy_proj_batch_info(fizzy_proj_batch_t b, int *n_items, int *grid, size_t *smem_bytes);
 
 int fizzy_proj_batch_destroy(fizzy_proj_batch_t b);

@@ -42,7 +42,8 @@ class Desc(ctypes.Structure):
 
 class Tuning(ctypes.Structure):
     _fields_ = [("ctas_per_sm", ctypes.c_int), ("flux_planes", ctypes.c_int),
-                ("x_lines", ctypes.c_int), ("y_cols", ctypes.c_int), ("order", ctypes.c_int)]
+                ("x_lines", ctypes.c_int), ("y_cols", ctypes.c_int), ("order", ctypes.c_int),
+                ("form", ctypes.c_int), ("chains", ctypes.c_int)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}

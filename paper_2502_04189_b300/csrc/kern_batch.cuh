@@ -44,7 +44,11 @@ enum BatchKind : int {
     BK_XACC,
     BK_RCORR,   // residual fused with the correction (slot s)
     BK_CORRIF,  // the correction, unless a fused residual pass has run
-    BK_CORRECT
+    BK_CORRECT,
+    // grouped form only: the flux pass split by its compile-time density
+    // branch (rho0 = rho_l, rho0 = rho_g), so each launch holds one body
+    BK_FLUX_L,
+    BK_FLUX_G
 };
 
 // One instance as the persistent kernel sees it (device memory, read-only
@@ -101,26 +105,24 @@ struct BatchArgs {
     int stall_inst;  // test support: this instance's first dependency never completes (-1: none)
 };
 
-__device__ __forceinline__ void batch_run_tile(const BatchInst &I, const BatchItem &w, int tile,
-                                               unsigned char *smem) {
-    const int kind = I.kind[w.pass];
+// One tile of a pass of kind KIND (compile-time) of instance I.  CG: data
+// written by other CTAs of the same launch is read through L2 (the persistent
+// form); the grouped form reads it after a launch boundary and passes false.
+// The same body, with the same arithmetic, runs in either form and in the
+// stand-alone kernels.
+template <int KIND, bool CG>
+__device__ __forceinline__ void run_kind(const BatchInst &I, int pass, int tile, unsigned char *smem) {
     const GridDev &g = I.g;
-    switch (kind) {
-    case BK_FLUX: {
+    if constexpr (KIND == BK_FLUX || KIND == BK_FLUX_L || KIND == BK_FLUX_G) {
         const VB vb{tile % I.fgx, (tile / I.fgx) % I.fgy, tile / (I.fgx * I.fgy)};
         double *slot = I.usq_part ? I.usq_part + tile : nullptr;
-        if (I.rho0_is_g)
+        if (KIND == BK_FLUX_G || (KIND == BK_FLUX && I.rho0_is_g))
             flux_body<true>(g, I.kc, vb, I.phi, I.pn, I.pnm1, I.u, I.v, I.w, I.qx, I.qy, I.qz, slot);
         else
             flux_body<false>(g, I.kc, vb, I.phi, I.pn, I.pnm1, I.u, I.v, I.w, I.qx, I.qy, I.qz, slot);
-        break;
-    }
-    case BK_SUM:
-        sum_partials_body<true>(I.usq_part, I.n_usq_part, I.usq_sum);
-        break;
-    case BK_XFWD64:
-    case BK_XFWD_MIX:
-    case BK_XLOAD: {
+    } else if constexpr (KIND == BK_SUM) {
+        sum_partials_body<CG>(I.usq_part, I.n_usq_part, I.usq_sum);
+    } else if constexpr (KIND == BK_XFWD64 || KIND == BK_XFWD_MIX || KIND == BK_XLOAD) {
         XArgs a;
         memset(&a, 0, sizeof(a));
         a.qx = I.qx;
@@ -128,20 +130,17 @@ __device__ __forceinline__ void batch_run_tile(const BatchInst &I, const BatchIt
         a.qz = I.qz;
         a.f_out = I.f;
         a.st = I.st;
-        if (kind == BK_XFWD64) {
+        if constexpr (KIND == BK_XFWD64) {
             a.out = I.fhat64;
-            xfwd_body<double, XF_F64_DIVQ, true>(g, I.fx64, I.Lx, a, tile, I.tiles[w.pass], smem);
-        } else if (kind == BK_XFWD_MIX) {
+            xfwd_body<double, XF_F64_DIVQ, CG>(g, I.fx64, I.Lx, a, tile, I.tiles[pass], smem);
+        } else if constexpr (KIND == BK_XFWD_MIX) {
             a.out = I.fhat32;
-            xfwd_body<float, XF_MIX_DIVQ, true>(g, I.fx32, I.Lx, a, tile, I.tiles[w.pass], smem);
+            xfwd_body<float, XF_MIX_DIVQ, CG>(g, I.fx32, I.Lx, a, tile, I.tiles[pass], smem);
         } else {
             a.out = I.fhat32;
-            xfwd_body<float, XF_MIX_LOAD, true>(g, I.fx32, I.Lx, a, tile, I.tiles[w.pass], smem);
+            xfwd_body<float, XF_MIX_LOAD, CG>(g, I.fx32, I.Lx, a, tile, I.tiles[pass], smem);
         }
-        break;
-    }
-    case BK_RES0:
-    case BK_RCORR: {
+    } else if constexpr (KIND == BK_RES0 || KIND == BK_RCORR) {
         RArgs a;
         a.p = I.p;
         a.f = I.f;
@@ -153,64 +152,77 @@ __device__ __forceinline__ void batch_run_tile(const BatchInst &I, const BatchIt
         a.w = I.w;
         a.r32 = I.fhat32;
         a.st = I.st;
-        a.slot = I.slot[w.pass];
+        a.slot = I.slot[pass];
         a.tol = I.tol;
         const int txy = I.cgx * I.cgy, z = tile / txy, r = tile - z * txy, y = r / I.cgx;
         const VB vb{r - y * I.cgx, y, z};
-        if (kind == BK_RES0) resid_body<true, false>(g, RESID_KC, a, vb, I.tiles[w.pass], (double *)smem);
-        else resid_body<true, true>(g, RESID_KC, a, vb, I.tiles[w.pass], (double *)smem);
-        break;
-    }
-    case BK_YF64:
-        ypass_body<double, false, true>(g.nx, g.ny, I.fy64, I.TXy, I.fhat64, nullptr, tile % I.ygx,
-                                        tile / I.ygx, smem);
-        break;
-    case BK_YI64:
-        ypass_body<double, true, true>(g.nx, g.ny, I.fy64, I.TXy, I.fhat64, nullptr, tile % I.ygx,
-                                       tile / I.ygx, smem);
-        break;
-    case BK_YF32:
-    case BK_YF32C:
-        ypass_body<float, false, true>(g.nx, g.ny, I.fy32, I.TXy, I.fhat32,
-                                       kind == BK_YF32C ? &I.st->converged : nullptr, tile % I.ygx,
-                                       tile / I.ygx, smem);
-        break;
-    case BK_YI32:
-    case BK_YI32C:
-        ypass_body<float, true, true>(g.nx, g.ny, I.fy32, I.TXy, I.fhat32,
-                                      kind == BK_YI32C ? &I.st->converged : nullptr, tile % I.ygx,
-                                      tile / I.ygx, smem);
-        break;
-    case BK_TH64:
-        thomas_body<double, false, true>(g, I.Ux, I.Uy, I.mtab64, I.ibtab64, I.cup64, I.fhat64,
-                                         nullptr, tile * BATCH_THREADS, nullptr, I.wtab64, I.qtab64);
-        break;
-    case BK_TH32:
-    case BK_TH32C:
-        thomas_body<float, false, true>(g, I.Ux, I.Uy, I.mtab32, I.ibtab32, I.cup32, I.fhat32,
-                                        kind == BK_TH32C ? &I.st->converged : nullptr,
-                                        tile * BATCH_THREADS, nullptr, I.wtab32, I.qtab32);
-        break;
-    case BK_XI64:
-        xinv_body<double, XI_STORE, true>(g, I.fx64, I.Lx, I.fhat64, I.p, I.st, tile, smem);
-        break;
-    case BK_XI32:
-        xinv_body<float, XI_STORE, true>(g, I.fx32, I.Lx, I.fhat32, I.p, I.st, tile, smem);
-        break;
-    case BK_XACC:
-        xinv_body<float, XI_ACCUM, true>(g, I.fx32, I.Lx, I.fhat32, I.p, I.st, tile, smem);
-        break;
-    case BK_CORRIF:
-        if (__ldcg(&I.st->n_resid) != 1) break;  // a fused residual pass wrote u
-        [[fallthrough]];
-    case BK_CORRECT: {
+        resid_body<CG, KIND == BK_RCORR>(g, RESID_KC, a, vb, I.tiles[pass], (double *)smem);
+    } else if constexpr (KIND == BK_YF64 || KIND == BK_YI64) {
+        ypass_body<double, KIND == BK_YI64, CG>(g.nx, g.ny, I.fy64, I.TXy, I.fhat64, nullptr,
+                                                tile % I.ygx, tile / I.ygx, smem);
+    } else if constexpr (KIND == BK_YF32 || KIND == BK_YF32C || KIND == BK_YI32 || KIND == BK_YI32C) {
+        ypass_body<float, KIND == BK_YI32 || KIND == BK_YI32C, CG>(
+            g.nx, g.ny, I.fy32, I.TXy, I.fhat32,
+            (KIND == BK_YF32C || KIND == BK_YI32C) ? &I.st->converged : nullptr, tile % I.ygx,
+            tile / I.ygx, smem);
+    } else if constexpr (KIND == BK_TH64) {
+        thomas_body<double, false, CG>(g, I.Ux, I.Uy, I.mtab64, I.ibtab64, I.cup64, I.fhat64, nullptr,
+                                       tile * BATCH_THREADS, nullptr, I.wtab64, I.qtab64);
+    } else if constexpr (KIND == BK_TH32 || KIND == BK_TH32C) {
+        thomas_body<float, false, CG>(g, I.Ux, I.Uy, I.mtab32, I.ibtab32, I.cup32, I.fhat32,
+                                      KIND == BK_TH32C ? &I.st->converged : nullptr,
+                                      tile * BATCH_THREADS, nullptr, I.wtab32, I.qtab32);
+    } else if constexpr (KIND == BK_XI64) {
+        xinv_body<double, XI_STORE, CG>(g, I.fx64, I.Lx, I.fhat64, I.p, I.st, tile, smem);
+    } else if constexpr (KIND == BK_XI32) {
+        xinv_body<float, XI_STORE, CG>(g, I.fx32, I.Lx, I.fhat32, I.p, I.st, tile, smem);
+    } else if constexpr (KIND == BK_XACC) {
+        xinv_body<float, XI_ACCUM, CG>(g, I.fx32, I.Lx, I.fhat32, I.p, I.st, tile, smem);
+    } else if constexpr (KIND == BK_CORRIF || KIND == BK_CORRECT) {
+        if (KIND == BK_CORRIF && ldp<CG>(&I.st->n_resid) != 1) return;  // a fused residual pass wrote u
         const VB vb{tile % I.cgx, (tile / I.cgx) % I.cgy, tile / (I.cgx * I.cgy)};
-        correct_body<true>(g, I.p, I.qx, I.qy, I.qz, I.u, I.v, I.w, vb);
-        break;
+        correct_body<CG>(g, I.p, I.qx, I.qy, I.qz, I.u, I.v, I.w, vb);
     }
+}
+
+// Refinement-sweep passes: empty once the instance has converged.
+__host__ __device__ constexpr bool refine_kind(int kind) {
+    return kind == BK_XLOAD || kind == BK_YF32C || kind == BK_TH32C || kind == BK_YI32C ||
+           kind == BK_XACC || kind == BK_RCORR;
+}
+
+__device__ __forceinline__ void batch_run_tile(const BatchInst &I, const BatchItem &w, int tile,
+                                               unsigned char *smem) {
+#define FZ_RUN(K)                                    \
+    case K:                                          \
+        run_kind<K, true>(I, w.pass, tile, smem);    \
+        break;
+    switch (I.kind[w.pass]) {
+        FZ_RUN(BK_FLUX)
+        FZ_RUN(BK_SUM)
+        FZ_RUN(BK_XFWD64)
+        FZ_RUN(BK_YF64)
+        FZ_RUN(BK_TH64)
+        FZ_RUN(BK_YI64)
+        FZ_RUN(BK_XI64)
+        FZ_RUN(BK_XFWD_MIX)
+        FZ_RUN(BK_YF32)
+        FZ_RUN(BK_TH32)
+        FZ_RUN(BK_YI32)
+        FZ_RUN(BK_XI32)
+        FZ_RUN(BK_RES0)
+        FZ_RUN(BK_XLOAD)
+        FZ_RUN(BK_YF32C)
+        FZ_RUN(BK_TH32C)
+        FZ_RUN(BK_YI32C)
+        FZ_RUN(BK_XACC)
+        FZ_RUN(BK_RCORR)
+        FZ_RUN(BK_CORRIF)
+        FZ_RUN(BK_CORRECT)
     default:
         break;
     }
+#undef FZ_RUN
 }
 
 // Five resident CTAs per SM (48 registers; about 400 bytes of spills, served
@@ -231,8 +243,7 @@ __global__ void __launch_bounds__(BATCH_THREADS, 5) k_batch(BatchArgs A) {
         if (threadIdx.x == 0) {
             int ok = 1;
             const int kind = I.kind[w.pass];
-            const bool refine = kind == BK_XLOAD || kind == BK_YF32C || kind == BK_TH32C ||
-                                kind == BK_YI32C || kind == BK_XACC || kind == BK_RCORR;
+            const bool refine = refine_kind(kind);
             // refinement work of an instance that has already converged is
             // empty: publish it without waiting (the flag is set once, by the
             // last tile of a residual pass, and never cleared in the launch)
@@ -263,6 +274,116 @@ __global__ void __launch_bounds__(BATCH_THREADS, 5) k_batch(BatchArgs A) {
         __syncthreads();
         if (threadIdx.x == 0) atomicAdd(A.done + (size_t)w.inst * BATCH_MAXP + w.pass, w.ntile);
     }
+}
+
+// ---- Grouped form: pass s of many instances as one ordinary launch.
+//
+// The host captures one launch per (chain, pass index, pass kind): the tiles
+// of every instance of the chain whose pass s has that kind, numbered one
+// after another (segment i covers global tiles seg[i].tile0 onward).  Launch
+// order carries the dependencies, so no tile waits for another; each kernel
+// has its own registers and occupancy (the persistent kernel must fit the
+// largest body in one register budget).  Refinement tiles of an instance that
+// has converged return at once.  The z-solve uses the shared-memory cp.async
+// ring of the stand-alone kernel (32-line tiles) on wall-bounded z.
+struct GroupSeg {
+    int inst, tile0;
+};
+
+struct GroupArgs {
+    const BatchInst *insts;
+    const GroupSeg *seg;  // n_seg segments, ascending tile0, seg[0].tile0 = 0
+    int n_seg, pass, total;
+};
+
+__device__ __forceinline__ int group_seg(const GroupArgs &A, int t) {
+    int lo = 0, hi = A.n_seg - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (A.seg[mid].tile0 <= t) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// A segment whose tiles are all empty: a refinement pass of an instance that
+// has converged, or the conditional correction after a fused residual pass.
+template <int KIND>
+__device__ __forceinline__ bool seg_empty(const BatchInst &I) {
+    if constexpr (refine_kind(KIND)) return *(volatile const int *)&I.st->converged != 0;
+    if constexpr (KIND == BK_CORRIF) return *(volatile const int *)&I.st->n_resid != 1;
+    return false;
+}
+
+// The next tile of this block's stride past the end of segment s.
+__device__ __forceinline__ int skip_seg(const GroupArgs &A, int s, int t) {
+    const int end = s + 1 < A.n_seg ? A.seg[s + 1].tile0 : A.total;
+    return t + ((end - t + (int)gridDim.x - 1) / (int)gridDim.x) * (int)gridDim.x;
+}
+
+// Resident CTAs per SM the FP64-bound grouped kernels are compiled for: the
+// instance's constants and pointers live in registers here (kernel
+// parameters in the stand-alone kernels), which would otherwise cost them
+// occupancy.
+constexpr int group_min_blocks(int kind) {
+    return (kind == BK_FLUX_L || kind == BK_FLUX_G || kind == BK_RES0 || kind == BK_RCORR) ? 5 : 1;
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(BATCH_THREADS, group_min_blocks(KIND)) k_bgroup(GroupArgs A) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    for (int t = blockIdx.x; t < A.total;) {
+        const int s = group_seg(A, t);
+        const GroupSeg sg = A.seg[s];
+        const BatchInst &I = A.insts[sg.inst];
+        if (seg_empty<KIND>(I)) {
+            t = skip_seg(A, s, t);
+            continue;
+        }
+        run_kind<KIND, false>(I, A.pass, t - sg.tile0, smem_raw);
+        __syncthreads();  // shared memory is reused by the next tile
+        t += gridDim.x;
+    }
+}
+
+// z-solve of the grouped form: THOMAS_BLOCK lines per tile, the cp.async ring
+// on wall-bounded z, the register-prefetch cyclic solve on periodic z.
+template <typename T, bool C>
+__global__ void __launch_bounds__(THOMAS_BLOCK) k_bgroup_th(GroupArgs A) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    for (int t = blockIdx.x; t < A.total; t += gridDim.x) {
+        const int s = group_seg(A, t);
+        const GroupSeg sg = A.seg[s];
+        const BatchInst &I = A.insts[sg.inst];
+        const int *conv = C ? &I.st->converged : nullptr;
+        if (C && *(volatile const int *)conv) {
+            t = skip_seg(A, s, t) - (int)gridDim.x;
+            continue;
+        }
+        const int lb = (t - sg.tile0) * THOMAS_BLOCK;
+        if constexpr (sizeof(T) == 8) {
+            if (I.g.perz)
+                thomas_body<double, false, false>(I.g, I.Ux, I.Uy, I.mtab64, I.ibtab64, I.cup64, I.fhat64,
+                                                  nullptr, lb, nullptr, I.wtab64, I.qtab64);
+            else
+                thomas_body<double, true, false>(I.g, I.Ux, I.Uy, I.mtab64, I.ibtab64, I.cup64, I.fhat64,
+                                                 nullptr, lb, (double *)smem_raw);
+        } else {
+            if (I.g.perz)
+                thomas_body<float, false, false>(I.g, I.Ux, I.Uy, I.mtab32, I.ibtab32, I.cup32, I.fhat32,
+                                                 conv, lb, nullptr, I.wtab32, I.qtab32);
+            else
+                thomas_body<float, true, false>(I.g, I.Ux, I.Uy, I.mtab32, I.ibtab32, I.cup32, I.fhat32,
+                                                conv, lb, (float *)smem_raw);
+        }
+    }
+}
+
+// Zero every instance's stats (block i: instance i) before a grouped solve.
+__global__ void k_bgroup_reset(const BatchInst *insts, int n) {
+    if ((int)blockIdx.x >= n) return;
+    unsigned *s = (unsigned *)insts[blockIdx.x].st;
+    for (int i = threadIdx.x; i < (int)(sizeof(DevStats) / sizeof(unsigned)); i += blockDim.x) s[i] = 0u;
 }
 
 }  // namespace fz

@@ -129,3 +129,17 @@ def test_dirichlet_and_mixed_boundary_descriptors():
     fake = [ctypes.c_void_p(8)] * 7
     assert _abi.lib().fizzy_proj_solve_noalloc(ctypes.byref(d), *fake, None) == -2
     assert _abi.lib().fizzy_poisson_solve(None, None, None, None, None) == -1
+
+
+def test_batch_tuning_struct_matches_header():
+    """The ctypes mirror of fizzy_batch_tuning lists the header's int fields
+    in the header's order (a mismatch would shift every field)."""
+    import re
+    from paper_2502_04189_b300 import _abi
+    hdr = open(os.path.join(os.path.dirname(__file__), "..", "include", "fizzy_proj.h")).read()
+    body = re.search(r"typedef struct fizzy_batch_tuning \{(.*?)\} fizzy_batch_tuning;", hdr, re.S).group(1)
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    names = re.findall(r"int\s+(\w+)\s*;", body)
+    assert names == [n for n, _ in _abi.Tuning._fields_]
+    assert ctypes.sizeof(_abi.Tuning) == 4 * len(names)
+

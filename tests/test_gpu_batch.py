@@ -207,3 +207,76 @@ def test_batch_wait_timeout_is_reported_and_recoverable(cuda_ok):
     batch.close()
     for p in plans:
         p.close()
+
+
+FORMS = [dict(form=1, chains=1), dict(form=1, chains=2), dict(form=1, chains=8, flux_planes=32),
+         dict(order=2)]
+FORM_IDS = ["grouped1", "grouped2", "grouped8", "staggered"]
+
+
+@pytest.mark.parametrize("precision", [F.MIXED, F.FP64], ids=["mixed", "fp64"])
+@pytest.mark.parametrize("tuning", FORMS, ids=FORM_IDS)
+def test_batch_forms_equal_alone(cuda_ok, precision, tuning):
+    """The grouped launches (one ordinary launch per pass over every instance
+    of a chain, 1, 2 or 8 concurrent chains) and the staggered work list run
+    the same bodies: each instance equals its solve alone bit for bit, here
+    with a swapped-density instance among them."""
+    import dataclasses
+    import torch
+    specs = small_batch_specs(5)
+    specs.append(dataclasses.replace(specs[1], rho_l=specs[1].rho_g, rho_g=specs[1].rho_l))
+    cases = [I.make_case(s) for s in specs]
+    alone = [run_alone(c, precision) for c in cases]
+    plans = [F.Plan.for_case(c, precision=precision) for c in cases]
+    arrays = [(to_dev(c.phi), to_dev(c.pn), to_dev(c.pnm1), to_dev(c.u), to_dev(c.v), to_dev(c.w),
+               torch.empty(c.shape, dtype=torch.float64, device="cuda")) for c in cases]
+    batch = F.Batch(plans, arrays, tuning=tuning)
+    info = batch.info()
+    assert info["items"] >= 7 and info["grid"] >= 1
+    for rep in range(2):
+        for c, arr in zip(cases, arrays):
+            arr[3].copy_(to_dev(c.u))
+            arr[4].copy_(to_dev(c.v))
+            arr[5].copy_(to_dev(c.w))
+        batch.solve()
+        assert batch.status() == 0
+        for c, arr, a, plan in zip(cases, arrays, alone, plans):
+            for key, t in (("p", arr[6]), ("u", arr[3]), ("v", arr[4]), ("w", arr[5])):
+                assert np.array_equal(t.cpu().numpy(), a[key]), (c.spec, key, rep)
+            st = plan.stats()
+            assert st["converged"] == 1
+            assert st["iterations"] == a["stats"]["iterations"]
+    if tuning.get("form") == 1:
+        with pytest.raises(F.FizzyError):
+            batch.inject_stall(inst=0, spin_limit=16)  # no waits in the grouped form
+    batch.close()
+    for p in plans:
+        p.close()
+
+
+@pytest.mark.parametrize("precision", [F.MIXED, F.FP64], ids=["mixed", "fp64"])
+def test_batch_grouped_equals_persistent_on_uneven_batch(cuda_ok, precision):
+    """All 64 instances of the uneven-batch recipe (sizes 32-192, every
+    boundary mix, lengths of the register-resident passes included): the
+    grouped form with two chains gives the persistent launch's bits."""
+    import torch
+    cases = [I.make_case(s) for s in I.batch_specs(64)]
+    plans = [F.Plan.for_case(c, precision=precision) for c in cases]
+    outs = {}
+    for name, tun in (("persistent", None), ("grouped", dict(form=1, chains=2))):
+        arrays = [(to_dev(c.phi), to_dev(c.pn), to_dev(c.pnm1), to_dev(c.u), to_dev(c.v),
+                   to_dev(c.w), torch.empty(c.shape, dtype=torch.float64, device="cuda"))
+                  for c in cases]
+        batch = F.Batch(plans, arrays, tuning=tun)
+        batch.solve()
+        assert batch.status() == 0
+        outs[name] = [[a[k].cpu().numpy() for k in (6, 3, 4, 5)] for a in arrays]
+        outs[name + "_iters"] = [p.stats()["iterations"] for p in plans]
+        batch.close()
+        del arrays
+    for c, a, b in zip(cases, outs["persistent"], outs["grouped"]):
+        for x, y, key in zip(a, b, "puvw"):
+            assert np.array_equal(x, y), (c.spec, key)
+    assert outs["persistent_iters"] == outs["grouped_iters"]
+    for p in plans:
+        p.close()
