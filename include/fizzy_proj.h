@@ -303,11 +303,13 @@ int fizzy_proj_timing(fizzy_proj_plan_t p, int idx, const char **name, double *m
  * (instance, pass, tile) items; an item waits (bounded spin) until every tile
  * of its instance's previous pass is done.  Grouped form: one ordinary launch
  * per pass covers that pass of every instance (of a chain), so launch order
- * carries the dependencies.  Results are the same in both forms and equal
- * each plan's own fizzy_proj_solve (same kernel bodies, same arithmetic per
- * tile; a mixed plan with an x or y length of 128, 256 or 512 solved alone
- * runs register-resident FP32 transform passes instead, within the mixed
- * tolerance).
+ * carries the dependencies.  Solo-chain form: each instance's own
+ * stand-alone launch sequence, instances on concurrent chains.  Results are
+ * the same in every form and equal each plan's own fizzy_proj_solve (same
+ * kernel bodies, same arithmetic per tile), except that a mixed plan with an
+ * x or y length the register-resident FP32 transform passes cover runs them
+ * alone and in the solo-chain form, and the Stockham passes in the other two
+ * forms (the results agree within the mixed tolerance).
  *
  * arrays: 7*n device pointers, for instance i at 7i..7i+6:
  *         phi, p_n, p_nm1, u, v, w (u*, in/out), p_np1 -- fixed for the batch
@@ -330,10 +332,12 @@ typedef struct fizzy_batch_tuning {
                         alternate by size, four passes behind the other half)  */
     int form;        /* 0 persistent launch; 1 grouped: one ordinary launch per
                         pass index and pass kind, covering the tiles of every
-                        instance at that pass (no dependency waits)            */
-    int chains;      /* grouped form: instances split (by size, round robin)
+                        instance at that pass (no dependency waits); 2 solo
+                        chains: each instance's own fizzy_proj_solve launch
+                        sequence, captured                                     */
+    int chains;      /* forms 1 and 2: instances split (by size, round robin)
                         into this many independent launch chains that the
-                        graph runs concurrently (1..8); 0 = 1                  */
+                        graph runs concurrently (1..16); 0 = 1                 */
 } fizzy_batch_tuning;
 
 /* Build the batch (work list, device descriptors) and capture its graph.
@@ -357,8 +361,8 @@ int fizzy_proj_batch_status(fizzy_proj_batch_t b, void *stream);
  * that solve invalid); the context stays usable.  inst = -1 and
  * spin_limit = 0 restore the defaults (no stall, 2^26 polls).  Returns
  * FIZZY_ERR_INVALID for a null batch or out-of-range arguments,
- * FIZZY_ERR_UNSUPPORTED for a batch built in the grouped form (it has no
- * dependency waits), else the status of the rebuild. */
+ * FIZZY_ERR_UNSUPPORTED for a batch built in the grouped or solo-chain form
+ * (they have no dependency waits), else the status of the rebuild. */
 int fizzy_proj_batch_inject_stall(fizzy_proj_batch_t b, int inst, long long spin_limit);
 
 /* Time candidate tunings (reps replays each, CUDA events on stream), rebuild
@@ -366,7 +370,7 @@ int fizzy_proj_batch_inject_stall(fizzy_proj_batch_t b, int inst, long long spin
  * *best_ms (either may be NULL).  The candidates cover both forms: the
  * persistent launch with varied CTAs per SM, flux planes per tile, x-pass
  * lines per tile, y-pass columns per tile and work-list order, and the
- * grouped launches with 2, 4 or 8 chains.  Overwrites the batch outputs while
+ * grouped launches with 2, 4 or 8 chains, and the solo chains with 8 or 16.  Overwrites the batch outputs while
  * timing. */
 int fizzy_proj_batch_autotune(fizzy_proj_batch_t b, int reps, fizzy_batch_tuning *chosen,
                               double *best_ms, void *stream);

@@ -135,7 +135,8 @@ def test_batch_autotune_keeps_results(cuda_ok):
                        to_dev(c.w), torch.empty(c.shape, dtype=torch.float64, device="cuda")))
     batch = F.Batch(plans, arrays)
     tuning, ms = batch.autotune(reps=2)
-    assert ms > 0 and tuning["flux_planes"] in (16, 32)
+    assert ms > 0 and tuning["form"] in (0, 1, 2)
+    assert tuning["form"] == 2 or tuning["flux_planes"] in (16, 32)  # solo chains keep the plan's tiles
     for c, arr in zip(cases, arrays):
         arr[3].copy_(to_dev(c.u))
         arr[4].copy_(to_dev(c.v))
@@ -143,7 +144,8 @@ def test_batch_autotune_keeps_results(cuda_ok):
     batch.solve()
     assert batch.status() == 0
     for c, arr in zip(cases, arrays):
-        a = run_alone(c, F.MIXED)
+        # the solo-chain form runs each plan's own passes
+        a = run_plain(c, F.MIXED) if tuning["form"] == 2 else run_alone(c, F.MIXED)
         assert np.array_equal(arr[6].cpu().numpy(), a["p"])
         assert np.array_equal(arr[3].cpu().numpy(), a["u"])
     batch.close()
@@ -278,5 +280,51 @@ def test_batch_grouped_equals_persistent_on_uneven_batch(cuda_ok, precision):
         for x, y, key in zip(a, b, "puvw"):
             assert np.array_equal(x, y), (c.spec, key)
     assert outs["persistent_iters"] == outs["grouped_iters"]
+    for p in plans:
+        p.close()
+
+
+@pytest.mark.parametrize("precision", [F.MIXED, F.FP64], ids=["mixed", "fp64"])
+@pytest.mark.parametrize("chains", [1, 3, 16])
+def test_batch_solo_chains_equal_plain(cuda_ok, precision, chains):
+    """The solo-chain form replays each instance's own stand-alone launch
+    sequence on concurrent chains: every instance equals its plain solve bit
+    for bit (register-resident FP32 passes included), over two replays, and
+    the largest matches the oracle."""
+    import dataclasses
+    import torch
+    specs = small_batch_specs(5)
+    specs.append(dataclasses.replace(specs[1], rho_l=specs[1].rho_g, rho_g=specs[1].rho_l))
+    specs += sorted((s for s in I.batch_specs(64) if s.nx in R_LENGTHS or s.ny in R_LENGTHS),
+                    key=lambda s: s.nx * s.ny * s.nz)[:2]
+    cases = [I.make_case(s) for s in specs]
+    plain = [run_plain(c, precision) for c in cases]
+    plans = [F.Plan.for_case(c, precision=precision) for c in cases]
+    arrays = [(to_dev(c.phi), to_dev(c.pn), to_dev(c.pnm1), to_dev(c.u), to_dev(c.v), to_dev(c.w),
+               torch.empty(c.shape, dtype=torch.float64, device="cuda")) for c in cases]
+    batch = F.Batch(plans, arrays, tuning=dict(form=2, chains=chains))
+    assert batch.info()["items"] == len(cases)
+    for rep in range(2):
+        for c, arr in zip(cases, arrays):
+            arr[3].copy_(to_dev(c.u))
+            arr[4].copy_(to_dev(c.v))
+            arr[5].copy_(to_dev(c.w))
+        batch.solve()
+        assert batch.status() == 0
+        for c, arr, a, plan in zip(cases, arrays, plain, plans):
+            for key, t in (("p", arr[6]), ("u", arr[3]), ("v", arr[4]), ("w", arr[5])):
+                assert np.array_equal(t.cpu().numpy(), a[key]), (c.spec, key, rep)
+            st = plan.stats()
+            assert st["converged"] == 1 and st["iterations"] == a["stats"]["iterations"]
+    with pytest.raises(F.FizzyError):
+        batch.inject_stall(inst=0, spin_limit=16)  # no waits in the solo-chain form
+    k = max(range(len(cases)), key=lambda i: cases[i].npts)
+    ref = O.project_case(cases[k])
+    got = dict(p=arrays[k][6].cpu().numpy(), u=arrays[k][3].cpu().numpy(),
+               v=arrays[k][4].cpu().numpy(), w=arrays[k][5].cpu().numpy())
+    ep, eu = compare(cases[k], got, ref)
+    tol = 1e-9 if precision == F.MIXED else 1e-12
+    assert ep <= tol and eu <= tol, (ep, eu)
+    batch.close()
     for p in plans:
         p.close()
