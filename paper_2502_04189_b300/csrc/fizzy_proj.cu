@@ -97,7 +97,8 @@ struct fizzy_proj_plan_s {
     int host_calls = 0;
     // launch shapes
     int Lx = 1, TXy = 2;
-    int x_r16 = 0;  // mixed, nx = 128, 256 or 512: register-resident FP32 x-passes
+    int x_r16 = 0;  // mixed, nx of a register-resident length: register-resident FP32 x-passes
+    int xthr32 = 256, ythr32 = 256;  // threads per CTA of the FP32 x- and y-pass kernels
     // mixed, nx = ny = 256 or 512, periodic or wall x/y: fused x-y cluster passes
     int xy_fused = 0;
     XYFwdK xyf_div = nullptr, xyf_load = nullptr;
@@ -509,15 +510,13 @@ PassKernels pick_kernels(int fx, int fy) {
     return fx == 256 ? kernels_for_y<256>(fy) : fx == 512 ? kernels_for_y<512>(fy) : kernels_for_y<0>(fy);
 }
 
-// The length of a direction that has register-resident FP32 passes (any
-// boundary; 0: none).
-// (64 would fit the same transform, 16 x 4, but its 64 lines per CTA leave
-// a 64^3 grid 32 x-pass tiles for 148 SMs: slower than the Stockham passes.)
-int r_len(int n) { return (n == 128 || n == 256 || n == 512) ? n : 0; }
+// The length of a direction that has register-resident FP32 passes
+// (periodic or Neumann; 0: none).
+int r_len(int n) { return r_supported(n) ? n : 0; }
 
 // Mixed plans: the register-resident FP32 passes (static shared memory, no
-// opt-in) replace the Stockham ones along a direction of length 128, 256
-// or 512.
+// opt-in) replace the Stockham ones along a direction of a supported
+// length.
 template <int N, int KIND> void r_kernels_x(PassKernels &k) {
     k.xf32d = k_xfwd_r_divq<N, KIND>;
     k.xf32l = k_xfwd_r_load<N, KIND>;
@@ -528,14 +527,38 @@ template <int N, int KIND> void r_kernels_y(PassKernels &k) {
     k.yf32 = k_ypass_r<false, N, KIND>;
     k.yi32 = k_ypass_r<true, N, KIND>;
 }
+template <int N> void r_kernels_xn(PassKernels &k, bool dct) {
+    dct ? r_kernels_x<N, KIND_DCT>(k) : r_kernels_x<N, KIND_PERIODIC>(k);
+}
+template <int N> void r_kernels_yn(PassKernels &k, bool dct) {
+    dct ? r_kernels_y<N, KIND_DCT>(k) : r_kernels_y<N, KIND_PERIODIC>(k);
+}
 void pick_r_kernels(PassKernels &k, int nx, int bcx, int ny, int bcy) {
     const bool dx = bcx == FIZZY_BC_NEUMANN, dy = bcy == FIZZY_BC_NEUMANN;
-    if (nx == 128) dx ? r_kernels_x<128, KIND_DCT>(k) : r_kernels_x<128, KIND_PERIODIC>(k);
-    if (nx == 256) dx ? r_kernels_x<256, KIND_DCT>(k) : r_kernels_x<256, KIND_PERIODIC>(k);
-    if (nx == 512) dx ? r_kernels_x<512, KIND_DCT>(k) : r_kernels_x<512, KIND_PERIODIC>(k);
-    if (ny == 128) dy ? r_kernels_y<128, KIND_DCT>(k) : r_kernels_y<128, KIND_PERIODIC>(k);
-    if (ny == 256) dy ? r_kernels_y<256, KIND_DCT>(k) : r_kernels_y<256, KIND_PERIODIC>(k);
-    if (ny == 512) dy ? r_kernels_y<512, KIND_DCT>(k) : r_kernels_y<512, KIND_PERIODIC>(k);
+    switch (nx) {
+    case 32: r_kernels_xn<32>(k, dx); break;
+    case 48: r_kernels_xn<48>(k, dx); break;
+    case 64: r_kernels_xn<64>(k, dx); break;
+    case 96: r_kernels_xn<96>(k, dx); break;
+    case 128: r_kernels_xn<128>(k, dx); break;
+    case 192: r_kernels_xn<192>(k, dx); break;
+    case 256: r_kernels_xn<256>(k, dx); break;
+    case 384: r_kernels_xn<384>(k, dx); break;
+    case 512: r_kernels_xn<512>(k, dx); break;
+    default: break;
+    }
+    switch (ny) {
+    case 32: r_kernels_yn<32>(k, dy); break;
+    case 48: r_kernels_yn<48>(k, dy); break;
+    case 64: r_kernels_yn<64>(k, dy); break;
+    case 96: r_kernels_yn<96>(k, dy); break;
+    case 128: r_kernels_yn<128>(k, dy); break;
+    case 192: r_kernels_yn<192>(k, dy); break;
+    case 256: r_kernels_yn<256>(k, dy); break;
+    case 384: r_kernels_yn<384>(k, dy); break;
+    case 512: r_kernels_yn<512>(k, dy); break;
+    default: break;
+    }
 }
 
 // The fused x-y cluster kernels of a length and transform kinds.
@@ -624,17 +647,17 @@ void opt_in_smem(fizzy_proj_plan_t p, int bytes) {
 // sx32r: dynamic shared memory of the FP32 x-passes (0 for the
 // register-resident ones)
 void pass_caps(int *cap, const PassKernels &k, size_t sx64, size_t sx32, size_t sx32r, size_t sy64,
-               size_t sy32) {
+               size_t sy32, int tx32, int ty32) {
     cap[CAP_XF64] = resident_grid(k.xf64, 256, sx64);
-    cap[CAP_XF32D] = resident_grid(k.xf32d, 256, sx32r);
-    cap[CAP_XF32L] = resident_grid(k.xf32l, 256, sx32r);
+    cap[CAP_XF32D] = resident_grid(k.xf32d, tx32, sx32r);
+    cap[CAP_XF32L] = resident_grid(k.xf32l, tx32, sx32r);
     cap[CAP_Y64F] = resident_grid(k.yf64, 256, sy64);
     cap[CAP_Y64I] = resident_grid(k.yi64, 256, sy64);
-    cap[CAP_Y32F] = resident_grid(k.yf32, 256, sy32);
-    cap[CAP_Y32I] = resident_grid(k.yi32, 256, sy32);
+    cap[CAP_Y32F] = resident_grid(k.yf32, ty32, sy32);
+    cap[CAP_Y32I] = resident_grid(k.yi32, ty32, sy32);
     cap[CAP_XI64] = resident_grid(k.xi64, 256, sx64);
-    cap[CAP_XI32S] = resident_grid(k.xi32s, 256, sx32r);
-    cap[CAP_XI32A] = resident_grid(k.xi32a, 256, sx32r);
+    cap[CAP_XI32S] = resident_grid(k.xi32s, tx32, sx32r);
+    cap[CAP_XI32A] = resident_grid(k.xi32a, tx32, sx32r);
     cap[CAP_TH64] = resident_grid(k_thomas<double>, THOMAS_BLOCK, thomas_smem<double>());
     cap[CAP_TH32] = resident_grid(k_thomas<float>, THOMAS_BLOCK, thomas_smem<float>());
     cap[CAP_TH64C] = resident_grid(k_thomas_cyc<double>, THOMAS_BLOCK, thomas_cyc_smem<double>());
@@ -918,8 +941,10 @@ int fizzy_proj_plan(fizzy_proj_plan_t *out, const fizzy_proj_desc *d, void *stre
         (d->flags & FIZZY_FLAG_FUSED_XY))
         p->xy_fused = setup_xy(p, nx, d->bc_x == FIZZY_BC_NEUMANN ? KIND_DCT : KIND_PERIODIC,
                                d->bc_y == FIZZY_BC_NEUMANN ? KIND_DCT : KIND_PERIODIC);
+    p->xthr32 = p->x_r16 ? r_threads(nx) : 256;
+    p->ythr32 = y_r16 ? r_threads(ny) : 256;
     pass_caps(p->cap, p->kern, p->smem_x64, p->smem_x32, p->x_r16 ? 0 : p->smem_x32, p->smem_y64,
-              p->smem_y32);
+              p->smem_y32, p->xthr32, p->ythr32);
     // stream-ordered plans are ready for work queued after them on their
     // stream; other plans are complete on return
     cudaError_t e = p->async_alloc ? cudaGetLastError() : cudaDeviceSynchronize();
@@ -1126,8 +1151,8 @@ int fizzy_proj_solve(fizzy_proj_plan_t p, const double *phi, const double *p_n, 
         if (p->xy_fused) {
             TIMED(KS_XFWD, (p->xyf_div<<<xyg, p->xy_threads, p->xy_smem, s>>>(g, xa)));
         } else {
-            TIMED(KS_XFWD, (p->kern.xf32d<<<grid(xrt, CAP_XF32D), 256, smx32r, s>>>(g, p->fx.d32, p->Lx, xa, xrt)));
-            TIMED(KS_YFWD, (p->kern.yf32<<<grid(ytiles, CAP_Y32F), 256, p->smem_y32, s>>>(nx, ny, p->fy.d32, p->TXy, p->fhat32, nullptr, ygx, ytiles)));
+            TIMED(KS_XFWD, (p->kern.xf32d<<<grid(xrt, CAP_XF32D), p->xthr32, smx32r, s>>>(g, p->fx.d32, p->Lx, xa, xrt)));
+            TIMED(KS_YFWD, (p->kern.yf32<<<grid(ytiles, CAP_Y32F), p->ythr32, p->smem_y32, s>>>(nx, ny, p->fy.d32, p->TXy, p->fhat32, nullptr, ygx, ytiles)));
         }
         if (g.perz)
             TIMED(KS_THOMAS, (k_thomas_cyc<float><<<grid(ttiles, CAP_TH32C), THOMAS_BLOCK, thomas_cyc_smem<float>(), s>>>(g, p->Ux, p->Uy, p->mtab32, p->ibtab32, p->cup32, p->wtab32, p->qtab32, p->fhat32, nullptr, ttiles)));
@@ -1136,8 +1161,8 @@ int fizzy_proj_solve(fizzy_proj_plan_t p, const double *phi, const double *p_n, 
         if (p->xy_fused) {
             TIMED(KS_XINV, (p->xyi_store<<<xyg, p->xy_threads, p->xy_smem, s>>>(g, p->fhat32, p_np1, p->st)));
         } else {
-            TIMED(KS_YINV, (p->kern.yi32<<<grid(ytiles, CAP_Y32I), 256, p->smem_y32, s>>>(nx, ny, p->fy.d32, p->TXy, p->fhat32, nullptr, ygx, ytiles)));
-            TIMED(KS_XINV, (p->kern.xi32s<<<grid(xrt, CAP_XI32S), 256, smx32r, s>>>(g, p->fx.d32, p->Lx, p->fhat32, p_np1, p->st, xrt)));
+            TIMED(KS_YINV, (p->kern.yi32<<<grid(ytiles, CAP_Y32I), p->ythr32, p->smem_y32, s>>>(nx, ny, p->fy.d32, p->TXy, p->fhat32, nullptr, ygx, ytiles)));
+            TIMED(KS_XINV, (p->kern.xi32s<<<grid(xrt, CAP_XI32S), p->xthr32, smx32r, s>>>(g, p->fx.d32, p->Lx, p->fhat32, p_np1, p->st, xrt)));
         }
         // residual of the FP32 solution (slot 0), then refinement sweeps
         // sw = 1..max_refine: transform of the stored residual, FP32 y/z/y^-1,
@@ -1167,8 +1192,8 @@ int fizzy_proj_solve(fizzy_proj_plan_t p, const double *phi, const double *p_n, 
             if (p->xy_fused) {
                 TIMED(KS_XFWD_R, (p->xyf_load<<<xyg, p->xy_threads, p->xy_smem, s>>>(g, la)));
             } else {
-                TIMED(KS_XFWD_R, (p->kern.xf32l<<<gs(xrt, CAP_XF32L), 256, smx32r, s>>>(g, p->fx.d32, p->Lx, la, xrt)));
-                TIMED(KS_YFWD_R, (p->kern.yf32<<<gs(ytiles, CAP_Y32F), 256, p->smem_y32, s>>>(nx, ny, p->fy.d32, p->TXy, p->fhat32, conv, ygx, ytiles)));
+                TIMED(KS_XFWD_R, (p->kern.xf32l<<<gs(xrt, CAP_XF32L), p->xthr32, smx32r, s>>>(g, p->fx.d32, p->Lx, la, xrt)));
+                TIMED(KS_YFWD_R, (p->kern.yf32<<<gs(ytiles, CAP_Y32F), p->ythr32, p->smem_y32, s>>>(nx, ny, p->fy.d32, p->TXy, p->fhat32, conv, ygx, ytiles)));
             }
             if (g.perz)
                 TIMED(KS_THOMAS_R, (k_thomas_cyc<float><<<gs(ttiles, CAP_TH32C), THOMAS_BLOCK, thomas_cyc_smem<float>(), s>>>(g, p->Ux, p->Uy, p->mtab32, p->ibtab32, p->cup32, p->wtab32, p->qtab32, p->fhat32, conv, ttiles)));
@@ -1177,8 +1202,8 @@ int fizzy_proj_solve(fizzy_proj_plan_t p, const double *phi, const double *p_n, 
             if (p->xy_fused) {
                 TIMED(KS_XACC, (p->xyi_accum<<<xyg, p->xy_threads, p->xy_smem, s>>>(g, p->fhat32, p_np1, p->st)));
             } else {
-                TIMED(KS_YINV_R, (p->kern.yi32<<<gs(ytiles, CAP_Y32I), 256, p->smem_y32, s>>>(nx, ny, p->fy.d32, p->TXy, p->fhat32, conv, ygx, ytiles)));
-                TIMED(KS_XACC, (p->kern.xi32a<<<gs(xrt, CAP_XI32A), 256, smx32r, s>>>(g, p->fx.d32, p->Lx, p->fhat32, p_np1, p->st, xrt)));
+                TIMED(KS_YINV_R, (p->kern.yi32<<<gs(ytiles, CAP_Y32I), p->ythr32, p->smem_y32, s>>>(nx, ny, p->fy.d32, p->TXy, p->fhat32, conv, ygx, ytiles)));
+                TIMED(KS_XACC, (p->kern.xi32a<<<gs(xrt, CAP_XI32A), p->xthr32, smx32r, s>>>(g, p->fx.d32, p->Lx, p->fhat32, p_np1, p->st, xrt)));
             }
             ra.slot = sw;
             TIMED(KS_RCORR, (k_resid<true><<<gs(rctiles, CAP_RC), rcb, 0, s>>>(g, RESID_KC, ra, rtgx, rtgy, rctiles)));

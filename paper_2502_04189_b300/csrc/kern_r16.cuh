@@ -1,28 +1,31 @@
-// Register-resident FP32 transforms of length 128, 256 and 512 (mixed mode).
+// Register-resident FP32 transforms of length 32, 48, 64, 96, 128, 192, 256,
+// 384 and 512 (mixed mode).
 //
 // The FP32 transform passes of the mixed-precision solve (the fast direct
-// solver's real FFTs, or DCT-II for wall directions, along x and y).  A DFT of length
-// N = 16 M (M = 8, 16; 4 builds too) is split 16 x M, the four-step form of
-// the Cooley-Tukey factorisation: with n = M n1 + n2 and k = k1 + 16 k2,
-//     X[k1 + 16 k2] = sum_n2 WM^(n2 k2) [ WN^(n2 k1) sum_n1 x[M n1 + n2] W16^(n1 k1) ],
-// W_N = exp(-2 pi i / N) (the inverse uses the conjugates; neither direction
+// solver's real FFTs, or DCT-II for wall directions, along x and y).  A DFT of
+// length NH = P M (P = 12, 16 or 24 values per thread, M = 2, 4, 8 or 16
+// threads, M dividing P) is split P x M, the four-step form of the
+// Cooley-Tukey factorisation: with n = M n1 + n2 and k = k1 + P k2,
+//     X[k1 + P k2] = sum_n2 WM^(n2 k2) [ WNH^(n2 k1) sum_n1 x[M n1 + n2] WP^(n1 k1) ],
+// W_L = exp(-2 pi i / L) (the inverse uses the conjugates; neither direction
 // is scaled).  A complex line (two real lines as real and imaginary part) is
 // held by M threads: thread t owns the samples x[M n1 + t], computes their
-// 16-point DFT in registers and applies the twiddles WN^(t k1); one pass
-// through shared memory then hands it the values of k1 = t + M j, whose
-// M-point DFTs give X[t + M j + 16 k2].  The separation of the two real
-// spectra (forward) pairs X[k] with X[N - k], held in register 15 - r of
-// thread (M - t) mod M of the same line, through warp shuffles; the inverse
-// combination reads both values of a pair.  A wall direction keeps
-// Makhoul's packing of the DCT-II (even samples forward, odd backward) and
-// applies the post-twiddles (cos, sin)(pi m / (2N)) in the separation and
-// combination.
+// P-point DFT in registers (16 = 4 x 4, 12 = 3 x 4, 24 = 3 x 8) and applies
+// the twiddles WNH^(t k1); one pass through shared memory then hands it the
+// values of k1 = t + M j (j < P/M), whose M-point DFTs give
+// X[t + M j + P k2].  The separation of the two real spectra (forward) pairs
+// X[k] with X[N - k], held in register P - 1 - r of thread (M - t) mod M of
+// the same line, through warp shuffles; the inverse combination reads both
+// values of a pair.  A wall direction keeps Makhoul's packing of the DCT-II
+// (even samples forward, odd backward) and applies the post-twiddles
+// (cos, sin)(pi m / (2N)) in the separation and combination.
 //
-// Length 512 first takes one radix-2 step of decimation in frequency,
-//     X[2k]     = DFT256( x[n] + x[n + 256] )[k],
-//     X[2k + 1] = DFT256( (x[n] - x[n + 256]) W512^n )[k],
-// over two groups of 16 threads (a warp per line) that swap their halves
-// with one shuffle; each group then runs the 256-point transform.
+// Lengths 384 and 512 first take one radix-2 step of decimation in
+// frequency, N = 2 NH,
+//     X[2k]     = DFT_NH( x[n] + x[n + NH] )[k],
+//     X[2k + 1] = DFT_NH( (x[n] - x[n + NH]) W_N^n )[k],
+// over two groups of M threads of a line that swap their halves with one
+// shuffle; each group then runs the NH-point transform.
 //
 // Same arithmetic as the Stockham passes (about 11 FP32 multiply-adds per
 // real point at n = 256); what it removes is their per-stage shared-memory
@@ -39,6 +42,29 @@ __device__ __forceinline__ float2 c_mul(float2 a, float c, float s) {
     return make_float2(fmaf(a.x, c, -a.y * s), fmaf(a.x, s, a.y * c));
 }
 
+// 2-point DFT in place.
+__device__ __forceinline__ void dft2(float2 &a0, float2 &a1) {
+    const float2 t = a0;
+    a0 = c_add(t, a1);
+    a1 = c_sub(t, a1);
+}
+
+// 3-point DFT in place (forward: W3 = -1/2 - i sqrt(3)/2).
+template <bool INV>
+__device__ __forceinline__ void dft3(float2 &a0, float2 &a1, float2 &a2) {
+    constexpr float H = 0.86602540378443864676f;  // sqrt(3)/2
+    const float2 s = c_add(a1, a2), d = c_sub(a1, a2);
+    const float2 m = make_float2(fmaf(-0.5f, s.x, a0.x), fmaf(-0.5f, s.y, a0.y));
+    a0 = c_add(a0, s);
+    if (!INV) {  // X1 = m - i H d, X2 = m + i H d
+        a1 = make_float2(fmaf(H, d.y, m.x), fmaf(-H, d.x, m.y));
+        a2 = make_float2(fmaf(-H, d.y, m.x), fmaf(H, d.x, m.y));
+    } else {
+        a1 = make_float2(fmaf(-H, d.y, m.x), fmaf(H, d.x, m.y));
+        a2 = make_float2(fmaf(H, d.y, m.x), fmaf(-H, d.x, m.y));
+    }
+}
+
 // 4-point DFT in place (forward: W4 = -i).
 template <bool INV>
 __device__ __forceinline__ void dft4(float2 &a0, float2 &a1, float2 &a2, float2 &a3) {
@@ -52,6 +78,44 @@ __device__ __forceinline__ void dft4(float2 &a0, float2 &a1, float2 &a2, float2 
         a1 = make_float2(t1.x - t3.y, t1.y + t3.x);
         a3 = make_float2(t1.x + t3.y, t1.y - t3.x);
     }
+}
+
+// v times W24^e (forward) or its conjugate (INV), 0 <= e < 24; e is a
+// compile-time value once the callers' loops are unrolled.  cos and sin of
+// pi e / 12 from the exact values of 15-degree multiples:
+// cos 15 = (sqrt 6 + sqrt 2)/4, sin 15 = (sqrt 6 - sqrt 2)/4.
+__device__ __forceinline__ float cos_pi12(int e) {
+    constexpr float C15 = 0.96592582628906828675f, S15 = 0.25881904510252076235f;
+    constexpr float H3 = 0.86602540378443864676f, H2 = 0.70710678118654752440f;
+    e = e % 24;
+    if (e > 12) e = 24 - e;  // cos is even about pi
+    switch (e) {
+    case 0: return 1.f;
+    case 1: return C15;
+    case 2: return H3;
+    case 3: return H2;
+    case 4: return 0.5f;
+    case 5: return S15;
+    case 6: return 0.f;
+    case 7: return -S15;
+    case 8: return -0.5f;
+    case 9: return -H2;
+    case 10: return -H3;
+    case 11: return -C15;
+    default: return -1.f;
+    }
+}
+__device__ __forceinline__ float sin_pi12(int e) { return cos_pi12(e + 18); }  // sin x = cos(x - pi/2)
+
+template <bool INV>
+__device__ __forceinline__ float2 w24(float2 v, int e) {
+    e %= 24;
+    if (e == 0) return v;
+    if (e == 12) return make_float2(-v.x, -v.y);
+    if (e == 6) return INV ? make_float2(-v.y, v.x) : make_float2(v.y, -v.x);  // -+ i
+    if (e == 18) return INV ? make_float2(v.y, -v.x) : make_float2(-v.y, v.x);  // +- i
+    const float s = sin_pi12(e);
+    return c_mul(v, cos_pi12(e), INV ? s : -s);
 }
 
 // v times W16^e (forward) or its conjugate (INV), e in {1, 2, 3, 4, 6, 9}.
@@ -79,8 +143,9 @@ __device__ __forceinline__ float2 w16(float2 v) {
 }
 
 // 16-point DFT of v[0..15] in place, natural order in and out (4 x 4 split).
-template <bool INV>
-__device__ __forceinline__ void dft16(float2 (&v)[16]) {
+template <bool INV, int S>
+__device__ __forceinline__ void dft16(float2 (&v)[S]) {
+    static_assert(S == 16, "dft16 works on 16 values");
 #pragma unroll
     for (int b = 0; b < 4; ++b) dft4<INV>(v[b], v[4 + b], v[8 + b], v[12 + b]);
     // v[4 k1 + b] now holds the k1-th output of column b: twiddle W16^(b k1)
@@ -107,8 +172,8 @@ __device__ __forceinline__ void dft16(float2 (&v)[16]) {
 
 // 8-point DFT of v[O..O+7] in place, natural order in and out: 4-point DFTs
 // of the even and the odd samples joined by W8^k (= W16^(2k)).
-template <bool INV, int O>
-__device__ __forceinline__ void dft8(float2 (&v)[16]) {
+template <bool INV, int O, int S>
+__device__ __forceinline__ void dft8(float2 (&v)[S]) {
     float2 e0 = v[O], e1 = v[O + 2], e2 = v[O + 4], e3 = v[O + 6];
     float2 o0 = v[O + 1], o1 = v[O + 3], o2 = v[O + 5], o3 = v[O + 7];
     dft4<INV>(e0, e1, e2, e3);
@@ -126,53 +191,113 @@ __device__ __forceinline__ void dft8(float2 (&v)[16]) {
     v[O + 7] = c_sub(e3, o3);
 }
 
-// Launch shape of a length.  N = 16 M (M = 4, 8, 16): M threads hold a
-// line, 16 values each; N = 512: a warp per line, two 16-thread groups.
-// Complex lines per CTA of 256 threads and per warp, the line stride in
-// shared memory (padded), and the y-pass tile width in real columns.
+// 12- and 24-point DFTs in place, natural order in and out: L = 3 Q with
+// n = Q n1 + n2, k = k1 + 3 k2: 3-point DFTs over n1, the twiddles
+// W_L^(n2 k1), then Q-point DFTs over n2 (Q = 4, 8).
+template <bool INV, int Q>
+__device__ __forceinline__ void dft3q(float2 (&v)[3 * Q]) {
+    float2 y[3 * Q];  // y[Q k1 + n2]
+#pragma unroll
+    for (int n2 = 0; n2 < Q; ++n2) {
+        float2 a = v[n2], b = v[Q + n2], c = v[2 * Q + n2];
+        dft3<INV>(a, b, c);
+        y[n2] = a;
+        y[Q + n2] = w24<INV>(b, (24 / (3 * Q)) * n2);
+        y[2 * Q + n2] = w24<INV>(c, (24 / (3 * Q)) * 2 * n2);
+    }
+    if constexpr (Q == 4) {
+#pragma unroll
+        for (int k1 = 0; k1 < 3; ++k1) dft4<INV>(y[4 * k1], y[4 * k1 + 1], y[4 * k1 + 2], y[4 * k1 + 3]);
+    } else {
+        dft8<INV, 0>(y);
+        dft8<INV, 8>(y);
+        dft8<INV, 16>(y);
+    }
+#pragma unroll
+    for (int k1 = 0; k1 < 3; ++k1)
+#pragma unroll
+        for (int k2 = 0; k2 < Q; ++k2) v[k1 + 3 * k2] = y[Q * k1 + k2];
+}
+
+// The P-point DFT of a thread's values.
+template <bool INV, int P>
+__device__ __forceinline__ void dft_p(float2 (&v)[P]) {
+    if constexpr (P == 16) dft16<INV>(v);
+    else if constexpr (P == 12) dft3q<INV, 4>(v);
+    else dft3q<INV, 8>(v);
+}
+
+constexpr bool r_supported(int n) {
+    return n == 32 || n == 48 || n == 64 || n == 96 || n == 128 || n == 192 || n == 256 || n == 384 ||
+           n == 512;
+}
+
+// Launch shape of a length.  G: 2 for the radix-2 step (384, 512), else 1;
+// NH = N / G = P M; TPL = G M threads hold a complex line; THREADS per CTA
+// (fewer for the short and the 24-value lengths, so that small grids still
+// spread over the SMs and the 24-value threads keep their registers);
+// LINES complex lines per CTA and LPW per warp, the line stride in shared
+// memory (padded), the y-pass tile width TX in real columns, and the
+// resident CTAs per SM the kernels are compiled for.
 template <int N> struct RShape {
-    static_assert(N == 64 || N == 128 || N == 256 || N == 512, "register-resident lengths");
-    static constexpr int M = N == 512 ? 16 : N / 16;  // threads of one 16 x M transform
-    static constexpr int TPL = N == 512 ? 32 : M;     // threads per line
-    static constexpr int LINES = 256 / TPL;
+    static_assert(r_supported(N), "register-resident lengths");
+    static constexpr int G = (N == 384 || N == 512) ? 2 : 1;
+    static constexpr int NH = N / G;
+    static constexpr int P = (NH % 3 != 0) ? 16 : (NH == 48 ? 12 : 24);
+    static constexpr int M = NH / P;
+    static constexpr int TPL = G * M;
+    static constexpr int THREADS = N == 32 ? 64 : (N == 128 || N == 256 || N == 512) ? 256 : 128;
+    static constexpr int LINES = THREADS / TPL;
     static constexpr int LPW = 32 / TPL;
     static constexpr int LS = N + 1;
     static constexpr int TX = 2 * LINES;
+    static constexpr int MINB = P == 24 ? 5 : P == 12 ? 6 : 65536 / (THREADS * 64);
+    static_assert(P % M == 0 && TPL <= 32 && TPL % 2 == 0, "shape");
 };
+constexpr int r_threads(int n) {
+    return n == 32 ? RShape<32>::THREADS : n == 48 ? RShape<48>::THREADS : n == 64 ? RShape<64>::THREADS
+         : n == 96 ? RShape<96>::THREADS : n == 128 ? RShape<128>::THREADS : n == 192 ? RShape<192>::THREADS
+         : n == 256 ? RShape<256>::THREADS : n == 384 ? RShape<384>::THREADS : RShape<512>::THREADS;
+}
 constexpr int r_tile_cols(int n) {
-    return n == 64 ? RShape<64>::TX : n == 128 ? RShape<128>::TX : n == 256 ? RShape<256>::TX : RShape<512>::TX;
+    return n == 32 ? RShape<32>::TX : n == 48 ? RShape<48>::TX : n == 64 ? RShape<64>::TX
+         : n == 96 ? RShape<96>::TX : n == 128 ? RShape<128>::TX : n == 192 ? RShape<192>::TX
+         : n == 256 ? RShape<256>::TX : n == 384 ? RShape<384>::TX : RShape<512>::TX;
 }
 constexpr int r_tile_lines(int n) { return r_tile_cols(n); }  // x-passes: real lines per CTA
 
-// Shared memory of one CTA: its lines (64 x 65 complex values covers every
-// length's LINES x LS), reused for the 16 x M exchanges; the twiddles
-// W_(16M)^(t k1) at [k1][t] and W512^n (n < 256), conjugated for the
-// inverse; for a DCT direction the post-twiddles (cos, sin)(pi m / (2n)),
-// m < n/2.
-struct R16Smem {
-    float2 x[64 * 65];
-    float2 tw[256];
-    float2 tw2[256];
-    float2 cs[256];
+// Shared memory of one CTA: its lines, reused for the P x M exchanges; the
+// twiddles W_NH^(t k1) at [k1][t] and, for the radix-2 lengths, W_N^n
+// (n < NH), conjugated for the inverse; for a DCT direction the
+// post-twiddles (cos, sin)(pi m / (2N)), m < N/2.
+template <int N> struct RSmem {
+    float2 x[RShape<N>::LINES * RShape<N>::LS];
+    float2 tw[RShape<N>::NH];
+    float2 tw2[RShape<N>::G == 2 ? RShape<N>::NH : 1];
+    float2 cs[N / 2];
 };
 
-// (SM: any shared-memory struct with the tw, tw2 and cs tables of R16Smem)
+// (SM: any shared-memory struct with the tw, tw2 and cs tables of RSmem)
 template <bool INV, int N, int KIND, typename SM>
 __device__ __forceinline__ void r16_tables(SM &sm) {
-    constexpr int M = RShape<N>::M;
+    constexpr int M = RShape<N>::M, NH = RShape<N>::NH;
     float s, c;
-    if (threadIdx.x < 16 * M) {
-        const int k1 = threadIdx.x / M, t = threadIdx.x % M;
-        sincospif(-(float)(t * k1) / (float)(8 * M), &s, &c);
-        sm.tw[threadIdx.x] = make_float2(c, INV ? -s : s);
+    for (int i = threadIdx.x; i < NH; i += blockDim.x) {
+        const int k1 = i / M, t = i % M;
+        sincospif(-(float)(2 * t * k1) / (float)NH, &s, &c);
+        sm.tw[i] = make_float2(c, INV ? -s : s);
     }
-    if (N == 512 && threadIdx.x < 256) {  // (blocks may have more than 256 threads)
-        sincospif(-(float)threadIdx.x / 256.f, &s, &c);
-        sm.tw2[threadIdx.x] = make_float2(c, INV ? -s : s);
+    if constexpr (RShape<N>::G == 2) {
+        for (int i = threadIdx.x; i < NH; i += blockDim.x) {
+            sincospif(-(float)(2 * i) / (float)N, &s, &c);
+            sm.tw2[i] = make_float2(c, INV ? -s : s);
+        }
     }
-    if (KIND == KIND_DCT && threadIdx.x < N / 2) {
-        sincospif((float)threadIdx.x / (float)(2 * N), &s, &c);
-        sm.cs[threadIdx.x] = make_float2(c, s);
+    if constexpr (KIND == KIND_DCT) {
+        for (int i = threadIdx.x; i < N / 2; i += blockDim.x) {
+            sincospif((float)i / (float)(2 * N), &s, &c);
+            sm.cs[i] = make_float2(c, s);
+        }
     }
 }
 
@@ -187,26 +312,26 @@ __device__ __forceinline__ int r_src(int p) {
 }
 constexpr float R_SQRT2 = 1.41421356237309504880f;  // the n/2 term of the DCT (2 cos(pi/4))
 
-// The 16 x M four-step DFT on the 16 M values at X: thread t holds
-// v[n1] = x[M n1 + t] and ends with v[j M + k2] = X[t + M j + 16 k2]
-// (j < 16/M, k2 < M): a 16-point DFT, the twiddles W_(16M)^(t k1), one
+// The P x M four-step DFT on the P M values at X: thread t holds
+// v[n1] = x[M n1 + t] and ends with v[j M + k2] = X[t + M j + P k2]
+// (j < P/M, k2 < M): a P-point DFT, the twiddles W_(PM)^(t k1), one
 // swizzled exchange through X (a permutation of M slots both ways), then
-// 16/M M-point DFTs.  X is overwritten; its threads (all in one warp) must
+// P/M M-point DFTs.  X is overwritten; its threads (all in one warp) must
 // have finished reading X before the call (warp barriers inside, the last
 // one after the exchange reads).
-template <bool INV, int M, typename SM>
-__device__ __forceinline__ void r_core(const SM &sm, float2 *X, int t, float2 (&v)[16]) {
-    dft16<INV>(v);
+template <bool INV, int P, int M, typename SM>
+__device__ __forceinline__ void r_core(const SM &sm, float2 *X, int t, float2 (&v)[P]) {
+    dft_p<INV, P>(v);
 #pragma unroll
-    for (int k1 = 1; k1 < 16; ++k1) {
+    for (int k1 = 1; k1 < P; ++k1) {
         const float2 w = sm.tw[k1 * M + t];
         v[k1] = c_mul(v[k1], w.x, w.y);
     }
 #pragma unroll
-    for (int k1 = 0; k1 < 16; ++k1) X[k1 * M + (t ^ (k1 & (M - 1)))] = v[k1];
+    for (int k1 = 0; k1 < P; ++k1) X[k1 * M + (t ^ (k1 & (M - 1)))] = v[k1];
     __syncwarp();
 #pragma unroll
-    for (int j = 0; j < 16 / M; ++j)
+    for (int j = 0; j < P / M; ++j)
 #pragma unroll
         for (int n2 = 0; n2 < M; ++n2) v[j * M + n2] = X[(t + M * j) * M + (n2 ^ t)];
     __syncwarp();
@@ -215,60 +340,65 @@ __device__ __forceinline__ void r_core(const SM &sm, float2 *X, int t, float2 (&
     } else if constexpr (M == 8) {
         dft8<INV, 0>(v);
         dft8<INV, 8>(v);
+        if constexpr (P == 24) dft8<INV, 16>(v);
+    } else if constexpr (M == 4) {
+#pragma unroll
+        for (int j = 0; j < P / 4; ++j) dft4<INV>(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
     } else {
 #pragma unroll
-        for (int j = 0; j < 4; ++j) dft4<INV>(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+        for (int j = 0; j < P / 2; ++j) dft2(v[2 * j], v[2 * j + 1]);
     }
 }
 
 // Position of a thread: complex line ln of the CTA, group h (the half of a
-// 512-line), index t in its 16 x M transform.  Its inputs are the samples
-// in_index(n1), its outputs the indices out_index(r).
+// radix-2 line), index t in its P x M transform.  Its inputs are the
+// samples in_index(n1), its outputs the indices out_index(r).
 template <int N> struct RPos {
-    static constexpr int M = RShape<N>::M;
+    static constexpr int M = RShape<N>::M, P = RShape<N>::P, NH = RShape<N>::NH;
     int ln, h, t;
     __device__ __forceinline__ RPos() {
         t = threadIdx.x & (M - 1);
         ln = threadIdx.x / RShape<N>::TPL;
-        h = N == 512 ? (threadIdx.x >> 4) & 1 : 0;
+        h = RShape<N>::G == 2 ? (threadIdx.x / M) & 1 : 0;
     }
-    __device__ __forceinline__ int in_index(int n1) const {
-        return N == 512 ? 16 * n1 + t + 256 * h : M * n1 + t;
-    }
+    __device__ __forceinline__ int in_index(int n1) const { return M * n1 + t + NH * h; }
     __device__ __forceinline__ int out_index(int r) const {
-        return N == 512 ? 2 * (t + 16 * r) + h : t + M * (r / M) + 16 * (r % M);
+        const int k = t + M * (r / M) + P * (r % M);
+        return RShape<N>::G == 2 ? 2 * k + h : k;
     }
 };
 
-// The register holding the partner X[N - k] of register r when the thread
+// The register holding the partner X[NH - k] of register r when the thread
 // is its own partner (t = 0, group 0): r = j M + k2 maps to
-// (M - k2) mod M for j = 0, else (16/M - j) M + M - 1 - k2.
-template <int M> constexpr int self_reg(int r) {
-    return r / M == 0 ? (M - r % M) % M : (16 / M - r / M) * M + (M - 1 - r % M);
+// (M - k2) mod M for j = 0, else (P/M - j) M + M - 1 - k2.
+template <int P, int M> constexpr int self_reg(int r) {
+    return r / M == 0 ? (M - r % M) % M : (P / M - r / M) * M + (M - 1 - r % M);
 }
 
 // The transform of one line: v[n1] = the input at in_index(n1) on entry,
 // v[r] = the output at out_index(r) on return.  X: the line's region
 // (N values); warp barriers only (a line never spans warps).
 template <bool INV, int N, typename SM>
-__device__ __forceinline__ void r_fft(const SM &sm, float2 *X, const RPos<N> &q, float2 (&v)[16]) {
-    if constexpr (N == 512) {  // radix-2 step: group 0 gets lo + hi, group 1 (lo - hi) W512^n
+__device__ __forceinline__ void r_fft(const SM &sm, float2 *X, const RPos<N> &q,
+                                      float2 (&v)[RShape<N>::P]) {
+    constexpr int P = RShape<N>::P, M = RShape<N>::M;
+    if constexpr (RShape<N>::G == 2) {  // radix-2 step: group 0 gets lo + hi, group 1 (lo - hi) W_N^n
 #pragma unroll
-        for (int n1 = 0; n1 < 16; ++n1) {
+        for (int n1 = 0; n1 < P; ++n1) {
             const float2 own = v[n1];
-            const float2 oth = make_float2(__shfl_xor_sync(0xffffffffu, own.x, 16),
-                                           __shfl_xor_sync(0xffffffffu, own.y, 16));
+            const float2 oth = make_float2(__shfl_xor_sync(0xffffffffu, own.x, M),
+                                           __shfl_xor_sync(0xffffffffu, own.y, M));
             const float2 lo = q.h ? oth : own, hi = q.h ? own : oth;
             if (q.h == 0) {
                 v[n1] = c_add(lo, hi);
             } else {
-                const float2 w = sm.tw2[16 * n1 + q.t];
+                const float2 w = sm.tw2[M * n1 + q.t];
                 v[n1] = c_mul(c_sub(lo, hi), w.x, w.y);
             }
         }
-        r_core<INV, 16>(sm, X + 256 * q.h, q.t, v);
+        r_core<INV, P, M>(sm, X + RShape<N>::NH * q.h, q.t, v);
     } else {
-        r_core<INV, RShape<N>::M>(sm, X, q.t, v);
+        r_core<INV, P, M>(sm, X, q.t, v);
     }
 }
 
@@ -276,24 +406,23 @@ __device__ __forceinline__ void r_fft(const SM &sm, float2 *X, const RPos<N> &q,
 // real and imaginary part): the spectra of both, scaled by 2 (the
 // conventions of the Stockham passes: half-complex for a periodic direction,
 // DCT-II coefficients through the post-twiddle (c, s)_m for a wall), through
-// fn(k, a_k, b_k).  X[K] pairs with X[N - K], held in register 15 - r of
+// fn(k, a_k, b_k).  X[K] pairs with X[N - K], held in register P - 1 - r of
 // thread (M - t) mod M of the line, or (t = 0) in this thread's register
-// self_reg(r); at 512 the odd outputs pair within group 1 with thread
-// 15 - t, register 15 - r.
+// self_reg(r); for the radix-2 lengths the odd outputs pair within group 1
+// with thread M - 1 - t, register P - 1 - r.
 template <int N, int KIND, typename SM, typename F>
-__device__ __forceinline__ void r_separate(const float2 (&v)[16], const RPos<N> &q, const SM &sm,
-                                           F &&fn) {
-    constexpr int M = RShape<N>::M;
-    const int lane = threadIdx.x & 31;
-    const int src = (N != 512 || q.h == 0) ? ((lane & ~(M - 1)) | ((M - q.t) & (M - 1)))
-                                           : (16 | (15 - q.t));
+__device__ __forceinline__ void r_separate(const float2 (&v)[RShape<N>::P], const RPos<N> &q,
+                                           const SM &sm, F &&fn) {
+    constexpr int M = RShape<N>::M, P = RShape<N>::P;
+    const int lane = threadIdx.x & 31, base = lane & ~(M - 1);
+    const int src = q.h == 0 ? (base | ((M - q.t) & (M - 1))) : (base | (M - 1 - q.t));
     const bool self = q.h == 0 && q.t == 0;
 #pragma unroll
-    for (int r = 0; r < 16; ++r) {
-        const float qx = __shfl_sync(0xffffffffu, v[15 - r].x, src);
-        const float qy = __shfl_sync(0xffffffffu, v[15 - r].y, src);
+    for (int r = 0; r < P; ++r) {
+        const float qx = __shfl_sync(0xffffffffu, v[P - 1 - r].x, src);
+        const float qy = __shfl_sync(0xffffffffu, v[P - 1 - r].y, src);
         const float2 z = v[r];
-        const float2 y = self ? v[self_reg<M>(r)] : make_float2(qx, qy);
+        const float2 y = self ? v[self_reg<P, M>(r)] : make_float2(qx, qy);
         const int k = q.out_index(r);
         if (KIND == KIND_PERIODIC) {
             // k <= n/2: (Re A_k, Re B_k) x 2; k > n/2: (Im A_m, Im B_m) x 2, m = n - k
@@ -319,11 +448,12 @@ __device__ __forceinline__ void r_separate(const float2 (&v)[16], const RPos<N> 
 // the spectra of the two real lines read through get(k) = (a_k, b_k)
 // (half-complex, or DCT-II coefficients pre-twiddled by (c, s)_m).
 template <int N, int KIND, typename SM, typename G>
-__device__ __forceinline__ void r_combine(float2 (&v)[16], const RPos<N> &q, const SM &sm, G &&get) {
+__device__ __forceinline__ void r_combine(float2 (&v)[RShape<N>::P], const RPos<N> &q, const SM &sm,
+                                          G &&get) {
 #pragma unroll
-    for (int n1 = 0; n1 < 16; ++n1) {
+    for (int n1 = 0; n1 < RShape<N>::P; ++n1) {
         const int k = q.in_index(n1);
-        const float2 o = get(k), p = get((N - k) & (N - 1));  // indices k and n - k
+        const float2 o = get(k), p = get(k == 0 ? 0 : N - k);  // indices k and n - k
         if (KIND == KIND_PERIODIC) {
             if (k == 0 || k == N / 2) v[n1] = o;
             else if (k < N / 2) v[n1] = make_float2(o.x - p.y, p.x + o.y);
@@ -344,67 +474,50 @@ __device__ __forceinline__ void r_combine(float2 (&v)[16], const RPos<N> &q, con
     }
 }
 
-// ---- y-passes: one tile = TX real columns (bx) of one z-plane of an
-// (nz, N, nx) FP32 array, transformed along y in place.  The N x TX tile
-// (8192 values at every length) moves between global and shared memory as
-// elements e = lane + 32 (warp + 8 i): each warp access is 32 consecutive
-// columns (TX >= 32) or two rows of 16 (TX = 16).  Column 2l + c of the tile
-// is component c of complex line l.  Forward: real columns -> spectra
-// scaled by 2 (half-complex, or DCT-II for a wall direction); inverse: the
-// reverse, unscaled.
+// ---- y-passes: the columns of an (nz, N, nx) FP32 array, flattened over the
+// planes (column cc = k nx + i), in tiles of TX consecutive columns, each
+// transformed along y in place.  Thread e of the CTA owns column e mod TX of
+// the tile and rows e / TX + (THREADS / TX) i, i < 2P (THREADS / TX = TPL/2
+// rows apart): one address per thread, each warp access 32 consecutive
+// columns (TX >= 32) or two rows of 16.  Column 2l + c of the tile is
+// component c of complex line l.  Forward: real columns -> spectra scaled by
+// 2 (half-complex, or DCT-II for a wall direction); inverse: the reverse,
+// unscaled.
 template <bool INV, int N, int KIND>
-__device__ __forceinline__ void ypass_r_tile(int nx, float *data, int bx, int kplane, R16Smem &sm) {
-    constexpr int TX = RShape<N>::TX, LS = RShape<N>::LS;
-    static_assert(N * TX == 32 * 256, "one tile is 32 values per thread");
+__device__ __forceinline__ void ypass_r_tile(int nx, int ncol, float *data, int tile, RSmem<N> &sm) {
+    typedef RShape<N> S;
+    constexpr int TX = S::TX, LS = S::LS, P = S::P, RSTEP = S::THREADS / TX;
+    static_assert(S::THREADS % TX == 0 && N * TX == 2 * P * S::THREADS, "tile shape");
     const RPos<N> q;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int c0 = bx * TX;
-    float *plane = data + (size_t)kplane * N * nx + c0;
-    float *sf = (float *)sm.x;
+    const int col = threadIdx.x % TX, row0 = threadIdx.x / TX;
+    const int cc = tile * TX + col;
+    const bool ok = cc < ncol;
+    const int kp = ok ? cc / nx : 0;
+    // the thread's first element and the step between its rows
+    float *g0 = data + (size_t)kp * N * nx + (ok ? cc - kp * nx : 0) + (size_t)row0 * nx;
+    const size_t gstep = (size_t)RSTEP * nx;
+    float *s0 = (float *)sm.x + (col >> 1) * (2 * LS) + (col & 1) + 2 * row0;
     float2 *X = sm.x + q.ln * LS;
-    // element i of this thread: (row, col) of e = lane + 32 (warp + 8 i); for
-    // TX <= 32 the column is the thread's own (one pointer per thread)
-    auto rc = [&](int i, int &row, int &col) {
-        const int e = lane + 32 * (warp + 8 * i);
-        row = e / TX;
-        col = e % TX;
-    };
-    // one column per thread (TX <= 32): its pointers and the rows linear in i
-    constexpr int RPW = TX <= 32 ? 32 / TX : 1;
-    const int tcol = lane % TX, rsub = lane / TX;
-    const bool tcol_ok = c0 + tcol < nx;
-    float *gcol = plane + tcol;
-    float *scol = sf + (tcol >> 1) * (2 * LS) + (tcol & 1);
-    auto row_of = [&](int i) { return i * (8 * RPW) + warp * RPW + rsub; };
-    // 1. stage the tile (sixteen loads in flight)
+    // 1. stage the tile (eight loads in flight)
+    {
+        const float *gp = g0;
+        float *sp = s0;
 #pragma unroll 1
-    for (int i0 = 0; i0 < 32; i0 += 16) {
-        float r[16];
-        if constexpr (TX <= 32) {
+        for (int i0 = 0; i0 < 2 * P; i0 += 8) {
+            float r[8];
 #pragma unroll
-            for (int u = 0; u < 16; ++u) r[u] = tcol_ok ? gcol[(size_t)row_of(i0 + u) * nx] : 0.f;
+            for (int u = 0; u < 8; ++u) r[u] = ok ? gp[u * gstep] : 0.f;
 #pragma unroll
-            for (int u = 0; u < 16; ++u) scol[2 * row_of(i0 + u)] = r[u];
-        } else {
-#pragma unroll
-            for (int u = 0; u < 16; ++u) {
-                int row, col;
-                rc(i0 + u, row, col);
-                r[u] = c0 + col < nx ? plane[(size_t)row * nx + col] : 0.f;
-            }
-#pragma unroll
-            for (int u = 0; u < 16; ++u) {
-                int row, col;
-                rc(i0 + u, row, col);
-                sf[(col >> 1) * (2 * LS) + 2 * row + (col & 1)] = r[u];
-            }
+            for (int u = 0; u < 8; ++u) sp[2 * RSTEP * u] = r[u];
+            gp += 8 * gstep;
+            sp += 16 * RSTEP;
         }
     }
     __syncthreads();
-    float2 v[16];
+    float2 v[P];
     if (!INV) {
 #pragma unroll
-        for (int n1 = 0; n1 < 16; ++n1) v[n1] = X[r_src<N, KIND>(q.in_index(n1))];
+        for (int n1 = 0; n1 < P; ++n1) v[n1] = X[r_src<N, KIND>(q.in_index(n1))];
     } else {
         r_combine<N, KIND>(v, q, sm, [&](int k) { return X[k]; });
     }
@@ -414,114 +527,121 @@ __device__ __forceinline__ void ypass_r_tile(int nx, float *data, int bx, int kp
         r_separate<N, KIND>(v, q, sm, [&](int k, float a, float b) { X[k] = make_float2(a, b); });
     } else {
 #pragma unroll
-        for (int r = 0; r < 16; ++r) X[r_src<N, KIND>(q.out_index(r))] = v[r];
+        for (int r = 0; r < P; ++r) X[r_src<N, KIND>(q.out_index(r))] = v[r];
     }
     __syncthreads();
     // 2. write the tile back
+    if (ok) {
+        float *gp = g0;
+        const float *sp = s0;
+#pragma unroll 1
+        for (int i0 = 0; i0 < 2 * P; i0 += 8) {
 #pragma unroll
-    for (int i = 0; i < 32; ++i) {
-        if constexpr (TX <= 32) {
-            const int row = row_of(i);
-            if (tcol_ok) gcol[(size_t)row * nx] = scol[2 * row];
-        } else {
-            int row, col;
-            rc(i, row, col);
-            if (c0 + col < nx) plane[(size_t)row * nx + col] = sf[(col >> 1) * (2 * LS) + 2 * row + (col & 1)];
+            for (int u = 0; u < 8; ++u) gp[u * gstep] = sp[2 * RSTEP * u];
+            gp += 8 * gstep;
+            sp += 16 * RSTEP;
         }
     }
     __syncthreads();  // the buffer is free for the next tile
 }
 
-// y-pass over ntiles = ygx x nz tiles (ygx = ceil(nx / TX)); the signature of
-// k_ypass, so the plan can launch either.  conv: return at once when the
-// refinement has converged.
+// y-pass with the signature of k_ypass, so the plan can launch either: the
+// launch covers ntiles = ygx nz per-plane tiles of the Stockham pass
+// (ygx = ceil(nx / TX)), the kernel the ceil(nx nz / TX) flattened tiles
+// (never more).  conv: return at once when the refinement has converged.
 template <bool INV, int N, int KIND>
-__global__ void __launch_bounds__(256, 4) k_ypass_r(int nx, int ny, FFTDesc D, int TX, float *data,
-                                                    const int *conv, int ygx, int ntiles) {
+__global__ void __launch_bounds__(RShape<N>::THREADS, RShape<N>::MINB)
+    k_ypass_r(int nx, int ny, FFTDesc D, int TX, float *data, const int *conv, int ygx, int ntiles) {
     (void)ny;
     (void)D;
     (void)TX;
-    __shared__ R16Smem sm;
+    __shared__ RSmem<N> sm;
     if (conv && *(volatile const int *)conv) return;
     r16_tables<INV, N, KIND>(sm);
     __syncthreads();
-    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const int kplane = tile / ygx;
-        ypass_r_tile<INV, N, KIND>(nx, data, tile - kplane * ygx, kplane, sm);
-    }
+    const int nz = ntiles / ygx, ncol = nx * nz;
+    const int nflat = (ncol + RShape<N>::TX - 1) / RShape<N>::TX;
+    for (int tile = blockIdx.x; tile < nflat; tile += gridDim.x)
+        ypass_r_tile<INV, N, KIND>(nx, ncol, data, tile, sm);
 }
 
 // ---- x-passes: 2 LINES real lines of the [nz][ny] line set per CTA.  A
 // warp owns LPW complex lines (2 LPW real rows, rows 2l and 2l + 1 packed as
-// line l); it stages them row by row through their shared-memory regions
-// (lane = x mod 32: 128-byte accesses), transforms them and writes them back
-// the same way, with warp barriers only.
+// line l), 2 LPW N = 64 P consecutive floats of the array; it stages them
+// through their shared-memory regions (element e = lane + 32 s of the warp's
+// span: 128-byte accesses), transforms them and writes them back the same
+// way, with warp barriers only.
 
 // The warp's first line (of the CTA).
 template <int N> __device__ __forceinline__ int r_warp_line() {
     return (threadIdx.x >> 5) * RShape<N>::LPW;
 }
 
-// A warp's rows hold 2 LPW x N = 32 x 32 values at every length: slot s
-// (s < 32) of a lane is row s / (N/32), x = lane + 32 (s mod N/32).
-template <int N> __device__ __forceinline__ int r_slot_row(int s) { return s / (N / 32); }
-template <int N> __device__ __forceinline__ int r_slot_x(int s) {
-    return (threadIdx.x & 31) + 32 * (s % (N / 32));
-}
+// Slot s (s < 2P) of a lane: element e = lane + 32 s of the warp's rows,
+// row e / N of the warp, x = e mod N.
+template <int N> __device__ __forceinline__ int r_slot_row(int s) { return ((threadIdx.x & 31) + 32 * s) / N; }
+template <int N> __device__ __forceinline__ int r_slot_x(int s) { return ((threadIdx.x & 31) + 32 * s) % N; }
 // The shared-memory float of (row r of the warp, x): line l0 + r/2, component r & 1.
 template <int N> __device__ __forceinline__ int r_slot_f(int r, int x) {
     return (r_warp_line<N>() + (r >> 1)) * (2 * RShape<N>::LS) + 2 * x + (r & 1);
 }
 
 // Rows of the warp from an FP32 array [nlines][N] into the line regions
-// (zeros past the last line), all 32 loads of a lane in flight.
+// (zeros past the last line), CH loads of a lane in flight (all 2P, or
+// 16 at a time for the 24-value lengths, whose registers are the tighter).
 template <int N>
-__device__ __forceinline__ void r_rows_in(const float *src, int row0, int nlines, R16Smem &sm) {
+__device__ __forceinline__ void r_rows_in(const float *src, int row0, int nlines, RSmem<N> &sm) {
+    constexpr int P = RShape<N>::P, CH = P == 24 ? 16 : 2 * P;
     float *sf = (float *)sm.x;
-    float x[32];
+    const float *base = src + (size_t)row0 * N + (threadIdx.x & 31);
+#pragma unroll 1
+    for (int s0 = 0; s0 < 2 * P; s0 += CH) {
+        float x[CH];
 #pragma unroll
-    for (int s = 0; s < 32; ++s) {
-        const int row = row0 + r_slot_row<N>(s);
-        x[s] = row < nlines ? src[(size_t)row * N + r_slot_x<N>(s)] : 0.f;
+        for (int u = 0; u < CH; ++u)
+            x[u] = row0 + r_slot_row<N>(s0 + u) < nlines ? base[32 * (s0 + u)] : 0.f;
+#pragma unroll
+        for (int u = 0; u < CH; ++u) sf[r_slot_f<N>(r_slot_row<N>(s0 + u), r_slot_x<N>(s0 + u))] = x[u];
     }
-#pragma unroll
-    for (int s = 0; s < 32; ++s) sf[r_slot_f<N>(r_slot_row<N>(s), r_slot_x<N>(s))] = x[s];
     __syncwarp();
 }
 
 // Rows of the warp from the line regions back to an FP32 array.
 template <int N>
-__device__ __forceinline__ void r_rows_out(float *dst, int row0, int nlines, const R16Smem &sm) {
+__device__ __forceinline__ void r_rows_out(float *dst, int row0, int nlines, const RSmem<N> &sm) {
     const float *sf = (const float *)sm.x;
+    float *base = dst + (size_t)row0 * N + (threadIdx.x & 31);
     __syncwarp();
 #pragma unroll
-    for (int s = 0; s < 32; ++s) {
-        const int row = row0 + r_slot_row<N>(s);
-        if (row < nlines) dst[(size_t)row * N + r_slot_x<N>(s)] = sf[r_slot_f<N>(r_slot_row<N>(s), r_slot_x<N>(s))];
-    }
+    for (int s = 0; s < 2 * RShape<N>::P; ++s)
+        if (row0 + r_slot_row<N>(s) < nlines) base[32 * s] = sf[r_slot_f<N>(r_slot_row<N>(s), r_slot_x<N>(s))];
     __syncwarp();
 }
 
 // Forward transform of the staged lines: inputs from the line region X,
 // the spectra back into it.
 template <int N, int KIND>
-__device__ __forceinline__ void r_forward_line(const R16Smem &sm, float2 *X, const RPos<N> &q) {
-    float2 v[16];
+__device__ __forceinline__ void r_forward_line(const RSmem<N> &sm, float2 *X, const RPos<N> &q) {
+    float2 v[RShape<N>::P];
 #pragma unroll
-    for (int n1 = 0; n1 < 16; ++n1) v[n1] = X[r_src<N, KIND>(q.in_index(n1))];
+    for (int n1 = 0; n1 < RShape<N>::P; ++n1) v[n1] = X[r_src<N, KIND>(q.in_index(n1))];
     __syncwarp();  // the line's region is the exchange buffer next
     r_fft<false, N>(sm, X, q, v);
     r_separate<N, KIND>(v, q, sm, [&](int k, float a, float b) { X[k] = make_float2(a, b); });
 }
 
+// Lengths whose M = 16 threads of a line read and write their two rows in
+// 64-byte runs: the x-passes access global memory directly.
+template <int N> constexpr bool r_direct() { return N == 256 || N == 512; }
+
 // The transform of the stored FP32 residual (refinement sweeps), in place:
 // the mode XF_MIX_LOAD of k_xfwd.
 template <int N, int KIND>
-__global__ void __launch_bounds__(256, 4) k_xfwd_r_load(GridDev g, FFTDesc D, int L, XArgs a,
-                                                        int ntiles) {
+__global__ void __launch_bounds__(RShape<N>::THREADS, RShape<N>::MINB)
+    k_xfwd_r_load(GridDev g, FFTDesc D, int L, XArgs a, int ntiles) {
     (void)D;
     (void)L;
-    __shared__ R16Smem sm;
+    __shared__ RSmem<N> sm;
     if (*(volatile const int *)&a.st->converged) return;
     r16_tables<false, N, KIND>(sm);
     __syncthreads();
@@ -531,15 +651,13 @@ __global__ void __launch_bounds__(256, 4) k_xfwd_r_load(GridDev g, FFTDesc D, in
     float2 *X = sm.x + q.ln * RShape<N>::LS;
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const int row0 = tile * r_tile_lines(N) + 2 * r_warp_line<N>();
-        if constexpr (N >= 256) {
-            // a 16-thread group reads and writes 64 consecutive bytes of each
-            // of its line's two rows at a time: direct global access
+        if constexpr (r_direct<N>()) {
             const int ra = tile * r_tile_lines(N) + 2 * q.ln;
             const bool oka = ra < nlines, okb = ra + 1 < nlines;
             float *la = data + (size_t)ra * N, *lb = la + N;
-            float2 v[16];
+            float2 v[RShape<N>::P];
 #pragma unroll
-            for (int n1 = 0; n1 < 16; ++n1) {
+            for (int n1 = 0; n1 < RShape<N>::P; ++n1) {
                 const int i = r_src<N, KIND>(q.in_index(n1));
                 v[n1] = make_float2(oka ? la[i] : 0.f, okb ? lb[i] : 0.f);
             }
@@ -559,16 +677,18 @@ __global__ void __launch_bounds__(256, 4) k_xfwd_r_load(GridDev g, FFTDesc D, in
 
 // The first x-pass of the mixed solve (the mode XF_MIX_DIVQ of k_xfwd):
 // f = rho0 D(q') in FP64 (stored, and max|f| recorded), then the forward
-// transform of its FP32 image sigma f.  f is formed row by row (lane = x mod
-// 32, coalesced) into the line regions.
+// transform of its FP32 image sigma f.  f is formed into the line regions
+// row by row for rows of N >= 256 cells (lane = x mod 32, the row's
+// constants once), else slot by slot (coalesced either way).
 template <int N, int KIND>
-__global__ void __launch_bounds__(256, 4) k_xfwd_r_divq(GridDev g, FFTDesc D, int L, XArgs a,
-                                                        int ntiles) {
+__global__ void __launch_bounds__(RShape<N>::THREADS, RShape<N>::MINB)
+    k_xfwd_r_divq(GridDev g, FFTDesc D, int L, XArgs a, int ntiles) {
     (void)D;
     (void)L;
-    __shared__ R16Smem sm;
+    __shared__ RSmem<N> sm;
     r16_tables<false, N, KIND>(sm);
     __syncthreads();
+    constexpr int P = RShape<N>::P;
     const RPos<N> q;
     const int nlines = g.ny * g.nz, l0 = r_warp_line<N>();
     constexpr int LS = RShape<N>::LS;
@@ -600,9 +720,9 @@ __global__ void __launch_bounds__(256, 4) k_xfwd_r_divq(GridDev g, FFTDesc D, in
                     for (int i = 0; i < N / 32; ++i) dr[2 * (lane + 32 * i)] = 0.f;
                 }
             }
-        } else {  // short rows: the warp's 32 slots per lane
+        } else {  // short rows: the warp's 2P slots per lane
 #pragma unroll 4
-            for (int s = 0; s < 32; ++s) {
+            for (int s = 0; s < 2 * P; ++s) {
                 const int r = r_slot_row<N>(s), x = r_slot_x<N>(s), row = row0 + r;
                 float val = 0.f;
                 if (row < nlines) {
@@ -616,10 +736,10 @@ __global__ void __launch_bounds__(256, 4) k_xfwd_r_divq(GridDev g, FFTDesc D, in
             }
         }
         __syncwarp();
-        if constexpr (N >= 256) {  // the spectra straight to global memory
-            float2 v[16];
+        if constexpr (r_direct<N>()) {  // the spectra straight to global memory
+            float2 v[P];
 #pragma unroll
-            for (int n1 = 0; n1 < 16; ++n1) v[n1] = X[r_src<N, KIND>(q.in_index(n1))];
+            for (int n1 = 0; n1 < P; ++n1) v[n1] = X[r_src<N, KIND>(q.in_index(n1))];
             __syncwarp();  // the line's region is the exchange buffer next
             r_fft<false, N>(sm, X, q, v);
             const int ra = tile * r_tile_lines(N) + 2 * q.ln;
@@ -641,14 +761,15 @@ __global__ void __launch_bounds__(256, 4) k_xfwd_r_divq(GridDev g, FFTDesc D, in
 // Inverse x-pass to p (FP64): XI_STORE p = the FP32 solution, XI_ACCUM
 // p += delta 2^e (e: exponent of max|f|); the modes of k_xinv.
 template <int MODE, int N, int KIND>
-__global__ void __launch_bounds__(256, 4) k_xinv_r(GridDev g, FFTDesc D, int L, const float *in,
-                                                   double *p, const DevStats *st, int ntiles) {
+__global__ void __launch_bounds__(RShape<N>::THREADS, RShape<N>::MINB)
+    k_xinv_r(GridDev g, FFTDesc D, int L, const float *in, double *p, const DevStats *st, int ntiles) {
     (void)D;
     (void)L;
-    __shared__ R16Smem sm;
+    __shared__ RSmem<N> sm;
     if (MODE == XI_ACCUM && *(volatile const int *)&st->converged) return;
     r16_tables<true, N, KIND>(sm);
     __syncthreads();
+    constexpr int P = RShape<N>::P;
     const int ef = MODE == XI_ACCUM ? exp_of_bits(*(volatile const unsigned long long *)&st->fmax_bits) : 0;
     const RPos<N> q;
     const int nlines = g.ny * g.nz, l0 = r_warp_line<N>();
@@ -656,31 +777,30 @@ __global__ void __launch_bounds__(256, 4) k_xinv_r(GridDev g, FFTDesc D, int L, 
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const int row0 = tile * r_tile_lines(N) + 2 * l0;
         r_rows_in<N>(in, row0, nlines, sm);
-        float2 v[16];
+        float2 v[P];
         r_combine<N, KIND>(v, q, sm, [&](int k) { return X[k]; });
         __syncwarp();  // the line's region is the exchange buffer next
         r_fft<true, N>(sm, X, q, v);
 #pragma unroll
-        for (int r = 0; r < 16; ++r) X[r_src<N, KIND>(q.out_index(r))] = v[r];
+        for (int r = 0; r < P; ++r) X[r_src<N, KIND>(q.out_index(r))] = v[r];
         __syncwarp();
         // p (or p += delta) by slots (lane = x mod 32), eight values of p in
         // flight per lane
         const float *sf = (const float *)sm.x;
-#pragma unroll
-        for (int s0 = 0; s0 < 32; s0 += 8) {
+        double *pb = p + (size_t)row0 * N + (threadIdx.x & 31);
+#pragma unroll(P == 24 ? 1 : 2 * P / 8)
+        for (int s0 = 0; s0 < 2 * P; s0 += 8) {
             double qv[8];
             if (MODE == XI_ACCUM) {
 #pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    const int row = row0 + r_slot_row<N>(s0 + u);
-                    qv[u] = row < nlines ? p[(size_t)row * N + r_slot_x<N>(s0 + u)] : 0.0;
-                }
+                for (int u = 0; u < 8; ++u)
+                    qv[u] = row0 + r_slot_row<N>(s0 + u) < nlines ? pb[32 * (s0 + u)] : 0.0;
             }
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
-                const int r = r_slot_row<N>(s0 + u), x = r_slot_x<N>(s0 + u), row = row0 + r;
+                const int r = r_slot_row<N>(s0 + u), x = r_slot_x<N>(s0 + u);
                 const double d = f32_to_f64_shift(sf[r_slot_f<N>(r, x)], ef);
-                if (row < nlines) p[(size_t)row * N + x] = MODE == XI_ACCUM ? qv[u] + d : d;
+                if (row0 + r < nlines) pb[32 * (s0 + u)] = MODE == XI_ACCUM ? qv[u] + d : d;
             }
         }
         __syncwarp();  // the line regions are rewritten by the next tile

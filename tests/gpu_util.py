@@ -44,7 +44,8 @@ def compare(case, got, ref):
 
 # ---- one instance solved alone, as the batched executor solves it
 
-R_LENGTHS = (128, 256, 512)  # register-resident FP32 passes in plain mixed solves
+# register-resident FP32 passes in plain mixed solves (periodic or Neumann)
+R_LENGTHS = (32, 48, 64, 96, 128, 192, 256, 384, 512)
 
 
 def plain_differs(case, precision):

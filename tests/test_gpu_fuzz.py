@@ -1,7 +1,7 @@
 """Seeded random configurations against the FP64 oracle (needs a B300).
 
-Sizes are products of 2 and 3 (including the register-resident lengths 128,
-256 and 512 and odd lengths such as 3, 9, 27), boundaries, stretching, density ratio,
+Sizes are products of 2 and 3 (including the register-resident lengths 32, 48, 64,
+96, 128, 192, 256, 384 and 512 and odd lengths such as 3, 9, 27), boundaries, stretching, density ratio,
 drop count, velocity recipe and the phase that is light all drawn at random;
 every case must meet the same bars as the named parity cases: FP64 <= 1e-12,
 mixed <= 1e-9 after refinement, divergence <= 1e-10.
@@ -28,7 +28,7 @@ from gpu_util import compare, gpu_project, run_alone, to_dev
 
 pytestmark = pytest.mark.gpu
 
-LENGTHS = (2, 3, 4, 6, 8, 9, 12, 16, 18, 24, 27, 32, 36, 48, 54, 64, 72, 96, 128, 256, 512)
+LENGTHS = (2, 3, 4, 6, 8, 9, 12, 16, 18, 24, 27, 32, 36, 48, 54, 64, 72, 96, 128, 192, 256, 384, 512)
 
 
 def fuzz_specs(n=32, seed=2024, bcz_mix=False):

@@ -74,9 +74,8 @@ def small_cases():
                                     radius_cells=3, config=32),
         "b512x3x3_wxy": I.CaseSpec(nx=512, ny=3, nz=3, bcx=1, bcy=1, n_bubbles=1, radius_cells=1,
                                    config=33),
-        # length 128 (the 16 x 8 transform, 4 lines per warp) and 64 (the
-        # Stockham passes): walls and periodic, odd nx, ragged y tiles, odd
-        # line counts
+        # length 128 (the 16 x 8 transform, 4 lines per warp) and 64 (16 x 4):
+        # walls and periodic, odd nx, ragged y tiles, odd line counts
         "b27x64x9_wy": I.CaseSpec(nx=27, ny=64, nz=9, bcx=0, bcy=1, beta=1.3, n_bubbles=1,
                                   radius_cells=3, config=34),
         "b36x128x10": I.CaseSpec(nx=36, ny=128, nz=10, bcx=1, bcy=0, n_bubbles=2, radius_cells=3,
@@ -90,6 +89,31 @@ def small_cases():
                                    config=39),
         "b27x128x5_wy": I.CaseSpec(nx=27, ny=128, nz=5, bcx=1, bcy=1, beta=1.8, n_bubbles=1,
                                    radius_cells=2, config=42),
+        # the register-resident lengths 32 (16 x 2), 48 (12 x 4), 96 (24 x 4),
+        # 192 (24 x 8) and 384 (radix-2 split ahead of 24 x 8): periodic and
+        # walls, odd line counts, y tiles flattened over ragged planes
+        "b32x24x9_wx": I.CaseSpec(nx=32, ny=24, nz=9, bcx=1, bcy=0, beta=1.4, n_bubbles=1,
+                                  radius_cells=3, config=43),
+        "b9x32x7": I.CaseSpec(nx=9, ny=32, nz=7, bcx=0, bcy=0, n_bubbles=1, radius_cells=3,
+                               config=44),
+        "b48x6x7_wx": I.CaseSpec(nx=48, ny=6, nz=7, bcx=1, bcy=1, n_bubbles=1, radius_cells=2,
+                                 config=45),
+        "b27x48x6": I.CaseSpec(nx=27, ny=48, nz=6, bcx=0, bcy=0, beta=1.2, n_bubbles=1,
+                               radius_cells=3, config=46),
+        "b96x9x5": I.CaseSpec(nx=96, ny=9, nz=5, bcx=0, bcy=1, n_bubbles=1, radius_cells=2,
+                              config=47),
+        "b27x96x6_wy": I.CaseSpec(nx=27, ny=96, nz=6, bcx=0, bcy=1, beta=1.5, n_bubbles=2,
+                                  radius_cells=3, config=48),
+        "b192x6x3_wx": I.CaseSpec(nx=192, ny=6, nz=3, bcx=1, bcy=0, n_bubbles=1, radius_cells=2,
+                                  config=49),
+        "b18x192x4": I.CaseSpec(nx=18, ny=192, nz=4, bcx=1, bcy=0, n_bubbles=1, radius_cells=3,
+                                config=50),
+        "b9x384x3": I.CaseSpec(nx=9, ny=384, nz=3, bcx=0, bcy=0, n_bubbles=1, radius_cells=3,
+                                config=51),
+        "b384x9x3": I.CaseSpec(nx=384, ny=9, nz=3, bcx=0, bcy=1, beta=1.3, n_bubbles=1,
+                               radius_cells=2, config=52),
+        "b18x384x2_wy": I.CaseSpec(nx=18, ny=384, nz=2, bcx=1, bcy=1, n_bubbles=1, radius_cells=3,
+                                   config=53),
         # light drops in a heavy phase: rho0 = rho_l, split term from 1 - phi
         "b48x32x24_swapped": I.CaseSpec(nx=48, ny=32, nz=24, bcx=0, bcy=1, beta=1.5, n_bubbles=3,
                                         radius_cells=4, rho_l=1e-3, rho_g=1.0, config=19),
@@ -119,7 +143,10 @@ def test_fp64_matches_oracle(cuda_ok, name):
                                   "b6x512x4", "b24x512x8", "b9x512x3", "b512x3x3_wy",
                                   "b48x256x12_wy", "b256x12x10_wx", "b24x512x8_wxy", "b512x3x3_wxy",
                                   "b27x64x9_wy", "b36x128x10", "b64x9x7", "b128x6x5_wx",
-                                  "b64x128x16_w", "b128x3x3_odd", "b27x128x5_wy"])
+                                  "b64x128x16_w", "b128x3x3_odd", "b27x128x5_wy",
+                                  "b32x24x9_wx", "b9x32x7", "b48x6x7_wx", "b27x48x6", "b96x9x5",
+                                  "b27x96x6_wy", "b192x6x3_wx", "b18x192x4", "b9x384x3",
+                                  "b384x9x3", "b18x384x2_wy"])
 def test_mixed_matches_oracle(cuda_ok, name):
     c = I.make_case(CASES[name])
     ref = O.project_case(c)
@@ -137,7 +164,8 @@ def test_mixed_matches_oracle(cuda_ok, name):
 @pytest.mark.parametrize("name", ["b48x256x12", "b27x256x6_wx", "b256x12x10", "b256x9x5_wy",
                                   "b24x512x8", "b512x8x5", "b48x256x12_wy", "b256x12x10_wx",
                                   "b24x512x8_wxy", "b27x64x9_wy", "b128x6x5_wx", "b64x128x16_w",
-                                  "b96x64x33"])
+                                  "b96x64x33", "b32x24x9_wx", "b27x48x6", "b27x96x6_wy",
+                                  "b18x192x4", "b9x384x3", "b384x9x3"])
 def test_fp32_solve_accuracy(cuda_ok, name):
     """The FP32 solve alone (stopped at its first residual) is accurate to
     FP32 level, whichever transform kernels it runs: the Stockham and the
