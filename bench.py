@@ -530,6 +530,41 @@ def run_serve_loop(args, F, torch, n_requests, slots):
     return summ, info
 
 
+SMALL_PTS = 128 ** 3  # serving size classes: small <= 128^3 points < large
+
+
+def run_serve_classes(args, F, torch, slots, n_small=1500, n_large=300):
+    """Service capacity by request size: the request recipe's small
+    (<= 128^3 points) and large requests served as two separate backlogs
+    (every request queued at t = 0, no deadline), so the server stays busy
+    and points / wall time is the class's throughput.  The ratio small/large
+    says how well small requests use the GPU."""
+    import paper_2502_04189_b300.serve as S
+    arrivals, specs = I.serve_specs(8 * (n_small + n_large))
+    small = [s for s in specs if s.nx * s.ny * s.nz <= SMALL_PTS][:n_small]
+    large = [s for s in specs if s.nx * s.ny * s.nz > SMALL_PTS][:n_large]
+    tmpl = I.make_case(I.bubbles256_spec())
+    fields = S.TemplateFields(tmpl)
+    server = F.Server(120 * (1 << 30), slots=slots)
+
+    def fill(r, views, stream):
+        fields.fill(views, r.desc, r.offset, stream)
+
+    out = {"split_pts": SMALL_PTS, "slots": slots}
+    for name, cls in (("small", small), ("large", large)):
+        reqs = S.requests_from_specs([0.0] * len(cls), cls, F.MIXED)
+        S.run(server, reqs[:4], fill, deadline=60.0)  # plans and pool warm
+        torch.cuda.synchronize()
+        _, summ = S.run(server, reqs, fill, deadline=60.0)
+        out[name] = {"requests": summ["requests"], "mean_pts": summ["points_done"] / max(1, summ["admitted"]),
+                     "throughput_pts_s": summ["throughput_pts_s"], "wall_s": summ["wall_s"],
+                     "all_converged": summ["all_converged"]}
+    out["small_over_large"] = out["small"]["throughput_pts_s"] / out["large"]["throughput_pts_s"]
+    server.close()
+    del fields
+    return out
+
+
 def run_fizzy(args):
     import torch
     import paper_2502_04189_b300 as F
@@ -725,6 +760,8 @@ def run_fizzy(args):
                  "rejected_fraction": summ["rejected_fraction"], "requests_per_s": summ["requests_per_s"],
                  "all_converged": summ["all_converged"], "max_relres": summ["max_relres"],
                  "plans_built": info.get("plans_built")}
+        torch.cuda.empty_cache()
+        serve["by_size"] = run_serve_classes(args, F, torch, args.serve_slots)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "pts/s", "n_gpus": world,
@@ -800,6 +837,7 @@ def run_serve(args):
     clocks = ClockSampler()
     clocks.start()
     summ, info = run_serve_loop(args, F, torch, args.serve_requests, args.serve_slots)
+    by_size = run_serve_classes(args, F, torch, args.serve_slots)
     clk = clocks.stop()
     if rank == 0:
         line = {"metric": METRIC, "value": summ["throughput_pts_s"], "unit": "pts/s",
@@ -809,7 +847,7 @@ def run_serve(args):
                 "config": {"workload": "serve", "arrival_rate_per_s": 2000,
                            "requests": summ["requests"], "budget_gb": 120, "slots": args.serve_slots,
                            "deadline_ms": 100, "precision": "mixed", "tol": 1e-10},
-                "serving": summ, "server": info, "clocks": clk}
+                "serving": summ, "server": info, "by_size": by_size, "clocks": clk}
         print(json.dumps(line), flush=True)
     return 0
 
@@ -947,7 +985,7 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=4000)
     ap.add_argument("--sub-serve-requests", type=int, default=1000,
                     help="requests of the serving run embedded in the default line")
-    ap.add_argument("--serve-slots", type=int, default=8)
+    ap.add_argument("--serve-slots", type=int, default=16)
     ap.add_argument("--e2e-steps", type=int, default=6)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-sub", action="store_true", help="skip the embedded batch and serving runs")

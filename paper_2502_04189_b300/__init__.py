@@ -348,10 +348,14 @@ class Server:
         return rc, slot.value, [ptrs[i] for i in range(7)]
 
     def stream(self, slot):
-        import torch
-        st = ctypes.c_void_p()
-        _abi.lib().fizzy_serve_stream(self._h, int(slot), ctypes.byref(st))
-        return torch.cuda.ExternalStream(st.value)
+        """The slot's stream (a torch ExternalStream, made once per slot)."""
+        cache = self.__dict__.setdefault("_streams", {})
+        if slot not in cache:
+            import torch
+            st = ctypes.c_void_p()
+            _abi.lib().fizzy_serve_stream(self._h, int(slot), ctypes.byref(st))
+            cache[slot] = torch.cuda.ExternalStream(st.value)
+        return cache[slot]
 
     def launch(self, slot):
         rc = _abi.lib().fizzy_serve_launch(self._h, int(slot))
@@ -406,8 +410,17 @@ def crop_fill(src, dst, offset, bcx=PERIODIC, bcy=PERIODIC, stream=None):
     nz, ny, nx = dst[0].shape
     if any(t.shape != (tz, ty, tx) for t in src) or any(t.shape != (nz, ny, nx) for t in dst):
         raise ValueError("fields of one side must share a shape")
-    sp = (ctypes.c_void_p * 6)(*[_ptr(t).value for t in src])
-    dp = (ctypes.c_void_p * 6)(*[_ptr(t).value for t in dst])
+    crop_fill_ptrs([_ptr(t).value for t in src], (tz, ty, tx), [_ptr(t).value for t in dst],
+                   (nz, ny, nx), offset, bcx, bcy, stream)
+
+
+def crop_fill_ptrs(src, src_shape, dst, dst_shape, offset, bcx=PERIODIC, bcy=PERIODIC, stream=None):
+    """crop_fill on raw device pointers: six float64 sources of shape
+    src_shape = (tz, ty, tx) and six destinations of shape (nz, ny, nx)."""
+    tz, ty, tx = (int(v) for v in src_shape)
+    nz, ny, nx = (int(v) for v in dst_shape)
+    sp = (ctypes.c_void_p * 6)(*src[:6])
+    dp = (ctypes.c_void_p * 6)(*dst[:6])
     oz, oy, ox = (int(o) for o in offset)
     rc = _abi.lib().fizzy_crop_fill(sp, tx, ty, tz, dp, nx, ny, nz, ox, oy, oz, int(bcx), int(bcy),
                                     _stream_handle(stream))

@@ -63,8 +63,11 @@ struct fizzy_proj_plan_s {
     int max_refine = 4;
     GridDev g;
     double sigma = 0.0;
-    // device memory
+    // device memory: one arena sized by plan_bytes, carved by dev_alloc
+    // (later or larger requests get allocations of their own)
     std::vector<void *> allocs;
+    unsigned char *arena = nullptr;
+    size_t arena_size = 0, arena_off = 0;
     size_t bytes = 0;
     FFTHost fx, fy;
     int Ux = 0, Uy = 0;
@@ -175,6 +178,13 @@ template <typename T> T *dev_alloc(fizzy_proj_plan_t p, size_t count, int *statu
     if (*status) return nullptr;
     void *ptr = nullptr;
     const size_t b = count * sizeof(T);
+    const size_t ba = (b + 255) & ~(size_t)255;  // 256-byte aligned pieces
+    if (p->arena && p->arena_off + ba <= p->arena_size) {
+        ptr = p->arena + p->arena_off;
+        p->arena_off += ba;
+        p->bytes += b;
+        return (T *)ptr;
+    }
     cudaError_t e = p->async_alloc ? cudaMallocAsync(&ptr, b > 0 ? b : 16, p->alloc_stream)
                                    : cudaMalloc(&ptr, b > 0 ? b : 16);
     if (e != cudaSuccess) {
@@ -324,21 +334,45 @@ int build_fft(fizzy_proj_plan_t p, int n, int bc, FFTHost &F, int *status) {
         if (dct4) fill_dct4_tables(n, T.tw.data(), T.cs.data(), T.tw32.data(), T.cs32.data());
         else fill_fft_tables(n, T.tw.data(), T.cs.data(), T.tw32.data(), T.cs32.data());
     }
-    const std::vector<double> &tw = T.tw, &cs = T.cs;
-    const std::vector<float> &tw32 = T.tw32, &cs32 = T.cs32;
-    F.tw64 = dev_alloc<double>(p, tw.size(), status);
-    F.cs64 = dev_alloc<double>(p, cs.size(), status);
-    if (p->mixed) {
-        F.tw32 = dev_alloc<float>(p, tw32.size(), status);
-        F.cs32 = dev_alloc<float>(p, cs32.size(), status);
+    // ... and their device copies once per device: read-only, shared by every
+    // plan of that length and family, kept for the life of the process
+    struct DevTabs {
+        void *tw64 = nullptr, *cs64 = nullptr, *tw32 = nullptr, *cs32 = nullptr;
+    };
+    static std::map<std::tuple<int, int, int>, DevTabs> dcache;
+    int dev = 0;
+    note(p, cudaGetDevice(&dev));
+    DevTabs &D = dcache[std::make_tuple(dev, n, dct4 ? 1 : 0)];
+    if (!D.tw64) {
+        DevTabs t;
+        const size_t b64 = T.tw.size() * sizeof(double), c64 = T.cs.size() * sizeof(double);
+        const size_t b32 = T.tw32.size() * sizeof(float), c32 = T.cs32.size() * sizeof(float);
+        cudaError_t e = cudaMalloc(&t.tw64, b64 + c64 + b32 + c32);
+        if (e == cudaSuccess) {
+            unsigned char *base = (unsigned char *)t.tw64;
+            t.cs64 = base + b64;
+            t.tw32 = base + b64 + c64;
+            t.cs32 = base + b64 + c64 + b32;
+            std::vector<unsigned char> h(b64 + c64 + b32 + c32);
+            memcpy(h.data(), T.tw.data(), b64);
+            memcpy(h.data() + b64, T.cs.data(), c64);
+            memcpy(h.data() + b64 + c64, T.tw32.data(), b32);
+            memcpy(h.data() + b64 + c64 + b32, T.cs32.data(), c32);
+            e = cudaMemcpy(t.tw64, h.data(), h.size(), cudaMemcpyHostToDevice);
+            if (e != cudaSuccess) cudaFree(t.tw64);
+        }
+        if (e != cudaSuccess) {
+            (void)cudaGetLastError();
+            *status = FIZZY_ERR_NOMEM;
+            p->err = "twiddle tables: " + std::string(cudaGetErrorString(e));
+            return *status;
+        }
+        D = t;
     }
-    if (*status) return *status;
-    note(p, cudaMemcpyAsync(F.tw64, tw.data(), tw.size() * sizeof(double), cudaMemcpyHostToDevice, p->alloc_stream));
-    note(p, cudaMemcpyAsync(F.cs64, cs.data(), cs.size() * sizeof(double), cudaMemcpyHostToDevice, p->alloc_stream));
-    if (p->mixed) {
-        note(p, cudaMemcpyAsync(F.tw32, tw32.data(), tw32.size() * sizeof(float), cudaMemcpyHostToDevice, p->alloc_stream));
-        note(p, cudaMemcpyAsync(F.cs32, cs32.data(), cs32.size() * sizeof(float), cudaMemcpyHostToDevice, p->alloc_stream));
-    }
+    F.tw64 = D.tw64;
+    F.cs64 = D.cs64;
+    F.tw32 = D.tw32;
+    F.cs32 = D.cs32;
     FFTDesc d;
     memset(&d, 0, sizeof(d));
     if (dct4) {  // stages of the half-length complex FFT; lines of length n
@@ -727,12 +761,15 @@ int fizzy_proj_destroy(fizzy_proj_plan_t p) {
     if (p->async_alloc) {
         // stream-ordered: frees run after the work already queued on the plan's stream
         for (void *a : p->allocs) cudaFreeAsync(a, p->alloc_stream);
+        if (p->arena) cudaFreeAsync(p->arena, p->alloc_stream);
         p->allocs.clear();
+        p->arena = nullptr;
     } else {
         cudaDeviceSynchronize();
     }
     for (auto &e : p->ev) cudaEventDestroy(e);
     for (void *a : p->allocs) cudaFree(a);
+    if (p->arena) cudaFree(p->arena);
     if (p->d2h) cudaStreamSynchronize(p->d2h);
     for (int b = 0; b < 2; ++b) {
         for (int t = 0; t < 7; ++t)
@@ -794,15 +831,52 @@ int fizzy_proj_plan(fizzy_proj_plan_t *out, const fizzy_proj_desc *d, void *stre
         zt[T_DZF * nz + k] = dzf[k];
         zt[T_DZC * nz + k] = dzc[k];
     }
+    // the plan's device memory in one allocation (dev_alloc carves it)
+    {
+        p->arena_size = plan_bytes(d) + 64 * 256;
+        void *a = nullptr;
+        const cudaError_t e = p->async_alloc ? cudaMallocAsync(&a, p->arena_size, p->alloc_stream)
+                                             : cudaMalloc(&a, p->arena_size);
+        if (e != cudaSuccess) {
+            (void)cudaGetLastError();
+            fizzy_proj_destroy(p);
+            return FIZZY_ERR_NOMEM;
+        }
+        p->arena = (unsigned char *)a;
+    }
+    // eigenvalues of the x and y second differences per transform slot
+    const int Ux = d->bc_x == FIZZY_BC_PERIODIC ? nx / 2 + 1 : nx;
+    const int Uy = d->bc_y == FIZZY_BC_PERIODIC ? ny / 2 + 1 : ny;
+    std::vector<double> lam((size_t)Ux + Uy);
+    for (int u = 0; u < Ux; ++u) lam[u] = eig(u, nx, d->dx, d->bc_x);
+    for (int u = 0; u < Uy; ++u) lam[Ux + u] = eig(u, ny, d->dy, d->bc_y);
+    const double *C = &zt[T_LZC * nz];
+    // one upload of the host-built tables: per-k rows | eigenvalues | c_k (FP64, FP32)
+    const size_t o_lam = zt.size() * sizeof(double), o_c64 = o_lam + lam.size() * sizeof(double);
+    const size_t o_c32 = o_c64 + (size_t)nz * sizeof(double), up_bytes = o_c32 + (size_t)nz * sizeof(float);
     int status = 0;
-    double *zt_d = dev_alloc<double>(p, zt.size(), &status);
+    unsigned char *up_d = dev_alloc<unsigned char>(p, up_bytes, &status);
     if (status) {
         int st = status;
         fizzy_proj_destroy(p);
         return st;
     }
+    {
+        std::vector<unsigned char> up(up_bytes);
+        memcpy(up.data(), zt.data(), o_lam);
+        memcpy(up.data() + o_lam, lam.data(), lam.size() * sizeof(double));
+        memcpy(up.data() + o_c64, C, (size_t)nz * sizeof(double));
+        for (int k = 0; k < nz; ++k) {
+            const float c = (float)C[k];
+            memcpy(up.data() + o_c32 + (size_t)k * sizeof(float), &c, sizeof(float));
+        }
+        note(p, cudaMemcpyAsync(up_d, up.data(), up_bytes, cudaMemcpyHostToDevice, p->alloc_stream));
+    }
+    double *zt_d = (double *)up_d;
+    const double *lam_d = (const double *)(up_d + o_lam);
     p->zt = zt_d;
-    note(p, cudaMemcpyAsync(zt_d, zt.data(), zt.size() * sizeof(double), cudaMemcpyHostToDevice, p->alloc_stream));
+    p->cup64 = (double *)(up_d + o_c64);
+    p->cup32 = p->mixed ? (float *)(up_d + o_c32) : nullptr;
 
     GridDev &g = p->g;
     memset(&g, 0, sizeof(g));
@@ -839,22 +913,14 @@ int fizzy_proj_plan(fizzy_proj_plan_t *out, const fizzy_proj_desc *d, void *stre
     build_fft(p, ny, d->bc_y, p->fy, &status);
 
     // ---- z factorisation tables per distinct eigenvalue pair
-    const int Ux = d->bc_x == FIZZY_BC_PERIODIC ? nx / 2 + 1 : nx;
-    const int Uy = d->bc_y == FIZZY_BC_PERIODIC ? ny / 2 + 1 : ny;
     p->Ux = Ux;
     p->Uy = Uy;
     const size_t ts = (size_t)Ux * Uy;
-    std::vector<double> lam((size_t)Ux + Uy);
-    for (int u = 0; u < Ux; ++u) lam[u] = eig(u, nx, d->dx, d->bc_x);
-    for (int u = 0; u < Uy; ++u) lam[Ux + u] = eig(u, ny, d->dy, d->bc_y);
-    const double *C = &zt[T_LZC * nz];
     p->mtab64 = dev_alloc<double>(p, ts * nz, &status);
     p->ibtab64 = dev_alloc<double>(p, ts * nz, &status);
-    p->cup64 = dev_alloc<double>(p, nz, &status);
     if (p->mixed) {
         p->mtab32 = dev_alloc<float>(p, ts * nz, &status);
         p->ibtab32 = dev_alloc<float>(p, ts * nz, &status);
-        p->cup32 = dev_alloc<float>(p, nz, &status);
     }
     if (perz) {
         p->wtab64 = dev_alloc<double>(p, ts * nz, &status);
@@ -886,13 +952,6 @@ int fizzy_proj_plan(fizzy_proj_plan_t *out, const fizzy_proj_desc *d, void *stre
     }
     // factorisation tables on the device (bitwise the host recurrence)
     {
-        double *lam_d = dev_alloc<double>(p, lam.size(), &status);
-        if (status) {
-            int st = status;
-            fizzy_proj_destroy(p);
-            return st;
-        }
-        note(p, cudaMemcpyAsync(lam_d, lam.data(), lam.size() * sizeof(double), cudaMemcpyHostToDevice, p->alloc_stream));
         const int blocks = (int)std::min<size_t>((ts + 127) / 128, 4096);
         if (perz)
             k_ztables_cyc<<<blocks, 128, 0, p->alloc_stream>>>(
@@ -905,11 +964,6 @@ int fizzy_proj_plan(fizzy_proj_plan_t *out, const fizzy_proj_desc *d, void *stre
                                                            zt_d + T_LZC * nz, p->mtab64, p->ibtab64,
                                                            p->mixed ? p->mtab32 : nullptr,
                                                            p->mixed ? p->ibtab32 : nullptr, g.sing);
-    }
-    note(p, cudaMemcpyAsync(p->cup64, C, nz * sizeof(double), cudaMemcpyHostToDevice, p->alloc_stream));
-    if (p->mixed) {
-        std::vector<float> c32(C, C + nz);
-        note(p, cudaMemcpyAsync(p->cup32, c32.data(), nz * sizeof(float), cudaMemcpyHostToDevice, p->alloc_stream));
     }
     note(p, cudaMemsetAsync(p->st, 0, sizeof(DevStats), p->alloc_stream));
 

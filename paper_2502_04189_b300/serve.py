@@ -20,7 +20,7 @@ from typing import Callable, Optional
 
 import numpy as np
 
-from . import Server, crop_fill, device_view
+from . import Server, crop_fill, crop_fill_ptrs, device_view
 
 
 @dataclasses.dataclass
@@ -52,8 +52,33 @@ class TemplateFields:
 
     def fill(self, views, desc, offset, stream):
         """Write crops of shape (nz, ny, nx) starting at offset into views[0..5]
-        (one fizzy_crop_fill kernel: 96 bytes of device traffic per point)."""
-        crop_fill(self.fields, views[:6], offset, desc.get("bcx", 0), desc.get("bcy", 0), stream)
+        (one fizzy_crop_fill kernel: 96 bytes of device traffic per point);
+        views may be tensors or RequestViews (raw pointers, no tensors made)."""
+        if isinstance(views, RequestViews):
+            if not hasattr(self, "_src_ptrs"):
+                self._src_ptrs = [t.data_ptr() for t in self.fields]
+            crop_fill_ptrs(self._src_ptrs, self.shape, views.ptrs, views.shape, offset,
+                           desc.get("bcx", 0), desc.get("bcy", 0), stream)
+        else:
+            crop_fill(self.fields, views[:6], offset, desc.get("bcx", 0), desc.get("bcy", 0), stream)
+
+
+class RequestViews:
+    """A request's seven device arrays: raw pointers, with the tensor view of
+    array k made by view_fn on first access (views[k])."""
+
+    def __init__(self, ptrs, shape, view_fn):
+        self.ptrs, self.shape, self._fn, self._t = ptrs, shape, view_fn, {}
+
+    def __getitem__(self, k):
+        if isinstance(k, slice):
+            return [self[i] for i in range(*k.indices(len(self.ptrs)))]
+        if k not in self._t:
+            self._t[k] = self._fn(self.ptrs[k], self.shape)
+        return self._t[k]
+
+    def __len__(self):
+        return len(self.ptrs)
 
 
 def run(server: Server, requests, fill: Callable, deadline: float = 0.1,
@@ -89,7 +114,7 @@ def run(server: Server, requests, fill: Callable, deadline: float = 0.1,
                 break
             pending.popleft()
             shape = (r.desc["nz"], r.desc["ny"], r.desc["nx"])
-            views = [view_fn(p, shape) for p in ptrs]
+            views = RequestViews(ptrs, shape, view_fn)
             fill(r, views, server.stream(slot))
             server.launch(slot)
             inflight[slot] = (r, views)
