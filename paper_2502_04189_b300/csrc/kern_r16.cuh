@@ -252,6 +252,7 @@ template <int N> struct RShape {
     static constexpr int LS = N + 1;
     static constexpr int TX = 2 * LINES;
     static constexpr int MINB = P == 24 ? 5 : P == 12 ? 6 : 65536 / (THREADS * 64);
+    static constexpr int YCH = P == 12 ? 12 : 16;  // y-pass loads of a thread in flight
     static_assert(P % M == 0 && TPL <= 32 && TPL % 2 == 0, "shape");
 };
 constexpr int r_threads(int n) {
@@ -479,7 +480,8 @@ __device__ __forceinline__ void r_combine(float2 (&v)[RShape<N>::P], const RPos<
 // transformed along y in place.  Thread e of the CTA owns column e mod TX of
 // the tile and rows e / TX + (THREADS / TX) i, i < 2P (THREADS / TX = TPL/2
 // rows apart): one address per thread, each warp access 32 consecutive
-// columns (TX >= 32) or two rows of 16.  Column 2l + c of the tile is
+// columns (TX >= 32) or two rows of 16 (YCH of a thread's loads in flight).
+// Column 2l + c of the tile is
 // component c of complex line l.  Forward: real columns -> spectra scaled by
 // 2 (half-complex, or DCT-II for a wall direction); inverse: the reverse,
 // unscaled.
@@ -493,24 +495,21 @@ __device__ __forceinline__ void ypass_r_tile(int nx, int ncol, float *data, int 
     const int cc = tile * TX + col;
     const bool ok = cc < ncol;
     const int kp = ok ? cc / nx : 0;
-    // the thread's first element and the step between its rows
-    float *g0 = data + (size_t)kp * N * nx + (ok ? cc - kp * nx : 0) + (size_t)row0 * nx;
-    const size_t gstep = (size_t)RSTEP * nx;
-    float *s0 = (float *)sm.x + (col >> 1) * (2 * LS) + (col & 1) + 2 * row0;
+    // the thread's column (32-bit row offsets within its plane)
+    float *gcol = data + (size_t)kp * N * nx + (ok ? cc - kp * nx : 0);
+    float *scol = (float *)sm.x + (col >> 1) * (2 * LS) + (col & 1);
     float2 *X = sm.x + q.ln * LS;
-    // 1. stage the tile (eight loads in flight)
+    // 1. stage the tile (YCH loads in flight)
     {
-        const float *gp = g0;
-        float *sp = s0;
+        constexpr int CH = S::YCH;
+        static_assert((2 * P) % CH == 0, "y-pass chunks");
 #pragma unroll 1
-        for (int i0 = 0; i0 < 2 * P; i0 += 8) {
-            float r[8];
+        for (int i0 = 0; i0 < 2 * P; i0 += CH) {
+            float r[CH];
 #pragma unroll
-            for (int u = 0; u < 8; ++u) r[u] = ok ? gp[u * gstep] : 0.f;
+            for (int u = 0; u < CH; ++u) r[u] = ok ? gcol[(size_t)(row0 + RSTEP * (i0 + u)) * nx] : 0.f;
 #pragma unroll
-            for (int u = 0; u < 8; ++u) sp[2 * RSTEP * u] = r[u];
-            gp += 8 * gstep;
-            sp += 16 * RSTEP;
+            for (int u = 0; u < CH; ++u) scol[2 * (row0 + RSTEP * (i0 + u))] = r[u];
         }
     }
     __syncthreads();
@@ -531,16 +530,10 @@ __device__ __forceinline__ void ypass_r_tile(int nx, int ncol, float *data, int 
     }
     __syncthreads();
     // 2. write the tile back
-    if (ok) {
-        float *gp = g0;
-        const float *sp = s0;
-#pragma unroll 1
-        for (int i0 = 0; i0 < 2 * P; i0 += 8) {
 #pragma unroll
-            for (int u = 0; u < 8; ++u) gp[u * gstep] = sp[2 * RSTEP * u];
-            gp += 8 * gstep;
-            sp += 16 * RSTEP;
-        }
+    for (int i = 0; i < 2 * P; ++i) {
+        const int row = row0 + RSTEP * i;
+        if (ok) gcol[(size_t)row * nx] = scol[2 * row];
     }
     __syncthreads();  // the buffer is free for the next tile
 }
