@@ -417,11 +417,16 @@ int fizzy_serve_admit(fizzy_serve_t s, const fizzy_proj_desc *d, int *slot, doub
 /* The slot's stream (fill the inputs on it before launch). */
 int fizzy_serve_stream(fizzy_serve_t s, int slot, void **stream);
 
-/* Queue the projection of an admitted slot on its stream. */
+/* Queue the projection of an admitted slot on its stream.  A mixed plan's
+ * solve is queued with at most two refinement sweeps (most solves converge
+ * after one); see fizzy_serve_poll for the rest. */
 int fizzy_serve_launch(fizzy_serve_t s, int slot);
 
 /* Report up to max launched slots whose projection has finished (without
- * blocking); returns how many were written to slots[]. */
+ * blocking); returns how many were written to slots[].  A mixed solve that
+ * has finished its queued sweeps without converging has its remaining sweeps
+ * (up to its plan's max_refine) queued here instead, and is reported once
+ * they have run: the results equal those of fizzy_proj_solve. */
 int fizzy_serve_poll(fizzy_serve_t s, int *slots, int max);
 
 /* Stats of a finished slot's projection. */

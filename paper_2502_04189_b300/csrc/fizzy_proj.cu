@@ -1134,16 +1134,38 @@ int fizzy_proj_timing(fizzy_proj_plan_t p, int idx, const char **name, double *m
     return KS_N;
 }
 
+// The launches of one solve.  sw_first = 0: the whole sequence with the
+// refinement sweeps 1 .. sw_last (mixed) and the conditional correction;
+// sw_first >= 1 (mixed only): the sweeps sw_first .. sw_last alone, which
+// continue a solve whose sweeps up to sw_first - 1 ran without converging
+// (the stored residual, p and u are where those sweeps left them).  The
+// kernels of a sweep return at once when the solve has converged, so the
+// results do not depend on how the sweeps are split between calls.
+static int solve_launch(fizzy_proj_plan_t p, const double *phi, const double *p_n,
+                        const double *p_nm1, double *u, double *v, double *w, double *p_np1,
+                        cudaStream_t s, int sw_first, int sw_last);
+
 int fizzy_proj_solve(fizzy_proj_plan_t p, const double *phi, const double *p_n, const double *p_nm1,
                      double *u, double *v, double *w, double *p_np1, fizzy_proj_stats *st,
                      void *stream) {
     if (!p) return FIZZY_ERR_INVALID;
+    const int rc = solve_launch(p, phi, p_n, p_nm1, u, v, w, p_np1, (cudaStream_t)stream, 0, p->max_refine);
+    if (rc) return rc;
+    if (st) return fizzy_proj_get_stats(p, st, stream);
+    return FIZZY_OK;
+}
+
+static int solve_launch(fizzy_proj_plan_t p, const double *phi, const double *p_n,
+                        const double *p_nm1, double *u, double *v, double *w, double *p_np1,
+                        cudaStream_t s, int sw_first, int sw_last) {
     if (!phi || !p_n || !p_nm1 || !u || !v || !w || !p_np1)
         return set_err(p, FIZZY_ERR_INVALID, "null array pointer");
     if (p_np1 == phi || p_np1 == p_n || p_np1 == p_nm1 || p_np1 == u || p_np1 == v || p_np1 == w)
         return set_err(p, FIZZY_ERR_INVALID, "p_np1 aliases an input");
     if (!staggered_bcs(p->desc)) return set_err(p, FIZZY_ERR_UNSUPPORTED, kNeedsStaggeredBcs);
-    cudaStream_t s = (cudaStream_t)stream;
+    if (sw_first < 0 || (sw_first > 0 && !p->mixed) || sw_last > p->max_refine)
+        return set_err(p, FIZZY_ERR_INVALID, "refinement sweeps out of range");
+    const bool head = sw_first == 0;  // the sequence up to the residual of the FP32 solution
     const GridDev &g = p->g;
     const int nx = g.nx, ny = g.ny, nz = g.nz;
     const dim3 cblk(32, 8), cgrd((nx + 31) / 32, (ny + 7) / 8, nz);
@@ -1169,18 +1191,20 @@ int fizzy_proj_solve(fizzy_proj_plan_t p, const double *phi, const double *p_n, 
     xa.qz = p->qz;
     xa.st = p->st;
     cudaError_t e = cudaSuccess;
-    if (p->mixed || p->check) e = cudaMemsetAsync(p->st, 0, sizeof(DevStats), s);
+    if (head && (p->mixed || p->check)) e = cudaMemsetAsync(p->st, 0, sizeof(DevStats), s);
     if (e != cudaSuccess) return cuda_err(p, e, "memset");
 
     const bool need_usq = p->check || p->mixed;
     const dim3 fgrd = flux_grid(nx, ny, nz), fblk(FLUX_BX, FLUX_BY);
-    if (p->desc.rho_g <= p->desc.rho_l)
+    if (!head) {
+        // continuation: only the sweeps below
+    } else if (p->desc.rho_g <= p->desc.rho_l)
         TIMED(KS_FLUX, (k_flux<true><<<fgrd, fblk, 0, s>>>(g, kFluxKc, phi, p_n, p_nm1, u, v, w, p->qx,
                                                            p->qy, p->qz, need_usq ? p->usq_part : nullptr)));
     else
         TIMED(KS_FLUX, (k_flux<false><<<fgrd, fblk, 0, s>>>(g, kFluxKc, phi, p_n, p_nm1, u, v, w, p->qx,
                                                             p->qy, p->qz, need_usq ? p->usq_part : nullptr)));
-    if (need_usq)
+    if (head && need_usq)
         TIMED(KS_SUM, (k_sum_partials<<<1, 1024, 0, s>>>(p->usq_part, p->n_usq_part, p->usq_sum)));
     if (!p->mixed) {
         xa.out = p->fhat64;
@@ -1202,17 +1226,23 @@ int fizzy_proj_solve(fizzy_proj_plan_t p, const double *phi, const double *p_n, 
         xa.f_out = p->f;
         const int *conv = &p->st->converged;
         const int xyg = XY_CL * nz;  // fused x-y passes: one cluster per z-plane
-        if (p->xy_fused) {
+        if (!head) {
+            // continuation: the FP32 solution, its residual and the first
+            // sweeps are already on the stream
+        } else if (p->xy_fused) {
             TIMED(KS_XFWD, (p->xyf_div<<<xyg, p->xy_threads, p->xy_smem, s>>>(g, xa)));
         } else {
             TIMED(KS_XFWD, (p->kern.xf32d<<<grid(xrt, CAP_XF32D), p->xthr32, smx32r, s>>>(g, p->fx.d32, p->Lx, xa, xrt)));
             TIMED(KS_YFWD, (p->kern.yf32<<<grid(ytiles, CAP_Y32F), p->ythr32, p->smem_y32, s>>>(nx, ny, p->fy.d32, p->TXy, p->fhat32, nullptr, ygx, ytiles)));
         }
-        if (g.perz)
-            TIMED(KS_THOMAS, (k_thomas_cyc<float><<<grid(ttiles, CAP_TH32C), THOMAS_BLOCK, thomas_cyc_smem<float>(), s>>>(g, p->Ux, p->Uy, p->mtab32, p->ibtab32, p->cup32, p->wtab32, p->qtab32, p->fhat32, nullptr, ttiles)));
-        else
-            TIMED(KS_THOMAS, (k_thomas<float><<<grid(ttiles, CAP_TH32), THOMAS_BLOCK, thomas_smem<float>(), s>>>(g, p->Ux, p->Uy, p->mtab32, p->ibtab32, p->cup32, p->fhat32, nullptr, ttiles)));
-        if (p->xy_fused) {
+        if (head) {
+            if (g.perz)
+                TIMED(KS_THOMAS, (k_thomas_cyc<float><<<grid(ttiles, CAP_TH32C), THOMAS_BLOCK, thomas_cyc_smem<float>(), s>>>(g, p->Ux, p->Uy, p->mtab32, p->ibtab32, p->cup32, p->wtab32, p->qtab32, p->fhat32, nullptr, ttiles)));
+            else
+                TIMED(KS_THOMAS, (k_thomas<float><<<grid(ttiles, CAP_TH32), THOMAS_BLOCK, thomas_smem<float>(), s>>>(g, p->Ux, p->Uy, p->mtab32, p->ibtab32, p->cup32, p->fhat32, nullptr, ttiles)));
+        }
+        if (!head) {
+        } else if (p->xy_fused) {
             TIMED(KS_XINV, (p->xyi_store<<<xyg, p->xy_threads, p->xy_smem, s>>>(g, p->fhat32, p_np1, p->st)));
         } else {
             TIMED(KS_YINV, (p->kern.yi32<<<grid(ytiles, CAP_Y32I), p->ythr32, p->smem_y32, s>>>(nx, ny, p->fy.d32, p->TXy, p->fhat32, nullptr, ygx, ytiles)));
@@ -1237,12 +1267,15 @@ int fizzy_proj_solve(fizzy_proj_plan_t p, const double *phi, const double *p_n, 
         const dim3 rcb(FLUX_BX, FLUX_BY);
         const int rtgx = (nx + FLUX_BX - 1) / FLUX_BX, rtgy = (ny + FLUX_BY - 1) / FLUX_BY;
         const int rctiles = rtgx * rtgy * ((nz + RESID_KC - 1) / RESID_KC);
-        TIMED(KS_RESID, (k_resid<false><<<grid(rctiles, CAP_RC), rcb, 0, s>>>(g, RESID_KC, ra, rtgx, rtgy, rctiles)));
+        if (head)
+            TIMED(KS_RESID, (k_resid<false><<<grid(rctiles, CAP_RC), rcb, 0, s>>>(g, RESID_KC, ra, rtgx, rtgy, rctiles)));
         XArgs la = xa;  // in-place transform of the stored residual
         la.f_out = nullptr;
-        for (int sw = 1; sw <= p->max_refine; ++sw) {
-            // a one-sweep solve runs sweep 1; later sweeps usually return at once
-            auto gs = [&](int tiles, int c) { return sw == 1 ? grid(tiles, c) : rgrid(tiles, c); };
+        const int sw0 = head ? 1 : sw_first;
+        for (int sw = sw0; sw <= sw_last; ++sw) {
+            // the first sweep of a call runs a grid per tile; later sweeps
+            // usually return at once and run the resident grid
+            auto gs = [&](int tiles, int c) { return sw == sw0 ? grid(tiles, c) : rgrid(tiles, c); };
             if (p->xy_fused) {
                 TIMED(KS_XFWD_R, (p->xyf_load<<<xyg, p->xy_threads, p->xy_smem, s>>>(g, la)));
             } else {
@@ -1262,15 +1295,20 @@ int fizzy_proj_solve(fizzy_proj_plan_t p, const double *phi, const double *p_n, 
             ra.slot = sw;
             TIMED(KS_RCORR, (k_resid<true><<<gs(rctiles, CAP_RC), rcb, 0, s>>>(g, RESID_KC, ra, rtgx, rtgy, rctiles)));
         }
-        // the correction, unless a fused residual pass has written u
+        // the correction, unless a fused residual pass has written u (a
+        // continuation follows at least one fused pass: nothing to do)
         const int ctiles = rtgx * rtgy * nz;
-        TIMED(KS_CORRECT, (k_correct_if<<<rgrid(ctiles, CAP_CIF), rcb, 0, s>>>(g, p_np1, p->qx, p->qy, p->qz, u, v, w, p->st, rtgx, rtgy, ctiles)));
+        if (head)
+            TIMED(KS_CORRECT, (k_correct_if<<<rgrid(ctiles, CAP_CIF), rcb, 0, s>>>(g, p_np1, p->qx, p->qy, p->qz, u, v, w, p->st, rtgx, rtgy, ctiles)));
     }
     if (!p->mixed) TIMED(KS_CORRECT, (k_correct<<<cgrd, cblk, 0, s>>>(g, p_np1, p->qx, p->qy, p->qz, u, v, w)));
+    if (p->check && !head) {  // the continuation's u replaces the one measured before
+        e = cudaMemsetAsync(&p->st->divmax_bits, 0, sizeof(p->st->divmax_bits), s);
+        if (e != cudaSuccess) return cuda_err(p, e, "memset");
+    }
     if (p->check) TIMED(KS_DIVMAX, (k_divmax<<<rgrd, rblk, 0, s>>>(g, u, v, w, p->st)));
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_err(p, e, "solve launch");
-    if (st) return fizzy_proj_get_stats(p, st, stream);
     return FIZZY_OK;
 }
 

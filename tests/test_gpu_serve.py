@@ -152,3 +152,54 @@ def test_served_periodic_z_requests(cuda_ok):
             got = dict(p=served[i][0], u=served[i][1], v=served[i][2], w=served[i][3])
             ep, eu = compare(c, got, O.project_case(c))
             assert ep <= 1e-9 and eu <= 1e-9, (i, ep, eu)
+
+
+def test_served_sweeps_beyond_the_first_two(cuda_ok):
+    """A served mixed solve is queued with two refinement sweeps; one that
+    has not converged by then (here: tol = 1e-30, divergence rule off, so it
+    stops only at the residual floor) gets its remaining sweeps queued when
+    it is polled.  Results and stats equal the plain solve's bit for bit."""
+    import ctypes
+    import torch
+    from paper_2502_04189_b300 import _abi
+    tmpl = I.make_case(I.CaseSpec(nx=48, ny=48, nz=40, n_bubbles=4, radius_cells=5, config=41))
+    fields = S.TemplateFields(tmpl)
+    reqs = []
+    for i, (nx, ny, nz, beta) in enumerate([(32, 48, 24, 0.0), (48, 32, 30, 1.5), (32, 32, 16, 1.2)]):
+        desc = dict(nx=nx, ny=ny, nz=nz, dx=1.0 / nx, dy=1.0 / nx, zf=I.z_faces(nz, nz / nx, beta),
+                    bcx=i % 2, bcy=0, rho_l=1.0, rho_g=1e-3, dt=1e-4, precision=F.MIXED,
+                    tol=1e-30, div_tol=-1.0, max_refine=6)
+        reqs.append(S.Request(i, 0.0, desc, (3 * i, 5, 7)))
+    server = F.Server(4 << 30, slots=4)
+    served, stats = {}, {}
+
+    def fill(r, views, stream):
+        fields.fill(views, r.desc, r.offset, stream)
+
+    def on_done(r, views):
+        served[r.index] = [views[k].cpu().numpy() for k in (6, 3, 4, 5)]
+
+    out, summ = S.run(server, reqs, fill, deadline=30.0, on_done=on_done)
+    server.close()
+    assert summ["admitted"] == 3
+    for o in out:
+        stats[o.index] = o.stats
+    for r in reqs:
+        d = dict(r.desc)
+        plan = F.Plan(d["nx"], d["ny"], d["nz"], d["dx"], d["dy"], zf=d["zf"], bcx=d["bcx"],
+                      bcy=d["bcy"], rho_l=d["rho_l"], rho_g=d["rho_g"], dt=d["dt"], precision=F.MIXED,
+                      tol=d["tol"], div_tol=d["div_tol"], max_refine=d["max_refine"])
+        phi, pn, pm, u, v, w = (to_dev(a) for a in crop(tmpl, d, r.offset))
+        p = torch.empty_like(phi)
+        plan.solve(phi, pn, pm, u, v, w, p)
+        torch.cuda.synchronize()
+        raw = _abi.Stats()  # read directly: a solve at the floor may report not converged
+        _abi.lib().fizzy_proj_get_stats(plan._h, ctypes.byref(raw), None)
+        st = raw.as_dict()
+        plan.close()
+        assert st["iterations"] >= 3, st  # the continuation ran
+        assert stats[r.index]["iterations"] == st["iterations"]
+        assert stats[r.index]["relres"] == st["relres"]
+        assert stats[r.index]["converged"] == st["converged"]
+        for got, ref in zip(served[r.index], (p, u, v, w)):
+            assert np.array_equal(got, ref.cpu().numpy()), r.index
