@@ -54,6 +54,7 @@ FP64_PER_CLK_PER_SM = 2
 
 WORKLOADS = {
     "bubbles512_stretched": I.bubbles512_stretched_spec,
+    "bubbles384_stretched": I.bubbles384_stretched_spec,
     "bubbles256": I.bubbles256_spec,
     "drop32": I.drop32_spec,
     "emulsion256": I.emulsion256_spec,

@@ -351,6 +351,13 @@ def bubbles512_stretched_spec() -> CaseSpec:
     return bubbles_spec(512, 400, 6.0, 1.5, config=2)
 
 
+def bubbles384_stretched_spec() -> CaseSpec:
+    """The 512^3 stretched recipe at 384^3 (a length of the register-resident
+    passes that is not a power of two: 384 = 2 x 24 x 8); 170 drops keep the
+    gas fraction of the 512^3 case."""
+    return bubbles_spec(384, 170, 6.0, 1.5, config=70)
+
+
 def emulsion_spec(n: int = 256, n_drops: int = 400, radius_cells: float = 8.0,
                   config: int = 5) -> CaseSpec:
     """n^3 unit triperiodic box (periodic x, y and z), standing in for the
