@@ -499,18 +499,20 @@ __device__ __forceinline__ void ypass_r_tile(int nx, int ncol, float *data, int 
     float *gcol = data + (size_t)kp * N * nx + (ok ? cc - kp * nx : 0);
     float *scol = (float *)sm.x + (col >> 1) * (2 * LS) + (col & 1);
     float2 *X = sm.x + q.ln * LS;
-    // 1. stage the tile (YCH loads in flight)
-    {
-        constexpr int CH = S::YCH;
-        static_assert((2 * P) % CH == 0, "y-pass chunks");
-#pragma unroll 1
-        for (int i0 = 0; i0 < 2 * P; i0 += CH) {
-            float r[CH];
+    // 1. stage the tile: every element of the thread's column as an
+    // asynchronous 4-byte global -> shared copy (all 2P in flight, no
+    // registers held), zeros past the last column
+    if (ok) {
 #pragma unroll
-            for (int u = 0; u < CH; ++u) r[u] = ok ? gcol[(size_t)(row0 + RSTEP * (i0 + u)) * nx] : 0.f;
-#pragma unroll
-            for (int u = 0; u < CH; ++u) scol[2 * (row0 + RSTEP * (i0 + u))] = r[u];
+        for (int i = 0; i < 2 * P; ++i) {
+            const int row = row0 + RSTEP * i;
+            cp_async<4>(scol + 2 * row, gcol + (size_t)row * nx);
         }
+        cp_async_commit();
+        cp_async_wait<0>();
+    } else {
+#pragma unroll
+        for (int i = 0; i < 2 * P; ++i) scol[2 * (row0 + RSTEP * i)] = 0.f;
     }
     __syncthreads();
     float2 v[P];
