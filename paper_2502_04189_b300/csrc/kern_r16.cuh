@@ -703,13 +703,22 @@ __global__ void __launch_bounds__(RShape<N>::THREADS, RShape<N>::MINB)
                 if (row < nlines) {
                     const int k = fdiv(row, g.ny, g.rny), j = row - k * g.ny;
                     const double cz = g.dvz[k];
-#pragma unroll 4
-                    for (int i = 0; i < N / 32; ++i) {
-                        const int x = lane + 32 * i;
-                        const double f = div_q<false>(g, x, j, k, g.dvx, g.dvy, cz, a.qx, a.qy, a.qz);
-                        a.f_out[(size_t)row * N + x] = f;
-                        mx = umax64(mx, absbits(f));
-                        dr[2 * x] = f64_to_f32_shift(f, 0) * scale32;
+                    // the face loads of two cells ahead of their arithmetic
+                    // and stores (a store to f could alias a later load)
+                    constexpr int U = 2;
+#pragma unroll 1
+                    for (int i0 = 0; i0 < N / 32; i0 += U) {
+                        QFaces qf[U];
+#pragma unroll
+                        for (int u = 0; u < U; ++u) qf[u] = div_q_ld<false>(g, lane + 32 * (i0 + u), j, k, a.qx, a.qy, a.qz);
+#pragma unroll
+                        for (int u = 0; u < U; ++u) {
+                            const int x = lane + 32 * (i0 + u);
+                            const double f = div_q_eval(qf[u], g.dvx, g.dvy, cz);
+                            a.f_out[(size_t)row * N + x] = f;
+                            mx = umax64(mx, absbits(f));
+                            dr[2 * x] = f64_to_f32_shift(f, 0) * scale32;
+                        }
                     }
                 } else {
                     for (int i = 0; i < N / 32; ++i) dr[2 * (lane + 32 * i)] = 0.f;
