@@ -1418,8 +1418,17 @@ __device__ __forceinline__ void resid_body(const GridDev &g, int kc, const RArgs
     unsigned long long mx = 0ull;
     int buf = 0;
     for (int k = k0; k < k1; ++k) {
-        double de = 0.0, dn = 0.0, dt = 0.0, pt = 0.0;
+        double de = 0.0, dn = 0.0, dt = 0.0, pt = 0.0, fc = 0.0;
         if (on) {
+            // every load of the cell first: a store below could alias a later
+            // load, which would then wait for it
+            double qxc = 0.0, qyc = 0.0, qzc = 0.0;
+            if (CORR) {
+                qxc = ldp<CG>(a.qx + c);
+                qyc = ldp<CG>(a.qy + c);
+                qzc = ldp<CG>(a.qz + c);
+            }
+            fc = ldp<CG>(a.f + c);
             if (hasE) de = ldp<CG>(a.p + c + oE) - pc;
             if (hasN) dn = ldp<CG>(a.p + c + oN) - pc;
             if (k < g.nz - 1) {
@@ -1429,9 +1438,9 @@ __device__ __forceinline__ void resid_body(const GridDev &g, int kc, const RArgs
                 dt = ldp<CG>(a.p + c - (size_t)k * pl) - pc;  // seam to plane 0
             }
             if (CORR) {
-                a.u[c] = (g.bcx == BC_NEUMANN && i == g.nx - 1) ? 0.0 : fmaT(-g.cgx, de, ldp<CG>(a.qx + c));
-                a.v[c] = (g.bcy == BC_NEUMANN && j == g.ny - 1) ? 0.0 : fmaT(-g.cgy, dn, ldp<CG>(a.qy + c));
-                a.w[c] = (k < g.nz - 1 || g.perz) ? fmaT(-g.cgz[k], dt, ldp<CG>(a.qz + c)) : 0.0;
+                a.u[c] = (g.bcx == BC_NEUMANN && i == g.nx - 1) ? 0.0 : fmaT(-g.cgx, de, qxc);
+                a.v[c] = (g.bcy == BC_NEUMANN && j == g.ny - 1) ? 0.0 : fmaT(-g.cgy, dn, qyc);
+                a.w[c] = (k < g.nz - 1 || g.perz) ? fmaT(-g.cgz[k], dt, qzc) : 0.0;
             }
             sdn[(buf * FLUX_BY + ty) * FLUX_BX + tx] = dn;
         }
@@ -1441,7 +1450,7 @@ __device__ __forceinline__ void resid_body(const GridDev &g, int kc, const RArgs
             if (tx == 0) dw = hasW ? pc - ldp<CG>(a.p + c + oW) : 0.0;
             const double ds = (ty > 0) ? sdn[(buf * FLUX_BY + ty - 1) * FLUX_BX + tx]
                                        : (hasS ? pc - ldp<CG>(a.p + c + oS) : 0.0);
-            double res = fmaT(-g.idx2, de - dw, ldp<CG>(a.f + c));
+            double res = fmaT(-g.idx2, de - dw, fc);
             res = fmaT(-g.idy2, dn - ds, res);
             res = fmaT(-g.lzc[k], dt, res);
             res = fmaT(g.lza[k], db, res);
