@@ -142,6 +142,43 @@ __device__ __forceinline__ double f32_to_f64_shift(float f, int es) {
     return __hiloint2double((int)(hi | (b & 0x80000000u)), (int)(a << 29));
 }
 
+// Double-float arithmetic (an unevaluated sum hi + lo of two floats, about
+// 48 significant bits): Knuth's two-sum, Dekker's fast two-sum and the
+// FMA-based exact product, written with explicit round-to-nearest
+// operations so the compiler neither contracts nor reorders them.
+__device__ __forceinline__ float2 two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b), bb = __fsub_rn(s, a);
+    return make_float2(s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb)));
+}
+__device__ __forceinline__ float2 fast_two_sum(float a, float b) {  // |a| >= |b| or a = 0
+    const float s = __fadd_rn(a, b);
+    return make_float2(s, __fsub_rn(b, __fsub_rn(s, a)));
+}
+__device__ __forceinline__ float2 df_add(float2 x, float2 y) {
+    const float2 s = two_sum(x.x, y.x);
+    return fast_two_sum(s.x, __fadd_rn(s.y, __fadd_rn(x.y, y.y)));
+}
+__device__ __forceinline__ float2 df_neg(float2 x) { return make_float2(-x.x, -x.y); }
+__device__ __forceinline__ float2 df_mul(float2 x, float2 c) {
+    const float p = __fmul_rn(x.x, c.x);
+    float e = __fmaf_rn(x.x, c.x, -p);  // the product's rounding error, exactly
+    e = __fmaf_rn(x.x, c.y, e);
+    e = __fmaf_rn(x.y, c.x, e);
+    return fast_two_sum(p, e);
+}
+// A double as hi + lo floats with integer operations only: hi is the double
+// truncated to 24 bits, lo the remaining 29 mantissa bits rounded to 24, so
+// |x - hi - lo| <= 2^-47 |x| for 2^-74 <= |x| < 2^128 (below 2^-74 lo
+// flushes to 0 and the error is at most 2^-24 |x|).
+__device__ __forceinline__ float2 f64_split(double x) {
+    const float hi = f64_to_f32_shift(x, 0);
+    const unsigned h = (unsigned)__double2hiint(x), l = (unsigned)__double2loint(x);
+    const int sb = (int)((h >> 20) & 0x7ff) - 1075 + 127;  // biased float exponent of 2^(E - 1075)
+    float lo = 0.f;
+    if (sb > 0) lo = __fmul_rn(__uint2float_rn(l & 0x1fffffffu), __int_as_float(sb << 23));
+    return make_float2(hi, (h & 0x80000000u) ? -lo : lo);
+}
+
 // Asynchronous global -> shared copies (cp.async, LDGSTS): the copy runs in
 // the background and the issuing thread waits for its own groups.
 template <int BYTES>
