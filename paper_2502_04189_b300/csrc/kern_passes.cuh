@@ -1409,6 +1409,15 @@ __device__ __forceinline__ unsigned long long resid0_df_march(
     float2 *sd = (float2 *)sdn;
     auto pf = [&](size_t at) { return f64_to_f32_shift(ldp<CG>(a.p + at), 0); };  // exact
     const float2 cx = f64_split(-g.idx2), cy = f64_split(-g.idy2);
+    // the tile's per-plane factors -c_k and a_k as float pairs, split once
+    __shared__ float2 s_cz[2][RESID_KC];
+    {
+        const int t = threadIdx.x + threadIdx.y * blockDim.x;
+        if (t < k1 - k0) {
+            s_cz[0][t] = f64_split(-g.lzc[k0 + t]);
+            s_cz[1][t] = f64_split(g.lza[k0 + t]);
+        }
+    }
     float pc = on ? pf(c) : 0.f;
     float2 db = make_float2(0.f, 0.f);
     if (on && k0 > 0) db = two_sum(pc, -pf(c - pl));
@@ -1440,8 +1449,8 @@ __device__ __forceinline__ unsigned long long resid0_df_march(
             float2 res = f64_split(fc);
             res = df_add(res, df_mul(df_add(de, df_neg(dw)), cx));
             res = df_add(res, df_mul(df_add(dn, df_neg(ds)), cy));
-            res = df_add(res, df_mul(dt, f64_split(-g.lzc[k])));
-            res = df_add(res, df_mul(db, f64_split(g.lza[k])));
+            res = df_add(res, df_mul(dt, s_cz[0][k - k0]));
+            res = df_add(res, df_mul(db, s_cz[1][k - k0]));
             const float r = __fadd_rn(res.x, res.y);
             mx = umax64(mx, absbits(f32_to_f64_shift(r, 0)));
             a.r32[c] = f64_to_f32_shift(f32_to_f64_shift(r, 0), ef) * scale32;
