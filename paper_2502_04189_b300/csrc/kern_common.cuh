@@ -179,6 +179,27 @@ __device__ __forceinline__ float2 f64_split(double x) {
     return make_float2(hi, (h & 0x80000000u) ? -lo : lo);
 }
 
+// A double as the exact sum h + m + l of three floats (integer operations):
+// h the top 24 significant bits, m the next 24, l the last 5, for
+// 2^-78 <= |x| < 2^128 (below, the parts that fall under the float range
+// flush to 0).
+struct F3 {
+    float h, m, l;
+};
+__device__ __forceinline__ F3 f64_split3(double x) {
+    const unsigned hb = (unsigned)__double2hiint(x), lb = (unsigned)__double2loint(x);
+    const int E = (int)((hb >> 20) & 0x7ff);
+    const bool neg = (hb & 0x80000000u) != 0;
+    F3 r;
+    r.h = f64_to_f32_shift(x, 0);
+    const int sm = E - 1070 + 127, sl = E - 1075 + 127;  // biased float exponents of 2^(E-1070), 2^(E-1075)
+    const float m = sm > 0 ? __fmul_rn(__uint2float_rn((lb >> 5) & 0xffffffu), __int_as_float(sm << 23)) : 0.f;
+    const float l = sl > 0 ? __fmul_rn(__uint2float_rn(lb & 0x1fu), __int_as_float(sl << 23)) : 0.f;
+    r.m = neg ? -m : m;
+    r.l = neg ? -l : l;
+    return r;
+}
+
 // Asynchronous global -> shared copies (cp.async, LDGSTS): the copy runs in
 // the background and the issuing thread waits for its own groups.
 template <int BYTES>

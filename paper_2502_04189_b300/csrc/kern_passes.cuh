@@ -1391,23 +1391,46 @@ struct RArgs {
     double tol;
 };
 
-// The march of the first residual (slot 0) in double-float.  Its p is the
-// FP32 solution, every value exactly a float, so each face difference
-// p_b - p_a is exact as a float pair (two-sum); the rest of r = f - L_h p
-// (the second differences, the metric factors, f itself split from FP64)
-// runs in double-float arithmetic on the FP32 pipe: relative error about
-// 2^-44 per operation, so |r - r_exact| stays near 1e-13 max|f|, far below
-// the 1e-10 the refinement aims at, without FP64 instructions.  Same tile,
-// order of faces and neighbour exchange as the FP64 march; sdn holds the
-// float pairs of dN.
-template <bool CG>
-__device__ __forceinline__ unsigned long long resid0_df_march(
-    const GridDev &g, const RArgs &a, int k0, int k1, size_t c, bool on, int tx, int ty, bool hasE,
-    bool hasW, bool hasN, bool hasS, long long oE, long long oW, long long oN, long long oS, int ef,
-    float scale32, double *sdn) {
+// The residual marches in double-float.  The first residual's p is the FP32
+// solution, every value exactly a float; later p (the solution plus
+// corrections, FP64) is held as the exact sum of three floats (f64_split3).
+// Either way each face difference p_b - p_a is formed from exact float
+// differences (two-sum), so it carries no cancellation error; the rest of
+// r = f - L_h p (the second differences, the metric factors, f split from
+// FP64) runs in double-float arithmetic on the FP32 pipe, relative error
+// about 2^-44 per operation: |r - r_exact| stays near 1e-13 max|f|, far below
+// the 1e-10 the refinement aims at.  CORR also writes the correction
+// u = q' - (dt/rho0) G p from the same differences (each rounded to FP64,
+// then one FP64 multiply-add per face).  Same tile, order of faces and
+// neighbour exchange as before; sdn holds the float pairs of dN.
+template <bool CORR> struct PVal {
+    float h;
+    __device__ __forceinline__ static PVal load(double x) { return PVal{f64_to_f32_shift(x, 0)}; }  // exact
+    __device__ __forceinline__ static PVal zero() { return PVal{0.f}; }
+    __device__ __forceinline__ float2 minus(const PVal &a) const { return two_sum(h, -a.h); }
+};
+template <> struct PVal<true> {
+    F3 v;
+    __device__ __forceinline__ static PVal load(double x) { return PVal{f64_split3(x)}; }
+    __device__ __forceinline__ static PVal zero() { return PVal{F3{0.f, 0.f, 0.f}}; }
+    __device__ __forceinline__ float2 minus(const PVal &a) const {
+        const float2 d = df_add(two_sum(v.h, -a.v.h), two_sum(v.m, -a.v.m));
+        return df_add(d, make_float2(__fsub_rn(v.l, a.v.l), 0.f));
+    }
+};
+__device__ __forceinline__ double df_to_f64(float2 d) {
+    return f32_to_f64_shift(d.x, 0) + f32_to_f64_shift(d.y, 0);
+}
+
+template <bool CG, bool CORR>
+__device__ __forceinline__ unsigned long long resid_df_march(
+    const GridDev &g, const RArgs &a, int k0, int k1, size_t c, bool on, int i, int j, int tx, int ty,
+    bool hasE, bool hasW, bool hasN, bool hasS, long long oE, long long oW, long long oN, long long oS,
+    int ef, float scale32, double *sdn) {
+    typedef PVal<CORR> PV;
     const size_t pl = (size_t)g.nx * g.ny;
     float2 *sd = (float2 *)sdn;
-    auto pf = [&](size_t at) { return f64_to_f32_shift(ldp<CG>(a.p + at), 0); };  // exact
+    auto pv = [&](size_t at) { return PV::load(ldp<CG>(a.p + at)); };
     const float2 cx = f64_split(-g.idx2), cy = f64_split(-g.idy2);
     // the tile's per-plane factors -c_k and a_k as float pairs, split once
     __shared__ float2 s_cz[2][RESID_KC];
@@ -1418,34 +1441,44 @@ __device__ __forceinline__ unsigned long long resid0_df_march(
             s_cz[1][t] = f64_split(g.lza[k0 + t]);
         }
     }
-    float pc = on ? pf(c) : 0.f;
+    PV pc = on ? pv(c) : PV::zero();
     float2 db = make_float2(0.f, 0.f);
-    if (on && k0 > 0) db = two_sum(pc, -pf(c - pl));
-    else if (on && g.perz) db = two_sum(pc, -pf(c + (size_t)(g.nz - 1) * pl));  // seam
+    if (on && k0 > 0) db = pc.minus(pv(c - pl));
+    else if (on && g.perz) db = pc.minus(pv(c + (size_t)(g.nz - 1) * pl));  // seam
     unsigned long long mx = 0ull;
     int buf = 0;
     for (int k = k0; k < k1; ++k) {
         float2 de = make_float2(0.f, 0.f), dn = de, dt = de;
-        float pt = 0.f;
-        double fc = 0.0;
+        PV pt = PV::zero();
+        double fc = 0.0, qxc = 0.0, qyc = 0.0, qzc = 0.0;
         if (on) {
+            if (CORR) {  // every load before the stores below (which could alias them)
+                qxc = ldp<CG>(a.qx + c);
+                qyc = ldp<CG>(a.qy + c);
+                qzc = ldp<CG>(a.qz + c);
+            }
             fc = ldp<CG>(a.f + c);
-            if (hasE) de = two_sum(pf(c + oE), -pc);
-            if (hasN) dn = two_sum(pf(c + oN), -pc);
+            if (hasE) de = pv(c + oE).minus(pc);
+            if (hasN) dn = pv(c + oN).minus(pc);
             if (k < g.nz - 1) {
-                pt = pf(c + pl);
-                dt = two_sum(pt, -pc);
+                pt = pv(c + pl);
+                dt = pt.minus(pc);
             } else if (g.perz) {
-                dt = two_sum(pf(c - (size_t)k * pl), -pc);  // seam to plane 0
+                dt = pv(c - (size_t)k * pl).minus(pc);  // seam to plane 0
+            }
+            if (CORR) {
+                a.u[c] = (g.bcx == BC_NEUMANN && i == g.nx - 1) ? 0.0 : fmaT(-g.cgx, df_to_f64(de), qxc);
+                a.v[c] = (g.bcy == BC_NEUMANN && j == g.ny - 1) ? 0.0 : fmaT(-g.cgy, df_to_f64(dn), qyc);
+                a.w[c] = (k < g.nz - 1 || g.perz) ? fmaT(-g.cgz[k], df_to_f64(dt), qzc) : 0.0;
             }
             sd[(buf * FLUX_BY + ty) * FLUX_BX + tx] = dn;
         }
         float2 dw = make_float2(__shfl_up_sync(0xffffffffu, de.x, 1), __shfl_up_sync(0xffffffffu, de.y, 1));
         __syncthreads();
         if (on) {
-            if (tx == 0) dw = hasW ? two_sum(pc, -pf(c + oW)) : make_float2(0.f, 0.f);
+            if (tx == 0) dw = hasW ? pc.minus(pv(c + oW)) : make_float2(0.f, 0.f);
             const float2 ds = (ty > 0) ? sd[(buf * FLUX_BY + ty - 1) * FLUX_BX + tx]
-                                       : (hasS ? two_sum(pc, -pf(c + oS)) : make_float2(0.f, 0.f));
+                                       : (hasS ? pc.minus(pv(c + oS)) : make_float2(0.f, 0.f));
             float2 res = f64_split(fc);
             res = df_add(res, df_mul(df_add(de, df_neg(dw)), cx));
             res = df_add(res, df_mul(df_add(dn, df_neg(ds)), cy));
@@ -1472,7 +1505,6 @@ __device__ __forceinline__ void resid_body(const GridDev &g, int kc, const RArgs
     const int i = vb.x * FLUX_BX + tx, j = vb.y * FLUX_BY + ty;
     const int k0 = vb.z * kc, k1 = min(g.nz, k0 + kc);
     const bool on = i < g.nx && j < g.ny;
-    const size_t pl = (size_t)g.nx * g.ny;
     const int ef = exp_of_bits(ldp<CG>(&a.st->fmax_bits));
     const float scale32 = (float)g.sigma;
     const bool per_x = g.bcx == BC_PERIODIC, per_y = g.bcy == BC_PERIODIC;
@@ -1482,62 +1514,9 @@ __device__ __forceinline__ void resid_body(const GridDev &g, int kc, const RArgs
     const long long oW = (i > 0) ? -1 : (long long)(g.nx - 1);
     const long long oN = (j < g.ny - 1) ? (long long)g.nx : -(long long)j * g.nx;
     const long long oS = (j > 0) ? -(long long)g.nx : (long long)(g.ny - 1) * g.nx;
-    size_t c = on ? cidx(g, i, j, k0) : 0;
-    double pc = on ? ldp<CG>(a.p + c) : 0.0;
-    double db = 0.0;
-    if (on && k0 > 0) db = pc - ldp<CG>(a.p + c - pl);
-    else if (on && g.perz) db = pc - ldp<CG>(a.p + c + (size_t)(g.nz - 1) * pl);  // seam
-    unsigned long long mx = 0ull;
-    int buf = 0;
-    if constexpr (!CORR)
-        mx = resid0_df_march<CG>(g, a, k0, k1, c, on, tx, ty, hasE, hasW, hasN, hasS, oE, oW, oN, oS, ef,
-                                 scale32, sdn);
-    else
-    for (int k = k0; k < k1; ++k) {
-        double de = 0.0, dn = 0.0, dt = 0.0, pt = 0.0, fc = 0.0;
-        if (on) {
-            // every load of the cell first: a store below could alias a later
-            // load, which would then wait for it
-            double qxc = 0.0, qyc = 0.0, qzc = 0.0;
-            if (CORR) {
-                qxc = ldp<CG>(a.qx + c);
-                qyc = ldp<CG>(a.qy + c);
-                qzc = ldp<CG>(a.qz + c);
-            }
-            fc = ldp<CG>(a.f + c);
-            if (hasE) de = ldp<CG>(a.p + c + oE) - pc;
-            if (hasN) dn = ldp<CG>(a.p + c + oN) - pc;
-            if (k < g.nz - 1) {
-                pt = ldp<CG>(a.p + c + pl);
-                dt = pt - pc;
-            } else if (g.perz) {
-                dt = ldp<CG>(a.p + c - (size_t)k * pl) - pc;  // seam to plane 0
-            }
-            if (CORR) {
-                a.u[c] = (g.bcx == BC_NEUMANN && i == g.nx - 1) ? 0.0 : fmaT(-g.cgx, de, qxc);
-                a.v[c] = (g.bcy == BC_NEUMANN && j == g.ny - 1) ? 0.0 : fmaT(-g.cgy, dn, qyc);
-                a.w[c] = (k < g.nz - 1 || g.perz) ? fmaT(-g.cgz[k], dt, qzc) : 0.0;
-            }
-            sdn[(buf * FLUX_BY + ty) * FLUX_BX + tx] = dn;
-        }
-        double dw = __shfl_up_sync(0xffffffffu, de, 1);
-        __syncthreads();
-        if (on) {
-            if (tx == 0) dw = hasW ? pc - ldp<CG>(a.p + c + oW) : 0.0;
-            const double ds = (ty > 0) ? sdn[(buf * FLUX_BY + ty - 1) * FLUX_BX + tx]
-                                       : (hasS ? pc - ldp<CG>(a.p + c + oS) : 0.0);
-            double res = fmaT(-g.idx2, de - dw, fc);
-            res = fmaT(-g.idy2, dn - ds, res);
-            res = fmaT(-g.lzc[k], dt, res);
-            res = fmaT(g.lza[k], db, res);
-            mx = umax64(mx, absbits(res));
-            a.r32[c] = f64_to_f32_shift(res, ef) * scale32;
-        }
-        db = dt;
-        pc = pt;
-        c += pl;
-        buf ^= 1;
-    }
+    const size_t c = on ? cidx(g, i, j, k0) : 0;
+    const unsigned long long mx = resid_df_march<CG, CORR>(g, a, k0, k1, c, on, i, j, tx, ty, hasE, hasW, hasN,
+                                                           hasS, oE, oW, oN, oS, ef, scale32, sdn);
     block_max_atomic(mx, &a.st->rmax_bits[a.slot]);
     __shared__ int last;
     __syncthreads();
