@@ -90,8 +90,9 @@ def measured_traffic(workload, precision, kernel):
 
 
 def algorithmic_per_point(nx, ny, mixed):
-    """Algorithmic HBM bytes and FP64 flops (FMA = 2) per grid point of each
-    kernel of one projection.  Transform passes use the conventional real-FFT
+    """Algorithmic HBM bytes and flops (FMA = 2) per grid point of each
+    kernel of one projection (the stencil's flops for the mixed residuals,
+    which evaluate it in double-float on the FP32 pipe).  Transform passes use the conventional real-FFT
     count 2.5 log2(n) flops per point (FP64 passes only).  The split-term flux
     counts 32: per face t, s', the Newton quotient (2 FMA), dphat and the
     final FMA (10 flops), times 3, plus phat = 2p^n - p^(n-1)."""
@@ -128,14 +129,16 @@ def fft_fp64_instr_per_point(n, dct):
 def fp64_instr_per_point(nx, ny, bcx, bcy, mixed, bcz=1):
     """FP64 instructions per grid point of each kernel, counted from the code
     (flux 6 per face + phat; divergence 6; z-solve 3, or 5 with periodic z
-    (the Sherman-Morrison dot product and correction); correction 6; mixed
-    residual 10, fused with the correction 13)."""
+    (the Sherman-Morrison dot product and correction); correction 6; the
+    mixed residuals run in double-float on the FP32 pipe: none for the first,
+    and for the one fused with the correction 2 per face (the difference
+    rounded to FP64, the multiply-add))."""
     fx = fft_fp64_instr_per_point(nx, bcx == 1)
     fy = fft_fp64_instr_per_point(ny, bcy == 1)
     if not mixed:
         return {"flux": 19, "div_fwdx": 6 + fx, "fwd_y": fy, "thomas": 5 if bcz == 0 else 3, "inv_y": fy,
                 "inv_x": fx, "correct": 6}
-    return {"flux": 19, "div_fwdx": 6, "resid": 10, "resid_correct": 13, "inv_x_update": 1,
+    return {"flux": 19, "div_fwdx": 6, "resid": 0, "resid_correct": 6, "inv_x_update": 1,
             "correct": 6}
 
 

@@ -42,8 +42,8 @@ def test_mixed_path_counts_each_sweep():
     assert two["bytes_per_pt"] - one["bytes_per_pt"] == sweep
     # with no sweep the stand-alone correction runs instead of the fused one
     assert one["bytes_per_pt"] - none["bytes_per_pt"] == sweep - per["correct"][0]
-    assert one["fp64_instr_per_pt"] == 19 + 6 + 10 + 1 + 13
-    assert none["fp64_instr_per_pt"] == 19 + 6 + 10 + 6
+    assert one["fp64_instr_per_pt"] == 19 + 6 + 0 + 1 + 6
+    assert none["fp64_instr_per_pt"] == 19 + 6 + 0 + 6
     assert one["io_floor_bytes_per_pt"] == 80
 
 
