@@ -889,6 +889,7 @@ int fizzy_proj_plan(fizzy_proj_plan_t *out, const fizzy_proj_desc *d, void *stre
     g.sing = (d->bc_x <= FIZZY_BC_NEUMANN && d->bc_y <= FIZZY_BC_NEUMANN) ? 1 : 0;
     g.rny = (unsigned)((1ull << 32) / (unsigned)ny + 1);
     physics_consts(g, d->rho_l, d->rho_g, d->dt, d->dx, d->dy, sig);
+    g.flux_df = p->mixed;
     g.idx2 = 1.0 / (d->dx * d->dx);
     g.idy2 = 1.0 / (d->dy * d->dy);
     g.idx1 = 1.0 / d->dx;

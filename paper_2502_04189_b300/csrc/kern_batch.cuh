@@ -117,9 +117,9 @@ __device__ __forceinline__ void run_kind(const BatchInst &I, int pass, int tile,
         const VB vb{tile % I.fgx, (tile / I.fgx) % I.fgy, tile / (I.fgx * I.fgy)};
         double *slot = I.usq_part ? I.usq_part + tile : nullptr;
         if (KIND == BK_FLUX_G || (KIND == BK_FLUX && I.rho0_is_g))
-            flux_body<true>(g, I.kc, vb, I.phi, I.pn, I.pnm1, I.u, I.v, I.w, I.qx, I.qy, I.qz, slot);
+            flux_any<true>(g, I.kc, vb, I.phi, I.pn, I.pnm1, I.u, I.v, I.w, I.qx, I.qy, I.qz, slot);
         else
-            flux_body<false>(g, I.kc, vb, I.phi, I.pn, I.pnm1, I.u, I.v, I.w, I.qx, I.qy, I.qz, slot);
+            flux_any<false>(g, I.kc, vb, I.phi, I.pn, I.pnm1, I.u, I.v, I.w, I.qx, I.qy, I.qz, slot);
     } else if constexpr (KIND == BK_SUM) {
         sum_partials_body<CG>(I.usq_part, I.n_usq_part, I.usq_sum);
     } else if constexpr (KIND == BK_XFWD64 || KIND == BK_XFWD_MIX || KIND == BK_XLOAD) {

@@ -200,6 +200,46 @@ __device__ __forceinline__ F3 f64_split3(double x) {
     return r;
 }
 
+// x 2^-es as hi + lo floats, integer operations only (f64_split with the
+// binary exponent shifted by -es): hi is x 2^-es truncated to 24 bits, lo the
+// remaining 29 mantissa bits rounded to 24, |x 2^-es - hi - lo| <= 2^-47 |x 2^-es|
+// while x 2^-es lies in [2^-74, 2^128).  x = 0 gives 0 only for es >= -896
+// (below, the zero exponent field would read as a normal number after the
+// shift), so callers shifting by the exponent of a small x pass non-zero x.
+__device__ __forceinline__ float2 f64_split_sh(double x, int es) {
+    const float hi = f64_to_f32_shift(x, es);
+    const unsigned h = (unsigned)__double2hiint(x), l = (unsigned)__double2loint(x);
+    const int sb = (int)((h >> 20) & 0x7ff) - es - 1075 + 127;
+    float lo = 0.f;
+    if (sb > 0) lo = __fmul_rn(__uint2float_rn(l & 0x1fffffffu), __int_as_float(sb << 23));
+    return make_float2(hi, (h & 0x80000000u) ? -lo : lo);
+}
+
+// a / b in double-float (b.x a positive normal float): the FP32 reciprocal y
+// of b.x (rcp.approx, then one Newton step), the quotient q1 = a.x y, its
+// remainder a - b q1 (a.x - b.x q1 is exact by Sterbenz, the rounding error
+// of b.x q1 comes from an FMA) and the correction q2 = remainder * y:
+// relative error about 2^-45.  a = 0 gives exactly 0.
+__device__ __forceinline__ float2 df_div(float2 a, float2 b) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(b.x));
+    y = __fmaf_rn(__fmaf_rn(-b.x, y, 1.f), y, y);
+    const float q1 = __fmul_rn(a.x, y);
+    const float p = __fmul_rn(b.x, q1);
+    float e = __fmaf_rn(b.x, q1, -p);
+    e = __fmaf_rn(b.y, q1, e);
+    const float r = __fadd_rn(__fsub_rn(__fsub_rn(a.x, p), e), a.y);
+    return fast_two_sum(q1, __fmul_rn(r, y));
+}
+
+// b - a of two doubles held as exact float triples, in double-float: the
+// three float differences are exact (two-sum), their sum is rounded once per
+// double-float addition (relative error about 2^-47 of the difference).
+__device__ __forceinline__ float2 f3_diff(const F3 &b, const F3 &a) {
+    const float2 d = df_add(two_sum(b.h, -a.h), two_sum(b.m, -a.m));
+    return df_add(d, make_float2(__fsub_rn(b.l, a.l), 0.f));
+}
+
 // Asynchronous global -> shared copies (cp.async, LDGSTS): the copy runs in
 // the background and the issuing thread waits for its own groups.
 template <int BYTES>

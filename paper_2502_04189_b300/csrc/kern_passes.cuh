@@ -77,6 +77,7 @@ struct GridDev {
     double inv_3n;        // 1/(3 nx ny nz)
     double div_tol;       // < 0: divergence criterion off
     const double *usq;    // sum of u*^2 over all faces (device scalar)
+    int flux_df;          // 1: the face flux's split term in double-float (mixed plans)
 };
 
 // Mixed-mode stopping rule, evaluated by one thread once max|r| is known:
@@ -264,6 +265,161 @@ __device__ __forceinline__ void flux_body(const GridDev &g, int kc, VB vb, const
     }
 }
 
+// Mixed plans: the same face flux with its split term in double-float on the
+// FP32 pipe.  FP64 issues at 2 instructions per clock per SM against 128 for
+// FP32, and the FP64 body above spends 19 FP64 instructions per cell; here
+// phat = 2 p^n - p^(n-1) keeps its one FP64 FMA per cell (the same value the
+// FP64 body forms) and each face keeps two FP64 additions, q' = (u* + x_hi) +
+// x_lo, for the split term x = kappa (phat_b - phat_a):
+//   * psi (= phi, or 1 - phi when rho0 = rho_l) as a float pair, 2^-47 |phi|;
+//   * t = psi_a + psi_b, s' = a' t + r' and kappa = t / s' in double-float,
+//     with a' and r' scaled by 2^-sh (the seed shift of the FP64 body), which
+//     keeps s' near [2^-fsh, 2^(2+fsh)] and kappa within float range for
+//     every density ratio the plan accepts; x is scaled back by 2^sh when it
+//     is moved to FP64 (integer operations, exact);
+//   * phat_b - phat_a from phat held as the exact sum of three floats
+//     (f64_split3): exact float differences, then double-float sums;
+//   * relative error of x about 2^-44; the pure rho0 phase (psi = 0 on both
+//     sides) gives kappa = 0 and q' = u* exactly, as in the FP64 body.
+// The divergence identity D(u) = (dt/rho0)(f - L_h p) does not depend on
+// this precision: the right-hand side and the correction read the same
+// stored q'.  Range: |phat| below 2^100 (float range after the products).
+__device__ __forceinline__ double face_flux_df(float2 psi_a, float2 psi_b, const F3 &ph_a, const F3 &ph_b,
+                                               double ustar, float2 A, float2 R, int sh) {
+    const float2 t = df_add(psi_a, psi_b);
+    const float2 sp = df_add(df_mul(t, A), R);
+    const float2 x = df_mul(df_div(t, sp), f3_diff(ph_b, ph_a));
+    return __dadd_rn(__dadd_rn(ustar, f32_to_f64_shift(x.x, -sh)), f32_to_f64_shift(x.y, -sh));
+}
+
+// The double-float flux tile: the tile, march, halo and face order of
+// flux_body; phat (as three floats) and psi (as a float pair) of each plane
+// sit in shared memory, and one thread splits the z-face constants a', r' of
+// the plane for the others.
+template <bool RHO0_IS_G>
+__device__ __forceinline__ void flux_body_df(const GridDev &g, int kc, VB vb, const double *phi,
+                                             const double *pn, const double *pnm1, const double *u,
+                                             const double *v, const double *w, double *qx, double *qy,
+                                             double *qz, double *usq_slot) {
+    __shared__ float s_ph[3][FLUX_BY + 1][FLUX_BX + 1];
+    __shared__ float2 s_psi[FLUX_BY + 1][FLUX_BX + 1];
+    __shared__ float2 s_zc[2];
+    __shared__ int s_zsh;
+    const int tid = block_tid();
+    const int tx = tid & (FLUX_BX - 1), ty = tid / FLUX_BX;
+    const int i0 = vb.x * FLUX_BX, j0 = vb.y * FLUX_BY;
+    const int i = i0 + tx, j = j0 + ty;
+    const int k0 = vb.z * kc;
+    const int k1 = min(k0 + kc, g.nz);
+    const bool in = (i < g.nx && j < g.ny);
+    const size_t plane = (size_t)g.nx * g.ny;
+    auto src_i = [&](int ii) { return ii < g.nx ? ii : (g.bcx == BC_PERIODIC ? ii % g.nx : g.nx - 1); };
+    auto src_j = [&](int jj) { return jj < g.ny ? jj : (g.bcy == BC_PERIODIC ? jj % g.ny : g.ny - 1); };
+    const size_t own = (size_t)src_j(j) * g.nx + src_i(i);
+    int hy = -1, hx = -1;
+    size_t hoff = 0;
+    if (tid < FLUX_BX) {
+        hy = FLUX_BY;
+        hx = tid;
+    } else if (tid < FLUX_BX + FLUX_BY) {
+        hy = tid - FLUX_BX;
+        hx = FLUX_BX;
+    }
+    if (hy >= 0) hoff = (size_t)src_j(j0 + hy) * g.nx + src_i(i0 + hx);
+    auto psi = [&](size_t at) {
+        const float2 f = f64_split(phi[at]);
+        return RHO0_IS_G ? f : df_add(make_float2(1.f, 0.f), df_neg(f));
+    };
+    auto phat = [&](size_t at) { return f64_split3(fmaT(2.0, pn[at], -pnm1[at])); };
+    const bool var = g.var_rho != 0;
+    const int shx = var ? seed_shift(g.frx, g.fsh) : 0, shy = var ? seed_shift(g.fry, g.fsh) : 0;
+    const float2 Ax = var ? f64_split_sh(g.fax, shx) : make_float2(0.f, 0.f);
+    const float2 Rx = var ? f64_split_sh(g.frx, shx) : make_float2(0.f, 0.f);
+    const float2 Ay = var ? f64_split_sh(g.fay, shy) : make_float2(0.f, 0.f);
+    const float2 Ry = var ? f64_split_sh(g.fry, shy) : make_float2(0.f, 0.f);
+    float2 psi_c = make_float2(0.f, 0.f);
+    F3 ph_c{0.f, 0.f, 0.f};
+    float usq = 0.f;
+    for (int k = k0; k < k1; ++k) {
+        const size_t base = (size_t)k * plane;
+        if (k == k0) {
+            psi_c = psi(base + own);
+            ph_c = phat(base + own);
+        }
+        s_ph[0][ty][tx] = ph_c.h;
+        s_ph[1][ty][tx] = ph_c.m;
+        s_ph[2][ty][tx] = ph_c.l;
+        s_psi[ty][tx] = psi_c;
+        if (hy >= 0) {
+            s_psi[hy][hx] = psi(base + hoff);
+            const F3 h3 = phat(base + hoff);
+            s_ph[0][hy][hx] = h3.h;
+            s_ph[1][hy][hx] = h3.m;
+            s_ph[2][hy][hx] = h3.l;
+        }
+        const bool top_face = k + 1 < g.nz || g.perz;  // periodic z: the seam joins plane 0
+        if (tid == FLUX_BX * FLUX_BY - 1 && var && top_face) {
+            // r' > 0 on every face that exists; the top wall's zero entry is never split
+            const double rz = g.frz[k];
+            const int sh = seed_shift(rz, g.fsh);
+            s_zc[0] = f64_split_sh(g.faz[k], sh);
+            s_zc[1] = f64_split_sh(rz, sh);
+            s_zsh = sh;
+        }
+        __syncthreads();
+        float2 psi_t = make_float2(0.f, 0.f);
+        F3 ph_t{0.f, 0.f, 0.f};
+        if (top_face) {
+            const size_t nxt = (k + 1 < g.nz) ? base + plane : 0;
+            psi_t = psi(nxt + own);
+            ph_t = phat(nxt + own);
+        }
+        if (in) {
+            const size_t c = base + (size_t)j * g.nx + i;
+            const double uc = u[c], vc = v[c], wc = w[c];
+            if (usq_slot) {
+                const float a = abs_scaled_f32(uc), b = abs_scaled_f32(vc), d = abs_scaled_f32(wc);
+                usq = fmaf(a, a, fmaf(b, b, fmaf(d, d, usq)));
+            }
+            double q = 0.0;
+            if (!(g.bcx == BC_NEUMANN && i == g.nx - 1)) {
+                const F3 pe{s_ph[0][ty][tx + 1], s_ph[1][ty][tx + 1], s_ph[2][ty][tx + 1]};
+                q = var ? face_flux_df(psi_c, s_psi[ty][tx + 1], ph_c, pe, uc, Ax, Rx, shx) : uc;
+            }
+            qx[c] = q;
+            q = 0.0;
+            if (!(g.bcy == BC_NEUMANN && j == g.ny - 1)) {
+                const F3 pnb{s_ph[0][ty + 1][tx], s_ph[1][ty + 1][tx], s_ph[2][ty + 1][tx]};
+                q = var ? face_flux_df(psi_c, s_psi[ty + 1][tx], ph_c, pnb, vc, Ay, Ry, shy) : vc;
+            }
+            qy[c] = q;
+            q = 0.0;
+            if (top_face) q = var ? face_flux_df(psi_c, psi_t, ph_c, ph_t, wc, s_zc[0], s_zc[1], s_zsh) : wc;
+            qz[c] = q;
+        }
+        ph_c = ph_t;
+        psi_c = psi_t;
+        __syncthreads();
+    }
+    if (usq_slot) {
+        const double sm = block_sum(f32_to_f64_shift(usq, 128));
+        if (tid == 0) *usq_slot = sm;
+    }
+}
+
+// The flux tile of a plan: double-float split term on mixed plans
+// (g.flux_df), FP64 otherwise.
+template <bool RHO0_IS_G>
+__device__ __forceinline__ void flux_any(const GridDev &g, int kc, VB vb, const double *phi, const double *pn,
+                                         const double *pnm1, const double *u, const double *v,
+                                         const double *w, double *qx, double *qy, double *qz,
+                                         double *usq_slot) {
+    if (g.flux_df)
+        flux_body_df<RHO0_IS_G>(g, kc, vb, phi, pn, pnm1, u, v, w, qx, qy, qz, usq_slot);
+    else
+        flux_body<RHO0_IS_G>(g, kc, vb, phi, pn, pnm1, u, v, w, qx, qy, qz, usq_slot);
+}
+
 template <bool RHO0_IS_G>
 __global__ void __launch_bounds__(256) k_flux(GridDev g, int kc, const double *__restrict__ phi,
                                               const double *__restrict__ pn,
@@ -276,7 +432,7 @@ __global__ void __launch_bounds__(256) k_flux(GridDev g, int kc, const double *_
                                               double *__restrict__ usq_part) {
     double *slot = usq_part ? usq_part + ((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x
                             : nullptr;
-    flux_body<RHO0_IS_G>(g, kc, vb_of_grid(), phi, pn, pnm1, u, v, w, qx, qy, qz, slot);
+    flux_any<RHO0_IS_G>(g, kc, vb_of_grid(), phi, pn, pnm1, u, v, w, qx, qy, qz, slot);
 }
 
 // Deterministic final sum of per-block partials (one block).
