@@ -477,6 +477,20 @@ __device__ __forceinline__ double div_q(const GridDev &g, int i, int j, int k, d
                                         const double *qz) {
     return div_q_eval(div_q_ld<CG>(g, i, j, k, qx, qy, qz), cx, cy, cz);
 }
+// The same divergence in double-float (the mixed plans' first x-pass): each
+// face value as a float pair (f64_split, 2^-47 relative), the differences,
+// their products with the split constants and the sum in double-float on the
+// FP32 pipe, f moved to FP64 with one addition.  Error about 2^-46 max|q'| c,
+// the size of the double-float flux's own rounding of q'; the divergence the
+// correction leaves sees it as (dt/rho0)|df| dx/U, about 2^-46 max|q'|/U.
+// q' = 0 on all six faces gives f = 0 exactly.
+__device__ __forceinline__ double div_q_eval_df(const QFaces &q, float2 cx, float2 cy, float2 cz) {
+    const float2 ex = df_add(f64_split(q.qe), df_neg(f64_split(q.qw)));
+    const float2 ey = df_add(f64_split(q.qn), df_neg(f64_split(q.qs)));
+    const float2 ez = df_add(f64_split(q.qt), df_neg(f64_split(q.qb)));
+    const float2 f = df_add(df_add(df_mul(ex, cx), df_mul(ey, cy)), df_mul(ez, cz));
+    return __dadd_rn(f32_to_f64_shift(f.x, 0), f32_to_f64_shift(f.y, 0));
+}
 
 // L_h p at one cell in flux (difference) form: each face difference is
 // formed first, so a smooth p loses no accuracy to cancellation.  Wall faces
@@ -505,7 +519,7 @@ __device__ __forceinline__ double lap(const GridDev &g, int i, int j, int k, con
 
 enum {
     XF_F64_DIVQ = 0,   // FP64 mode: sigma rho0 D(q), FP64 transform
-    XF_MIX_DIVQ = 1,   // mixed: f = rho0 D(q) stored (FP64), FP32 transform of sigma f
+    XF_MIX_DIVQ = 1,   // mixed: f = rho0 D(q) (double-float) stored in FP64, FP32 transform of sigma f
     XF_MIX_LOAD = 2    // transform, in place, of a stored right-hand side: mixed mode's FP32
                        // sigma 2^-e r; with T = double the preconditioner of the
                        // variable-coefficient solve (sigma r)
@@ -697,7 +711,8 @@ __device__ __forceinline__ void xfwd_body(const GridDev &g, const FFTDesc &D, in
                         if (a.track_fmax) mx = umax64(mx, absbits(f));
                         val = (T)f;
                     } else {
-                        const double f = div_q_eval(qf[u], g.dvx, g.dvy, g.dvz[k]);
+                        const double f = div_q_eval_df(qf[u], f64_split(g.dvx), f64_split(g.dvy),
+                                                       f64_split(g.dvz[k]));
                         a.f_out[(size_t)line * n + i] = f;
                         mx = umax64(mx, absbits(f));
                         val = (T)(f64_to_f32_shift(f, 0) * scale32);

@@ -671,8 +671,9 @@ __global__ void __launch_bounds__(RShape<N>::THREADS, RShape<N>::MINB)
 }
 
 // The first x-pass of the mixed solve (the mode XF_MIX_DIVQ of k_xfwd):
-// f = rho0 D(q') in FP64 (stored, and max|f| recorded), then the forward
-// transform of its FP32 image sigma f.  f is formed into the line regions
+// f = rho0 D(q') in double-float (div_q_eval_df; stored in FP64, and max|f|
+// recorded), then the forward transform of its FP32 image sigma f.  f is
+// formed into the line regions
 // row by row for rows of N >= 256 cells (lane = x mod 32, the row's
 // constants once), else slot by slot (coalesced either way).
 template <int N, int KIND>
@@ -688,6 +689,7 @@ __global__ void __launch_bounds__(RShape<N>::THREADS, RShape<N>::MINB)
     const int nlines = g.ny * g.nz, l0 = r_warp_line<N>();
     constexpr int LS = RShape<N>::LS;
     const float scale32 = (float)g.sigma;
+    const float2 cx = f64_split(g.dvx), cy = f64_split(g.dvy);
     float *out = (float *)a.out;
     float *sf = (float *)sm.x;
     float2 *X = sm.x + q.ln * LS;
@@ -702,7 +704,7 @@ __global__ void __launch_bounds__(RShape<N>::THREADS, RShape<N>::MINB)
                 float *dr = sf + r_slot_f<N>(r, 0);
                 if (row < nlines) {
                     const int k = fdiv(row, g.ny, g.rny), j = row - k * g.ny;
-                    const double cz = g.dvz[k];
+                    const float2 cz = f64_split(g.dvz[k]);
                     // the face loads of two cells ahead of their arithmetic
                     // and stores (a store to f could alias a later load)
                     constexpr int U = 2;
@@ -714,7 +716,7 @@ __global__ void __launch_bounds__(RShape<N>::THREADS, RShape<N>::MINB)
 #pragma unroll
                         for (int u = 0; u < U; ++u) {
                             const int x = lane + 32 * (i0 + u);
-                            const double f = div_q_eval(qf[u], g.dvx, g.dvy, cz);
+                            const double f = div_q_eval_df(qf[u], cx, cy, cz);
                             a.f_out[(size_t)row * N + x] = f;
                             mx = umax64(mx, absbits(f));
                             dr[2 * x] = f64_to_f32_shift(f, 0) * scale32;
@@ -731,7 +733,8 @@ __global__ void __launch_bounds__(RShape<N>::THREADS, RShape<N>::MINB)
                 float val = 0.f;
                 if (row < nlines) {
                     const int k = fdiv(row, g.ny, g.rny), j = row - k * g.ny;
-                    const double f = div_q<false>(g, x, j, k, g.dvx, g.dvy, g.dvz[k], a.qx, a.qy, a.qz);
+                    const double f = div_q_eval_df(div_q_ld<false>(g, x, j, k, a.qx, a.qy, a.qz), cx, cy,
+                                                   f64_split(g.dvz[k]));
                     a.f_out[(size_t)row * N + x] = f;
                     mx = umax64(mx, absbits(f));
                     val = f64_to_f32_shift(f, 0) * scale32;

@@ -93,7 +93,7 @@ __global__ void __cluster_dims__(XY_CL, 1, 1) __launch_bounds__(XYShape<N>::THRE
         } else {
             // f row by row into the line's region (x = lane + 32 i, component = row)
             const float scale32 = (float)g.sigma;
-            const double cz = g.dvz[z];
+            const float2 cx = f64_split(g.dvx), cy = f64_split(g.dvy), cz = f64_split(g.dvz[z]);
             // the warp's rows: lines ln0 .. ln0 + LPW - 1, as interleaved
             // (row 2l, row 2l + 1) pairs in their line regions
             constexpr int LPW = RShape<N>::LPW;
@@ -106,7 +106,7 @@ __global__ void __cluster_dims__(XY_CL, 1, 1) __launch_bounds__(XYShape<N>::THRE
 #pragma unroll 4
                 for (int i = 0; i < N / 32; ++i) {
                     const int x = lane + 32 * i;
-                    const double f = div_q<false>(g, x, y, z, g.dvx, g.dvy, cz, a.qx, a.qy, a.qz);
+                    const double f = div_q_eval_df(div_q_ld<false>(g, x, y, z, a.qx, a.qy, a.qz), cx, cy, cz);
                     a.f_out[((size_t)z * N + y) * N + x] = f;
                     mx = umax64(mx, absbits(f));
                     dr[2 * x] = f64_to_f32_shift(f, 0) * scale32;
