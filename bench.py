@@ -129,16 +129,18 @@ def fft_fp64_instr_per_point(n, dct):
 def fp64_instr_per_point(nx, ny, bcx, bcy, mixed, bcz=1):
     """FP64 instructions per grid point of each kernel, counted from the code
     (flux 6 per face + phat; divergence 6; z-solve 3, or 5 with periodic z
-    (the Sherman-Morrison dot product and correction); correction 6; the
-    mixed residuals run in double-float on the FP32 pipe: none for the first,
-    and for the one fused with the correction 2 per face (the difference
-    rounded to FP64, the multiply-add))."""
+    (the Sherman-Morrison dot product and correction); correction 6).  Mixed
+    plans run the flux's split term, the first x-pass's divergence and the
+    residuals in double-float on the FP32 pipe: the flux keeps phat (1 per
+    cell) and 2 additions per face (q' = (u* + x_hi) + x_lo), the divergence
+    1 (f moved to FP64), the first residual none, and the one fused with the
+    correction 2 per face (the difference rounded to FP64, the multiply-add)."""
     fx = fft_fp64_instr_per_point(nx, bcx == 1)
     fy = fft_fp64_instr_per_point(ny, bcy == 1)
     if not mixed:
         return {"flux": 19, "div_fwdx": 6 + fx, "fwd_y": fy, "thomas": 5 if bcz == 0 else 3, "inv_y": fy,
                 "inv_x": fx, "correct": 6}
-    return {"flux": 19, "div_fwdx": 6, "resid": 0, "resid_correct": 6, "inv_x_update": 1,
+    return {"flux": 7, "div_fwdx": 1, "resid": 0, "resid_correct": 6, "inv_x_update": 1,
             "correct": 6}
 
 
@@ -367,7 +369,9 @@ def dominant_roofline(dom, live, st, steps, mixed, max_refine, spec, npts, hbm_p
     (FMA = 2) per launch over the launch time, against twice the DFMA issue
     rate measured in the same run; the FP64 instruction rate against that
     issue rate and the HBM rate against the measured copy bandwidth sit
-    beside it."""
+    beside it.  The mixed plans' double-float kernels (flux, first x-pass,
+    residuals) do most of their arithmetic on the FP32 pipe, so they report
+    against HBM, with their remaining FP64 instructions beside it."""
     tot_ms, cnt = live
     # refinement kernels return at once after convergence: count only the
     # launches that did the pass (from the solve's sweep count)
@@ -386,7 +390,8 @@ def dominant_roofline(dom, live, st, steps, mixed, max_refine, spec, npts, hbm_p
     tpt, tsrc = measured_traffic(workload, "mixed" if mixed else "fp64", dom)
     traffic = tpt * npts if tpt is not None else None
     issue = ipt * npts / avg_s
-    if ipt and ipt / dfma > b_pt / (hbm_peak * 1e9):
+    df_kernel = mixed and dom in ("flux", "div_fwdx", "resid", "resid_correct")
+    if ipt and not df_kernel and ipt / dfma > b_pt / (hbm_peak * 1e9):
         peak = 2.0 * dfma / 1e12
         tfl = fl_pt * npts / avg_s / 1e12
         roof = {"bound": "alu", "achieved": tfl, "peak": peak, "unit": "TFLOP/s", "frac": tfl / peak,
@@ -541,8 +546,12 @@ def run_serve_classes(args, F, torch, slots, n_small=1500, n_large=300):
     """Service capacity by request size: the request recipe's small
     (<= 128^3 points) and large requests served as two separate backlogs
     (every request queued at t = 0, no deadline), so the server stays busy
-    and points / wall time is the class's throughput.  The ratio small/large
-    says how well small requests use the GPU."""
+    and points / wall time is the class's throughput.  Each backlog is served
+    once untimed first, so the timed pass finds every plan of the class in
+    the server's device-resident cache (the steady state of a server whose
+    request grids recur; the Poisson run above builds plans as grids first
+    arrive).  The ratio small/large says how well small requests use the
+    GPU."""
     import paper_2502_04189_b300.serve as S
     arrivals, specs = I.serve_specs(8 * (n_small + n_large))
     small = [s for s in specs if s.nx * s.ny * s.nz <= SMALL_PTS][:n_small]
@@ -557,7 +566,7 @@ def run_serve_classes(args, F, torch, slots, n_small=1500, n_large=300):
     out = {"split_pts": SMALL_PTS, "slots": slots}
     for name, cls in (("small", small), ("large", large)):
         reqs = S.requests_from_specs([0.0] * len(cls), cls, F.MIXED)
-        S.run(server, reqs[:4], fill, deadline=60.0)  # plans and pool warm
+        S.run(server, reqs, fill, deadline=60.0)  # every plan of the class cached, pool warm
         torch.cuda.synchronize()
         _, summ = S.run(server, reqs, fill, deadline=60.0)
         out[name] = {"requests": summ["requests"], "mean_pts": summ["points_done"] / max(1, summ["admitted"]),

@@ -1199,12 +1199,12 @@ static int solve_launch(fizzy_proj_plan_t p, const double *phi, const double *p_
     const dim3 fgrd = flux_grid(nx, ny, nz), fblk(FLUX_BX, FLUX_BY);
     if (!head) {
         // continuation: only the sweeps below
-    } else if (p->desc.rho_g <= p->desc.rho_l)
-        TIMED(KS_FLUX, (k_flux<true><<<fgrd, fblk, 0, s>>>(g, kFluxKc, phi, p_n, p_nm1, u, v, w, p->qx,
-                                                           p->qy, p->qz, need_usq ? p->usq_part : nullptr)));
-    else
-        TIMED(KS_FLUX, (k_flux<false><<<fgrd, fblk, 0, s>>>(g, kFluxKc, phi, p_n, p_nm1, u, v, w, p->qx,
-                                                            p->qy, p->qz, need_usq ? p->usq_part : nullptr)));
+    } else {
+        const bool g0 = p->desc.rho_g <= p->desc.rho_l;
+        auto kf = g.flux_df ? (g0 ? k_flux_df<true> : k_flux_df<false>) : (g0 ? k_flux<true> : k_flux<false>);
+        TIMED(KS_FLUX, (kf<<<fgrd, fblk, 0, s>>>(g, kFluxKc, phi, p_n, p_nm1, u, v, w, p->qx, p->qy, p->qz,
+                                                 need_usq ? p->usq_part : nullptr)));
+    }
     if (head && need_usq)
         TIMED(KS_SUM, (k_sum_partials<<<1, 1024, 0, s>>>(p->usq_part, p->n_usq_part, p->usq_sum)));
     if (!p->mixed) {

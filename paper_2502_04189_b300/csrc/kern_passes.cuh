@@ -432,7 +432,24 @@ __global__ void __launch_bounds__(256) k_flux(GridDev g, int kc, const double *_
                                               double *__restrict__ usq_part) {
     double *slot = usq_part ? usq_part + ((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x
                             : nullptr;
-    flux_any<RHO0_IS_G>(g, kc, vb_of_grid(), phi, pn, pnm1, u, v, w, qx, qy, qz, slot);
+    flux_body<RHO0_IS_G>(g, kc, vb_of_grid(), phi, pn, pnm1, u, v, w, qx, qy, qz, slot);
+}
+
+// The double-float body (mixed plans, g.flux_df = 1) as a kernel of its own,
+// held to five CTAs per SM (40 warps: its loads wait on latency).
+template <bool RHO0_IS_G>
+__global__ void __launch_bounds__(256, 5) k_flux_df(GridDev g, int kc, const double *__restrict__ phi,
+                                                    const double *__restrict__ pn,
+                                                    const double *__restrict__ pnm1,
+                                                    const double *__restrict__ u,
+                                                    const double *__restrict__ v,
+                                                    const double *__restrict__ w,
+                                                    double *__restrict__ qx, double *__restrict__ qy,
+                                                    double *__restrict__ qz,
+                                                    double *__restrict__ usq_part) {
+    double *slot = usq_part ? usq_part + ((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x
+                            : nullptr;
+    flux_body_df<RHO0_IS_G>(g, kc, vb_of_grid(), phi, pn, pnm1, u, v, w, qx, qy, qz, slot);
 }
 
 // Deterministic final sum of per-block partials (one block).

@@ -42,14 +42,15 @@ def test_mixed_path_counts_each_sweep():
     assert two["bytes_per_pt"] - one["bytes_per_pt"] == sweep
     # with no sweep the stand-alone correction runs instead of the fused one
     assert one["bytes_per_pt"] - none["bytes_per_pt"] == sweep - per["correct"][0]
-    assert one["fp64_instr_per_pt"] == 19 + 6 + 0 + 1 + 6
-    assert none["fp64_instr_per_pt"] == 19 + 6 + 0 + 6
+    # mixed: double-float flux (7), divergence (1) and first residual (0)
+    assert one["fp64_instr_per_pt"] == 7 + 1 + 0 + 1 + 6
+    assert none["fp64_instr_per_pt"] == 7 + 1 + 0 + 6
     assert one["io_floor_bytes_per_pt"] == 80
 
 
 def test_dominant_roofline_against_measured_dfma_rate():
     """The dominant kernel's roofline divides by the DFMA issue rate measured
-    in the run: an FP64-bound flux launch is "alu", its flop fraction is the
+    in the run: an FP64-mode flux launch is "alu", its flop fraction is the
     algorithmic flops over twice that rate, and its issue fraction the
     counted FP64 instructions over the rate itself."""
     from paper_2502_04189_b300 import inputs as I
@@ -58,7 +59,7 @@ def test_dominant_roofline_against_measured_dfma_rate():
     dfma = 0.6e12
     t_ms = 0.6  # per launch
     st = {"iterations": 1}
-    r = bench.dominant_roofline("flux", (t_ms * 20, 20), st, 20, True, 4, spec, n, 6504.1, "m", dfma,
+    r = bench.dominant_roofline("flux", (t_ms * 20, 20), st, 20, False, 4, spec, n, 6504.1, "m", dfma,
                                 "no-such-workload")
     assert r["bound"] == "alu" and r["kernel"] == "flux"
     assert r["achieved"] == pytest.approx(32 * n / (t_ms * 1e-3) / 1e12)
@@ -66,6 +67,12 @@ def test_dominant_roofline_against_measured_dfma_rate():
     assert r["fp64_issue"]["frac"] == pytest.approx(19 * n / (t_ms * 1e-3) / dfma)
     assert r["hbm_gbs"] == pytest.approx(72 * n / (t_ms * 1e-3) / 1e9)
     assert r["traffic"] is None
+    # the mixed plans' double-float flux reports against HBM, its 7 FP64
+    # instructions per point beside it
+    r = bench.dominant_roofline("flux", (t_ms * 20, 20), st, 20, True, 4, spec, n, 6504.1, "m", dfma,
+                                "no-such-workload")
+    assert r["bound"] == "hbm" and r["frac"] == pytest.approx(72 * n / (t_ms * 1e-3) / 1e9 / 6504.1)
+    assert r["fp64_issue"]["frac"] == pytest.approx(7 * n / (t_ms * 1e-3) / dfma)
     # a refinement kernel counts only the launches of sweeps that ran
     r2 = bench.dominant_roofline("thomas_refine", (1.0, 80), st, 20, True, 4, spec, n, 6504.1, "m",
                                  dfma, "no-such-workload")
