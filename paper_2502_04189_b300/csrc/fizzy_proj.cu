@@ -697,7 +697,7 @@ void pass_caps(int *cap, const PassKernels &k, size_t sx64, size_t sx32, size_t 
     cap[CAP_TH64C] = resident_grid(k_thomas_cyc<double>, THOMAS_BLOCK, thomas_cyc_smem<double>());
     cap[CAP_TH32C] = resident_grid(k_thomas_cyc<float>, THOMAS_BLOCK, thomas_cyc_smem<float>());
     cap[CAP_RM] = resident_grid(k_residmax, 256, 0);
-    cap[CAP_RC] = resident_grid(k_resid<true>, 256, 0);
+    cap[CAP_RC] = resident_grid(k_resid_corr<true>, 256, 0);
     cap[CAP_CIF] = resident_grid(k_correct_if, 256, 0);
 }
 
@@ -1294,7 +1294,7 @@ static int solve_launch(fizzy_proj_plan_t p, const double *phi, const double *p_
                 TIMED(KS_XACC, (p->kern.xi32a<<<gs(xrt, CAP_XI32A), p->xthr32, smx32r, s>>>(g, p->fx.d32, p->Lx, p->fhat32, p_np1, p->st, xrt)));
             }
             ra.slot = sw;
-            TIMED(KS_RCORR, (k_resid<true><<<gs(rctiles, CAP_RC), rcb, 0, s>>>(g, RESID_KC, ra, rtgx, rtgy, rctiles)));
+            TIMED(KS_RCORR, (k_resid_corr<true><<<gs(rctiles, CAP_RC), rcb, 0, s>>>(g, RESID_KC, ra, rtgx, rtgy, rctiles)));
         }
         // the correction, unless a fused residual pass has written u (a
         // continuation follows at least one fused pass: nothing to do)

@@ -1633,41 +1633,63 @@ __device__ __forceinline__ unsigned long long resid_df_march(
     float2 db = make_float2(0.f, 0.f);
     if (on && k0 > 0) db = pc.minus(pv(c - pl));
     else if (on && g.perz) db = pc.minus(pv(c + (size_t)(g.nz - 1) * pl));  // seam
+    // f and the east, north and top p of a plane (and the west / south p on
+    // the tile's first column / row), loaded one plane ahead of the
+    // arithmetic (raw FP64 values, split when used)
+    struct Ahead {
+        double f, pe, pn, pt, pw, ps;
+    };
+    auto load_ahead = [&](size_t cc, int kk) {
+        Ahead r{0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+        r.f = ldp<CG>(a.f + cc);
+        if (hasE) r.pe = ldp<CG>(a.p + cc + oE);
+        if (hasN) r.pn = ldp<CG>(a.p + cc + oN);
+        if (tx == 0 && hasW) r.pw = ldp<CG>(a.p + cc + oW);
+        if (ty == 0 && hasS) r.ps = ldp<CG>(a.p + cc + oS);
+        if (kk < g.nz - 1) r.pt = ldp<CG>(a.p + cc + pl);
+        else if (g.perz) r.pt = ldp<CG>(a.p + cc - (size_t)kk * pl);  // seam to plane 0
+        return r;
+    };
+    Ahead cur{0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    if (on) cur = load_ahead(c, k0);
     unsigned long long mx = 0ull;
     int buf = 0;
     for (int k = k0; k < k1; ++k) {
+        Ahead nxt{0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+        if (on && k + 1 < k1) nxt = load_ahead(c + pl, k + 1);
         float2 de = make_float2(0.f, 0.f), dn = de, dt = de;
         PV pt = PV::zero();
-        double fc = 0.0, qxc = 0.0, qyc = 0.0, qzc = 0.0;
+        double qxc = 0.0, qyc = 0.0, qzc = 0.0;
         if (on) {
-            if (CORR) {  // every load before the stores below (which could alias them)
+            if (CORR) {
                 qxc = ldp<CG>(a.qx + c);
                 qyc = ldp<CG>(a.qy + c);
                 qzc = ldp<CG>(a.qz + c);
             }
-            fc = ldp<CG>(a.f + c);
-            if (hasE) de = pv(c + oE).minus(pc);
-            if (hasN) dn = pv(c + oN).minus(pc);
+            if (hasE) de = PV::load(cur.pe).minus(pc);
+            if (hasN) dn = PV::load(cur.pn).minus(pc);
             if (k < g.nz - 1) {
-                pt = pv(c + pl);
+                pt = PV::load(cur.pt);
                 dt = pt.minus(pc);
             } else if (g.perz) {
-                dt = pv(c - (size_t)k * pl).minus(pc);  // seam to plane 0
-            }
-            if (CORR) {
-                a.u[c] = (g.bcx == BC_NEUMANN && i == g.nx - 1) ? 0.0 : fmaT(-g.cgx, df_to_f64(de), qxc);
-                a.v[c] = (g.bcy == BC_NEUMANN && j == g.ny - 1) ? 0.0 : fmaT(-g.cgy, df_to_f64(dn), qyc);
-                a.w[c] = (k < g.nz - 1 || g.perz) ? fmaT(-g.cgz[k], df_to_f64(dt), qzc) : 0.0;
+                dt = PV::load(cur.pt).minus(pc);
             }
             sd[(buf * FLUX_BY + ty) * FLUX_BX + tx] = dn;
         }
         float2 dw = make_float2(__shfl_up_sync(0xffffffffu, de.x, 1), __shfl_up_sync(0xffffffffu, de.y, 1));
         __syncthreads();
         if (on) {
-            if (tx == 0) dw = hasW ? pc.minus(pv(c + oW)) : make_float2(0.f, 0.f);
+            // the correction's stores come after every load of this plane
+            // and the next (they could alias the q' loads)
+            if (CORR) {
+                a.u[c] = (g.bcx == BC_NEUMANN && i == g.nx - 1) ? 0.0 : fmaT(-g.cgx, df_to_f64(de), qxc);
+                a.v[c] = (g.bcy == BC_NEUMANN && j == g.ny - 1) ? 0.0 : fmaT(-g.cgy, df_to_f64(dn), qyc);
+                a.w[c] = (k < g.nz - 1 || g.perz) ? fmaT(-g.cgz[k], df_to_f64(dt), qzc) : 0.0;
+            }
+            if (tx == 0) dw = hasW ? pc.minus(PV::load(cur.pw)) : make_float2(0.f, 0.f);
             const float2 ds = (ty > 0) ? sd[(buf * FLUX_BY + ty - 1) * FLUX_BX + tx]
-                                       : (hasS ? pc.minus(pv(c + oS)) : make_float2(0.f, 0.f));
-            float2 res = f64_split(fc);
+                                       : (hasS ? pc.minus(PV::load(cur.ps)) : make_float2(0.f, 0.f));
+            float2 res = f64_split(cur.f);
             res = df_add(res, df_mul(df_add(de, df_neg(dw)), cx));
             res = df_add(res, df_mul(df_add(dn, df_neg(ds)), cy));
             res = df_add(res, df_mul(dt, s_cz[0][k - k0]));
@@ -1678,6 +1700,7 @@ __device__ __forceinline__ unsigned long long resid_df_march(
         }
         db = dt;
         pc = pt;
+        cur = nxt;
         c += pl;
         buf ^= 1;
     }
@@ -1732,17 +1755,30 @@ __device__ __forceinline__ void resid_body(const GridDev &g, int kc, const RArgs
     }
 }
 
-// One block per tile; tiles of kc planes.
+// One block per tile; tiles of kc planes.  The fused residual-correction
+// (CORR) is held to four CTAs per SM (64 registers): its march's loads run
+// one plane ahead, which costs registers.
 template <bool CORR>
-__global__ void __launch_bounds__(256) k_resid(GridDev g, int kc, RArgs a, int tgx, int tgy,
-                                               int ntiles) {
-    __shared__ double sdn[2 * FLUX_BY * FLUX_BX];
+__device__ __forceinline__ void resid_tiles(const GridDev &g, int kc, const RArgs &a, int tgx, int tgy,
+                                            int ntiles, double *sdn) {
     if (*(volatile const int *)&a.st->converged) return;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const int txy = tgx * tgy, z = t / txy, r = t - z * txy, y = r / tgx;
         resid_body<false, CORR>(g, kc, a, VB{r - y * tgx, y, z}, ntiles, sdn);
         __syncthreads();
     }
+}
+template <bool CORR>
+__global__ void __launch_bounds__(256) k_resid(GridDev g, int kc, RArgs a, int tgx, int tgy,
+                                               int ntiles) {
+    __shared__ double sdn[2 * FLUX_BY * FLUX_BX];
+    resid_tiles<CORR>(g, kc, a, tgx, tgy, ntiles, sdn);
+}
+template <bool CORR>
+__global__ void __launch_bounds__(256, 4) k_resid_corr(GridDev g, int kc, RArgs a, int tgx, int tgy,
+                                                       int ntiles) {
+    __shared__ double sdn[2 * FLUX_BY * FLUX_BX];
+    resid_tiles<CORR>(g, kc, a, tgx, tgy, ntiles, sdn);
 }
 
 // The correction when no fused residual pass has run (the solve converged
