@@ -292,10 +292,13 @@ __device__ __forceinline__ double face_flux_df(float2 psi_a, float2 psi_b, const
     return __dadd_rn(__dadd_rn(ustar, f32_to_f64_shift(x.x, -sh)), f32_to_f64_shift(x.y, -sh));
 }
 
-// The double-float flux tile: the tile, march, halo and face order of
-// flux_body; phat (as three floats) and psi (as a float pair) of each plane
-// sit in shared memory, and one thread splits the z-face constants a', r' of
-// the plane for the others.
+// The double-float flux tile: the tile, halo and face order of flux_body;
+// phat (as three floats) and psi (as a float pair) of each plane sit in
+// shared memory, and one thread splits the z-face constants a', r' of the
+// plane for the others.  The march is software-pipelined one plane ahead:
+// while plane k is evaluated, the loads of plane k+1's face values u*, v*, w*
+// and halo cell and of the own cell above plane k+1 are in flight, so
+// neither the barrier nor the faces wait on a fresh load.
 template <bool RHO0_IS_G>
 __device__ __forceinline__ void flux_body_df(const GridDev &g, int kc, VB vb, const double *phi,
                                              const double *pn, const double *pnm1, const double *u,
@@ -316,6 +319,7 @@ __device__ __forceinline__ void flux_body_df(const GridDev &g, int kc, VB vb, co
     auto src_i = [&](int ii) { return ii < g.nx ? ii : (g.bcx == BC_PERIODIC ? ii % g.nx : g.nx - 1); };
     auto src_j = [&](int jj) { return jj < g.ny ? jj : (g.bcy == BC_PERIODIC ? jj % g.ny : g.ny - 1); };
     const size_t own = (size_t)src_j(j) * g.nx + src_i(i);
+    const size_t cell = (size_t)(in ? j : 0) * g.nx + (in ? i : 0);
     int hy = -1, hx = -1;
     size_t hoff = 0;
     if (tid < FLUX_BX) {
@@ -326,39 +330,70 @@ __device__ __forceinline__ void flux_body_df(const GridDev &g, int kc, VB vb, co
         hx = FLUX_BX;
     }
     if (hy >= 0) hoff = (size_t)src_j(j0 + hy) * g.nx + src_i(i0 + hx);
-    auto psi = [&](size_t at) {
-        const float2 f = f64_split(phi[at]);
+    // raw FP64 values of one cell (phi, p^n, p^(n-1)) and their split forms
+    struct Raw {
+        double phi, pn, pm;
+    };
+    auto load = [&](size_t at) { return Raw{phi[at], pn[at], pnm1[at]}; };
+    auto psi = [&](const Raw &r) {
+        const float2 f = f64_split(r.phi);
         return RHO0_IS_G ? f : df_add(make_float2(1.f, 0.f), df_neg(f));
     };
-    auto phat = [&](size_t at) { return f64_split3(fmaT(2.0, pn[at], -pnm1[at])); };
+    auto phat = [&](const Raw &r) { return f64_split3(fmaT(2.0, r.pn, -r.pm)); };
+    // the plane above plane kk (periodic z: the seam joins plane 0); -1: none
+    auto above = [&](int kk) { return kk + 1 < g.nz ? kk + 1 : (g.perz ? 0 : -1); };
     const bool var = g.var_rho != 0;
     const int shx = var ? seed_shift(g.frx, g.fsh) : 0, shy = var ? seed_shift(g.fry, g.fsh) : 0;
     const float2 Ax = var ? f64_split_sh(g.fax, shx) : make_float2(0.f, 0.f);
     const float2 Rx = var ? f64_split_sh(g.frx, shx) : make_float2(0.f, 0.f);
     const float2 Ay = var ? f64_split_sh(g.fay, shy) : make_float2(0.f, 0.f);
     const float2 Ry = var ? f64_split_sh(g.fry, shy) : make_float2(0.f, 0.f);
-    float2 psi_c = make_float2(0.f, 0.f);
-    F3 ph_c{0.f, 0.f, 0.f};
     float usq = 0.f;
+    // the pipeline's first stage: plane k0's own cell (split), halo cell and
+    // face values, and the own cell above it; every virtual block holds at
+    // least one plane (k0 < k1 <= nz)
+    const Raw c0 = load((size_t)k0 * plane + own);
+    float2 psi_c = psi(c0);
+    F3 ph_c = phat(c0);
+    Raw hr{0.0, 0.0, 0.0}, tr{0.0, 0.0, 0.0};
+    double uc = 0.0, vc = 0.0, wc = 0.0;
+    if (hy >= 0) hr = load((size_t)k0 * plane + hoff);
+    if (above(k0) >= 0) tr = load((size_t)above(k0) * plane + own);
+    if (in) {
+        const size_t c = (size_t)k0 * plane + cell;
+        uc = u[c];
+        vc = v[c];
+        wc = w[c];
+    }
     for (int k = k0; k < k1; ++k) {
         const size_t base = (size_t)k * plane;
-        if (k == k0) {
-            psi_c = psi(base + own);
-            ph_c = phat(base + own);
+        const int kt = above(k);
+        const bool more = k + 1 < k1;
+        // the next stage's loads
+        Raw hr_n{0.0, 0.0, 0.0}, tr_n{0.0, 0.0, 0.0};
+        double un = 0.0, vn = 0.0, wn = 0.0;
+        if (more) {
+            if (hy >= 0) hr_n = load(base + plane + hoff);
+            if (above(k + 1) >= 0) tr_n = load((size_t)above(k + 1) * plane + own);
+            if (in) {
+                const size_t c = base + plane + cell;
+                un = u[c];
+                vn = v[c];
+                wn = w[c];
+            }
         }
         s_ph[0][ty][tx] = ph_c.h;
         s_ph[1][ty][tx] = ph_c.m;
         s_ph[2][ty][tx] = ph_c.l;
         s_psi[ty][tx] = psi_c;
         if (hy >= 0) {
-            s_psi[hy][hx] = psi(base + hoff);
-            const F3 h3 = phat(base + hoff);
+            s_psi[hy][hx] = psi(hr);
+            const F3 h3 = phat(hr);
             s_ph[0][hy][hx] = h3.h;
             s_ph[1][hy][hx] = h3.m;
             s_ph[2][hy][hx] = h3.l;
         }
-        const bool top_face = k + 1 < g.nz || g.perz;  // periodic z: the seam joins plane 0
-        if (tid == FLUX_BX * FLUX_BY - 1 && var && top_face) {
+        if (tid == FLUX_BX * FLUX_BY - 1 && var && kt >= 0) {
             // r' > 0 on every face that exists; the top wall's zero entry is never split
             const double rz = g.frz[k];
             const int sh = seed_shift(rz, g.fsh);
@@ -366,17 +401,15 @@ __device__ __forceinline__ void flux_body_df(const GridDev &g, int kc, VB vb, co
             s_zc[1] = f64_split_sh(rz, sh);
             s_zsh = sh;
         }
-        __syncthreads();
         float2 psi_t = make_float2(0.f, 0.f);
         F3 ph_t{0.f, 0.f, 0.f};
-        if (top_face) {
-            const size_t nxt = (k + 1 < g.nz) ? base + plane : 0;
-            psi_t = psi(nxt + own);
-            ph_t = phat(nxt + own);
+        if (kt >= 0) {
+            psi_t = psi(tr);
+            ph_t = phat(tr);
         }
+        __syncthreads();
         if (in) {
-            const size_t c = base + (size_t)j * g.nx + i;
-            const double uc = u[c], vc = v[c], wc = w[c];
+            const size_t c = base + cell;
             if (usq_slot) {
                 const float a = abs_scaled_f32(uc), b = abs_scaled_f32(vc), d = abs_scaled_f32(wc);
                 usq = fmaf(a, a, fmaf(b, b, fmaf(d, d, usq)));
@@ -394,11 +427,16 @@ __device__ __forceinline__ void flux_body_df(const GridDev &g, int kc, VB vb, co
             }
             qy[c] = q;
             q = 0.0;
-            if (top_face) q = var ? face_flux_df(psi_c, psi_t, ph_c, ph_t, wc, s_zc[0], s_zc[1], s_zsh) : wc;
+            if (kt >= 0) q = var ? face_flux_df(psi_c, psi_t, ph_c, ph_t, wc, s_zc[0], s_zc[1], s_zsh) : wc;
             qz[c] = q;
         }
         ph_c = ph_t;
         psi_c = psi_t;
+        hr = hr_n;
+        tr = tr_n;
+        uc = un;
+        vc = vn;
+        wc = wn;
         __syncthreads();
     }
     if (usq_slot) {
@@ -436,9 +474,9 @@ __global__ void __launch_bounds__(256) k_flux(GridDev g, int kc, const double *_
 }
 
 // The double-float body (mixed plans, g.flux_df = 1) as a kernel of its own,
-// held to five CTAs per SM (40 warps: its loads wait on latency).
+// held to four CTAs per SM (64 registers for its one-plane-ahead loads).
 template <bool RHO0_IS_G>
-__global__ void __launch_bounds__(256, 5) k_flux_df(GridDev g, int kc, const double *__restrict__ phi,
+__global__ void __launch_bounds__(256, 4) k_flux_df(GridDev g, int kc, const double *__restrict__ phi,
                                                     const double *__restrict__ pn,
                                                     const double *__restrict__ pnm1,
                                                     const double *__restrict__ u,
