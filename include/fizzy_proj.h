@@ -324,7 +324,7 @@ typedef struct fizzy_proj_batch_s *fizzy_proj_batch_t;
 typedef struct fizzy_batch_tuning {
     int ctas_per_sm; /* resident CTAs per SM (256-thread kernels); 0 = as many
                         as fit                                                  */
-    int flux_planes; /* z planes per flux tile, multiple of 16; 0 = 16           */
+    int flux_planes; /* z planes per flux tile, multiple of 32; 0 = 32           */
     int x_lines;     /* x-pass line pairs per tile (1..16); 0 = per-size default */
     int y_cols;      /* y-pass columns per tile (even, 2..32); 0 = default       */
     int order;       /* persistent form's work-list order: 0 pass-major,

@@ -701,7 +701,7 @@ void pass_caps(int *cap, const PassKernels &k, size_t sx64, size_t sx32, size_t 
     cap[CAP_CIF] = resident_grid(k_correct_if, 256, 0);
 }
 
-constexpr int kFluxKc = 16;  // planes marched by one flux CTA
+constexpr int kFluxKc = 32;  // planes marched by one flux CTA
 dim3 flux_grid(int nx, int ny, int nz) {
     return dim3((nx + FLUX_BX - 1) / FLUX_BX, (ny + FLUX_BY - 1) / FLUX_BY, (nz + kFluxKc - 1) / kFluxKc);
 }

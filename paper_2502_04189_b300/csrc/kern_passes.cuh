@@ -1606,7 +1606,7 @@ __global__ void __launch_bounds__(256) k_correct(GridDev g, const double *__rest
 // the left, dS from the row below through shared memory (double-buffered per
 // plane), dB carried from the plane below.  Wall faces carry zero flux.
 // Virtual block: 32 x 8 cells marching kc planes; sdn: 2 x 8 x 32 doubles.
-constexpr int RESID_KC = 16;  // planes marched by one residual tile
+constexpr int RESID_KC = 32;  // planes marched by one residual tile
 
 struct RArgs {
     const double *p, *f, *qx, *qy, *qz;

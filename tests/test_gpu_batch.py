@@ -136,7 +136,7 @@ def test_batch_autotune_keeps_results(cuda_ok):
     batch = F.Batch(plans, arrays)
     tuning, ms = batch.autotune(reps=2)
     assert ms > 0 and tuning["form"] in (0, 1, 2)
-    assert tuning["form"] == 2 or tuning["flux_planes"] in (16, 32)  # solo chains keep the plan's tiles
+    assert tuning["form"] == 2 or tuning["flux_planes"] in (32, 64)  # solo chains keep the plan's tiles
     for c, arr in zip(cases, arrays):
         arr[3].copy_(to_dev(c.u))
         arr[4].copy_(to_dev(c.v))
