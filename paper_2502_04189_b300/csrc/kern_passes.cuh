@@ -1626,8 +1626,9 @@ struct RArgs {
 // FP64) runs in double-float arithmetic on the FP32 pipe, relative error
 // about 2^-44 per operation: |r - r_exact| stays near 1e-13 max|f|, far below
 // the 1e-10 the refinement aims at.  CORR also writes the correction
-// u = q' - (dt/rho0) G p from the same differences (each rounded to FP64,
-// then one FP64 multiply-add per face).  Same tile, order of faces and
+// u = q' - (dt/rho0) G p from the same face values, with the FP64 difference
+// of the FP64 p and one FP64 multiply-add per face (as the FP64 correction
+// forms it; the p values are loaded once for both).  Same tile, order of faces and
 // neighbour exchange as before; sdn holds the float pairs of dN.
 template <bool CORR> struct PVal {
     float h;
@@ -1667,7 +1668,9 @@ __device__ __forceinline__ unsigned long long resid_df_march(
             s_cz[1][t] = f64_split(g.lza[k0 + t]);
         }
     }
-    PV pc = on ? pv(c) : PV::zero();
+    // pcr: the raw FP64 p of the current cell (the correction's differences)
+    double pcr = on ? ldp<CG>(a.p + c) : 0.0;
+    PV pc = PV::load(pcr);
     float2 db = make_float2(0.f, 0.f);
     if (on && k0 > 0) db = pc.minus(pv(c - pl));
     else if (on && g.perz) db = pc.minus(pv(c + (size_t)(g.nz - 1) * pl));  // seam
@@ -1720,9 +1723,10 @@ __device__ __forceinline__ unsigned long long resid_df_march(
             // the correction's stores come after every load of this plane
             // and the next (they could alias the q' loads)
             if (CORR) {
-                a.u[c] = (g.bcx == BC_NEUMANN && i == g.nx - 1) ? 0.0 : fmaT(-g.cgx, df_to_f64(de), qxc);
-                a.v[c] = (g.bcy == BC_NEUMANN && j == g.ny - 1) ? 0.0 : fmaT(-g.cgy, df_to_f64(dn), qyc);
-                a.w[c] = (k < g.nz - 1 || g.perz) ? fmaT(-g.cgz[k], df_to_f64(dt), qzc) : 0.0;
+                // FP64 differences of the FP64 p, as the FP64 correction forms them
+                a.u[c] = (g.bcx == BC_NEUMANN && i == g.nx - 1) ? 0.0 : fmaT(-g.cgx, __dsub_rn(cur.pe, pcr), qxc);
+                a.v[c] = (g.bcy == BC_NEUMANN && j == g.ny - 1) ? 0.0 : fmaT(-g.cgy, __dsub_rn(cur.pn, pcr), qyc);
+                a.w[c] = (k < g.nz - 1 || g.perz) ? fmaT(-g.cgz[k], __dsub_rn(cur.pt, pcr), qzc) : 0.0;
             }
             if (tx == 0) dw = hasW ? pc.minus(PV::load(cur.pw)) : make_float2(0.f, 0.f);
             const float2 ds = (ty > 0) ? sd[(buf * FLUX_BY + ty - 1) * FLUX_BX + tx]
@@ -1738,6 +1742,7 @@ __device__ __forceinline__ unsigned long long resid_df_march(
         }
         db = dt;
         pc = pt;
+        pcr = cur.pt;
         cur = nxt;
         c += pl;
         buf ^= 1;
