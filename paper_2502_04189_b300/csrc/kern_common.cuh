@@ -232,14 +232,6 @@ __device__ __forceinline__ float2 df_div(float2 a, float2 b) {
     return fast_two_sum(q1, __fmul_rn(r, y));
 }
 
-// b - a of two doubles held as exact float triples, in double-float: the
-// three float differences are exact (two-sum), their sum is rounded once per
-// double-float addition (relative error about 2^-47 of the difference).
-__device__ __forceinline__ float2 f3_diff(const F3 &b, const F3 &a) {
-    const float2 d = df_add(two_sum(b.h, -a.h), two_sum(b.m, -a.m));
-    return df_add(d, make_float2(__fsub_rn(b.l, a.l), 0.f));
-}
-
 // Asynchronous global -> shared copies (cp.async, LDGSTS): the copy runs in
 // the background and the issuing thread waits for its own groups.
 template <int BYTES>

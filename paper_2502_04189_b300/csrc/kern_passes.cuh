@@ -265,36 +265,35 @@ __device__ __forceinline__ void flux_body(const GridDev &g, int kc, VB vb, const
     }
 }
 
-// Mixed plans: the same face flux with its split term in double-float on the
-// FP32 pipe.  FP64 issues at 2 instructions per clock per SM against 128 for
-// FP32, and the FP64 body above spends 19 FP64 instructions per cell; here
-// phat = 2 p^n - p^(n-1) keeps its one FP64 FMA per cell (the same value the
-// FP64 body forms) and each face keeps two FP64 additions, q' = (u* + x_hi) +
-// x_lo, for the split term x = kappa (phat_b - phat_a):
+// Mixed plans: the same face flux with its density factor in double-float on
+// the FP32 pipe.  FP64 issues at 2 instructions per clock per SM against 128
+// for FP32, and the FP64 body above spends 19 FP64 instructions per cell;
+// here phat = 2 p^n - p^(n-1) keeps its one FP64 FMA per cell (the same value
+// the FP64 body forms) and each face spends three FP64 instructions,
+// q' = u* + kappa (phat_b - phat_a): the difference, kappa moved to FP64 and
+// the multiply-add, as the FP64 body ends:
 //   * psi (= phi, or 1 - phi when rho0 = rho_l) as a float pair, 2^-47 |phi|;
 //   * t = psi_a + psi_b, s' = a' t + r' and kappa = t / s' in double-float,
 //     with a' and r' scaled by 2^-sh (the seed shift of the FP64 body), which
 //     keeps s' near [2^-fsh, 2^(2+fsh)] and kappa within float range for
-//     every density ratio the plan accepts; x is scaled back by 2^sh when it
-//     is moved to FP64 (integer operations, exact);
-//   * phat_b - phat_a from phat held as the exact sum of three floats
-//     (f64_split3): exact float differences, then double-float sums;
-//   * relative error of x about 2^-44; the pure rho0 phase (psi = 0 on both
-//     sides) gives kappa = 0 and q' = u* exactly, as in the FP64 body.
+//     every density ratio the plan accepts; kappa is scaled back by 2^sh when
+//     its two floats are moved to FP64 (integer operations, exact) and added;
+//   * relative error of kappa about 2^-44, of the difference 2^-53; the pure
+//     rho0 phase (psi = 0 on both sides) gives kappa = 0 and q' = u* exactly,
+//     as in the FP64 body.
 // The divergence identity D(u) = (dt/rho0)(f - L_h p) does not depend on
 // this precision: the right-hand side and the correction read the same
-// stored q'.  Range: |phat| below 2^100 (float range after the products).
-__device__ __forceinline__ double face_flux_df(float2 psi_a, float2 psi_b, const F3 &ph_a, const F3 &ph_b,
+// stored q'.
+__device__ __forceinline__ double face_flux_df(float2 psi_a, float2 psi_b, double ph_a, double ph_b,
                                                double ustar, float2 A, float2 R, int sh) {
     const float2 t = df_add(psi_a, psi_b);
-    const float2 sp = df_add(df_mul(t, A), R);
-    const float2 x = df_mul(df_div(t, sp), f3_diff(ph_b, ph_a));
-    return __dadd_rn(__dadd_rn(ustar, f32_to_f64_shift(x.x, -sh)), f32_to_f64_shift(x.y, -sh));
+    const float2 kap = df_div(t, df_add(df_mul(t, A), R));
+    const double kd = __dadd_rn(f32_to_f64_shift(kap.x, -sh), f32_to_f64_shift(kap.y, -sh));
+    return fmaT(kd, __dsub_rn(ph_b, ph_a), ustar);
 }
 
 // The double-float flux tile: the tile, halo and face order of flux_body;
-// phat (as three floats) and psi (as a float pair) of each plane sit in
-// shared memory, and one thread splits the z-face constants a', r' of the
+// phat (FP64) and psi (as a float pair) of each plane sit in shared memory, and one thread splits the z-face constants a', r' of the
 // plane for the others.  The march is software-pipelined one plane ahead:
 // while plane k is evaluated, the loads of plane k+1's face values u*, v*, w*
 // and halo cell and of the own cell above plane k+1 are in flight, so
@@ -304,7 +303,7 @@ __device__ __forceinline__ void flux_body_df(const GridDev &g, int kc, VB vb, co
                                              const double *pn, const double *pnm1, const double *u,
                                              const double *v, const double *w, double *qx, double *qy,
                                              double *qz, double *usq_slot) {
-    __shared__ float s_ph[3][FLUX_BY + 1][FLUX_BX + 1];
+    __shared__ double s_ph[FLUX_BY + 1][FLUX_BX + 1];
     __shared__ float2 s_psi[FLUX_BY + 1][FLUX_BX + 1];
     __shared__ float2 s_zc[2];
     __shared__ int s_zsh;
@@ -339,7 +338,7 @@ __device__ __forceinline__ void flux_body_df(const GridDev &g, int kc, VB vb, co
         const float2 f = f64_split(r.phi);
         return RHO0_IS_G ? f : df_add(make_float2(1.f, 0.f), df_neg(f));
     };
-    auto phat = [&](const Raw &r) { return f64_split3(fmaT(2.0, r.pn, -r.pm)); };
+    auto phat = [&](const Raw &r) { return fmaT(2.0, r.pn, -r.pm); };
     // the plane above plane kk (periodic z: the seam joins plane 0); -1: none
     auto above = [&](int kk) { return kk + 1 < g.nz ? kk + 1 : (g.perz ? 0 : -1); };
     const bool var = g.var_rho != 0;
@@ -354,7 +353,7 @@ __device__ __forceinline__ void flux_body_df(const GridDev &g, int kc, VB vb, co
     // least one plane (k0 < k1 <= nz)
     const Raw c0 = load((size_t)k0 * plane + own);
     float2 psi_c = psi(c0);
-    F3 ph_c = phat(c0);
+    double ph_c = phat(c0);
     Raw hr{0.0, 0.0, 0.0}, tr{0.0, 0.0, 0.0};
     double uc = 0.0, vc = 0.0, wc = 0.0;
     if (hy >= 0) hr = load((size_t)k0 * plane + hoff);
@@ -382,16 +381,11 @@ __device__ __forceinline__ void flux_body_df(const GridDev &g, int kc, VB vb, co
                 wn = w[c];
             }
         }
-        s_ph[0][ty][tx] = ph_c.h;
-        s_ph[1][ty][tx] = ph_c.m;
-        s_ph[2][ty][tx] = ph_c.l;
+        s_ph[ty][tx] = ph_c;
         s_psi[ty][tx] = psi_c;
         if (hy >= 0) {
             s_psi[hy][hx] = psi(hr);
-            const F3 h3 = phat(hr);
-            s_ph[0][hy][hx] = h3.h;
-            s_ph[1][hy][hx] = h3.m;
-            s_ph[2][hy][hx] = h3.l;
+            s_ph[hy][hx] = phat(hr);
         }
         if (tid == FLUX_BX * FLUX_BY - 1 && var && kt >= 0) {
             // r' > 0 on every face that exists; the top wall's zero entry is never split
@@ -402,7 +396,7 @@ __device__ __forceinline__ void flux_body_df(const GridDev &g, int kc, VB vb, co
             s_zsh = sh;
         }
         float2 psi_t = make_float2(0.f, 0.f);
-        F3 ph_t{0.f, 0.f, 0.f};
+        double ph_t = 0.0;
         if (kt >= 0) {
             psi_t = psi(tr);
             ph_t = phat(tr);
@@ -416,14 +410,12 @@ __device__ __forceinline__ void flux_body_df(const GridDev &g, int kc, VB vb, co
             }
             double q = 0.0;
             if (!(g.bcx == BC_NEUMANN && i == g.nx - 1)) {
-                const F3 pe{s_ph[0][ty][tx + 1], s_ph[1][ty][tx + 1], s_ph[2][ty][tx + 1]};
-                q = var ? face_flux_df(psi_c, s_psi[ty][tx + 1], ph_c, pe, uc, Ax, Rx, shx) : uc;
+                q = var ? face_flux_df(psi_c, s_psi[ty][tx + 1], ph_c, s_ph[ty][tx + 1], uc, Ax, Rx, shx) : uc;
             }
             qx[c] = q;
             q = 0.0;
             if (!(g.bcy == BC_NEUMANN && j == g.ny - 1)) {
-                const F3 pnb{s_ph[0][ty + 1][tx], s_ph[1][ty + 1][tx], s_ph[2][ty + 1][tx]};
-                q = var ? face_flux_df(psi_c, s_psi[ty + 1][tx], ph_c, pnb, vc, Ay, Ry, shy) : vc;
+                q = var ? face_flux_df(psi_c, s_psi[ty + 1][tx], ph_c, s_ph[ty + 1][tx], vc, Ay, Ry, shy) : vc;
             }
             qy[c] = q;
             q = 0.0;
