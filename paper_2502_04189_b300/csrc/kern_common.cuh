@@ -232,6 +232,29 @@ __device__ __forceinline__ float2 df_div(float2 a, float2 b) {
     return fast_two_sum(q1, __fmul_rn(r, y));
 }
 
+// A normalized float pair hi + lo (|lo| <= half an ulp of hi) times 2^-es
+// as one double, integer operations only: hi moves to FP64 exactly and lo is
+// added as an integer count of that double's last places, k = lo 2^(52 - e)
+// for hi = 1.m 2^e (|k| <= 2^28, truncated toward zero: relative error below
+// 2^-52).  The one case whose sum leaves hi's binade is hi a power of two and
+// lo of the other sign: there the lower binade's places are half as large
+// and the count doubles.  hi below the float normal range gives 0, as
+// f32_to_f64_shift does.
+__device__ __forceinline__ double df_pair_to_f64_shift(float2 d, int es) {
+    const double h = f32_to_f64_shift(d.x, es);
+    const unsigned bh = __float_as_uint(d.x), bl = __float_as_uint(d.y);
+    const unsigned al = bl & 0x7fffffffu;
+    if (al < 0x00800000u || (bh & 0x7fffffffu) < 0x00800000u) return h;
+    const int s = (int)(al >> 23) - (int)((bh >> 23) & 0xffu) + 29;
+    if (s < -24) return h;  // lo below the double's last place
+    const unsigned ml = (al & 0x7fffffu) | 0x800000u;
+    long long k = (long long)(s >= 0 ? (ml << s) : (ml >> -s));
+    const bool opposite = ((bh ^ bl) & 0x80000000u) != 0;
+    if (opposite && (bh & 0x7fffffu) == 0u) k <<= 1;  // hi a power of two, sum below it
+    const long long hb = __double_as_longlong(h);
+    return __longlong_as_double(opposite ? hb - k : hb + k);
+}
+
 // Asynchronous global -> shared copies (cp.async, LDGSTS): the copy runs in
 // the background and the issuing thread waits for its own groups.
 template <int BYTES>

@@ -269,15 +269,16 @@ __device__ __forceinline__ void flux_body(const GridDev &g, int kc, VB vb, const
 // the FP32 pipe.  FP64 issues at 2 instructions per clock per SM against 128
 // for FP32, and the FP64 body above spends 19 FP64 instructions per cell;
 // here phat = 2 p^n - p^(n-1) keeps its one FP64 FMA per cell (the same value
-// the FP64 body forms) and each face spends three FP64 instructions,
-// q' = u* + kappa (phat_b - phat_a): the difference, kappa moved to FP64 and
-// the multiply-add, as the FP64 body ends:
+// the FP64 body forms) and each face spends two FP64 instructions,
+// q' = u* + kappa (phat_b - phat_a): the difference and the multiply-add, as
+// the FP64 body ends:
 //   * psi (= phi, or 1 - phi when rho0 = rho_l) as a float pair, 2^-47 |phi|;
 //   * t = psi_a + psi_b, s' = a' t + r' and kappa = t / s' in double-float,
 //     with a' and r' scaled by 2^-sh (the seed shift of the FP64 body), which
 //     keeps s' near [2^-fsh, 2^(2+fsh)] and kappa within float range for
 //     every density ratio the plan accepts; kappa is scaled back by 2^sh when
-//     its two floats are moved to FP64 (integer operations, exact) and added;
+//     its two floats are merged into one double (integer operations,
+//     df_pair_to_f64_shift);
 //   * relative error of kappa about 2^-44, of the difference 2^-53; the pure
 //     rho0 phase (psi = 0 on both sides) gives kappa = 0 and q' = u* exactly,
 //     as in the FP64 body.
@@ -288,7 +289,7 @@ __device__ __forceinline__ double face_flux_df(float2 psi_a, float2 psi_b, doubl
                                                double ustar, float2 A, float2 R, int sh) {
     const float2 t = df_add(psi_a, psi_b);
     const float2 kap = df_div(t, df_add(df_mul(t, A), R));
-    const double kd = __dadd_rn(f32_to_f64_shift(kap.x, -sh), f32_to_f64_shift(kap.y, -sh));
+    const double kd = df_pair_to_f64_shift(kap, -sh);
     return fmaT(kd, __dsub_rn(ph_b, ph_a), ustar);
 }
 
