@@ -132,16 +132,16 @@ def fp64_instr_per_point(nx, ny, bcx, bcy, mixed, bcz=1):
     (the Sherman-Morrison dot product and correction); correction 6).  Mixed
     plans run the flux's density factor, the first x-pass's divergence and
     the residuals in double-float on the FP32 pipe: the flux keeps phat (1
-    per cell) and 3 per face (the phat difference, kappa moved to FP64, the
-    multiply-add), the divergence 1 (f moved to FP64), the first residual
-    none, and the one fused with the correction 2 per face (the FP64
-    difference of p, the multiply-add)."""
+    per cell) and 2 per face (the phat difference and the multiply-add;
+    kappa is merged into a double with integer operations), the divergence
+    1 (f moved to FP64), the first residual none, and the one fused with the
+    correction 2 per face (the FP64 difference of p, the multiply-add)."""
     fx = fft_fp64_instr_per_point(nx, bcx == 1)
     fy = fft_fp64_instr_per_point(ny, bcy == 1)
     if not mixed:
         return {"flux": 19, "div_fwdx": 6 + fx, "fwd_y": fy, "thomas": 5 if bcz == 0 else 3, "inv_y": fy,
                 "inv_x": fx, "correct": 6}
-    return {"flux": 10, "div_fwdx": 1, "resid": 0, "resid_correct": 6, "inv_x_update": 1,
+    return {"flux": 7, "div_fwdx": 1, "resid": 0, "resid_correct": 6, "inv_x_update": 1,
             "correct": 6}
 
 

@@ -42,9 +42,9 @@ def test_mixed_path_counts_each_sweep():
     assert two["bytes_per_pt"] - one["bytes_per_pt"] == sweep
     # with no sweep the stand-alone correction runs instead of the fused one
     assert one["bytes_per_pt"] - none["bytes_per_pt"] == sweep - per["correct"][0]
-    # mixed: double-float flux (10), divergence (1) and first residual (0)
-    assert one["fp64_instr_per_pt"] == 10 + 1 + 0 + 1 + 6
-    assert none["fp64_instr_per_pt"] == 10 + 1 + 0 + 6
+    # mixed: double-float flux (7), divergence (1) and first residual (0)
+    assert one["fp64_instr_per_pt"] == 7 + 1 + 0 + 1 + 6
+    assert none["fp64_instr_per_pt"] == 7 + 1 + 0 + 6
     assert one["io_floor_bytes_per_pt"] == 80
 
 
@@ -67,12 +67,12 @@ def test_dominant_roofline_against_measured_dfma_rate():
     assert r["fp64_issue"]["frac"] == pytest.approx(19 * n / (t_ms * 1e-3) / dfma)
     assert r["hbm_gbs"] == pytest.approx(72 * n / (t_ms * 1e-3) / 1e9)
     assert r["traffic"] is None
-    # the mixed plans' double-float flux reports against HBM, its 10 FP64
+    # the mixed plans' double-float flux reports against HBM, its 7 FP64
     # instructions per point beside it
     r = bench.dominant_roofline("flux", (t_ms * 20, 20), st, 20, True, 4, spec, n, 6504.1, "m", dfma,
                                 "no-such-workload")
     assert r["bound"] == "hbm" and r["frac"] == pytest.approx(72 * n / (t_ms * 1e-3) / 1e9 / 6504.1)
-    assert r["fp64_issue"]["frac"] == pytest.approx(10 * n / (t_ms * 1e-3) / dfma)
+    assert r["fp64_issue"]["frac"] == pytest.approx(7 * n / (t_ms * 1e-3) / dfma)
     # a refinement kernel counts only the launches of sweeps that ran
     r2 = bench.dominant_roofline("thomas_refine", (1.0, 80), st, 20, True, 4, spec, n, 6504.1, "m",
                                  dfma, "no-such-workload")
