@@ -142,6 +142,16 @@ __device__ __forceinline__ double f32_to_f64_shift(float f, int es) {
     return __hiloint2double((int)(hi | (b & 0x80000000u)), (int)(a << 29));
 }
 
+// f 2^-es for a float, as f64_to_f32_shift(f32_to_f64_shift(f, 0), es)
+// gives it (integer operations): float denormals and results below 2^-126
+// flush to a signed zero.
+__device__ __forceinline__ float f32_shift(float f, int es) {
+    const unsigned b = __float_as_uint(f), a = b & 0x7fffffffu;
+    const int ne = (int)(a >> 23) - es;
+    if (a < 0x00800000u || ne <= 0) return __uint_as_float(b & 0x80000000u);
+    return __uint_as_float(((unsigned)ne << 23) | (a & 0x7fffffu) | (b & 0x80000000u));
+}
+
 // Double-float arithmetic (an unevaluated sum hi + lo of two floats, about
 // 48 significant bits): Knuth's two-sum, Dekker's fast two-sum and the
 // FMA-based exact product, written with explicit round-to-nearest

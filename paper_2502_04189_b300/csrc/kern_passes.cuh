@@ -1686,7 +1686,7 @@ __device__ __forceinline__ unsigned long long resid_df_march(
     };
     Ahead cur{0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
     if (on) cur = load_ahead(c, k0);
-    unsigned long long mx = 0ull;
+    unsigned mxf = 0u;  // max |r| as float bits (monotone in |r|)
     int buf = 0;
     for (int k = k0; k < k1; ++k) {
         Ahead nxt{0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
@@ -1730,8 +1730,8 @@ __device__ __forceinline__ unsigned long long resid_df_march(
             res = df_add(res, df_mul(dt, s_cz[0][k - k0]));
             res = df_add(res, df_mul(db, s_cz[1][k - k0]));
             const float r = __fadd_rn(res.x, res.y);
-            mx = umax64(mx, absbits(f32_to_f64_shift(r, 0)));
-            a.r32[c] = f64_to_f32_shift(f32_to_f64_shift(r, 0), ef) * scale32;
+            mxf = max(mxf, absbits(r));
+            a.r32[c] = f32_shift(r, ef) * scale32;
         }
         db = dt;
         pc = pt;
@@ -1740,7 +1740,7 @@ __device__ __forceinline__ unsigned long long resid_df_march(
         c += pl;
         buf ^= 1;
     }
-    return mx;
+    return absbits(f32_to_f64_shift(__uint_as_float(mxf), 0));
 }
 
 template <bool CG, bool CORR>
